@@ -1,0 +1,115 @@
+"""Per-point material law of the diffuse-interface model (test infrastructure, see package docstring).
+
+Every function evaluates the paper's formula literally, on arrays of level-set values / gradients:
+  distance   d(phi) = eps log((1 + phi) / (1 - phi))                                   Eq. (distance)
+  heaviside  H = 0 (d <= -3 eps), 1/2 + d/(6 eps) + sin(pi d / (3 eps)) / (2 pi), 1 (d >= 3 eps)   Eq. (heaviside)
+  delta      delta = |grad H(phi)| = H'(d) d'(phi) |grad phi|                          Eq. (delta)
+  density    1/rho = H/rho_l + (1 - H)/rho_g  (reciprocal)                             Eq. (rhoEff)
+  viscosity  mu = H mu_l + (1 - H) mu_g                                                Eq. (muEff)
+  normal     n = grad phi / |grad phi|                                                 Eq. (normal_vector)
+  dilation   v = mdot (1/rho_l - 1/rho_g) delta                                        Eq. (evaporDil)
+
+Reading of the branch boundaries (the paper's cases are in d; d(phi) is increasing): the interface zone
+0 < H < 1 is |phi| < tanh(3/2), i.e. -3 eps < d < 3 eps.  Outside it H is 0 or 1, its derivatives vanish and the
+logarithm is never evaluated (|phi| may round to 1 there).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+PHI_BAND = np.tanh(1.5)  # phi at d = 3 eps, Eq. (initial_phi) evaluated at d = 3 eps
+
+
+def distance(phi, eps):
+    """Signed distance recovered from the regularized level set, Eq. (distance)."""
+    phi = np.asarray(phi, dtype=float)
+    return eps * np.log((1.0 + phi) / (1.0 - phi))
+
+
+def in_zone(phi):
+    """Interface zone 0 < H < 1 (equivalently -3 eps < d(phi) < 3 eps)."""
+    return np.abs(np.asarray(phi, dtype=float)) < PHI_BAND
+
+
+def heaviside_parts(phi, eps):
+    """Returns (H, dH/dd, d^2H/dd^2, d, zone) at every point; derivatives are zero outside the zone."""
+    phi = np.asarray(phi, dtype=float)
+    zone = in_zone(phi)
+    H = np.where(phi >= PHI_BAND, 1.0, 0.0)
+    dH = np.zeros_like(phi)
+    d2H = np.zeros_like(phi)
+    d = np.zeros_like(phi)
+    pz = phi[zone]
+    dz = distance(pz, eps)
+    arg = np.pi * dz / (3.0 * eps)
+    H[zone] = 0.5 + dz / (6.0 * eps) + np.sin(arg) / (2.0 * np.pi)
+    dH[zone] = (1.0 + np.cos(arg)) / (6.0 * eps)
+    d2H[zone] = -np.pi * np.sin(arg) / (18.0 * eps * eps)
+    d[zone] = dz
+    return H, dH, d2H, d, zone
+
+
+def heaviside(phi, eps):
+    return heaviside_parts(phi, eps)[0]
+
+
+def ddist_dphi(phi, eps):
+    """d'(phi) = 2 eps / (1 - phi^2)."""
+    phi = np.asarray(phi, dtype=float)
+    return 2.0 * eps / (1.0 - phi * phi)
+
+
+def d2dist_dphi2(phi, eps):
+    """d''(phi) = 4 eps phi / (1 - phi^2)^2."""
+    phi = np.asarray(phi, dtype=float)
+    return 4.0 * eps * phi / (1.0 - phi * phi) ** 2
+
+
+def density(H, rho_l, rho_g, mode="reciprocal"):
+    """Effective density: reciprocal interpolation Eq. (rhoEff); mode 'arithmetic' is the contrast case of Sec. 3.1."""
+    H = np.asarray(H, dtype=float)
+    if mode == "arithmetic":
+        return H * rho_l + (1.0 - H) * rho_g
+    return 1.0 / (H / rho_l + (1.0 - H) / rho_g)
+
+
+def viscosity(H, mu_l, mu_g):
+    """Effective dynamic viscosity, Eq. (muEff)."""
+    H = np.asarray(H, dtype=float)
+    return H * mu_l + (1.0 - H) * mu_g
+
+
+def normal(grad_phi):
+    """Unit normal of Eq. (normal_vector), grad_phi[..., 3]; zero where the gradient vanishes exactly."""
+    g = np.asarray(grad_phi, dtype=float)
+    nrm = np.sqrt(np.sum(g * g, axis=-1, keepdims=True))
+    out = np.zeros_like(g)
+    nz = nrm[..., 0] > 0.0
+    out[nz] = g[nz] / nrm[nz]
+    return out
+
+
+def delta(phi, grad_phi, eps):
+    """Regularized Dirac delta |grad H(phi)| of Eq. (delta) (chain rule through d(phi))."""
+    phi = np.asarray(phi, dtype=float)
+    _, dH, _, _, zone = heaviside_parts(phi, eps)
+    g = np.sqrt(np.sum(np.asarray(grad_phi, dtype=float) ** 2, axis=-1))
+    out = np.zeros_like(phi)
+    out[zone] = dH[zone] * ddist_dphi(phi[zone], eps) * g[zone]
+    return out
+
+
+def dilation_rate(mdot, phi, grad_phi, eps, rho_l, rho_g):
+    """Regularized evaporative dilation rate, Eq. (evaporDil)."""
+    return np.asarray(mdot, dtype=float) * (1.0 / rho_l - 1.0 / rho_g) * delta(phi, grad_phi, eps)
+
+
+def corrected_strain(eps_tensor, n, active=True):
+    """Corrected rate of deformation, Eq. (modified_rate_of_deformation): eps - tr(eps) n (x) n.
+
+    eps_tensor[..., d, d], n[..., d]; ``active`` gates the correction (interface zone)."""
+    e = np.asarray(eps_tensor, dtype=float)
+    tr = np.trace(e, axis1=-2, axis2=-1)
+    corr = tr[..., None, None] * n[..., :, None] * n[..., None, :]
+    act = np.asarray(active, dtype=float)
+    return e - act[..., None, None] * corr if act.ndim else e - act * corr
