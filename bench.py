@@ -1,0 +1,383 @@
+"""Benchmark of the matrix-free evaporation hot path on GB300.
+
+One step = one pass of the whole hot path over the 64^3-cell four-sphere workload (Q2 velocity, 6.44 M velocity
+DoFs, 275 k level-set DoFs, density ratio 1e3, random-Fourier velocity):
+  set_fields (material law table + variant-2 transport velocity with closest-point projection)
+  -> momentum apply FP64 with divergence row -> momentum apply FP32 -> level-set advect / reinit / reinit RHS (FP64)
+  -> adjoint apply (all four gradients) -> mixed-precision GMRES(30) solve to 1e-10.
+value = velocity DoFs per step / step time (GDoF/s of the whole pass); per-operator GDoF/s, bytes and the roofline
+of the dominant kernel are reported beside it.  Inputs (~0.5 GB touched per step) exceed the 129 MB L2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun every rank runs an independent replica (weak scaling, no collective on the data path); rank 0 prints
+one JSON line.  --impl reference times the CPU oracle on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+WORKLOAD = "spheres64"
+METRIC = "operator-apply GDoF/s and %HBM roofline (FP64 vs FP32-inner) + adjoint GDoF/s"
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(path)), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# Nominal FP64 rate of GB300 (profiling recipe table: 1.25 TFLOP/s); the FP64 FMA probe measured 1.19 TFLOP/s.
+FP64_PEAK_TFLOPS = 1.25
+
+
+def algorithmic_counts(n: int, p: int):
+    """Algorithmic bytes and flops per apply (minimal traffic: every nodal vector read/written once; sum
+    factorization flop count of the kernels' arithmetic)."""
+    M = p * n + 1
+    Nu, Np, nc = M ** 3, (n + 1) ** 3, n ** 3
+    Q = p + 1
+    nq = Q ** 3
+    sweep = Q * nq                        # multiply-adds of one 1D sweep over a cell
+    # per component: 3 value sweeps + 3 collocation-gradient sweeps (interpolation); same transposed for testing
+    interp = 6 * sweep
+    flux = 60 * nq                        # F and T at a point (mass, convection, Newton, sym grad, correction)
+    mom_flop = 2 * nc * (3 * interp + 3 * interp + 3 * interp) + 2 * nc * flux
+    adj_flop = 2 * nc * (3 * interp * 3 + 6 * interp) + 2 * nc * 3 * flux
+    return dict(
+        Nu=Nu, Np=Np, ncell=nc,
+        mom64_bytes=8 * (3 * Nu * 3 + 2 * Np),          # x, u0, y, phi, mdot
+        mom32_bytes=4 * 9 * Nu + 8 * 2 * Np,
+        mom_flop=mom_flop,
+        ls_adv_bytes=8 * (Np + Np + 3 * Np),
+        ls_reinit_bytes=8 * 3 * Np,
+        adj_bytes=8 * (3 * Nu * 5 + 5 * Np),            # x, w, u0 in; g_x, g_u0 out; phi, mdot, w_p in; g_phi, g_mdot out
+        adj_flop=adj_flop,
+    )
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_info():
+    cores = os.cpu_count()
+    try:
+        model = [l for l in open("/proc/cpuinfo") if l.lower().startswith(("model name", "cpu part"))][0].split(":")[1]
+        model = model.strip()
+    except Exception:
+        model = "unknown"
+    return cores, model
+
+
+def oracle_sample(wl, nb: int = 8, reps: int = 1):
+    """Time the CPU oracle on a bounded sample: every hot-path row of an nb^3-cell sub-block of the workload
+    (momentum element matrices and apply with divergence rows, transport velocity of the sub-block's band nodes,
+    level-set advect/reinit/reinit-RHS, adjoint parameter gradients).  Returns (seconds, velocity DoFs covered)."""
+    from oracle import adjoint, fe, levelset, momentum, transport
+    n = wl.n
+    mesh = fe.Mesh(n, wl.p, wl.L)
+    pb = momentum.Problem.from_workload(wl)
+    c0 = n // 2 - nb // 2
+    r = np.arange(c0, c0 + nb)
+    Z, Y, X = np.meshgrid(r, r, r, indexing="ij")
+    cells = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+    du = np.unique(mesh.dofs_u(cells))
+    d1 = np.unique(mesh.dofs_phi(cells))
+    rng = np.random.default_rng(0)
+    w = rng.uniform(-1, 1, wl.x.shape)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        momentum.apply_rows(pb, wl.x, du)
+        momentum.divergence_rows(pb, wl.x, d1)
+        band = d1[(wl.phi[d1] > -workloads_tanh3()) & (wl.phi[d1] < np.tanh(1.5))]
+        transport.transport_velocity(mesh, wl.phi, wl.u0, wl.mdot, wl.params, nodes=band[: max(1, len(band) // 4)])
+        sub = fe.Mesh(nb, 1, nb * mesh.h)
+        ug = np.zeros(3 * sub.n_phi)
+        phis = rng.uniform(-1, 1, sub.n_phi)
+        for mode in ("advect", "reinit", "reinit_rhs"):
+            levelset.apply(sub, mode, phis, phis, ug, wl.params)
+        sub_wl = workloads.random_workload(nb, p=wl.p, seed=1)
+        sub_pb = momentum.Problem.from_workload(sub_wl)
+        adjoint.param_gradients(sub_pb, sub_wl.x, sub_wl.x, np.ones(sub_pb.mesh.n_phi))
+    dt = (time.perf_counter() - t0) / reps
+    return dt, 3 * len(du)
+
+
+def workloads_tanh3():
+    return float.fromhex("0x1.fd77d111a0b00p-1")
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle, timed on a bounded sample per step (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = workloads.make_workload(WORKLOAD)
+    for _ in range(args.warmup):
+        oracle_sample(wl, nb=4)
+    times = []
+    dofs = 0
+    for _ in range(args.steps):
+        dt, dofs = oracle_sample(wl, nb=6)
+        times.append(dt)
+    t = float(np.sum(times))
+    value = dofs * args.steps / t / 1e9
+    cores, model = cpu_info()
+    out = dict(impl="reference", metric=METRIC, value=value, unit="GDoF/s", n_gpus=args.gpus, steps=args.steps,
+               warmup=args.warmup, ms_per_step=1e3 * t / args.steps, higher_is_better=True, scaling="weak",
+               vs_baseline=None, dtype="f64", data="synthetic",
+               config=dict(workload="spheres64: 64^3 cells, Q2 velocity, 4 random spheres, density ratio 1e3, "
+                                    "random-Fourier velocity (seed 2)", sample="6^3-cell sub-block per step",
+                           l2="sample fits in host caches (CPU)"),
+               cpu_baseline=dict(value=value, unit="GDoF/s", cores=1, kind="oracle",
+                                 sample="all hot-path rows of a 6^3-cell sub-block of the 64^3 workload",
+                                 cpu=model),
+               e2e=dict(value=value, unit="GDoF/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--profile", action="store_true", help="fewer host syncs; for ncu launch lists")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    import paper_2401_07805_gb300 as evap
+    from paper_2401_07805_gb300 import build
+    if not os.path.exists(evap.library_path()):
+        build.build()
+
+    wl = workloads.make_workload(WORKLOAD)
+    counts = algorithmic_counts(wl.n, wl.p)
+    dev = torch.device("cuda", local)
+    op = evap.Operator(wl.n, wl.p, wl.L, dict(wl.params))
+    rng = np.random.default_rng(100 + rank)
+    host = dict(phi=wl.phi, u0=wl.u0, mdot=wl.mdot, x=wl.x, w=rng.uniform(-1, 1, wl.x.shape),
+                wp=rng.uniform(-1, 1, wl.phi.shape), psi=wl.phi.copy(), f=rng.uniform(-1, 1, wl.x.shape))
+    d = {k: torch.from_numpy(v).to(dev) for k, v in host.items()}
+    d["x32"] = d["x"].float()
+    stream = torch.cuda.current_stream()
+    names = ["set_fields", "mom64", "mom32", "ls_advect", "ls_reinit", "ls_rhs", "adjoint", "solve"]
+    solve_info = {}
+
+    def step(dd, ev=None):
+        def mark(i):
+            if ev is not None:
+                ev[i].record(stream)
+        mark(0)
+        op.set_fields(dd["phi"], dd["u0"], dd["mdot"])
+        mark(1)
+        y, yp = op.apply_momentum(dd["x"], prec=64, with_divergence=True)
+        mark(2)
+        y32 = op.apply_momentum(dd["x32"], prec=32)
+        mark(3)
+        la = op.apply_levelset(dd["psi"], mode="advect")
+        mark(4)
+        lr = op.apply_levelset(dd["psi"], mode="reinit")
+        mark(5)
+        lh = op.apply_levelset(dd["psi"], mode="reinit_rhs")
+        mark(6)
+        g = op.apply_adjoint(dd["w"], dd["x"], dd["wp"])
+        mark(7)
+        xs, info = op.solve(dd["f"], mixed=True, restart=30, rtol=1e-10, max_iter=400)
+        mark(8)
+        solve_info.update(info)
+        return dict(y=y, yp=yp, y32=y32, la=la, lr=lr, lh=lh, gx=g["x"], gu=g["u0"], gphi=g["phi"], gm=g["mdot"], xs=xs)
+
+    for _ in range(args.warmup):
+        step(d)
+    torch.cuda.synchronize()
+    K = args.steps
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(9)] for _ in range(K)]
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = evap.launch_count()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for k in range(K):
+        step(d, evs[k])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    launches = evap.launch_count() - l0
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms_total = t_start.elapsed_time(t_end)
+    if world > 1:
+        tt = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_total = float(tt.item())
+    ms_step = ms_total / K
+    part = {nm: float(np.mean([evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(K)])) for i, nm in enumerate(names)}
+    Nu3 = 3 * counts["Nu"]
+    value = world * Nu3 / (ms_step * 1e-3) / 1e9
+
+    # end to end: pinned host inputs copied in and all results copied out inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        pinned = {k: torch.from_numpy(v).pin_memory() for k, v in host.items()}
+        outs_host = None
+        h2d = sum(v.numel() * v.element_size() for v in pinned.values()) + d["x32"].numel() * 4
+        for it in range(args.warmup + K):
+            if it == args.warmup:
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            dd = {k: v.to(dev, non_blocking=True) for k, v in pinned.items()}
+            dd["x32"] = dd["x"].float()
+            outs = step(dd)
+            if outs_host is None:
+                outs_host = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in outs.items()}
+            for k, v in outs.items():
+                outs_host[k].copy_(v, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        d2h = sum(v.numel() * v.element_size() for v in outs_host.values())
+        e_ms = e0.elapsed_time(e1) / K
+        if world > 1:
+            tt = torch.tensor([e_ms], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e_ms = float(tt.item())
+        e2e = dict(value=world * Nu3 / (e_ms * 1e-3) / 1e9, unit="GDoF/s", ms_per_step=e_ms,
+                   h2d_bytes_per_step=int(h2d), d2h_bytes_per_step=int(d2h))
+
+    peaks, peak_src = load_peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    # dominant kernel: the FP64 momentum apply (FP64-pipe bound); alu roofline against FP64 peak
+    t_mom = part["mom64"] * 1e-3
+    mom_tflops = counts["mom_flop"] / t_mom / 1e12
+    breakdown = {
+        "set_fields_ms": part["set_fields"],
+        "momentum_fp64": dict(ms=part["mom64"], gdofs=Nu3 / (part["mom64"] * 1e-3) / 1e9,
+                              gbs=counts["mom64_bytes"] / (part["mom64"] * 1e-3) / 1e9,
+                              hbm_frac=counts["mom64_bytes"] / (part["mom64"] * 1e-3) / 1e9 / hbm,
+                              fp64_tflops=mom_tflops),
+        "momentum_fp32": dict(ms=part["mom32"], gdofs=Nu3 / (part["mom32"] * 1e-3) / 1e9,
+                              gbs=counts["mom32_bytes"] / (part["mom32"] * 1e-3) / 1e9,
+                              hbm_frac=counts["mom32_bytes"] / (part["mom32"] * 1e-3) / 1e9 / hbm),
+        "levelset_advect": dict(ms=part["ls_advect"], gdofs=counts["Np"] / (part["ls_advect"] * 1e-3) / 1e9),
+        "levelset_reinit": dict(ms=part["ls_reinit"], gdofs=counts["Np"] / (part["ls_reinit"] * 1e-3) / 1e9),
+        "levelset_reinit_rhs": dict(ms=part["ls_rhs"], gdofs=counts["Np"] / (part["ls_rhs"] * 1e-3) / 1e9),
+        "adjoint": dict(ms=part["adjoint"], gdofs=Nu3 / (part["adjoint"] * 1e-3) / 1e9,
+                        fp64_tflops=counts["adj_flop"] / (part["adjoint"] * 1e-3) / 1e12),
+        "solve_mixed": dict(ms=part["solve"], iters=solve_info.get("iters"), relres=solve_info.get("relres")),
+    }
+    roofline = dict(bound="alu", kernel="k_momentum<double,2,8> (FP64 apply)", achieved=mom_tflops,
+                    peak=FP64_PEAK_TFLOPS, unit="TFLOP/s", frac=mom_tflops / FP64_PEAK_TFLOPS,
+                    traffic=None, peak_source="nominal FP64 rate of the profiling recipe (probe measured 1.19)",
+                    hbm=dict(achieved=breakdown["momentum_fp64"]["gbs"], peak=hbm, unit="GB/s",
+                             frac=breakdown["momentum_fp64"]["hbm_frac"], source=peak_src))
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        reps = 1
+        dt, dofs = oracle_sample(wl, nb=6, reps=reps)
+        cores, model = cpu_info()
+        cpu = dict(value=dofs / dt / 1e9, unit="GDoF/s", cores=1, kind="oracle",
+                   sample="all hot-path rows of a 6^3-cell sub-block of the 64^3 workload (numpy, single thread)",
+                   seconds=dt, cpu=model, host_cores=cores)
+    if rank == 0:
+        out = dict(metric=METRIC, value=value, unit="GDoF/s", n_gpus=world, steps=K, warmup=args.warmup,
+                   ms_per_step=ms_step, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
+                   data="synthetic",
+                   config=dict(workload="spheres64: 64^3 cells, Q2 velocity (6.44 M DoFs), Q1 level set (275 k "
+                                        "DoFs), 4 random spheres, density ratio 1e3, random-Fourier velocity",
+                               step="set_fields + FP64/FP32 momentum + 3 level-set applies + adjoint + mixed solve",
+                               l2="inputs larger than L2 (no flush)", parallelism=f"replicas x{world}"),
+                   roofline=roofline, breakdown=breakdown, cpu_baseline=cpu, e2e=e2e, gpu_launches=int(launches),
+                   clocks=clocks)
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

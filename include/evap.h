@@ -1,0 +1,150 @@
+/*
+ * evap.h - C ABI of the GB300 matrix-free operators of the diffuse-interface evaporation model
+ *          (Schreter-Fleischhacker et al., "A consistent diffuse-interface model for two-phase flow problems
+ *          with rapid evaporation", arXiv 2401.07805).
+ *
+ * The library applies, cell by cell and without assembling matrices (Sec. 2.5: y = sum_i R_i^T A_i R_i x), the
+ * finite element operators of the model on a uniform n^3 hexahedral mesh of [0, L]^3:
+ *   - the linearized momentum operator for Q_p velocity (p = 2 or 3): mass/dt + Newton convection + viscous
+ *     stress with the corrected rate of deformation (Eqs. modified_rate_of_deformation, modified_viscous_stress),
+ *     with the reciprocal density (Eq. rhoEff) and arithmetic viscosity (Eq. muEff), plus the divergence row
+ *     with the evaporation source (Eq. continuity, Eq. evaporDil; first line of Eq. weakNavierStokes);
+ *   - the Q1 level-set advection (Crank-Nicolson, Eq. weakFormLevelSet) and reinitialization operators
+ *     (Eq. reinitialization), driven by the transport velocity of Eqs. (transport_vel_local_continuous),
+ *     (transport_vel_extension_liquid), (transport_vel_extension_gas) with the closest-point projection of App. C;
+ *   - the adjoint of the momentum apply and a restarted GMRES solve with an FP32 inner operator and FP64
+ *     iterative refinement.
+ *
+ * Conventions shared by every entry point
+ *   Mesh:     n cells per axis, h = L / n.  Velocity (Q_p) nodes: M = p n + 1 per axis, N_u = M^3; level-set /
+ *             mass-flux / pressure-space (Q1) nodes: N_phi = (n + 1)^3.  Node index i + M (j + M k), i fastest
+ *             (x), then y, then z.  Inside a cell the Q_p nodes sit at the Gauss-Lobatto points of [0, 1].
+ *   Vectors:  component-major: v[c * N + node] for c = 0, 1, 2 (x, y, z components).
+ *   Pointers: every array argument is a DEVICE pointer owned by the caller (e.g. a contiguous torch CUDA
+ *             tensor).  The library keeps no reference to caller arrays after a call returns on the host:
+ *             evap_set_fields copies its inputs into library-owned device memory.  Output arrays must not alias
+ *             inputs.
+ *   Streams:  `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  All work of a call is
+ *             enqueued on that stream and the call returns without synchronizing, except where stated.
+ *   Errors:   every function returns EVAP_OK (0) or a negative status; evap_status_string() names it and
+ *             evap_last_error() returns the message of the most recent failure in the calling host thread.
+ *             Arguments are validated before any work is enqueued; on EVAP_EINVAL nothing was enqueued.
+ *   Precision: `prec` selects the arithmetic of an operator apply: 64 (x, y are double*) or 32 (float*).  The
+ *             material law (Heaviside, density, viscosity, normal, dilation rate) is always evaluated in FP64
+ *             (in evap_set_fields) and rounded to the apply precision.
+ */
+#ifndef EVAP_H
+#define EVAP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct evap_mesh* evap_handle; /* opaque, owned by the library */
+
+enum evap_status {
+    EVAP_OK = 0,
+    EVAP_EINVAL = -1,      /* null pointer, bad size, degree, mode or precision */
+    EVAP_ECUDA = -2,       /* a CUDA call or kernel launch failed; evap_last_error() has the CUDA message */
+    EVAP_ENOTCONV = -3,    /* solve hit its iteration cap; the last iterate and its residual are returned */
+    EVAP_ENOFIELDS = -4,   /* an apply or solve was called before evap_set_fields */
+    EVAP_ENOMEM = -5       /* device allocation failed */
+};
+
+enum evap_levelset_mode {
+    EVAP_ADVECT = 0,       /* y = (w, x) + theta dt (w, u_Gamma . grad x)                           Eq. weakFormLevelSet */
+    EVAP_REINIT = 1,       /* y = (w, x)/dtau + eps (grad w . n, grad x . n)                     Eq. reinitialization */
+    EVAP_REINIT_RHS = 2    /* y = (w, x)/dtau + (grad w, (1 - x^2)/2 n)   (explicit part, x = psi at pseudo-time 0) */
+};
+
+typedef struct {
+    double rho_l, rho_g;   /* phase densities, reciprocal interpolation Eq. (rhoEff) */
+    double mu_l, mu_g;     /* phase viscosities, arithmetic interpolation Eq. (muEff) */
+    double eps;            /* interface thickness parameter, Eq. (initial_phi) */
+    double dt;             /* time step of the level-set Crank-Nicolson operator */
+    double c_mass;         /* mass coefficient of the momentum operator (1/dt; 1.5/dt is the BDF2 leading term) */
+    double theta;          /* Crank-Nicolson weight (1/2) */
+    double dtau;           /* reinitialization pseudo-time step, min(eps, dt) (Sec. 2.2.2) */
+    int variant;           /* transport velocity: 1 local (Eq. transport_vel_local_continuous),
+                              2 liquid extension (Eq. transport_vel_extension_liquid), 3 gas extension */
+    int stress;            /* 0 standard Stokes (Eq. stokesLaw), 1 corrected (Eq. modified_viscous_stress) */
+    int corr_zone;         /* 0: correction only in the interface zone 0 < H < 1 (Sec. 2.4.2); 1: everywhere */
+    int newton;            /* 1: Newton linearization (x . grad) u0 included (App. D); 0: Picard */
+    unsigned dirichlet_faces; /* homogeneous velocity Dirichlet faces, bit 2a: x_a = 0, bit 2a+1: x_a = L */
+    double cpp_tol;        /* closest-point tolerance in cell units (App. C) */
+    int cpp_kmax;          /* closest-point outer iteration cap (App. C) */
+} evap_params;
+
+/* Create the mesh/operator object.  n_cells >= 1, degree_u in {2, 3}, L > 0, prm not NULL with rho_l, rho_g,
+ * eps, dtau > 0, variant in {1,2,3}.  Allocates the library-owned device state of the current CUDA device
+ * (fields, FP32 copies, quadrature-point coefficient table, transport velocity).  *out is set on success only. */
+int evap_create_mesh(int n_cells, int degree_u, double L, const evap_params* prm, evap_handle* out);
+
+/* Release all device memory of the handle (synchronizes the device). NULL is accepted and ignored. */
+int evap_destroy(evap_handle h);
+
+/* Number of Q_p velocity nodes (N_u; a velocity vector has 3 N_u entries) and of Q1 nodes (N_phi). */
+int evap_sizes(evap_handle h, int64_t* n_u, int64_t* n_phi);
+
+/* Set the coefficient fields of the operators: phi [N_phi] (regularized level set, Eq. initial_phi; values are
+ * clamped to [-1, 1]), u [3 N_u] (velocity about which the momentum operator is linearized; also the fluid
+ * velocity of the transport velocity), mdot [N_phi] (evaporative mass flux, Eq. evaporDil).  Copies the fields,
+ * evaluates the material law at every quadrature point of the interface cells (Eqs. heaviside, rhoEff, muEff,
+ * normal_vector, delta, evaporDil) in FP64, and computes the transport velocity u_Gamma [3 N_phi] of the selected
+ * variant (App. C closest-point projection for variants 2/3). */
+int evap_set_fields(evap_handle h, const double* phi, const double* u, const double* mdot, void* stream);
+
+/* Replace the transport velocity used by EVAP_ADVECT with caller data u_gamma [3 N_phi] (copied). */
+int evap_set_transport_velocity(evap_handle h, const double* u_gamma, void* stream);
+
+/* Copy the current transport velocity to u_gamma [3 N_phi] and the per-node closest-point flags to flags
+ * [N_phi] (0 converged or not projected, 1 not converged; either pointer may be NULL).  If n_flagged is not NULL
+ * the number of flagged nodes is written to it (host pointer; this synchronizes the stream). */
+int evap_get_transport_velocity(evap_handle h, double* u_gamma, int32_t* flags, int64_t* n_flagged, void* stream);
+
+/* Momentum apply y = A x (velocity block of Eq. weakNavierStokes linearized about u, App. D):
+ *   y_(i,c) = sum_q W_q [ N_i rho (c_mass x_c + (u . grad) x_c + newton (x . grad) u_c) + grad N_i . 2 mu eps_mod(x)_c ]
+ * on unconstrained DoFs; on Dirichlet DoFs y = x and x does not enter other rows.  If y_p is not NULL the
+ * divergence row y_p [N_phi] = sum_q W_q N^1_j (div x - v_dil) is written too (same precision).
+ * prec 64: x, y, y_p double*;  prec 32: float*.  x [3 N_u], y [3 N_u]. */
+int evap_apply_momentum(evap_handle h, int prec, const void* x, void* y, void* y_p, void* stream);
+
+/* Level-set apply y = A x on Q1 for the given mode (evap_levelset_mode); x, y [N_phi]; prec 64 or 32.
+ * The normal n is grad phi / |grad phi| of the level set of evap_set_fields. */
+int evap_apply_levelset(evap_handle h, int mode, int prec, const void* x, void* y, void* stream);
+
+/* Adjoint of the momentum apply for L = w . A(phi, mdot, u) x + w_p . (B x - g(phi, mdot)):
+ *   g_x = A^T w + B^T w_p,  g_u0 = dL/du [3 N_u],  g_phi = dL/dphi [N_phi],  g_mdot = dL/dmdot [N_phi],
+ * quadrature-point data recomputed from the fields (nothing stored).  w [3 N_u] and x [3 N_u] required; w_p may be
+ * NULL (no divergence row); any g_* may be NULL (not computed).  FP64 only. */
+int evap_apply_adjoint(evap_handle h, const double* w, const double* w_p, const double* x, double* g_x,
+                       double* g_u0, double* g_phi, double* g_mdot, void* stream);
+
+/* Solve A x = f for the momentum operator with restarted GMRES(restart) and right Jacobi preconditioning
+ * (Table tab:solver_settings: GMRES with a diagonal preconditioner).  mixed = 0: FP64 throughout; mixed = 1:
+ * FP32 operator and Krylov basis inside FP64 iterative refinement (outer residual r = f - A x, norms and dot
+ * products in FP64).  x holds the initial guess on entry and the solution on exit.  Stops when ||f - A x|| <=
+ * rtol ||f|| (FP64 residual) or after max_iter operator applications.  iters_out (host, may be NULL): operator
+ * applications used; relres_out (host, may be NULL): final ||f - A x|| / ||f||.  Synchronizes the stream.
+ * Returns EVAP_ENOTCONV if the cap was reached. */
+int evap_solve(evap_handle h, const double* f, double* x, int mixed, int restart, double rtol, int max_iter,
+               int* iters_out, double* relres_out, void* stream);
+
+/* Diagonal of the momentum operator [3 N_u] (1 on Dirichlet DoFs), the Jacobi preconditioner of evap_solve,
+ * evaluated in FP32 arithmetic from the FP64 coefficient table and written as double. */
+int evap_jacobi_diagonal(evap_handle h, double* diag, void* stream);
+
+const char* evap_status_string(int status);
+const char* evap_last_error(void);
+
+/* Number of CUDA kernels this library has launched in the process so far (all handles, all threads); used to
+ * count the kernels of a timed region.  The paper has no counterpart (instrumentation). */
+int64_t evap_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EVAP_H */

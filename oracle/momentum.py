@@ -236,3 +236,20 @@ def apply_rows(pb: Problem, x: np.ndarray, nodes: np.ndarray) -> np.ndarray:
         np.add.at(y, g.ravel(), ye.ravel())
     y = np.where(mask, x, y)
     return np.stack([y[c * Nu + nodes] for c in range(3)])
+
+
+def divergence_rows(pb: Problem, x: np.ndarray, q1nodes: np.ndarray) -> np.ndarray:
+    """Rows y_p[j] = (B x - g)[j] of the given Q1 nodes, from the cells around them only."""
+    mesh = pb.mesh
+    Nu = mesh.n_u
+    xt = np.where(pb.constrained(), 0.0, x)
+    cells = cells_touching_nodes(mesh, q1nodes, 1)
+    yp = np.zeros(mesh.n_phi)
+    for sl in _chunks(len(cells)):
+        q = qp_fields(pb, cells[sl])
+        W, bu, b1, du, d1 = q["W"], q["bu"], q["b1"], q["du"], q["d1"]
+        xe = np.stack([xt[c * Nu + du] for c in range(3)], axis=1)               # [nc, 3, nloc]
+        div = np.einsum("nci,ciq->nq", xe, bu.G)                                  # sum_c d_c x_c
+        re = np.einsum("q,jq,nq->nj", W, b1.N, div - q["vdil"])
+        np.add.at(yp, d1.ravel(), re.ravel())
+    return yp[q1nodes]

@@ -17,7 +17,11 @@ from __future__ import annotations
 
 import numpy as np
 
-PHI_BAND = np.tanh(1.5)  # phi at d = 3 eps, Eq. (initial_phi) evaluated at d = 3 eps
+# phi at d = 3 eps (Eq. initial_phi at d = 3 eps): tanh(3/2) = 0.90514825364486643824..., correctly rounded
+# (numpy's tanh(1.5) is one ulp above it).  The zone test |phi| < PHI_BAND decides an integer (inside / outside),
+# so it is taken with this exact double.
+PHI_BAND = float.fromhex("0x1.cf6f9786df577p-1")
+PHI_GAS_BAND = float.fromhex("0x1.fd77d111a0b00p-1")  # tanh(3) correctly rounded (d = 6 eps)
 
 
 def distance(phi, eps):

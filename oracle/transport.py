@@ -180,10 +180,10 @@ def transport_velocity(mesh: fe.Mesh, phi: np.ndarray, u0: np.ndarray, mdot: np.
             ug[:, t] = u0v[:, vnode] + mx / rho * nx
             continue
         if variant == 2:
-            band = (-math.tanh(3.0) < phx) and (phx < physics.PHI_BAND)
+            band = (-physics.PHI_GAS_BAND < phx) and (phx < physics.PHI_BAND)
             d_t, rho_t = 3.0 * eps, prm["rho_l"]
         else:
-            band = (-physics.PHI_BAND < phx) and (phx < math.tanh(3.0))
+            band = (-physics.PHI_BAND < phx) and (phx < physics.PHI_GAS_BAND)
             d_t, rho_t = -3.0 * eps, prm["rho_g"]
         y = sx
         if band:

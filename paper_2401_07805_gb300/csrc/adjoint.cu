@@ -1,0 +1,312 @@
+// Adjoint of the momentum apply, FP64, quadrature-point data recomputed from the fields (nothing stored).
+//
+// L = w . A(phi, u0) x + w_p . (B x - g(phi, mdot))  (velocity block and divergence row of Eq. weakNavierStokes).
+// Per quadrature point with W the weight, (X, G) values/gradients of x, (Om, OmG) of w, (U, GU) of u0, pi of w_p:
+//   dL/dX_d     = W rho (c_m Om_d + newton sum_c Om_c GU_cd)
+//   dL/dG_db    = W rho Om_d U_b + 2 W mu (sym(OmG)_db - z delta_db (n . OmG n)) + W pi delta_db
+//   dL/dU_b     = W rho sum_c Om_c G_cb,           dL/dGU_cd = newton W rho Om_c X_d
+//   dL/drho     = W Om . (c_m X + G U + newton GU X),  dL/dmu = 2 W OmG : eps_mod(X)
+//   dL/dn       = -2 W mu z tr(G) (OmG + OmG^T) n,  dL/dv_dil = -W pi
+//   chain rule through Eqs. (heaviside), (rhoEff), (muEff), (normal_vector), (delta), (evaporDil):
+//     drho/dH = -rho^2 (1/rho_l - 1/rho_g), dmu/dH = mu_l - mu_g, dH/dphi = H'(d) d'(phi),
+//     d delta/dphi = (H''(d) d'(phi)^2 + H'(d) d''(phi)) |grad phi|, d delta/d grad phi = H'(d) d'(phi) n,
+//     dn/d grad phi = (I - n n^T)/|grad phi|; the zone gate is piecewise constant.
+// The value/gradient sensitivities are tested like the forward operator (S^T and Dc^T sweeps); the Q1 sensitivities
+// are integrated against N^1_j and grad N^1_j.
+#include "physics.cuh"
+
+namespace evap {
+
+__device__ __forceinline__ bool cons_node(int gx, int gy, int gz, int M, unsigned f) {
+    return ((f & 1u) && gx == 0) || ((f & 2u) && gx == M - 1) || ((f & 4u) && gy == 0) ||
+           ((f & 8u) && gy == M - 1) || ((f & 16u) && gz == 0) || ((f & 32u) && gz == M - 1);
+}
+
+__global__ void k_adjoint_init(int M, int64_t Nu, int64_t Np, unsigned faces, const double* __restrict__ w,
+                               double* gx, double* gu, double* gphi, double* gm) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 3 * Nu; i += stride) {
+        if (gx) {
+            const int64_t node = i % Nu;
+            const int a = (int)(node % M), b = (int)((node / M) % M), c = (int)(node / ((int64_t)M * M));
+            gx[i] = cons_node(a, b, c, M, faces) ? w[i] : 0.0;
+        }
+        if (gu) gu[i] = 0.0;
+    }
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < Np; i += stride) {
+        if (gphi) gphi[i] = 0.0;
+        if (gm) gm[i] = 0.0;
+    }
+}
+
+template <int P, int CB>
+__global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
+    k_adjoint(MeshArgs<double> m, Basis<double> bas, const double* __restrict__ phi, const double* __restrict__ mdot,
+              const double* __restrict__ u0, const double* __restrict__ w, const double* __restrict__ wp,
+              const double* __restrict__ x, double* gx, double* gu, double* gphi, double* gm) {
+    constexpr int Q = P + 1, NQ = Q * Q * Q;
+    __shared__ double sS[Q][Q], sDc[Q][Q];
+    __shared__ double buf[2][CB][12][NQ];
+    const int tid = threadIdx.x;
+    const int lc = tid / NQ, t = tid % NQ;
+    const int64_t cell = (int64_t)blockIdx.x * CB + lc;
+    const bool active = cell < m.ncell;
+    if (tid < Q * Q) {
+        sS[tid / Q][tid % Q] = bas.S[tid / Q][tid % Q];
+        sDc[tid / Q][tid % Q] = bas.Dc[tid / Q][tid % Q];
+    }
+    const int a = t % Q, b = (t / Q) % Q, c = t / (Q * Q);
+    const int n = m.n, M = m.M;
+    const int64_t m1 = n + 1;
+    int cx = 0, cy = 0, cz = 0;
+    int64_t gidx = 0;
+    bool cons = false;
+    if (active) {
+        cx = (int)(cell % n);
+        cy = (int)((cell / n) % n);
+        cz = (int)(cell / ((int64_t)n * n));
+        const int gxi = P * cx + a, gyi = P * cy + b, gzi = P * cz + c;
+        gidx = gxi + (int64_t)M * (gyi + (int64_t)M * gzi);
+        cons = cons_node(gxi, gyi, gzi, M, m.faces);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            buf[0][lc][k][t] = cons ? 0.0 : x[k * m.Nu + gidx];
+            buf[0][lc][3 + k][t] = cons ? 0.0 : w[k * m.Nu + gidx];
+            buf[0][lc][6 + k][t] = u0[k * m.Nu + gidx];
+        }
+    }
+    __syncthreads();
+    if (active)
+        for (int f = 0; f < 9; ++f) {
+            double s = 0;
+#pragma unroll
+            for (int k = 0; k < Q; ++k) s += sS[a][k] * buf[0][lc][f][k + Q * (b + Q * c)];
+            buf[1][lc][f][t] = s;
+        }
+    __syncthreads();
+    if (active)
+        for (int f = 0; f < 9; ++f) {
+            double s = 0;
+#pragma unroll
+            for (int k = 0; k < Q; ++k) s += sS[b][k] * buf[1][lc][f][a + Q * (k + Q * c)];
+            buf[0][lc][f][t] = s;
+        }
+    __syncthreads();
+    if (active)
+        for (int f = 0; f < 9; ++f) {
+            double s = 0;
+#pragma unroll
+            for (int k = 0; k < Q; ++k) s += sS[c][k] * buf[0][lc][f][a + Q * (b + Q * k)];
+            buf[1][lc][f][t] = s;
+        }
+    __syncthreads();
+    double gxv[3] = {0, 0, 0}, guv[3] = {0, 0, 0}, gxg[3][3] = {}, gug[3][3] = {};
+    double dphi = 0.0, dg[3] = {0, 0, 0}, dm = 0.0;
+    if (active) {
+        double V[9], Gr[9][3];
+        for (int f = 0; f < 9; ++f) {
+            V[f] = buf[1][lc][f][t];
+            double g0 = 0, g1 = 0, g2 = 0;
+#pragma unroll
+            for (int r = 0; r < Q; ++r) {
+                g0 += sDc[a][r] * buf[1][lc][f][r + Q * (b + Q * c)];
+                g1 += sDc[b][r] * buf[1][lc][f][a + Q * (r + Q * c)];
+                g2 += sDc[c][r] * buf[1][lc][f][a + Q * (b + Q * r)];
+            }
+            Gr[f][0] = g0 * m.inv_h; Gr[f][1] = g1 * m.inv_h; Gr[f][2] = g2 * m.inv_h;
+        }
+        // Q1 fields at the point
+        const double tx = bas.t[a], ty = bas.t[b], tz = bas.t[c];
+        double ph = 0, gp[3] = {0, 0, 0}, md = 0, pi = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int ja = j & 1, jb = (j >> 1) & 1, jc = j >> 2;
+            const int64_t nd = (cx + ja) + m1 * ((cy + jb) + m1 * (cz + jc));
+            const double wx = ja ? tx : 1.0 - tx, wy = jb ? ty : 1.0 - ty, wz = jc ? tz : 1.0 - tz;
+            const double dx = ja ? 1.0 : -1.0, dy = jb ? 1.0 : -1.0, dz = jc ? 1.0 : -1.0;
+            const double pv = phi[nd];
+            ph += wx * wy * wz * pv;
+            gp[0] += dx * wy * wz * pv;
+            gp[1] += wx * dy * wz * pv;
+            gp[2] += wx * wy * dz * pv;
+            md += wx * wy * wz * mdot[nd];
+            if (wp) pi += wx * wy * wz * wp[nd];
+        }
+        gp[0] *= m.inv_h; gp[1] *= m.inv_h; gp[2] *= m.inv_h;
+        const Material mat = material(ph, gp[0], gp[1], gp[2], m);
+        const double zg = correction_on(m, mat.zone) ? 1.0 : 0.0;
+        double dH = 0.0, d2H = 0.0, dd = 0.0, d2d = 0.0;
+        if (mat.zone) {
+            const double d = m.eps * log((1.0 + ph) / (1.0 - ph));
+            double sn, cs;
+            sincos(PI * d / (3.0 * m.eps), &sn, &cs);
+            dH = (1.0 + cs) / (6.0 * m.eps);
+            d2H = -PI * sn / (18.0 * m.eps * m.eps);
+            const double om = 1.0 - ph * ph;
+            dd = 2.0 * m.eps / om;
+            d2d = 4.0 * m.eps * ph / (om * om);
+        }
+        const double W = bas.w[a] * bas.w[b] * bas.w[c] * m.vol_w;
+        const double rho = mat.rho, mu = mat.mu;
+        const double* nv = mat.n;
+        const double* X = &V[0];
+        const double* Om = &V[3];
+        const double* U = &V[6];
+        double (*G)[3] = &Gr[0];
+        double (*OmG)[3] = &Gr[3];
+        double (*GU)[3] = &Gr[6];
+        const double nw = m.newton ? 1.0 : 0.0;
+        const double tr = G[0][0] + G[1][1] + G[2][2];
+        // n . OmG n
+        double nOn = 0.0;
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) nOn += nv[i] * OmG[i][j] * nv[j];
+        for (int d = 0; d < 3; ++d) {
+            gxv[d] = W * rho * (m.c_mass * Om[d] + nw * (Om[0] * GU[0][d] + Om[1] * GU[1][d] + Om[2] * GU[2][d]));
+            guv[d] = W * rho * (Om[0] * G[0][d] + Om[1] * G[1][d] + Om[2] * G[2][d]);
+            for (int e = 0; e < 3; ++e) {
+                gxg[d][e] = W * rho * Om[d] * U[e] +
+                            2.0 * W * mu * (0.5 * (OmG[d][e] + OmG[e][d]) - (d == e ? zg * nOn : 0.0)) +
+                            (d == e ? W * pi : 0.0);
+                gug[d][e] = nw * W * rho * Om[d] * X[e];
+            }
+        }
+        // coefficient sensitivities
+        double dL_drho = 0.0, dL_dmu = 0.0, dL_dn[3];
+        for (int k = 0; k < 3; ++k) {
+            const double Fk = m.c_mass * X[k] + U[0] * G[k][0] + U[1] * G[k][1] + U[2] * G[k][2] +
+                              nw * (GU[k][0] * X[0] + GU[k][1] * X[1] + GU[k][2] * X[2]);
+            dL_drho += Om[k] * Fk;
+            for (int l = 0; l < 3; ++l)
+                dL_dmu += OmG[k][l] * (0.5 * (G[k][l] + G[l][k]) - zg * tr * nv[k] * nv[l]);
+        }
+        dL_drho *= W;
+        dL_dmu *= 2.0 * W;
+        for (int i = 0; i < 3; ++i) {
+            double s = 0.0;
+            for (int j = 0; j < 3; ++j) s += (OmG[i][j] + OmG[j][i]) * nv[j];
+            dL_dn[i] = -2.0 * W * mu * zg * tr * s;
+        }
+        const double krho = 1.0 / m.rho_l - 1.0 / m.rho_g;
+        const double drho_dH = -rho * rho * krho;
+        const double dmu_dH = m.mu_l - m.mu_g;
+        dphi = (dL_drho * drho_dH + dL_dmu * dmu_dH) * dH * dd;
+        const double gn = sqrt(gp[0] * gp[0] + gp[1] * gp[1] + gp[2] * gp[2]);
+        if (gn > 0.0) {
+            const double pn = dL_dn[0] * nv[0] + dL_dn[1] * nv[1] + dL_dn[2] * nv[2];
+            for (int i = 0; i < 3; ++i) dg[i] = (dL_dn[i] - pn * nv[i]) / gn;
+        }
+        if (wp) {
+            const double dL_dv = -W * pi;
+            const double delta = mat.zone ? dH * dd * gn : 0.0;
+            dm = dL_dv * krho * delta;
+            dphi += dL_dv * md * krho * (d2H * dd * dd + dH * d2d) * gn;
+            for (int i = 0; i < 3; ++i) dg[i] += dL_dv * md * krho * dH * dd * nv[i];
+        }
+    }
+    __syncthreads();
+    if (active) {
+        for (int s = 0; s < 9; ++s) buf[0][lc][s][t] = gxg[s / 3][s % 3];
+        for (int s = 0; s < 3; ++s) buf[0][lc][9 + s][t] = gug[0][s];
+        for (int s = 0; s < 6; ++s) buf[1][lc][s][t] = gug[1 + s / 3][s % 3];
+        buf[1][lc][6][t] = dphi;
+        buf[1][lc][7][t] = dg[0];
+        buf[1][lc][8][t] = dg[1];
+        buf[1][lc][9][t] = dg[2];
+        buf[1][lc][10][t] = dm;
+    }
+    __syncthreads();
+    double tx3[3], tu3[3];
+    if (active) {
+        for (int k = 0; k < 3; ++k) {
+            double s0 = 0, s1 = 0, s2 = 0, u0s = 0, u1s = 0, u2s = 0;
+            const int ib = 3 * k;       // gxg[k][*] slots in buf[0]
+            const int iu = 9 + 3 * k;   // gug[k][*] slots: 9..17 over buf[0][9..11], buf[1][0..5]
+#pragma unroll
+            for (int r = 0; r < Q; ++r) {
+                const int p0 = r + Q * (b + Q * c), p1 = a + Q * (r + Q * c), p2 = a + Q * (b + Q * r);
+                s0 += sDc[r][a] * buf[0][lc][ib + 0][p0];
+                s1 += sDc[r][b] * buf[0][lc][ib + 1][p1];
+                s2 += sDc[r][c] * buf[0][lc][ib + 2][p2];
+                const int j0 = iu + 0, j1 = iu + 1, j2 = iu + 2;
+                u0s += sDc[r][a] * (j0 < 12 ? buf[0][lc][j0][p0] : buf[1][lc][j0 - 12][p0]);
+                u1s += sDc[r][b] * (j1 < 12 ? buf[0][lc][j1][p1] : buf[1][lc][j1 - 12][p1]);
+                u2s += sDc[r][c] * (j2 < 12 ? buf[0][lc][j2][p2] : buf[1][lc][j2 - 12][p2]);
+            }
+            tx3[k] = gxv[k] + (s0 + s1 + s2) * m.inv_h;
+            tu3[k] = guv[k] + (u0s + u1s + u2s) * m.inv_h;
+        }
+        if (t < 8) {  // Q1 sensitivities of node j = t
+            const int ja = t & 1, jb = (t >> 1) & 1, jc = t >> 2;
+            double sp = 0.0, sm = 0.0;
+            for (int q = 0; q < NQ; ++q) {
+                const int qa = q % Q, qb = (q / Q) % Q, qc = q / (Q * Q);
+                const double tqa = bas.t[qa], tqb = bas.t[qb], tqc = bas.t[qc];
+                const double wx = ja ? tqa : 1.0 - tqa, wy = jb ? tqb : 1.0 - tqb, wz = jc ? tqc : 1.0 - tqc;
+                const double dx = ja ? 1.0 : -1.0, dy = jb ? 1.0 : -1.0, dz = jc ? 1.0 : -1.0;
+                const double N = wx * wy * wz;
+                sp += N * buf[1][lc][6][q] +
+                      m.inv_h * (dx * wy * wz * buf[1][lc][7][q] + wx * dy * wz * buf[1][lc][8][q] +
+                                 wx * wy * dz * buf[1][lc][9][q]);
+                sm += N * buf[1][lc][10][q];
+            }
+            const int64_t nd = (cx + ja) + m1 * ((cy + jb) + m1 * (cz + jc));
+            if (gphi) atomicAdd(&gphi[nd], sp);
+            if (gm) atomicAdd(&gm[nd], sm);
+        }
+    }
+    __syncthreads();
+    if (active)
+        for (int k = 0; k < 3; ++k) {
+            buf[0][lc][k][t] = tx3[k];
+            buf[0][lc][3 + k][t] = tu3[k];
+        }
+    __syncthreads();
+    if (active)
+        for (int f = 0; f < 6; ++f) {
+            double s = 0;
+#pragma unroll
+            for (int q = 0; q < Q; ++q) s += sS[q][c] * buf[0][lc][f][a + Q * (b + Q * q)];
+            buf[1][lc][f][t] = s;
+        }
+    __syncthreads();
+    if (active)
+        for (int f = 0; f < 6; ++f) {
+            double s = 0;
+#pragma unroll
+            for (int q = 0; q < Q; ++q) s += sS[q][b] * buf[1][lc][f][a + Q * (q + Q * c)];
+            buf[0][lc][f][t] = s;
+        }
+    __syncthreads();
+    if (active)
+        for (int f = 0; f < 6; ++f) {
+            double s = 0;
+#pragma unroll
+            for (int q = 0; q < Q; ++q) s += sS[q][a] * buf[0][lc][f][q + Q * (b + Q * c)];
+            if (f < 3) {
+                if (gx && !cons) atomicAdd(&gx[f * m.Nu + gidx], s);
+            } else if (gu) {
+                atomicAdd(&gu[(f - 3) * m.Nu + gidx], s);
+            }
+        }
+}
+
+int launch_adjoint(evap_mesh* h, const double* w, const double* wp, const double* x, double* gx, double* gu,
+                   double* gphi, double* gm, cudaStream_t s) {
+    const MeshArgs<double>& m = h->m;
+    k_adjoint_init<<<blocks_for(3 * m.Nu, 256), 256, 0, s>>>(m.M, m.Nu, m.Nphi, m.faces, w, gx, gu, gphi, gm);
+    EVAP_CHECK_LAUNCH("adjoint_init");
+    if (m.P == 2) {
+        constexpr int CB = 4;
+        k_adjoint<2, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 27, 0, s>>>(m, h->b, h->phi, h->mdot, h->u, w, wp,
+                                                                                x, gx, gu, gphi, gm);
+    } else {
+        constexpr int CB = 2;
+        k_adjoint<3, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 64, 0, s>>>(m, h->b, h->phi, h->mdot, h->u, w, wp,
+                                                                                x, gx, gu, gphi, gm);
+    }
+    EVAP_CHECK_LAUNCH("adjoint");
+    return EVAP_OK;
+}
+
+}  // namespace evap

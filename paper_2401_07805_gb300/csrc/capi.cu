@@ -1,0 +1,338 @@
+// C ABI entry points: argument validation, library-owned state, dispatch to the kernel launchers.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <atomic>
+#include <new>
+
+#include "evap_internal.cuh"
+
+namespace evap {
+
+static thread_local std::string g_last_error;
+static std::atomic<long long> g_launches{0};
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+int cuda_fail(const char* what, cudaError_t e) {
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? EVAP_ENOMEM : EVAP_ECUDA;
+}
+
+// Gauss-Legendre rule on [0, 1] with Q points (closed forms for Q <= 4).
+static void gauss_rule(int Q, double* t, double* w) {
+    double x[MAXQ], W[MAXQ];
+    if (Q == 2) {
+        x[0] = -1.0 / std::sqrt(3.0); x[1] = -x[0];
+        W[0] = W[1] = 1.0;
+    } else if (Q == 3) {
+        x[0] = -std::sqrt(0.6); x[1] = 0.0; x[2] = -x[0];
+        W[0] = W[2] = 5.0 / 9.0; W[1] = 8.0 / 9.0;
+    } else {  // Q == 4
+        const double a = std::sqrt(3.0 / 7.0 - 2.0 / 7.0 * std::sqrt(1.2));
+        const double b = std::sqrt(3.0 / 7.0 + 2.0 / 7.0 * std::sqrt(1.2));
+        x[0] = -b; x[1] = -a; x[2] = a; x[3] = b;
+        W[1] = W[2] = (18.0 + std::sqrt(30.0)) / 36.0;
+        W[0] = W[3] = (18.0 - std::sqrt(30.0)) / 36.0;
+    }
+    for (int q = 0; q < Q; ++q) {
+        t[q] = 0.5 * (x[q] + 1.0);
+        w[q] = 0.5 * W[q];
+    }
+}
+
+// Lagrange polynomial l_a through nodes[0..m) and its derivative at x (product formula).
+static void lagrange(const double* nodes, int m, int a, double x, double* val, double* der) {
+    double v = 1.0;
+    for (int k = 0; k < m; ++k)
+        if (k != a) v *= (x - nodes[k]) / (nodes[a] - nodes[k]);
+    double d = 0.0;
+    for (int k = 0; k < m; ++k) {
+        if (k == a) continue;
+        double term = 1.0 / (nodes[a] - nodes[k]);
+        for (int j = 0; j < m; ++j)
+            if (j != a && j != k) term *= (x - nodes[j]) / (nodes[a] - nodes[j]);
+        d += term;
+    }
+    *val = v;
+    *der = d;
+}
+
+void host_basis(int P, Basis<double>& b) {
+    std::memset(&b, 0, sizeof(b));
+    b.P = P;
+    b.Q = P + 1;
+    double nodes[MAXQ];
+    if (P == 2) {
+        nodes[0] = 0.0; nodes[1] = 0.5; nodes[2] = 1.0;
+    } else {
+        const double r = 0.5 / std::sqrt(5.0);
+        nodes[0] = 0.0; nodes[1] = 0.5 - r; nodes[2] = 0.5 + r; nodes[3] = 1.0;
+    }
+    gauss_rule(b.Q, b.t, b.w);
+    for (int q = 0; q < b.Q; ++q) {
+        for (int a = 0; a < b.Q; ++a) lagrange(nodes, b.Q, a, b.t[q], &b.S[q][a], &b.D[q][a]);
+        for (int r = 0; r < b.Q; ++r) {
+            double v;
+            lagrange(b.t, b.Q, r, b.t[q], &v, &b.Dc[q][r]);
+        }
+        b.N1[q][0] = 1.0 - b.t[q];
+        b.N1[q][1] = b.t[q];
+    }
+    gauss_rule(2, b.g2t, b.g2w);
+}
+
+template <typename T>
+Basis<T> cast_basis(const Basis<double>& b) {
+    Basis<T> o;
+    std::memset(&o, 0, sizeof(o));
+    o.P = b.P;
+    o.Q = b.Q;
+    for (int i = 0; i < MAXQ; ++i) {
+        for (int j = 0; j < MAXQ; ++j) {
+            o.S[i][j] = (T)b.S[i][j];
+            o.D[i][j] = (T)b.D[i][j];
+            o.Dc[i][j] = (T)b.Dc[i][j];
+        }
+        o.w[i] = (T)b.w[i];
+        o.t[i] = (T)b.t[i];
+        o.N1[i][0] = (T)b.N1[i][0];
+        o.N1[i][1] = (T)b.N1[i][1];
+    }
+    for (int i = 0; i < 2; ++i) {
+        o.g2t[i] = (T)b.g2t[i];
+        o.g2w[i] = (T)b.g2w[i];
+    }
+    return o;
+}
+template Basis<double> cast_basis<double>(const Basis<double>&);
+template Basis<float> cast_basis<float>(const Basis<double>&);
+
+template <typename T>
+MeshArgs<T> mesh_args(const evap_mesh* h) {
+    const MeshArgs<double>& m = h->m;
+    MeshArgs<T> o;
+    o.n = m.n; o.P = m.P; o.M = m.M;
+    o.Nu = m.Nu; o.Nphi = m.Nphi; o.ncell = m.ncell;
+    o.h = (T)m.h; o.inv_h = (T)m.inv_h; o.vol_w = (T)m.vol_w;
+    o.rho_l = (T)m.rho_l; o.rho_g = (T)m.rho_g; o.mu_l = (T)m.mu_l; o.mu_g = (T)m.mu_g; o.c_mass = (T)m.c_mass;
+    o.rho_H1 = (T)m.rho_H1; o.rho_H0 = (T)m.rho_H0; o.mu_H1 = (T)m.mu_H1; o.mu_H0 = (T)m.mu_H0;
+    o.eps = (T)m.eps; o.dt = (T)m.dt; o.theta = (T)m.theta; o.dtau = (T)m.dtau;
+    o.newton = m.newton; o.stress = m.stress; o.corr_zone = m.corr_zone; o.variant = m.variant;
+    o.faces = m.faces;
+    return o;
+}
+template MeshArgs<double> mesh_args<double>(const evap_mesh*);
+template MeshArgs<float> mesh_args<float>(const evap_mesh*);
+
+}  // namespace evap
+
+using namespace evap;
+
+static int fail(int code, const char* msg) {
+    set_error(msg);
+    return code;
+}
+
+static void free_all(evap_mesh* h) {
+    void* ptrs[] = {h->phi, h->u, h->mdot, h->u32, h->phi32, h->cell_code, h->table_index, h->table_count,
+                    h->table, h->table32, h->ugamma, h->ugamma32, h->cpp_flags, h->flag_count, h->diag,
+                    h->diag32, h->ws, h->red};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (h->red_host) cudaFreeHost(h->red_host);
+}
+
+extern "C" {
+
+const char* evap_status_string(int status) {
+    switch (status) {
+        case EVAP_OK: return "EVAP_OK";
+        case EVAP_EINVAL: return "EVAP_EINVAL";
+        case EVAP_ECUDA: return "EVAP_ECUDA";
+        case EVAP_ENOTCONV: return "EVAP_ENOTCONV";
+        case EVAP_ENOFIELDS: return "EVAP_ENOFIELDS";
+        case EVAP_ENOMEM: return "EVAP_ENOMEM";
+        default: return "EVAP_UNKNOWN";
+    }
+}
+
+const char* evap_last_error(void) { return g_last_error.c_str(); }
+
+int64_t evap_launch_count(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }
+
+int evap_create_mesh(int n_cells, int degree_u, double L, const evap_params* prm, evap_handle* out) {
+    if (!out || !prm) return fail(EVAP_EINVAL, "evap_create_mesh: null argument");
+    if (n_cells < 1 || n_cells > 1024) return fail(EVAP_EINVAL, "evap_create_mesh: n_cells must be in [1, 1024]");
+    if (degree_u != 2 && degree_u != 3) return fail(EVAP_EINVAL, "evap_create_mesh: degree_u must be 2 or 3");
+    if (!(L > 0.0)) return fail(EVAP_EINVAL, "evap_create_mesh: L must be positive");
+    if (!(prm->rho_l > 0.0) || !(prm->rho_g > 0.0) || !(prm->eps > 0.0) || !(prm->dtau > 0.0) ||
+        !(prm->mu_l >= 0.0) || !(prm->mu_g >= 0.0))
+        return fail(EVAP_EINVAL, "evap_create_mesh: rho_l, rho_g, eps, dtau must be > 0 and mu >= 0");
+    if (prm->variant < 1 || prm->variant > 3) return fail(EVAP_EINVAL, "evap_create_mesh: variant must be 1, 2 or 3");
+    if (prm->cpp_kmax < 0 || !(prm->cpp_tol > 0.0))
+        return fail(EVAP_EINVAL, "evap_create_mesh: cpp_tol must be > 0 and cpp_kmax >= 0");
+    evap_mesh* h = new (std::nothrow) evap_mesh();
+    if (!h) return fail(EVAP_ENOMEM, "evap_create_mesh: host allocation failed");
+    cudaGetDevice(&h->device);
+    h->prm = *prm;
+    MeshArgs<double>& m = h->m;
+    m.n = n_cells;
+    m.P = degree_u;
+    m.M = degree_u * n_cells + 1;
+    m.Nu = (int64_t)m.M * m.M * m.M;
+    m.Nphi = (int64_t)(n_cells + 1) * (n_cells + 1) * (n_cells + 1);
+    m.ncell = (int64_t)n_cells * n_cells * n_cells;
+    m.h = L / n_cells;
+    m.inv_h = 1.0 / m.h;
+    m.vol_w = m.h * m.h * m.h;
+    m.rho_l = prm->rho_l; m.rho_g = prm->rho_g; m.mu_l = prm->mu_l; m.mu_g = prm->mu_g;
+    m.rho_H1 = 1.0 / (1.0 / prm->rho_l + (1.0 - 1.0) / prm->rho_g);
+    m.rho_H0 = 1.0 / (0.0 / prm->rho_l + (1.0 - 0.0) / prm->rho_g);
+    m.mu_H1 = 1.0 * prm->mu_l + (1.0 - 1.0) * prm->mu_g;
+    m.mu_H0 = 0.0 * prm->mu_l + (1.0 - 0.0) * prm->mu_g;
+    m.c_mass = prm->c_mass; m.eps = prm->eps; m.dt = prm->dt; m.theta = prm->theta; m.dtau = prm->dtau;
+    m.newton = prm->newton ? 1 : 0;
+    m.stress = prm->stress ? 1 : 0;
+    m.corr_zone = prm->corr_zone ? 1 : 0;
+    m.variant = prm->variant;
+    m.faces = prm->dirichlet_faces & 0x3Fu;
+    host_basis(degree_u, h->b);
+    const int64_t Nu = m.Nu, Np = m.Nphi;
+    cudaError_t e = cudaSuccess;
+    auto al = [&](void** p, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+    };
+    al((void**)&h->phi, Np * sizeof(double));
+    al((void**)&h->u, 3 * Nu * sizeof(double));
+    al((void**)&h->mdot, Np * sizeof(double));
+    al((void**)&h->u32, 3 * Nu * sizeof(float));
+    al((void**)&h->phi32, Np * sizeof(float));
+    al((void**)&h->cell_code, m.ncell * sizeof(int8_t));
+    al((void**)&h->table_index, m.ncell * sizeof(int32_t));
+    al((void**)&h->table_count, sizeof(int32_t));
+    al((void**)&h->ugamma, 3 * Np * sizeof(double));
+    al((void**)&h->ugamma32, 3 * Np * sizeof(float));
+    al((void**)&h->cpp_flags, Np * sizeof(int32_t));
+    al((void**)&h->flag_count, sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+        int rc = cuda_fail("evap_create_mesh: cudaMalloc", e);
+        free_all(h);
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return EVAP_OK;
+}
+
+int evap_destroy(evap_handle h) {
+    if (!h) return EVAP_OK;
+    cudaDeviceSynchronize();
+    free_all(h);
+    delete h;
+    return EVAP_OK;
+}
+
+int evap_sizes(evap_handle h, int64_t* n_u, int64_t* n_phi) {
+    if (!h) return fail(EVAP_EINVAL, "evap_sizes: null handle");
+    if (n_u) *n_u = h->m.Nu;
+    if (n_phi) *n_phi = h->m.Nphi;
+    return EVAP_OK;
+}
+
+int evap_set_fields(evap_handle h, const double* phi, const double* u, const double* mdot, void* stream) {
+    if (!h || !phi || !u || !mdot) return fail(EVAP_EINVAL, "evap_set_fields: null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t Nu = h->m.Nu, Np = h->m.Nphi;
+    EVAP_CUDA(cudaMemcpyAsync(h->phi, phi, Np * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    EVAP_CUDA(cudaMemcpyAsync(h->u, u, 3 * Nu * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    EVAP_CUDA(cudaMemcpyAsync(h->mdot, mdot, Np * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    int rc = launch_setup_coefficients(h, s);  // clamps phi, FP32 copies, coefficient table
+    if (rc) return rc;
+    rc = launch_transport_velocity(h, s);
+    if (rc) return rc;
+    h->has_fields = true;
+    h->diag_valid = false;
+    return EVAP_OK;
+}
+
+int evap_set_transport_velocity(evap_handle h, const double* u_gamma, void* stream) {
+    if (!h || !u_gamma) return fail(EVAP_EINVAL, "evap_set_transport_velocity: null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t Np = h->m.Nphi;
+    EVAP_CUDA(cudaMemcpyAsync(h->ugamma, u_gamma, 3 * Np * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    int rc = launch_to_float(h->ugamma, h->ugamma32, 3 * Np, s);
+    if (rc) return rc;
+    EVAP_CUDA(cudaMemsetAsync(h->cpp_flags, 0, Np * sizeof(int32_t), s));
+    EVAP_CUDA(cudaMemsetAsync(h->flag_count, 0, sizeof(unsigned long long), s));
+    return EVAP_OK;
+}
+
+int evap_get_transport_velocity(evap_handle h, double* u_gamma, int32_t* flags, int64_t* n_flagged, void* stream) {
+    if (!h) return fail(EVAP_EINVAL, "evap_get_transport_velocity: null handle");
+    if (!h->has_fields) return fail(EVAP_ENOFIELDS, "evap_get_transport_velocity: fields not set");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t Np = h->m.Nphi;
+    if (u_gamma)
+        EVAP_CUDA(cudaMemcpyAsync(u_gamma, h->ugamma, 3 * Np * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (flags) EVAP_CUDA(cudaMemcpyAsync(flags, h->cpp_flags, Np * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    if (n_flagged) {
+        unsigned long long c = 0;
+        EVAP_CUDA(cudaMemcpyAsync(&c, h->flag_count, sizeof(c), cudaMemcpyDeviceToHost, s));
+        EVAP_CUDA(cudaStreamSynchronize(s));
+        *n_flagged = (int64_t)c;
+    }
+    return EVAP_OK;
+}
+
+int evap_apply_momentum(evap_handle h, int prec, const void* x, void* y, void* y_p, void* stream) {
+    if (!h || !x || !y) return fail(EVAP_EINVAL, "evap_apply_momentum: null argument");
+    if (prec != 64 && prec != 32) return fail(EVAP_EINVAL, "evap_apply_momentum: prec must be 64 or 32");
+    if (x == y) return fail(EVAP_EINVAL, "evap_apply_momentum: x and y must not alias");
+    if (!h->has_fields) return fail(EVAP_ENOFIELDS, "evap_apply_momentum: call evap_set_fields first");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (prec == 64) return launch_momentum<double>(h, (const double*)x, (double*)y, (double*)y_p, s);
+    return launch_momentum<float>(h, (const float*)x, (float*)y, (float*)y_p, s);
+}
+
+int evap_apply_levelset(evap_handle h, int mode, int prec, const void* x, void* y, void* stream) {
+    if (!h || !x || !y) return fail(EVAP_EINVAL, "evap_apply_levelset: null argument");
+    if (mode < EVAP_ADVECT || mode > EVAP_REINIT_RHS) return fail(EVAP_EINVAL, "evap_apply_levelset: bad mode");
+    if (prec != 64 && prec != 32) return fail(EVAP_EINVAL, "evap_apply_levelset: prec must be 64 or 32");
+    if (x == y) return fail(EVAP_EINVAL, "evap_apply_levelset: x and y must not alias");
+    if (!h->has_fields) return fail(EVAP_ENOFIELDS, "evap_apply_levelset: call evap_set_fields first");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (prec == 64) return launch_levelset<double>(h, mode, (const double*)x, (double*)y, s);
+    return launch_levelset<float>(h, mode, (const float*)x, (float*)y, s);
+}
+
+int evap_apply_adjoint(evap_handle h, const double* w, const double* w_p, const double* x, double* g_x,
+                       double* g_u0, double* g_phi, double* g_mdot, void* stream) {
+    if (!h || !w || !x) return fail(EVAP_EINVAL, "evap_apply_adjoint: null argument");
+    if (!h->has_fields) return fail(EVAP_ENOFIELDS, "evap_apply_adjoint: call evap_set_fields first");
+    return launch_adjoint(h, w, w_p, x, g_x, g_u0, g_phi, g_mdot, (cudaStream_t)stream);
+}
+
+int evap_jacobi_diagonal(evap_handle h, double* diag, void* stream) {
+    if (!h || !diag) return fail(EVAP_EINVAL, "evap_jacobi_diagonal: null argument");
+    if (!h->has_fields) return fail(EVAP_ENOFIELDS, "evap_jacobi_diagonal: call evap_set_fields first");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = launch_diagonal(h, s);
+    if (rc) return rc;
+    EVAP_CUDA(cudaMemcpyAsync(diag, h->diag, 3 * h->m.Nu * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    return EVAP_OK;
+}
+
+int evap_solve(evap_handle h, const double* f, double* x, int mixed, int restart, double rtol, int max_iter,
+               int* iters_out, double* relres_out, void* stream) {
+    if (!h || !f || !x) return fail(EVAP_EINVAL, "evap_solve: null argument");
+    if (f == x) return fail(EVAP_EINVAL, "evap_solve: f and x must not alias");
+    if (restart < 1 || restart > 200) return fail(EVAP_EINVAL, "evap_solve: restart must be in [1, 200]");
+    if (!(rtol > 0.0) || max_iter < 1) return fail(EVAP_EINVAL, "evap_solve: rtol > 0 and max_iter >= 1 required");
+    if (!h->has_fields) return fail(EVAP_ENOFIELDS, "evap_solve: call evap_set_fields first");
+    return solve_gmres(h, f, x, mixed ? 1 : 0, restart, rtol, max_iter, iters_out, relres_out, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,139 @@
+// Internal declarations of the GB300 evaporation-operator library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "../../include/evap.h"
+
+namespace evap {
+
+constexpr int MAXQ = 4;  // up to degree 3 velocity: 4 Gauss points per direction
+
+// 1D tables of the tensor-product bases (Sec. 2.5): Lagrange polynomials l_a on the Gauss-Lobatto support points of
+// degree P evaluated at the Q = P + 1 Gauss-Legendre points t_q of [0, 1].
+template <typename T>
+struct Basis {
+    int P, Q;
+    T S[MAXQ][MAXQ];   // S[q][a]  = l_a(t_q)
+    T D[MAXQ][MAXQ];   // D[q][a]  = l_a'(t_q)
+    T Dc[MAXQ][MAXQ];  // Dc[q][r] = L_r'(t_q), L_r the Lagrange polynomials through the Gauss points (collocation)
+    T w[MAXQ];         // Gauss weights on [0, 1]
+    T t[MAXQ];         // Gauss points on [0, 1]
+    T N1[MAXQ][2];     // Q1 shape values (1 - t_q, t_q)
+    T g2t[2], g2w[2];  // 2-point Gauss rule of the Q1 operators
+};
+
+// Scalars every kernel needs (passed by value).
+template <typename T>
+struct MeshArgs {
+    int n, P, M;
+    int64_t Nu, Nphi, ncell;
+    T h, inv_h, vol_w;  // cell size, 1/h, h^3
+    T rho_l, rho_g, mu_l, mu_g, c_mass;
+    T rho_H1, rho_H0, mu_H1, mu_H0;  // Eqs. (rhoEff), (muEff) evaluated at H = 1 and H = 0
+    T eps, dt, theta, dtau;
+    int newton, stress, corr_zone, variant;
+    unsigned faces;
+};
+
+enum CellCode : int8_t { CELL_GAS = 0, CELL_LIQUID = 1, CELL_TABLE = 2 };
+constexpr int TAB_K = 6;  // table entries per quadrature point: rho, mu, z n_x, z n_y, z n_z, v_dil
+
+template <typename T>
+struct Coeffs {            // quadrature-point coefficients of the momentum operator
+    const int8_t* cell_code;
+    const int32_t* table_index;
+    const T* table;        // [ntable][TAB_K][nq]
+    const T* u0;           // [3 N_u]
+};
+
+void host_basis(int P, Basis<double>& b);
+template <typename T>
+Basis<T> cast_basis(const Basis<double>& b);
+
+}  // namespace evap
+
+struct evap_mesh {
+    evap::MeshArgs<double> m;
+    evap::Basis<double> b;
+    evap_params prm;
+    int device = 0;
+    bool has_fields = false;
+    // fields (library-owned copies)
+    double* phi = nullptr;
+    double* u = nullptr;
+    double* mdot = nullptr;
+    float* u32 = nullptr;
+    float* phi32 = nullptr;
+    // quadrature-point coefficient table of the interface cells
+    int8_t* cell_code = nullptr;
+    int32_t* table_index = nullptr;
+    int32_t* table_count = nullptr;  // device counter
+    int64_t table_cap = 0;           // cells the table can hold
+    double* table = nullptr;
+    float* table32 = nullptr;
+    // transport velocity
+    double* ugamma = nullptr;
+    float* ugamma32 = nullptr;
+    int32_t* cpp_flags = nullptr;
+    unsigned long long* flag_count = nullptr;
+    // Jacobi diagonal and Krylov workspace (allocated by the first solve)
+    double* diag = nullptr;
+    float* diag32 = nullptr;
+    bool diag_valid = false;
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    double* red = nullptr;   // device reduction scratch
+    double* red_host = nullptr;  // pinned host mirror
+    size_t red_len = 0;
+};
+
+namespace evap {
+
+void set_error(const std::string& msg);
+int cuda_fail(const char* what, cudaError_t e);
+void count_launch();
+#define EVAP_CHECK_LAUNCH(what)                                         \
+    do {                                                                \
+        ::evap::count_launch();                                         \
+        cudaError_t _e = cudaGetLastError();                            \
+        if (_e != cudaSuccess) return ::evap::cuda_fail(what, _e);      \
+    } while (0)
+#define EVAP_CUDA(call)                                                 \
+    do {                                                                \
+        cudaError_t _e = (call);                                        \
+        if (_e != cudaSuccess) return ::evap::cuda_fail(#call, _e);     \
+    } while (0)
+
+template <typename T>
+MeshArgs<T> mesh_args(const evap_mesh* h);
+
+// kernels launchers (each returns an evap_status)
+int launch_setup_coefficients(evap_mesh* h, cudaStream_t s);
+int launch_transport_velocity(evap_mesh* h, cudaStream_t s);
+template <typename T>
+int launch_momentum(evap_mesh* h, const T* x, T* y, T* yp, cudaStream_t s);
+template <typename T>
+int launch_levelset(evap_mesh* h, int mode, const T* x, T* y, cudaStream_t s);
+int launch_adjoint(evap_mesh* h, const double* w, const double* wp, const double* x, double* gx, double* gu,
+                   double* gphi, double* gm, cudaStream_t s);
+int launch_diagonal(evap_mesh* h, cudaStream_t s);
+int solve_gmres(evap_mesh* h, const double* f, double* x, int mixed, int restart, double rtol, int max_iter,
+                int* iters, double* relres, cudaStream_t s);
+
+// small vector kernels used by several files
+template <typename T>
+int launch_fill(T* p, int64_t n, T v, cudaStream_t s);
+int launch_to_float(const double* a, float* b, int64_t n, cudaStream_t s);
+
+inline int blocks_for(int64_t n, int threads, int64_t cap = 152 * 64) {
+    int64_t b = (n + threads - 1) / threads;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+}  // namespace evap

@@ -1,0 +1,527 @@
+// Krylov solve of the momentum system (Table tab:solver_settings: GMRES with a diagonal preconditioner):
+// restarted GMRES(m) with right Jacobi preconditioning and classical Gram-Schmidt with one re-orthogonalization.
+//   mixed = 0: FP64 operator, basis and reductions.
+//   mixed = 1: FP64 iterative refinement: r = f - A64 x (FP64), inner GMRES on A32 d = r/|r| with the FP32 operator
+//              and FP32 basis, x += |r| d in FP64.  FP32 dot products form each product exactly (FMA two-product)
+//              and accumulate per thread in a float-float pair (two-sum), then in FP64 across threads, so the
+//              reductions carry FP64-level accuracy without using the (slow) FP64 pipe per element.
+// The Hessenberg matrix, Givens rotations and the small triangular solve run on the host in FP64; one
+// device-to-host copy per Arnoldi step carries the new column.
+#include <cmath>
+#include <vector>
+
+#include "evap_internal.cuh"
+
+namespace evap {
+
+// ------------------------------------------------------------------------------------------- Jacobi diagonal
+// diag_(i,c) = sum_q W [ rho c_m N_i^2 + rho N_i (u0 . grad N_i) + newton rho N_i^2 d_c u0_c
+//                      + 2 mu ( (|grad N_i|^2 + (d_c N_i)^2)/2 - (z n)_c d_c N_i ((z n) . grad N_i) ) ]
+// in FP32 from the FP32 coefficient table; one thread per (cell, local node).
+template <int P, int CB>
+__global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
+    k_diagonal(MeshArgs<float> m, Basis<float> bas, const int8_t* __restrict__ code, const int32_t* __restrict__ tindex,
+               const float* __restrict__ table, const float* __restrict__ u0, float* __restrict__ diag) {
+    constexpr int Q = P + 1, NQ = Q * Q * Q;
+    __shared__ float sS[Q][Q], sD[Q][Q];
+    __shared__ float sU[CB][NQ];
+    __shared__ float qd[CB][12][NQ];  // per point: W rho, U(3), GU_cc(3), 2 W mu, z n(3)
+    const int tid = threadIdx.x, lc = tid / NQ, t = tid % NQ;
+    const int64_t cell = (int64_t)blockIdx.x * CB + lc;
+    const bool active = cell < m.ncell;
+    if (tid < Q * Q) {
+        sS[tid / Q][tid % Q] = bas.S[tid / Q][tid % Q];
+        sD[tid / Q][tid % Q] = bas.D[tid / Q][tid % Q];
+    }
+    const int a = t % Q, b = (t / Q) % Q, c = t / (Q * Q);
+    const int n = m.n, M = m.M;
+    int64_t gidx = 0;
+    int cx = 0, cy = 0, cz = 0;
+    if (active) {
+        cx = (int)(cell % n); cy = (int)((cell / n) % n); cz = (int)(cell / ((int64_t)n * n));
+        gidx = (P * cx + a) + (int64_t)M * ((P * cy + b) + (int64_t)M * (P * cz + c));
+    }
+    // u0 values and gradients at point t, component by component
+    float U[3], GUd[3];
+    for (int k = 0; k < 3; ++k) {
+        __syncthreads();
+        if (active) sU[lc][t] = u0[k * m.Nu + gidx];
+        __syncthreads();
+        float v = 0, g = 0;
+        if (active)
+            for (int i = 0; i < NQ; ++i) {
+                const int ia = i % Q, ib = (i / Q) % Q, ic = i / (Q * Q);
+                const float s3 = sS[a][ia] * sS[b][ib] * sS[c][ic];
+                const float dk = (k == 0 ? sD[a][ia] * sS[b][ib] * sS[c][ic]
+                                         : (k == 1 ? sS[a][ia] * sD[b][ib] * sS[c][ic] : sS[a][ia] * sS[b][ib] * sD[c][ic]));
+                v += s3 * sU[lc][i];
+                g += dk * sU[lc][i];
+            }
+        U[k] = v;
+        GUd[k] = g * m.inv_h;
+    }
+    if (active) {
+        float rho, mu, nz[3];
+        const int8_t cc = code[cell];
+        if (cc == CELL_TABLE) {
+            const float* tb = table + (int64_t)tindex[cell] * TAB_K * NQ + t;
+            rho = tb[0]; mu = tb[NQ]; nz[0] = tb[2 * NQ]; nz[1] = tb[3 * NQ]; nz[2] = tb[4 * NQ];
+        } else {
+            const bool liq = cc == CELL_LIQUID;
+            rho = liq ? m.rho_H1 : m.rho_H0;
+            mu = liq ? m.mu_H1 : m.mu_H0;
+            nz[0] = nz[1] = nz[2] = 0.f;
+        }
+        const float W = bas.w[a] * bas.w[b] * bas.w[c] * m.vol_w;
+        qd[lc][0][t] = W * rho;
+        for (int k = 0; k < 3; ++k) {
+            qd[lc][1 + k][t] = U[k];
+            qd[lc][4 + k][t] = GUd[k];
+            qd[lc][8 + k][t] = nz[k];
+        }
+        qd[lc][7][t] = 2.f * W * mu;
+    }
+    __syncthreads();
+    if (!active) return;
+    float dsum[3] = {0.f, 0.f, 0.f};
+    for (int q = 0; q < NQ; ++q) {
+        const int qa = q % Q, qb = (q / Q) % Q, qc = q / (Q * Q);
+        const float N = sS[qa][a] * sS[qb][b] * sS[qc][c];
+        const float g[3] = {sD[qa][a] * sS[qb][b] * sS[qc][c] * m.inv_h, sS[qa][a] * sD[qb][b] * sS[qc][c] * m.inv_h,
+                            sS[qa][a] * sS[qb][b] * sD[qc][c] * m.inv_h};
+        const float wr = qd[lc][0][q], wm = qd[lc][7][q];
+        const float conv = qd[lc][1][q] * g[0] + qd[lc][2][q] * g[1] + qd[lc][3][q] * g[2];
+        const float gg = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+        const float ng = qd[lc][8][q] * g[0] + qd[lc][9][q] * g[1] + qd[lc][10][q] * g[2];
+        for (int k = 0; k < 3; ++k) {
+            float v = wr * (m.c_mass * N * N + N * conv + (m.newton ? N * N * qd[lc][4 + k][q] : 0.f));
+            v += wm * (0.5f * (gg + g[k] * g[k]) - qd[lc][8 + k][q] * g[k] * ng);
+            dsum[k] += v;
+        }
+    }
+    for (int k = 0; k < 3; ++k) atomicAdd(&diag[k * m.Nu + gidx], dsum[k]);
+}
+
+__device__ __forceinline__ bool dnode(int64_t node, int M, unsigned f) {
+    const int gx = (int)(node % M), gy = (int)((node / M) % M), gz = (int)(node / ((int64_t)M * M));
+    return ((f & 1u) && gx == 0) || ((f & 2u) && gx == M - 1) || ((f & 4u) && gy == 0) ||
+           ((f & 8u) && gy == M - 1) || ((f & 16u) && gz == 0) || ((f & 32u) && gz == M - 1);
+}
+
+__global__ void k_diag_finish(int M, int64_t Nu, unsigned faces, float* d32, double* d64) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 3 * Nu; i += (int64_t)gridDim.x * blockDim.x) {
+        float v = dnode(i % Nu, M, faces) ? 1.f : d32[i];
+        if (!(v != 0.f)) v = 1.f;  // guard a vanishing diagonal entry (never expected with c_mass > 0)
+        d32[i] = v;
+        d64[i] = (double)v;
+    }
+}
+
+int launch_diagonal(evap_mesh* h, cudaStream_t s) {
+    if (h->diag_valid) return EVAP_OK;
+    const int64_t N = 3 * h->m.Nu;
+    if (!h->diag) EVAP_CUDA(cudaMalloc(&h->diag, N * sizeof(double)));
+    if (!h->diag32) EVAP_CUDA(cudaMalloc(&h->diag32, N * sizeof(float)));
+    EVAP_CUDA(cudaMemsetAsync(h->diag32, 0, N * sizeof(float), s));
+    const MeshArgs<float> m = mesh_args<float>(h);
+    const Basis<float> b = cast_basis<float>(h->b);
+    if (m.P == 2) {
+        constexpr int CB = 8;
+        k_diagonal<2, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 27, 0, s>>>(m, b, h->cell_code, h->table_index,
+                                                                                 h->table32, h->u32, h->diag32);
+    } else {
+        constexpr int CB = 4;
+        k_diagonal<3, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 64, 0, s>>>(m, b, h->cell_code, h->table_index,
+                                                                                 h->table32, h->u32, h->diag32);
+    }
+    EVAP_CHECK_LAUNCH("diagonal");
+    k_diag_finish<<<blocks_for(N, 256), 256, 0, s>>>(m.M, m.Nu, m.faces, h->diag32, h->diag);
+    EVAP_CHECK_LAUNCH("diag_finish");
+    h->diag_valid = true;
+    return EVAP_OK;
+}
+
+// ----------------------------------------------------------------------------------------------- reductions
+constexpr int RED_THREADS = 256;
+constexpr int RED_BLOCKS = 304;  // 2 per SM
+
+struct FF {  // float-float accumulator
+    float hi, lo;
+};
+__device__ __forceinline__ void ff_add(FF& s, float v) {
+    const float t = s.hi + v;
+    const float bp = t - s.hi;
+    const float err = (s.hi - (t - bp)) + (v - bp);
+    s.hi = t;
+    s.lo += err;
+}
+
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double sh[RED_THREADS / 32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < RED_THREADS / 32; ++i) r += sh[i];
+    return r;
+}
+
+// partial[i * RED_BLOCKS + block] = sum_k V_i[k] w[k]   for i = blockIdx.y
+__global__ void k_mdot64(const double* __restrict__ V, int64_t ld, const double* __restrict__ w, int64_t N,
+                         double* __restrict__ partial) {
+    const double* v = V + blockIdx.y * ld;
+    double s = 0.0;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x)
+        s = fma(v[k], w[k], s);
+    s = block_sum(s);
+    if (threadIdx.x == 0) partial[blockIdx.y * RED_BLOCKS + blockIdx.x] = s;
+}
+
+__global__ void k_mdot32(const float* __restrict__ V, int64_t ld, const float* __restrict__ w, int64_t N,
+                         double* __restrict__ partial) {
+    const float* v = V + blockIdx.y * ld;
+    FF acc = {0.f, 0.f};
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
+        const float p = v[k] * w[k];
+        const float e = fmaf(v[k], w[k], -p);  // exact product p + e
+        ff_add(acc, p);
+        acc.lo += e;
+    }
+    double s = block_sum((double)acc.hi + (double)acc.lo);
+    if (threadIdx.x == 0) partial[blockIdx.y * RED_BLOCKS + blockIdx.x] = s;
+}
+
+// out[i] (+)= sum_b partial[i * RED_BLOCKS + b]
+__global__ void k_reduce_rows(const double* __restrict__ partial, double* out, int accumulate) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < RED_BLOCKS; b += blockDim.x) s += partial[blockIdx.x * RED_BLOCKS + b];
+    s = block_sum(s);
+    if (threadIdx.x == 0) out[blockIdx.x] = accumulate ? out[blockIdx.x] + s : s;
+}
+
+// w -= sum_{i<=j} h[i] V_i ; partial norm^2 of the result
+template <typename T>
+__global__ void k_maxpy_norm(const T* __restrict__ V, int64_t ld, const double* __restrict__ hcol, int nv, T* w,
+                             int64_t N, double* __restrict__ partial) {
+    __shared__ T hs[256];
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) hs[i] = (T)hcol[i];
+    __syncthreads();
+    double s64 = 0.0;
+    FF acc = {0.f, 0.f};
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
+        T v = w[k];
+        for (int i = 0; i < nv; ++i) v -= hs[i] * V[i * ld + k];
+        w[k] = v;
+        if (sizeof(T) == 8) {
+            s64 = fma((double)v, (double)v, s64);
+        } else {
+            const float fv = (float)v;
+            const float p = fv * fv;
+            ff_add(acc, p);
+            acc.lo += fmaf(fv, fv, -p);
+        }
+    }
+    double s = sizeof(T) == 8 ? s64 : (double)acc.hi + (double)acc.lo;
+    s = block_sum(s);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+template <typename T>
+__global__ void k_scale_to(const T* __restrict__ src, T* __restrict__ dst, const double* __restrict__ nrm2, int64_t N) {
+    const double inv = 1.0 / sqrt(*nrm2);
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x)
+        dst[k] = (T)(src[k] * inv);
+}
+
+template <typename T>
+__global__ void k_mul(const T* __restrict__ a, const T* __restrict__ dinv_src, T* __restrict__ out, int64_t N) {
+    // out = a / diag
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x)
+        out[k] = a[k] / dinv_src[k];
+}
+
+// x += diag^{-1} sum_i y[i] V_i
+template <typename T>
+__global__ void k_update(const T* __restrict__ V, int64_t ld, const double* __restrict__ y, int nv,
+                         const T* __restrict__ diag, T* x, int64_t N) {
+    __shared__ T ys[256];
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) ys[i] = (T)y[i];
+    __syncthreads();
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
+        T s = 0;
+        for (int i = 0; i < nv; ++i) s += ys[i] * V[i * ld + k];
+        x[k] += s / diag[k];
+    }
+}
+
+// r = b - Ax
+template <typename T>
+__global__ void k_residual(const T* __restrict__ b, const T* __restrict__ Ax, T* __restrict__ r, int64_t N) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x)
+        r[k] = b[k] - Ax[k];
+}
+
+__global__ void k_scaled_to_float(const double* __restrict__ r, const double* __restrict__ nrm2, float* __restrict__ out,
+                                  int64_t N) {
+    const double inv = 1.0 / sqrt(*nrm2);
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x)
+        out[k] = (float)(r[k] * inv);
+}
+
+__global__ void k_refine(double* x, const float* __restrict__ d, const double* __restrict__ nrm2, int64_t N) {
+    const double s = sqrt(*nrm2);
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x)
+        x[k] += s * (double)d[k];
+}
+
+// ---------------------------------------------------------------------------------------------- GMRES core
+struct Ctx {
+    evap_mesh* h;
+    cudaStream_t s;
+    int64_t N;
+    double* partial;   // [(m+1) * RED_BLOCKS]
+    double* dcol;      // device column [m+2]
+    double* dnorm;     // device scalar
+    double* hcol;      // pinned host [m+3]
+};
+
+template <typename T>
+static int apply_op(Ctx& c, const T* x, T* y) {
+    return launch_momentum<T>(c.h, x, y, (T*)nullptr, c.s);
+}
+
+template <typename T>
+__global__ void k_norm2(const T* __restrict__ v, int64_t N, double* __restrict__ partial) {
+    double s64 = 0.0;
+    FF acc = {0.f, 0.f};
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
+        if (sizeof(T) == 8) {
+            s64 = fma((double)v[k], (double)v[k], s64);
+        } else {
+            const float fv = (float)v[k];
+            const float p = fv * fv;
+            ff_add(acc, p);
+            acc.lo += fmaf(fv, fv, -p);
+        }
+    }
+    double s = sizeof(T) == 8 ? s64 : (double)acc.hi + (double)acc.lo;
+    s = block_sum(s);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+template <typename T>
+static int norm2_dev(Ctx& c, const T* v, double* out) {
+    // ||v||^2 -> out (device)
+    k_norm2<T><<<RED_BLOCKS, RED_THREADS, 0, c.s>>>(v, c.N, c.partial);
+    EVAP_CHECK_LAUNCH("norm");
+    k_reduce_rows<<<1, RED_THREADS, 0, c.s>>>(c.partial, out, 0);
+    EVAP_CHECK_LAUNCH("norm_reduce");
+    return EVAP_OK;
+}
+
+static int fetch(Ctx& c, const double* dev, int n, double* host) {
+    EVAP_CUDA(cudaMemcpyAsync(host, dev, n * sizeof(double), cudaMemcpyDeviceToHost, c.s));
+    EVAP_CUDA(cudaStreamSynchronize(c.s));
+    return EVAP_OK;
+}
+
+// GMRES(m) on A x = b with right preconditioner diag^{-1}; x updated in place.  Stops when the preconditioned
+// Arnoldi residual estimate is <= tol_abs or after maxit applications.  Returns applications used via *its.
+template <typename T>
+static int gmres(Ctx& c, int m, const T* b, T* x, const T* diag, T* V, T* w, T* z, double tol_abs, int maxit,
+                 int* its, double* res_out) {
+    const int64_t N = c.N;
+    const int G = blocks_for(N, 256);
+    std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+    int used = 0, rc;
+    double beta = 0.0;
+    while (true) {
+        // r = b - A x  into V_0 (unnormalized), beta = |r|
+        if ((rc = apply_op<T>(c, x, w))) return rc;
+        ++used;
+        k_residual<T><<<G, 256, 0, c.s>>>(b, w, V, N);
+        EVAP_CHECK_LAUNCH("residual");
+        if ((rc = norm2_dev<T>(c, V, c.dnorm))) return rc;
+        if ((rc = fetch(c, c.dnorm, 1, c.hcol))) return rc;
+        beta = std::sqrt(c.hcol[0]);
+        *res_out = beta;
+        if (beta <= tol_abs || used >= maxit || !(beta > 0.0)) break;
+        k_scale_to<T><<<G, 256, 0, c.s>>>(V, V, c.dnorm, N);
+        EVAP_CHECK_LAUNCH("scale");
+        std::fill(g.begin(), g.end(), 0.0);
+        g[0] = beta;
+        int j = 0;
+        bool done = false;
+        for (; j < m; ++j) {
+            T* Vj = V + (int64_t)j * N;
+            k_mul<T><<<G, 256, 0, c.s>>>(Vj, diag, z, N);
+            EVAP_CHECK_LAUNCH("precond");
+            if ((rc = apply_op<T>(c, z, w))) return rc;
+            ++used;
+            const int nv = j + 1;
+            for (int pass = 0; pass < 2; ++pass) {
+                if (sizeof(T) == 8)
+                    k_mdot64<<<dim3(RED_BLOCKS, nv), RED_THREADS, 0, c.s>>>((const double*)V, N, (const double*)w, N,
+                                                                            c.partial);
+                else
+                    k_mdot32<<<dim3(RED_BLOCKS, nv), RED_THREADS, 0, c.s>>>((const float*)V, N, (const float*)w, N,
+                                                                            c.partial);
+                EVAP_CHECK_LAUNCH("mdot");
+                k_reduce_rows<<<nv, RED_THREADS, 0, c.s>>>(c.partial, c.dcol + (pass ? m + 1 : 0), 0);
+                EVAP_CHECK_LAUNCH("mdot_reduce");
+                k_maxpy_norm<T><<<RED_BLOCKS, RED_THREADS, 0, c.s>>>(V, N, c.dcol + (pass ? m + 1 : 0), nv, w, N,
+                                                                     c.partial);
+                EVAP_CHECK_LAUNCH("maxpy");
+            }
+            k_reduce_rows<<<1, RED_THREADS, 0, c.s>>>(c.partial, c.dnorm, 0);
+            EVAP_CHECK_LAUNCH("norm_reduce");
+            // host column: h = h1 + h2, h_{j+1} = |w|
+            EVAP_CUDA(cudaMemcpyAsync(c.hcol, c.dcol, (size_t)(2 * m + 2) * sizeof(double), cudaMemcpyDeviceToHost, c.s));
+            EVAP_CUDA(cudaMemcpyAsync(c.hcol + 2 * m + 2, c.dnorm, sizeof(double), cudaMemcpyDeviceToHost, c.s));
+            EVAP_CUDA(cudaStreamSynchronize(c.s));
+            double* col = &H[(size_t)j * (m + 1)];
+            for (int i = 0; i <= j; ++i) col[i] = c.hcol[i] + c.hcol[m + 1 + i];
+            const double hn = std::sqrt(c.hcol[2 * m + 2]);
+            col[j + 1] = hn;
+            if (hn > 0.0 && j + 1 < m + 1) {
+                k_scale_to<T><<<G, 256, 0, c.s>>>(w, V + (int64_t)(j + 1) * N, c.dnorm, N);
+                EVAP_CHECK_LAUNCH("scale_next");
+            }
+            for (int i = 0; i < j; ++i) {
+                const double t0 = cs[i] * col[i] + sn[i] * col[i + 1];
+                col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+                col[i] = t0;
+            }
+            const double rr = std::hypot(col[j], col[j + 1]);
+            cs[j] = rr > 0.0 ? col[j] / rr : 1.0;
+            sn[j] = rr > 0.0 ? col[j + 1] / rr : 0.0;
+            col[j] = rr;
+            col[j + 1] = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            const double est = std::fabs(g[j + 1]);
+            if (est <= tol_abs || used >= maxit || !(hn > 0.0)) {
+                ++j;
+                done = true;
+                break;
+            }
+        }
+        // y = R^{-1} g, x += diag^{-1} V y
+        const int k = j;
+        for (int i = k - 1; i >= 0; --i) {
+            double s = g[i];
+            for (int l = i + 1; l < k; ++l) s -= H[(size_t)l * (m + 1) + i] * y[l];
+            y[i] = s / H[(size_t)i * (m + 1) + i];
+        }
+        EVAP_CUDA(cudaMemcpyAsync(c.dcol, y.data(), k * sizeof(double), cudaMemcpyHostToDevice, c.s));
+        k_update<T><<<G, 256, 0, c.s>>>(V, N, c.dcol, k, diag, x, N);
+        EVAP_CHECK_LAUNCH("update");
+        EVAP_CUDA(cudaStreamSynchronize(c.s));  // y is a pageable host buffer
+        (void)done;  // the true residual of the updated x is checked at the top of the loop
+    }
+    *its = used;
+    return EVAP_OK;
+}
+
+int solve_gmres(evap_mesh* h, const double* f, double* x, int mixed, int m, double rtol, int max_iter, int* iters,
+                double* relres, cudaStream_t s) {
+    int rc = launch_diagonal(h, s);
+    if (rc) return rc;
+    const int64_t N = 3 * h->m.Nu;
+    // workspace, every sub-array starting on a 256-byte boundary:
+    //   FP64: V [(m+1) N], w [N], z [N] doubles;  mixed: V [(m+1) N], w32, z32, r32, d32 [N] floats, r64, Ax [N] doubles
+    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t fV = al((size_t)(m + 1) * N * sizeof(float)), fN = al((size_t)N * sizeof(float));
+    const size_t dV = al((size_t)(m + 1) * N * sizeof(double)), dN = al((size_t)N * sizeof(double));
+    const size_t bytes = mixed ? fV + 4 * fN + 2 * dN : dV + 2 * dN;
+    if (h->ws_bytes < bytes) {
+        if (h->ws) cudaFree(h->ws);
+        h->ws = nullptr;
+        h->ws_bytes = 0;
+        EVAP_CUDA(cudaMalloc(&h->ws, bytes));
+        h->ws_bytes = bytes;
+    }
+    const size_t red_need = (size_t)(m + 2) * RED_BLOCKS + 2 * (m + 2) + 8;
+    if (h->red_len < red_need) {
+        if (h->red) cudaFree(h->red);
+        if (h->red_host) cudaFreeHost(h->red_host);
+        h->red = nullptr;
+        h->red_host = nullptr;
+        h->red_len = 0;
+        EVAP_CUDA(cudaMalloc(&h->red, red_need * sizeof(double)));
+        EVAP_CUDA(cudaMallocHost(&h->red_host, red_need * sizeof(double)));
+        h->red_len = red_need;
+    }
+    Ctx c;
+    c.h = h;
+    c.s = s;
+    c.N = N;
+    c.partial = h->red;
+    c.dcol = h->red + (size_t)(m + 2) * RED_BLOCKS;
+    c.dnorm = c.dcol + 2 * (m + 2);
+    c.hcol = h->red_host;
+    const int G = blocks_for(N, 256);
+    // |f|
+    if ((rc = norm2_dev<double>(c, f, c.dnorm))) return rc;
+    if ((rc = fetch(c, c.dnorm, 1, c.hcol))) return rc;
+    const double fn = std::sqrt(c.hcol[0]);
+    if (!(fn > 0.0)) {
+        EVAP_CUDA(cudaMemsetAsync(x, 0, N * sizeof(double), s));
+        EVAP_CUDA(cudaStreamSynchronize(s));
+        if (iters) *iters = 0;
+        if (relres) *relres = 0.0;
+        return EVAP_OK;
+    }
+    int used = 0;
+    double res = 0.0;
+    char* base = (char*)h->ws;
+    if (!mixed) {
+        double* V = (double*)base;
+        double* w = (double*)(base + dV);
+        double* z = (double*)(base + dV + dN);
+        int its = 0;
+        if ((rc = gmres<double>(c, m, f, x, h->diag, V, w, z, rtol * fn, max_iter, &its, &res))) return rc;
+        used = its;
+    } else {
+        float* V = (float*)base;
+        float* w32 = (float*)(base + fV);
+        float* z32 = (float*)(base + fV + fN);
+        float* r32 = (float*)(base + fV + 2 * fN);
+        float* d32 = (float*)(base + fV + 3 * fN);
+        double* r64 = (double*)(base + fV + 4 * fN);
+        double* Ax = (double*)(base + fV + 4 * fN + dN);
+        const double inner_rtol = 1e-5;
+        while (true) {
+            if ((rc = launch_momentum<double>(h, x, Ax, nullptr, s))) return rc;
+            ++used;
+            k_residual<double><<<G, 256, 0, s>>>(f, Ax, r64, N);
+            EVAP_CHECK_LAUNCH("residual64");
+            if ((rc = norm2_dev<double>(c, r64, c.dnorm))) return rc;
+            if ((rc = fetch(c, c.dnorm, 1, c.hcol))) return rc;
+            res = std::sqrt(c.hcol[0]);
+            if (res <= rtol * fn || used >= max_iter) break;
+            k_scaled_to_float<<<G, 256, 0, s>>>(r64, c.dnorm, r32, N);
+            EVAP_CHECK_LAUNCH("to32");
+            EVAP_CUDA(cudaMemsetAsync(d32, 0, N * sizeof(float), s));
+            int its = 0;
+            double inner_res = 0.0;
+            const int budget = std::min(max_iter - used, 4 * m);
+            if ((rc = gmres<float>(c, m, r32, d32, h->diag32, V, w32, z32, inner_rtol, budget, &its, &inner_res)))
+                return rc;
+            used += its;
+            // keep the FP64 residual norm on the device for the refinement scale
+            if ((rc = norm2_dev<double>(c, r64, c.dnorm))) return rc;
+            k_refine<<<G, 256, 0, s>>>(x, d32, c.dnorm, N);
+            EVAP_CHECK_LAUNCH("refine");
+        }
+    }
+    EVAP_CUDA(cudaStreamSynchronize(s));
+    if (iters) *iters = used;
+    if (relres) *relres = res / fn;
+    return res <= rtol * fn ? EVAP_OK : EVAP_ENOTCONV;
+}
+
+}  // namespace evap

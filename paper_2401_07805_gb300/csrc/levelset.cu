@@ -1,0 +1,112 @@
+// Matrix-free Q1 level-set operators with the 2^3 Gauss rule (Sec. 2.5), one thread per cell:
+//   EVAP_ADVECT      y_i = sum_q W [ N_i x + theta dt N_i (u_Gamma . grad x) ]            Eq. (weakFormLevelSet), CN
+//   EVAP_REINIT      y_i = sum_q W [ N_i x / dtau + eps (grad N_i . n)(grad x . n) ]      Eq. (reinitialization)
+//   EVAP_REINIT_RHS  y_i = sum_q W [ N_i x / dtau + (grad N_i . n) (1 - x^2) / 2 ]        explicit compressive flux
+// with n = grad phi / |grad phi| of the level set at the quadrature point (Eq. normal_vector).
+#include "evap_internal.cuh"
+
+namespace evap {
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(128) k_levelset(MeshArgs<T> m, Basis<T> bas, const T* __restrict__ phi,
+                                                  const T* __restrict__ ug, const T* __restrict__ x, T* __restrict__ y) {
+    const int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (cell >= m.ncell) return;
+    const int n = m.n;
+    const int64_t m1 = n + 1;
+    const int cx = (int)(cell % n), cy = (int)((cell / n) % n), cz = (int)(cell / ((int64_t)n * n));
+    int64_t node[8];
+    T xv[8], pv[8], uv[3][8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        node[j] = (cx + (j & 1)) + m1 * ((cy + ((j >> 1) & 1)) + m1 * (cz + (j >> 2)));
+        xv[j] = x[node[j]];
+        if (MODE == EVAP_ADVECT) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) uv[k][j] = ug[k * m.Nphi + node[j]];
+        } else {
+            pv[j] = phi[node[j]];
+        }
+    }
+    T out[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) out[j] = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int qx = q & 1, qy = (q >> 1) & 1, qz = q >> 2;
+        const T tx = bas.g2t[qx], ty = bas.g2t[qy], tz = bas.g2t[qz];
+        const T W = bas.g2w[qx] * bas.g2w[qy] * bas.g2w[qz] * m.vol_w;
+        const T Nx[2] = {T(1) - tx, tx}, Ny[2] = {T(1) - ty, ty}, Nz[2] = {T(1) - tz, tz};
+        const T Dd[2] = {T(-1), T(1)};
+        T N[8], dN[8][3];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int ja = j & 1, jb = (j >> 1) & 1, jc = j >> 2;
+            N[j] = Nx[ja] * Ny[jb] * Nz[jc];
+            dN[j][0] = Dd[ja] * Ny[jb] * Nz[jc] * m.inv_h;
+            dN[j][1] = Nx[ja] * Dd[jb] * Nz[jc] * m.inv_h;
+            dN[j][2] = Nx[ja] * Ny[jb] * Dd[jc] * m.inv_h;
+        }
+        T X = 0, GX[3] = {0, 0, 0};
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            X += N[j] * xv[j];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) GX[d] += dN[j][d] * xv[j];
+        }
+        T Fv, Gf[3] = {0, 0, 0};
+        if (MODE == EVAP_ADVECT) {
+            T U[3] = {0, 0, 0};
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) U[k] += N[j] * uv[k][j];
+            Fv = W * (X + m.theta * m.dt * (U[0] * GX[0] + U[1] * GX[1] + U[2] * GX[2]));
+        } else {
+            T g[3] = {0, 0, 0};
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+#pragma unroll
+                for (int d = 0; d < 3; ++d) g[d] += dN[j][d] * pv[j];
+            const T gn = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+            T nv[3] = {0, 0, 0};
+            if (gn > T(0)) {
+                nv[0] = g[0] / gn; nv[1] = g[1] / gn; nv[2] = g[2] / gn;
+            }
+            Fv = W * X / m.dtau;
+            const T s = (MODE == EVAP_REINIT) ? W * m.eps * (GX[0] * nv[0] + GX[1] * nv[1] + GX[2] * nv[2])
+                                              : W * T(0.5) * (T(1) - X * X);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) Gf[d] = s * nv[d];
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) out[j] += N[j] * Fv + dN[j][0] * Gf[0] + dN[j][1] * Gf[1] + dN[j][2] * Gf[2];
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) atomicAdd(&y[node[j]], out[j]);
+}
+
+template <typename T>
+int launch_levelset(evap_mesh* h, int mode, const T* x, T* y, cudaStream_t s) {
+    const MeshArgs<T> m = mesh_args<T>(h);
+    const Basis<T> b = cast_basis<T>(h->b);
+    const bool dbl = sizeof(T) == 8;
+    const T* phi = dbl ? (const T*)h->phi : (const T*)h->phi32;
+    const T* ug = dbl ? (const T*)h->ugamma : (const T*)h->ugamma32;
+    int rc = launch_fill<T>(y, m.Nphi, T(0), s);
+    if (rc) return rc;
+    const int threads = 128;
+    const unsigned grid = (unsigned)((m.ncell + threads - 1) / threads);
+    if (mode == EVAP_ADVECT)
+        k_levelset<T, EVAP_ADVECT><<<grid, threads, 0, s>>>(m, b, phi, ug, x, y);
+    else if (mode == EVAP_REINIT)
+        k_levelset<T, EVAP_REINIT><<<grid, threads, 0, s>>>(m, b, phi, ug, x, y);
+    else
+        k_levelset<T, EVAP_REINIT_RHS><<<grid, threads, 0, s>>>(m, b, phi, ug, x, y);
+    EVAP_CHECK_LAUNCH("levelset");
+    return EVAP_OK;
+}
+template int launch_levelset<double>(evap_mesh*, int, const double*, double*, cudaStream_t);
+template int launch_levelset<float>(evap_mesh*, int, const float*, float*, cudaStream_t);
+
+}  // namespace evap

@@ -1,0 +1,247 @@
+// Matrix-free momentum apply y = A x (velocity block of Eq. weakNavierStokes linearized about u0, App. D) with the
+// divergence row y_p = B x - g (Eq. continuity with the dilation rate of Eq. evaporDil), by sum factorization.
+//
+// Per cell (Sec. 2.5: y = sum_i R_i^T A_i R_i x):
+//   gather   x, u0 at the (P+1)^3 nodes (Dirichlet nodes of x read as 0)
+//   values   3 sweeps of the 1D matrix S[q][a] = l_a(t_q) per component            -> x_c, u0_c at the Gauss points
+//   grads    collocation derivative Dc at the Gauss points along each direction     -> d_b x_c, d_b u0_c
+//   flux     F_c  = W rho (c_m x_c + u0 . grad x_c + newton (grad u0 x)_c)
+//            T_cb = 2 W mu (eps_cb - tr(eps) (z n)_c (z n)_b),  eps = sym grad x          (Eq. modified_viscous_stress)
+//            rho, mu, z n from the FP64 coefficient table of interface cells or the pure-phase constants
+//   test     w_c = F_c + sum_b Dc^T T_cb, then 3 transposed sweeps S^T            -> nodal contributions
+//   scatter  atomic add into y (constrained rows hold y = x, written by the init kernel)
+// Thread layout: one thread per quadrature point, CB cells per block; sweeps go through shared memory.
+#include "evap_internal.cuh"
+
+namespace evap {
+
+__device__ __forceinline__ bool constrained_node(int gx, int gy, int gz, int M, unsigned f) {
+    return ((f & 1u) && gx == 0) || ((f & 2u) && gx == M - 1) || ((f & 4u) && gy == 0) ||
+           ((f & 8u) && gy == M - 1) || ((f & 16u) && gz == 0) || ((f & 32u) && gz == M - 1);
+}
+
+// y = x on Dirichlet DoFs, 0 elsewhere; y_p = 0.
+template <typename T>
+__global__ void k_momentum_init(int M, int64_t Nu, unsigned faces, const T* __restrict__ x, T* __restrict__ y,
+                                T* __restrict__ yp, int64_t Np) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 3 * Nu; i += stride) {
+        const int64_t node = i % Nu;
+        const int gx = (int)(node % M), gy = (int)((node / M) % M), gz = (int)(node / ((int64_t)M * M));
+        y[i] = constrained_node(gx, gy, gz, M, faces) ? x[i] : T(0);
+    }
+    if (yp)
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < Np; i += stride) yp[i] = T(0);
+}
+
+template <typename T, int P, int CB>
+__global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
+    k_momentum(MeshArgs<T> m, Basis<T> bas, const int8_t* __restrict__ code, const int32_t* __restrict__ tindex,
+               const T* __restrict__ table, const T* __restrict__ u0, const T* __restrict__ x, T* __restrict__ y,
+               T* __restrict__ yp) {
+    constexpr int Q = P + 1, NQ = Q * Q * Q;
+    __shared__ T sS[Q][Q], sDc[Q][Q], sN1[Q][2];
+    __shared__ T buf[2][CB][6][NQ];
+    const int tid = threadIdx.x;
+    const int lc = tid / NQ, t = tid % NQ;
+    const int64_t cell = (int64_t)blockIdx.x * CB + lc;
+    const bool active = cell < m.ncell;
+    if (tid < Q * Q) {
+        sS[tid / Q][tid % Q] = bas.S[tid / Q][tid % Q];
+        sDc[tid / Q][tid % Q] = bas.Dc[tid / Q][tid % Q];
+    }
+    if (tid < 2 * Q) sN1[tid / 2][tid % 2] = bas.N1[tid / 2][tid % 2];
+    const int a = t % Q, b = (t / Q) % Q, c = t / (Q * Q);
+    const int n = m.n, M = m.M;
+    int cx = 0, cy = 0, cz = 0;
+    int64_t gidx = 0;
+    bool cons = false;
+    if (active) {
+        cx = (int)(cell % n);
+        cy = (int)((cell / n) % n);
+        cz = (int)(cell / ((int64_t)n * n));
+        const int gx = P * cx + a, gy = P * cy + b, gz = P * cz + c;
+        gidx = gx + (int64_t)M * (gy + (int64_t)M * gz);
+        cons = constrained_node(gx, gy, gz, M, m.faces);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            buf[0][lc][k][t] = cons ? T(0) : x[k * m.Nu + gidx];
+            buf[0][lc][3 + k][t] = u0[k * m.Nu + gidx];
+        }
+    }
+    __syncthreads();
+    // values at the Gauss points: x-, y-, z-sweeps of S
+    if (active) {
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+            T s = 0;
+#pragma unroll
+            for (int k = 0; k < Q; ++k) s += sS[a][k] * buf[0][lc][f][k + Q * (b + Q * c)];
+            buf[1][lc][f][t] = s;
+        }
+    }
+    __syncthreads();
+    if (active) {
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+            T s = 0;
+#pragma unroll
+            for (int k = 0; k < Q; ++k) s += sS[b][k] * buf[1][lc][f][a + Q * (k + Q * c)];
+            buf[0][lc][f][t] = s;
+        }
+    }
+    __syncthreads();
+    if (active) {
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+            T s = 0;
+#pragma unroll
+            for (int k = 0; k < Q; ++k) s += sS[c][k] * buf[0][lc][f][a + Q * (b + Q * k)];
+            buf[1][lc][f][t] = s;
+        }
+    }
+    __syncthreads();
+    // quadrature-point physics and fluxes
+    T F[3] = {0, 0, 0}, Tf[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, rdiv = 0;
+    if (active) {
+        T X[3], U[3], G[3][3], GU[3][3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            X[k] = buf[1][lc][k][t];
+            U[k] = buf[1][lc][3 + k][t];
+            T g0 = 0, g1 = 0, g2 = 0, h0 = 0, h1 = 0, h2 = 0;
+#pragma unroll
+            for (int r = 0; r < Q; ++r) {
+                g0 += sDc[a][r] * buf[1][lc][k][r + Q * (b + Q * c)];
+                g1 += sDc[b][r] * buf[1][lc][k][a + Q * (r + Q * c)];
+                g2 += sDc[c][r] * buf[1][lc][k][a + Q * (b + Q * r)];
+                h0 += sDc[a][r] * buf[1][lc][3 + k][r + Q * (b + Q * c)];
+                h1 += sDc[b][r] * buf[1][lc][3 + k][a + Q * (r + Q * c)];
+                h2 += sDc[c][r] * buf[1][lc][3 + k][a + Q * (b + Q * r)];
+            }
+            G[k][0] = g0 * m.inv_h; G[k][1] = g1 * m.inv_h; G[k][2] = g2 * m.inv_h;
+            GU[k][0] = h0 * m.inv_h; GU[k][1] = h1 * m.inv_h; GU[k][2] = h2 * m.inv_h;
+        }
+        T rho, mu, nz[3], vd;
+        const int8_t cc = code[cell];
+        if (cc == CELL_TABLE) {
+            const T* tb = table + (int64_t)tindex[cell] * TAB_K * NQ + t;
+            rho = tb[0]; mu = tb[NQ]; nz[0] = tb[2 * NQ]; nz[1] = tb[3 * NQ]; nz[2] = tb[4 * NQ]; vd = tb[5 * NQ];
+        } else {
+            const bool liq = cc == CELL_LIQUID;
+            rho = liq ? m.rho_H1 : m.rho_H0;
+            mu = liq ? m.mu_H1 : m.mu_H0;
+            nz[0] = nz[1] = nz[2] = 0;
+            vd = 0;
+        }
+        const T W = bas.w[a] * bas.w[b] * bas.w[c] * m.vol_w;
+        const T wr = W * rho, wm = 2 * W * mu;
+        const T tr = G[0][0] + G[1][1] + G[2][2];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            T v = m.c_mass * X[k] + U[0] * G[k][0] + U[1] * G[k][1] + U[2] * G[k][2];
+            if (m.newton) v += GU[k][0] * X[0] + GU[k][1] * X[1] + GU[k][2] * X[2];
+            F[k] = wr * v;
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int l = 0; l < 3; ++l) Tf[k][l] = wm * (T(0.5) * (G[k][l] + G[l][k]) - tr * nz[k] * nz[l]);
+        rdiv = W * (tr - vd);
+    }
+    __syncthreads();
+    if (active) {
+#pragma unroll
+        for (int s = 0; s < 9; ++s) buf[s / 6][lc][s % 6][t] = Tf[s / 3][s % 3];
+        buf[1][lc][3][t] = rdiv;
+    }
+    __syncthreads();
+    // test with gradients: w_c = F_c + sum_b Dc^T T_cb
+    T wv[3];
+    if (active) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            T s0 = 0, s1 = 0, s2 = 0;
+#pragma unroll
+            for (int r = 0; r < Q; ++r) {
+                const int i0 = 3 * k + 0, i1 = 3 * k + 1, i2 = 3 * k + 2;
+                s0 += sDc[r][a] * buf[i0 / 6][lc][i0 % 6][r + Q * (b + Q * c)];
+                s1 += sDc[r][b] * buf[i1 / 6][lc][i1 % 6][a + Q * (r + Q * c)];
+                s2 += sDc[r][c] * buf[i2 / 6][lc][i2 % 6][a + Q * (b + Q * r)];
+            }
+            wv[k] = F[k] + (s0 + s1 + s2) * m.inv_h;
+        }
+        if (yp && t < 8) {  // divergence row: sum_q N1_j(q) W (div x - v_dil) for the 8 Q1 nodes of the cell
+            const int ja = t & 1, jb = (t >> 1) & 1, jc = t >> 2;
+            T s = 0;
+            for (int q = 0; q < NQ; ++q) {
+                const int qa = q % Q, qb = (q / Q) % Q, qc = q / (Q * Q);
+                s += sN1[qa][ja] * sN1[qb][jb] * sN1[qc][jc] * buf[1][lc][3][q];
+            }
+            const int64_t m1 = n + 1;
+            atomicAdd(&yp[(cx + ja) + m1 * ((cy + jb) + m1 * (cz + jc))], s);
+        }
+    }
+    __syncthreads();
+    if (active) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) buf[0][lc][k][t] = wv[k];
+    }
+    __syncthreads();
+    // transposed sweeps S^T: z, y, x
+    if (active) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            T s = 0;
+#pragma unroll
+            for (int q = 0; q < Q; ++q) s += sS[q][c] * buf[0][lc][k][a + Q * (b + Q * q)];
+            buf[1][lc][k][t] = s;
+        }
+    }
+    __syncthreads();
+    if (active) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            T s = 0;
+#pragma unroll
+            for (int q = 0; q < Q; ++q) s += sS[q][b] * buf[1][lc][k][a + Q * (q + Q * c)];
+            buf[0][lc][k][t] = s;
+        }
+    }
+    __syncthreads();
+    if (active && !cons) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            T s = 0;
+#pragma unroll
+            for (int q = 0; q < Q; ++q) s += sS[q][a] * buf[0][lc][k][q + Q * (b + Q * c)];
+            atomicAdd(&y[k * m.Nu + gidx], s);
+        }
+    }
+}
+
+template <typename T>
+int launch_momentum(evap_mesh* h, const T* x, T* y, T* yp, cudaStream_t s) {
+    const MeshArgs<T> m = mesh_args<T>(h);
+    const Basis<T> b = cast_basis<T>(h->b);
+    const bool dbl = sizeof(T) == 8;
+    const T* table = dbl ? (const T*)h->table : (const T*)h->table32;
+    const T* u0 = dbl ? (const T*)h->u : (const T*)h->u32;
+    k_momentum_init<T><<<blocks_for(3 * m.Nu, 256), 256, 0, s>>>(m.M, m.Nu, m.faces, x, y, yp, m.Nphi);
+    EVAP_CHECK_LAUNCH("momentum_init");
+    if (m.P == 2) {
+        constexpr int CB = 8;
+        const int64_t grid = (m.ncell + CB - 1) / CB;
+        k_momentum<T, 2, CB><<<(unsigned)grid, CB * 27, 0, s>>>(m, b, h->cell_code, h->table_index, table, u0, x, y, yp);
+    } else {
+        constexpr int CB = 4;
+        const int64_t grid = (m.ncell + CB - 1) / CB;
+        k_momentum<T, 3, CB><<<(unsigned)grid, CB * 64, 0, s>>>(m, b, h->cell_code, h->table_index, table, u0, x, y, yp);
+    }
+    EVAP_CHECK_LAUNCH("momentum");
+    return EVAP_OK;
+}
+template int launch_momentum<double>(evap_mesh*, const double*, double*, double*, cudaStream_t);
+template int launch_momentum<float>(evap_mesh*, const float*, float*, float*, cudaStream_t);
+
+}  // namespace evap

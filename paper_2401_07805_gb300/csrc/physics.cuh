@@ -1,0 +1,51 @@
+// Material law of the diffuse-interface model at one point, FP64 (device).
+#pragma once
+
+#include "evap_internal.cuh"
+
+namespace evap {
+
+// phi at d = 3 eps: tanh(3/2), the edge of the interface zone 0 < H < 1 (Eqs. initial_phi, heaviside).
+constexpr double PHI_BAND = 0x1.cf6f9786df577p-1;      // tanh(3/2), correctly rounded
+constexpr double PHI_GAS_BAND = 0x1.fd77d111a0b00p-1;  // tanh(3), correctly rounded (d = 6 eps)
+constexpr double PI = 3.14159265358979323846;
+
+struct Material {
+    double H, rho, mu, n[3], delta;
+    bool zone;
+};
+
+// Eq. (heaviside) with d from Eq. (distance), Eq. (rhoEff), Eq. (muEff), Eq. (normal_vector), Eq. (delta).
+// Outside the zone (|phi| >= tanh(3/2)) H is 0 or 1 and the logarithm is not evaluated.
+__device__ __forceinline__ Material material(double phi, double gx, double gy, double gz, const MeshArgs<double>& m) {
+    Material r;
+    r.zone = fabs(phi) < PHI_BAND;
+    double dH = 0.0, dd = 0.0;
+    if (r.zone) {
+        const double d = m.eps * log((1.0 + phi) / (1.0 - phi));
+        double sn, cs;
+        sincos(PI * d / (3.0 * m.eps), &sn, &cs);
+        r.H = 0.5 + d / (6.0 * m.eps) + sn / (2.0 * PI);
+        dH = (1.0 + cs) / (6.0 * m.eps);
+        dd = 2.0 * m.eps / (1.0 - phi * phi);
+    } else {
+        r.H = phi >= PHI_BAND ? 1.0 : 0.0;
+    }
+    r.rho = 1.0 / (r.H / m.rho_l + (1.0 - r.H) / m.rho_g);
+    r.mu = r.H * m.mu_l + (1.0 - r.H) * m.mu_g;
+    const double gn = sqrt(gx * gx + gy * gy + gz * gz);
+    if (gn > 0.0) {
+        r.n[0] = gx / gn; r.n[1] = gy / gn; r.n[2] = gz / gn;
+    } else {
+        r.n[0] = r.n[1] = r.n[2] = 0.0;
+    }
+    r.delta = r.zone ? dH * dd * gn : 0.0;
+    return r;
+}
+
+// Whether the corrected-strain term is active at a point (Sec. 2.4.2; zone gate or everywhere).
+__device__ __forceinline__ bool correction_on(const MeshArgs<double>& m, bool zone) {
+    return m.stress != 0 && (m.corr_zone != 0 || zone);
+}
+
+}  // namespace evap

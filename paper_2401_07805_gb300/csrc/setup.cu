@@ -1,0 +1,364 @@
+// evap_set_fields work: field preparation, FP64 quadrature-point coefficient table of the interface cells, and
+// the level-set transport velocity with closest-point projection (App. C).
+#include <cmath>
+
+#include "physics.cuh"
+
+namespace evap {
+
+template <typename T>
+__global__ void k_fill(T* p, int64_t n, T v) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+__global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = (float)a[i];
+}
+
+template <typename T>
+int launch_fill(T* p, int64_t n, T v, cudaStream_t s) {
+    k_fill<T><<<blocks_for(n, 256), 256, 0, s>>>(p, n, v);
+    EVAP_CHECK_LAUNCH("fill");
+    return EVAP_OK;
+}
+template int launch_fill<double>(double*, int64_t, double, cudaStream_t);
+template int launch_fill<float>(float*, int64_t, float, cudaStream_t);
+
+int launch_to_float(const double* a, float* b, int64_t n, cudaStream_t s) {
+    k_to_float<<<blocks_for(n, 256), 256, 0, s>>>(a, b, n);
+    EVAP_CHECK_LAUNCH("to_float");
+    return EVAP_OK;
+}
+
+// phi clamped to [-1, 1]; FP32 copies of phi and u.
+__global__ void k_prepare(double* phi, float* phi32, const double* __restrict__ u, float* __restrict__ u32,
+                          int64_t Np, int64_t Nu3) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < Np; i += stride) {
+        double v = phi[i];
+        v = v > 1.0 ? 1.0 : (v < -1.0 ? -1.0 : v);
+        phi[i] = v;
+        phi32[i] = (float)v;
+    }
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < Nu3; i += stride) u32[i] = (float)u[i];
+}
+
+// Q1 field value and physical gradient at reference point (t[qx], t[qy], t[qz]) of cell (cx, cy, cz).
+__device__ __forceinline__ void q1_at(const double* __restrict__ f, int n, int cx, int cy, int cz, double x, double y,
+                                      double z, double inv_h, double& val, double g[3]) {
+    const int m1 = n + 1;
+    val = 0.0;
+    g[0] = g[1] = g[2] = 0.0;
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                const double v = f[(cx + a) + (int64_t)m1 * ((cy + b) + (int64_t)m1 * (cz + c))];
+                const double wx = a ? x : 1.0 - x, wy = b ? y : 1.0 - y, wz = c ? z : 1.0 - z;
+                const double dx = a ? 1.0 : -1.0, dy = b ? 1.0 : -1.0, dz = c ? 1.0 : -1.0;
+                val += wx * wy * wz * v;
+                g[0] += dx * wy * wz * v;
+                g[1] += wx * dy * wz * v;
+                g[2] += wx * wy * dz * v;
+            }
+    g[0] *= inv_h;
+    g[1] *= inv_h;
+    g[2] *= inv_h;
+}
+
+// Cell classification: all quadrature points liquid (H = 1), all gas (H = 0), or a table cell (interface zone,
+// mixed phases, or correction applied everywhere).  Table cells get a slot by an atomic counter.
+__global__ void k_classify(MeshArgs<double> m, Basis<double> b, const double* __restrict__ phi, int8_t* code,
+                           int32_t* tindex, int32_t* counter) {
+    const int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (cell >= m.ncell) return;
+    const int n = m.n;
+    const int cx = (int)(cell % n), cy = (int)((cell / n) % n), cz = (int)(cell / ((int64_t)n * n));
+    bool all_liq = true, all_gas = true;
+    for (int qz = 0; qz < b.Q; ++qz)
+        for (int qy = 0; qy < b.Q; ++qy)
+            for (int qx = 0; qx < b.Q; ++qx) {
+                double v, g[3];
+                q1_at(phi, n, cx, cy, cz, b.t[qx], b.t[qy], b.t[qz], m.inv_h, v, g);
+                all_liq = all_liq && (v >= PHI_BAND);
+                all_gas = all_gas && (v <= -PHI_BAND);
+            }
+    const bool everywhere = m.stress != 0 && m.corr_zone != 0;
+    int8_t c = (!everywhere && all_liq) ? CELL_LIQUID : ((!everywhere && all_gas) ? CELL_GAS : CELL_TABLE);
+    code[cell] = c;
+    tindex[cell] = c == CELL_TABLE ? atomicAdd(counter, 1) : -1;
+}
+
+// Table entries at one quadrature point of a table cell: rho, mu, z n (z = correction gate), v_dil (Eq. evaporDil).
+__global__ void k_fill_table(MeshArgs<double> m, Basis<double> b, const double* __restrict__ phi,
+                             const double* __restrict__ mdot, const int8_t* __restrict__ code,
+                             const int32_t* __restrict__ tindex, double* table, float* table32) {
+    const int nq = b.Q * b.Q * b.Q;
+    const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t cell = gid / nq;
+    if (cell >= m.ncell || code[cell] != CELL_TABLE) return;
+    const int q = (int)(gid % nq);
+    const int qx = q % b.Q, qy = (q / b.Q) % b.Q, qz = q / (b.Q * b.Q);
+    const int n = m.n;
+    const int cx = (int)(cell % n), cy = (int)((cell / n) % n), cz = (int)(cell / ((int64_t)n * n));
+    double ph, g[3], md, gm[3];
+    q1_at(phi, n, cx, cy, cz, b.t[qx], b.t[qy], b.t[qz], m.inv_h, ph, g);
+    q1_at(mdot, n, cx, cy, cz, b.t[qx], b.t[qy], b.t[qz], m.inv_h, md, gm);
+    const Material mat = material(ph, g[0], g[1], g[2], m);
+    const double z = correction_on(m, mat.zone) ? 1.0 : 0.0;
+    const double vals[TAB_K] = {mat.rho, mat.mu, z * mat.n[0], z * mat.n[1], z * mat.n[2],
+                                md * (1.0 / m.rho_l - 1.0 / m.rho_g) * mat.delta};
+    const int64_t base = (int64_t)tindex[cell] * TAB_K * nq + q;
+#pragma unroll
+    for (int k = 0; k < TAB_K; ++k) {
+        table[base + (int64_t)k * nq] = vals[k];
+        table32[base + (int64_t)k * nq] = (float)vals[k];
+    }
+}
+
+int launch_setup_coefficients(evap_mesh* h, cudaStream_t s) {
+    const MeshArgs<double>& m = h->m;
+    k_prepare<<<blocks_for(3 * m.Nu, 256), 256, 0, s>>>(h->phi, h->phi32, h->u, h->u32, m.Nphi, 3 * m.Nu);
+    EVAP_CHECK_LAUNCH("prepare");
+    EVAP_CUDA(cudaMemsetAsync(h->table_count, 0, sizeof(int32_t), s));
+    k_classify<<<blocks_for(m.ncell, 128, 1LL << 40), 128, 0, s>>>(m, h->b, h->phi, h->cell_code, h->table_index,
+                                                                   h->table_count);
+    EVAP_CHECK_LAUNCH("classify");
+    int32_t count = 0;
+    EVAP_CUDA(cudaMemcpyAsync(&count, h->table_count, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    EVAP_CUDA(cudaStreamSynchronize(s));
+    const int nq = h->b.Q * h->b.Q * h->b.Q;
+    if (count > h->table_cap) {
+        if (h->table) cudaFree(h->table);
+        if (h->table32) cudaFree(h->table32);
+        h->table = nullptr;
+        h->table32 = nullptr;
+        h->table_cap = 0;
+        const int64_t cap = count + count / 8 + 16;
+        EVAP_CUDA(cudaMalloc(&h->table, cap * TAB_K * nq * sizeof(double)));
+        EVAP_CUDA(cudaMalloc(&h->table32, cap * TAB_K * nq * sizeof(float)));
+        h->table_cap = cap;
+    }
+    if (count > 0) {
+        const int64_t total = m.ncell * nq;
+        k_fill_table<<<blocks_for(total, 256, 1LL << 40), 256, 0, s>>>(m, h->b, h->phi, h->mdot, h->cell_code,
+                                                                       h->table_index, h->table, h->table32);
+        EVAP_CHECK_LAUNCH("fill_table");
+    }
+    return EVAP_OK;
+}
+
+// ------------------------------------------------------------------------------------------ transport velocity
+// Point evaluation in cell units s = y / h: cell = clamp(floor(s), 0, n - 1), trilinear phi, Q_p velocity.
+struct PointEval {
+    const double* phi;
+    const double* u;
+    MeshArgs<double> m;
+    double gl[MAXQ];  // Gauss-Lobatto support points of the velocity element
+
+    __device__ void locate(const double s[3], int k[3], double xi[3]) const {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            int c = (int)floor(s[a]);
+            c = c < 0 ? 0 : (c > m.n - 1 ? m.n - 1 : c);
+            k[a] = c;
+            xi[a] = s[a] - c;
+        }
+    }
+    __device__ void phi_grad(const double s[3], double& val, double g[3]) const {
+        int k[3];
+        double xi[3];
+        locate(s, k, xi);
+        q1_at(phi, m.n, k[0], k[1], k[2], xi[0], xi[1], xi[2], m.inv_h, val, g);
+    }
+    __device__ void velocity(const double s[3], double out[3]) const {
+        int k[3];
+        double xi[3];
+        locate(s, k, xi);
+        const int P = m.P, Q = P + 1;
+        double l[3][MAXQ];
+        for (int d = 0; d < 3; ++d)
+            for (int a = 0; a < Q; ++a) {
+                double v = 1.0;
+                for (int j = 0; j < Q; ++j)
+                    if (j != a) v *= (xi[d] - gl[j]) / (gl[a] - gl[j]);
+                l[d][a] = v;
+            }
+        out[0] = out[1] = out[2] = 0.0;
+        for (int c = 0; c < Q; ++c)
+            for (int b = 0; b < Q; ++b)
+                for (int a = 0; a < Q; ++a) {
+                    const int64_t node = (int64_t)(P * k[0] + a) +
+                                         (int64_t)m.M * ((int64_t)(P * k[1] + b) + (int64_t)m.M * (P * k[2] + c));
+                    const double wgt = l[0][a] * l[1][b] * l[2][c];
+                    out[0] += wgt * u[node];
+                    out[1] += wgt * u[m.Nu + node];
+                    out[2] += wgt * u[2 * m.Nu + node];
+                }
+    }
+};
+
+constexpr double PHI_CLAMP = 1.0 - 0x1p-40;
+constexpr int CPP_NORMAL_STEPS = 20;
+constexpr int CPP_BACKTRACK = 6;
+
+__device__ __forceinline__ double clampd(double v, double lo, double hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+// Normal steps y <- y - (d(y) - d*) / |grad d(y)| n(y) (App. C), returns whether |d(y) - d*| <= tol h.
+__device__ bool cpp_project(const PointEval& e, double y[3], double d_t, double tol) {
+    const double eps = e.m.eps, h = e.m.h, nn = (double)e.m.n;
+    for (int it = 0; it < CPP_NORMAL_STEPS; ++it) {
+        double ph, g[3];
+        e.phi_grad(y, ph, g);
+        ph = clampd(ph, -PHI_CLAMP, PHI_CLAMP);
+        const double r = eps * log((1.0 + ph) / (1.0 - ph)) - d_t;
+        if (fabs(r) <= tol * h) return true;
+        const double nrm = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+        if (nrm == 0.0) return false;
+        const double grad_d = 2.0 * eps / (1.0 - ph * ph) * nrm;
+        const double step = r / grad_d / h;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) y[a] = clampd(y[a] - step * (g[a] / nrm), 0.0, nn);
+    }
+    double ph, g[3];
+    e.phi_grad(y, ph, g);
+    ph = clampd(ph, -PHI_CLAMP, PHI_CLAMP);
+    return fabs(eps * log((1.0 + ph) / (1.0 - ph)) - d_t) <= tol * h;
+}
+
+// Components of y - x along the tangents t0, t1 of the isocontour at y (App. C).
+__device__ void cpp_tangential(const PointEval& e, const double x[3], const double y[3], double tp[3]) {
+    double ph, g[3];
+    e.phi_grad(y, ph, g);
+    const double nrm = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    tp[0] = tp[1] = tp[2] = 0.0;
+    if (nrm == 0.0) return;
+    const double nv[3] = {g[0] / nrm, g[1] / nrm, g[2] / nrm};
+    double v[3] = {1.0, 0.0, 0.0};
+    if (fabs(nv[0]) > 0.9) { v[0] = 0.0; v[1] = 1.0; }
+    const double vn = v[0] * nv[0] + v[1] * nv[1] + v[2] * nv[2];
+    double t0[3] = {v[0] - vn * nv[0], v[1] - vn * nv[1], v[2] - vn * nv[2]};
+    const double t0n = sqrt(t0[0] * t0[0] + t0[1] * t0[1] + t0[2] * t0[2]);
+    if (t0n > 0.0) { t0[0] /= t0n; t0[1] /= t0n; t0[2] /= t0n; }
+    const double t1[3] = {nv[1] * t0[2] - nv[2] * t0[1], nv[2] * t0[0] - nv[0] * t0[2], nv[0] * t0[1] - nv[1] * t0[0]};
+    const double dl[3] = {y[0] - x[0], y[1] - x[1], y[2] - x[2]};
+    const double a0 = dl[0] * t0[0] + dl[1] * t0[1] + dl[2] * t0[2];
+    const double a1 = dl[0] * t1[0] + dl[1] * t1[1] + dl[2] * t1[2];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) tp[a] = a0 * t0[a] + a1 * t1[a];
+}
+
+__device__ __forceinline__ double dist3(const double a[3], const double b[3]) {
+    const double d0 = a[0] - b[0], d1 = a[1] - b[1], d2 = a[2] - b[2];
+    return sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+}
+
+// Closest point of x on d(phi_h) = d_t with the backtracked tangential step; returns converged.
+__device__ bool cpp_closest(const PointEval& e, const double x[3], double y[3], double d_t, double tol, int kmax) {
+    const double nn = (double)e.m.n;
+    y[0] = x[0]; y[1] = x[1]; y[2] = x[2];
+    if (!cpp_project(e, y, d_t, tol)) return false;
+    double dist = dist3(y, x);
+    for (int k = 0; k < kmax; ++k) {
+        double tp[3];
+        cpp_tangential(e, x, y, tp);
+        bool accepted = false;
+        double omega = 1.0;
+        double yn[3];
+        for (int bt = 0; bt < CPP_BACKTRACK; ++bt) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) yn[a] = clampd(y[a] - omega * tp[a], 0.0, nn);
+            const bool on = cpp_project(e, yn, d_t, tol);
+            const double dn = dist3(yn, x);
+            if (on && dn < dist) {
+                accepted = true;
+                dist = dn;
+                break;
+            }
+            omega *= 0.5;
+        }
+        if (!accepted) return true;
+        const double step = dist3(yn, y);
+        y[0] = yn[0]; y[1] = yn[1]; y[2] = yn[2];
+        if (step <= tol) return true;
+    }
+    return false;
+}
+
+// One thread per Q1 node: variant 1 (Eq. transport_vel_local_continuous), 2 (liquid extension) or 3 (gas).
+__global__ void k_transport_velocity(PointEval e, const double* __restrict__ mdot, double tol, int kmax,
+                                     double* __restrict__ ug, int32_t* __restrict__ flags,
+                                     unsigned long long* flag_count) {
+    const MeshArgs<double>& m = e.m;
+    const int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (node >= m.Nphi) return;
+    const int m1 = m.n + 1;
+    const int i = (int)(node % m1), j = (int)((node / m1) % m1), k = (int)(node / ((int64_t)m1 * m1));
+    const double sx[3] = {(double)i, (double)j, (double)k};
+    const double phx = e.phi[node];
+    double ph, g[3];
+    e.phi_grad(sx, ph, g);
+    const double nrm = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    double nx[3] = {0.0, 0.0, 0.0};
+    if (nrm > 0.0) { nx[0] = g[0] / nrm; nx[1] = g[1] / nrm; nx[2] = g[2] / nrm; }
+    const double mx = mdot[node];
+    double out[3];
+    int flag = 0;
+    if (m.variant == 1) {
+        const Material mat = material(phx, 0.0, 0.0, 0.0, m);
+        const int64_t vn = (int64_t)(m.P * i) + (int64_t)m.M * ((int64_t)(m.P * j) + (int64_t)m.M * (m.P * k));
+        const double c = mx / mat.rho;
+        out[0] = e.u[vn] + c * nx[0];
+        out[1] = e.u[m.Nu + vn] + c * nx[1];
+        out[2] = e.u[2 * m.Nu + vn] + c * nx[2];
+    } else {
+        bool band;
+        double d_t, rho_t;
+        if (m.variant == 2) {
+            band = (-PHI_GAS_BAND < phx) && (phx < PHI_BAND);
+            d_t = 3.0 * m.eps;
+            rho_t = m.rho_l;
+        } else {
+            band = (-PHI_BAND < phx) && (phx < PHI_GAS_BAND);
+            d_t = -3.0 * m.eps;
+            rho_t = m.rho_g;
+        }
+        double y[3] = {sx[0], sx[1], sx[2]};
+        if (band) flag = cpp_closest(e, sx, y, d_t, tol, kmax) ? 0 : 1;
+        e.velocity(y, out);
+        const double c = mx / rho_t;
+        out[0] += c * nx[0];
+        out[1] += c * nx[1];
+        out[2] += c * nx[2];
+    }
+    ug[node] = out[0];
+    ug[m.Nphi + node] = out[1];
+    ug[2 * m.Nphi + node] = out[2];
+    flags[node] = flag;
+    if (flag) atomicAdd(flag_count, 1ULL);
+}
+
+int launch_transport_velocity(evap_mesh* h, cudaStream_t s) {
+    PointEval e;
+    e.phi = h->phi;
+    e.u = h->u;
+    e.m = h->m;
+    const int P = h->m.P;
+    if (P == 2) {
+        e.gl[0] = 0.0; e.gl[1] = 0.5; e.gl[2] = 1.0; e.gl[3] = 0.0;
+    } else {
+        const double r = 0.5 / std::sqrt(5.0);
+        e.gl[0] = 0.0; e.gl[1] = 0.5 - r; e.gl[2] = 0.5 + r; e.gl[3] = 1.0;
+    }
+    EVAP_CUDA(cudaMemsetAsync(h->flag_count, 0, sizeof(unsigned long long), s));
+    k_transport_velocity<<<blocks_for(h->m.Nphi, 128, 1LL << 40), 128, 0, s>>>(
+        e, h->mdot, h->prm.cpp_tol, h->prm.cpp_kmax, h->ugamma, h->cpp_flags, h->flag_count);
+    EVAP_CHECK_LAUNCH("transport_velocity");
+    return launch_to_float(h->ugamma, h->ugamma32, 3 * h->m.Nphi, s);
+}
+
+}  // namespace evap
