@@ -136,6 +136,18 @@ int evap_solve(evap_handle h, const double* f, double* x, int mixed, int restart
  * evaluated in FP32 arithmetic from the FP64 coefficient table and written as double. */
 int evap_jacobi_diagonal(evap_handle h, double* diag, void* stream);
 
+/* Allocation-free variant of evap_jacobi_diagonal, for callers that cannot let the library call cudaMalloc when
+ * they need the diagonal: their device memory is owned by another allocator, or they must not let the library
+ * synchronize the device (cudaMalloc/cudaFree may).  The paper has no counterpart.
+ * Writes the same diagonal [3 N_u] (FP32 arithmetic, written as double, 1 on Dirichlet DoFs) into diag, accumulating
+ * in a fixed 16 MiB array that is part of the library image on every GPU that loads it (held until exit).  Limit:
+ * 3 N_u <= 4194304 (Q2 up to 55^3 cells, Q3 up to 36^3); larger meshes return EVAP_EINVAL.  The handle's device must be
+ * current.  The first call on a device looks up that array's device address (cudaGetSymbolAddress); make that
+ * first call before any stream capture.  The array keeps the last call's contents and is cleared at the start of
+ * every call; calls that overlap on the GPU (other streams, other handles, other threads) race on it and must be
+ * serialized by the caller.  Calls no cudaMalloc, cudaFree or allocating library routine. */
+int evap_jacobi_diagonal_noalloc(evap_handle h, double* diag, void* stream);
+
 const char* evap_status_string(int status);
 const char* evap_last_error(void);
 

@@ -55,6 +55,7 @@ SIGNATURES = {
     "evap_solve": (_c_int, [_vp, _vp, _vp, _c_int, _c_int, _c_dbl, _c_int, ctypes.POINTER(_c_int),
                             ctypes.POINTER(_c_dbl), _vp]),
     "evap_jacobi_diagonal": (_c_int, [_vp, _vp, _vp]),
+    "evap_jacobi_diagonal_noalloc": (_c_int, [_vp, _vp, _vp]),
     "evap_status_string": (ctypes.c_char_p, [_c_int]),
     "evap_last_error": (ctypes.c_char_p, []),
     "evap_launch_count": (ctypes.c_int64, []),

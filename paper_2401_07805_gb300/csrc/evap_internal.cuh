@@ -121,6 +121,7 @@ int launch_levelset(evap_mesh* h, int mode, const T* x, T* y, cudaStream_t s);
 int launch_adjoint(evap_mesh* h, const double* w, const double* wp, const double* x, double* gx, double* gu,
                    double* gphi, double* gm, cudaStream_t s);
 int launch_diagonal(evap_mesh* h, cudaStream_t s);
+int launch_diagonal_into(evap_mesh* h, float* acc, double* out, cudaStream_t s);
 int solve_gmres(evap_mesh* h, const double* f, double* x, int mixed, int restart, double rtol, int max_iter,
                 int* iters, double* relres, cudaStream_t s);
 

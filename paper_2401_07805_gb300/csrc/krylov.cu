@@ -141,6 +141,28 @@ int launch_diagonal(evap_mesh* h, cudaStream_t s) {
     return EVAP_OK;
 }
 
+// Same diagonal, accumulated in the caller-given FP32 array acc [3 N_u] and written as double to out [3 N_u];
+// allocates nothing (used by the allocation-free entry point).
+int launch_diagonal_into(evap_mesh* h, float* acc, double* out, cudaStream_t s) {
+    const int64_t N = 3 * h->m.Nu;
+    EVAP_CUDA(cudaMemsetAsync(acc, 0, N * sizeof(float), s));
+    const MeshArgs<float> m = mesh_args<float>(h);
+    const Basis<float> b = cast_basis<float>(h->b);
+    if (m.P == 2) {
+        constexpr int CB = 8;
+        k_diagonal<2, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 27, 0, s>>>(m, b, h->cell_code, h->table_index,
+                                                                                 h->table32, h->u32, acc);
+    } else {
+        constexpr int CB = 4;
+        k_diagonal<3, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 64, 0, s>>>(m, b, h->cell_code, h->table_index,
+                                                                                 h->table32, h->u32, acc);
+    }
+    EVAP_CHECK_LAUNCH("diagonal_into");
+    k_diag_finish<<<blocks_for(N, 256), 256, 0, s>>>(m.M, m.Nu, m.faces, acc, out);
+    EVAP_CHECK_LAUNCH("diag_finish_into");
+    return EVAP_OK;
+}
+
 // ----------------------------------------------------------------------------------------------- reductions
 constexpr int RED_THREADS = 256;
 constexpr int RED_BLOCKS = 304;  // 2 per SM
