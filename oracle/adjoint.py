@@ -85,7 +85,7 @@ def param_gradients(pb: momentum.Problem, x, w, w_p=None):
         dmu_dH = prm["mu_l"] - prm["mu_g"]
         dL_dphi = (dL_drho * drho_dH + dL_dmu * dmu_dH) * dH * dd
         dL_dg = np.zeros_like(gphi)
-        nz = gnorm > 0.0
+        nz = physics.has_normal(gnorm, mesh.h)
         proj = dL_dn - np.einsum("nqa,nqa->nq", dL_dn, n)[..., None] * n
         dL_dg[nz] = proj[nz] / gnorm[nz][:, None]
         dL_dm = np.zeros_like(phi_q)

@@ -26,7 +26,7 @@ def q1_rule(mesh: fe.Mesh):
 
 def _normal_at_qp(mesh, phi, d1, b1):
     phin = phi[d1]
-    return physics.normal(np.einsum("nj,bjq->nqb", phin, b1.G))
+    return physics.normal(np.einsum("nj,bjq->nqb", phin, b1.G), mesh.h)
 
 
 def _assemble(mesh: fe.Mesh, elem_fn) -> sp.csr_matrix:

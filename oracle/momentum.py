@@ -76,7 +76,7 @@ def qp_fields(pb: Problem, cells: np.ndarray):
     H, _, _, _, zone = physics.heaviside_parts(phi_q, prm["eps"])
     rho = physics.density(H, prm["rho_l"], prm["rho_g"], pb.rho_mode)
     mu = physics.viscosity(H, prm["mu_l"], prm["mu_g"])
-    n = physics.normal(gphi)
+    n = physics.normal(gphi, mesh.h)
     vdil = physics.dilation_rate(mdot_q, phi_q, gphi, prm["eps"], prm["rho_l"], prm["rho_g"])
     if int(prm.get("stress", 1)) == 0:
         z = np.zeros_like(phi_q)

@@ -83,12 +83,23 @@ def viscosity(H, mu_l, mu_g):
     return H * mu_l + (1.0 - H) * mu_g
 
 
-def normal(grad_phi):
-    """Unit normal of Eq. (normal_vector), grad_phi[..., 3]; zero where the gradient vanishes exactly."""
+GRAD_TINY = 1e-4  # |grad phi| h at or below this: phi varies by < 1e-4 across a cell (> ~9 eps from the interface)
+
+
+def has_normal(gnorm, h):
+    """Where the normal of Eq. (normal_vector) is taken as defined: |grad phi| h > 1e-4.  Reading: where phi has
+    saturated towards +-1 (more than ~9 eps from any interface, outside the interface zone and the projection band)
+    the direction of grad phi is ill-conditioned (relative error ~ 1e-16 / (|grad phi| h), pure rounding noise where
+    phi is exactly +-1) and without physical meaning; n is taken as 0 there."""
+    return np.asarray(gnorm) * h > GRAD_TINY
+
+
+def normal(grad_phi, h):
+    """Unit normal of Eq. (normal_vector), grad_phi[..., 3]; zero where the gradient is negligible (has_normal)."""
     g = np.asarray(grad_phi, dtype=float)
     nrm = np.sqrt(np.sum(g * g, axis=-1, keepdims=True))
     out = np.zeros_like(g)
-    nz = nrm[..., 0] > 0.0
+    nz = has_normal(nrm[..., 0], h)
     out[nz] = g[nz] / nrm[nz]
     return out
 

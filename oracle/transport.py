@@ -14,19 +14,23 @@ Readings where App. C leaves details open (the same on the GPU):
   * a normal step moves y along n(y) by (d(y) - d*) / |grad d(y)|, d = d(phi_h); App. C writes the step for a
     distance function (|grad d| = 1), which d(phi_h) is only approximately when h is comparable to eps, and the
     plain step then converges slowly or overshoots.
-  * a projection is a sequence of at most 20 normal steps, stopping once |d(y) - d*| <= tol h.  The iteration
+  * a projection is a sequence of normal steps, stopping once |d(y) - d*| <= tol h: at most 20 from the node, at
+    most 6 for a trial point of the tangential step (it starts next to the isocontour).  The iteration
     starts with the projection of x.  Each outer iteration then takes the tangential step (t0 = v - (v.n) n
     normalised, t1 = n x t0, v = e_x unless |n_x| > 0.9, then e_y; it maps y to x + ((y - x).n(y)) n(y)) followed
     by a projection.  The full tangential step is a gradient step on |y - x|^2 along the isocontour that
     overshoots by the ratio of the distance to the curvature radius, so the step is read as backtracked: its length
     factor is halved (1, 1/2, ..., 1/32) until the projected point reached the isocontour and is strictly closer
-    to x; if none is, the current point is final.  The iteration also stops when |y^{k+1} - y^k| <= tol (cell units).
+    to x; if none is, the current point is final.  The iteration also stops when |y^{k+1} - y^k| <= tol (cell units)
+    or when an accepted step shortens |y - x| by at most 1e-12 of it (|y - x| is quadratic in the tangential error,
+    so this pins y to ~1e-6 cells; it ends the zigzag along creases of the piecewise-trilinear isocontour).
     A node is flagged as not converged when the first projection does not reach the isocontour (e.g. it does not
     exist inside a thin droplet) or after kmax outer iterations.
   * positions are handled in cell units s = y / h and clamped to the domain [0, n]^3; point location takes
     cell = clamp(floor(s), 0, n - 1) per axis; phi and grad phi are the trilinear Q1 interpolant of that cell,
     u the Q_p interpolant; d(phi) uses phi clamped to |phi| <= 1 - 2^-40.
-  * n(x) is the normalised gradient of the Q1 interpolant at the node (point-located as above), 0 if it vanishes.
+  * n(x) is the normalised gradient of the Q1 interpolant at the node (point-located as above), 0 where it is
+    negligible (physics.has_normal).
 """
 from __future__ import annotations
 
@@ -38,6 +42,8 @@ from . import fe, physics
 
 PHI_CLAMP = 1.0 - 2.0 ** -40
 BACKTRACK = 6  # tangential step lengths tried per outer iteration
+TRIAL_STEPS = 6  # normal steps of the projection of a trial point (it starts next to the isocontour)
+STALL = 1e-12  # an accepted step shortening |y - x| by less than this fraction ends the iteration
 
 
 class PointEval:
@@ -91,14 +97,14 @@ def _unit(g):
     return (g / nrm if nrm > 0.0 else np.zeros(3)), nrm
 
 
-def project(ev: PointEval, y: np.ndarray, d_target: float, eps: float, tol: float):
+def project(ev: PointEval, y: np.ndarray, d_target: float, eps: float, tol: float, max_steps: int = 20):
     """Normal steps y <- y - (d(y) - d*) / |grad d(y)| n(y) (App. C), in cell units, clamped to the domain.
 
     Returns (y, reached) with reached = |d(y) - d*| <= tol h at the returned point."""
     n = ev.mesh.n
     h = ev.mesh.h
     y = y.copy()
-    for _ in range(20):
+    for _ in range(max_steps):
         ph, g = ev.phi_grad(y)
         ph = min(max(ph, -PHI_CLAMP), PHI_CLAMP)
         r = float(physics.distance(ph, eps)) - d_target
@@ -139,7 +145,7 @@ def closest_point(ev: PointEval, sx: np.ndarray, d_target: float, eps: float, to
         accepted = False
         omega = 1.0
         for _ in range(BACKTRACK):
-            y_new, on_new = project(ev, np.clip(y - omega * tp, 0.0, n), d_target, eps, tol)
+            y_new, on_new = project(ev, np.clip(y - omega * tp, 0.0, n), d_target, eps, tol, TRIAL_STEPS)
             dist_new = math.sqrt(float((y_new - sx) @ (y_new - sx)))
             if on_new and dist_new < dist:
                 accepted = True
@@ -148,8 +154,9 @@ def closest_point(ev: PointEval, sx: np.ndarray, d_target: float, eps: float, to
         if not accepted:
             return y, True
         step = math.sqrt(float((y_new - y) @ (y_new - y)))
+        gain = dist - dist_new
         y, dist = y_new, dist_new
-        if step <= tol:
+        if step <= tol or gain <= STALL * dist:
             return y, True
     return y, False
 
@@ -171,7 +178,7 @@ def transport_velocity(mesh: fe.Mesh, phi: np.ndarray, u0: np.ndarray, mdot: np.
         sx = np.array([i, j, k], dtype=float)
         phx = float(phi[node])
         _, g = ev.phi_grad(sx)
-        nx, _ = _unit(g)
+        nx = physics.normal(g, mesh.h)
         mx = float(mdot[node])
         if variant == 1:
             H = physics.heaviside(np.array([phx]), eps)[0]

@@ -63,7 +63,7 @@ SIGNATURES = {
 
 DEFAULT_PARAMS = dict(rho_l=1000.0, rho_g=1.0, mu_l=1e-3, mu_g=1e-5, eps=None, dt=1e-4, c_mass=None, theta=0.5,
                       dtau=None, variant=2, stress=1, corr_zone=0, newton=1, dirichlet_faces=0x3F, cpp_tol=1e-10,
-                      cpp_kmax=50)
+                      cpp_kmax=20)
 
 
 def library_path() -> str:

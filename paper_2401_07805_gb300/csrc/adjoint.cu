@@ -45,8 +45,9 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
               const double* __restrict__ u0, const double* __restrict__ w, const double* __restrict__ wp,
               const double* __restrict__ x, double* gx, double* gu, double* gphi, double* gm) {
     constexpr int Q = P + 1, NQ = Q * Q * Q;
-    __shared__ double sS[Q][Q], sDc[Q][Q];
+    __shared__ double sS[Q][Q], sDc[Q][Q], sN1[Q][2];
     __shared__ double buf[2][CB][12][NQ];
+    __shared__ double q1a[CB][5][2 * Q * Q], q1b[CB][5][4 * Q];  // Q1 test sweeps of the phi / mdot sensitivities
     const int tid = threadIdx.x;
     const int lc = tid / NQ, t = tid % NQ;
     const int64_t cell = (int64_t)blockIdx.x * CB + lc;
@@ -55,6 +56,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
         sS[tid / Q][tid % Q] = bas.S[tid / Q][tid % Q];
         sDc[tid / Q][tid % Q] = bas.Dc[tid / Q][tid % Q];
     }
+    if (tid < 2 * Q) sN1[tid / 2][tid % 2] = bas.N1[tid / 2][tid % 2];
     const int a = t % Q, b = (t / Q) % Q, c = t / (Q * Q);
     const int n = m.n, M = m.M;
     const int64_t m1 = n + 1;
@@ -77,6 +79,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
     }
     __syncthreads();
     if (active)
+#pragma unroll
         for (int f = 0; f < 9; ++f) {
             double s = 0;
 #pragma unroll
@@ -85,6 +88,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
         }
     __syncthreads();
     if (active)
+#pragma unroll
         for (int f = 0; f < 9; ++f) {
             double s = 0;
 #pragma unroll
@@ -93,6 +97,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
         }
     __syncthreads();
     if (active)
+#pragma unroll
         for (int f = 0; f < 9; ++f) {
             double s = 0;
 #pragma unroll
@@ -104,6 +109,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
     double dphi = 0.0, dg[3] = {0, 0, 0}, dm = 0.0;
     if (active) {
         double V[9], Gr[9][3];
+#pragma unroll
         for (int f = 0; f < 9; ++f) {
             V[f] = buf[1][lc][f][t];
             double g0 = 0, g1 = 0, g2 = 0;
@@ -192,7 +198,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
         const double dmu_dH = m.mu_l - m.mu_g;
         dphi = (dL_drho * drho_dH + dL_dmu * dmu_dH) * dH * dd;
         const double gn = sqrt(gp[0] * gp[0] + gp[1] * gp[1] + gp[2] * gp[2]);
-        if (gn > 0.0) {
+        if (gn * m.h > GRAD_TINY) {
             const double pn = dL_dn[0] * nv[0] + dL_dn[1] * nv[1] + dL_dn[2] * nv[2];
             for (int i = 0; i < 3; ++i) dg[i] = (dL_dn[i] - pn * nv[i]) / gn;
         }
@@ -236,33 +242,58 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
             tx3[k] = gxv[k] + (s0 + s1 + s2) * m.inv_h;
             tu3[k] = guv[k] + (u0s + u1s + u2s) * m.inv_h;
         }
-        if (t < 8) {  // Q1 sensitivities of node j = t
-            const int ja = t & 1, jb = (t >> 1) & 1, jc = t >> 2;
-            double sp = 0.0, sm = 0.0;
-            for (int q = 0; q < NQ; ++q) {
-                const int qa = q % Q, qb = (q / Q) % Q, qc = q / (Q * Q);
-                const double tqa = bas.t[qa], tqb = bas.t[qb], tqc = bas.t[qc];
-                const double wx = ja ? tqa : 1.0 - tqa, wy = jb ? tqb : 1.0 - tqb, wz = jc ? tqc : 1.0 - tqc;
-                const double dx = ja ? 1.0 : -1.0, dy = jb ? 1.0 : -1.0, dz = jc ? 1.0 : -1.0;
-                const double N = wx * wy * wz;
-                sp += N * buf[1][lc][6][q] +
-                      m.inv_h * (dx * wy * wz * buf[1][lc][7][q] + wx * dy * wz * buf[1][lc][8][q] +
-                                 wx * wy * dz * buf[1][lc][9][q]);
-                sm += N * buf[1][lc][10][q];
+        // Q1 sensitivities: g_phi[j] = sum_q N1_j dL/dphi + grad N1_j . dL/dgrad phi, g_mdot[j] = sum_q N1_j dL/dmdot,
+        // by three sweeps; field f: 0 dL/dphi, 1..3 dL/dgrad phi (x, y, z), 4 dL/dmdot.  Along direction d the 1D
+        // factor is d N1/dt = (-1, 1) for field 1 + d, N1(t_q) otherwise.  x-sweep: [jx][qy][qz].
+        if (t < 2 * Q * Q) {
+            const int jx = t & 1, qy = (t >> 1) % Q, qz = (t >> 1) / Q;
+            const double dj = jx ? 1.0 : -1.0;
+#pragma unroll
+            for (int f = 0; f < 5; ++f) {
+                double sacc = 0.0;
+#pragma unroll
+                for (int q = 0; q < Q; ++q) sacc += (f == 1 ? dj : sN1[q][jx]) * buf[1][lc][6 + f][q + Q * (qy + Q * qz)];
+                q1a[lc][f][t] = sacc;
             }
-            const int64_t nd = (cx + ja) + m1 * ((cy + jb) + m1 * (cz + jc));
-            if (gphi) atomicAdd(&gphi[nd], sp);
-            if (gm) atomicAdd(&gm[nd], sm);
         }
     }
     __syncthreads();
-    if (active)
+    if (active) {
+#pragma unroll
         for (int k = 0; k < 3; ++k) {
             buf[0][lc][k][t] = tx3[k];
             buf[0][lc][3 + k][t] = tu3[k];
         }
+        if (t < 4 * Q) {  // Q1 y-sweep: [jx][jy][qz]
+            const int jx = t & 1, jy = (t >> 1) & 1, qz = t >> 2;
+            const double dj = jy ? 1.0 : -1.0;
+#pragma unroll
+            for (int f = 0; f < 5; ++f) {
+                double sacc = 0.0;
+#pragma unroll
+                for (int q = 0; q < Q; ++q) sacc += (f == 2 ? dj : sN1[q][jy]) * q1a[lc][f][jx + 2 * (q + Q * qz)];
+                q1b[lc][f][t] = sacc;
+            }
+        }
+    }
     __syncthreads();
+    if (active && t < 8) {  // Q1 z-sweep and scatter of node (jx, jy, jz)
+        const int jx = t & 1, jy = (t >> 1) & 1, jz = t >> 2;
+        const double dj = jz ? 1.0 : -1.0;
+        double r[5];
+#pragma unroll
+        for (int f = 0; f < 5; ++f) {
+            double sacc = 0.0;
+#pragma unroll
+            for (int q = 0; q < Q; ++q) sacc += (f == 3 ? dj : sN1[q][jz]) * q1b[lc][f][jx + 2 * (jy + 2 * q)];
+            r[f] = sacc;
+        }
+        const int64_t nd = (cx + jx) + m1 * ((cy + jy) + m1 * (cz + jz));
+        if (gphi) atomicAdd(&gphi[nd], r[0] + m.inv_h * (r[1] + r[2] + r[3]));
+        if (gm) atomicAdd(&gm[nd], r[4]);
+    }
     if (active)
+#pragma unroll
         for (int f = 0; f < 6; ++f) {
             double s = 0;
 #pragma unroll
@@ -271,6 +302,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
         }
     __syncthreads();
     if (active)
+#pragma unroll
         for (int f = 0; f < 6; ++f) {
             double s = 0;
 #pragma unroll
@@ -279,6 +311,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
         }
     __syncthreads();
     if (active)
+#pragma unroll
         for (int f = 0; f < 6; ++f) {
             double s = 0;
 #pragma unroll

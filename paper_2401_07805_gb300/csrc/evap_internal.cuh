@@ -80,6 +80,8 @@ struct evap_mesh {
     float* ugamma32 = nullptr;
     int32_t* cpp_flags = nullptr;
     unsigned long long* flag_count = nullptr;
+    int32_t* band_list = nullptr;   // Q1 nodes that run the closest-point iteration
+    int32_t* band_count = nullptr;
     // Jacobi diagonal and Krylov workspace (allocated by the first solve)
     double* diag = nullptr;
     float* diag32 = nullptr;

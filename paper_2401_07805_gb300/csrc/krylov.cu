@@ -164,6 +164,8 @@ int launch_diagonal_into(evap_mesh* h, float* acc, double* out, cudaStream_t s) 
 }
 
 // ----------------------------------------------------------------------------------------------- reductions
+// Vector kernels stream FP32 data as float4 and FP64 data as double2 (bases 16-byte aligned: the Krylov basis has a
+// leading dimension padded to 64 entries) with a scalar tail.
 constexpr int RED_THREADS = 256;
 constexpr int RED_BLOCKS = 304;  // 2 per SM
 
@@ -176,6 +178,29 @@ __device__ __forceinline__ void ff_add(FF& s, float v) {
     const float err = (s.hi - (t - bp)) + (v - bp);
     s.hi = t;
     s.lo += err;
+}
+// acc += a * b with the product formed exactly (two-product) in FP32, or an FP64 fma.
+struct Acc {
+    double d = 0.0;
+    FF f = {0.f, 0.f};
+    __device__ __forceinline__ void add(double a, double b) { d = fma(a, b, d); }
+    __device__ __forceinline__ void add(float a, float b) {
+        const float p = a * b;
+        ff_add(f, p);
+        f.lo += fmaf(a, b, -p);
+    }
+    __device__ __forceinline__ double value() const { return d + (double)f.hi + (double)f.lo; }
+};
+
+template <typename T> struct V2;
+template <> struct V2<float> { using t = float4; static constexpr int w = 4; };
+template <> struct V2<double> { using t = double2; static constexpr int w = 2; };
+
+__device__ __forceinline__ void dot_vec(Acc& a, const float4& x, const float4& y) {
+    a.add(x.x, y.x); a.add(x.y, y.y); a.add(x.z, y.z); a.add(x.w, y.w);
+}
+__device__ __forceinline__ void dot_vec(Acc& a, const double2& x, const double2& y) {
+    a.add(x.x, y.x); a.add(x.y, y.y);
 }
 
 __device__ __forceinline__ double block_sum(double v) {
@@ -191,28 +216,22 @@ __device__ __forceinline__ double block_sum(double v) {
     return r;
 }
 
-// partial[i * RED_BLOCKS + block] = sum_k V_i[k] w[k]   for i = blockIdx.y
-__global__ void k_mdot64(const double* __restrict__ V, int64_t ld, const double* __restrict__ w, int64_t N,
-                         double* __restrict__ partial) {
-    const double* v = V + blockIdx.y * ld;
-    double s = 0.0;
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x)
-        s = fma(v[k], w[k], s);
-    s = block_sum(s);
-    if (threadIdx.x == 0) partial[blockIdx.y * RED_BLOCKS + blockIdx.x] = s;
-}
-
-__global__ void k_mdot32(const float* __restrict__ V, int64_t ld, const float* __restrict__ w, int64_t N,
-                         double* __restrict__ partial) {
-    const float* v = V + blockIdx.y * ld;
-    FF acc = {0.f, 0.f};
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
-        const float p = v[k] * w[k];
-        const float e = fmaf(v[k], w[k], -p);  // exact product p + e
-        ff_add(acc, p);
-        acc.lo += e;
-    }
-    double s = block_sum((double)acc.hi + (double)acc.lo);
+// partial[i * RED_BLOCKS + block] = sum_k V_i[k] w[k] for i = blockIdx.y < nv; row nv (if present) = w . w
+template <typename T>
+__global__ void k_mdot(const T* __restrict__ V, int64_t ld, int nv, const T* __restrict__ w, int64_t N,
+                       double* __restrict__ partial) {
+    using VT = typename V2<T>::t;
+    constexpr int W = V2<T>::w;
+    const T* v = blockIdx.y < (unsigned)nv ? V + blockIdx.y * ld : w;
+    Acc acc;
+    const int64_t nvec = N / W;
+    const VT* v4 = reinterpret_cast<const VT*>(v);
+    const VT* w4 = reinterpret_cast<const VT*>(w);
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nvec; k += (int64_t)gridDim.x * blockDim.x)
+        dot_vec(acc, v4[k], w4[k]);
+    for (int64_t k = nvec * W + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x)
+        acc.add(v[k], w[k]);
+    const double s = block_sum(acc.value());
     if (threadIdx.x == 0) partial[blockIdx.y * RED_BLOCKS + blockIdx.x] = s;
 }
 
@@ -224,48 +243,87 @@ __global__ void k_reduce_rows(const double* __restrict__ partial, double* out, i
     if (threadIdx.x == 0) out[blockIdx.x] = accumulate ? out[blockIdx.x] + s : s;
 }
 
-// w -= sum_{i<=j} h[i] V_i ; partial norm^2 of the result
+// w -= sum_{i<nv} h[i] V_i ; partial |w|^2 of the result
 template <typename T>
 __global__ void k_maxpy_norm(const T* __restrict__ V, int64_t ld, const double* __restrict__ hcol, int nv, T* w,
                              int64_t N, double* __restrict__ partial) {
+    using VT = typename V2<T>::t;
+    constexpr int W = V2<T>::w;
     __shared__ T hs[256];
     for (int i = threadIdx.x; i < nv; i += blockDim.x) hs[i] = (T)hcol[i];
     __syncthreads();
-    double s64 = 0.0;
-    FF acc = {0.f, 0.f};
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
+    Acc acc;
+    const int64_t nvec = N / W;
+    VT* w4 = reinterpret_cast<VT*>(w);
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nvec; k += (int64_t)gridDim.x * blockDim.x) {
+        VT a = w4[k];
+        T* ap = reinterpret_cast<T*>(&a);
+        for (int i = 0; i < nv; ++i) {
+            const VT b = reinterpret_cast<const VT*>(V + i * ld)[k];
+            const T* bp = reinterpret_cast<const T*>(&b);
+#pragma unroll
+            for (int e = 0; e < W; ++e) ap[e] -= hs[i] * bp[e];
+        }
+        w4[k] = a;
+        dot_vec(acc, a, a);
+    }
+    for (int64_t k = nvec * W + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
         T v = w[k];
         for (int i = 0; i < nv; ++i) v -= hs[i] * V[i * ld + k];
         w[k] = v;
-        if (sizeof(T) == 8) {
-            s64 = fma((double)v, (double)v, s64);
-        } else {
-            const float fv = (float)v;
-            const float p = fv * fv;
-            ff_add(acc, p);
-            acc.lo += fmaf(fv, fv, -p);
-        }
+        acc.add(v, v);
     }
-    double s = sizeof(T) == 8 ? s64 : (double)acc.hi + (double)acc.lo;
-    s = block_sum(s);
+    const double s = block_sum(acc.value());
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
 template <typename T>
-__global__ void k_scale_to(const T* __restrict__ src, T* __restrict__ dst, const double* __restrict__ nrm2, int64_t N) {
-    const double inv = 1.0 / sqrt(*nrm2);
+__global__ void k_norm2(const T* __restrict__ v, int64_t N, double* __restrict__ partial) {
+    Acc acc;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x)
-        dst[k] = (T)(src[k] * inv);
+        acc.add(v[k], v[k]);
+    const double s = block_sum(acc.value());
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
+// dst = src / sqrt(nrm2)
 template <typename T>
-__global__ void k_mul(const T* __restrict__ a, const T* __restrict__ dinv_src, T* __restrict__ out, int64_t N) {
-    // out = a / diag
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x)
-        out[k] = a[k] / dinv_src[k];
+__global__ void k_scale_to(const T* __restrict__ src, T* __restrict__ dst, const double* __restrict__ nrm2, int64_t N) {
+    using VT = typename V2<T>::t;
+    constexpr int W = V2<T>::w;
+    const T inv = (T)(1.0 / sqrt(*nrm2));
+    const int64_t nvec = N / W;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nvec; k += (int64_t)gridDim.x * blockDim.x) {
+        VT a = reinterpret_cast<const VT*>(src)[k];
+        T* ap = reinterpret_cast<T*>(&a);
+#pragma unroll
+        for (int e = 0; e < W; ++e) ap[e] *= inv;
+        reinterpret_cast<VT*>(dst)[k] = a;
+    }
+    for (int64_t k = nvec * W + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x)
+        dst[k] = src[k] * inv;
 }
 
-// x += diag^{-1} sum_i y[i] V_i
+// out = a / diag (right Jacobi preconditioner)
+template <typename T>
+__global__ void k_precond(const T* __restrict__ a, const T* __restrict__ diag, T* __restrict__ out, int64_t N) {
+    using VT = typename V2<T>::t;
+    constexpr int W = V2<T>::w;
+    const int64_t nvec = N / W;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nvec; k += (int64_t)gridDim.x * blockDim.x) {
+        VT x = reinterpret_cast<const VT*>(a)[k];
+        const VT d = reinterpret_cast<const VT*>(diag)[k];
+        T* xp = reinterpret_cast<T*>(&x);
+        const T* dp = reinterpret_cast<const T*>(&d);
+#pragma unroll
+        for (int e = 0; e < W; ++e) xp[e] /= dp[e];
+        reinterpret_cast<VT*>(out)[k] = x;
+    }
+    for (int64_t k = nvec * W + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x)
+        out[k] = a[k] / diag[k];
+}
+
+// x += diag^{-1} sum_i y[i] V_i   (x may be unaligned caller memory: scalar)
 template <typename T>
 __global__ void k_update(const T* __restrict__ V, int64_t ld, const double* __restrict__ y, int nv,
                          const T* __restrict__ diag, T* x, int64_t N) {
@@ -303,11 +361,11 @@ __global__ void k_refine(double* x, const float* __restrict__ d, const double* _
 struct Ctx {
     evap_mesh* h;
     cudaStream_t s;
-    int64_t N;
-    double* partial;   // [(m+1) * RED_BLOCKS]
-    double* dcol;      // device column [m+2]
-    double* dnorm;     // device scalar
-    double* hcol;      // pinned host [m+3]
+    int64_t N, ld;
+    double* partial;   // [(m+2) * RED_BLOCKS]
+    double* dcol;      // device columns [2 (m+2)]
+    double* dnorm;     // device scalars [4]
+    double* hcol;      // pinned host mirror
 };
 
 template <typename T>
@@ -316,27 +374,7 @@ static int apply_op(Ctx& c, const T* x, T* y) {
 }
 
 template <typename T>
-__global__ void k_norm2(const T* __restrict__ v, int64_t N, double* __restrict__ partial) {
-    double s64 = 0.0;
-    FF acc = {0.f, 0.f};
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
-        if (sizeof(T) == 8) {
-            s64 = fma((double)v[k], (double)v[k], s64);
-        } else {
-            const float fv = (float)v[k];
-            const float p = fv * fv;
-            ff_add(acc, p);
-            acc.lo += fmaf(fv, fv, -p);
-        }
-    }
-    double s = sizeof(T) == 8 ? s64 : (double)acc.hi + (double)acc.lo;
-    s = block_sum(s);
-    if (threadIdx.x == 0) partial[blockIdx.x] = s;
-}
-
-template <typename T>
 static int norm2_dev(Ctx& c, const T* v, double* out) {
-    // ||v||^2 -> out (device)
     k_norm2<T><<<RED_BLOCKS, RED_THREADS, 0, c.s>>>(v, c.N, c.partial);
     EVAP_CHECK_LAUNCH("norm");
     k_reduce_rows<<<1, RED_THREADS, 0, c.s>>>(c.partial, out, 0);
@@ -350,22 +388,45 @@ static int fetch(Ctx& c, const double* dev, int n, double* host) {
     return EVAP_OK;
 }
 
-// GMRES(m) on A x = b with right preconditioner diag^{-1}; x updated in place.  Stops when the preconditioned
-// Arnoldi residual estimate is <= tol_abs or after maxit applications.  Returns applications used via *its.
+// One classical Gram-Schmidt pass of w against V_0..V_{nv-1}: h_out[0..nv) = V^T w (and h_out[nv] = |w|^2 before
+// the pass if with_pre), then w -= V h and |w|^2 after the pass -> c.dnorm[0].
 template <typename T>
-static int gmres(Ctx& c, int m, const T* b, T* x, const T* diag, T* V, T* w, T* z, double tol_abs, int maxit,
-                 int* its, double* res_out) {
+static int cgs_pass(Ctx& c, const T* V, T* w, int nv, double* h_out, bool with_pre) {
+    const int rows = nv + (with_pre ? 1 : 0);
+    k_mdot<T><<<dim3(RED_BLOCKS, rows), RED_THREADS, 0, c.s>>>(V, c.ld, nv, w, c.N, c.partial);
+    EVAP_CHECK_LAUNCH("mdot");
+    k_reduce_rows<<<rows, RED_THREADS, 0, c.s>>>(c.partial, h_out, 0);
+    EVAP_CHECK_LAUNCH("mdot_reduce");
+    k_maxpy_norm<T><<<RED_BLOCKS, RED_THREADS, 0, c.s>>>(V, c.ld, h_out, nv, w, c.N, c.partial);
+    EVAP_CHECK_LAUNCH("maxpy");
+    k_reduce_rows<<<1, RED_THREADS, 0, c.s>>>(c.partial, c.dnorm, 0);
+    EVAP_CHECK_LAUNCH("norm_reduce");
+    return EVAP_OK;
+}
+
+// GMRES(m) on A x = b with right preconditioner diag^{-1}; x updated in place.  x_zero: x is known to be 0 on entry
+// (the first residual is b, no apply).  Classical Gram-Schmidt with a second pass only when the first one removed
+// more than half of |w|^2 (DGKS criterion with eta = 1/sqrt 2).  Stops when the Arnoldi residual estimate is
+// <= tol_abs (then the true residual is recomputed) or after maxit applications.
+template <typename T>
+static int gmres(Ctx& c, int m, const T* b, T* x, bool x_zero, const T* diag, T* V, T* w, T* z, double tol_abs,
+                 int maxit, int* its, double* res_out) {
     const int64_t N = c.N;
     const int G = blocks_for(N, 256);
     std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
     int used = 0, rc;
     double beta = 0.0;
+    bool first = true;
     while (true) {
-        // r = b - A x  into V_0 (unnormalized), beta = |r|
-        if ((rc = apply_op<T>(c, x, w))) return rc;
-        ++used;
-        k_residual<T><<<G, 256, 0, c.s>>>(b, w, V, N);
-        EVAP_CHECK_LAUNCH("residual");
+        if (first && x_zero) {
+            EVAP_CUDA(cudaMemcpyAsync(V, b, N * sizeof(T), cudaMemcpyDeviceToDevice, c.s));
+        } else {
+            if ((rc = apply_op<T>(c, x, w))) return rc;
+            ++used;
+            k_residual<T><<<G, 256, 0, c.s>>>(b, w, V, N);
+            EVAP_CHECK_LAUNCH("residual");
+        }
+        first = false;
         if ((rc = norm2_dev<T>(c, V, c.dnorm))) return rc;
         if ((rc = fetch(c, c.dnorm, 1, c.hcol))) return rc;
         beta = std::sqrt(c.hcol[0]);
@@ -376,40 +437,33 @@ static int gmres(Ctx& c, int m, const T* b, T* x, const T* diag, T* V, T* w, T* 
         std::fill(g.begin(), g.end(), 0.0);
         g[0] = beta;
         int j = 0;
-        bool done = false;
         for (; j < m; ++j) {
-            T* Vj = V + (int64_t)j * N;
-            k_mul<T><<<G, 256, 0, c.s>>>(Vj, diag, z, N);
+            T* Vj = V + (int64_t)j * c.ld;
+            k_precond<T><<<G, 256, 0, c.s>>>(Vj, diag, z, N);
             EVAP_CHECK_LAUNCH("precond");
             if ((rc = apply_op<T>(c, z, w))) return rc;
             ++used;
             const int nv = j + 1;
-            for (int pass = 0; pass < 2; ++pass) {
-                if (sizeof(T) == 8)
-                    k_mdot64<<<dim3(RED_BLOCKS, nv), RED_THREADS, 0, c.s>>>((const double*)V, N, (const double*)w, N,
-                                                                            c.partial);
-                else
-                    k_mdot32<<<dim3(RED_BLOCKS, nv), RED_THREADS, 0, c.s>>>((const float*)V, N, (const float*)w, N,
-                                                                            c.partial);
-                EVAP_CHECK_LAUNCH("mdot");
-                k_reduce_rows<<<nv, RED_THREADS, 0, c.s>>>(c.partial, c.dcol + (pass ? m + 1 : 0), 0);
-                EVAP_CHECK_LAUNCH("mdot_reduce");
-                k_maxpy_norm<T><<<RED_BLOCKS, RED_THREADS, 0, c.s>>>(V, N, c.dcol + (pass ? m + 1 : 0), nv, w, N,
-                                                                     c.partial);
-                EVAP_CHECK_LAUNCH("maxpy");
-            }
-            k_reduce_rows<<<1, RED_THREADS, 0, c.s>>>(c.partial, c.dnorm, 0);
-            EVAP_CHECK_LAUNCH("norm_reduce");
-            // host column: h = h1 + h2, h_{j+1} = |w|
-            EVAP_CUDA(cudaMemcpyAsync(c.hcol, c.dcol, (size_t)(2 * m + 2) * sizeof(double), cudaMemcpyDeviceToHost, c.s));
-            EVAP_CUDA(cudaMemcpyAsync(c.hcol + 2 * m + 2, c.dnorm, sizeof(double), cudaMemcpyDeviceToHost, c.s));
-            EVAP_CUDA(cudaStreamSynchronize(c.s));
             double* col = &H[(size_t)j * (m + 1)];
-            for (int i = 0; i <= j; ++i) col[i] = c.hcol[i] + c.hcol[m + 1 + i];
-            const double hn = std::sqrt(c.hcol[2 * m + 2]);
+            if ((rc = cgs_pass<T>(c, V, w, nv, c.dcol, true))) return rc;
+            EVAP_CUDA(cudaMemcpyAsync(c.hcol, c.dcol, (size_t)(nv + 1) * sizeof(double), cudaMemcpyDeviceToHost, c.s));
+            EVAP_CUDA(cudaMemcpyAsync(c.hcol + m + 2, c.dnorm, sizeof(double), cudaMemcpyDeviceToHost, c.s));
+            EVAP_CUDA(cudaStreamSynchronize(c.s));
+            for (int i = 0; i < nv; ++i) col[i] = c.hcol[i];
+            double after = c.hcol[m + 2];
+            const double before = c.hcol[nv];
+            if (after < 0.5 * before) {  // cancellation: re-orthogonalize once
+                if ((rc = cgs_pass<T>(c, V, w, nv, c.dcol + (m + 2), false))) return rc;
+                EVAP_CUDA(cudaMemcpyAsync(c.hcol, c.dcol + (m + 2), (size_t)nv * sizeof(double), cudaMemcpyDeviceToHost, c.s));
+                EVAP_CUDA(cudaMemcpyAsync(c.hcol + m + 2, c.dnorm, sizeof(double), cudaMemcpyDeviceToHost, c.s));
+                EVAP_CUDA(cudaStreamSynchronize(c.s));
+                for (int i = 0; i < nv; ++i) col[i] += c.hcol[i];
+                after = c.hcol[m + 2];
+            }
+            const double hn = std::sqrt(after);
             col[j + 1] = hn;
-            if (hn > 0.0 && j + 1 < m + 1) {
-                k_scale_to<T><<<G, 256, 0, c.s>>>(w, V + (int64_t)(j + 1) * N, c.dnorm, N);
+            if (hn > 0.0) {
+                k_scale_to<T><<<G, 256, 0, c.s>>>(w, V + (int64_t)(j + 1) * c.ld, c.dnorm, N);
                 EVAP_CHECK_LAUNCH("scale_next");
             }
             for (int i = 0; i < j; ++i) {
@@ -427,22 +481,21 @@ static int gmres(Ctx& c, int m, const T* b, T* x, const T* diag, T* V, T* w, T* 
             const double est = std::fabs(g[j + 1]);
             if (est <= tol_abs || used >= maxit || !(hn > 0.0)) {
                 ++j;
-                done = true;
                 break;
             }
         }
-        // y = R^{-1} g, x += diag^{-1} V y
+        // y = R^{-1} g, x += diag^{-1} V y; the true residual of the new x is checked at the top of the loop
         const int k = j;
         for (int i = k - 1; i >= 0; --i) {
             double s = g[i];
             for (int l = i + 1; l < k; ++l) s -= H[(size_t)l * (m + 1) + i] * y[l];
             y[i] = s / H[(size_t)i * (m + 1) + i];
         }
-        EVAP_CUDA(cudaMemcpyAsync(c.dcol, y.data(), k * sizeof(double), cudaMemcpyHostToDevice, c.s));
-        k_update<T><<<G, 256, 0, c.s>>>(V, N, c.dcol, k, diag, x, N);
+        for (int i = 0; i < k; ++i) c.hcol[i] = y[i];
+        EVAP_CUDA(cudaMemcpyAsync(c.dcol, c.hcol, k * sizeof(double), cudaMemcpyHostToDevice, c.s));
+        k_update<T><<<G, 256, 0, c.s>>>(V, c.ld, c.dcol, k, diag, x, N);
         EVAP_CHECK_LAUNCH("update");
-        EVAP_CUDA(cudaStreamSynchronize(c.s));  // y is a pageable host buffer
-        (void)done;  // the true residual of the updated x is checked at the top of the loop
+        EVAP_CUDA(cudaStreamSynchronize(c.s));  // c.hcol is reused by the next fetch
     }
     *its = used;
     return EVAP_OK;
@@ -453,11 +506,12 @@ int solve_gmres(evap_mesh* h, const double* f, double* x, int mixed, int m, doub
     int rc = launch_diagonal(h, s);
     if (rc) return rc;
     const int64_t N = 3 * h->m.Nu;
-    // workspace, every sub-array starting on a 256-byte boundary:
-    //   FP64: V [(m+1) N], w [N], z [N] doubles;  mixed: V [(m+1) N], w32, z32, r32, d32 [N] floats, r64, Ax [N] doubles
+    const int64_t ld = (N + 63) / 64 * 64;
+    // workspace, every sub-array on a 256-byte boundary:
+    //   FP64: V [(m+1) ld], w [ld], z [ld] doubles;  mixed: V [(m+1) ld], w32, z32, r32, d32 [ld] floats, r64, Ax [ld]
     auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
-    const size_t fV = al((size_t)(m + 1) * N * sizeof(float)), fN = al((size_t)N * sizeof(float));
-    const size_t dV = al((size_t)(m + 1) * N * sizeof(double)), dN = al((size_t)N * sizeof(double));
+    const size_t fV = al((size_t)(m + 1) * ld * sizeof(float)), fN = al((size_t)ld * sizeof(float));
+    const size_t dV = al((size_t)(m + 1) * ld * sizeof(double)), dN = al((size_t)ld * sizeof(double));
     const size_t bytes = mixed ? fV + 4 * fN + 2 * dN : dV + 2 * dN;
     if (h->ws_bytes < bytes) {
         if (h->ws) cudaFree(h->ws);
@@ -481,15 +535,18 @@ int solve_gmres(evap_mesh* h, const double* f, double* x, int mixed, int m, doub
     c.h = h;
     c.s = s;
     c.N = N;
+    c.ld = ld;
     c.partial = h->red;
     c.dcol = h->red + (size_t)(m + 2) * RED_BLOCKS;
     c.dnorm = c.dcol + 2 * (m + 2);
     c.hcol = h->red_host;
     const int G = blocks_for(N, 256);
-    // |f|
+    // |f|, |x0|
     if ((rc = norm2_dev<double>(c, f, c.dnorm))) return rc;
-    if ((rc = fetch(c, c.dnorm, 1, c.hcol))) return rc;
+    if ((rc = norm2_dev<double>(c, x, c.dnorm + 1))) return rc;
+    if ((rc = fetch(c, c.dnorm, 2, c.hcol))) return rc;
     const double fn = std::sqrt(c.hcol[0]);
+    bool x_zero = c.hcol[1] == 0.0;
     if (!(fn > 0.0)) {
         EVAP_CUDA(cudaMemsetAsync(x, 0, N * sizeof(double), s));
         EVAP_CUDA(cudaStreamSynchronize(s));
@@ -505,7 +562,7 @@ int solve_gmres(evap_mesh* h, const double* f, double* x, int mixed, int m, doub
         double* w = (double*)(base + dV);
         double* z = (double*)(base + dV + dN);
         int its = 0;
-        if ((rc = gmres<double>(c, m, f, x, h->diag, V, w, z, rtol * fn, max_iter, &its, &res))) return rc;
+        if ((rc = gmres<double>(c, m, f, x, x_zero, h->diag, V, w, z, rtol * fn, max_iter, &its, &res))) return rc;
         used = its;
     } else {
         float* V = (float*)base;
@@ -517,13 +574,20 @@ int solve_gmres(evap_mesh* h, const double* f, double* x, int mixed, int m, doub
         double* Ax = (double*)(base + fV + 4 * fN + dN);
         const double inner_rtol = 1e-5;
         while (true) {
-            if ((rc = launch_momentum<double>(h, x, Ax, nullptr, s))) return rc;
-            ++used;
-            k_residual<double><<<G, 256, 0, s>>>(f, Ax, r64, N);
-            EVAP_CHECK_LAUNCH("residual64");
-            if ((rc = norm2_dev<double>(c, r64, c.dnorm))) return rc;
-            if ((rc = fetch(c, c.dnorm, 1, c.hcol))) return rc;
-            res = std::sqrt(c.hcol[0]);
+            if (x_zero) {  // r = f
+                EVAP_CUDA(cudaMemcpyAsync(r64, f, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+                res = fn;
+                if ((rc = norm2_dev<double>(c, r64, c.dnorm))) return rc;
+            } else {
+                if ((rc = launch_momentum<double>(h, x, Ax, nullptr, s))) return rc;
+                ++used;
+                k_residual<double><<<G, 256, 0, s>>>(f, Ax, r64, N);
+                EVAP_CHECK_LAUNCH("residual64");
+                if ((rc = norm2_dev<double>(c, r64, c.dnorm))) return rc;
+                if ((rc = fetch(c, c.dnorm, 1, c.hcol))) return rc;
+                res = std::sqrt(c.hcol[0]);
+            }
+            x_zero = false;
             if (res <= rtol * fn || used >= max_iter) break;
             k_scaled_to_float<<<G, 256, 0, s>>>(r64, c.dnorm, r32, N);
             EVAP_CHECK_LAUNCH("to32");
@@ -531,10 +595,10 @@ int solve_gmres(evap_mesh* h, const double* f, double* x, int mixed, int m, doub
             int its = 0;
             double inner_res = 0.0;
             const int budget = std::min(max_iter - used, 4 * m);
-            if ((rc = gmres<float>(c, m, r32, d32, h->diag32, V, w32, z32, inner_rtol, budget, &its, &inner_res)))
+            if ((rc = gmres<float>(c, m, r32, d32, true, h->diag32, V, w32, z32, inner_rtol, budget, &its, &inner_res)))
                 return rc;
             used += its;
-            // keep the FP64 residual norm on the device for the refinement scale
+            // the refinement scale |r| is needed on the device again (the inner solve reused the scalar slot)
             if ((rc = norm2_dev<double>(c, r64, c.dnorm))) return rc;
             k_refine<<<G, 256, 0, s>>>(x, d32, c.dnorm, N);
             EVAP_CHECK_LAUNCH("refine");

@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(128) k_levelset(MeshArgs<T> m, Basis<T> bas, c
                 for (int d = 0; d < 3; ++d) g[d] += dN[j][d] * pv[j];
             const T gn = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
             T nv[3] = {0, 0, 0};
-            if (gn > T(0)) {
+            if (gn * m.h > T(1e-4)) {  // normal taken as 0 where phi varies < 1e-4 across the cell (far field)
                 nv[0] = g[0] / gn; nv[1] = g[1] / gn; nv[2] = g[2] / gn;
             }
             Fv = W * X / m.dtau;

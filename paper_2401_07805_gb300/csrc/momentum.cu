@@ -42,6 +42,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
     constexpr int Q = P + 1, NQ = Q * Q * Q;
     __shared__ T sS[Q][Q], sDc[Q][Q], sN1[Q][2];
     __shared__ T buf[2][CB][6][NQ];
+    __shared__ T q1a[CB][2 * Q * Q], q1b[CB][4 * Q];  // divergence-row test sweeps (Q1 nodes)
     const int tid = threadIdx.x;
     const int lc = tid / NQ, t = tid % NQ;
     const int64_t cell = (int64_t)blockIdx.x * CB + lc;
@@ -171,21 +172,26 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
             }
             wv[k] = F[k] + (s0 + s1 + s2) * m.inv_h;
         }
-        if (yp && t < 8) {  // divergence row: sum_q N1_j(q) W (div x - v_dil) for the 8 Q1 nodes of the cell
-            const int ja = t & 1, jb = (t >> 1) & 1, jc = t >> 2;
+        // divergence row, Q1 test functions: sum_q N1_j(q) r_q by three sweeps; x-sweep here: [jx][qy][qz]
+        if (yp && t < 2 * Q * Q) {
+            const int jx = t & 1, qy = (t >> 1) % Q, qz = (t >> 1) / Q;
             T s = 0;
-            for (int q = 0; q < NQ; ++q) {
-                const int qa = q % Q, qb = (q / Q) % Q, qc = q / (Q * Q);
-                s += sN1[qa][ja] * sN1[qb][jb] * sN1[qc][jc] * buf[1][lc][3][q];
-            }
-            const int64_t m1 = n + 1;
-            atomicAdd(&yp[(cx + ja) + m1 * ((cy + jb) + m1 * (cz + jc))], s);
+#pragma unroll
+            for (int q = 0; q < Q; ++q) s += sN1[q][jx] * buf[1][lc][3][q + Q * (qy + Q * qz)];
+            q1a[lc][t] = s;
         }
     }
     __syncthreads();
     if (active) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) buf[0][lc][k][t] = wv[k];
+        if (yp && t < 4 * Q) {  // y-sweep: [jx][jy][qz]
+            const int jx = t & 1, jy = (t >> 1) & 1, qz = t >> 2;
+            T s = 0;
+#pragma unroll
+            for (int q = 0; q < Q; ++q) s += sN1[q][jy] * q1a[lc][jx + 2 * (q + Q * qz)];
+            q1b[lc][t] = s;
+        }
     }
     __syncthreads();
     // transposed sweeps S^T: z, y, x
@@ -196,6 +202,14 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
 #pragma unroll
             for (int q = 0; q < Q; ++q) s += sS[q][c] * buf[0][lc][k][a + Q * (b + Q * q)];
             buf[1][lc][k][t] = s;
+        }
+        if (yp && t < 8) {  // z-sweep: Q1 node (jx, jy, jz)
+            const int jx = t & 1, jy = (t >> 1) & 1, jz = t >> 2;
+            T s = 0;
+#pragma unroll
+            for (int q = 0; q < Q; ++q) s += sN1[q][jz] * q1b[lc][jx + 2 * (jy + 2 * q)];
+            const int64_t m1 = n + 1;
+            atomicAdd(&yp[(cx + jx) + m1 * ((cy + jy) + m1 * (cz + jz))], s);
         }
     }
     __syncthreads();

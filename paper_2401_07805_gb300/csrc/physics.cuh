@@ -9,6 +9,10 @@ namespace evap {
 constexpr double PHI_BAND = 0x1.cf6f9786df577p-1;      // tanh(3/2), correctly rounded
 constexpr double PHI_GAS_BAND = 0x1.fd77d111a0b00p-1;  // tanh(3), correctly rounded (d = 6 eps)
 constexpr double PI = 3.14159265358979323846;
+// The normal grad phi/|grad phi| (Eq. normal_vector) is taken as 0 where |grad phi| h <= GRAD_TINY: phi varies by
+// less than 1e-4 across the cell (more than ~9 eps from the interface), where the direction is ill-conditioned
+// (rounding noise where phi has saturated to +-1).
+constexpr double GRAD_TINY = 1e-4;
 
 struct Material {
     double H, rho, mu, n[3], delta;
@@ -34,7 +38,7 @@ __device__ __forceinline__ Material material(double phi, double gx, double gy, d
     r.rho = 1.0 / (r.H / m.rho_l + (1.0 - r.H) / m.rho_g);
     r.mu = r.H * m.mu_l + (1.0 - r.H) * m.mu_g;
     const double gn = sqrt(gx * gx + gy * gy + gz * gz);
-    if (gn > 0.0) {
+    if (gn * m.h > GRAD_TINY) {
         r.n[0] = gx / gn; r.n[1] = gy / gn; r.n[2] = gz / gn;
     } else {
         r.n[0] = r.n[1] = r.n[2] = 0.0;

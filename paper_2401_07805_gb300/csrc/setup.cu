@@ -203,15 +203,17 @@ struct PointEval {
 };
 
 constexpr double PHI_CLAMP = 1.0 - 0x1p-40;
-constexpr int CPP_NORMAL_STEPS = 20;
+constexpr int CPP_NORMAL_STEPS = 20;  // projection of the node
+constexpr int CPP_TRIAL_STEPS = 6;    // projection of a trial point of the tangential step
 constexpr int CPP_BACKTRACK = 6;
+constexpr double CPP_STALL = 1e-12;   // an accepted step shortening |y - x| by less than this fraction ends it
 
 __device__ __forceinline__ double clampd(double v, double lo, double hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
 // Normal steps y <- y - (d(y) - d*) / |grad d(y)| n(y) (App. C), returns whether |d(y) - d*| <= tol h.
-__device__ bool cpp_project(const PointEval& e, double y[3], double d_t, double tol) {
+__device__ bool cpp_project(const PointEval& e, double y[3], double d_t, double tol, int max_steps) {
     const double eps = e.m.eps, h = e.m.h, nn = (double)e.m.n;
-    for (int it = 0; it < CPP_NORMAL_STEPS; ++it) {
+    for (int it = 0; it < max_steps; ++it) {
         double ph, g[3];
         e.phi_grad(y, ph, g);
         ph = clampd(ph, -PHI_CLAMP, PHI_CLAMP);
@@ -261,7 +263,7 @@ __device__ __forceinline__ double dist3(const double a[3], const double b[3]) {
 __device__ bool cpp_closest(const PointEval& e, const double x[3], double y[3], double d_t, double tol, int kmax) {
     const double nn = (double)e.m.n;
     y[0] = x[0]; y[1] = x[1]; y[2] = x[2];
-    if (!cpp_project(e, y, d_t, tol)) return false;
+    if (!cpp_project(e, y, d_t, tol, CPP_NORMAL_STEPS)) return false;
     double dist = dist3(y, x);
     for (int k = 0; k < kmax; ++k) {
         double tp[3];
@@ -269,10 +271,11 @@ __device__ bool cpp_closest(const PointEval& e, const double x[3], double y[3], 
         bool accepted = false;
         double omega = 1.0;
         double yn[3];
+        const double dist_prev = dist;
         for (int bt = 0; bt < CPP_BACKTRACK; ++bt) {
 #pragma unroll
             for (int a = 0; a < 3; ++a) yn[a] = clampd(y[a] - omega * tp[a], 0.0, nn);
-            const bool on = cpp_project(e, yn, d_t, tol);
+            const bool on = cpp_project(e, yn, d_t, tol, CPP_TRIAL_STEPS);
             const double dn = dist3(yn, x);
             if (on && dn < dist) {
                 accepted = true;
@@ -283,63 +286,91 @@ __device__ bool cpp_closest(const PointEval& e, const double x[3], double y[3], 
         }
         if (!accepted) return true;
         const double step = dist3(yn, y);
+        const double gain = dist_prev - dist;
         y[0] = yn[0]; y[1] = yn[1]; y[2] = yn[2];
-        if (step <= tol) return true;
+        if (step <= tol || gain <= CPP_STALL * dist) return true;
     }
     return false;
 }
 
-// One thread per Q1 node: variant 1 (Eq. transport_vel_local_continuous), 2 (liquid extension) or 3 (gas).
-__global__ void k_transport_velocity(PointEval e, const double* __restrict__ mdot, double tol, int kmax,
-                                     double* __restrict__ ug, int32_t* __restrict__ flags,
-                                     unsigned long long* flag_count) {
+// Transport velocity at Q1 node `node` from the point y (cell units) whose velocity is extended:
+// u_Gamma = u(y) + mdot/rho_* n(x), n(x) the point-located normal at the node.
+__device__ void transport_finish(const PointEval& e, const double* __restrict__ mdot, int64_t node, const double y[3],
+                                 double rho_t, double* __restrict__ ug) {
     const MeshArgs<double>& m = e.m;
-    const int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (node >= m.Nphi) return;
     const int m1 = m.n + 1;
-    const int i = (int)(node % m1), j = (int)((node / m1) % m1), k = (int)(node / ((int64_t)m1 * m1));
-    const double sx[3] = {(double)i, (double)j, (double)k};
-    const double phx = e.phi[node];
+    const double sx[3] = {(double)(node % m1), (double)((node / m1) % m1), (double)(node / ((int64_t)m1 * m1))};
     double ph, g[3];
     e.phi_grad(sx, ph, g);
     const double nrm = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
     double nx[3] = {0.0, 0.0, 0.0};
-    if (nrm > 0.0) { nx[0] = g[0] / nrm; nx[1] = g[1] / nrm; nx[2] = g[2] / nrm; }
-    const double mx = mdot[node];
+    if (nrm * m.h > GRAD_TINY) { nx[0] = g[0] / nrm; nx[1] = g[1] / nrm; nx[2] = g[2] / nrm; }
     double out[3];
-    int flag = 0;
+    e.velocity(y, out);
+    const double c = mdot[node] / rho_t;
+    ug[node] = out[0] + c * nx[0];
+    ug[m.Nphi + node] = out[1] + c * nx[1];
+    ug[2 * m.Nphi + node] = out[2] + c * nx[2];
+}
+
+__device__ __forceinline__ bool in_projection_band(int variant, double phx) {
+    return variant == 2 ? (-PHI_GAS_BAND < phx) && (phx < PHI_BAND) : (-PHI_BAND < phx) && (phx < PHI_GAS_BAND);
+}
+
+// Pass 1, one thread per Q1 node: variant 1 (Eq. transport_vel_local_continuous) and the nodes of variants 2/3
+// outside the projection band (y = x) are finished here; band nodes are appended to a list for pass 2, so that
+// the iterating nodes fill whole warps.
+__global__ void k_transport_direct(PointEval e, const double* __restrict__ mdot, double* __restrict__ ug,
+                                   int32_t* __restrict__ flags, int32_t* __restrict__ band, int32_t* band_count) {
+    const MeshArgs<double>& m = e.m;
+    const int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (node >= m.Nphi) return;
+    const double phx = e.phi[node];
+    flags[node] = 0;
     if (m.variant == 1) {
+        const int m1 = m.n + 1;
+        const int i = (int)(node % m1), j = (int)((node / m1) % m1), k = (int)(node / ((int64_t)m1 * m1));
+        const double sx[3] = {(double)i, (double)j, (double)k};
+        double ph, g[3];
+        e.phi_grad(sx, ph, g);
+        const double nrm = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+        double nx[3] = {0.0, 0.0, 0.0};
+        if (nrm * m.h > GRAD_TINY) { nx[0] = g[0] / nrm; nx[1] = g[1] / nrm; nx[2] = g[2] / nrm; }
         const Material mat = material(phx, 0.0, 0.0, 0.0, m);
         const int64_t vn = (int64_t)(m.P * i) + (int64_t)m.M * ((int64_t)(m.P * j) + (int64_t)m.M * (m.P * k));
-        const double c = mx / mat.rho;
-        out[0] = e.u[vn] + c * nx[0];
-        out[1] = e.u[m.Nu + vn] + c * nx[1];
-        out[2] = e.u[2 * m.Nu + vn] + c * nx[2];
-    } else {
-        bool band;
-        double d_t, rho_t;
-        if (m.variant == 2) {
-            band = (-PHI_GAS_BAND < phx) && (phx < PHI_BAND);
-            d_t = 3.0 * m.eps;
-            rho_t = m.rho_l;
-        } else {
-            band = (-PHI_BAND < phx) && (phx < PHI_GAS_BAND);
-            d_t = -3.0 * m.eps;
-            rho_t = m.rho_g;
-        }
-        double y[3] = {sx[0], sx[1], sx[2]};
-        if (band) flag = cpp_closest(e, sx, y, d_t, tol, kmax) ? 0 : 1;
-        e.velocity(y, out);
-        const double c = mx / rho_t;
-        out[0] += c * nx[0];
-        out[1] += c * nx[1];
-        out[2] += c * nx[2];
+        const double c = mdot[node] / mat.rho;
+        ug[node] = e.u[vn] + c * nx[0];
+        ug[m.Nphi + node] = e.u[m.Nu + vn] + c * nx[1];
+        ug[2 * m.Nphi + node] = e.u[2 * m.Nu + vn] + c * nx[2];
+        return;
     }
-    ug[node] = out[0];
-    ug[m.Nphi + node] = out[1];
-    ug[2 * m.Nphi + node] = out[2];
-    flags[node] = flag;
-    if (flag) atomicAdd(flag_count, 1ULL);
+    if (in_projection_band(m.variant, phx)) {
+        band[atomicAdd(band_count, 1)] = (int32_t)node;
+        return;
+    }
+    const int m1 = m.n + 1;
+    const double y[3] = {(double)(node % m1), (double)((node / m1) % m1), (double)(node / ((int64_t)m1 * m1))};
+    transport_finish(e, mdot, node, y, m.variant == 2 ? m.rho_l : m.rho_g, ug);
+}
+
+// Pass 2, one thread per band node: closest point on the liquid (variant 2) or gas (variant 3) end of the zone.
+__global__ void k_transport_band(PointEval e, const double* __restrict__ mdot, double tol, int kmax,
+                                 const int32_t* __restrict__ band, const int32_t* __restrict__ band_count,
+                                 double* __restrict__ ug, int32_t* __restrict__ flags, unsigned long long* flag_count) {
+    const MeshArgs<double>& m = e.m;
+    const int count = *band_count;
+    const int m1 = m.n + 1;
+    const double d_t = m.variant == 2 ? 3.0 * m.eps : -3.0 * m.eps;
+    const double rho_t = m.variant == 2 ? m.rho_l : m.rho_g;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < count; b += gridDim.x * blockDim.x) {
+        const int64_t node = band[b];
+        const double sx[3] = {(double)(node % m1), (double)((node / m1) % m1), (double)(node / ((int64_t)m1 * m1))};
+        double y[3];
+        const int flag = cpp_closest(e, sx, y, d_t, tol, kmax) ? 0 : 1;
+        transport_finish(e, mdot, node, y, rho_t, ug);
+        flags[node] = flag;
+        if (flag) atomicAdd(flag_count, 1ULL);
+    }
 }
 
 int launch_transport_velocity(evap_mesh* h, cudaStream_t s) {
@@ -355,9 +386,16 @@ int launch_transport_velocity(evap_mesh* h, cudaStream_t s) {
         e.gl[0] = 0.0; e.gl[1] = 0.5 - r; e.gl[2] = 0.5 + r; e.gl[3] = 1.0;
     }
     EVAP_CUDA(cudaMemsetAsync(h->flag_count, 0, sizeof(unsigned long long), s));
-    k_transport_velocity<<<blocks_for(h->m.Nphi, 128, 1LL << 40), 128, 0, s>>>(
-        e, h->mdot, h->prm.cpp_tol, h->prm.cpp_kmax, h->ugamma, h->cpp_flags, h->flag_count);
-    EVAP_CHECK_LAUNCH("transport_velocity");
+    EVAP_CUDA(cudaMemsetAsync(h->band_count, 0, sizeof(int32_t), s));
+    k_transport_direct<<<blocks_for(h->m.Nphi, 128, 1LL << 40), 128, 0, s>>>(e, h->mdot, h->ugamma, h->cpp_flags,
+                                                                            h->band_list, h->band_count);
+    EVAP_CHECK_LAUNCH("transport_direct");
+    if (h->m.variant != 1) {
+        k_transport_band<<<blocks_for(h->m.Nphi, 64, 152 * 32), 64, 0, s>>>(
+            e, h->mdot, h->prm.cpp_tol, h->prm.cpp_kmax, h->band_list, h->band_count, h->ugamma, h->cpp_flags,
+            h->flag_count);
+        EVAP_CHECK_LAUNCH("transport_band");
+    }
     return launch_to_float(h->ugamma, h->ugamma32, 3 * h->m.Nphi, s);
 }
 
