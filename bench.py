@@ -53,11 +53,14 @@ def algorithmic_counts(n: int, p: int):
     Q = p + 1
     nq = Q ** 3
     sweep = Q * nq                        # multiply-adds of one 1D sweep over a cell
-    # per component: 3 value sweeps + 3 collocation-gradient sweeps (interpolation); same transposed for testing
+    # momentum apply with cached quadrature-point coefficients, per cell and velocity component: 3 value sweeps +
+    # 3 collocation-gradient sweeps (interpolation), 3 transposed gradient sweeps + 3 transposed value sweeps
+    # (testing); ~50 multiply-adds per point for the fluxes; an FMA counts 2 flops
     interp = 6 * sweep
-    flux = 60 * nq                        # F and T at a point (mass, convection, Newton, sym grad, correction)
-    mom_flop = 2 * nc * (3 * interp + 3 * interp + 3 * interp) + 2 * nc * flux
-    adj_flop = 2 * nc * (3 * interp * 3 + 6 * interp) + 2 * nc * 3 * flux
+    mom_flop = 2 * nc * (3 * interp + 3 * interp + 50 * nq)
+    # adjoint: interpolation of x, w, u0 (9 components), testing of g_x and g_u0 (6 components), ~300 multiply-adds
+    # per point for the adjoint fluxes and the material-law derivatives
+    adj_flop = 2 * nc * (9 * interp + 6 * interp + 300 * nq)
     return dict(
         Nu=Nu, Np=Np, ncell=nc,
         mom64_bytes=8 * (3 * Nu * 3 + 2 * Np),          # x, u0, y, phi, mdot

@@ -138,7 +138,7 @@ static int fail(int code, const char* msg) {
 
 static void free_all(evap_mesh* h) {
     void* ptrs[] = {h->phi, h->u, h->mdot, h->u32, h->phi32, h->cell_code, h->table_index, h->table_count,
-                    h->table, h->table32, h->ugamma, h->ugamma32, h->cpp_flags, h->flag_count, h->band_list,
+                    h->table, h->table32, h->qc, h->qc32, h->ugamma, h->ugamma32, h->cpp_flags, h->flag_count, h->band_list,
                     h->band_count, h->diag,
                     h->diag32, h->ws, h->red};
     for (void* p : ptrs)
@@ -253,6 +253,8 @@ int evap_set_fields(evap_handle h, const double* phi, const double* u, const dou
     EVAP_CUDA(cudaMemcpyAsync(h->u, u, 3 * Nu * sizeof(double), cudaMemcpyDeviceToDevice, s));
     EVAP_CUDA(cudaMemcpyAsync(h->mdot, mdot, Np * sizeof(double), cudaMemcpyDeviceToDevice, s));
     int rc = launch_setup_coefficients(h, s);  // clamps phi, FP32 copies, coefficient table
+    if (rc) return rc;
+    rc = launch_qp_coeffs(h, s);  // quadrature-point coefficients of the momentum operator
     if (rc) return rc;
     rc = launch_transport_velocity(h, s);
     if (rc) return rc;

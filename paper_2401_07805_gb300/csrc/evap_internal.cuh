@@ -41,6 +41,7 @@ struct MeshArgs {
 
 enum CellCode : int8_t { CELL_GAS = 0, CELL_LIQUID = 1, CELL_TABLE = 2 };
 constexpr int TAB_K = 6;  // table entries per quadrature point: rho, mu, z n_x, z n_y, z n_z, v_dil
+constexpr int QC_K = 19;  // cached momentum coefficients per quadrature point (see k_qp_coeffs)
 
 template <typename T>
 struct Coeffs {            // quadrature-point coefficients of the momentum operator
@@ -75,6 +76,10 @@ struct evap_mesh {
     int64_t table_cap = 0;           // cells the table can hold
     double* table = nullptr;
     float* table32 = nullptr;
+    // quadrature-point coefficients of the momentum operator, all cells [ncell][QC_K][nq]
+    double* qc = nullptr;
+    float* qc32 = nullptr;
+    int64_t qc_len = 0;
     // transport velocity
     double* ugamma = nullptr;
     float* ugamma32 = nullptr;
@@ -115,6 +120,7 @@ MeshArgs<T> mesh_args(const evap_mesh* h);
 
 // kernels launchers (each returns an evap_status)
 int launch_setup_coefficients(evap_mesh* h, cudaStream_t s);
+int launch_qp_coeffs(evap_mesh* h, cudaStream_t s);
 int launch_transport_velocity(evap_mesh* h, cudaStream_t s);
 template <typename T>
 int launch_momentum(evap_mesh* h, const T* x, T* y, T* yp, cudaStream_t s);

@@ -7,10 +7,13 @@
 //   grads    collocation derivative Dc at the Gauss points along each direction     -> d_b x_c, d_b u0_c
 //   flux     F_c  = W rho (c_m x_c + u0 . grad x_c + newton (grad u0 x)_c)
 //            T_cb = 2 W mu (eps_cb - tr(eps) (z n)_c (z n)_b),  eps = sym grad x          (Eq. modified_viscous_stress)
-//            rho, mu, z n from the FP64 coefficient table of interface cells or the pure-phase constants
+//            with the quadrature-point coefficients (W rho c_m, W rho u0, W rho grad u0, 2 W mu, z n, W, W v_dil)
+//            evaluated once per set_fields in FP64 (k_qp_coeffs) and read per apply: on GB300 the FP64 pipe, not
+//            HBM, bounds this operator, and re-interpolating u0 on every apply cost ~30 % of its FP64 work
 //   test     w_c = F_c + sum_b Dc^T T_cb, then 3 transposed sweeps S^T            -> nodal contributions
 //   scatter  atomic add into y (constrained rows hold y = x, written by the init kernel)
-// Thread layout: one thread per quadrature point, CB cells per block; sweeps go through shared memory.
+// Thread layout: one thread per quadrature point, CB cells per block; sweeps go through shared memory, each thread
+// keeps its rows/columns of the 1D matrices in registers.
 #include "evap_internal.cuh"
 
 namespace evap {
@@ -34,10 +37,114 @@ __global__ void k_momentum_init(int M, int64_t Nu, unsigned faces, const T* __re
         for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < Np; i += stride) yp[i] = T(0);
 }
 
+// Quadrature-point coefficients of the momentum operator, evaluated once per set_fields in FP64 from u0 and the
+// material-law table (layout [cell][QC_K][nq], FP64 and an FP32 copy):
+//   0: W rho c_m   1..3: W rho u0_b   4..12: newton W rho d_d u0_c (index 4 + 3c + d)   13: 2 W mu
+//   14..16: z n_b (correction gate times normal)   17: W   18: W v_dil
+// W = w_qx w_qy w_qz h^3.  One thread per quadrature point, CB cells per block (u0 interpolated by sum factorization).
+template <int P, int CB>
+__global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
+    k_qp_coeffs(MeshArgs<double> m, Basis<double> bas, const int8_t* __restrict__ code,
+                const int32_t* __restrict__ tindex, const double* __restrict__ table, const double* __restrict__ u0,
+                double* __restrict__ qc, float* __restrict__ qc32) {
+    constexpr int Q = P + 1, NQ = Q * Q * Q;
+    __shared__ double sS[Q][Q], sDc[Q][Q];
+    __shared__ double buf[2][CB][3][NQ];
+    const int tid = threadIdx.x;
+    const int lc = tid / NQ, t = tid % NQ;
+    const int64_t cell = (int64_t)blockIdx.x * CB + lc;
+    const bool active = cell < m.ncell;
+    if (tid < Q * Q) {
+        sS[tid / Q][tid % Q] = bas.S[tid / Q][tid % Q];
+        sDc[tid / Q][tid % Q] = bas.Dc[tid / Q][tid % Q];
+    }
+    const int a = t % Q, b = (t / Q) % Q, c = t / (Q * Q);
+    const int n = m.n, M = m.M;
+    if (active) {
+        const int cx = (int)(cell % n), cy = (int)((cell / n) % n), cz = (int)(cell / ((int64_t)n * n));
+        const int64_t gidx = (P * cx + a) + (int64_t)M * ((P * cy + b) + (int64_t)M * (P * cz + c));
+#pragma unroll
+        for (int k = 0; k < 3; ++k) buf[0][lc][k][t] = u0[k * m.Nu + gidx];
+    }
+    __syncthreads();
+    if (active)
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            double s = 0;
+#pragma unroll
+            for (int k = 0; k < Q; ++k) s += sS[a][k] * buf[0][lc][f][k + Q * (b + Q * c)];
+            buf[1][lc][f][t] = s;
+        }
+    __syncthreads();
+    if (active)
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            double s = 0;
+#pragma unroll
+            for (int k = 0; k < Q; ++k) s += sS[b][k] * buf[1][lc][f][a + Q * (k + Q * c)];
+            buf[0][lc][f][t] = s;
+        }
+    __syncthreads();
+    if (active)
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            double s = 0;
+#pragma unroll
+            for (int k = 0; k < Q; ++k) s += sS[c][k] * buf[0][lc][f][a + Q * (b + Q * k)];
+            buf[1][lc][f][t] = s;
+        }
+    __syncthreads();
+    if (!active) return;
+    double U[3], GU[3][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        U[k] = buf[1][lc][k][t];
+        double g0 = 0, g1 = 0, g2 = 0;
+#pragma unroll
+        for (int r = 0; r < Q; ++r) {
+            g0 += sDc[a][r] * buf[1][lc][k][r + Q * (b + Q * c)];
+            g1 += sDc[b][r] * buf[1][lc][k][a + Q * (r + Q * c)];
+            g2 += sDc[c][r] * buf[1][lc][k][a + Q * (b + Q * r)];
+        }
+        GU[k][0] = g0 * m.inv_h; GU[k][1] = g1 * m.inv_h; GU[k][2] = g2 * m.inv_h;
+    }
+    double rho, mu, nz[3], vd;
+    const int8_t cc = code[cell];
+    if (cc == CELL_TABLE) {
+        const double* tb = table + (int64_t)tindex[cell] * TAB_K * NQ + t;
+        rho = tb[0]; mu = tb[NQ]; nz[0] = tb[2 * NQ]; nz[1] = tb[3 * NQ]; nz[2] = tb[4 * NQ]; vd = tb[5 * NQ];
+    } else {
+        const bool liq = cc == CELL_LIQUID;
+        rho = liq ? m.rho_H1 : m.rho_H0;
+        mu = liq ? m.mu_H1 : m.mu_H0;
+        nz[0] = nz[1] = nz[2] = 0.0;
+        vd = 0.0;
+    }
+    const double W = bas.w[a] * bas.w[b] * bas.w[c] * m.vol_w;
+    const double wr = W * rho;
+    double v[QC_K];
+    v[0] = wr * m.c_mass;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) v[1 + k] = wr * U[k];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) v[4 + 3 * k + d] = m.newton ? wr * GU[k][d] : 0.0;
+    v[13] = 2.0 * W * mu;
+    v[14] = nz[0]; v[15] = nz[1]; v[16] = nz[2];
+    v[17] = W;
+    v[18] = W * vd;
+    const int64_t base = cell * QC_K * NQ + t;
+#pragma unroll
+    for (int k = 0; k < QC_K; ++k) {
+        qc[base + (int64_t)k * NQ] = v[k];
+        qc32[base + (int64_t)k * NQ] = (float)v[k];
+    }
+}
+
 template <typename T, int P, int CB>
 __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
-    k_momentum(MeshArgs<T> m, Basis<T> bas, const int8_t* __restrict__ code, const int32_t* __restrict__ tindex,
-               const T* __restrict__ table, const T* __restrict__ u0, const T* __restrict__ x, T* __restrict__ y,
+    k_momentum(MeshArgs<T> m, Basis<T> bas, const T* __restrict__ qc, const T* __restrict__ x, T* __restrict__ y,
                T* __restrict__ yp) {
     constexpr int Q = P + 1, NQ = Q * Q * Q;
     __shared__ T sS[Q][Q], sDc[Q][Q], sN1[Q][2];
@@ -49,7 +156,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
     const bool active = cell < m.ncell;
     if (tid < Q * Q) {
         sS[tid / Q][tid % Q] = bas.S[tid / Q][tid % Q];
-        sDc[tid / Q][tid % Q] = bas.Dc[tid / Q][tid % Q];
+        sDc[tid / Q][tid % Q] = bas.Dc[tid / Q][tid % Q] * m.inv_h;  // physical collocation derivative
     }
     if (tid < 2 * Q) sN1[tid / 2][tid % 2] = bas.N1[tid / 2][tid % 2];
     const int a = t % Q, b = (t / Q) % Q, c = t / (Q * Q);
@@ -65,90 +172,83 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
         gidx = gx + (int64_t)M * (gy + (int64_t)M * gz);
         cons = constrained_node(gx, gy, gz, M, m.faces);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            buf[0][lc][k][t] = cons ? T(0) : x[k * m.Nu + gidx];
-            buf[0][lc][3 + k][t] = u0[k * m.Nu + gidx];
-        }
+        for (int k = 0; k < 3; ++k) buf[0][lc][k][t] = cons ? T(0) : x[k * m.Nu + gidx];
     }
     __syncthreads();
+    // this thread's rows (forward) and columns (transposed) of S and Dc, kept in registers
+    T Sa[Q], Sb[Q], Sc[Q], Da[Q], Db[Q], Dz[Q], Ta[Q], Tb[Q], Tc[Q], Ea[Q], Eb[Q], Ec[Q];
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+        Sa[k] = sS[a][k]; Sb[k] = sS[b][k]; Sc[k] = sS[c][k];
+        Da[k] = sDc[a][k]; Db[k] = sDc[b][k]; Dz[k] = sDc[c][k];
+        Ta[k] = sS[k][a]; Tb[k] = sS[k][b]; Tc[k] = sS[k][c];
+        Ea[k] = sDc[k][a]; Eb[k] = sDc[k][b]; Ec[k] = sDc[k][c];
+    }
     // values at the Gauss points: x-, y-, z-sweeps of S
     if (active) {
 #pragma unroll
-        for (int f = 0; f < 6; ++f) {
+        for (int f = 0; f < 3; ++f) {
             T s = 0;
 #pragma unroll
-            for (int k = 0; k < Q; ++k) s += sS[a][k] * buf[0][lc][f][k + Q * (b + Q * c)];
+            for (int k = 0; k < Q; ++k) s += Sa[k] * buf[0][lc][f][k + Q * (b + Q * c)];
             buf[1][lc][f][t] = s;
         }
     }
     __syncthreads();
     if (active) {
 #pragma unroll
-        for (int f = 0; f < 6; ++f) {
+        for (int f = 0; f < 3; ++f) {
             T s = 0;
 #pragma unroll
-            for (int k = 0; k < Q; ++k) s += sS[b][k] * buf[1][lc][f][a + Q * (k + Q * c)];
+            for (int k = 0; k < Q; ++k) s += Sb[k] * buf[1][lc][f][a + Q * (k + Q * c)];
             buf[0][lc][f][t] = s;
         }
     }
     __syncthreads();
     if (active) {
 #pragma unroll
-        for (int f = 0; f < 6; ++f) {
+        for (int f = 0; f < 3; ++f) {
             T s = 0;
 #pragma unroll
-            for (int k = 0; k < Q; ++k) s += sS[c][k] * buf[0][lc][f][a + Q * (b + Q * k)];
+            for (int k = 0; k < Q; ++k) s += Sc[k] * buf[0][lc][f][a + Q * (b + Q * k)];
             buf[1][lc][f][t] = s;
         }
     }
     __syncthreads();
-    // quadrature-point physics and fluxes
+    // quadrature-point fluxes from the cached coefficients
     T F[3] = {0, 0, 0}, Tf[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, rdiv = 0;
     if (active) {
-        T X[3], U[3], G[3][3], GU[3][3];
+        T X[3], G[3][3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             X[k] = buf[1][lc][k][t];
-            U[k] = buf[1][lc][3 + k][t];
-            T g0 = 0, g1 = 0, g2 = 0, h0 = 0, h1 = 0, h2 = 0;
+            T g0 = 0, g1 = 0, g2 = 0;
 #pragma unroll
             for (int r = 0; r < Q; ++r) {
-                g0 += sDc[a][r] * buf[1][lc][k][r + Q * (b + Q * c)];
-                g1 += sDc[b][r] * buf[1][lc][k][a + Q * (r + Q * c)];
-                g2 += sDc[c][r] * buf[1][lc][k][a + Q * (b + Q * r)];
-                h0 += sDc[a][r] * buf[1][lc][3 + k][r + Q * (b + Q * c)];
-                h1 += sDc[b][r] * buf[1][lc][3 + k][a + Q * (r + Q * c)];
-                h2 += sDc[c][r] * buf[1][lc][3 + k][a + Q * (b + Q * r)];
+                g0 += Da[r] * buf[1][lc][k][r + Q * (b + Q * c)];
+                g1 += Db[r] * buf[1][lc][k][a + Q * (r + Q * c)];
+                g2 += Dz[r] * buf[1][lc][k][a + Q * (b + Q * r)];
             }
-            G[k][0] = g0 * m.inv_h; G[k][1] = g1 * m.inv_h; G[k][2] = g2 * m.inv_h;
-            GU[k][0] = h0 * m.inv_h; GU[k][1] = h1 * m.inv_h; GU[k][2] = h2 * m.inv_h;
+            G[k][0] = g0; G[k][1] = g1; G[k][2] = g2;
         }
-        T rho, mu, nz[3], vd;
-        const int8_t cc = code[cell];
-        if (cc == CELL_TABLE) {
-            const T* tb = table + (int64_t)tindex[cell] * TAB_K * NQ + t;
-            rho = tb[0]; mu = tb[NQ]; nz[0] = tb[2 * NQ]; nz[1] = tb[3 * NQ]; nz[2] = tb[4 * NQ]; vd = tb[5 * NQ];
-        } else {
-            const bool liq = cc == CELL_LIQUID;
-            rho = liq ? m.rho_H1 : m.rho_H0;
-            mu = liq ? m.mu_H1 : m.mu_H0;
-            nz[0] = nz[1] = nz[2] = 0;
-            vd = 0;
-        }
-        const T W = bas.w[a] * bas.w[b] * bas.w[c] * m.vol_w;
-        const T wr = W * rho, wm = 2 * W * mu;
+        const T* q = qc + cell * QC_K * NQ + t;
+        T cf[QC_K];
+#pragma unroll
+        for (int k = 0; k < QC_K; ++k) cf[k] = q[k * NQ];
         const T tr = G[0][0] + G[1][1] + G[2][2];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            T v = m.c_mass * X[k] + U[0] * G[k][0] + U[1] * G[k][1] + U[2] * G[k][2];
-            if (m.newton) v += GU[k][0] * X[0] + GU[k][1] * X[1] + GU[k][2] * X[2];
-            F[k] = wr * v;
+            T v = cf[0] * X[k];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) v += cf[1 + d] * G[k][d] + cf[4 + 3 * k + d] * X[d];
+            F[k] = v;
         }
+        const T sm = cf[13] * tr;
 #pragma unroll
         for (int k = 0; k < 3; ++k)
 #pragma unroll
-            for (int l = 0; l < 3; ++l) Tf[k][l] = wm * (T(0.5) * (G[k][l] + G[l][k]) - tr * nz[k] * nz[l]);
-        rdiv = W * (tr - vd);
+            for (int l = 0; l < 3; ++l) Tf[k][l] = cf[13] * (T(0.5) * (G[k][l] + G[l][k])) - sm * cf[14 + k] * cf[14 + l];
+        rdiv = cf[17] * tr - cf[18];
     }
     __syncthreads();
     if (active) {
@@ -166,11 +266,11 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
 #pragma unroll
             for (int r = 0; r < Q; ++r) {
                 const int i0 = 3 * k + 0, i1 = 3 * k + 1, i2 = 3 * k + 2;
-                s0 += sDc[r][a] * buf[i0 / 6][lc][i0 % 6][r + Q * (b + Q * c)];
-                s1 += sDc[r][b] * buf[i1 / 6][lc][i1 % 6][a + Q * (r + Q * c)];
-                s2 += sDc[r][c] * buf[i2 / 6][lc][i2 % 6][a + Q * (b + Q * r)];
+                s0 += Ea[r] * buf[i0 / 6][lc][i0 % 6][r + Q * (b + Q * c)];
+                s1 += Eb[r] * buf[i1 / 6][lc][i1 % 6][a + Q * (r + Q * c)];
+                s2 += Ec[r] * buf[i2 / 6][lc][i2 % 6][a + Q * (b + Q * r)];
             }
-            wv[k] = F[k] + (s0 + s1 + s2) * m.inv_h;
+            wv[k] = F[k] + (s0 + s1 + s2);
         }
         // divergence row, Q1 test functions: sum_q N1_j(q) r_q by three sweeps; x-sweep here: [jx][qy][qz]
         if (yp && t < 2 * Q * Q) {
@@ -200,7 +300,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
         for (int k = 0; k < 3; ++k) {
             T s = 0;
 #pragma unroll
-            for (int q = 0; q < Q; ++q) s += sS[q][c] * buf[0][lc][k][a + Q * (b + Q * q)];
+            for (int q = 0; q < Q; ++q) s += Tc[q] * buf[0][lc][k][a + Q * (b + Q * q)];
             buf[1][lc][k][t] = s;
         }
         if (yp && t < 8) {  // z-sweep: Q1 node (jx, jy, jz)
@@ -218,7 +318,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
         for (int k = 0; k < 3; ++k) {
             T s = 0;
 #pragma unroll
-            for (int q = 0; q < Q; ++q) s += sS[q][b] * buf[1][lc][k][a + Q * (q + Q * c)];
+            for (int q = 0; q < Q; ++q) s += Tb[q] * buf[1][lc][k][a + Q * (q + Q * c)];
             buf[0][lc][k][t] = s;
         }
     }
@@ -228,29 +328,54 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
         for (int k = 0; k < 3; ++k) {
             T s = 0;
 #pragma unroll
-            for (int q = 0; q < Q; ++q) s += sS[q][a] * buf[0][lc][k][q + Q * (b + Q * c)];
+            for (int q = 0; q < Q; ++q) s += Ta[q] * buf[0][lc][k][q + Q * (b + Q * c)];
             atomicAdd(&y[k * m.Nu + gidx], s);
         }
     }
+}
+
+int launch_qp_coeffs(evap_mesh* h, cudaStream_t s) {
+    const MeshArgs<double>& m = h->m;
+    const int nq = h->b.Q * h->b.Q * h->b.Q;
+    const int64_t need = m.ncell * QC_K * nq;
+    if (h->qc_len < need) {
+        if (h->qc) cudaFree(h->qc);
+        if (h->qc32) cudaFree(h->qc32);
+        h->qc = nullptr;
+        h->qc32 = nullptr;
+        h->qc_len = 0;
+        EVAP_CUDA(cudaMalloc(&h->qc, need * sizeof(double)));
+        EVAP_CUDA(cudaMalloc(&h->qc32, need * sizeof(float)));
+        h->qc_len = need;
+    }
+    if (m.P == 2) {
+        constexpr int CB = 8;
+        k_qp_coeffs<2, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 27, 0, s>>>(m, h->b, h->cell_code, h->table_index,
+                                                                                  h->table, h->u, h->qc, h->qc32);
+    } else {
+        constexpr int CB = 4;
+        k_qp_coeffs<3, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 64, 0, s>>>(m, h->b, h->cell_code, h->table_index,
+                                                                                  h->table, h->u, h->qc, h->qc32);
+    }
+    EVAP_CHECK_LAUNCH("qp_coeffs");
+    return EVAP_OK;
 }
 
 template <typename T>
 int launch_momentum(evap_mesh* h, const T* x, T* y, T* yp, cudaStream_t s) {
     const MeshArgs<T> m = mesh_args<T>(h);
     const Basis<T> b = cast_basis<T>(h->b);
-    const bool dbl = sizeof(T) == 8;
-    const T* table = dbl ? (const T*)h->table : (const T*)h->table32;
-    const T* u0 = dbl ? (const T*)h->u : (const T*)h->u32;
+    const T* qc = sizeof(T) == 8 ? (const T*)h->qc : (const T*)h->qc32;
     k_momentum_init<T><<<blocks_for(3 * m.Nu, 256), 256, 0, s>>>(m.M, m.Nu, m.faces, x, y, yp, m.Nphi);
     EVAP_CHECK_LAUNCH("momentum_init");
     if (m.P == 2) {
         constexpr int CB = 8;
         const int64_t grid = (m.ncell + CB - 1) / CB;
-        k_momentum<T, 2, CB><<<(unsigned)grid, CB * 27, 0, s>>>(m, b, h->cell_code, h->table_index, table, u0, x, y, yp);
+        k_momentum<T, 2, CB><<<(unsigned)grid, CB * 27, 0, s>>>(m, b, qc, x, y, yp);
     } else {
         constexpr int CB = 4;
         const int64_t grid = (m.ncell + CB - 1) / CB;
-        k_momentum<T, 3, CB><<<(unsigned)grid, CB * 64, 0, s>>>(m, b, h->cell_code, h->table_index, table, u0, x, y, yp);
+        k_momentum<T, 3, CB><<<(unsigned)grid, CB * 64, 0, s>>>(m, b, qc, x, y, yp);
     }
     EVAP_CHECK_LAUNCH("momentum");
     return EVAP_OK;
