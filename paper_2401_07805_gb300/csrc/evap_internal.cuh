@@ -76,9 +76,8 @@ struct evap_mesh {
     int64_t table_cap = 0;           // cells the table can hold
     double* table = nullptr;
     float* table32 = nullptr;
-    // quadrature-point coefficients of the momentum operator, all cells [ncell][QC_K][nq]
+    // quadrature-point coefficients of the FP64 momentum operator, all cells [ncell][QC_K][nq]
     double* qc = nullptr;
-    float* qc32 = nullptr;
     int64_t qc_len = 0;
     // transport velocity
     double* ugamma = nullptr;
@@ -121,6 +120,7 @@ MeshArgs<T> mesh_args(const evap_mesh* h);
 // kernels launchers (each returns an evap_status)
 int launch_setup_coefficients(evap_mesh* h, cudaStream_t s);
 int launch_qp_coeffs(evap_mesh* h, cudaStream_t s);
+int launch_momentum32(evap_mesh* h, const float* x, float* y, float* yp, cudaStream_t s);
 int launch_transport_velocity(evap_mesh* h, cudaStream_t s);
 template <typename T>
 int launch_momentum(evap_mesh* h, const T* x, T* y, T* yp, cudaStream_t s);

@@ -243,14 +243,15 @@ __global__ void k_reduce_rows(const double* __restrict__ partial, double* out, i
     if (threadIdx.x == 0) out[blockIdx.x] = accumulate ? out[blockIdx.x] + s : s;
 }
 
-// w -= sum_{i<nv} h[i] V_i ; partial |w|^2 of the result
+// w -= sum_{i<nv} h[i] sc2[i] V_i ; partial |w|^2 of the result.  The basis is stored unnormalized: v_i = sc_i V_i,
+// so projecting out v_i takes the raw dot h[i] = V_i . w times sc_i^2.
 template <typename T>
-__global__ void k_maxpy_norm(const T* __restrict__ V, int64_t ld, const double* __restrict__ hcol, int nv, T* w,
-                             int64_t N, double* __restrict__ partial) {
+__global__ void k_maxpy_norm(const T* __restrict__ V, int64_t ld, const double* __restrict__ hcol,
+                             const double* __restrict__ sc2, int nv, T* w, int64_t N, double* __restrict__ partial) {
     using VT = typename V2<T>::t;
     constexpr int W = V2<T>::w;
     __shared__ T hs[256];
-    for (int i = threadIdx.x; i < nv; i += blockDim.x) hs[i] = (T)hcol[i];
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) hs[i] = (T)(hcol[i] * sc2[i]);
     __syncthreads();
     Acc acc;
     const int64_t nvec = N / W;
@@ -286,27 +287,9 @@ __global__ void k_norm2(const T* __restrict__ v, int64_t N, double* __restrict__
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
-// dst = src / sqrt(nrm2)
+// out = sc a / diag (right Jacobi preconditioner applied to the normalized basis vector sc a)
 template <typename T>
-__global__ void k_scale_to(const T* __restrict__ src, T* __restrict__ dst, const double* __restrict__ nrm2, int64_t N) {
-    using VT = typename V2<T>::t;
-    constexpr int W = V2<T>::w;
-    const T inv = (T)(1.0 / sqrt(*nrm2));
-    const int64_t nvec = N / W;
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nvec; k += (int64_t)gridDim.x * blockDim.x) {
-        VT a = reinterpret_cast<const VT*>(src)[k];
-        T* ap = reinterpret_cast<T*>(&a);
-#pragma unroll
-        for (int e = 0; e < W; ++e) ap[e] *= inv;
-        reinterpret_cast<VT*>(dst)[k] = a;
-    }
-    for (int64_t k = nvec * W + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x)
-        dst[k] = src[k] * inv;
-}
-
-// out = a / diag (right Jacobi preconditioner)
-template <typename T>
-__global__ void k_precond(const T* __restrict__ a, const T* __restrict__ diag, T* __restrict__ out, int64_t N) {
+__global__ void k_precond(const T* __restrict__ a, const T* __restrict__ diag, T* __restrict__ out, int64_t N, T sc) {
     using VT = typename V2<T>::t;
     constexpr int W = V2<T>::w;
     const int64_t nvec = N / W;
@@ -316,11 +299,11 @@ __global__ void k_precond(const T* __restrict__ a, const T* __restrict__ diag, T
         T* xp = reinterpret_cast<T*>(&x);
         const T* dp = reinterpret_cast<const T*>(&d);
 #pragma unroll
-        for (int e = 0; e < W; ++e) xp[e] /= dp[e];
+        for (int e = 0; e < W; ++e) xp[e] = sc * xp[e] / dp[e];
         reinterpret_cast<VT*>(out)[k] = x;
     }
     for (int64_t k = nvec * W + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x)
-        out[k] = a[k] / diag[k];
+        out[k] = sc * a[k] / diag[k];
 }
 
 // x += diag^{-1} sum_i y[i] V_i   (x may be unaligned caller memory: scalar)
@@ -365,7 +348,9 @@ struct Ctx {
     double* partial;   // [(m+2) * RED_BLOCKS]
     double* dcol;      // device columns [2 (m+2)]
     double* dnorm;     // device scalars [4]
+    double* dsc2;      // device squared scales of the unnormalized basis vectors [m+2]
     double* hcol;      // pinned host mirror
+    double* hsc2;      // pinned staging of dsc2 [m+2]
 };
 
 template <typename T>
@@ -388,8 +373,8 @@ static int fetch(Ctx& c, const double* dev, int n, double* host) {
     return EVAP_OK;
 }
 
-// One classical Gram-Schmidt pass of w against V_0..V_{nv-1}: h_out[0..nv) = V^T w (and h_out[nv] = |w|^2 before
-// the pass if with_pre), then w -= V h and |w|^2 after the pass -> c.dnorm[0].
+// One classical Gram-Schmidt pass of w against v_0..v_{nv-1} (v_i = sc_i V_i): h_out[0..nv) = V^T w (raw dots; and
+// h_out[nv] = |w|^2 before the pass if with_pre), then w -= sum sc_i^2 h_i V_i and |w|^2 after the pass -> c.dnorm[0].
 template <typename T>
 static int cgs_pass(Ctx& c, const T* V, T* w, int nv, double* h_out, bool with_pre) {
     const int rows = nv + (with_pre ? 1 : 0);
@@ -397,7 +382,7 @@ static int cgs_pass(Ctx& c, const T* V, T* w, int nv, double* h_out, bool with_p
     EVAP_CHECK_LAUNCH("mdot");
     k_reduce_rows<<<rows, RED_THREADS, 0, c.s>>>(c.partial, h_out, 0);
     EVAP_CHECK_LAUNCH("mdot_reduce");
-    k_maxpy_norm<T><<<RED_BLOCKS, RED_THREADS, 0, c.s>>>(V, c.ld, h_out, nv, w, c.N, c.partial);
+    k_maxpy_norm<T><<<RED_BLOCKS, RED_THREADS, 0, c.s>>>(V, c.ld, h_out, c.dsc2, nv, w, c.N, c.partial);
     EVAP_CHECK_LAUNCH("maxpy");
     k_reduce_rows<<<1, RED_THREADS, 0, c.s>>>(c.partial, c.dnorm, 0);
     EVAP_CHECK_LAUNCH("norm_reduce");
@@ -409,21 +394,35 @@ static int cgs_pass(Ctx& c, const T* V, T* w, int nv, double* h_out, bool with_p
 // more than half of |w|^2 (DGKS criterion with eta = 1/sqrt 2).  Stops when the Arnoldi residual estimate is
 // <= tol_abs (then the true residual is recomputed) or after maxit applications.
 template <typename T>
+static int set_scale(Ctx& c, int i, double sc) {
+    c.hsc2[i] = sc * sc;
+    EVAP_CUDA(cudaMemcpyAsync(c.dsc2 + i, c.hsc2 + i, sizeof(double), cudaMemcpyHostToDevice, c.s));
+    return EVAP_OK;
+}
+
+// GMRES(m) on A x = b with right preconditioner diag^{-1}; x updated in place.  x_zero: x is known to be 0 on entry
+// (the first residual is b, no apply).  The Krylov basis is kept unnormalized (v_i = sc_i V_i): the operator writes
+// A z straight into the next basis slot and the scales enter the Gram-Schmidt coefficients, so no vector pass is
+// spent on normalization.  Classical Gram-Schmidt with a second pass only when the first one removed more than half
+// of |w|^2 (DGKS criterion with eta = 1/sqrt 2).  Stops when the Arnoldi residual estimate is <= tol_abs (then the
+// true residual is recomputed) or after maxit applications.
+template <typename T>
 static int gmres(Ctx& c, int m, const T* b, T* x, bool x_zero, const T* diag, T* V, T* w, T* z, double tol_abs,
                  int maxit, int* its, double* res_out) {
     const int64_t N = c.N;
     const int G = blocks_for(N, 256);
-    std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+    std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m), sc(m + 1);
     int used = 0, rc;
     double beta = 0.0;
     bool first = true;
+    (void)w;
     while (true) {
         if (first && x_zero) {
             EVAP_CUDA(cudaMemcpyAsync(V, b, N * sizeof(T), cudaMemcpyDeviceToDevice, c.s));
         } else {
-            if ((rc = apply_op<T>(c, x, w))) return rc;
+            if ((rc = apply_op<T>(c, x, z))) return rc;
             ++used;
-            k_residual<T><<<G, 256, 0, c.s>>>(b, w, V, N);
+            k_residual<T><<<G, 256, 0, c.s>>>(b, z, V, N);
             EVAP_CHECK_LAUNCH("residual");
         }
         first = false;
@@ -432,39 +431,40 @@ static int gmres(Ctx& c, int m, const T* b, T* x, bool x_zero, const T* diag, T*
         beta = std::sqrt(c.hcol[0]);
         *res_out = beta;
         if (beta <= tol_abs || used >= maxit || !(beta > 0.0)) break;
-        k_scale_to<T><<<G, 256, 0, c.s>>>(V, V, c.dnorm, N);
-        EVAP_CHECK_LAUNCH("scale");
+        sc[0] = 1.0 / beta;
+        if ((rc = set_scale<T>(c, 0, sc[0]))) return rc;
         std::fill(g.begin(), g.end(), 0.0);
         g[0] = beta;
         int j = 0;
         for (; j < m; ++j) {
             T* Vj = V + (int64_t)j * c.ld;
-            k_precond<T><<<G, 256, 0, c.s>>>(Vj, diag, z, N);
+            T* Wn = V + (int64_t)(j + 1) * c.ld;  // A z goes straight into the next basis slot
+            k_precond<T><<<G, 256, 0, c.s>>>(Vj, diag, z, N, (T)sc[j]);
             EVAP_CHECK_LAUNCH("precond");
-            if ((rc = apply_op<T>(c, z, w))) return rc;
+            if ((rc = apply_op<T>(c, z, Wn))) return rc;
             ++used;
             const int nv = j + 1;
             double* col = &H[(size_t)j * (m + 1)];
-            if ((rc = cgs_pass<T>(c, V, w, nv, c.dcol, true))) return rc;
+            if ((rc = cgs_pass<T>(c, V, Wn, nv, c.dcol, true))) return rc;
             EVAP_CUDA(cudaMemcpyAsync(c.hcol, c.dcol, (size_t)(nv + 1) * sizeof(double), cudaMemcpyDeviceToHost, c.s));
             EVAP_CUDA(cudaMemcpyAsync(c.hcol + m + 2, c.dnorm, sizeof(double), cudaMemcpyDeviceToHost, c.s));
             EVAP_CUDA(cudaStreamSynchronize(c.s));
-            for (int i = 0; i < nv; ++i) col[i] = c.hcol[i];
+            for (int i = 0; i < nv; ++i) col[i] = sc[i] * c.hcol[i];
             double after = c.hcol[m + 2];
             const double before = c.hcol[nv];
             if (after < 0.5 * before) {  // cancellation: re-orthogonalize once
-                if ((rc = cgs_pass<T>(c, V, w, nv, c.dcol + (m + 2), false))) return rc;
+                if ((rc = cgs_pass<T>(c, V, Wn, nv, c.dcol + (m + 2), false))) return rc;
                 EVAP_CUDA(cudaMemcpyAsync(c.hcol, c.dcol + (m + 2), (size_t)nv * sizeof(double), cudaMemcpyDeviceToHost, c.s));
                 EVAP_CUDA(cudaMemcpyAsync(c.hcol + m + 2, c.dnorm, sizeof(double), cudaMemcpyDeviceToHost, c.s));
                 EVAP_CUDA(cudaStreamSynchronize(c.s));
-                for (int i = 0; i < nv; ++i) col[i] += c.hcol[i];
+                for (int i = 0; i < nv; ++i) col[i] += sc[i] * c.hcol[i];
                 after = c.hcol[m + 2];
             }
             const double hn = std::sqrt(after);
             col[j + 1] = hn;
             if (hn > 0.0) {
-                k_scale_to<T><<<G, 256, 0, c.s>>>(w, V + (int64_t)(j + 1) * c.ld, c.dnorm, N);
-                EVAP_CHECK_LAUNCH("scale_next");
+                sc[j + 1] = 1.0 / hn;
+                if ((rc = set_scale<T>(c, j + 1, sc[j + 1]))) return rc;
             }
             for (int i = 0; i < j; ++i) {
                 const double t0 = cs[i] * col[i] + sn[i] * col[i + 1];
@@ -484,14 +484,15 @@ static int gmres(Ctx& c, int m, const T* b, T* x, bool x_zero, const T* diag, T*
                 break;
             }
         }
-        // y = R^{-1} g, x += diag^{-1} V y; the true residual of the new x is checked at the top of the loop
+        // y = R^{-1} g, x += diag^{-1} sum_i y_i v_i = diag^{-1} sum_i (y_i sc_i) V_i; the true residual of the new x
+        // is checked at the top of the loop
         const int k = j;
         for (int i = k - 1; i >= 0; --i) {
             double s = g[i];
             for (int l = i + 1; l < k; ++l) s -= H[(size_t)l * (m + 1) + i] * y[l];
             y[i] = s / H[(size_t)i * (m + 1) + i];
         }
-        for (int i = 0; i < k; ++i) c.hcol[i] = y[i];
+        for (int i = 0; i < k; ++i) c.hcol[i] = y[i] * sc[i];
         EVAP_CUDA(cudaMemcpyAsync(c.dcol, c.hcol, k * sizeof(double), cudaMemcpyHostToDevice, c.s));
         k_update<T><<<G, 256, 0, c.s>>>(V, c.ld, c.dcol, k, diag, x, N);
         EVAP_CHECK_LAUNCH("update");
@@ -520,7 +521,7 @@ int solve_gmres(evap_mesh* h, const double* f, double* x, int mixed, int m, doub
         EVAP_CUDA(cudaMalloc(&h->ws, bytes));
         h->ws_bytes = bytes;
     }
-    const size_t red_need = (size_t)(m + 2) * RED_BLOCKS + 2 * (m + 2) + 8;
+    const size_t red_need = (size_t)(m + 2) * RED_BLOCKS + 3 * (m + 2) + 8;
     if (h->red_len < red_need) {
         if (h->red) cudaFree(h->red);
         if (h->red_host) cudaFreeHost(h->red_host);
@@ -539,7 +540,9 @@ int solve_gmres(evap_mesh* h, const double* f, double* x, int mixed, int m, doub
     c.partial = h->red;
     c.dcol = h->red + (size_t)(m + 2) * RED_BLOCKS;
     c.dnorm = c.dcol + 2 * (m + 2);
+    c.dsc2 = c.dnorm + 8;
     c.hcol = h->red_host;
+    c.hsc2 = h->red_host + red_need - (m + 2);
     const int G = blocks_for(N, 256);
     // |f|, |x0|
     if ((rc = norm2_dev<double>(c, f, c.dnorm))) return rc;

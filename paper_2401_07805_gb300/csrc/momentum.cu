@@ -37,8 +37,8 @@ __global__ void k_momentum_init(int M, int64_t Nu, unsigned faces, const T* __re
         for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < Np; i += stride) yp[i] = T(0);
 }
 
-// Quadrature-point coefficients of the momentum operator, evaluated once per set_fields in FP64 from u0 and the
-// material-law table (layout [cell][QC_K][nq], FP64 and an FP32 copy):
+// Quadrature-point coefficients of the FP64 momentum operator, evaluated once per set_fields from u0 and the
+// material-law table (layout [cell][QC_K][nq]):
 //   0: W rho c_m   1..3: W rho u0_b   4..12: newton W rho d_d u0_c (index 4 + 3c + d)   13: 2 W mu
 //   14..16: z n_b (correction gate times normal)   17: W   18: W v_dil
 // W = w_qx w_qy w_qz h^3.  One thread per quadrature point, CB cells per block (u0 interpolated by sum factorization).
@@ -46,7 +46,7 @@ template <int P, int CB>
 __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
     k_qp_coeffs(MeshArgs<double> m, Basis<double> bas, const int8_t* __restrict__ code,
                 const int32_t* __restrict__ tindex, const double* __restrict__ table, const double* __restrict__ u0,
-                double* __restrict__ qc, float* __restrict__ qc32) {
+                double* __restrict__ qc) {
     constexpr int Q = P + 1, NQ = Q * Q * Q;
     __shared__ double sS[Q][Q], sDc[Q][Q];
     __shared__ double buf[2][CB][3][NQ];
@@ -136,10 +136,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
     v[18] = W * vd;
     const int64_t base = cell * QC_K * NQ + t;
 #pragma unroll
-    for (int k = 0; k < QC_K; ++k) {
-        qc[base + (int64_t)k * NQ] = v[k];
-        qc32[base + (int64_t)k * NQ] = (float)v[k];
-    }
+    for (int k = 0; k < QC_K; ++k) qc[base + (int64_t)k * NQ] = v[k];
 }
 
 template <typename T, int P, int CB>
@@ -148,7 +145,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
                T* __restrict__ yp) {
     constexpr int Q = P + 1, NQ = Q * Q * Q;
     __shared__ T sS[Q][Q], sDc[Q][Q], sN1[Q][2];
-    __shared__ T buf[2][CB][6][NQ];
+    __shared__ T buf[2][6][CB][NQ];  // [half][slot][cell][point]: conflict-free lanes
     __shared__ T q1a[CB][2 * Q * Q], q1b[CB][4 * Q];  // divergence-row test sweeps (Q1 nodes)
     const int tid = threadIdx.x;
     const int lc = tid / NQ, t = tid % NQ;
@@ -172,7 +169,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
         gidx = gx + (int64_t)M * (gy + (int64_t)M * gz);
         cons = constrained_node(gx, gy, gz, M, m.faces);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) buf[0][lc][k][t] = cons ? T(0) : x[k * m.Nu + gidx];
+        for (int k = 0; k < 3; ++k) buf[0][k][lc][t] = cons ? T(0) : x[k * m.Nu + gidx];
     }
     __syncthreads();
     // this thread's rows (forward) and columns (transposed) of S and Dc, kept in registers
@@ -190,8 +187,8 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
         for (int f = 0; f < 3; ++f) {
             T s = 0;
 #pragma unroll
-            for (int k = 0; k < Q; ++k) s += Sa[k] * buf[0][lc][f][k + Q * (b + Q * c)];
-            buf[1][lc][f][t] = s;
+            for (int k = 0; k < Q; ++k) s += Sa[k] * buf[0][f][lc][k + Q * (b + Q * c)];
+            buf[1][f][lc][t] = s;
         }
     }
     __syncthreads();
@@ -200,8 +197,8 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
         for (int f = 0; f < 3; ++f) {
             T s = 0;
 #pragma unroll
-            for (int k = 0; k < Q; ++k) s += Sb[k] * buf[1][lc][f][a + Q * (k + Q * c)];
-            buf[0][lc][f][t] = s;
+            for (int k = 0; k < Q; ++k) s += Sb[k] * buf[1][f][lc][a + Q * (k + Q * c)];
+            buf[0][f][lc][t] = s;
         }
     }
     __syncthreads();
@@ -210,8 +207,8 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
         for (int f = 0; f < 3; ++f) {
             T s = 0;
 #pragma unroll
-            for (int k = 0; k < Q; ++k) s += Sc[k] * buf[0][lc][f][a + Q * (b + Q * k)];
-            buf[1][lc][f][t] = s;
+            for (int k = 0; k < Q; ++k) s += Sc[k] * buf[0][f][lc][a + Q * (b + Q * k)];
+            buf[1][f][lc][t] = s;
         }
     }
     __syncthreads();
@@ -221,13 +218,13 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
         T X[3], G[3][3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            X[k] = buf[1][lc][k][t];
+            X[k] = buf[1][k][lc][t];
             T g0 = 0, g1 = 0, g2 = 0;
 #pragma unroll
             for (int r = 0; r < Q; ++r) {
-                g0 += Da[r] * buf[1][lc][k][r + Q * (b + Q * c)];
-                g1 += Db[r] * buf[1][lc][k][a + Q * (r + Q * c)];
-                g2 += Dz[r] * buf[1][lc][k][a + Q * (b + Q * r)];
+                g0 += Da[r] * buf[1][k][lc][r + Q * (b + Q * c)];
+                g1 += Db[r] * buf[1][k][lc][a + Q * (r + Q * c)];
+                g2 += Dz[r] * buf[1][k][lc][a + Q * (b + Q * r)];
             }
             G[k][0] = g0; G[k][1] = g1; G[k][2] = g2;
         }
@@ -253,8 +250,8 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
     __syncthreads();
     if (active) {
 #pragma unroll
-        for (int s = 0; s < 9; ++s) buf[s / 6][lc][s % 6][t] = Tf[s / 3][s % 3];
-        buf[1][lc][3][t] = rdiv;
+        for (int s = 0; s < 9; ++s) buf[s / 6][s % 6][lc][t] = Tf[s / 3][s % 3];
+        buf[1][3][lc][t] = rdiv;
     }
     __syncthreads();
     // test with gradients: w_c = F_c + sum_b Dc^T T_cb
@@ -266,9 +263,9 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
 #pragma unroll
             for (int r = 0; r < Q; ++r) {
                 const int i0 = 3 * k + 0, i1 = 3 * k + 1, i2 = 3 * k + 2;
-                s0 += Ea[r] * buf[i0 / 6][lc][i0 % 6][r + Q * (b + Q * c)];
-                s1 += Eb[r] * buf[i1 / 6][lc][i1 % 6][a + Q * (r + Q * c)];
-                s2 += Ec[r] * buf[i2 / 6][lc][i2 % 6][a + Q * (b + Q * r)];
+                s0 += Ea[r] * buf[i0 / 6][i0 % 6][lc][r + Q * (b + Q * c)];
+                s1 += Eb[r] * buf[i1 / 6][i1 % 6][lc][a + Q * (r + Q * c)];
+                s2 += Ec[r] * buf[i2 / 6][i2 % 6][lc][a + Q * (b + Q * r)];
             }
             wv[k] = F[k] + (s0 + s1 + s2);
         }
@@ -277,14 +274,14 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
             const int jx = t & 1, qy = (t >> 1) % Q, qz = (t >> 1) / Q;
             T s = 0;
 #pragma unroll
-            for (int q = 0; q < Q; ++q) s += sN1[q][jx] * buf[1][lc][3][q + Q * (qy + Q * qz)];
+            for (int q = 0; q < Q; ++q) s += sN1[q][jx] * buf[1][3][lc][q + Q * (qy + Q * qz)];
             q1a[lc][t] = s;
         }
     }
     __syncthreads();
     if (active) {
 #pragma unroll
-        for (int k = 0; k < 3; ++k) buf[0][lc][k][t] = wv[k];
+        for (int k = 0; k < 3; ++k) buf[0][k][lc][t] = wv[k];
         if (yp && t < 4 * Q) {  // y-sweep: [jx][jy][qz]
             const int jx = t & 1, jy = (t >> 1) & 1, qz = t >> 2;
             T s = 0;
@@ -300,8 +297,8 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
         for (int k = 0; k < 3; ++k) {
             T s = 0;
 #pragma unroll
-            for (int q = 0; q < Q; ++q) s += Tc[q] * buf[0][lc][k][a + Q * (b + Q * q)];
-            buf[1][lc][k][t] = s;
+            for (int q = 0; q < Q; ++q) s += Tc[q] * buf[0][k][lc][a + Q * (b + Q * q)];
+            buf[1][k][lc][t] = s;
         }
         if (yp && t < 8) {  // z-sweep: Q1 node (jx, jy, jz)
             const int jx = t & 1, jy = (t >> 1) & 1, jz = t >> 2;
@@ -318,8 +315,8 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
         for (int k = 0; k < 3; ++k) {
             T s = 0;
 #pragma unroll
-            for (int q = 0; q < Q; ++q) s += Tb[q] * buf[1][lc][k][a + Q * (q + Q * c)];
-            buf[0][lc][k][t] = s;
+            for (int q = 0; q < Q; ++q) s += Tb[q] * buf[1][k][lc][a + Q * (q + Q * c)];
+            buf[0][k][lc][t] = s;
         }
     }
     __syncthreads();
@@ -328,7 +325,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
         for (int k = 0; k < 3; ++k) {
             T s = 0;
 #pragma unroll
-            for (int q = 0; q < Q; ++q) s += Ta[q] * buf[0][lc][k][q + Q * (b + Q * c)];
+            for (int q = 0; q < Q; ++q) s += Ta[q] * buf[0][k][lc][q + Q * (b + Q * c)];
             atomicAdd(&y[k * m.Nu + gidx], s);
         }
     }
@@ -340,22 +337,19 @@ int launch_qp_coeffs(evap_mesh* h, cudaStream_t s) {
     const int64_t need = m.ncell * QC_K * nq;
     if (h->qc_len < need) {
         if (h->qc) cudaFree(h->qc);
-        if (h->qc32) cudaFree(h->qc32);
         h->qc = nullptr;
-        h->qc32 = nullptr;
         h->qc_len = 0;
         EVAP_CUDA(cudaMalloc(&h->qc, need * sizeof(double)));
-        EVAP_CUDA(cudaMalloc(&h->qc32, need * sizeof(float)));
         h->qc_len = need;
     }
     if (m.P == 2) {
         constexpr int CB = 8;
         k_qp_coeffs<2, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 27, 0, s>>>(m, h->b, h->cell_code, h->table_index,
-                                                                                  h->table, h->u, h->qc, h->qc32);
+                                                                                  h->table, h->u, h->qc);
     } else {
         constexpr int CB = 4;
         k_qp_coeffs<3, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 64, 0, s>>>(m, h->b, h->cell_code, h->table_index,
-                                                                                  h->table, h->u, h->qc, h->qc32);
+                                                                                  h->table, h->u, h->qc);
     }
     EVAP_CHECK_LAUNCH("qp_coeffs");
     return EVAP_OK;
@@ -365,20 +359,26 @@ template <typename T>
 int launch_momentum(evap_mesh* h, const T* x, T* y, T* yp, cudaStream_t s) {
     const MeshArgs<T> m = mesh_args<T>(h);
     const Basis<T> b = cast_basis<T>(h->b);
-    const T* qc = sizeof(T) == 8 ? (const T*)h->qc : (const T*)h->qc32;
+    const T* qc = (const T*)h->qc;  // FP64 only (the FP32 apply takes the line kernel)
     k_momentum_init<T><<<blocks_for(3 * m.Nu, 256), 256, 0, s>>>(m.M, m.Nu, m.faces, x, y, yp, m.Nphi);
     EVAP_CHECK_LAUNCH("momentum_init");
-    if (m.P == 2) {
-        constexpr int CB = 8;
-        const int64_t grid = (m.ncell + CB - 1) / CB;
-        k_momentum<T, 2, CB><<<(unsigned)grid, CB * 27, 0, s>>>(m, b, qc, x, y, yp);
+    if constexpr (sizeof(T) == 4) {  // FP32: line-oriented kernel with u0 interpolated on the fly (momentum32.cu)
+        (void)b;
+        (void)qc;
+        return launch_momentum32(h, x, y, yp, s);
     } else {
-        constexpr int CB = 4;
-        const int64_t grid = (m.ncell + CB - 1) / CB;
-        k_momentum<T, 3, CB><<<(unsigned)grid, CB * 64, 0, s>>>(m, b, qc, x, y, yp);
+        if (m.P == 2) {
+            constexpr int CB = 8;
+            const int64_t grid = (m.ncell + CB - 1) / CB;
+            k_momentum<T, 2, CB><<<(unsigned)grid, CB * 27, 0, s>>>(m, b, qc, x, y, yp);
+        } else {
+            constexpr int CB = 4;
+            const int64_t grid = (m.ncell + CB - 1) / CB;
+            k_momentum<T, 3, CB><<<(unsigned)grid, CB * 64, 0, s>>>(m, b, qc, x, y, yp);
+        }
+        EVAP_CHECK_LAUNCH("momentum");
+        return EVAP_OK;
     }
-    EVAP_CHECK_LAUNCH("momentum");
-    return EVAP_OK;
 }
 template int launch_momentum<double>(evap_mesh*, const double*, double*, double*, cudaStream_t);
 template int launch_momentum<float>(evap_mesh*, const float*, float*, float*, cudaStream_t);

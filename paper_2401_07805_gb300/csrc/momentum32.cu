@@ -1,0 +1,314 @@
+// FP32 momentum apply (the inner operator of the mixed-precision solve), line-oriented sum factorization.
+//
+// Same operator as k_momentum (velocity block of Eq. weakNavierStokes linearized about u0, App. D, corrected stress
+// of Eq. modified_viscous_stress, divergence row of Eq. continuity), evaluated in FP32 with the material law from the
+// FP32 copy of the FP64 interface table.  The FP32 pipe is 60x faster than FP64 on GB300, so here the limit is the
+// load/store unit, not arithmetic; the kernel is laid out to move few operands through shared memory:
+//   * (P+1)^2 threads per cell, each owning one line of points; the 1D matrices are kernel parameters indexed at
+//     compile time (constant-bank operands, no loads);
+//   * values and gradients by the sweep tree: z-line S and D (registers) -> y-line S, D on S-output and S on
+//     D-output -> x-line S, D, S, S: every sweep reads and writes whole lines (no collocation derivative, whose
+//     cross-line reads would cost Q loads per point and direction);
+//   * u0 is interpolated on the fly (FP32 arithmetic is cheap) instead of streaming cached coefficients;
+//   * the testing runs the tree backwards (x-line S^T/D^T in registers, then y-lines, then z-lines and the atomic
+//     scatter); four block barriers per batch of cells.
+#include "evap_internal.cuh"
+
+namespace evap {
+
+__device__ __forceinline__ bool constrained32(int gx, int gy, int gz, int M, unsigned f) {
+    return ((f & 1u) && gx == 0) || ((f & 2u) && gx == M - 1) || ((f & 4u) && gy == 0) ||
+           ((f & 8u) && gy == M - 1) || ((f & 16u) && gz == 0) || ((f & 32u) && gz == M - 1);
+}
+
+struct Basis32 {
+    float S[MAXQ][MAXQ];   // l_a(t_q)
+    float D[MAXQ][MAXQ];   // l_a'(t_q) / h (physical)
+    float N1[MAXQ][2];     // Q1 values at the Gauss points
+    float W[MAXQ];         // Gauss weights times h (so that W_x W_y W_z = w_q h^3)
+};
+
+template <int P, int CB>
+__global__ void __launch_bounds__(CB*(P + 1) * (P + 1), 2)
+    k_momentum32(MeshArgs<float> m, const __grid_constant__ Basis32 B, const int8_t* __restrict__ code,
+                 const int32_t* __restrict__ tindex, const float* __restrict__ table, const float* __restrict__ u0,
+                 const float* __restrict__ x, float* __restrict__ y, float* __restrict__ yp) {
+    constexpr int Q = P + 1, NQ = Q * Q * Q, L = Q * Q;
+    constexpr int OFF_Z = 6 * NQ, OFF_Y = 12 * NQ, OFF_PD = 18 * NQ, OFF_QD = OFF_PD + 2 * L;
+    constexpr int CS = (OFF_QD + 4 * Q) | 1;  // floats per cell (odd stride against bank conflicts)
+    __shared__ float sm[CB * CS];
+    const int tid = threadIdx.x;
+    const int lc = tid / L, l = tid % L;
+    const int64_t cell = (int64_t)blockIdx.x * CB + lc;
+    const bool active = cell < m.ncell;
+    float* cs = sm + lc * CS;
+    auto at = [](int z, int yy, int xx) { return xx + Q * (yy + Q * z); };
+    const int n = m.n, M = m.M;
+    int cx = 0, cy = 0, cz = 0;
+    if (active) {
+        cx = (int)(cell % n);
+        cy = (int)((cell / n) % n);
+        cz = (int)(cell / ((int64_t)n * n));
+    }
+    // ---------------------------------------------------------------- z-lines: gather, S and D along z
+    {
+        const int i = l % Q, j = l / Q;
+        if (active) {
+#pragma unroll
+            for (int f = 0; f < 6; ++f) {
+                float v[Q];
+#pragma unroll
+                for (int k = 0; k < Q; ++k) {
+                    const int gx = P * cx + i, gy = P * cy + j, gz = P * cz + k;
+                    const int64_t node = gx + (int64_t)M * (gy + (int64_t)M * gz);
+                    const int comp = f % 3;
+                    if (f < 3)
+                        v[k] = constrained32(gx, gy, gz, M, m.faces) ? 0.f : x[comp * m.Nu + node];
+                    else
+                        v[k] = u0[comp * m.Nu + node];
+                }
+#pragma unroll
+                for (int q = 0; q < Q; ++q) {
+                    float a = 0.f, d = 0.f;
+#pragma unroll
+                    for (int k = 0; k < Q; ++k) {
+                        a += B.S[q][k] * v[k];
+                        d += B.D[q][k] * v[k];
+                    }
+                    cs[f * NQ + at(q, j, i)] = a;
+                    cs[OFF_Z + f * NQ + at(q, j, i)] = d;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // ---------------------------------------------------------------- y-lines: S, D on A; S on Az
+    {
+        const int i = l % Q, qz = l / Q;
+        if (active) {
+#pragma unroll
+            for (int f = 0; f < 6; ++f) {
+                float a[Q], az[Q];
+#pragma unroll
+                for (int jj = 0; jj < Q; ++jj) {
+                    a[jj] = cs[f * NQ + at(qz, jj, i)];
+                    az[jj] = cs[OFF_Z + f * NQ + at(qz, jj, i)];
+                }
+#pragma unroll
+                for (int q = 0; q < Q; ++q) {
+                    float bs = 0.f, bd = 0.f, bz = 0.f;
+#pragma unroll
+                    for (int jj = 0; jj < Q; ++jj) {
+                        bs += B.S[q][jj] * a[jj];
+                        bd += B.D[q][jj] * a[jj];
+                        bz += B.S[q][jj] * az[jj];
+                    }
+                    cs[f * NQ + at(qz, q, i)] = bs;
+                    cs[OFF_Y + f * NQ + at(qz, q, i)] = bd;
+                    cs[OFF_Z + f * NQ + at(qz, q, i)] = bz;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // ---------------------------------------------------------------- x-lines: points, fluxes, x-line testing
+    {
+        const int qy = l % Q, qz = l / Q;
+        if (active) {
+            float bs[6][Q], by[6][Q], bz[6][Q];
+#pragma unroll
+            for (int f = 0; f < 6; ++f)
+#pragma unroll
+                for (int ii = 0; ii < Q; ++ii) {
+                    bs[f][ii] = cs[f * NQ + at(qz, qy, ii)];
+                    by[f][ii] = cs[OFF_Y + f * NQ + at(qz, qy, ii)];
+                    bz[f][ii] = cs[OFF_Z + f * NQ + at(qz, qy, ii)];
+                }
+            const int8_t cc = code[cell];
+            const float* tb = cc == CELL_TABLE ? table + (int64_t)tindex[cell] * TAB_K * NQ : nullptr;
+            float Pv[3][Q], Py[3][Q], Pz[3][Q], Pd[2];
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int ii = 0; ii < Q; ++ii) Pv[c][ii] = Py[c][ii] = Pz[c][ii] = 0.f;
+            Pd[0] = Pd[1] = 0.f;
+#pragma unroll
+            for (int qx = 0; qx < Q; ++qx) {
+                float X[3], G[3][3], U[3], GU[3][3];
+#pragma unroll
+                for (int f = 0; f < 6; ++f) {
+                    float v = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+#pragma unroll
+                    for (int ii = 0; ii < Q; ++ii) {
+                        v += B.S[qx][ii] * bs[f][ii];
+                        gx += B.D[qx][ii] * bs[f][ii];
+                        gy += B.S[qx][ii] * by[f][ii];
+                        gz += B.S[qx][ii] * bz[f][ii];
+                    }
+                    if (f < 3) {
+                        X[f] = v; G[f][0] = gx; G[f][1] = gy; G[f][2] = gz;
+                    } else {
+                        U[f - 3] = v; GU[f - 3][0] = gx; GU[f - 3][1] = gy; GU[f - 3][2] = gz;
+                    }
+                }
+                float rho, mu, nz[3], vd;
+                const int qi = at(qz, qy, qx);
+                if (tb) {
+                    rho = tb[qi]; mu = tb[NQ + qi]; nz[0] = tb[2 * NQ + qi]; nz[1] = tb[3 * NQ + qi];
+                    nz[2] = tb[4 * NQ + qi]; vd = tb[5 * NQ + qi];
+                } else {
+                    const bool liq = cc == CELL_LIQUID;
+                    rho = liq ? m.rho_H1 : m.rho_H0;
+                    mu = liq ? m.mu_H1 : m.mu_H0;
+                    nz[0] = nz[1] = nz[2] = 0.f;
+                    vd = 0.f;
+                }
+                const float W = B.W[qx] * B.W[qy] * B.W[qz];
+                const float wr = W * rho, wm = 2.f * W * mu;
+                const float tr = G[0][0] + G[1][1] + G[2][2];
+                float F[3], T[3][3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    float v = m.c_mass * X[c] + U[0] * G[c][0] + U[1] * G[c][1] + U[2] * G[c][2];
+                    if (m.newton) v += GU[c][0] * X[0] + GU[c][1] * X[1] + GU[c][2] * X[2];
+                    F[c] = wr * v;
+                }
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+#pragma unroll
+                    for (int b = 0; b < 3; ++b) T[c][b] = wm * (0.5f * (G[c][b] + G[b][c]) - tr * nz[c] * nz[b]);
+                const float rdiv = W * (tr - vd);
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+#pragma unroll
+                    for (int ii = 0; ii < Q; ++ii) {
+                        Pv[c][ii] += B.S[qx][ii] * F[c] + B.D[qx][ii] * T[c][0];
+                        Py[c][ii] += B.S[qx][ii] * T[c][1];
+                        Pz[c][ii] += B.S[qx][ii] * T[c][2];
+                    }
+                Pd[0] += B.N1[qx][0] * rdiv;
+                Pd[1] += B.N1[qx][1] * rdiv;
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int ii = 0; ii < Q; ++ii) {
+                    cs[c * NQ + at(qz, qy, ii)] = Pv[c][ii];
+                    cs[OFF_Y + c * NQ + at(qz, qy, ii)] = Py[c][ii];
+                    cs[OFF_Z + c * NQ + at(qz, qy, ii)] = Pz[c][ii];
+                }
+            cs[OFF_PD + 0 * L + qy + Q * qz] = Pd[0];
+            cs[OFF_PD + 1 * L + qy + Q * qz] = Pd[1];
+        }
+    }
+    __syncthreads();
+    // ---------------------------------------------------------------- y-lines backwards
+    {
+        const int i = l % Q, qz = l / Q;
+        if (active) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float pv[Q], py[Q], pz[Q];
+#pragma unroll
+                for (int q = 0; q < Q; ++q) {
+                    pv[q] = cs[c * NQ + at(qz, q, i)];
+                    py[q] = cs[OFF_Y + c * NQ + at(qz, q, i)];
+                    pz[q] = cs[OFF_Z + c * NQ + at(qz, q, i)];
+                }
+#pragma unroll
+                for (int jj = 0; jj < Q; ++jj) {
+                    float r = 0.f, rz = 0.f;
+#pragma unroll
+                    for (int q = 0; q < Q; ++q) {
+                        r += B.S[q][jj] * pv[q] + B.D[q][jj] * py[q];
+                        rz += B.S[q][jj] * pz[q];
+                    }
+                    cs[c * NQ + at(qz, jj, i)] = r;
+                    cs[OFF_Z + c * NQ + at(qz, jj, i)] = rz;
+                }
+            }
+            if (yp && l < 2 * Q) {  // divergence row: y-sweep [jx][jy][qz]
+                const int jx = l % 2, qq = l / 2;
+                float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+                for (int q = 0; q < Q; ++q) {
+                    const float v = cs[OFF_PD + jx * L + q + Q * qq];
+                    s0 += B.N1[q][0] * v;
+                    s1 += B.N1[q][1] * v;
+                }
+                cs[OFF_QD + jx + 2 * (0 + 2 * qq)] = s0;
+                cs[OFF_QD + jx + 2 * (1 + 2 * qq)] = s1;
+            }
+        }
+    }
+    __syncthreads();
+    // ---------------------------------------------------------------- z-lines backwards and scatter
+    {
+        const int i = l % Q, j = l / Q;
+        if (active) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float r[Q], rz[Q];
+#pragma unroll
+                for (int q = 0; q < Q; ++q) {
+                    r[q] = cs[c * NQ + at(q, j, i)];
+                    rz[q] = cs[OFF_Z + c * NQ + at(q, j, i)];
+                }
+#pragma unroll
+                for (int k = 0; k < Q; ++k) {
+                    float o = 0.f;
+#pragma unroll
+                    for (int q = 0; q < Q; ++q) o += B.S[q][k] * r[q] + B.D[q][k] * rz[q];
+                    const int gx = P * cx + i, gy = P * cy + j, gz = P * cz + k;
+                    if (!constrained32(gx, gy, gz, M, m.faces))
+                        atomicAdd(&y[c * m.Nu + gx + (int64_t)M * (gy + (int64_t)M * gz)], o);
+                }
+            }
+            if (yp && l < 4) {  // divergence row: z-sweep, Q1 node (jx, jy, jz)
+                const int jx = l % 2, jy = l / 2;
+                float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+                for (int q = 0; q < Q; ++q) {
+                    const float v = cs[OFF_QD + jx + 2 * (jy + 2 * q)];
+                    s0 += B.N1[q][0] * v;
+                    s1 += B.N1[q][1] * v;
+                }
+                const int64_t m1 = n + 1;
+                atomicAdd(&yp[(cx + jx) + m1 * ((cy + jy) + m1 * (cz + 0))], s0);
+                atomicAdd(&yp[(cx + jx) + m1 * ((cy + jy) + m1 * (cz + 1))], s1);
+            }
+        }
+    }
+}
+
+template <int P>
+static void launch32(const evap_mesh* h, const MeshArgs<float>& m, const Basis32& b, const float* x, float* y,
+                     float* yp, cudaStream_t s) {
+    constexpr int L = (P + 1) * (P + 1);
+    constexpr int CB = P == 2 ? 32 : 16;  // 288 / 256 threads
+    k_momentum32<P, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * L, 0, s>>>(m, b, h->cell_code, h->table_index,
+                                                                               h->table32, h->u32, x, y, yp);
+}
+
+int launch_momentum32(evap_mesh* h, const float* x, float* y, float* yp, cudaStream_t s) {
+    const MeshArgs<float> m = mesh_args<float>(h);
+    Basis32 b;
+    const Basis<double>& d = h->b;
+    for (int q = 0; q < MAXQ; ++q) {
+        for (int a = 0; a < MAXQ; ++a) {
+            b.S[q][a] = (float)d.S[q][a];
+            b.D[q][a] = (float)(d.D[q][a] * h->m.inv_h);
+        }
+        b.N1[q][0] = (float)d.N1[q][0];
+        b.N1[q][1] = (float)d.N1[q][1];
+        b.W[q] = (float)(d.w[q] * h->m.h);
+    }
+    if (m.P == 2)
+        launch32<2>(h, m, b, x, y, yp, s);
+    else
+        launch32<3>(h, m, b, x, y, yp, s);
+    EVAP_CHECK_LAUNCH("momentum32");
+    return EVAP_OK;
+}
+
+}  // namespace evap
