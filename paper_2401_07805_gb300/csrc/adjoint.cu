@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
     const bool active = cell < m.ncell;
     if (tid < Q * Q) {
         sS[tid / Q][tid % Q] = bas.S[tid / Q][tid % Q];
-        sDc[tid / Q][tid % Q] = bas.Dc[tid / Q][tid % Q];
+        sDc[tid / Q][tid % Q] = bas.Dc[tid / Q][tid % Q] * m.inv_h;  // physical collocation derivative
     }
     if (tid < 2 * Q) sN1[tid / 2][tid % 2] = bas.N1[tid / 2][tid % 2];
     const int a = t % Q, b = (t / Q) % Q, c = t / (Q * Q);
@@ -119,42 +119,25 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
                 g1 += sDc[b][r] * buf[1][lc][f][a + Q * (r + Q * c)];
                 g2 += sDc[c][r] * buf[1][lc][f][a + Q * (b + Q * r)];
             }
-            Gr[f][0] = g0 * m.inv_h; Gr[f][1] = g1 * m.inv_h; Gr[f][2] = g2 * m.inv_h;
+            Gr[f][0] = g0; Gr[f][1] = g1; Gr[f][2] = g2;  // sDc holds the physical derivative (1/h folded in)
         }
-        // Q1 fields at the point
+        // Q1 fields at the point: trilinear weights of the 8 cell nodes
         const double tx = bas.t[a], ty = bas.t[b], tz = bas.t[c];
-        double ph = 0, gp[3] = {0, 0, 0}, md = 0, pi = 0;
+        double wq[8];
+        double ph = 0, pi = 0;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const int ja = j & 1, jb = (j >> 1) & 1, jc = j >> 2;
             const int64_t nd = (cx + ja) + m1 * ((cy + jb) + m1 * (cz + jc));
-            const double wx = ja ? tx : 1.0 - tx, wy = jb ? ty : 1.0 - ty, wz = jc ? tz : 1.0 - tz;
-            const double dx = ja ? 1.0 : -1.0, dy = jb ? 1.0 : -1.0, dz = jc ? 1.0 : -1.0;
-            const double pv = phi[nd];
-            ph += wx * wy * wz * pv;
-            gp[0] += dx * wy * wz * pv;
-            gp[1] += wx * dy * wz * pv;
-            gp[2] += wx * wy * dz * pv;
-            md += wx * wy * wz * mdot[nd];
-            if (wp) pi += wx * wy * wz * wp[nd];
+            wq[j] = (ja ? tx : 1.0 - tx) * (jb ? ty : 1.0 - ty) * (jc ? tz : 1.0 - tz);
+            ph += wq[j] * phi[nd];
+            if (wp) pi += wq[j] * wp[nd];
         }
-        gp[0] *= m.inv_h; gp[1] *= m.inv_h; gp[2] *= m.inv_h;
-        const Material mat = material(ph, gp[0], gp[1], gp[2], m);
-        const double zg = correction_on(m, mat.zone) ? 1.0 : 0.0;
-        double dH = 0.0, d2H = 0.0, dd = 0.0, d2d = 0.0;
-        if (mat.zone) {
-            const double d = m.eps * log((1.0 + ph) / (1.0 - ph));
-            double sn, cs;
-            sincos(PI * d / (3.0 * m.eps), &sn, &cs);
-            dH = (1.0 + cs) / (6.0 * m.eps);
-            d2H = -PI * sn / (18.0 * m.eps * m.eps);
-            const double om = 1.0 - ph * ph;
-            dd = 2.0 * m.eps / om;
-            d2d = 4.0 * m.eps * ph / (om * om);
-        }
+        const bool zone = fabs(ph) < PHI_BAND;
+        // the phi / mdot sensitivities and the normal are needed only in the interface zone (or with the correction
+        // applied everywhere); elsewhere H is 0 or 1, its derivatives vanish and rho, mu are the phase constants
+        const bool full = zone || (m.stress != 0 && m.corr_zone != 0);
         const double W = bas.w[a] * bas.w[b] * bas.w[c] * m.vol_w;
-        const double rho = mat.rho, mu = mat.mu;
-        const double* nv = mat.n;
         const double* X = &V[0];
         const double* Om = &V[3];
         const double* U = &V[6];
@@ -162,52 +145,101 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
         double (*OmG)[3] = &Gr[3];
         double (*GU)[3] = &Gr[6];
         const double nw = m.newton ? 1.0 : 0.0;
-        const double tr = G[0][0] + G[1][1] + G[2][2];
-        // n . OmG n
-        double nOn = 0.0;
-        for (int i = 0; i < 3; ++i)
-            for (int j = 0; j < 3; ++j) nOn += nv[i] * OmG[i][j] * nv[j];
+        double rho, mu;
+        Material mat;
+        double gp[3] = {0, 0, 0}, md = 0.0;
+        if (full) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int ja = j & 1, jb = (j >> 1) & 1, jc = j >> 2;
+                const int64_t nd = (cx + ja) + m1 * ((cy + jb) + m1 * (cz + jc));
+                const double pv = phi[nd];
+                gp[0] += (ja ? 1.0 : -1.0) * (jb ? ty : 1.0 - ty) * (jc ? tz : 1.0 - tz) * pv;
+                gp[1] += (ja ? tx : 1.0 - tx) * (jb ? 1.0 : -1.0) * (jc ? tz : 1.0 - tz) * pv;
+                gp[2] += (ja ? tx : 1.0 - tx) * (jb ? ty : 1.0 - ty) * (jc ? 1.0 : -1.0) * pv;
+                md += wq[j] * mdot[nd];
+            }
+            gp[0] *= m.inv_h; gp[1] *= m.inv_h; gp[2] *= m.inv_h;
+            mat = material(ph, gp[0], gp[1], gp[2], m);
+            rho = mat.rho;
+            mu = mat.mu;
+        } else {
+            const bool liq = ph >= PHI_BAND;
+            rho = liq ? m.rho_H1 : m.rho_H0;
+            mu = liq ? m.mu_H1 : m.mu_H0;
+        }
+        const double wr = W * rho, wm = 2.0 * W * mu;
+        // value / gradient sensitivities of the velocity block and of B^T w_p (the correction term added below)
+#pragma unroll
         for (int d = 0; d < 3; ++d) {
-            gxv[d] = W * rho * (m.c_mass * Om[d] + nw * (Om[0] * GU[0][d] + Om[1] * GU[1][d] + Om[2] * GU[2][d]));
-            guv[d] = W * rho * (Om[0] * G[0][d] + Om[1] * G[1][d] + Om[2] * G[2][d]);
+            gxv[d] = wr * (m.c_mass * Om[d] + nw * (Om[0] * GU[0][d] + Om[1] * GU[1][d] + Om[2] * GU[2][d]));
+            guv[d] = wr * (Om[0] * G[0][d] + Om[1] * G[1][d] + Om[2] * G[2][d]);
+#pragma unroll
             for (int e = 0; e < 3; ++e) {
-                gxg[d][e] = W * rho * Om[d] * U[e] +
-                            2.0 * W * mu * (0.5 * (OmG[d][e] + OmG[e][d]) - (d == e ? zg * nOn : 0.0)) +
-                            (d == e ? W * pi : 0.0);
-                gug[d][e] = nw * W * rho * Om[d] * X[e];
+                gxg[d][e] = wr * Om[d] * U[e] + wm * 0.5 * (OmG[d][e] + OmG[e][d]) + (d == e ? W * pi : 0.0);
+                gug[d][e] = nw * wr * Om[d] * X[e];
             }
         }
-        // coefficient sensitivities
-        double dL_drho = 0.0, dL_dmu = 0.0, dL_dn[3];
-        for (int k = 0; k < 3; ++k) {
-            const double Fk = m.c_mass * X[k] + U[0] * G[k][0] + U[1] * G[k][1] + U[2] * G[k][2] +
-                              nw * (GU[k][0] * X[0] + GU[k][1] * X[1] + GU[k][2] * X[2]);
-            dL_drho += Om[k] * Fk;
-            for (int l = 0; l < 3; ++l)
-                dL_dmu += OmG[k][l] * (0.5 * (G[k][l] + G[l][k]) - zg * tr * nv[k] * nv[l]);
-        }
-        dL_drho *= W;
-        dL_dmu *= 2.0 * W;
-        for (int i = 0; i < 3; ++i) {
-            double s = 0.0;
-            for (int j = 0; j < 3; ++j) s += (OmG[i][j] + OmG[j][i]) * nv[j];
-            dL_dn[i] = -2.0 * W * mu * zg * tr * s;
-        }
-        const double krho = 1.0 / m.rho_l - 1.0 / m.rho_g;
-        const double drho_dH = -rho * rho * krho;
-        const double dmu_dH = m.mu_l - m.mu_g;
-        dphi = (dL_drho * drho_dH + dL_dmu * dmu_dH) * dH * dd;
-        const double gn = sqrt(gp[0] * gp[0] + gp[1] * gp[1] + gp[2] * gp[2]);
-        if (gn * m.h > GRAD_TINY) {
-            const double pn = dL_dn[0] * nv[0] + dL_dn[1] * nv[1] + dL_dn[2] * nv[2];
-            for (int i = 0; i < 3; ++i) dg[i] = (dL_dn[i] - pn * nv[i]) / gn;
-        }
-        if (wp) {
-            const double dL_dv = -W * pi;
-            const double delta = mat.zone ? dH * dd * gn : 0.0;
-            dm = dL_dv * krho * delta;
-            dphi += dL_dv * md * krho * (d2H * dd * dd + dH * d2d) * gn;
-            for (int i = 0; i < 3; ++i) dg[i] += dL_dv * md * krho * dH * dd * nv[i];
+        if (full) {
+            const double zg = correction_on(m, mat.zone) ? 1.0 : 0.0;
+            const double* nv = mat.n;
+            const double tr = G[0][0] + G[1][1] + G[2][2];
+            double nOn = 0.0;
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) nOn += nv[i] * OmG[i][j] * nv[j];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) gxg[d][d] -= wm * zg * nOn;
+            double dH = 0.0, d2H = 0.0, dd = 0.0, d2d = 0.0;
+            if (mat.zone) {
+                const double dist = m.eps * log((1.0 + ph) / (1.0 - ph));
+                double sn, cs;
+                sincos(PI * dist / (3.0 * m.eps), &sn, &cs);
+                dH = (1.0 + cs) / (6.0 * m.eps);
+                d2H = -PI * sn / (18.0 * m.eps * m.eps);
+                const double om = 1.0 - ph * ph;
+                dd = 2.0 * m.eps / om;
+                d2d = 4.0 * m.eps * ph / (om * om);
+            }
+            // coefficient sensitivities
+            double dL_drho = 0.0, dL_dmu = 0.0, dL_dn[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const double Fk = m.c_mass * X[k] + U[0] * G[k][0] + U[1] * G[k][1] + U[2] * G[k][2] +
+                                  nw * (GU[k][0] * X[0] + GU[k][1] * X[1] + GU[k][2] * X[2]);
+                dL_drho += Om[k] * Fk;
+#pragma unroll
+                for (int l = 0; l < 3; ++l)
+                    dL_dmu += OmG[k][l] * (0.5 * (G[k][l] + G[l][k]) - zg * tr * nv[k] * nv[l]);
+            }
+            dL_drho *= W;
+            dL_dmu *= 2.0 * W;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                double sacc = 0.0;
+#pragma unroll
+                for (int j = 0; j < 3; ++j) sacc += (OmG[i][j] + OmG[j][i]) * nv[j];
+                dL_dn[i] = -wm * zg * tr * sacc;
+            }
+            const double krho = 1.0 / m.rho_l - 1.0 / m.rho_g;
+            const double drho_dH = -rho * rho * krho;
+            const double dmu_dH = m.mu_l - m.mu_g;
+            dphi = (dL_drho * drho_dH + dL_dmu * dmu_dH) * dH * dd;
+            const double gn = sqrt(gp[0] * gp[0] + gp[1] * gp[1] + gp[2] * gp[2]);
+            if (gn * m.h > GRAD_TINY) {
+                const double pn = dL_dn[0] * nv[0] + dL_dn[1] * nv[1] + dL_dn[2] * nv[2];
+#pragma unroll
+                for (int i = 0; i < 3; ++i) dg[i] = (dL_dn[i] - pn * nv[i]) / gn;
+            }
+            if (wp) {
+                const double dL_dv = -W * pi;
+                const double delta = mat.zone ? dH * dd * gn : 0.0;
+                dm = dL_dv * krho * delta;
+                dphi += dL_dv * md * krho * (d2H * dd * dd + dH * d2d) * gn;
+#pragma unroll
+                for (int i = 0; i < 3; ++i) dg[i] += dL_dv * md * krho * dH * dd * nv[i];
+            }
         }
     }
     __syncthreads();
@@ -239,8 +271,8 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
                 u1s += sDc[r][b] * (j1 < 12 ? buf[0][lc][j1][p1] : buf[1][lc][j1 - 12][p1]);
                 u2s += sDc[r][c] * (j2 < 12 ? buf[0][lc][j2][p2] : buf[1][lc][j2 - 12][p2]);
             }
-            tx3[k] = gxv[k] + (s0 + s1 + s2) * m.inv_h;
-            tu3[k] = guv[k] + (u0s + u1s + u2s) * m.inv_h;
+            tx3[k] = gxv[k] + (s0 + s1 + s2);
+            tu3[k] = guv[k] + (u0s + u1s + u2s);
         }
         // Q1 sensitivities: g_phi[j] = sum_q N1_j dL/dphi + grad N1_j . dL/dgrad phi, g_mdot[j] = sum_q N1_j dL/dmdot,
         // by three sweeps; field f: 0 dL/dphi, 1..3 dL/dgrad phi (x, y, z), 4 dL/dmdot.  Along direction d the 1D
