@@ -43,6 +43,9 @@ def load_peaks():
 
 # Nominal FP64 rate of GB300 (profiling recipe table: 1.25 TFLOP/s); the FP64 FMA probe measured 1.19 TFLOP/s.
 FP64_PEAK_TFLOPS = 1.25
+# FP32 peak from the unit counts and clocks of the profiling recipe: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x
+# 2.07 GHz maximum SM clock = 80.5 TFLOP/s (the FMA probe measured 73 TFLOP/s at the clocks it saw).
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
 def algorithmic_counts(n: int, p: int):
@@ -61,11 +64,19 @@ def algorithmic_counts(n: int, p: int):
     # adjoint: interpolation of x, w, u0 (9 components), testing of g_x and g_u0 (6 components), ~300 multiply-adds
     # per point for the adjoint fluxes and the material-law derivatives
     adj_flop = 2 * nc * (9 * interp + 6 * interp + 300 * nq)
+    # FP32 line kernel per cell (Q^2 line threads): z-sweeps (S, D on 6 fields), y-sweeps (S, D on S-output, S on
+    # D-output), x-lines (4 outputs per point and field + ~45 multiply-adds of fluxes per point + x-line testing),
+    # backward y- and z-sweeps of 3 components
+    L2 = Q * Q
+    mom32_fma = L2 * (6 * Q * 2 * Q) + L2 * (6 * Q * 3 * Q) + L2 * Q * (6 * 4 * Q + 45 + 3 * 3 * Q) \
+        + L2 * (3 * Q * 3 * Q) + L2 * (3 * Q * 2 * Q)
+    mom32_flop = 2 * nc * mom32_fma
     return dict(
         Nu=Nu, Np=Np, ncell=nc,
         mom64_bytes=8 * (3 * Nu * 3 + 2 * Np),          # x, u0, y, phi, mdot
         mom32_bytes=4 * 9 * Nu + 8 * 2 * Np,
         mom_flop=mom_flop,
+        mom32_flop=mom32_flop,
         ls_adv_bytes=8 * (Np + Np + 3 * Np),
         ls_reinit_bytes=8 * 3 * Np,
         adj_bytes=8 * (3 * Nu * 5 + 5 * Np),            # x, w, u0 in; g_x, g_u0 out; phi, mdot, w_p in; g_phi, g_mdot out
@@ -217,6 +228,52 @@ def solve_comparison(evap, torch, dev):
     return out
 
 
+def large_case(evap, torch, dev, p: int):
+    """deformed128: 128^3 cells, degree-p velocity (p = 2: 51 M DoFs, p = 3: 171 M DoFs), deformed sphere with
+    spherical-harmonic noise up to l = 6 (seed 5), density ratio 1e4.  FP64 and FP32 applies, the adjoint apply, and
+    the mixed-precision solve against the plain FP64 solve (both to 1e-10), each timed with CUDA events."""
+    wl = workloads.make_workload("deformed128", p=p)
+    op = evap.Operator(wl.n, wl.p, wl.L, dict(wl.params))
+    cu = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    stream = torch.cuda.current_stream()
+    phi, u0, md, x = cu(wl.phi), cu(wl.u0), cu(wl.mdot), cu(wl.x)
+
+    def timed(fn, reps=1):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps, out
+
+    nu3 = 3 * op.n_u
+    res = {"workload": f"deformed128 Q{p}: 128^3 cells, {nu3 / 1e6:.1f} M velocity DoFs, deformed sphere (seed 5), "
+                       "density ratio 1e4"}
+    res["set_fields_ms"], _ = timed(lambda: op.set_fields(phi, u0, md))
+    x32 = x.float()
+    t64, _ = timed(lambda: op.apply_momentum(x, prec=64), reps=3)
+    t32, _ = timed(lambda: op.apply_momentum(x32, prec=32), reps=5)
+    w = cu(np.random.default_rng(7).uniform(-1, 1, nu3))
+    tad, _ = timed(lambda: op.apply_adjoint(w, x, None), reps=2)
+    res["momentum_fp64"] = dict(ms=t64, gdofs=nu3 / t64 / 1e6)
+    res["momentum_fp32"] = dict(ms=t32, gdofs=nu3 / t32 / 1e6,
+                                hbm_gbs=(4 * 3 * nu3 + 8 * 2 * op.n_phi) / t32 / 1e6)
+    res["adjoint"] = dict(ms=tad, gdofs=nu3 / tad / 1e6)
+    tm, (xm, im) = timed(lambda: op.solve(x, mixed=True, rtol=1e-10, max_iter=5000))
+    tf, (xf, inf) = timed(lambda: op.solve(x, mixed=False, rtol=1e-10, max_iter=5000))
+    res["solve_fp64"] = dict(ms=tf, iters=inf["iters"], relres=inf["relres"])
+    res["solve_mixed"] = dict(ms=tm, iters=im["iters"], relres=im["relres"],
+                              diff_vs_fp64_solve=float((xm - xf).norm() / xf.norm()))
+    res["speedup_mixed_over_fp64"] = tf / tm
+    op.close()
+    del phi, u0, md, x, x32, w, xm, xf
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_reference(args):
     """--impl reference: the CPU oracle, timed on a bounded sample per step (rank 0 only)."""
     rank = int(os.environ.get("RANK", "0"))
@@ -251,6 +308,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-solve-compare", action="store_true", help="skip the 96^3 FP64-vs-mixed solve comparison")
+    ap.add_argument("--no-large", action="store_true", help="skip the 128^3 Q2/Q3 large case")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -382,6 +440,7 @@ def main():
                               hbm_frac=counts["mom64_bytes"] / (part["mom64"] * 1e-3) / 1e9 / hbm,
                               fp64_tflops=mom_tflops),
         "momentum_fp32": dict(ms=part["mom32"], gdofs=Nu3 / (part["mom32"] * 1e-3) / 1e9,
+                              fp32_tflops=counts["mom32_flop"] / (part["mom32"] * 1e-3) / 1e12,
                               gbs=counts["mom32_bytes"] / (part["mom32"] * 1e-3) / 1e9,
                               hbm_frac=counts["mom32_bytes"] / (part["mom32"] * 1e-3) / 1e9 / hbm),
         "levelset_advect": dict(ms=part["ls_advect"], gdofs=counts["Np"] / (part["ls_advect"] * 1e-3) / 1e9),
@@ -391,14 +450,29 @@ def main():
                         fp64_tflops=counts["adj_flop"] / (part["adjoint"] * 1e-3) / 1e12),
         "solve_mixed": dict(ms=part["solve"], iters=solve_info.get("iters"), relres=solve_info.get("relres")),
     }
-    roofline = dict(bound="alu", kernel="k_momentum<double,2,8> (FP64 apply)", achieved=mom_tflops,
-                    peak=FP64_PEAK_TFLOPS, unit="TFLOP/s", frac=mom_tflops / FP64_PEAK_TFLOPS,
-                    traffic=None, peak_source="nominal FP64 rate of the profiling recipe (probe measured 1.19)",
-                    hbm=dict(achieved=breakdown["momentum_fp64"]["gbs"], peak=hbm, unit="GB/s",
-                             frac=breakdown["momentum_fp64"]["hbm_frac"], source=peak_src))
+    # dominant kernel of the step: the FP32 momentum apply (the inner operator, ~57 launches per step in the solve).
+    # Its arithmetic intensity (~50 flop per algorithmic byte) is above the FP32 machine balance (~12 flop/byte),
+    # so the binding roof is the FP32 pipe; the HBM fraction of its algorithmic bytes is reported beside it.
+    t32 = part["mom32"] * 1e-3
+    f32 = counts["mom32_flop"] / t32 / 1e12
+    roofline = dict(bound="alu", kernel="k_momentum32<2,32> (FP32 momentum apply inside the mixed solve)",
+                    achieved=f32, peak=FP32_PEAK_TFLOPS, unit="TFLOP/s", frac=f32 / FP32_PEAK_TFLOPS,
+                    traffic=None,
+                    peak_source="FP32 peak from the recipe's unit counts and max clock (152 SM x 128 lanes x 2 x "
+                                "2.07 GHz); the FMA probe measured 73 TFLOP/s",
+                    hbm=dict(achieved=breakdown["momentum_fp32"]["gbs"], peak=hbm, unit="GB/s",
+                             frac=breakdown["momentum_fp32"]["hbm_frac"], source=peak_src,
+                             bytes_per_launch=counts["mom32_bytes"]),
+                    fp64_kernel=dict(kernel="k_momentum<double,2,8>", bound="alu", achieved=mom_tflops,
+                                     peak=FP64_PEAK_TFLOPS, unit="TFLOP/s", frac=mom_tflops / FP64_PEAK_TFLOPS,
+                                     peak_source="nominal FP64 rate (profiling recipe); FMA probe measured 1.19"))
     solves = None
     if rank == 0 and not args.no_solve_compare:
         solves = solve_comparison(evap, torch, dev)
+    large = None
+    if rank == 0 and not args.no_large:
+        op.close()
+        large = {f"q{p}": large_case(evap, torch, dev, p) for p in (2, 3)}
     cpu = None
     if rank == 0 and not args.no_cpu:
         dt, dofs, used = oracle_sample_subprocess(nb=20)
@@ -415,7 +489,8 @@ def main():
                                         "DoFs), 4 random spheres, density ratio 1e3, random-Fourier velocity",
                                step="set_fields + FP64/FP32 momentum + 3 level-set applies + adjoint + mixed solve",
                                l2="inputs larger than L2 (no flush)", parallelism=f"replicas x{world}"),
-                   roofline=roofline, breakdown=breakdown, solve_comparison=solves, cpu_baseline=cpu, e2e=e2e,
+                   roofline=roofline, breakdown=breakdown, solve_comparison=solves, large_case=large,
+                   cpu_baseline=cpu, e2e=e2e,
                    gpu_launches=int(launches), clocks=clocks)
         print(json.dumps(out), flush=True)
     if world > 1:

@@ -155,3 +155,29 @@ def test_adjoint_finite_differences_48():
             assert abs(fd - an) <= 1e-6 * abs(an) + 1e-14 * l_abs / (2 * step), (name, fd, an)
             done += 1
         assert done == 50, (name, done)
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_large_case_sampled_rows(p):
+    """128^3 cells, degree p (51 M / 171 M velocity DoFs), deformed sphere, density ratio 1e4: sampled rows of the
+    FP64 apply (with divergence row) and of the FP32 apply against the oracle."""
+    import paper_2401_07805_gb300 as evap
+    wl = workloads.make_workload("deformed128", p=p)
+    op = evap.Operator(wl.n, wl.p, wl.L, dict(wl.params))
+    op.set_fields(cuda(wl.phi), cuda(wl.u0), cuda(wl.mdot))
+    x = cuda(wl.x)
+    y, yp = op.apply_momentum(x, prec=64, with_divergence=True)
+    nodes = _sample_nodes(wl, 48, 11)
+    pb = momentum.Problem.from_workload(wl)
+    yo = momentum.apply_rows(pb, wl.x, nodes)
+    y = y.view(3, -1)
+    assert rel(y[:, nodes].cpu().numpy(), yo) <= 1e-12
+    q1n = np.unique(np.concatenate([np.random.default_rng(5).integers(0, op.n_phi, 24),
+                                    np.nonzero(np.abs(wl.phi) < physics.PHI_BAND)[0][::4999]]))
+    assert rel(yp.cpu().numpy()[q1n], momentum.divergence_rows(pb, wl.x, q1n)) <= 1e-12
+    del y, yp
+    y32 = op.apply_momentum(x.float(), prec=32).view(3, -1)
+    yo32 = momentum.apply_rows(pb, wl.x.astype(np.float32).astype(np.float64), nodes)
+    assert rel(y32[:, nodes].double().cpu().numpy(), yo32) <= 2e-5
+    op.close()
+    torch.cuda.empty_cache()
