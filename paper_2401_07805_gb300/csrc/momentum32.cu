@@ -6,6 +6,9 @@
 // load/store unit, not arithmetic; the kernel is laid out to move few operands through shared memory:
 //   * (P+1)^2 threads per cell, each owning one line of points; the 1D matrices are kernel parameters indexed at
 //     compile time (constant-bank operands, no loads);
+//   * the cell index is the fastest thread index (a warp holds the same line of 32 consecutive cells) and shared
+//     memory is laid out [slot][cell], so every shared access of a warp touches consecutive words (no bank
+//     conflicts), the gather and the scatter of a warp walk along x, and the cell codes load coalesced;
 //   * values and gradients by the sweep tree: z-line S and D (registers) -> y-line S, D on S-output and S on
 //     D-output -> x-line S, D, S, S: every sweep reads and writes whole lines (no collocation derivative, whose
 //     cross-line reads would cost Q loads per point and direction);
@@ -28,20 +31,21 @@ struct Basis32 {
     float W[MAXQ];         // Gauss weights times h (so that W_x W_y W_z = w_q h^3)
 };
 
-template <int P, int CB>
-__global__ void __launch_bounds__(CB*(P + 1) * (P + 1), 2)
+template <int P, int CB, int MINB>
+__global__ void __launch_bounds__(CB*(P + 1) * (P + 1), MINB)
     k_momentum32(MeshArgs<float> m, const __grid_constant__ Basis32 B, const int8_t* __restrict__ code,
                  const int32_t* __restrict__ tindex, const float* __restrict__ table, const float* __restrict__ u0,
                  const float* __restrict__ x, float* __restrict__ y, float* __restrict__ yp) {
     constexpr int Q = P + 1, NQ = Q * Q * Q, L = Q * Q;
     constexpr int OFF_Z = 6 * NQ, OFF_Y = 12 * NQ, OFF_PD = 18 * NQ, OFF_QD = OFF_PD + 2 * L;
-    constexpr int CS = (OFF_QD + 4 * Q) | 1;  // floats per cell (odd stride against bank conflicts)
-    __shared__ float sm[CB * CS];
+    constexpr int CS = OFF_QD + 4 * Q;  // slots per cell
+    __shared__ float sm[CS * CB];      // slot s of cell lc at sm[s * CB + lc]
     const int tid = threadIdx.x;
-    const int lc = tid / L, l = tid % L;
+    const int lc = tid % CB, l = tid / CB;
     const int64_t cell = (int64_t)blockIdx.x * CB + lc;
     const bool active = cell < m.ncell;
-    float* cs = sm + lc * CS;
+    float* cs = sm + lc;
+    auto S_ = [cs](int slot) -> float& { return cs[slot * CB]; };
     auto at = [](int z, int yy, int xx) { return xx + Q * (yy + Q * z); };
     const int n = m.n, M = m.M;
     int cx = 0, cy = 0, cz = 0;
@@ -75,8 +79,8 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1), 2)
                         a += B.S[q][k] * v[k];
                         d += B.D[q][k] * v[k];
                     }
-                    cs[f * NQ + at(q, j, i)] = a;
-                    cs[OFF_Z + f * NQ + at(q, j, i)] = d;
+                    S_(f * NQ + at(q, j, i)) = a;
+                    S_(OFF_Z + f * NQ + at(q, j, i)) = d;
                 }
             }
         }
@@ -91,8 +95,8 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1), 2)
                 float a[Q], az[Q];
 #pragma unroll
                 for (int jj = 0; jj < Q; ++jj) {
-                    a[jj] = cs[f * NQ + at(qz, jj, i)];
-                    az[jj] = cs[OFF_Z + f * NQ + at(qz, jj, i)];
+                    a[jj] = S_(f * NQ + at(qz, jj, i));
+                    az[jj] = S_(OFF_Z + f * NQ + at(qz, jj, i));
                 }
 #pragma unroll
                 for (int q = 0; q < Q; ++q) {
@@ -103,9 +107,9 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1), 2)
                         bd += B.D[q][jj] * a[jj];
                         bz += B.S[q][jj] * az[jj];
                     }
-                    cs[f * NQ + at(qz, q, i)] = bs;
-                    cs[OFF_Y + f * NQ + at(qz, q, i)] = bd;
-                    cs[OFF_Z + f * NQ + at(qz, q, i)] = bz;
+                    S_(f * NQ + at(qz, q, i)) = bs;
+                    S_(OFF_Y + f * NQ + at(qz, q, i)) = bd;
+                    S_(OFF_Z + f * NQ + at(qz, q, i)) = bz;
                 }
             }
         }
@@ -120,9 +124,9 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1), 2)
             for (int f = 0; f < 6; ++f)
 #pragma unroll
                 for (int ii = 0; ii < Q; ++ii) {
-                    bs[f][ii] = cs[f * NQ + at(qz, qy, ii)];
-                    by[f][ii] = cs[OFF_Y + f * NQ + at(qz, qy, ii)];
-                    bz[f][ii] = cs[OFF_Z + f * NQ + at(qz, qy, ii)];
+                    bs[f][ii] = S_(f * NQ + at(qz, qy, ii));
+                    by[f][ii] = S_(OFF_Y + f * NQ + at(qz, qy, ii));
+                    bz[f][ii] = S_(OFF_Z + f * NQ + at(qz, qy, ii));
                 }
             const int8_t cc = code[cell];
             const float* tb = cc == CELL_TABLE ? table + (int64_t)tindex[cell] * TAB_K * NQ : nullptr;
@@ -193,12 +197,12 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1), 2)
             for (int c = 0; c < 3; ++c)
 #pragma unroll
                 for (int ii = 0; ii < Q; ++ii) {
-                    cs[c * NQ + at(qz, qy, ii)] = Pv[c][ii];
-                    cs[OFF_Y + c * NQ + at(qz, qy, ii)] = Py[c][ii];
-                    cs[OFF_Z + c * NQ + at(qz, qy, ii)] = Pz[c][ii];
+                    S_(c * NQ + at(qz, qy, ii)) = Pv[c][ii];
+                    S_(OFF_Y + c * NQ + at(qz, qy, ii)) = Py[c][ii];
+                    S_(OFF_Z + c * NQ + at(qz, qy, ii)) = Pz[c][ii];
                 }
-            cs[OFF_PD + 0 * L + qy + Q * qz] = Pd[0];
-            cs[OFF_PD + 1 * L + qy + Q * qz] = Pd[1];
+            S_(OFF_PD + 0 * L + qy + Q * qz) = Pd[0];
+            S_(OFF_PD + 1 * L + qy + Q * qz) = Pd[1];
         }
     }
     __syncthreads();
@@ -211,9 +215,9 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1), 2)
                 float pv[Q], py[Q], pz[Q];
 #pragma unroll
                 for (int q = 0; q < Q; ++q) {
-                    pv[q] = cs[c * NQ + at(qz, q, i)];
-                    py[q] = cs[OFF_Y + c * NQ + at(qz, q, i)];
-                    pz[q] = cs[OFF_Z + c * NQ + at(qz, q, i)];
+                    pv[q] = S_(c * NQ + at(qz, q, i));
+                    py[q] = S_(OFF_Y + c * NQ + at(qz, q, i));
+                    pz[q] = S_(OFF_Z + c * NQ + at(qz, q, i));
                 }
 #pragma unroll
                 for (int jj = 0; jj < Q; ++jj) {
@@ -223,8 +227,8 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1), 2)
                         r += B.S[q][jj] * pv[q] + B.D[q][jj] * py[q];
                         rz += B.S[q][jj] * pz[q];
                     }
-                    cs[c * NQ + at(qz, jj, i)] = r;
-                    cs[OFF_Z + c * NQ + at(qz, jj, i)] = rz;
+                    S_(c * NQ + at(qz, jj, i)) = r;
+                    S_(OFF_Z + c * NQ + at(qz, jj, i)) = rz;
                 }
             }
             if (yp && l < 2 * Q) {  // divergence row: y-sweep [jx][jy][qz]
@@ -232,12 +236,12 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1), 2)
                 float s0 = 0.f, s1 = 0.f;
 #pragma unroll
                 for (int q = 0; q < Q; ++q) {
-                    const float v = cs[OFF_PD + jx * L + q + Q * qq];
+                    const float v = S_(OFF_PD + jx * L + q + Q * qq);
                     s0 += B.N1[q][0] * v;
                     s1 += B.N1[q][1] * v;
                 }
-                cs[OFF_QD + jx + 2 * (0 + 2 * qq)] = s0;
-                cs[OFF_QD + jx + 2 * (1 + 2 * qq)] = s1;
+                S_(OFF_QD + jx + 2 * (0 + 2 * qq)) = s0;
+                S_(OFF_QD + jx + 2 * (1 + 2 * qq)) = s1;
             }
         }
     }
@@ -251,8 +255,8 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1), 2)
                 float r[Q], rz[Q];
 #pragma unroll
                 for (int q = 0; q < Q; ++q) {
-                    r[q] = cs[c * NQ + at(q, j, i)];
-                    rz[q] = cs[OFF_Z + c * NQ + at(q, j, i)];
+                    r[q] = S_(c * NQ + at(q, j, i));
+                    rz[q] = S_(OFF_Z + c * NQ + at(q, j, i));
                 }
 #pragma unroll
                 for (int k = 0; k < Q; ++k) {
@@ -269,7 +273,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1), 2)
                 float s0 = 0.f, s1 = 0.f;
 #pragma unroll
                 for (int q = 0; q < Q; ++q) {
-                    const float v = cs[OFF_QD + jx + 2 * (jy + 2 * q)];
+                    const float v = S_(OFF_QD + jx + 2 * (jy + 2 * q));
                     s0 += B.N1[q][0] * v;
                     s1 += B.N1[q][1] * v;
                 }
@@ -285,8 +289,9 @@ template <int P>
 static void launch32(const evap_mesh* h, const MeshArgs<float>& m, const Basis32& b, const float* x, float* y,
                      float* yp, cudaStream_t s) {
     constexpr int L = (P + 1) * (P + 1);
-    constexpr int CB = P == 2 ? 32 : 16;  // 288 / 256 threads
-    k_momentum32<P, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * L, 0, s>>>(m, b, h->cell_code, h->table_index,
+    constexpr int CB = 32;                // one warp per line: 288 / 512 threads
+    constexpr int MINB = P == 2 ? 2 : 1;  // 66 KB / 154 KB of shared memory per block
+    k_momentum32<P, CB, MINB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * L, 0, s>>>(m, b, h->cell_code, h->table_index,
                                                                                h->table32, h->u32, x, y, yp);
 }
 
