@@ -122,8 +122,10 @@ int launch_setup_coefficients(evap_mesh* h, cudaStream_t s);
 int launch_qp_coeffs(evap_mesh* h, cudaStream_t s);
 int launch_momentum32(evap_mesh* h, const float* x, float* y, float* yp, cudaStream_t s);
 int launch_transport_velocity(evap_mesh* h, cudaStream_t s);
+// y = A x (+ divergence row into yp if not null).  init = false: y already holds x on the Dirichlet DoFs and 0
+// elsewhere (and yp is null), e.g. written by the solver's fused preconditioner kernel.
 template <typename T>
-int launch_momentum(evap_mesh* h, const T* x, T* y, T* yp, cudaStream_t s);
+int launch_momentum(evap_mesh* h, const T* x, T* y, T* yp, cudaStream_t s, bool init = true);
 template <typename T>
 int launch_levelset(evap_mesh* h, int mode, const T* x, T* y, cudaStream_t s);
 int launch_adjoint(evap_mesh* h, const double* w, const double* wp, const double* x, double* gx, double* gu,

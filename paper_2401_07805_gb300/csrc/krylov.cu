@@ -287,23 +287,27 @@ __global__ void k_norm2(const T* __restrict__ v, int64_t N, double* __restrict__
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
-// out = sc a / diag (right Jacobi preconditioner applied to the normalized basis vector sc a)
+// z = sc v / diag (right Jacobi preconditioner applied to the normalized basis vector sc v), and w initialized for
+// the operator apply w = A z: z on the Dirichlet DoFs (identity rows), 0 elsewhere.  One warp per x-line
+// (component, gy, gz) of M nodes, as in the apply's own initialization.
 template <typename T>
-__global__ void k_precond(const T* __restrict__ a, const T* __restrict__ diag, T* __restrict__ out, int64_t N, T sc) {
-    using VT = typename V2<T>::t;
-    constexpr int W = V2<T>::w;
-    const int64_t nvec = N / W;
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nvec; k += (int64_t)gridDim.x * blockDim.x) {
-        VT x = reinterpret_cast<const VT*>(a)[k];
-        const VT d = reinterpret_cast<const VT*>(diag)[k];
-        T* xp = reinterpret_cast<T*>(&x);
-        const T* dp = reinterpret_cast<const T*>(&d);
-#pragma unroll
-        for (int e = 0; e < W; ++e) xp[e] = sc * xp[e] / dp[e];
-        reinterpret_cast<VT*>(out)[k] = x;
+__global__ void __launch_bounds__(256) k_precond_init(int M, int64_t Nu, unsigned faces, const T* __restrict__ v,
+                                                      const T* __restrict__ diag, T sc, T* __restrict__ z,
+                                                      T* __restrict__ w) {
+    const int lines = 3 * M * M;
+    const int wpb = blockDim.x / 32, warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    for (int line = blockIdx.x * wpb + warp; line < lines; line += gridDim.x * wpb) {
+        const int c = line / (M * M), rem = line - c * M * M, gz = rem / M, gy = rem - gz * M;
+        const bool cyz = ((faces & 4u) && gy == 0) || ((faces & 8u) && gy == M - 1) || ((faces & 16u) && gz == 0) ||
+                         ((faces & 32u) && gz == M - 1);
+        const int64_t off = c * Nu + (int64_t)M * (gy + (int64_t)M * gz);
+        for (int gx = lane; gx < M; gx += 32) {
+            const bool cons = cyz || ((faces & 1u) && gx == 0) || ((faces & 2u) && gx == M - 1);
+            const T zz = sc * v[off + gx] / diag[off + gx];
+            z[off + gx] = zz;
+            w[off + gx] = cons ? zz : T(0);
+        }
     }
-    for (int64_t k = nvec * W + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x)
-        out[k] = sc * a[k] / diag[k];
 }
 
 // x += diag^{-1} sum_i y[i] V_i   (x may be unaligned caller memory: scalar)
@@ -445,9 +449,13 @@ static int gmres(Ctx& c, int m, const T* b, T* x, bool x_zero, const T* diag, T*
         for (; j < m; ++j) {
             T* Vj = V + (int64_t)j * c.ld;
             T* Wn = V + (int64_t)(j + 1) * c.ld;  // A z goes straight into the next basis slot
-            k_precond<T><<<G, 256, 0, c.s>>>(Vj, diag, z, N, (T)sc[j]);
-            EVAP_CHECK_LAUNCH("precond");
-            if ((rc = apply_op<T>(c, z, Wn))) return rc;
+            {
+                const int M = c.h->m.M;
+                const unsigned gl = (unsigned)std::min<int64_t>((3 * (int64_t)M * M + 7) / 8, 152 * 16);
+                k_precond_init<T><<<gl, 256, 0, c.s>>>(M, c.h->m.Nu, c.h->m.faces, Vj, diag, (T)sc[j], z, Wn);
+                EVAP_CHECK_LAUNCH("precond");
+            }
+            if ((rc = launch_momentum<T>(c.h, z, Wn, (T*)nullptr, c.s, false))) return rc;
             ++used;
             const int nv = j + 1;
             double* col = &H[(size_t)j * (m + 1)];

@@ -23,18 +23,27 @@ __device__ __forceinline__ bool constrained_node(int gx, int gy, int gz, int M, 
            ((f & 8u) && gy == M - 1) || ((f & 16u) && gz == 0) || ((f & 32u) && gz == M - 1);
 }
 
-// y = x on Dirichlet DoFs, 0 elsewhere; y_p = 0.
+// y = x on Dirichlet DoFs, 0 elsewhere; y_p = 0.  Each warp walks whole x-lines (component c, gy, gz) of M nodes,
+// so the line's position is split once per warp and the lanes only test their own gx.
 template <typename T>
-__global__ void k_momentum_init(int M, int64_t Nu, unsigned faces, const T* __restrict__ x, T* __restrict__ y,
-                                T* __restrict__ yp, int64_t Np) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 3 * Nu; i += stride) {
-        const int64_t node = i % Nu;
-        const int gx = (int)(node % M), gy = (int)((node / M) % M), gz = (int)(node / ((int64_t)M * M));
-        y[i] = constrained_node(gx, gy, gz, M, faces) ? x[i] : T(0);
+__global__ void __launch_bounds__(256) k_momentum_init(int M, int64_t Nu, unsigned faces, const T* __restrict__ x,
+                                                       T* __restrict__ y, T* __restrict__ yp, int64_t Np) {
+    const int lines = 3 * M * M;
+    const int wpb = blockDim.x / 32, warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    for (int line = blockIdx.x * wpb + warp; line < lines; line += gridDim.x * wpb) {
+        const int c = line / (M * M), rem = line - c * M * M, gz = rem / M, gy = rem - gz * M;
+        const bool cyz = ((faces & 4u) && gy == 0) || ((faces & 8u) && gy == M - 1) || ((faces & 16u) && gz == 0) ||
+                         ((faces & 32u) && gz == M - 1);
+        const int64_t off = c * Nu + (int64_t)M * (gy + (int64_t)M * gz);
+        for (int gx = lane; gx < M; gx += 32) {
+            const bool cons = cyz || ((faces & 1u) && gx == 0) || ((faces & 2u) && gx == M - 1);
+            y[off + gx] = cons ? x[off + gx] : T(0);
+        }
     }
-    if (yp)
+    if (yp) {
+        const int64_t stride = (int64_t)gridDim.x * blockDim.x;
         for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < Np; i += stride) yp[i] = T(0);
+    }
 }
 
 // Quadrature-point coefficients of the FP64 momentum operator, evaluated once per set_fields from u0 and the
@@ -356,12 +365,16 @@ int launch_qp_coeffs(evap_mesh* h, cudaStream_t s) {
 }
 
 template <typename T>
-int launch_momentum(evap_mesh* h, const T* x, T* y, T* yp, cudaStream_t s) {
+int launch_momentum(evap_mesh* h, const T* x, T* y, T* yp, cudaStream_t s, bool init) {
     const MeshArgs<T> m = mesh_args<T>(h);
     const Basis<T> b = cast_basis<T>(h->b);
     const T* qc = (const T*)h->qc;  // FP64 only (the FP32 apply takes the line kernel)
-    k_momentum_init<T><<<blocks_for(3 * m.Nu, 256), 256, 0, s>>>(m.M, m.Nu, m.faces, x, y, yp, m.Nphi);
-    EVAP_CHECK_LAUNCH("momentum_init");
+    if (init) {
+        const int64_t lines = 3 * (int64_t)m.M * m.M;
+        const unsigned grid = (unsigned)std::min<int64_t>((lines + 7) / 8, 152 * 16);
+        k_momentum_init<T><<<grid, 256, 0, s>>>(m.M, m.Nu, m.faces, x, y, yp, m.Nphi);
+        EVAP_CHECK_LAUNCH("momentum_init");
+    }
     if constexpr (sizeof(T) == 4) {  // FP32: line-oriented kernel with u0 interpolated on the fly (momentum32.cu)
         (void)b;
         (void)qc;
@@ -380,7 +393,7 @@ int launch_momentum(evap_mesh* h, const T* x, T* y, T* yp, cudaStream_t s) {
         return EVAP_OK;
     }
 }
-template int launch_momentum<double>(evap_mesh*, const double*, double*, double*, cudaStream_t);
-template int launch_momentum<float>(evap_mesh*, const float*, float*, float*, cudaStream_t);
+template int launch_momentum<double>(evap_mesh*, const double*, double*, double*, cudaStream_t, bool);
+template int launch_momentum<float>(evap_mesh*, const float*, float*, float*, cudaStream_t, bool);
 
 }  // namespace evap

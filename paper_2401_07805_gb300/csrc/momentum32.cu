@@ -19,11 +19,6 @@
 
 namespace evap {
 
-__device__ __forceinline__ bool constrained32(int gx, int gy, int gz, int M, unsigned f) {
-    return ((f & 1u) && gx == 0) || ((f & 2u) && gx == M - 1) || ((f & 4u) && gy == 0) ||
-           ((f & 8u) && gy == M - 1) || ((f & 16u) && gz == 0) || ((f & 32u) && gz == M - 1);
-}
-
 struct Basis32 {
     float S[MAXQ][MAXQ];   // l_a(t_q)
     float D[MAXQ][MAXQ];   // l_a'(t_q) / h (physical)
@@ -42,17 +37,30 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1), MINB)
     __shared__ float sm[CS * CB];      // slot s of cell lc at sm[s * CB + lc]
     const int tid = threadIdx.x;
     const int lc = tid % CB, l = tid / CB;
-    const int64_t cell = (int64_t)blockIdx.x * CB + lc;
-    const bool active = cell < m.ncell;
+    const int n = m.n, M = m.M;
+    // A block holds CB consecutive cells of one x-row: (cx, cy, cz) = (CB * xb + lc, row % n, row / n).
+    const int nxc = (n + CB - 1) / CB;
+    const int row = (int)(blockIdx.x / (unsigned)nxc);
+    const int cx = ((int)blockIdx.x - row * nxc) * CB + lc, cy = row % n, cz = row / n;
+    const bool active = cx < n;
+    const int64_t cell = cx + (int64_t)n * row;
     float* cs = sm + lc;
     auto S_ = [cs](int slot) -> float& { return cs[slot * CB]; };
     auto at = [](int z, int yy, int xx) { return xx + Q * (yy + Q * z); };
-    const int n = m.n, M = m.M;
-    int cx = 0, cy = 0, cz = 0;
-    if (active) {
-        cx = (int)(cell % n);
-        cy = (int)((cell / n) % n);
-        cz = (int)(cell / ((int64_t)n * n));
+    // Nodes of this thread's z-line (gx, gy, P cz + k) and whether each is a free (unconstrained) DoF.
+    const int64_t MM = (int64_t)M * M;
+    int64_t zbase;
+    bool keep[Q];
+    {
+        const int i = l % Q, j = l / Q;
+        const int gx = P * cx + i, gy = P * cy + j, gz0 = P * cz;
+        const unsigned fc = m.faces;
+        const bool cxy = ((fc & 1u) && gx == 0) || ((fc & 2u) && gx == M - 1) || ((fc & 4u) && gy == 0) ||
+                         ((fc & 8u) && gy == M - 1);
+#pragma unroll
+        for (int k = 0; k < Q; ++k)
+            keep[k] = !(cxy || ((fc & 16u) && gz0 + k == 0) || ((fc & 32u) && gz0 + k == M - 1));
+        zbase = gx + (int64_t)M * gy + MM * gz0;
     }
     // ---------------------------------------------------------------- z-lines: gather, S and D along z
     {
@@ -61,16 +69,9 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1), MINB)
 #pragma unroll
             for (int f = 0; f < 6; ++f) {
                 float v[Q];
+                const float* src = (f < 3 ? x : u0) + (f % 3) * m.Nu + zbase;
 #pragma unroll
-                for (int k = 0; k < Q; ++k) {
-                    const int gx = P * cx + i, gy = P * cy + j, gz = P * cz + k;
-                    const int64_t node = gx + (int64_t)M * (gy + (int64_t)M * gz);
-                    const int comp = f % 3;
-                    if (f < 3)
-                        v[k] = constrained32(gx, gy, gz, M, m.faces) ? 0.f : x[comp * m.Nu + node];
-                    else
-                        v[k] = u0[comp * m.Nu + node];
-                }
+                for (int k = 0; k < Q; ++k) v[k] = (f >= 3 || keep[k]) ? src[k * MM] : 0.f;
 #pragma unroll
                 for (int q = 0; q < Q; ++q) {
                     float a = 0.f, d = 0.f;
@@ -263,9 +264,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1), MINB)
                     float o = 0.f;
 #pragma unroll
                     for (int q = 0; q < Q; ++q) o += B.S[q][k] * r[q] + B.D[q][k] * rz[q];
-                    const int gx = P * cx + i, gy = P * cy + j, gz = P * cz + k;
-                    if (!constrained32(gx, gy, gz, M, m.faces))
-                        atomicAdd(&y[c * m.Nu + gx + (int64_t)M * (gy + (int64_t)M * gz)], o);
+                    if (keep[k]) atomicAdd(&y[c * m.Nu + zbase + k * MM], o);
                 }
             }
             if (yp && l < 4) {  // divergence row: z-sweep, Q1 node (jx, jy, jz)
@@ -291,7 +290,8 @@ static void launch32(const evap_mesh* h, const MeshArgs<float>& m, const Basis32
     constexpr int L = (P + 1) * (P + 1);
     constexpr int CB = 32;                // one warp per line: 288 / 512 threads
     constexpr int MINB = P == 2 ? 2 : 1;  // 66 KB / 154 KB of shared memory per block
-    k_momentum32<P, CB, MINB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * L, 0, s>>>(m, b, h->cell_code, h->table_index,
+    const unsigned grid = (unsigned)(((m.n + CB - 1) / CB) * (int64_t)m.n * m.n);
+    k_momentum32<P, CB, MINB><<<grid, CB * L, 0, s>>>(m, b, h->cell_code, h->table_index,
                                                                                h->table32, h->u32, x, y, yp);
 }
 
