@@ -4,7 +4,7 @@ One step = one pass of the whole hot path over the 64^3-cell four-sphere workloa
 DoFs, 275 k level-set DoFs, density ratio 1e3, random-Fourier velocity):
   set_fields (material law table + variant-2 transport velocity with closest-point projection)
   -> momentum apply FP64 with divergence row -> momentum apply FP32 -> level-set advect / reinit / reinit RHS (FP64)
-  -> adjoint apply (all four gradients) -> mixed-precision GMRES(30) solve to 1e-10.
+  -> adjoint apply (all four gradients) -> mixed-precision GMRES(16) solve to 1e-10.
 value = velocity DoFs per step / step time (GDoF/s of the whole pass); per-operator GDoF/s, bytes and the roofline
 of the dominant kernel are reported beside it.  Inputs (~0.5 GB touched per step) exceed the 129 MB L2.
 
@@ -202,7 +202,7 @@ def oracle_sample_subprocess(nb: int, reps: int = 1):
 
 
 def solve_comparison(evap, torch, dev):
-    """96^3 slab (21.6 M velocity DoFs): FP64 GMRES(30) + Jacobi vs FP32-inner GMRES(30) with FP64 iterative
+    """96^3 slab (21.6 M velocity DoFs): FP64 GMRES(16) + Jacobi vs FP32-inner GMRES(16) with FP64 iterative
     refinement, both to ||f - A x|| <= 1e-10 ||f||; error of each against an FP64 solve driven to 1e-13."""
     wl = workloads.make_workload("slab96")
     op = evap.Operator(wl.n, wl.p, wl.L, dict(wl.params))
@@ -360,7 +360,7 @@ def main():
         mark(6)
         g = op.apply_adjoint(dd["w"], dd["x"], dd["wp"])
         mark(7)
-        xs, info = op.solve(dd["f"], mixed=True, restart=30, rtol=1e-10, max_iter=400)
+        xs, info = op.solve(dd["f"], mixed=True, restart=16, rtol=1e-10, max_iter=400)
         mark(8)
         solve_info.update(info)
         return dict(y=y, yp=yp, y32=y32, la=la, lr=lr, lh=lh, gx=g["x"], gu=g["u0"], gphi=g["phi"], gm=g["mdot"], xs=xs)

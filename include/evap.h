@@ -93,7 +93,8 @@ int evap_sizes(evap_handle h, int64_t* n_u, int64_t* n_phi);
  * velocity of the transport velocity), mdot [N_phi] (evaporative mass flux, Eq. evaporDil).  Copies the fields,
  * evaluates the material law at every quadrature point of the interface cells (Eqs. heaviside, rhoEff, muEff,
  * normal_vector, delta, evaporDil) in FP64, and computes the transport velocity u_Gamma [3 N_phi] of the selected
- * variant (App. C closest-point projection for variants 2/3). */
+ * variant (App. C closest-point projection for variants 2/3).  Synchronizes the stream twice (the sizes of the
+ * interface-cell table and of the projection band are read back to size the work). */
 int evap_set_fields(evap_handle h, const double* phi, const double* u, const double* mdot, void* stream);
 
 /* Replace the transport velocity used by EVAP_ADVECT with caller data u_gamma [3 N_phi] (copied). */

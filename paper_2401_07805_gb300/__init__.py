@@ -232,7 +232,7 @@ class Operator:
         _check(lib().evap_jacobi_diagonal(self._h, _ptr(d), _stream()), "evap_jacobi_diagonal")
         return d
 
-    def solve(self, f: torch.Tensor, x0: torch.Tensor | None = None, mixed: bool = True, restart: int = 30,
+    def solve(self, f: torch.Tensor, x0: torch.Tensor | None = None, mixed: bool = True, restart: int = 16,
               rtol: float = 1e-10, max_iter: int = 5000, raise_on_notconv: bool = False):
         f = self._dev(f, 3 * self.n_u, torch.float64, "f")
         x = torch.zeros_like(f) if x0 is None else self._dev(x0, 3 * self.n_u, torch.float64, "x0").clone()

@@ -139,7 +139,7 @@ static int fail(int code, const char* msg) {
 static void free_all(evap_mesh* h) {
     void* ptrs[] = {h->phi, h->u, h->mdot, h->u32, h->phi32, h->cell_code, h->table_index, h->table_count,
                     h->table, h->table32, h->qc, h->ugamma, h->ugamma32, h->cpp_flags, h->flag_count, h->band_list,
-                    h->band_count, h->diag,
+                    h->band_count, h->band_y, h->diag,
                     h->diag32, h->ws, h->red};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -219,7 +219,8 @@ int evap_create_mesh(int n_cells, int degree_u, double L, const evap_params* prm
     al((void**)&h->cpp_flags, Np * sizeof(int32_t));
     al((void**)&h->flag_count, sizeof(unsigned long long));
     al((void**)&h->band_list, Np * sizeof(int32_t));
-    al((void**)&h->band_count, sizeof(int32_t));
+    al((void**)&h->band_count, 2 * sizeof(int32_t));
+    al((void**)&h->band_y, 3 * Np * sizeof(double));
     if (e != cudaSuccess) {
         int rc = cuda_fail("evap_create_mesh: cudaMalloc", e);
         free_all(h);

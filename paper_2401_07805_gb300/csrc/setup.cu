@@ -210,87 +210,58 @@ constexpr double CPP_STALL = 1e-12;   // an accepted step shortening |y - x| by 
 
 __device__ __forceinline__ double clampd(double v, double lo, double hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
-// Normal steps y <- y - (d(y) - d*) / |grad d(y)| n(y) (App. C), returns whether |d(y) - d*| <= tol h.
-__device__ bool cpp_project(const PointEval& e, double y[3], double d_t, double tol, int max_steps) {
-    const double eps = e.m.eps, h = e.m.h, nn = (double)e.m.n;
-    for (int it = 0; it < max_steps; ++it) {
-        double ph, g[3];
-        e.phi_grad(y, ph, g);
-        ph = clampd(ph, -PHI_CLAMP, PHI_CLAMP);
-        const double r = eps * log((1.0 + ph) / (1.0 - ph)) - d_t;
-        if (fabs(r) <= tol * h) return true;
-        const double nrm = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
-        if (nrm == 0.0) return false;
-        const double grad_d = 2.0 * eps / (1.0 - ph * ph) * nrm;
-        const double step = r / grad_d / h;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) y[a] = clampd(y[a] - step * (g[a] / nrm), 0.0, nn);
-    }
-    double ph, g[3];
-    e.phi_grad(y, ph, g);
-    ph = clampd(ph, -PHI_CLAMP, PHI_CLAMP);
-    return fabs(eps * log((1.0 + ph) / (1.0 - ph)) - d_t) <= tol * h;
-}
-
-// Components of y - x along the tangents t0, t1 of the isocontour at y (App. C).
-__device__ void cpp_tangential(const PointEval& e, const double x[3], const double y[3], double tp[3]) {
-    double ph, g[3];
-    e.phi_grad(y, ph, g);
-    const double nrm = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
-    tp[0] = tp[1] = tp[2] = 0.0;
-    if (nrm == 0.0) return;
-    const double nv[3] = {g[0] / nrm, g[1] / nrm, g[2] / nrm};
-    double v[3] = {1.0, 0.0, 0.0};
-    if (fabs(nv[0]) > 0.9) { v[0] = 0.0; v[1] = 1.0; }
-    const double vn = v[0] * nv[0] + v[1] * nv[1] + v[2] * nv[2];
-    double t0[3] = {v[0] - vn * nv[0], v[1] - vn * nv[1], v[2] - vn * nv[2]};
-    const double t0n = sqrt(t0[0] * t0[0] + t0[1] * t0[1] + t0[2] * t0[2]);
-    if (t0n > 0.0) { t0[0] /= t0n; t0[1] /= t0n; t0[2] /= t0n; }
-    const double t1[3] = {nv[1] * t0[2] - nv[2] * t0[1], nv[2] * t0[0] - nv[0] * t0[2], nv[0] * t0[1] - nv[1] * t0[0]};
-    const double dl[3] = {y[0] - x[0], y[1] - x[1], y[2] - x[2]};
-    const double a0 = dl[0] * t0[0] + dl[1] * t0[1] + dl[2] * t0[2];
-    const double a1 = dl[0] * t1[0] + dl[1] * t1[1] + dl[2] * t1[2];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) tp[a] = a0 * t0[a] + a1 * t1[a];
-}
-
 __device__ __forceinline__ double dist3(const double a[3], const double b[3]) {
     const double d0 = a[0] - b[0], d1 = a[1] - b[1], d2 = a[2] - b[2];
     return sqrt(d0 * d0 + d1 * d1 + d2 * d2);
 }
 
-// Closest point of x on d(phi_h) = d_t with the backtracked tangential step; returns converged.
-__device__ bool cpp_closest(const PointEval& e, const double x[3], double y[3], double d_t, double tol, int kmax) {
-    const double nn = (double)e.m.n;
-    y[0] = x[0]; y[1] = x[1]; y[2] = x[2];
-    if (!cpp_project(e, y, d_t, tol, CPP_NORMAL_STEPS)) return false;
-    double dist = dist3(y, x);
-    for (int k = 0; k < kmax; ++k) {
-        double tp[3];
-        cpp_tangential(e, x, y, tp);
-        bool accepted = false;
-        double omega = 1.0;
-        double yn[3];
-        const double dist_prev = dist;
-        for (int bt = 0; bt < CPP_BACKTRACK; ++bt) {
+// Closest point of x on d(phi_h) = d_t with the backtracked tangential step (App. C), written as a state machine
+// in which every trip of the loop makes exactly one point evaluation of phi_h and grad phi_h: the projection of the
+// node (phase 0, at most CPP_NORMAL_STEPS normal steps), the tangential direction at y (phase 1), the projection of a
+// trial point y - omega t (phase 2, at most CPP_TRIAL_STEPS normal steps, omega = 1, 1/2, ..., 1/2^(CPP_BACKTRACK-1)).
+// Lanes of a warp run their own nodes but share the expensive part of every trip (the FP64 evaluation), and a lane
+// whose node is done takes the next band entry, so warps stay full.  The sequence of evaluations and updates of a
+// node is: project x (normal steps y <- y - (d(y) - d*) / |grad d(y)| n(y) until |d(y) - d*| <= tol h); then
+// repeat up to kmax times: tangential part t of y - x at y; for omega = 1, 1/2, ...: project y - omega t; accept
+// the first trial point that reached the isocontour and is strictly closer to x; stop when none is, when the accepted
+// step is <= tol or shortens |y - x| by <= CPP_STALL of it.  Not converged: the first projection failed or kmax
+// outer iterations ran without a stop.
+struct CppLane {
+    int b = -1;  // band entry, -1 none
+    int phase = 0, steps = 0, k = 0, bt = 0;
+    double x[3], y[3], yn[3], tp[3];
+    double dist = 0.0, dist_prev = 0.0, omega = 1.0;
+};
+
+// phi_h and grad phi_h (physical units) at s (cell units) by successive linear interpolation along x, y, z
+// (the trilinear Q1 interpolant of Sec. 2.5; fewer FP64 operations than the weighted sum over the 8 nodes).
+__device__ __forceinline__ void q1_lerp(const PointEval& e, const double s[3], double& val, double g[3]) {
+    int k[3];
+    double t[3];
+    e.locate(s, k, t);
+    const int64_t m1 = e.m.n + 1;
+    const double* f = e.phi + k[0] + m1 * (k[1] + m1 * k[2]);
+    double ex[2][2], dx[2][2];
 #pragma unroll
-            for (int a = 0; a < 3; ++a) yn[a] = clampd(y[a] - omega * tp[a], 0.0, nn);
-            const bool on = cpp_project(e, yn, d_t, tol, CPP_TRIAL_STEPS);
-            const double dn = dist3(yn, x);
-            if (on && dn < dist) {
-                accepted = true;
-                dist = dn;
-                break;
-            }
-            omega *= 0.5;
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const double v0 = f[m1 * (b + m1 * c)], v1 = f[1 + m1 * (b + m1 * c)];
+            dx[c][b] = v1 - v0;
+            ex[c][b] = fma(t[0], dx[c][b], v0);
         }
-        if (!accepted) return true;
-        const double step = dist3(yn, y);
-        const double gain = dist_prev - dist;
-        y[0] = yn[0]; y[1] = yn[1]; y[2] = yn[2];
-        if (step <= tol || gain <= CPP_STALL * dist) return true;
+    double exy[2], dxy[2], dyx[2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        dyx[c] = ex[c][1] - ex[c][0];
+        exy[c] = fma(t[1], dyx[c], ex[c][0]);
+        dxy[c] = fma(t[1], dx[c][1] - dx[c][0], dx[c][0]);
     }
-    return false;
+    const double dz = exy[1] - exy[0];
+    val = fma(t[2], dz, exy[0]);
+    g[0] = fma(t[2], dxy[1] - dxy[0], dxy[0]) * e.m.inv_h;
+    g[1] = fma(t[2], dyx[1] - dyx[0], dyx[0]) * e.m.inv_h;
+    g[2] = dz * e.m.inv_h;
 }
 
 // Transport velocity at Q1 node `node` from the point y (cell units) whose velocity is extended:
@@ -353,23 +324,136 @@ __global__ void k_transport_direct(PointEval e, const double* __restrict__ mdot,
     transport_finish(e, mdot, node, y, m.variant == 2 ? m.rho_l : m.rho_g, ug);
 }
 
-// Pass 2, one thread per band node: closest point on the liquid (variant 2) or gas (variant 3) end of the zone.
-__global__ void k_transport_band(PointEval e, const double* __restrict__ mdot, double tol, int kmax,
-                                 const int32_t* __restrict__ band, const int32_t* __restrict__ band_count,
-                                 double* __restrict__ ug, int32_t* __restrict__ flags, unsigned long long* flag_count) {
+// Pass 2, persistent: closest points of the band nodes on the liquid (variant 2) or gas (variant 3) end of the zone,
+// y of band entry b to band_y[3 b], the convergence flag to flags[node].  band_count[1] hands out the entries.
+__global__ void __launch_bounds__(32) k_transport_band(PointEval e, double tol, int kmax, const int32_t* __restrict__ band,
+                                                       int32_t* band_count, double* __restrict__ band_y,
+                                                       int32_t* __restrict__ flags, unsigned long long* flag_count) {
     const MeshArgs<double>& m = e.m;
-    const int count = *band_count;
+    const int count = band_count[0];
     const int m1 = m.n + 1;
     const double d_t = m.variant == 2 ? 3.0 * m.eps : -3.0 * m.eps;
-    const double rho_t = m.variant == 2 ? m.rho_l : m.rho_g;
+    const double eps = m.eps, h = m.h, nn = (double)m.n;
+    CppLane L;
+    auto take = [&]() {
+        L.b = atomicAdd(&band_count[1], 1);
+        if (L.b >= count) {
+            L.b = -1;
+            return;
+        }
+        const int64_t node = band[L.b];
+        L.x[0] = (double)(node % m1);
+        L.x[1] = (double)((node / m1) % m1);
+        L.x[2] = (double)(node / ((int64_t)m1 * m1));
+        L.y[0] = L.x[0]; L.y[1] = L.x[1]; L.y[2] = L.x[2];
+        L.phase = 0;
+        L.steps = 0;
+    };
+    auto finish = [&](bool converged) {
+        band_y[3 * (int64_t)L.b + 0] = L.y[0];
+        band_y[3 * (int64_t)L.b + 1] = L.y[1];
+        band_y[3 * (int64_t)L.b + 2] = L.y[2];
+        flags[band[L.b]] = converged ? 0 : 1;
+        if (!converged) atomicAdd(flag_count, 1ULL);
+        take();
+    };
+    take();
+    const double c_step = 1.0 / (2.0 * eps * h);  // step (cell units) = r / (|grad d| h), |grad d| = 2 eps |g| / (1 - ph^2)
+    while (__any_sync(0xffffffffu, L.b >= 0)) {
+        if (L.b < 0) continue;
+        // the trip's point evaluation and the quantities every phase needs (computed by all lanes alike)
+        const bool trial = L.phase == 2;
+        double p[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) p[a] = trial ? L.yn[a] : L.y[a];
+        double ph, g[3];
+        q1_lerp(e, p, ph, g);
+        ph = clampd(ph, -PHI_CLAMP, PHI_CLAMP);
+        const double r = eps * log((1.0 + ph) / (1.0 - ph)) - d_t;
+        const double nrm = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+        const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+        const double nv[3] = {g[0] * inv, g[1] * inv, g[2] * inv};
+        const bool on = fabs(r) <= tol * h;
+        const int max_steps = trial ? CPP_TRIAL_STEPS : CPP_NORMAL_STEPS;
+        const bool can_step = !on && L.steps < max_steps && nrm > 0.0;
+        if (L.phase != 1 && can_step) {  // normal step of the point being projected
+            const double step = r * (1.0 - ph * ph) * inv * c_step;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) p[a] = clampd(p[a] - step * nv[a], 0.0, nn);
+            ++L.steps;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                if (trial) L.yn[a] = p[a];
+                else L.y[a] = p[a];
+            }
+            continue;
+        }
+        if (L.phase == 0) {  // projection of the node ended
+            if (on) {
+                L.dist = dist3(L.y, L.x);
+                L.k = 0;
+                if (kmax <= 0) finish(false);
+                else L.phase = 1;
+            } else {
+                finish(false);
+            }
+        } else if (L.phase == 1) {  // tangential part of y - x at y, first trial point
+            L.tp[0] = L.tp[1] = L.tp[2] = 0.0;
+            if (nrm > 0.0) {
+                const bool alt = fabs(nv[0]) > 0.9;  // v = e_y instead of e_x
+                const double vn = alt ? nv[1] : nv[0];
+                double t0[3] = {(alt ? 0.0 : 1.0) - vn * nv[0], (alt ? 1.0 : 0.0) - vn * nv[1], -vn * nv[2]};
+                const double t0n = sqrt(t0[0] * t0[0] + t0[1] * t0[1] + t0[2] * t0[2]);
+                if (t0n > 0.0) {
+                    const double it = 1.0 / t0n;
+                    t0[0] *= it; t0[1] *= it; t0[2] *= it;
+                }
+                const double t1[3] = {nv[1] * t0[2] - nv[2] * t0[1], nv[2] * t0[0] - nv[0] * t0[2],
+                                      nv[0] * t0[1] - nv[1] * t0[0]};
+                const double dl[3] = {L.y[0] - L.x[0], L.y[1] - L.x[1], L.y[2] - L.x[2]};
+                const double a0 = dl[0] * t0[0] + dl[1] * t0[1] + dl[2] * t0[2];
+                const double a1 = dl[0] * t1[0] + dl[1] * t1[1] + dl[2] * t1[2];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) L.tp[a] = a0 * t0[a] + a1 * t1[a];
+            }
+            L.omega = 1.0;
+            L.bt = 0;
+            L.dist_prev = L.dist;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) L.yn[a] = clampd(L.y[a] - L.omega * L.tp[a], 0.0, nn);
+            L.steps = 0;
+            L.phase = 2;
+        } else {  // projection of the trial point ended: on the isocontour (on) or failed
+            const double dn = dist3(L.yn, L.x);
+            if (on && dn < L.dist) {  // accepted
+                L.dist = dn;
+                const double step = dist3(L.yn, L.y);
+                const double gain = L.dist_prev - L.dist;
+                L.y[0] = L.yn[0]; L.y[1] = L.yn[1]; L.y[2] = L.yn[2];
+                if (step <= tol || gain <= CPP_STALL * L.dist) finish(true);
+                else if (++L.k == kmax) finish(false);
+                else L.phase = 1;
+            } else if (++L.bt == CPP_BACKTRACK) {  // no shorter point on the isocontour
+                finish(true);
+            } else {
+                L.omega *= 0.5;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) L.yn[a] = clampd(L.y[a] - L.omega * L.tp[a], 0.0, nn);
+                L.steps = 0;
+            }
+        }
+    }
+}
+
+// Pass 3, one thread per band entry: u_Gamma at the band nodes from their closest points.
+__global__ void k_transport_band_finish(PointEval e, const double* __restrict__ mdot, const int32_t* __restrict__ band,
+                                        const int32_t* __restrict__ band_count, const double* __restrict__ band_y,
+                                        double* __restrict__ ug) {
+    const int count = band_count[0];
+    const double rho_t = e.m.variant == 2 ? e.m.rho_l : e.m.rho_g;
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < count; b += gridDim.x * blockDim.x) {
-        const int64_t node = band[b];
-        const double sx[3] = {(double)(node % m1), (double)((node / m1) % m1), (double)(node / ((int64_t)m1 * m1))};
-        double y[3];
-        const int flag = cpp_closest(e, sx, y, d_t, tol, kmax) ? 0 : 1;
-        transport_finish(e, mdot, node, y, rho_t, ug);
-        flags[node] = flag;
-        if (flag) atomicAdd(flag_count, 1ULL);
+        const double y[3] = {band_y[3 * (int64_t)b], band_y[3 * (int64_t)b + 1], band_y[3 * (int64_t)b + 2]};
+        transport_finish(e, mdot, band[b], y, rho_t, ug);
     }
 }
 
@@ -386,15 +470,24 @@ int launch_transport_velocity(evap_mesh* h, cudaStream_t s) {
         e.gl[0] = 0.0; e.gl[1] = 0.5 - r; e.gl[2] = 0.5 + r; e.gl[3] = 1.0;
     }
     EVAP_CUDA(cudaMemsetAsync(h->flag_count, 0, sizeof(unsigned long long), s));
-    EVAP_CUDA(cudaMemsetAsync(h->band_count, 0, sizeof(int32_t), s));
+    EVAP_CUDA(cudaMemsetAsync(h->band_count, 0, 2 * sizeof(int32_t), s));
     k_transport_direct<<<blocks_for(h->m.Nphi, 128, 1LL << 40), 128, 0, s>>>(e, h->mdot, h->ugamma, h->cpp_flags,
                                                                             h->band_list, h->band_count);
     EVAP_CHECK_LAUNCH("transport_direct");
     if (h->m.variant != 1) {
-        k_transport_band<<<blocks_for(h->m.Nphi, 64, 152 * 32), 64, 0, s>>>(
-            e, h->mdot, h->prm.cpp_tol, h->prm.cpp_kmax, h->band_list, h->band_count, h->ugamma, h->cpp_flags,
-            h->flag_count);
+        // Persistent pass sized to about 4 band nodes per lane (lanes that finish early take the remaining entries,
+        // so warps stay full until the tail), at most 8 warps per SM: the FP64 pipe, not occupancy, bounds it.
+        int32_t count = 0;
+        EVAP_CUDA(cudaMemcpyAsync(&count, h->band_count, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        EVAP_CUDA(cudaStreamSynchronize(s));
+        const int grid = (int)std::min<int64_t>(std::max<int64_t>(((int64_t)count + 127) / 128, 1), 152 * 8);
+        k_transport_band<<<grid, 32, 0, s>>>(e, h->prm.cpp_tol, h->prm.cpp_kmax, h->band_list, h->band_count,
+                                             h->band_y, h->cpp_flags, h->flag_count);
         EVAP_CHECK_LAUNCH("transport_band");
+        k_transport_band_finish<<<blocks_for(h->m.Nphi, 128, 152 * 16), 128, 0, s>>>(e, h->mdot, h->band_list,
+                                                                                      h->band_count, h->band_y,
+                                                                                      h->ugamma);
+        EVAP_CHECK_LAUNCH("transport_band_finish");
     }
     return launch_to_float(h->ugamma, h->ugamma32, 3 * h->m.Nphi, s);
 }
