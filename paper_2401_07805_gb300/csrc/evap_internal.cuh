@@ -42,6 +42,7 @@ struct MeshArgs {
 enum CellCode : int8_t { CELL_GAS = 0, CELL_LIQUID = 1, CELL_TABLE = 2 };
 constexpr int TAB_K = 6;  // table entries per quadrature point: rho, mu, z n_x, z n_y, z n_z, v_dil
 constexpr int QC_K = 19;  // cached momentum coefficients per quadrature point (see k_qp_coeffs)
+constexpr int QC32_K = 12;  // of which the u0 terms, in FP32 for the FP32 apply (slots 1..12)
 
 template <typename T>
 struct Coeffs {            // quadrature-point coefficients of the momentum operator
@@ -78,6 +79,9 @@ struct evap_mesh {
     float* table32 = nullptr;
     // quadrature-point coefficients of the FP64 momentum operator, all cells [ncell][QC_K][nq]
     double* qc = nullptr;
+    // FP32 copy of the u0 coefficients (slots 1..12 of qc) in the 32-cell block layout of the FP32 apply
+    float* qc32 = nullptr;
+    int64_t qc32_len = 0;
     int64_t qc_len = 0;
     // transport velocity
     double* ugamma = nullptr;

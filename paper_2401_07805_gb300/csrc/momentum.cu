@@ -51,11 +51,13 @@ __global__ void __launch_bounds__(256) k_momentum_init(int M, int64_t Nu, unsign
 //   0: W rho c_m   1..3: W rho u0_b   4..12: newton W rho d_d u0_c (index 4 + 3c + d)   13: 2 W mu
 //   14..16: z n_b (correction gate times normal)   17: W   18: W v_dil
 // W = w_qx w_qy w_qz h^3.  One thread per quadrature point, CB cells per block (u0 interpolated by sum factorization).
+// Slots 1..12 are also stored in FP32 for the FP32 apply, in its 32-cell block layout
+// qc32[((blk * QC32_K + k) * NQ + pt) * 32 + lane], cell (32 xb + lane, row) in block blk = xb + ceil(n / 32) row.
 template <int P, int CB>
 __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
     k_qp_coeffs(MeshArgs<double> m, Basis<double> bas, const int8_t* __restrict__ code,
                 const int32_t* __restrict__ tindex, const double* __restrict__ table, const double* __restrict__ u0,
-                double* __restrict__ qc) {
+                double* __restrict__ qc, float* __restrict__ qc32) {
     constexpr int Q = P + 1, NQ = Q * Q * Q;
     __shared__ double sS[Q][Q], sDc[Q][Q];
     __shared__ double buf[2][CB][3][NQ];
@@ -146,6 +148,12 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
     const int64_t base = cell * QC_K * NQ + t;
 #pragma unroll
     for (int k = 0; k < QC_K; ++k) qc[base + (int64_t)k * NQ] = v[k];
+    const int64_t row = cell / n;
+    const int cx = (int)(cell - row * n);
+    const int64_t blk = cx / 32 + (int64_t)((n + 31) / 32) * row;
+    float* dst = qc32 + (blk * QC32_K * NQ + t) * 32 + (cx % 32);
+#pragma unroll
+    for (int k = 0; k < QC32_K; ++k) dst[(int64_t)k * NQ * 32] = (float)v[1 + k];
 }
 
 template <typename T, int P, int CB>
@@ -351,14 +359,22 @@ int launch_qp_coeffs(evap_mesh* h, cudaStream_t s) {
         EVAP_CUDA(cudaMalloc(&h->qc, need * sizeof(double)));
         h->qc_len = need;
     }
+    const int64_t need32 = (int64_t)((m.n + 31) / 32) * m.n * m.n * QC32_K * nq * 32;
+    if (h->qc32_len < need32) {
+        if (h->qc32) cudaFree(h->qc32);
+        h->qc32 = nullptr;
+        h->qc32_len = 0;
+        EVAP_CUDA(cudaMalloc(&h->qc32, need32 * sizeof(float)));
+        h->qc32_len = need32;
+    }
     if (m.P == 2) {
         constexpr int CB = 8;
         k_qp_coeffs<2, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 27, 0, s>>>(m, h->b, h->cell_code, h->table_index,
-                                                                                  h->table, h->u, h->qc);
+                                                                                  h->table, h->u, h->qc, h->qc32);
     } else {
         constexpr int CB = 4;
         k_qp_coeffs<3, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 64, 0, s>>>(m, h->b, h->cell_code, h->table_index,
-                                                                                  h->table, h->u, h->qc);
+                                                                                  h->table, h->u, h->qc, h->qc32);
     }
     EVAP_CHECK_LAUNCH("qp_coeffs");
     return EVAP_OK;

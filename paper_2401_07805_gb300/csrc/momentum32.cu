@@ -12,7 +12,9 @@
 //   * values and gradients by the sweep tree: z-line S and D (registers) -> y-line S, D on S-output and S on
 //     D-output -> x-line S, D, S, S: every sweep reads and writes whole lines (no collocation derivative, whose
 //     cross-line reads would cost Q loads per point and direction);
-//   * u0 is interpolated on the fly (FP32 arithmetic is cheap) instead of streaming cached coefficients;
+//   * the u0 terms come from the quadrature-point cache of set_fields (k_qp_coeffs), rounded to FP32 (W rho u0 and
+//     newton W rho grad u0, 12 floats per point) in a layout [block][k][point][cell] that a warp reads as one
+//     128-byte line: interpolating u0 on the fly would double the sweep work, the shared-memory traffic and the registers;
 //   * the testing runs the tree backwards (x-line S^T/D^T in registers, then y-lines, then z-lines and the atomic
 //     scatter); four block barriers per batch of cells.
 #include "evap_internal.cuh"
@@ -29,10 +31,11 @@ struct Basis32 {
 template <int P, int CB, int MINB>
 __global__ void __launch_bounds__(CB*(P + 1) * (P + 1), MINB)
     k_momentum32(MeshArgs<float> m, const __grid_constant__ Basis32 B, const int8_t* __restrict__ code,
-                 const int32_t* __restrict__ tindex, const float* __restrict__ table, const float* __restrict__ u0,
+                 const int32_t* __restrict__ tindex, const float* __restrict__ table, const float* __restrict__ qc32,
                  const float* __restrict__ x, float* __restrict__ y, float* __restrict__ yp) {
+    static_assert(CB == 32, "the qc32 layout is for 32-cell blocks");
     constexpr int Q = P + 1, NQ = Q * Q * Q, L = Q * Q;
-    constexpr int OFF_Z = 6 * NQ, OFF_Y = 12 * NQ, OFF_PD = 18 * NQ, OFF_QD = OFF_PD + 2 * L;
+    constexpr int OFF_Z = 3 * NQ, OFF_Y = 6 * NQ, OFF_PD = 9 * NQ, OFF_QD = OFF_PD + 2 * L;
     constexpr int CS = OFF_QD + 4 * Q;  // slots per cell
     __shared__ float sm[CS * CB];      // slot s of cell lc at sm[s * CB + lc]
     const int tid = threadIdx.x;
@@ -67,11 +70,11 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1), MINB)
         const int i = l % Q, j = l / Q;
         if (active) {
 #pragma unroll
-            for (int f = 0; f < 6; ++f) {
+            for (int f = 0; f < 3; ++f) {
                 float v[Q];
-                const float* src = (f < 3 ? x : u0) + (f % 3) * m.Nu + zbase;
+                const float* src = x + f * m.Nu + zbase;
 #pragma unroll
-                for (int k = 0; k < Q; ++k) v[k] = (f >= 3 || keep[k]) ? src[k * MM] : 0.f;
+                for (int k = 0; k < Q; ++k) v[k] = keep[k] ? src[k * MM] : 0.f;
 #pragma unroll
                 for (int q = 0; q < Q; ++q) {
                     float a = 0.f, d = 0.f;
@@ -92,7 +95,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1), MINB)
         const int i = l % Q, qz = l / Q;
         if (active) {
 #pragma unroll
-            for (int f = 0; f < 6; ++f) {
+            for (int f = 0; f < 3; ++f) {
                 float a[Q], az[Q];
 #pragma unroll
                 for (int jj = 0; jj < Q; ++jj) {
@@ -120,9 +123,9 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1), MINB)
     {
         const int qy = l % Q, qz = l / Q;
         if (active) {
-            float bs[6][Q], by[6][Q], bz[6][Q];
+            float bs[3][Q], by[3][Q], bz[3][Q];
 #pragma unroll
-            for (int f = 0; f < 6; ++f)
+            for (int f = 0; f < 3; ++f)
 #pragma unroll
                 for (int ii = 0; ii < Q; ++ii) {
                     bs[f][ii] = S_(f * NQ + at(qz, qy, ii));
@@ -131,6 +134,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1), MINB)
                 }
             const int8_t cc = code[cell];
             const float* tb = cc == CELL_TABLE ? table + (int64_t)tindex[cell] * TAB_K * NQ : nullptr;
+            const float* cq = qc32 + (int64_t)blockIdx.x * QC32_K * NQ * 32 + lc;
             float Pv[3][Q], Py[3][Q], Pz[3][Q], Pd[2];
 #pragma unroll
             for (int c = 0; c < 3; ++c)
@@ -139,9 +143,9 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1), MINB)
             Pd[0] = Pd[1] = 0.f;
 #pragma unroll
             for (int qx = 0; qx < Q; ++qx) {
-                float X[3], G[3][3], U[3], GU[3][3];
+                float X[3], G[3][3];
 #pragma unroll
-                for (int f = 0; f < 6; ++f) {
+                for (int f = 0; f < 3; ++f) {
                     float v = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
 #pragma unroll
                     for (int ii = 0; ii < Q; ++ii) {
@@ -150,11 +154,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1), MINB)
                         gy += B.S[qx][ii] * by[f][ii];
                         gz += B.S[qx][ii] * bz[f][ii];
                     }
-                    if (f < 3) {
-                        X[f] = v; G[f][0] = gx; G[f][1] = gy; G[f][2] = gz;
-                    } else {
-                        U[f - 3] = v; GU[f - 3][0] = gx; GU[f - 3][1] = gy; GU[f - 3][2] = gz;
-                    }
+                    X[f] = v; G[f][0] = gx; G[f][1] = gy; G[f][2] = gz;
                 }
                 float rho, mu, nz[3], vd;
                 const int qi = at(qz, qy, qx);
@@ -171,13 +171,14 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1), MINB)
                 const float W = B.W[qx] * B.W[qy] * B.W[qz];
                 const float wr = W * rho, wm = 2.f * W * mu;
                 const float tr = G[0][0] + G[1][1] + G[2][2];
+                float cf[QC32_K];
+#pragma unroll
+                for (int k = 0; k < QC32_K; ++k) cf[k] = cq[(k * NQ + qi) * 32];
                 float F[3], T[3][3];
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    float v = m.c_mass * X[c] + U[0] * G[c][0] + U[1] * G[c][1] + U[2] * G[c][2];
-                    if (m.newton) v += GU[c][0] * X[0] + GU[c][1] * X[1] + GU[c][2] * X[2];
-                    F[c] = wr * v;
-                }
+                for (int c = 0; c < 3; ++c)
+                    F[c] = wr * m.c_mass * X[c] + cf[0] * G[c][0] + cf[1] * G[c][1] + cf[2] * G[c][2] +
+                           cf[3 + 3 * c] * X[0] + cf[4 + 3 * c] * X[1] + cf[5 + 3 * c] * X[2];
 #pragma unroll
                 for (int c = 0; c < 3; ++c)
 #pragma unroll
@@ -289,10 +290,10 @@ static void launch32(const evap_mesh* h, const MeshArgs<float>& m, const Basis32
                      float* yp, cudaStream_t s) {
     constexpr int L = (P + 1) * (P + 1);
     constexpr int CB = 32;                // one warp per line: 288 / 512 threads
-    constexpr int MINB = P == 2 ? 2 : 1;  // 66 KB / 154 KB of shared memory per block
+    constexpr int MINB = P == 2 ? 3 : 1;  // 35 KB / 80 KB of shared memory per block
     const unsigned grid = (unsigned)(((m.n + CB - 1) / CB) * (int64_t)m.n * m.n);
-    k_momentum32<P, CB, MINB><<<grid, CB * L, 0, s>>>(m, b, h->cell_code, h->table_index,
-                                                                               h->table32, h->u32, x, y, yp);
+    k_momentum32<P, CB, MINB><<<grid, CB * L, 0, s>>>(m, b, h->cell_code, h->table_index, h->table32, h->qc32, x, y,
+                                                       yp);
 }
 
 int launch_momentum32(evap_mesh* h, const float* x, float* y, float* yp, cudaStream_t s) {
