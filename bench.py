@@ -43,9 +43,12 @@ def load_peaks():
 
 # DRAM bytes (read + write) per launch of a kernel from an ncu capture of this bench, valid only while the kernel's
 # sources are unchanged: {(kernel, workload): (bytes, sha256 prefix of the sources, profile summary)}.
-MEASURED_TRAFFIC = {}
+MEASURED_TRAFFIC = {
+    ("k_momentum32", "spheres64"): (431_719_680, "8c2dde05716e8385", "profiles/k_momentum32_spheres64.md"),
+}
 TRAFFIC_SOURCES = {"k_momentum32": ("paper_2401_07805_gb300/csrc/momentum32.cu",
-                                    "paper_2401_07805_gb300/csrc/evap_internal.cuh")}
+                                    "paper_2401_07805_gb300/csrc/evap_internal.cuh",
+                                    "paper_2401_07805_gb300/csrc/basis_ct.cuh")}
 
 
 def sources_digest(kernel):

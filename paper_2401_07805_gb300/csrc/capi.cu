@@ -21,67 +21,40 @@ int cuda_fail(const char* what, cudaError_t e) {
     return e == cudaErrorMemoryAllocation ? EVAP_ENOMEM : EVAP_ECUDA;
 }
 
-// Gauss-Legendre rule on [0, 1] with Q points (closed forms for Q <= 4).
-static void gauss_rule(int Q, double* t, double* w) {
-    double x[MAXQ], W[MAXQ];
-    if (Q == 2) {
-        x[0] = -1.0 / std::sqrt(3.0); x[1] = -x[0];
-        W[0] = W[1] = 1.0;
-    } else if (Q == 3) {
-        x[0] = -std::sqrt(0.6); x[1] = 0.0; x[2] = -x[0];
-        W[0] = W[2] = 5.0 / 9.0; W[1] = 8.0 / 9.0;
-    } else {  // Q == 4
-        const double a = std::sqrt(3.0 / 7.0 - 2.0 / 7.0 * std::sqrt(1.2));
-        const double b = std::sqrt(3.0 / 7.0 + 2.0 / 7.0 * std::sqrt(1.2));
-        x[0] = -b; x[1] = -a; x[2] = a; x[3] = b;
-        W[1] = W[2] = (18.0 + std::sqrt(30.0)) / 36.0;
-        W[0] = W[3] = (18.0 - std::sqrt(30.0)) / 36.0;
-    }
-    for (int q = 0; q < Q; ++q) {
-        t[q] = 0.5 * (x[q] + 1.0);
-        w[q] = 0.5 * W[q];
+// 2-point Gauss-Legendre rule on [0, 1] (Q1 level-set operators).
+static void gauss_rule2(double* t, double* w) {
+    constexpr double r = 0.5773502691896257645091488;  // 1 / sqrt 3
+    t[0] = 0.5 * (1.0 - r);
+    t[1] = 0.5 * (1.0 + r);
+    w[0] = w[1] = 0.5;
+}
+
+template <int P>
+static void copy_ct_basis(Basis<double>& b) {
+    constexpr CtBasis<P> c = make_ct_basis<P>();
+    for (int q = 0; q <= P; ++q) {
+        b.t[q] = c.t[q];
+        b.w[q] = c.w[q];
+        b.N1[q][0] = c.N1[q][0];
+        b.N1[q][1] = c.N1[q][1];
+        for (int k = 0; k <= P; ++k) {
+            b.S[q][k] = c.S[q][k];
+            b.D[q][k] = c.D[q][k];
+            b.Dc[q][k] = c.Dc[q][k];
+        }
     }
 }
 
-// Lagrange polynomial l_a through nodes[0..m) and its derivative at x (product formula).
-static void lagrange(const double* nodes, int m, int a, double x, double* val, double* der) {
-    double v = 1.0;
-    for (int k = 0; k < m; ++k)
-        if (k != a) v *= (x - nodes[k]) / (nodes[a] - nodes[k]);
-    double d = 0.0;
-    for (int k = 0; k < m; ++k) {
-        if (k == a) continue;
-        double term = 1.0 / (nodes[a] - nodes[k]);
-        for (int j = 0; j < m; ++j)
-            if (j != a && j != k) term *= (x - nodes[j]) / (nodes[a] - nodes[j]);
-        d += term;
-    }
-    *val = v;
-    *der = d;
-}
-
+// The mesh's basis: the compile-time tables of basis_ct.cuh (also used as immediates by the FP32 apply).
 void host_basis(int P, Basis<double>& b) {
     std::memset(&b, 0, sizeof(b));
     b.P = P;
     b.Q = P + 1;
-    double nodes[MAXQ];
-    if (P == 2) {
-        nodes[0] = 0.0; nodes[1] = 0.5; nodes[2] = 1.0;
-    } else {
-        const double r = 0.5 / std::sqrt(5.0);
-        nodes[0] = 0.0; nodes[1] = 0.5 - r; nodes[2] = 0.5 + r; nodes[3] = 1.0;
-    }
-    gauss_rule(b.Q, b.t, b.w);
-    for (int q = 0; q < b.Q; ++q) {
-        for (int a = 0; a < b.Q; ++a) lagrange(nodes, b.Q, a, b.t[q], &b.S[q][a], &b.D[q][a]);
-        for (int r = 0; r < b.Q; ++r) {
-            double v;
-            lagrange(b.t, b.Q, r, b.t[q], &v, &b.Dc[q][r]);
-        }
-        b.N1[q][0] = 1.0 - b.t[q];
-        b.N1[q][1] = b.t[q];
-    }
-    gauss_rule(2, b.g2t, b.g2w);
+    if (P == 2)
+        copy_ct_basis<2>(b);
+    else
+        copy_ct_basis<3>(b);
+    gauss_rule2(b.g2t, b.g2w);
 }
 
 template <typename T>

@@ -7,6 +7,7 @@
 #include <string>
 
 #include "../../include/evap.h"
+#include "basis_ct.cuh"
 
 namespace evap {
 

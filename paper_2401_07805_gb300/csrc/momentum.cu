@@ -51,7 +51,8 @@ __global__ void __launch_bounds__(256) k_momentum_init(int M, int64_t Nu, unsign
 //   0: W rho c_m   1..3: W rho u0_b   4..12: newton W rho d_d u0_c (index 4 + 3c + d)   13: 2 W mu
 //   14..16: z n_b (correction gate times normal)   17: W   18: W v_dil
 // W = w_qx w_qy w_qz h^3.  One thread per quadrature point, CB cells per block (u0 interpolated by sum factorization).
-// Slots 1..12 are also stored in FP32 for the FP32 apply, in its 32-cell block layout
+// Slots 1..12 are also stored in FP32 for the FP32 apply (slots 1..3 divided by h: that kernel takes reference
+// gradients), in its 32-cell block layout
 // qc32[((blk * QC32_K + k) * NQ + pt) * 32 + lane], cell (32 xb + lane, row) in block blk = xb + ceil(n / 32) row.
 template <int P, int CB>
 __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
@@ -153,7 +154,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
     const int64_t blk = cx / 32 + (int64_t)((n + 31) / 32) * row;
     float* dst = qc32 + (blk * QC32_K * NQ + t) * 32 + (cx % 32);
 #pragma unroll
-    for (int k = 0; k < QC32_K; ++k) dst[(int64_t)k * NQ * 32] = (float)v[1 + k];
+    for (int k = 0; k < QC32_K; ++k) dst[(int64_t)k * NQ * 32] = (float)(k < 3 ? v[1 + k] * m.inv_h : v[1 + k]);
 }
 
 template <typename T, int P, int CB>

@@ -21,22 +21,25 @@
 
 namespace evap {
 
-struct Basis32 {
-    float S[MAXQ][MAXQ];   // l_a(t_q)
-    float D[MAXQ][MAXQ];   // l_a'(t_q) / h (physical)
-    float N1[MAXQ][2];     // Q1 values at the Gauss points
-    float W[MAXQ];         // Gauss weights times h (so that W_x W_y W_z = w_q h^3)
+// Mesh-size factors of the reference-derivative formulation (the 1D tables are compile-time, for the unit cell):
+// gradients are computed with D_ref = h D, so the kernel carries the powers of h instead.
+struct Scale32 {
+    float h2, h3;  // W = w_q h^3 (weights); the divergence row W (tr G - v) = w_q (h^2 tr G_ref - h^3 v)
+    float c2h;     // viscous flux tested with D: 2 W mu (sym G - ...) / h = w_q mu (2 h) (sym G_ref - ...) / h^2 * h^2
+    float hcm;     // mass term: W rho c_m = w_q rho (h^3 c_m)
 };
+
 
 template <int P, int CB, int MINB>
 __global__ void __launch_bounds__(CB*(P + 1) * (P + 1), MINB)
-    k_momentum32(MeshArgs<float> m, const __grid_constant__ Basis32 B, const int8_t* __restrict__ code,
+    k_momentum32(MeshArgs<float> m, Scale32 hs, const int8_t* __restrict__ code,
                  const int32_t* __restrict__ tindex, const float* __restrict__ table, const float* __restrict__ qc32,
                  const float* __restrict__ x, float* __restrict__ y, float* __restrict__ yp) {
     static_assert(CB == 32, "the qc32 layout is for 32-cell blocks");
     constexpr int Q = P + 1, NQ = Q * Q * Q, L = Q * Q;
     constexpr int OFF_Z = 3 * NQ, OFF_Y = 6 * NQ, OFF_PD = 9 * NQ, OFF_QD = OFF_PD + 2 * L;
     constexpr int CS = OFF_QD + 4 * Q;  // slots per cell
+    const CtBasis<P>& B = kCtBasis<P>;  // S, D (reference), N1, w: immediates after unrolling
     __shared__ float sm[CS * CB];      // slot s of cell lc at sm[s * CB + lc]
     const int tid = threadIdx.x;
     const int lc = tid % CB, l = tid / CB;
@@ -80,8 +83,8 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1), MINB)
                     float a = 0.f, d = 0.f;
 #pragma unroll
                     for (int k = 0; k < Q; ++k) {
-                        a += B.S[q][k] * v[k];
-                        d += B.D[q][k] * v[k];
+                        a += (float)B.S[q][k] * v[k];
+                        d += (float)B.D[q][k] * v[k];
                     }
                     S_(f * NQ + at(q, j, i)) = a;
                     S_(OFF_Z + f * NQ + at(q, j, i)) = d;
@@ -107,9 +110,9 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1), MINB)
                     float bs = 0.f, bd = 0.f, bz = 0.f;
 #pragma unroll
                     for (int jj = 0; jj < Q; ++jj) {
-                        bs += B.S[q][jj] * a[jj];
-                        bd += B.D[q][jj] * a[jj];
-                        bz += B.S[q][jj] * az[jj];
+                        bs += (float)B.S[q][jj] * a[jj];
+                        bd += (float)B.D[q][jj] * a[jj];
+                        bz += (float)B.S[q][jj] * az[jj];
                     }
                     S_(f * NQ + at(qz, q, i)) = bs;
                     S_(OFF_Y + f * NQ + at(qz, q, i)) = bd;
@@ -135,6 +138,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1), MINB)
             const int8_t cc = code[cell];
             const float* tb = cc == CELL_TABLE ? table + (int64_t)tindex[cell] * TAB_K * NQ : nullptr;
             const float* cq = qc32 + (int64_t)blockIdx.x * QC32_K * NQ * 32 + lc;
+            const float wyz = B.wf[qy] * B.wf[qz];
             float Pv[3][Q], Py[3][Q], Pz[3][Q], Pd[2];
 #pragma unroll
             for (int c = 0; c < 3; ++c)
@@ -149,10 +153,10 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1), MINB)
                     float v = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
 #pragma unroll
                     for (int ii = 0; ii < Q; ++ii) {
-                        v += B.S[qx][ii] * bs[f][ii];
-                        gx += B.D[qx][ii] * bs[f][ii];
-                        gy += B.S[qx][ii] * by[f][ii];
-                        gz += B.S[qx][ii] * bz[f][ii];
+                        v += (float)B.S[qx][ii] * bs[f][ii];
+                        gx += (float)B.D[qx][ii] * bs[f][ii];
+                        gy += (float)B.S[qx][ii] * by[f][ii];
+                        gz += (float)B.S[qx][ii] * bz[f][ii];
                     }
                     X[f] = v; G[f][0] = gx; G[f][1] = gy; G[f][2] = gz;
                 }
@@ -168,8 +172,9 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1), MINB)
                     nz[0] = nz[1] = nz[2] = 0.f;
                     vd = 0.f;
                 }
-                const float W = B.W[qx] * B.W[qy] * B.W[qz];
-                const float wr = W * rho, wm = 2.f * W * mu;
+                const float Wr = B.wf[qx] * wyz;  // reference weight w_q
+                const float wr = Wr * rho * hs.hcm;  // W rho c_m
+                const float wm = Wr * mu * hs.c2h;   // 2 W mu / h^2
                 const float tr = G[0][0] + G[1][1] + G[2][2];
                 float cf[QC32_K];
 #pragma unroll
@@ -177,23 +182,23 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1), MINB)
                 float F[3], T[3][3];
 #pragma unroll
                 for (int c = 0; c < 3; ++c)
-                    F[c] = wr * m.c_mass * X[c] + cf[0] * G[c][0] + cf[1] * G[c][1] + cf[2] * G[c][2] +
+                    F[c] = wr * X[c] + cf[0] * G[c][0] + cf[1] * G[c][1] + cf[2] * G[c][2] +
                            cf[3 + 3 * c] * X[0] + cf[4 + 3 * c] * X[1] + cf[5 + 3 * c] * X[2];
 #pragma unroll
                 for (int c = 0; c < 3; ++c)
 #pragma unroll
                     for (int b = 0; b < 3; ++b) T[c][b] = wm * (0.5f * (G[c][b] + G[b][c]) - tr * nz[c] * nz[b]);
-                const float rdiv = W * (tr - vd);
+                const float rdiv = Wr * (hs.h2 * tr - hs.h3 * vd);
 #pragma unroll
                 for (int c = 0; c < 3; ++c)
 #pragma unroll
                     for (int ii = 0; ii < Q; ++ii) {
-                        Pv[c][ii] += B.S[qx][ii] * F[c] + B.D[qx][ii] * T[c][0];
-                        Py[c][ii] += B.S[qx][ii] * T[c][1];
-                        Pz[c][ii] += B.S[qx][ii] * T[c][2];
+                        Pv[c][ii] += (float)B.S[qx][ii] * F[c] + (float)B.D[qx][ii] * T[c][0];
+                        Py[c][ii] += (float)B.S[qx][ii] * T[c][1];
+                        Pz[c][ii] += (float)B.S[qx][ii] * T[c][2];
                     }
-                Pd[0] += B.N1[qx][0] * rdiv;
-                Pd[1] += B.N1[qx][1] * rdiv;
+                Pd[0] += (float)B.N1[qx][0] * rdiv;
+                Pd[1] += (float)B.N1[qx][1] * rdiv;
             }
 #pragma unroll
             for (int c = 0; c < 3; ++c)
@@ -226,8 +231,8 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1), MINB)
                     float r = 0.f, rz = 0.f;
 #pragma unroll
                     for (int q = 0; q < Q; ++q) {
-                        r += B.S[q][jj] * pv[q] + B.D[q][jj] * py[q];
-                        rz += B.S[q][jj] * pz[q];
+                        r += (float)B.S[q][jj] * pv[q] + (float)B.D[q][jj] * py[q];
+                        rz += (float)B.S[q][jj] * pz[q];
                     }
                     S_(c * NQ + at(qz, jj, i)) = r;
                     S_(OFF_Z + c * NQ + at(qz, jj, i)) = rz;
@@ -239,8 +244,8 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1), MINB)
 #pragma unroll
                 for (int q = 0; q < Q; ++q) {
                     const float v = S_(OFF_PD + jx * L + q + Q * qq);
-                    s0 += B.N1[q][0] * v;
-                    s1 += B.N1[q][1] * v;
+                    s0 += (float)B.N1[q][0] * v;
+                    s1 += (float)B.N1[q][1] * v;
                 }
                 S_(OFF_QD + jx + 2 * (0 + 2 * qq)) = s0;
                 S_(OFF_QD + jx + 2 * (1 + 2 * qq)) = s1;
@@ -264,7 +269,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1), MINB)
                 for (int k = 0; k < Q; ++k) {
                     float o = 0.f;
 #pragma unroll
-                    for (int q = 0; q < Q; ++q) o += B.S[q][k] * r[q] + B.D[q][k] * rz[q];
+                    for (int q = 0; q < Q; ++q) o += (float)B.S[q][k] * r[q] + (float)B.D[q][k] * rz[q];
                     if (keep[k]) atomicAdd(&y[c * m.Nu + zbase + k * MM], o);
                 }
             }
@@ -274,8 +279,8 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1), MINB)
 #pragma unroll
                 for (int q = 0; q < Q; ++q) {
                     const float v = S_(OFF_QD + jx + 2 * (jy + 2 * q));
-                    s0 += B.N1[q][0] * v;
-                    s1 += B.N1[q][1] * v;
+                    s0 += (float)B.N1[q][0] * v;
+                    s1 += (float)B.N1[q][1] * v;
                 }
                 const int64_t m1 = n + 1;
                 atomicAdd(&yp[(cx + jx) + m1 * ((cy + jy) + m1 * (cz + 0))], s0);
@@ -286,33 +291,28 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1), MINB)
 }
 
 template <int P>
-static void launch32(const evap_mesh* h, const MeshArgs<float>& m, const Basis32& b, const float* x, float* y,
+static void launch32(const evap_mesh* h, const MeshArgs<float>& m, const Scale32& hs, const float* x, float* y,
                      float* yp, cudaStream_t s) {
     constexpr int L = (P + 1) * (P + 1);
     constexpr int CB = 32;                // one warp per line: 288 / 512 threads
     constexpr int MINB = P == 2 ? 3 : 1;  // 35 KB / 80 KB of shared memory per block
     const unsigned grid = (unsigned)(((m.n + CB - 1) / CB) * (int64_t)m.n * m.n);
-    k_momentum32<P, CB, MINB><<<grid, CB * L, 0, s>>>(m, b, h->cell_code, h->table_index, h->table32, h->qc32, x, y,
+    k_momentum32<P, CB, MINB><<<grid, CB * L, 0, s>>>(m, hs, h->cell_code, h->table_index, h->table32, h->qc32, x, y,
                                                        yp);
 }
 
 int launch_momentum32(evap_mesh* h, const float* x, float* y, float* yp, cudaStream_t s) {
     const MeshArgs<float> m = mesh_args<float>(h);
-    Basis32 b;
-    const Basis<double>& d = h->b;
-    for (int q = 0; q < MAXQ; ++q) {
-        for (int a = 0; a < MAXQ; ++a) {
-            b.S[q][a] = (float)d.S[q][a];
-            b.D[q][a] = (float)(d.D[q][a] * h->m.inv_h);
-        }
-        b.N1[q][0] = (float)d.N1[q][0];
-        b.N1[q][1] = (float)d.N1[q][1];
-        b.W[q] = (float)(d.w[q] * h->m.h);
-    }
+    const double hh = h->m.h;
+    Scale32 hs;
+    hs.h2 = (float)(hh * hh);
+    hs.h3 = (float)(hh * hh * hh);
+    hs.c2h = (float)(2.0 * hh);
+    hs.hcm = (float)(hh * hh * hh * h->m.c_mass);
     if (m.P == 2)
-        launch32<2>(h, m, b, x, y, yp, s);
+        launch32<2>(h, m, hs, x, y, yp, s);
     else
-        launch32<3>(h, m, b, x, y, yp, s);
+        launch32<3>(h, m, hs, x, y, yp, s);
     EVAP_CHECK_LAUNCH("momentum32");
     return EVAP_OK;
 }
