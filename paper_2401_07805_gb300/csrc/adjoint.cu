@@ -1,4 +1,6 @@
-// Adjoint of the momentum apply, FP64, quadrature-point data recomputed from the fields (nothing stored).
+// Adjoint of the momentum apply, FP64.  The u0 terms and the material coefficients come from the quadrature-point cache
+// of set_fields (the same FP64 values the forward apply uses, so g_x is exactly its transpose); the material-law
+// derivatives are recomputed from phi at the points of the interface zone.
 //
 // L = w . A(phi, u0) x + w_p . (B x - g(phi, mdot))  (velocity block and divergence row of Eq. weakNavierStokes).
 // Per quadrature point with W the weight, (X, G) values/gradients of x, (Om, OmG) of w, (U, GU) of u0, pi of w_p:
@@ -42,7 +44,8 @@ __global__ void k_adjoint_init(int M, int64_t Nu, int64_t Np, unsigned faces, co
 template <int P, int CB>
 __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
     k_adjoint(MeshArgs<double> m, Basis<double> bas, const double* __restrict__ phi, const double* __restrict__ mdot,
-              const double* __restrict__ u0, const double* __restrict__ w, const double* __restrict__ wp,
+              const int8_t* __restrict__ code, const int32_t* __restrict__ tindex, const double* __restrict__ table,
+              const double* __restrict__ qc, const double* __restrict__ w, const double* __restrict__ wp,
               const double* __restrict__ x, double* gx, double* gu, double* gphi, double* gm) {
     constexpr int Q = P + 1, NQ = Q * Q * Q;
     __shared__ double sS[Q][Q], sDc[Q][Q], sN1[Q][2];
@@ -74,13 +77,12 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
         for (int k = 0; k < 3; ++k) {
             buf[0][lc][k][t] = cons ? 0.0 : x[k * m.Nu + gidx];
             buf[0][lc][3 + k][t] = cons ? 0.0 : w[k * m.Nu + gidx];
-            buf[0][lc][6 + k][t] = u0[k * m.Nu + gidx];
         }
     }
     __syncthreads();
     if (active)
 #pragma unroll
-        for (int f = 0; f < 9; ++f) {
+        for (int f = 0; f < 6; ++f) {
             double s = 0;
 #pragma unroll
             for (int k = 0; k < Q; ++k) s += sS[a][k] * buf[0][lc][f][k + Q * (b + Q * c)];
@@ -89,7 +91,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
     __syncthreads();
     if (active)
 #pragma unroll
-        for (int f = 0; f < 9; ++f) {
+        for (int f = 0; f < 6; ++f) {
             double s = 0;
 #pragma unroll
             for (int k = 0; k < Q; ++k) s += sS[b][k] * buf[1][lc][f][a + Q * (k + Q * c)];
@@ -98,7 +100,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
     __syncthreads();
     if (active)
 #pragma unroll
-        for (int f = 0; f < 9; ++f) {
+        for (int f = 0; f < 6; ++f) {
             double s = 0;
 #pragma unroll
             for (int k = 0; k < Q; ++k) s += sS[c][k] * buf[0][lc][f][a + Q * (b + Q * k)];
@@ -108,9 +110,9 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
     double gxv[3] = {0, 0, 0}, guv[3] = {0, 0, 0}, gxg[3][3] = {}, gug[3][3] = {};
     double dphi = 0.0, dg[3] = {0, 0, 0}, dm = 0.0;
     if (active) {
-        double V[9], Gr[9][3];
+        double V[6], Gr[6][3];
 #pragma unroll
-        for (int f = 0; f < 9; ++f) {
+        for (int f = 0; f < 6; ++f) {
             V[f] = buf[1][lc][f][t];
             double g0 = 0, g1 = 0, g2 = 0;
 #pragma unroll
@@ -121,7 +123,24 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
             }
             Gr[f][0] = g0; Gr[f][1] = g1; Gr[f][2] = g2;  // sDc holds the physical derivative (1/h folded in)
         }
-        // Q1 fields at the point: trilinear weights of the 8 cell nodes
+        const double* X = &V[0];
+        const double* Om = &V[3];
+        double (*G)[3] = &Gr[0];
+        double (*OmG)[3] = &Gr[3];
+        // cached coefficients (k_qp_coeffs): 0 W rho c_m, 1..3 W rho u0, 4..12 newton W rho grad u0, 13 2 W mu, 17 W
+        double qv[QC_K];
+        {
+            const double* qp = qc + cell * QC_K * NQ + t;
+#pragma unroll
+            for (int k = 0; k < QC_K; ++k) qv[k] = (k >= 14 && k <= 16) || k == 18 ? 0.0 : qp[k * NQ];
+        }
+        const double W = qv[17];
+        const int8_t cc = code[cell];
+        const bool tcell = cc == CELL_TABLE;
+        const double rho_c = tcell ? table[(int64_t)tindex[cell] * TAB_K * NQ + t]
+                                   : (cc == CELL_LIQUID ? m.rho_H1 : m.rho_H0);
+        const double wr = W * rho_c;  // the W rho of the forward apply
+        // Q1 fields at the point: trilinear weights of the 8 cell nodes (phi only in table cells)
         const double tx = bas.t[a], ty = bas.t[b], tz = bas.t[c];
         double wq[8];
         double ph = 0, pi = 0;
@@ -130,22 +149,14 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
             const int ja = j & 1, jb = (j >> 1) & 1, jc = j >> 2;
             const int64_t nd = (cx + ja) + m1 * ((cy + jb) + m1 * (cz + jc));
             wq[j] = (ja ? tx : 1.0 - tx) * (jb ? ty : 1.0 - ty) * (jc ? tz : 1.0 - tz);
-            ph += wq[j] * phi[nd];
+            if (tcell) ph += wq[j] * phi[nd];
             if (wp) pi += wq[j] * wp[nd];
         }
-        const bool zone = fabs(ph) < PHI_BAND;
         // the phi / mdot sensitivities and the normal are needed only in the interface zone (or with the correction
-        // applied everywhere); elsewhere H is 0 or 1, its derivatives vanish and rho, mu are the phase constants
-        const bool full = zone || (m.stress != 0 && m.corr_zone != 0);
-        const double W = bas.w[a] * bas.w[b] * bas.w[c] * m.vol_w;
-        const double* X = &V[0];
-        const double* Om = &V[3];
-        const double* U = &V[6];
-        double (*G)[3] = &Gr[0];
-        double (*OmG)[3] = &Gr[3];
-        double (*GU)[3] = &Gr[6];
+        // applied everywhere), which lies in table cells; elsewhere H is 0 or 1 and its derivatives vanish
+        const bool zone = tcell && fabs(ph) < PHI_BAND;
+        const bool full = zone || (tcell && m.stress != 0 && m.corr_zone != 0);
         const double nw = m.newton ? 1.0 : 0.0;
-        double rho, mu;
         Material mat;
         double gp[3] = {0, 0, 0}, md = 0.0;
         if (full) {
@@ -161,26 +172,21 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
             }
             gp[0] *= m.inv_h; gp[1] *= m.inv_h; gp[2] *= m.inv_h;
             mat = material(ph, gp[0], gp[1], gp[2], m);
-            rho = mat.rho;
-            mu = mat.mu;
-        } else {
-            const bool liq = ph >= PHI_BAND;
-            rho = liq ? m.rho_H1 : m.rho_H0;
-            mu = liq ? m.mu_H1 : m.mu_H0;
         }
-        const double wr = W * rho, wm = 2.0 * W * mu;
+        const double wm = qv[13];
         // value / gradient sensitivities of the velocity block and of B^T w_p (the correction term added below)
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            gxv[d] = wr * (m.c_mass * Om[d] + nw * (Om[0] * GU[0][d] + Om[1] * GU[1][d] + Om[2] * GU[2][d]));
+            gxv[d] = qv[0] * Om[d] + Om[0] * qv[4 + d] + Om[1] * qv[7 + d] + Om[2] * qv[10 + d];
             guv[d] = wr * (Om[0] * G[0][d] + Om[1] * G[1][d] + Om[2] * G[2][d]);
 #pragma unroll
             for (int e = 0; e < 3; ++e) {
-                gxg[d][e] = wr * Om[d] * U[e] + wm * 0.5 * (OmG[d][e] + OmG[e][d]) + (d == e ? W * pi : 0.0);
+                gxg[d][e] = Om[d] * qv[1 + e] + wm * 0.5 * (OmG[d][e] + OmG[e][d]) + (d == e ? W * pi : 0.0);
                 gug[d][e] = nw * wr * Om[d] * X[e];
             }
         }
         if (full) {
+            const double rho = mat.rho;
             const double zg = correction_on(m, mat.zone) ? 1.0 : 0.0;
             const double* nv = mat.n;
             const double tr = G[0][0] + G[1][1] + G[2][2];
@@ -202,12 +208,14 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
                 dd = 2.0 * m.eps / om;
                 d2d = 4.0 * m.eps * ph / (om * om);
             }
-            // coefficient sensitivities
+            // coefficient sensitivities; u0 and newton grad u0 from the cached W rho u0 / (W rho)
+            const double iwr = 1.0 / wr;
             double dL_drho = 0.0, dL_dmu = 0.0, dL_dn[3];
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                const double Fk = m.c_mass * X[k] + U[0] * G[k][0] + U[1] * G[k][1] + U[2] * G[k][2] +
-                                  nw * (GU[k][0] * X[0] + GU[k][1] * X[1] + GU[k][2] * X[2]);
+                const double Fk = m.c_mass * X[k] +
+                                  (qv[1] * G[k][0] + qv[2] * G[k][1] + qv[3] * G[k][2] + qv[4 + 3 * k] * X[0] +
+                                   qv[5 + 3 * k] * X[1] + qv[6 + 3 * k] * X[2]) * iwr;
                 dL_drho += Om[k] * Fk;
 #pragma unroll
                 for (int l = 0; l < 3; ++l)
@@ -363,12 +371,12 @@ int launch_adjoint(evap_mesh* h, const double* w, const double* wp, const double
     EVAP_CHECK_LAUNCH("adjoint_init");
     if (m.P == 2) {
         constexpr int CB = 4;
-        k_adjoint<2, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 27, 0, s>>>(m, h->b, h->phi, h->mdot, h->u, w, wp,
-                                                                                x, gx, gu, gphi, gm);
+        k_adjoint<2, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 27, 0, s>>>(
+            m, h->b, h->phi, h->mdot, h->cell_code, h->table_index, h->table, h->qc, w, wp, x, gx, gu, gphi, gm);
     } else {
         constexpr int CB = 2;
-        k_adjoint<3, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 64, 0, s>>>(m, h->b, h->phi, h->mdot, h->u, w, wp,
-                                                                                x, gx, gu, gphi, gm);
+        k_adjoint<3, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 64, 0, s>>>(
+            m, h->b, h->phi, h->mdot, h->cell_code, h->table_index, h->table, h->qc, w, wp, x, gx, gu, gphi, gm);
     }
     EVAP_CHECK_LAUNCH("adjoint");
     return EVAP_OK;
