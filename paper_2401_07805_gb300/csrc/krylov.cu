@@ -167,7 +167,7 @@ int launch_diagonal_into(evap_mesh* h, float* acc, double* out, cudaStream_t s) 
 // Vector kernels stream FP32 data as float4 and FP64 data as double2 (bases 16-byte aligned: the Krylov basis has a
 // leading dimension padded to 64 entries) with a scalar tail.
 constexpr int RED_THREADS = 256;
-constexpr int RED_BLOCKS = 304;  // 2 per SM
+constexpr int RED_BLOCKS = 608;  // 4 per SM (register-limited residency of the unrolled kernels): one wave
 
 struct FF {  // float-float accumulator
     float hi, lo;
@@ -227,9 +227,15 @@ __global__ void k_mdot(const T* __restrict__ V, int64_t ld, int nv, const T* __r
     const int64_t nvec = N / W;
     const VT* v4 = reinterpret_cast<const VT*>(v);
     const VT* w4 = reinterpret_cast<const VT*>(w);
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nvec; k += (int64_t)gridDim.x * blockDim.x)
-        dot_vec(acc, v4[k], w4[k]);
-    for (int64_t k = nvec * W + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x)
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    for (; k + stride < nvec; k += 2 * stride) {  // two independent vector loads per operand in flight
+        const VT a0 = v4[k], b0 = w4[k], a1 = v4[k + stride], b1 = w4[k + stride];
+        dot_vec(acc, a0, b0);
+        dot_vec(acc, a1, b1);
+    }
+    if (k < nvec) dot_vec(acc, v4[k], w4[k]);
+    for (int64_t k = nvec * W + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += stride)
         acc.add(v[k], w[k]);
     const double s = block_sum(acc.value());
     if (threadIdx.x == 0) partial[blockIdx.y * RED_BLOCKS + blockIdx.x] = s;
@@ -256,7 +262,29 @@ __global__ void k_maxpy_norm(const T* __restrict__ V, int64_t ld, const double* 
     Acc acc;
     const int64_t nvec = N / W;
     VT* w4 = reinterpret_cast<VT*>(w);
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nvec; k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    for (; k + stride < nvec; k += 2 * stride) {  // two independent positions per thread
+        VT a = w4[k], a2 = w4[k + stride];
+        T* ap = reinterpret_cast<T*>(&a);
+        T* ap2 = reinterpret_cast<T*>(&a2);
+        for (int i = 0; i < nv; ++i) {
+            const VT* vi = reinterpret_cast<const VT*>(V + i * ld);
+            const VT b = vi[k], b2 = vi[k + stride];
+            const T* bp = reinterpret_cast<const T*>(&b);
+            const T* bp2 = reinterpret_cast<const T*>(&b2);
+#pragma unroll
+            for (int e = 0; e < W; ++e) {
+                ap[e] -= hs[i] * bp[e];
+                ap2[e] -= hs[i] * bp2[e];
+            }
+        }
+        w4[k] = a;
+        w4[k + stride] = a2;
+        dot_vec(acc, a, a);
+        dot_vec(acc, a2, a2);
+    }
+    if (k < nvec) {
         VT a = w4[k];
         T* ap = reinterpret_cast<T*>(&a);
         for (int i = 0; i < nv; ++i) {
