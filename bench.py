@@ -255,6 +255,76 @@ def solve_comparison(evap, torch, dev):
     return out
 
 
+def job_time_ms(torch, dist, ms: float, device, world: int) -> float:
+    """The job's time: the largest of the ranks' times (every rank receives it); the rank's own time at N = 1."""
+    if world <= 1:
+        return ms
+    tt = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def aggregate_gdofs(world: int, dofs_per_rank: int, ms: float) -> float:
+    """Whole-job throughput: all ranks' DoFs over the job's time (independent replicas, weak scaling)."""
+    return world * dofs_per_rank / (ms * 1e-3) / 1e9
+
+
+def back_to_back(torch, fn, reps, warm):
+    """Mean time (ms) of `reps` back-to-back calls after `warm` untimed ones, CUDA events on the current stream."""
+    stream = torch.cuda.current_stream()
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def operator_applies(evap, torch, dev, op, d, counts, hbm):
+    """Per-operator throughput on the 64^3 four-sphere workload: 100 back-to-back applies after 10 warm-ups each
+    (momentum FP64 with the divergence row, momentum FP32, level-set advection FP64), the closest-point transport
+    pass alone (20 repeats: band nodes/s, point evaluations, flags), and the adjoint on the 48^3 sphere
+    (2.74 M DoFs, 20 applies).  Inputs are larger than the L2 for every operator except the level set."""
+    nu3, nphi = 3 * op.n_u, op.n_phi
+    x, x32, psi = d["x"], d["x32"], d["psi"]
+    y64 = torch.empty(nu3, dtype=torch.float64, device=dev)
+    yp64 = torch.empty(nphi, dtype=torch.float64, device=dev)
+    y32 = torch.empty(nu3, dtype=torch.float32, device=dev)
+    yl = torch.empty(nphi, dtype=torch.float64, device=dev)
+    out = {}
+    t = back_to_back(torch, lambda: op.apply_momentum(x, prec=64, with_divergence=True, out=y64, out_p=yp64), 100, 10)
+    out["momentum_fp64"] = dict(ms=t, gdofs=nu3 / t / 1e6, gbs=counts["mom64_bytes"] / t / 1e6,
+                                fp64_tflops=counts["mom_flop"] / t / 1e9)
+    t = back_to_back(torch, lambda: op.apply_momentum(x32, prec=32, out=y32), 100, 10)
+    out["momentum_fp32"] = dict(ms=t, gdofs=nu3 / t / 1e6, gbs=counts["mom32_bytes"] / t / 1e6,
+                                hbm_frac=counts["mom32_bytes"] / t / 1e6 / hbm,
+                                fp32_tflops=counts["mom32_flop"] / t / 1e9,
+                                rel_err_vs_fp64=float((y32.double() - y64).norm() / y64.norm()))
+    t = back_to_back(torch, lambda: op.apply_levelset(psi, mode="advect", out=yl), 100, 10)
+    out["levelset_advect_fp64"] = dict(ms=t, gdofs=nphi / t / 1e6, gbs=counts["ls_adv_bytes"] / t / 1e6)
+    t = back_to_back(torch, op.update_transport_velocity, 20, 2)
+    st = op.transport_stats()
+    out["transport_velocity"] = dict(ms=t, band_nodes=st["band_nodes"], band_nodes_per_s=st["band_nodes"] / t * 1e3,
+                                     evaluations_per_node=st["evaluations"] / max(st["band_nodes"], 1),
+                                     flagged=st["flagged"])
+    # adjoint on the 48^3 sphere
+    wl = workloads.make_workload("sphere48")
+    op4 = evap.Operator(wl.n, wl.p, wl.L, dict(wl.params))
+    cu = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    op4.set_fields(cu(wl.phi), cu(wl.u0), cu(wl.mdot))
+    w, xx, wp = cu(wl.extra["w"]), cu(wl.x), cu(wl.extra["w_p"])
+    t = back_to_back(torch, lambda: op4.apply_adjoint(w, xx, wp), 20, 3)
+    c4 = algorithmic_counts(wl.n, wl.p)
+    out["adjoint_sphere48"] = dict(ms=t, gdofs=3 * op4.n_u / t / 1e6, fp64_tflops=c4["adj_flop"] / t / 1e9)
+    op4.close()
+    out["note"] = "100 back-to-back applies after 10 warm-ups (transport 20 after 2, adjoint 20 after 3)"
+    return out
+
+
 def large_case(evap, torch, dev, p: int):
     """deformed128: 128^3 cells, degree-p velocity (p = 2: 51 M DoFs, p = 3: 171 M DoFs), deformed sphere with
     spherical-harmonic noise up to l = 6 (seed 5), density ratio 1e4.  FP64 and FP32 applies, the adjoint apply, and
@@ -286,8 +356,8 @@ def large_case(evap, torch, dev, p: int):
     w = cu(np.random.default_rng(7).uniform(-1, 1, nu3))
     tad, _ = timed(lambda: op.apply_adjoint(w, x, None), reps=2)
     res["momentum_fp64"] = dict(ms=t64, gdofs=nu3 / t64 / 1e6)
-    res["momentum_fp32"] = dict(ms=t32, gdofs=nu3 / t32 / 1e6,
-                                hbm_gbs=(4 * 3 * nu3 + 8 * 2 * op.n_phi) / t32 / 1e6)
+    c = algorithmic_counts(wl.n, p)
+    res["momentum_fp32"] = dict(ms=t32, gdofs=nu3 / t32 / 1e6, hbm_gbs=c["mom32_bytes"] / t32 / 1e6)
     res["adjoint"] = dict(ms=tad, gdofs=nu3 / tad / 1e6)
     tm, (xm, im) = timed(lambda: op.solve(x, mixed=True, rtol=1e-10, max_iter=5000))
     tf, (xf, inf) = timed(lambda: op.solve(x, mixed=False, rtol=1e-10, max_iter=5000))
@@ -336,6 +406,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-solve-compare", action="store_true", help="skip the 96^3 FP64-vs-mixed solve comparison")
     ap.add_argument("--no-large", action="store_true", help="skip the 128^3 Q2/Q3 large case")
+    ap.add_argument("--no-applies", action="store_true", help="skip the per-operator back-to-back apply timings")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -415,15 +486,11 @@ def main():
     if world > 1:
         dist.barrier()
     clocks = sampler.stop()
-    ms_total = t_start.elapsed_time(t_end)
-    if world > 1:
-        tt = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_total = float(tt.item())
+    ms_total = job_time_ms(torch, dist, t_start.elapsed_time(t_end), dev, world)
     ms_step = ms_total / K
     part = {nm: float(np.mean([evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(K)])) for i, nm in enumerate(names)}
     Nu3 = 3 * counts["Nu"]
-    value = world * Nu3 / (ms_step * 1e-3) / 1e9
+    value = aggregate_gdofs(world, Nu3, ms_step)
 
     # end to end: pinned host inputs copied in and all results copied out inside the timed region
     e2e = None
@@ -447,17 +514,13 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         d2h = sum(v.numel() * v.element_size() for v in outs_host.values())
-        e_ms = e0.elapsed_time(e1) / K
-        if world > 1:
-            tt = torch.tensor([e_ms], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e_ms = float(tt.item())
-        e2e = dict(value=world * Nu3 / (e_ms * 1e-3) / 1e9, unit="GDoF/s", ms_per_step=e_ms,
+        e_ms = job_time_ms(torch, dist, e0.elapsed_time(e1) / K, dev, world)
+        e2e = dict(value=aggregate_gdofs(world, Nu3, e_ms), unit="GDoF/s", ms_per_step=e_ms,
                    h2d_bytes_per_step=int(h2d), d2h_bytes_per_step=int(d2h))
 
     peaks, peak_src = load_peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
-    # dominant kernel: the FP64 momentum apply (FP64-pipe bound); alu roofline against FP64 peak
+    # FP64 momentum apply: FP64-pipe bound (its FP64-pipe roofline is reported beside the dominant kernel's)
     t_mom = part["mom64"] * 1e-3
     mom_tflops = counts["mom_flop"] / t_mom / 1e12
     breakdown = {
@@ -500,6 +563,9 @@ def main():
                     fp64_kernel=dict(kernel="k_momentum<double,2,8>", bound="alu", achieved=mom_tflops,
                                      peak=FP64_PEAK_TFLOPS, unit="TFLOP/s", frac=mom_tflops / FP64_PEAK_TFLOPS,
                                      peak_source="nominal FP64 rate (profiling recipe); FMA probe measured 1.19"))
+    applies = None
+    if rank == 0 and not args.no_applies:
+        applies = operator_applies(evap, torch, dev, op, d, counts, hbm)
     solves = None
     if rank == 0 and not args.no_solve_compare:
         solves = solve_comparison(evap, torch, dev)
@@ -523,7 +589,7 @@ def main():
                                         "DoFs), 4 random spheres, density ratio 1e3, random-Fourier velocity",
                                step="set_fields + FP64/FP32 momentum + 3 level-set applies + adjoint + mixed solve",
                                l2="inputs larger than L2 (no flush)", parallelism=f"replicas x{world}"),
-                   roofline=roofline, breakdown=breakdown, solve_comparison=solves, large_case=large,
+                   roofline=roofline, breakdown=breakdown, applies=applies, solve_comparison=solves, large_case=large,
                    cpu_baseline=cpu, e2e=e2e,
                    gpu_launches=int(launches), clocks=clocks)
         print(json.dumps(out), flush=True)

@@ -105,6 +105,16 @@ int evap_set_transport_velocity(evap_handle h, const double* u_gamma, void* stre
  * the number of flagged nodes is written to it (host pointer; this synchronizes the stream). */
 int evap_get_transport_velocity(evap_handle h, double* u_gamma, int32_t* flags, int64_t* n_flagged, void* stream);
 
+/* Recompute the transport velocity (variant of the parameters; App. C closest-point projection for variants 2/3)
+ * from the fields of the last evap_set_fields, replacing any u_Gamma given by evap_set_transport_velocity.  The
+ * same pass evap_set_fields runs; separate so that it can be rerun or timed alone.  Synchronizes the stream once. */
+int evap_update_transport_velocity(evap_handle h, void* stream);
+
+/* Statistics of the last closest-point pass, written to host pointers (any may be NULL; synchronizes the stream):
+ * band_nodes = Q1 nodes that ran the projection, evaluations = point evaluations of phi_h and grad phi_h they made,
+ * flagged = nodes whose iteration did not converge.  Variant 1 (no projection) reports zeros. */
+int evap_transport_stats(evap_handle h, int64_t* band_nodes, int64_t* evaluations, int64_t* flagged, void* stream);
+
 /* Momentum apply y = A x (velocity block of Eq. weakNavierStokes linearized about u, App. D):
  *   y_(i,c) = sum_q W_q [ N_i rho (c_mass x_c + (u . grad) x_c + newton (x . grad) u_c) + grad N_i . 2 mu eps_mod(x)_c ]
  * on unconstrained DoFs; on Dirichlet DoFs y = x and x does not enter other rows.  If y_p is not NULL the
@@ -118,7 +128,8 @@ int evap_apply_levelset(evap_handle h, int mode, int prec, const void* x, void* 
 
 /* Adjoint of the momentum apply for L = w . A(phi, mdot, u) x + w_p . (B x - g(phi, mdot)):
  *   g_x = A^T w + B^T w_p,  g_u0 = dL/du [3 N_u],  g_phi = dL/dphi [N_phi],  g_mdot = dL/dmdot [N_phi],
- * quadrature-point data recomputed from the fields (nothing stored).  w [3 N_u] and x [3 N_u] required; w_p may be
+ * with the quadrature-point coefficients of evap_set_fields and the material-law derivatives recomputed at the
+ * points of the interface zone.  w [3 N_u] and x [3 N_u] required; w_p may be
  * NULL (no divergence row); any g_* may be NULL (not computed).  FP64 only. */
 int evap_apply_adjoint(evap_handle h, const double* w, const double* w_p, const double* x, double* g_x,
                        double* g_u0, double* g_phi, double* g_mdot, void* stream);

@@ -49,6 +49,9 @@ SIGNATURES = {
     "evap_set_fields": (_c_int, [_vp, _vp, _vp, _vp, _vp]),
     "evap_set_transport_velocity": (_c_int, [_vp, _vp, _vp]),
     "evap_get_transport_velocity": (_c_int, [_vp, _vp, _vp, ctypes.POINTER(ctypes.c_int64), _vp]),
+    "evap_update_transport_velocity": (_c_int, [_vp, _vp]),
+    "evap_transport_stats": (_c_int, [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                      ctypes.POINTER(ctypes.c_int64), _vp]),
     "evap_apply_momentum": (_c_int, [_vp, _c_int, _vp, _vp, _vp, _vp]),
     "evap_apply_levelset": (_c_int, [_vp, _c_int, _c_int, _vp, _vp, _vp]),
     "evap_apply_adjoint": (_c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
@@ -191,6 +194,17 @@ class Operator:
         _check(lib().evap_get_transport_velocity(self._h, _ptr(ug), _ptr(flags), ctypes.byref(nf), _stream()),
                "evap_get_transport_velocity")
         return ug, flags, nf.value
+
+    def update_transport_velocity(self):
+        """Recompute u_Gamma from the current fields (the pass set_fields runs)."""
+        _check(lib().evap_update_transport_velocity(self._h, _stream()), "evap_update_transport_velocity")
+
+    def transport_stats(self):
+        """(band nodes, point evaluations, flagged nodes) of the last closest-point pass."""
+        b, e, f = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().evap_transport_stats(self._h, ctypes.byref(b), ctypes.byref(e), ctypes.byref(f), _stream()),
+               "evap_transport_stats")
+        return dict(band_nodes=b.value, evaluations=e.value, flagged=f.value)
 
     def apply_momentum(self, x: torch.Tensor, prec: int = 64, with_divergence: bool = False, out=None, out_p=None):
         dt = torch.float64 if prec == 64 else torch.float32

@@ -112,7 +112,7 @@ static int fail(int code, const char* msg) {
 static void free_all(evap_mesh* h) {
     void* ptrs[] = {h->phi, h->u, h->mdot, h->u32, h->phi32, h->cell_code, h->table_index, h->table_count,
                     h->table, h->table32, h->qc, h->qc32, h->ugamma, h->ugamma32, h->cpp_flags, h->flag_count, h->band_list,
-                    h->band_count, h->band_y, h->diag,
+                    h->band_count, h->band_y, h->cpp_evals, h->diag,
                     h->diag32, h->ws, h->red};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -194,6 +194,7 @@ int evap_create_mesh(int n_cells, int degree_u, double L, const evap_params* prm
     al((void**)&h->band_list, Np * sizeof(int32_t));
     al((void**)&h->band_count, 2 * sizeof(int32_t));
     al((void**)&h->band_y, 3 * Np * sizeof(double));
+    al((void**)&h->cpp_evals, sizeof(unsigned long long));
     if (e != cudaSuccess) {
         int rc = cuda_fail("evap_create_mesh: cudaMalloc", e);
         free_all(h);
@@ -263,6 +264,29 @@ int evap_get_transport_velocity(evap_handle h, double* u_gamma, int32_t* flags, 
         EVAP_CUDA(cudaStreamSynchronize(s));
         *n_flagged = (int64_t)c;
     }
+    return EVAP_OK;
+}
+
+int evap_update_transport_velocity(evap_handle h, void* stream) {
+    if (!h) return fail(EVAP_EINVAL, "evap_update_transport_velocity: null handle");
+    if (!h->has_fields) return fail(EVAP_ENOFIELDS, "evap_update_transport_velocity: fields not set");
+    return launch_transport_velocity(h, (cudaStream_t)stream);
+}
+
+int evap_transport_stats(evap_handle h, int64_t* band_nodes, int64_t* evaluations, int64_t* flagged, void* stream) {
+    if (!h) return fail(EVAP_EINVAL, "evap_transport_stats: null handle");
+    if (!h->has_fields) return fail(EVAP_ENOFIELDS, "evap_transport_stats: fields not set");
+    cudaStream_t s = (cudaStream_t)stream;
+    int32_t cnt[2] = {0, 0};
+    unsigned long long ev = 0, fl = 0;
+    EVAP_CUDA(cudaMemcpyAsync(cnt, h->band_count, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    EVAP_CUDA(cudaMemcpyAsync(&ev, h->cpp_evals, sizeof(ev), cudaMemcpyDeviceToHost, s));
+    EVAP_CUDA(cudaMemcpyAsync(&fl, h->flag_count, sizeof(fl), cudaMemcpyDeviceToHost, s));
+    EVAP_CUDA(cudaStreamSynchronize(s));
+    const bool projected = h->m.variant != 1;
+    if (band_nodes) *band_nodes = projected ? cnt[0] : 0;
+    if (evaluations) *evaluations = projected ? (int64_t)ev : 0;
+    if (flagged) *flagged = (int64_t)fl;
     return EVAP_OK;
 }
 

@@ -92,6 +92,7 @@ struct evap_mesh {
     int32_t* band_list = nullptr;   // Q1 nodes that run the closest-point iteration
     int32_t* band_count = nullptr;  // [0] band nodes, [1] work counter of the closest-point pass
     double* band_y = nullptr;       // closest point (cell units) of band entry b at [3 b]
+    unsigned long long* cpp_evals = nullptr;  // point evaluations of the last closest-point pass
     // Jacobi diagonal and Krylov workspace (allocated by the first solve)
     double* diag = nullptr;
     float* diag32 = nullptr;

@@ -15,17 +15,15 @@
 namespace evap {
 
 // ------------------------------------------------------------------------------------------- Jacobi diagonal
-// diag_(i,c) = sum_q W [ rho c_m N_i^2 + rho N_i (u0 . grad N_i) + newton rho N_i^2 d_c u0_c
-//                      + 2 mu ( (|grad N_i|^2 + (d_c N_i)^2)/2 - (z n)_c d_c N_i ((z n) . grad N_i) ) ]
-// in FP32 from the FP32 coefficient table; one thread per (cell, local node).
+// diag_(i,c) = sum_q [ W rho c_m N_i^2 + N_i (W rho u0 . grad N_i) + N_i^2 newton W rho d_c u0_c
+//                      + 2 W mu ( (|grad N_i|^2 + (d_c N_i)^2)/2 - (z n)_c d_c N_i ((z n) . grad N_i) ) ]
+// in FP32 from the quadrature-point cache of set_fields (k_qp_coeffs); one thread per (cell, local node).
 template <int P, int CB>
 __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
-    k_diagonal(MeshArgs<float> m, Basis<float> bas, const int8_t* __restrict__ code, const int32_t* __restrict__ tindex,
-               const float* __restrict__ table, const float* __restrict__ u0, float* __restrict__ diag) {
+    k_diagonal(MeshArgs<float> m, Basis<float> bas, const double* __restrict__ qc, float* __restrict__ diag) {
     constexpr int Q = P + 1, NQ = Q * Q * Q;
     __shared__ float sS[Q][Q], sD[Q][Q];
-    __shared__ float sU[CB][NQ];
-    __shared__ float qd[CB][12][NQ];  // per point: W rho, U(3), GU_cc(3), 2 W mu, z n(3)
+    __shared__ float qd[CB][11][NQ];  // per point: W rho c_m, W rho U(3), newton W rho d_c u0_c (3), 2 W mu, z n(3)
     const int tid = threadIdx.x, lc = tid / NQ, t = tid % NQ;
     const int64_t cell = (int64_t)blockIdx.x * CB + lc;
     const bool active = cell < m.ncell;
@@ -34,70 +32,31 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
         sD[tid / Q][tid % Q] = bas.D[tid / Q][tid % Q];
     }
     const int a = t % Q, b = (t / Q) % Q, c = t / (Q * Q);
-    const int n = m.n, M = m.M;
-    int64_t gidx = 0;
-    int cx = 0, cy = 0, cz = 0;
     if (active) {
-        cx = (int)(cell % n); cy = (int)((cell / n) % n); cz = (int)(cell / ((int64_t)n * n));
-        gidx = (P * cx + a) + (int64_t)M * ((P * cy + b) + (int64_t)M * (P * cz + c));
-    }
-    // u0 values and gradients at point t, component by component
-    float U[3], GUd[3];
-    for (int k = 0; k < 3; ++k) {
-        __syncthreads();
-        if (active) sU[lc][t] = u0[k * m.Nu + gidx];
-        __syncthreads();
-        float v = 0, g = 0;
-        if (active)
-            for (int i = 0; i < NQ; ++i) {
-                const int ia = i % Q, ib = (i / Q) % Q, ic = i / (Q * Q);
-                const float s3 = sS[a][ia] * sS[b][ib] * sS[c][ic];
-                const float dk = (k == 0 ? sD[a][ia] * sS[b][ib] * sS[c][ic]
-                                         : (k == 1 ? sS[a][ia] * sD[b][ib] * sS[c][ic] : sS[a][ia] * sS[b][ib] * sD[c][ic]));
-                v += s3 * sU[lc][i];
-                g += dk * sU[lc][i];
-            }
-        U[k] = v;
-        GUd[k] = g * m.inv_h;
-    }
-    if (active) {
-        float rho, mu, nz[3];
-        const int8_t cc = code[cell];
-        if (cc == CELL_TABLE) {
-            const float* tb = table + (int64_t)tindex[cell] * TAB_K * NQ + t;
-            rho = tb[0]; mu = tb[NQ]; nz[0] = tb[2 * NQ]; nz[1] = tb[3 * NQ]; nz[2] = tb[4 * NQ];
-        } else {
-            const bool liq = cc == CELL_LIQUID;
-            rho = liq ? m.rho_H1 : m.rho_H0;
-            mu = liq ? m.mu_H1 : m.mu_H0;
-            nz[0] = nz[1] = nz[2] = 0.f;
-        }
-        const float W = bas.w[a] * bas.w[b] * bas.w[c] * m.vol_w;
-        qd[lc][0][t] = W * rho;
-        for (int k = 0; k < 3; ++k) {
-            qd[lc][1 + k][t] = U[k];
-            qd[lc][4 + k][t] = GUd[k];
-            qd[lc][8 + k][t] = nz[k];
-        }
-        qd[lc][7][t] = 2.f * W * mu;
+        const double* qp = qc + cell * QC_K * NQ + t;
+        constexpr int slot[11] = {0, 1, 2, 3, 4, 8, 12, 13, 14, 15, 16};
+#pragma unroll
+        for (int k = 0; k < 11; ++k) qd[lc][k][t] = (float)qp[slot[k] * NQ];
     }
     __syncthreads();
     if (!active) return;
+    const int n = m.n, M = m.M;
+    const int cx = (int)(cell % n), cy = (int)((cell / n) % n), cz = (int)(cell / ((int64_t)n * n));
+    const int64_t gidx = (P * cx + a) + (int64_t)M * ((P * cy + b) + (int64_t)M * (P * cz + c));
     float dsum[3] = {0.f, 0.f, 0.f};
     for (int q = 0; q < NQ; ++q) {
-        const int qa = q % Q, qb = (q / Q) % Q, qc = q / (Q * Q);
-        const float N = sS[qa][a] * sS[qb][b] * sS[qc][c];
-        const float g[3] = {sD[qa][a] * sS[qb][b] * sS[qc][c] * m.inv_h, sS[qa][a] * sD[qb][b] * sS[qc][c] * m.inv_h,
-                            sS[qa][a] * sS[qb][b] * sD[qc][c] * m.inv_h};
-        const float wr = qd[lc][0][q], wm = qd[lc][7][q];
+        const int qa = q % Q, qb = (q / Q) % Q, qcz = q / (Q * Q);
+        const float sa = sS[qa][a], sb = sS[qb][b], sc = sS[qcz][c];
+        const float N = sa * sb * sc;
+        const float g[3] = {sD[qa][a] * sb * sc * m.inv_h, sa * sD[qb][b] * sc * m.inv_h, sa * sb * sD[qcz][c] * m.inv_h};
         const float conv = qd[lc][1][q] * g[0] + qd[lc][2][q] * g[1] + qd[lc][3][q] * g[2];
         const float gg = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
         const float ng = qd[lc][8][q] * g[0] + qd[lc][9][q] * g[1] + qd[lc][10][q] * g[2];
-        for (int k = 0; k < 3; ++k) {
-            float v = wr * (m.c_mass * N * N + N * conv + (m.newton ? N * N * qd[lc][4 + k][q] : 0.f));
-            v += wm * (0.5f * (gg + g[k] * g[k]) - qd[lc][8 + k][q] * g[k] * ng);
-            dsum[k] += v;
-        }
+        const float wm = qd[lc][7][q], NN = N * N;
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            dsum[k] += qd[lc][0][q] * NN + N * conv + NN * qd[lc][4 + k][q] +
+                       wm * (0.5f * (gg + g[k] * g[k]) - qd[lc][8 + k][q] * g[k] * ng);
     }
     for (int k = 0; k < 3; ++k) atomicAdd(&diag[k * m.Nu + gidx], dsum[k]);
 }
@@ -127,12 +86,10 @@ int launch_diagonal(evap_mesh* h, cudaStream_t s) {
     const Basis<float> b = cast_basis<float>(h->b);
     if (m.P == 2) {
         constexpr int CB = 8;
-        k_diagonal<2, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 27, 0, s>>>(m, b, h->cell_code, h->table_index,
-                                                                                 h->table32, h->u32, h->diag32);
+        k_diagonal<2, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 27, 0, s>>>(m, b, h->qc, h->diag32);
     } else {
         constexpr int CB = 4;
-        k_diagonal<3, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 64, 0, s>>>(m, b, h->cell_code, h->table_index,
-                                                                                 h->table32, h->u32, h->diag32);
+        k_diagonal<3, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 64, 0, s>>>(m, b, h->qc, h->diag32);
     }
     EVAP_CHECK_LAUNCH("diagonal");
     k_diag_finish<<<blocks_for(N, 256), 256, 0, s>>>(m.M, m.Nu, m.faces, h->diag32, h->diag);
@@ -150,12 +107,10 @@ int launch_diagonal_into(evap_mesh* h, float* acc, double* out, cudaStream_t s) 
     const Basis<float> b = cast_basis<float>(h->b);
     if (m.P == 2) {
         constexpr int CB = 8;
-        k_diagonal<2, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 27, 0, s>>>(m, b, h->cell_code, h->table_index,
-                                                                                 h->table32, h->u32, acc);
+        k_diagonal<2, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 27, 0, s>>>(m, b, h->qc, acc);
     } else {
         constexpr int CB = 4;
-        k_diagonal<3, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 64, 0, s>>>(m, b, h->cell_code, h->table_index,
-                                                                                 h->table32, h->u32, acc);
+        k_diagonal<3, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 64, 0, s>>>(m, b, h->qc, acc);
     }
     EVAP_CHECK_LAUNCH("diagonal_into");
     k_diag_finish<<<blocks_for(N, 256), 256, 0, s>>>(m.M, m.Nu, m.faces, acc, out);
@@ -216,10 +171,32 @@ __device__ __forceinline__ double block_sum(double v) {
     return r;
 }
 
-// partial[i * RED_BLOCKS + block] = sum_k V_i[k] w[k] for i = blockIdx.y < nv; row nv (if present) = w . w
+// The block's partial sum s (valid in thread 0) of row `row` goes to partial[row * RED_BLOCKS + block]; the last
+// block of the row to arrive (atomic ticket after a memory fence; no block waits on another) sums the row's partials
+// in block order, writes out[row] and resets the ticket for the next reduction.
+__device__ __forceinline__ void row_finish(double s, double* partial, unsigned* cnt, int row, double* out) {
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        partial[row * RED_BLOCKS + blockIdx.x] = s;
+        __threadfence();
+        last = atomicAdd(&cnt[row], 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double v = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) v += __ldcg(&partial[row * RED_BLOCKS + b]);
+    v = block_sum(v);
+    if (threadIdx.x == 0) {
+        out[row] = v;
+        cnt[row] = 0u;
+    }
+}
+
+// out[i] = sum_k V_i[k] w[k] for i = blockIdx.y < nv; row nv (if present) = w . w
 template <typename T>
 __global__ void k_mdot(const T* __restrict__ V, int64_t ld, int nv, const T* __restrict__ w, int64_t N,
-                       double* __restrict__ partial) {
+                       double* __restrict__ partial, unsigned* cnt, double* out) {
     using VT = typename V2<T>::t;
     constexpr int W = V2<T>::w;
     const T* v = blockIdx.y < (unsigned)nv ? V + blockIdx.y * ld : w;
@@ -237,23 +214,15 @@ __global__ void k_mdot(const T* __restrict__ V, int64_t ld, int nv, const T* __r
     if (k < nvec) dot_vec(acc, v4[k], w4[k]);
     for (int64_t k = nvec * W + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += stride)
         acc.add(v[k], w[k]);
-    const double s = block_sum(acc.value());
-    if (threadIdx.x == 0) partial[blockIdx.y * RED_BLOCKS + blockIdx.x] = s;
+    row_finish(block_sum(acc.value()), partial, cnt, blockIdx.y, out);
 }
 
-// out[i] (+)= sum_b partial[i * RED_BLOCKS + b]
-__global__ void k_reduce_rows(const double* __restrict__ partial, double* out, int accumulate) {
-    double s = 0.0;
-    for (int b = threadIdx.x; b < RED_BLOCKS; b += blockDim.x) s += partial[blockIdx.x * RED_BLOCKS + b];
-    s = block_sum(s);
-    if (threadIdx.x == 0) out[blockIdx.x] = accumulate ? out[blockIdx.x] + s : s;
-}
-
-// w -= sum_{i<nv} h[i] sc2[i] V_i ; partial |w|^2 of the result.  The basis is stored unnormalized: v_i = sc_i V_i,
-// so projecting out v_i takes the raw dot h[i] = V_i . w times sc_i^2.
+// w -= sum_{i<nv} h[i] sc2[i] V_i ; out[0] = |w|^2 of the result.  The basis is stored unnormalized:
+// v_i = sc_i V_i, so projecting out v_i takes the raw dot h[i] = V_i . w times sc_i^2.
 template <typename T>
 __global__ void k_maxpy_norm(const T* __restrict__ V, int64_t ld, const double* __restrict__ hcol,
-                             const double* __restrict__ sc2, int nv, T* w, int64_t N, double* __restrict__ partial) {
+                             const double* __restrict__ sc2, int nv, T* w, int64_t N, double* __restrict__ partial,
+                             unsigned* cnt, double* out) {
     using VT = typename V2<T>::t;
     constexpr int W = V2<T>::w;
     __shared__ T hs[256];
@@ -302,17 +271,17 @@ __global__ void k_maxpy_norm(const T* __restrict__ V, int64_t ld, const double* 
         w[k] = v;
         acc.add(v, v);
     }
-    const double s = block_sum(acc.value());
-    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+    row_finish(block_sum(acc.value()), partial, cnt, 0, out);
 }
 
+// out[0] = |v|^2
 template <typename T>
-__global__ void k_norm2(const T* __restrict__ v, int64_t N, double* __restrict__ partial) {
+__global__ void k_norm2(const T* __restrict__ v, int64_t N, double* __restrict__ partial, unsigned* cnt,
+                        double* out) {
     Acc acc;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x)
         acc.add(v[k], v[k]);
-    const double s = block_sum(acc.value());
-    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+    row_finish(block_sum(acc.value()), partial, cnt, 0, out);
 }
 
 // z = sc v / diag (right Jacobi preconditioner applied to the normalized basis vector sc v), and w initialized for
@@ -385,6 +354,7 @@ struct Ctx {
     cudaStream_t s;
     int64_t N, ld;
     double* partial;   // [(m+2) * RED_BLOCKS]
+    unsigned* cnt;     // arrival tickets of the reductions [m+2], zero between kernels
     double* dcol;      // device columns [2 (m+2)]
     double* dnorm;     // device scalars [4]
     double* dsc2;      // device squared scales of the unnormalized basis vectors [m+2]
@@ -399,10 +369,8 @@ static int apply_op(Ctx& c, const T* x, T* y) {
 
 template <typename T>
 static int norm2_dev(Ctx& c, const T* v, double* out) {
-    k_norm2<T><<<RED_BLOCKS, RED_THREADS, 0, c.s>>>(v, c.N, c.partial);
+    k_norm2<T><<<RED_BLOCKS, RED_THREADS, 0, c.s>>>(v, c.N, c.partial, c.cnt, out);
     EVAP_CHECK_LAUNCH("norm");
-    k_reduce_rows<<<1, RED_THREADS, 0, c.s>>>(c.partial, out, 0);
-    EVAP_CHECK_LAUNCH("norm_reduce");
     return EVAP_OK;
 }
 
@@ -417,14 +385,11 @@ static int fetch(Ctx& c, const double* dev, int n, double* host) {
 template <typename T>
 static int cgs_pass(Ctx& c, const T* V, T* w, int nv, double* h_out, bool with_pre) {
     const int rows = nv + (with_pre ? 1 : 0);
-    k_mdot<T><<<dim3(RED_BLOCKS, rows), RED_THREADS, 0, c.s>>>(V, c.ld, nv, w, c.N, c.partial);
+    k_mdot<T><<<dim3(RED_BLOCKS, rows), RED_THREADS, 0, c.s>>>(V, c.ld, nv, w, c.N, c.partial, c.cnt, h_out);
     EVAP_CHECK_LAUNCH("mdot");
-    k_reduce_rows<<<rows, RED_THREADS, 0, c.s>>>(c.partial, h_out, 0);
-    EVAP_CHECK_LAUNCH("mdot_reduce");
-    k_maxpy_norm<T><<<RED_BLOCKS, RED_THREADS, 0, c.s>>>(V, c.ld, h_out, c.dsc2, nv, w, c.N, c.partial);
+    k_maxpy_norm<T><<<RED_BLOCKS, RED_THREADS, 0, c.s>>>(V, c.ld, h_out, c.dsc2, nv, w, c.N, c.partial, c.cnt,
+                                                          c.dnorm);
     EVAP_CHECK_LAUNCH("maxpy");
-    k_reduce_rows<<<1, RED_THREADS, 0, c.s>>>(c.partial, c.dnorm, 0);
-    EVAP_CHECK_LAUNCH("norm_reduce");
     return EVAP_OK;
 }
 
@@ -563,7 +528,7 @@ int solve_gmres(evap_mesh* h, const double* f, double* x, int mixed, int m, doub
         EVAP_CUDA(cudaMalloc(&h->ws, bytes));
         h->ws_bytes = bytes;
     }
-    const size_t red_need = (size_t)(m + 2) * RED_BLOCKS + 3 * (m + 2) + 8;
+    const size_t red_need = (size_t)(m + 2) * RED_BLOCKS + 4 * (m + 2) + 8;
     if (h->red_len < red_need) {
         if (h->red) cudaFree(h->red);
         if (h->red_host) cudaFreeHost(h->red_host);
@@ -583,6 +548,8 @@ int solve_gmres(evap_mesh* h, const double* f, double* x, int mixed, int m, doub
     c.dcol = h->red + (size_t)(m + 2) * RED_BLOCKS;
     c.dnorm = c.dcol + 2 * (m + 2);
     c.dsc2 = c.dnorm + 8;
+    c.cnt = reinterpret_cast<unsigned*>(c.dsc2 + (m + 2));
+    EVAP_CUDA(cudaMemsetAsync(c.cnt, 0, (size_t)(m + 2) * sizeof(unsigned), s));
     c.hcol = h->red_host;
     c.hsc2 = h->red_host + red_need - (m + 2);
     const int G = blocks_for(N, 256);

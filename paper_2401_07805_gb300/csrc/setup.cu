@@ -228,7 +228,7 @@ __device__ __forceinline__ double dist3(const double a[3], const double b[3]) {
 // outer iterations ran without a stop.
 struct CppLane {
     int b = -1;  // band entry, -1 none
-    int phase = 0, steps = 0, k = 0, bt = 0;
+    int phase = 0, steps = 0, k = 0, bt = 0, trips = 0;
     double x[3], y[3], yn[3], tp[3];
     double dist = 0.0, dist_prev = 0.0, omega = 1.0;
 };
@@ -328,7 +328,8 @@ __global__ void k_transport_direct(PointEval e, const double* __restrict__ mdot,
 // y of band entry b to band_y[3 b], the convergence flag to flags[node].  band_count[1] hands out the entries.
 __global__ void __launch_bounds__(32) k_transport_band(PointEval e, double tol, int kmax, const int32_t* __restrict__ band,
                                                        int32_t* band_count, double* __restrict__ band_y,
-                                                       int32_t* __restrict__ flags, unsigned long long* flag_count) {
+                                                       int32_t* __restrict__ flags, unsigned long long* flag_count,
+                                                       unsigned long long* evals) {
     const MeshArgs<double>& m = e.m;
     const int count = band_count[0];
     const int m1 = m.n + 1;
@@ -348,6 +349,7 @@ __global__ void __launch_bounds__(32) k_transport_band(PointEval e, double tol, 
         L.y[0] = L.x[0]; L.y[1] = L.x[1]; L.y[2] = L.x[2];
         L.phase = 0;
         L.steps = 0;
+        L.trips = 0;
     };
     auto finish = [&](bool converged) {
         band_y[3 * (int64_t)L.b + 0] = L.y[0];
@@ -355,12 +357,14 @@ __global__ void __launch_bounds__(32) k_transport_band(PointEval e, double tol, 
         band_y[3 * (int64_t)L.b + 2] = L.y[2];
         flags[band[L.b]] = converged ? 0 : 1;
         if (!converged) atomicAdd(flag_count, 1ULL);
+        atomicAdd(evals, (unsigned long long)L.trips);
         take();
     };
     take();
     const double c_step = 1.0 / (2.0 * eps * h);  // step (cell units) = r / (|grad d| h), |grad d| = 2 eps |g| / (1 - ph^2)
     while (__any_sync(0xffffffffu, L.b >= 0)) {
         if (L.b < 0) continue;
+        ++L.trips;
         // the trip's point evaluation and the quantities every phase needs (computed by all lanes alike)
         const bool trial = L.phase == 2;
         double p[3];
@@ -471,6 +475,7 @@ int launch_transport_velocity(evap_mesh* h, cudaStream_t s) {
     }
     EVAP_CUDA(cudaMemsetAsync(h->flag_count, 0, sizeof(unsigned long long), s));
     EVAP_CUDA(cudaMemsetAsync(h->band_count, 0, 2 * sizeof(int32_t), s));
+    EVAP_CUDA(cudaMemsetAsync(h->cpp_evals, 0, sizeof(unsigned long long), s));
     k_transport_direct<<<blocks_for(h->m.Nphi, 128, 1LL << 40), 128, 0, s>>>(e, h->mdot, h->ugamma, h->cpp_flags,
                                                                             h->band_list, h->band_count);
     EVAP_CHECK_LAUNCH("transport_direct");
@@ -482,7 +487,7 @@ int launch_transport_velocity(evap_mesh* h, cudaStream_t s) {
         EVAP_CUDA(cudaStreamSynchronize(s));
         const int grid = (int)std::min<int64_t>(std::max<int64_t>(((int64_t)count + 127) / 128, 1), 152 * 8);
         k_transport_band<<<grid, 32, 0, s>>>(e, h->prm.cpp_tol, h->prm.cpp_kmax, h->band_list, h->band_count,
-                                             h->band_y, h->cpp_flags, h->flag_count);
+                                             h->band_y, h->cpp_flags, h->flag_count, h->cpp_evals);
         EVAP_CHECK_LAUNCH("transport_band");
         k_transport_band_finish<<<blocks_for(h->m.Nphi, 128, 152 * 16), 128, 0, s>>>(e, h->mdot, h->band_list,
                                                                                       h->band_count, h->band_y,
