@@ -1,0 +1,132 @@
+"""Pins of the oracle's level-set geometry sub-solver (projected normal, regularized curvature, reinitialization;
+Eqs. normal_vector_regularized, curvature, curvature_regularized, reinitialization; Algorithm 2 steps 2-3) against
+closed forms and invariants.  CPU only."""
+import numpy as np
+import pytest
+
+from oracle import fe, geometry, levelset
+
+pytestmark = pytest.mark.filterwarnings("ignore::scipy.sparse.SparseEfficiencyWarning")
+
+
+def q1_nodes(mesh):
+    r = np.arange(mesh.n + 1) * mesh.h
+    Z, Y, X = np.meshgrid(r, r, r, indexing="ij")
+    return X.ravel(), Y.ravel(), Z.ravel()
+
+
+def test_helmholtz_exact_integrals():
+    """1^T A 1 = |Omega| (K annihilates constants); for x = z: x^T M x = 1/3 and x^T K x = 1 exactly (Q1 products
+    are integrated exactly by the 2-point Gauss rule)."""
+    mesh = fe.Mesh(5, 1, 1.0)
+    c = 0.37
+    A = geometry.helmholtz_matrix(mesh, c)
+    one = np.ones(mesh.n_phi)
+    assert one @ (A @ one) == pytest.approx(1.0, rel=1e-13)
+    assert np.abs(A @ one - geometry.helmholtz_matrix(mesh, 0.0) @ one).max() < 1e-14
+    _, _, z = q1_nodes(mesh)
+    assert z @ (A @ z) == pytest.approx(1.0 / 3.0 + c, rel=1e-13)
+
+
+def test_projected_normal_of_a_uniform_unit_normal_is_exact():
+    """phi = 0.1 (z - 1/2): nbar = e_z at every point, and since A 1 = M 1 the projection returns e_z exactly."""
+    mesh = fe.Mesh(6, 1, 1.0)
+    _, _, z = q1_nodes(mesh)
+    n = geometry.projected_normal(mesh, 0.1 * (z - 0.5))
+    assert np.abs(n[0]).max() < 1e-15 and np.abs(n[1]).max() < 1e-15
+    assert np.abs(n[2] - 1.0).max() < 1e-13
+    kappa = geometry.curvature(mesh, n)
+    assert np.abs(kappa).max() < 1e-12
+
+
+def test_projected_normal_of_a_slab_points_into_the_liquid():
+    """Liquid below z = 1/2 (phi > 0): n = -e_z at the interface; the x, y components vanish to rounding (phi is
+    constant in x and y, so their right-hand sides cancel pairwise) and kappa = 0 at the interface plane."""
+    n_cells = 16
+    mesh = fe.Mesh(n_cells, 1, 1.0)
+    eps = mesh.h
+    _, _, z = q1_nodes(mesh)
+    phi = np.tanh((0.5 - z) / (2 * eps))
+    n = geometry.projected_normal(mesh, phi)
+    assert np.abs(n[0]).max() < 1e-13 and np.abs(n[1]).max() < 1e-13
+    plane = np.abs(z - 0.5) < 1e-12
+    assert np.abs(n[2][plane] + 1.0).max() < 1e-3
+    kappa = geometry.curvature(mesh, n)
+    assert np.abs(kappa[plane]).max() < 1e-2
+
+
+@pytest.mark.parametrize("shape,expected", [("sphere", 2.0), ("cylinder", 1.0)])
+def test_curvature_of_sphere_and_cylinder(shape, expected):
+    """kappa = -div n with n pointing into the liquid drop: 2/R for a sphere, 1/R for a cylinder, at the interface
+    (discretization-limited, about first order in h: within 3 % / 10 % on 24^3 with R = 0.3, eps = h, and within
+    5 % on 32^3; a sign, factor or divergence mistake is off by 100 % or more)."""
+    mesh = fe.Mesh(24, 1, 1.0)
+    eps = mesh.h
+    R = 0.3
+    x, y, z = q1_nodes(mesh)
+    r = np.sqrt((x - 0.5) ** 2 + (y - 0.5) ** 2 + ((z - 0.5) ** 2 if shape == "sphere" else 0.0))
+    phi = np.tanh((R - r) / (2 * eps))
+    n = geometry.projected_normal(mesh, phi)
+    kappa = geometry.curvature(mesh, n)
+    band = np.abs(r - R) < 0.5 * mesh.h
+    assert band.sum() > 20
+    assert np.median(kappa[band]) == pytest.approx(expected / R, rel=0.12)
+
+
+def test_directional_stiffness_with_a_uniform_nodal_normal():
+    """With the frozen normal e_z everywhere, x^T K_n x = int (d_z x)^2: 1 for x = z, 0 for x = x-coordinate."""
+    mesh = fe.Mesh(4, 1, 1.0)
+    nf = np.zeros((3, mesh.n_phi))
+    nf[2] = 0.7  # normalized at the points
+    eps, dtau = 1.0, 1.0
+    A = geometry.reinit_matrix(mesh, None, nf, eps, dtau)
+    M = geometry.helmholtz_matrix(mesh, 0.0)
+    x, _, z = q1_nodes(mesh)
+    assert z @ ((A - M) @ z) == pytest.approx(1.0, rel=1e-13)
+    assert abs(x @ ((A - M) @ x)) < 1e-14
+
+
+def test_reinitialization_conserves_the_integral():
+    """Testing the step with w = 1: the diffusive and compressive fluxes drop out, so int psi is conserved to
+    rounding through every pseudo-time step."""
+    mesh = fe.Mesh(12, 1, 1.0)
+    eps = mesh.h
+    x, y, z = q1_nodes(mesh)
+    r = np.sqrt((x - 0.45) ** 2 + (y - 0.5) ** 2 + (z - 0.55) ** 2)
+    phi = np.tanh((0.3 - r) / (3 * eps))  # a too-wide profile: reinitialization sharpens it
+    n = geometry.projected_normal(mesh, phi)
+    M = geometry.helmholtz_matrix(mesh, 0.0)
+    one = np.ones(mesh.n_phi)
+    psi, change = geometry.reinitialize(mesh, phi, n, eps, min(eps, 1e-4), 5)
+    assert abs(one @ (M @ psi) - one @ (M @ phi)) < 1e-12 * abs(one @ (M @ phi)) + 1e-15
+    assert change > 0.0
+
+
+def test_reinitialization_sharpens_a_wide_slab_profile():
+    """A slab profile twice as wide as the equilibrium tanh(d / (2 eps)) moves towards it: after the pseudo-time
+    steps the error against the equilibrium profile is smaller than at the start."""
+    mesh = fe.Mesh(24, 1, 1.0)
+    eps = 2 * mesh.h
+    _, _, z = q1_nodes(mesh)
+    d = 0.5 - z
+    phi = np.tanh(d / (4 * eps))
+    target = np.tanh(d / (2 * eps))
+    n = geometry.projected_normal(mesh, phi)
+    psi, _ = geometry.reinitialize(mesh, phi, n, eps, eps, 40)
+    assert np.linalg.norm(psi - target) < 0.5 * np.linalg.norm(phi - target)
+
+
+def test_reinit_with_the_unit_normal_matches_the_level_set_operators():
+    """Without a nodal field the frozen normal is grad phi / |grad phi| at the point, i.e. the REINIT / REINIT_RHS
+    operators of oracle.levelset (independent assembly of the same weak forms)."""
+    mesh = fe.Mesh(5, 1, 1.0)
+    rng = np.random.default_rng(3)
+    phi = np.tanh(rng.uniform(-2, 2, mesh.n_phi))
+    psi = rng.uniform(-1, 1, mesh.n_phi)
+    eps, dtau = 0.2, 0.05
+    A1 = geometry.reinit_matrix(mesh, phi, None, eps, dtau)
+    A2 = levelset.reinit_matrix(mesh, phi, eps, dtau)
+    assert abs(A1 - A2).max() < 1e-13 * abs(A2).max()
+    r1 = geometry.reinit_rhs(mesh, phi, None, psi, dtau)
+    r2 = levelset.reinit_rhs(mesh, phi, psi, dtau)
+    assert np.abs(r1 - r2).max() < 1e-13 * np.abs(r2).max()
