@@ -75,6 +75,8 @@ typedef struct {
     unsigned dirichlet_faces; /* homogeneous velocity Dirichlet faces, bit 2a: x_a = 0, bit 2a+1: x_a = L */
     double cpp_tol;        /* closest-point tolerance in cell units (App. C) */
     int cpp_kmax;          /* closest-point outer iteration cap (App. C) */
+    double eta_n;          /* normal filter constant, Eq. (normal_vector_regularized): radius eta_n h^2 (default 2) */
+    double eta_kappa;      /* curvature filter constant, Eq. (curvature_regularized) (default 2) */
 } evap_params;
 
 /* Create the mesh/operator object.  n_cells >= 1, degree_u in {2, 3}, L > 0, prm not NULL with rho_l, rho_g,
@@ -125,6 +127,32 @@ int evap_apply_momentum(evap_handle h, int prec, const void* x, void* y, void* y
 /* Level-set apply y = A x on Q1 for the given mode (evap_levelset_mode); x, y [N_phi]; prec 64 or 32.
  * The normal n is grad phi / |grad phi| of the level set of evap_set_fields. */
 int evap_apply_levelset(evap_handle h, int mode, int prec, const void* x, void* y, void* stream);
+
+/* ---- level-set geometry sub-solver (steps 2 and 3 of Algorithm 2), FP64, homogeneous Neumann conditions ----
+ * Each linear system is solved by conjugate gradients with the diagonal preconditioner to
+ * |r| <= max(1e-12 |r_0|, 1e-20) (cap 1000 iterations; EVAP_ENOTCONV if not reached, results still written).
+ * iters (total CG iterations) and relres (largest final |r|/|r_0|) are host pointers and may be NULL; these calls
+ * synchronize the stream every few iterations. */
+
+/* Projected normal n [3 N_phi] (component-major) of the level set of evap_set_fields, Eq. (normal_vector_regularized):
+ * (M + eta_n h^2 K) n_c = (N_i, nbar_c), nbar = grad phi / |grad phi| at the point (Eq. normal_vector; zero where
+ * |grad phi| h <= 1e-4). */
+int evap_projected_normal(evap_handle h, double* n, int* iters, double* relres, void* stream);
+
+/* Regularized curvature kappa [N_phi] of the Q1 normal field n [3 N_phi], Eqs. (curvature), (curvature_regularized):
+ * (M + eta_kappa h^2 K) kappa = -(N_i, div n_h). */
+int evap_curvature(evap_handle h, const double* n, double* kappa, int* iters, double* relres, void* stream);
+
+/* Frozen normal of the reinitialization operators (EVAP_REINIT, EVAP_REINIT_RHS and evap_reinitialize): the nodal
+ * field n [3 N_phi] (copied; normalized at each quadrature point, zero where |n_h| <= 1e-4), e.g. the projected
+ * normal; n = NULL restores the unit normal grad phi / |grad phi| of the level set. */
+int evap_set_levelset_normal(evap_handle h, const double* n, void* stream);
+
+/* Reinitialization, Eq. (reinitialization) (Algorithm 2, step 2): psi [N_phi] holds psi^0 on entry and psi^steps on
+ * return after `steps` semi-implicit pseudo-time steps (M/dtau + eps K_n) psi^(k+1) = M psi^k/dtau +
+ * (grad N_i . n, (1 - (psi^k)^2)/2), n the frozen normal.  last_change (host, may be NULL) = |psi^steps -
+ * psi^(steps-1)|_2. */
+int evap_reinitialize(evap_handle h, double* psi, int steps, int* iters, double* last_change, void* stream);
 
 /* Adjoint of the momentum apply for L = w . A(phi, mdot, u) x + w_p . (B x - g(phi, mdot)):
  *   g_x = A^T w + B^T w_p,  g_u0 = dL/du [3 N_u],  g_phi = dL/dphi [N_phi],  g_mdot = dL/dmdot [N_phi],

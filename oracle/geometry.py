@@ -122,12 +122,13 @@ def reinit_rhs(mesh: fe.Mesh, phi, n_field, psi0: np.ndarray, dtau: float) -> np
     return r
 
 
-def reinitialize(mesh: fe.Mesh, phi: np.ndarray, n_field, eps: float, dtau: float, steps: int):
-    """psi^0 = phi, then `steps` semi-implicit pseudo-time steps (Algorithm 2, step 2) with the normal frozen at
-    tau = 0.  Returns (psi, |psi^steps - psi^(steps-1)|_2)."""
+def reinitialize(mesh: fe.Mesh, phi: np.ndarray, n_field, eps: float, dtau: float, steps: int, psi0=None):
+    """psi^0 = phi (or psi0), then `steps` semi-implicit pseudo-time steps (Algorithm 2, step 2) with the normal
+    frozen at tau = 0 (the nodal field n_field, or the unit normal of phi).  Returns (psi, |psi^steps -
+    psi^(steps-1)|_2)."""
     A = reinit_matrix(mesh, phi, n_field, eps, dtau).tocsc()
     lu = spla.splu(A)
-    psi = np.array(phi, dtype=float)
+    psi = np.array(phi if psi0 is None else psi0, dtype=float)
     change = 0.0
     for _ in range(steps):
         new = lu.solve(reinit_rhs(mesh, phi, n_field, psi, dtau))

@@ -39,7 +39,7 @@ class EvapParams(ctypes.Structure):
     _fields_ = [("rho_l", _c_dbl), ("rho_g", _c_dbl), ("mu_l", _c_dbl), ("mu_g", _c_dbl), ("eps", _c_dbl),
                 ("dt", _c_dbl), ("c_mass", _c_dbl), ("theta", _c_dbl), ("dtau", _c_dbl), ("variant", _c_int),
                 ("stress", _c_int), ("corr_zone", _c_int), ("newton", _c_int), ("dirichlet_faces", ctypes.c_uint),
-                ("cpp_tol", _c_dbl), ("cpp_kmax", _c_int)]
+                ("cpp_tol", _c_dbl), ("cpp_kmax", _c_int), ("eta_n", _c_dbl), ("eta_kappa", _c_dbl)]
 
 
 SIGNATURES = {
@@ -52,6 +52,10 @@ SIGNATURES = {
     "evap_update_transport_velocity": (_c_int, [_vp, _vp]),
     "evap_transport_stats": (_c_int, [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                       ctypes.POINTER(ctypes.c_int64), _vp]),
+    "evap_projected_normal": (_c_int, [_vp, _vp, ctypes.POINTER(_c_int), ctypes.POINTER(_c_dbl), _vp]),
+    "evap_curvature": (_c_int, [_vp, _vp, _vp, ctypes.POINTER(_c_int), ctypes.POINTER(_c_dbl), _vp]),
+    "evap_set_levelset_normal": (_c_int, [_vp, _vp, _vp]),
+    "evap_reinitialize": (_c_int, [_vp, _vp, _c_int, ctypes.POINTER(_c_int), ctypes.POINTER(_c_dbl), _vp]),
     "evap_apply_momentum": (_c_int, [_vp, _c_int, _vp, _vp, _vp, _vp]),
     "evap_apply_levelset": (_c_int, [_vp, _c_int, _c_int, _vp, _vp, _vp]),
     "evap_apply_adjoint": (_c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
@@ -66,7 +70,7 @@ SIGNATURES = {
 
 DEFAULT_PARAMS = dict(rho_l=1000.0, rho_g=1.0, mu_l=1e-3, mu_g=1e-5, eps=None, dt=1e-4, c_mass=None, theta=0.5,
                       dtau=None, variant=2, stress=1, corr_zone=0, newton=1, dirichlet_faces=0x3F, cpp_tol=1e-10,
-                      cpp_kmax=20)
+                      cpp_kmax=20, eta_n=2.0, eta_kappa=2.0)
 
 
 def library_path() -> str:
@@ -205,6 +209,37 @@ class Operator:
         _check(lib().evap_transport_stats(self._h, ctypes.byref(b), ctypes.byref(e), ctypes.byref(f), _stream()),
                "evap_transport_stats")
         return dict(band_nodes=b.value, evaluations=e.value, flagged=f.value)
+
+    # ---------------------------------------------------------------------------- level-set geometry sub-solver
+    def projected_normal(self, raise_on_notconv: bool = False):
+        """Q1 projected normal [3 N_phi] of the current level set (Eq. normal_vector_regularized) and CG info."""
+        n = torch.empty(3 * self.n_phi, dtype=torch.float64, device=self.device)
+        its, rel = ctypes.c_int(), ctypes.c_double()
+        rc = lib().evap_projected_normal(self._h, _ptr(n), ctypes.byref(its), ctypes.byref(rel), _stream())
+        _check(rc, "evap_projected_normal", allow=() if raise_on_notconv else (-3,))
+        return n, dict(iters=its.value, relres=rel.value, converged=rc == 0)
+
+    def curvature(self, n: torch.Tensor, raise_on_notconv: bool = False):
+        """Regularized curvature [N_phi] of the Q1 normal field n (Eq. curvature_regularized) and CG info."""
+        n = self._dev(n, 3 * self.n_phi, torch.float64, "n")
+        kappa = torch.empty(self.n_phi, dtype=torch.float64, device=self.device)
+        its, rel = ctypes.c_int(), ctypes.c_double()
+        rc = lib().evap_curvature(self._h, _ptr(n), _ptr(kappa), ctypes.byref(its), ctypes.byref(rel), _stream())
+        _check(rc, "evap_curvature", allow=() if raise_on_notconv else (-3,))
+        return kappa, dict(iters=its.value, relres=rel.value, converged=rc == 0)
+
+    def set_levelset_normal(self, n: torch.Tensor | None):
+        """Frozen normal of the reinitialization operators: nodal field n [3 N_phi], or None for grad phi/|grad phi|."""
+        nn = None if n is None else self._dev(n, 3 * self.n_phi, torch.float64, "n")
+        _check(lib().evap_set_levelset_normal(self._h, _ptr(nn), _stream()), "evap_set_levelset_normal")
+
+    def reinitialize(self, psi: torch.Tensor, steps: int, raise_on_notconv: bool = False):
+        """`steps` reinitialization pseudo-time steps from psi (Eq. reinitialization); returns (psi, info)."""
+        out = self._dev(psi, self.n_phi, torch.float64, "psi").clone()
+        its, ch = ctypes.c_int(), ctypes.c_double()
+        rc = lib().evap_reinitialize(self._h, _ptr(out), int(steps), ctypes.byref(its), ctypes.byref(ch), _stream())
+        _check(rc, "evap_reinitialize", allow=() if raise_on_notconv else (-3,))
+        return out, dict(iters=its.value, last_change=ch.value, converged=rc == 0)
 
     def apply_momentum(self, x: torch.Tensor, prec: int = 64, with_divergence: bool = False, out=None, out_p=None):
         dt = torch.float64 if prec == 64 else torch.float32

@@ -112,11 +112,12 @@ static int fail(int code, const char* msg) {
 static void free_all(evap_mesh* h) {
     void* ptrs[] = {h->phi, h->u, h->mdot, h->u32, h->phi32, h->cell_code, h->table_index, h->table_count,
                     h->table, h->table32, h->qc, h->qc32, h->ugamma, h->ugamma32, h->cpp_flags, h->flag_count, h->band_list,
-                    h->band_count, h->band_y, h->cpp_evals, h->diag,
+                    h->band_count, h->band_y, h->cpp_evals, h->ls_normal_store, h->ls_normal32_store, h->geo_ws, h->diag,
                     h->diag32, h->ws, h->red};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->red_host) cudaFreeHost(h->red_host);
+    if (h->geo_host) cudaFreeHost(h->geo_host);
 }
 
 extern "C" {
@@ -148,6 +149,8 @@ int evap_create_mesh(int n_cells, int degree_u, double L, const evap_params* prm
     if (prm->variant < 1 || prm->variant > 3) return fail(EVAP_EINVAL, "evap_create_mesh: variant must be 1, 2 or 3");
     if (prm->cpp_kmax < 0 || !(prm->cpp_tol > 0.0))
         return fail(EVAP_EINVAL, "evap_create_mesh: cpp_tol must be > 0 and cpp_kmax >= 0");
+    if (!(prm->eta_n >= 0.0) || !(prm->eta_kappa >= 0.0))
+        return fail(EVAP_EINVAL, "evap_create_mesh: eta_n and eta_kappa must be >= 0");
     evap_mesh* h = new (std::nothrow) evap_mesh();
     if (!h) return fail(EVAP_ENOMEM, "evap_create_mesh: host allocation failed");
     cudaGetDevice(&h->device);
@@ -288,6 +291,44 @@ int evap_transport_stats(evap_handle h, int64_t* band_nodes, int64_t* evaluation
     if (evaluations) *evaluations = projected ? (int64_t)ev : 0;
     if (flagged) *flagged = (int64_t)fl;
     return EVAP_OK;
+}
+
+int evap_projected_normal(evap_handle h, double* n, int* iters, double* relres, void* stream) {
+    if (!h || !n) return fail(EVAP_EINVAL, "evap_projected_normal: null argument");
+    if (!h->has_fields) return fail(EVAP_ENOFIELDS, "evap_projected_normal: fields not set");
+    return geo_projected_normal(h, n, iters, relres, (cudaStream_t)stream);
+}
+
+int evap_curvature(evap_handle h, const double* n, double* kappa, int* iters, double* relres, void* stream) {
+    if (!h || !n || !kappa) return fail(EVAP_EINVAL, "evap_curvature: null argument");
+    if ((const void*)n == (const void*)kappa) return fail(EVAP_EINVAL, "evap_curvature: n and kappa must not alias");
+    return geo_curvature(h, n, kappa, iters, relres, (cudaStream_t)stream);
+}
+
+int evap_set_levelset_normal(evap_handle h, const double* n, void* stream) {
+    if (!h) return fail(EVAP_EINVAL, "evap_set_levelset_normal: null handle");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!n) {
+        h->ls_normal = nullptr;
+        h->ls_normal32 = nullptr;
+        return EVAP_OK;
+    }
+    const int64_t Np = h->m.Nphi;
+    if (!h->ls_normal_store) EVAP_CUDA(cudaMalloc(&h->ls_normal_store, 3 * Np * sizeof(double)));
+    if (!h->ls_normal32_store) EVAP_CUDA(cudaMalloc(&h->ls_normal32_store, 3 * Np * sizeof(float)));
+    EVAP_CUDA(cudaMemcpyAsync(h->ls_normal_store, n, 3 * Np * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    int rc = launch_to_float(h->ls_normal_store, h->ls_normal32_store, 3 * Np, s);
+    if (rc) return rc;
+    h->ls_normal = h->ls_normal_store;
+    h->ls_normal32 = h->ls_normal32_store;
+    return EVAP_OK;
+}
+
+int evap_reinitialize(evap_handle h, double* psi, int steps, int* iters, double* last_change, void* stream) {
+    if (!h || !psi) return fail(EVAP_EINVAL, "evap_reinitialize: null argument");
+    if (steps < 0) return fail(EVAP_EINVAL, "evap_reinitialize: steps must be >= 0");
+    if (!h->has_fields) return fail(EVAP_ENOFIELDS, "evap_reinitialize: call evap_set_fields first");
+    return geo_reinitialize(h, psi, steps, iters, last_change, (cudaStream_t)stream);
 }
 
 int evap_apply_momentum(evap_handle h, int prec, const void* x, void* y, void* y_p, void* stream) {

@@ -93,6 +93,14 @@ struct evap_mesh {
     int32_t* band_count = nullptr;  // [0] band nodes, [1] work counter of the closest-point pass
     double* band_y = nullptr;       // closest point (cell units) of band entry b at [3 b]
     unsigned long long* cpp_evals = nullptr;  // point evaluations of the last closest-point pass
+    // frozen normal of the reinitialization operators: nodal Q1 field [3][N_phi] (FP64 and FP32) or none
+    double* ls_normal = nullptr;
+    float* ls_normal32 = nullptr;
+    double* ls_normal_store = nullptr;  // owned storage behind ls_normal
+    float* ls_normal32_store = nullptr;
+    // geometry sub-solver workspace (first use) and its pinned scalars
+    void* geo_ws = nullptr;
+    double* geo_host = nullptr;
     // Jacobi diagonal and Krylov workspace (allocated by the first solve)
     double* diag = nullptr;
     float* diag32 = nullptr;
@@ -138,6 +146,10 @@ int launch_levelset(evap_mesh* h, int mode, const T* x, T* y, cudaStream_t s);
 int launch_adjoint(evap_mesh* h, const double* w, const double* wp, const double* x, double* gx, double* gu,
                    double* gphi, double* gm, cudaStream_t s);
 int launch_diagonal(evap_mesh* h, cudaStream_t s);
+int geo_helmholtz(evap_mesh* h, double c, int ncomp, const double* x, double* y, cudaStream_t s);
+int geo_projected_normal(evap_mesh* h, double* n, int* iters, double* relres, cudaStream_t s);
+int geo_curvature(evap_mesh* h, const double* nf, double* kappa, int* iters, double* relres, cudaStream_t s);
+int geo_reinitialize(evap_mesh* h, double* psi, int steps, int* iters, double* last_change, cudaStream_t s);
 int launch_diagonal_into(evap_mesh* h, float* acc, double* out, cudaStream_t s);
 int solve_gmres(evap_mesh* h, const double* f, double* x, int mixed, int restart, double rtol, int max_iter,
                 int* iters, double* relres, cudaStream_t s);

@@ -1,0 +1,509 @@
+// Level-set geometry sub-solver on the Q1 level-set space (steps 2 and 3 of Algorithm 2), FP64:
+//   projected normal   (M + eta_n h^2 K) n_c = (N_i, nbar_c),        nbar = grad phi / |grad phi|   Eq. normal_vector_regularized
+//   curvature          (M + eta_k h^2 K) kappa = -(N_i, div n_h)                                    Eq. curvature_regularized
+//   reinitialization   (M / dtau + eps K_n) psi^(k+1) = M psi^k / dtau + (grad N_i . n, (1 - psi_k^2)/2)   Eq. reinitialization
+// with homogeneous Neumann conditions, each system solved by conjugate gradients with the diagonal (Jacobi)
+// preconditioner to |r| <= max(1e-12 |r_0|, 1e-20) (the solver table of the paper).
+//
+// M + c K has constant coefficients on the uniform Cartesian mesh: M = Mx (x) My (x) Mz, K = Kx My Mz + Mx Ky Mz +
+// Mx My Kz with the 1D Q1 mass (h/6, 2h/3 or h/3 at an end, h/6) and stiffness (-1/h, 2/h or 1/h, -1/h) rows, which the
+// 2-point Gauss rule integrates exactly.  Its apply is therefore a 27-point stencil, evaluated per node by separable
+// sums (x, then y, then z: 93 FMA per node) instead of per-cell quadrature.
+#include <algorithm>
+#include <cmath>
+
+#include "physics.cuh"
+
+namespace evap {
+
+// 1D rows of node i in [0, n]: mass m[d] and stiffness k[d] for the neighbours d = -1, 0, +1 (cell edge h).
+__device__ __forceinline__ void q1_rows(int i, int n, double h, double ih, double m[3], double k[3]) {
+    const bool lo = i > 0, hi = i < n;
+    m[0] = lo ? h / 6.0 : 0.0;
+    m[2] = hi ? h / 6.0 : 0.0;
+    m[1] = (lo ? h / 3.0 : 0.0) + (hi ? h / 3.0 : 0.0);
+    k[0] = lo ? -ih : 0.0;
+    k[2] = hi ? -ih : 0.0;
+    k[1] = (lo ? ih : 0.0) + (hi ? ih : 0.0);
+}
+
+// y = (M + c K) x for ncomp component fields of N_phi entries each (component-major), one thread per node.
+__global__ void __launch_bounds__(256) k_helmholtz(int n, double h, double c, int ncomp, const double* __restrict__ x,
+                                                   double* __restrict__ y) {
+    const int m1 = n + 1;
+    const int64_t Np = (int64_t)m1 * m1 * m1;
+    const double ih = 1.0 / h;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < Np * ncomp; t += (int64_t)gridDim.x * blockDim.x) {
+        const int comp = (int)(t / Np);
+        const int64_t node = t - comp * Np;
+        const int i = (int)(node % m1), j = (int)((node / m1) % m1), kz = (int)(node / ((int64_t)m1 * m1));
+        double mx[3], kx[3], my[3], ky[3], mz[3], kzr[3];
+        q1_rows(i, n, h, ih, mx, kx);
+        q1_rows(j, n, h, ih, my, ky);
+        q1_rows(kz, n, h, ih, mz, kzr);
+        const double* xc = x + comp * Np;
+        double acc = 0.0;
+#pragma unroll
+        for (int dz = -1; dz <= 1; ++dz) {
+            if ((dz < 0 && kz == 0) || (dz > 0 && kz == n)) continue;
+            double smm = 0.0, skm = 0.0, smk = 0.0;  // sums over y of (m_y x-mass), (m_y x-stiff), (k_y x-mass)
+#pragma unroll
+            for (int dy = -1; dy <= 1; ++dy) {
+                if ((dy < 0 && j == 0) || (dy > 0 && j == n)) continue;
+                const double* row = xc + (i + (int64_t)m1 * ((j + dy) + (int64_t)m1 * (kz + dz)));
+                double sm = 0.0, sk = 0.0;
+#pragma unroll
+                for (int dx = -1; dx <= 1; ++dx) {
+                    if ((dx < 0 && i == 0) || (dx > 0 && i == n)) continue;
+                    const double v = row[dx];
+                    sm += mx[dx + 1] * v;
+                    sk += kx[dx + 1] * v;
+                }
+                smm += my[dy + 1] * sm;
+                skm += my[dy + 1] * sk;
+                smk += ky[dy + 1] * sm;
+            }
+            acc += mz[dz + 1] * (smm + c * (skm + smk)) + c * kzr[dz + 1] * smm;
+        }
+        y[t] = acc;
+    }
+}
+
+// Diagonal of M + c K (the same for every component).
+__global__ void k_helmholtz_diag(int n, double h, double c, double* __restrict__ d) {
+    const int m1 = n + 1;
+    const int64_t Np = (int64_t)m1 * m1 * m1;
+    const double ih = 1.0 / h;
+    for (int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; node < Np; node += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(node % m1), j = (int)((node / m1) % m1), kz = (int)(node / ((int64_t)m1 * m1));
+        double mx[3], kx[3], my[3], ky[3], mz[3], kzr[3];
+        q1_rows(i, n, h, ih, mx, kx);
+        q1_rows(j, n, h, ih, my, ky);
+        q1_rows(kz, n, h, ih, mz, kzr);
+        d[node] = mx[1] * my[1] * mz[1] + c * (kx[1] * my[1] * mz[1] + mx[1] * ky[1] * mz[1] + mx[1] * my[1] * kzr[1]);
+    }
+}
+
+// Q1 cell data at the 2^3 Gauss points: shape values N[q][j] and reference derivative signs.
+struct Q1Cell {
+    int64_t node[8];
+};
+
+__device__ __forceinline__ void q1_cell_nodes(int64_t cell, int n, Q1Cell& c, int& cx, int& cy, int& cz) {
+    const int64_t m1 = n + 1;
+    cx = (int)(cell % n);
+    cy = (int)((cell / n) % n);
+    cz = (int)(cell / ((int64_t)n * n));
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+        c.node[j] = (cx + (j & 1)) + m1 * ((cy + ((j >> 1) & 1)) + m1 * (cz + (j >> 2)));
+}
+
+// Value and physical gradient weights of node j at Gauss point q of the 2-point rule (t = g2t).
+__device__ __forceinline__ void q1_weights(const double* g2t, int q, double inv_h, double N[8], double G[8][3]) {
+    const double tx = g2t[q & 1], ty = g2t[(q >> 1) & 1], tz = g2t[q >> 2];
+    const double Nx[2] = {1.0 - tx, tx}, Ny[2] = {1.0 - ty, ty}, Nz[2] = {1.0 - tz, tz};
+    const double Dd[2] = {-inv_h, inv_h};
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int a = j & 1, b = (j >> 1) & 1, c = j >> 2;
+        N[j] = Nx[a] * Ny[b] * Nz[c];
+        G[j][0] = Dd[a] * Ny[b] * Nz[c];
+        G[j][1] = Nx[a] * Dd[b] * Nz[c];
+        G[j][2] = Nx[a] * Ny[b] * Dd[c];
+    }
+}
+
+// b[c * stride + i] += sum_q W N_i nbar_c, nbar the unit normal of phi at the point (zero where
+// |grad phi| h <= GRAD_TINY).
+__global__ void __launch_bounds__(128) k_normal_rhs(MeshArgs<double> m, Basis<double> bas, const double* __restrict__ phi,
+                                                    double* __restrict__ b, int64_t stride) {
+    const int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (cell >= m.ncell) return;
+    Q1Cell c;
+    int cx, cy, cz;
+    q1_cell_nodes(cell, m.n, c, cx, cy, cz);
+    double pv[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) pv[j] = phi[c.node[j]];
+    double out[3][8] = {};
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        double N[8], G[8][3];
+        q1_weights(bas.g2t, q, m.inv_h, N, G);
+        const double W = bas.g2w[q & 1] * bas.g2w[(q >> 1) & 1] * bas.g2w[q >> 2] * m.vol_w;
+        double g[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) g[d] += G[j][d] * pv[j];
+        const double gn = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+        if (!(gn * m.h > GRAD_TINY)) continue;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const double wn = W * g[d] / gn;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) out[d][j] += N[j] * wn;
+        }
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) atomicAdd(&b[d * stride + c.node[j]], out[d][j]);
+}
+
+// b[i] += -sum_q W N_i div n_h for the Q1 vector field nf [3][N_phi].
+__global__ void __launch_bounds__(128) k_curvature_rhs(MeshArgs<double> m, Basis<double> bas,
+                                                       const double* __restrict__ nf, double* __restrict__ b) {
+    const int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (cell >= m.ncell) return;
+    Q1Cell c;
+    int cx, cy, cz;
+    q1_cell_nodes(cell, m.n, c, cx, cy, cz);
+    double nv[3][8];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) nv[d][j] = nf[d * m.Nphi + c.node[j]];
+    double out[8] = {};
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        double N[8], G[8][3];
+        q1_weights(bas.g2t, q, m.inv_h, N, G);
+        const double W = bas.g2w[q & 1] * bas.g2w[(q >> 1) & 1] * bas.g2w[q >> 2] * m.vol_w;
+        double div = 0.0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) div += G[j][0] * nv[0][j] + G[j][1] * nv[1][j] + G[j][2] * nv[2][j];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) out[j] -= N[j] * W * div;
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) atomicAdd(&b[c.node[j]], out[j]);
+}
+
+// diag_i += sum_q W (N_i^2 / dtau + eps (grad N_i . n)^2), the diagonal of the reinitialization operator.
+__global__ void __launch_bounds__(128) k_reinit_diag(MeshArgs<double> m, Basis<double> bas, const double* __restrict__ phi,
+                                                     const double* __restrict__ nf, double* __restrict__ d) {
+    const int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (cell >= m.ncell) return;
+    Q1Cell c;
+    int cx, cy, cz;
+    q1_cell_nodes(cell, m.n, c, cx, cy, cz);
+    double pv[8], nloc[3][8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        pv[j] = phi[c.node[j]];
+#pragma unroll
+        for (int e = 0; e < 3; ++e) nloc[e][j] = nf ? nf[e * m.Nphi + c.node[j]] : 0.0;
+    }
+    double out[8] = {};
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        double N[8], G[8][3], nv[3];
+        q1_weights(bas.g2t, q, m.inv_h, N, G);
+        const double W = bas.g2w[q & 1] * bas.g2w[(q >> 1) & 1] * bas.g2w[q >> 2] * m.vol_w;
+        ls_frozen_normal<double>(nf ? nloc : nullptr, pv, N, G, m.h, nv);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const double gn = G[j][0] * nv[0] + G[j][1] * nv[1] + G[j][2] * nv[2];
+            out[j] += W * (N[j] * N[j] / m.dtau + m.eps * gn * gn);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) atomicAdd(&d[c.node[j]], out[j]);
+}
+
+// ------------------------------------------------------------------------------- conjugate gradients (FP64)
+// Scalars on the device: S[0] r.z, S[1] p.q, S[2] r.r, S[3] r0.r0, S[4] beta.  Every reduction is finished by
+// the last block to arrive (memory fence + atomic ticket; no block waits on another), so an iteration needs no
+// host round trip; the host reads |r| every CG_CHECK iterations.
+constexpr int CG_THREADS = 256;
+constexpr int CG_BLOCKS = 304;
+constexpr int CG_CHECK = 8;
+
+__device__ __forceinline__ double cg_block_sum(double v) {
+    __shared__ double sh[CG_THREADS / 32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < CG_THREADS / 32; ++i) r += sh[i];
+    return r;
+}
+
+// Two block partials (valid in thread 0) to part[2][CG_BLOCKS]; returns true in the last block to arrive, whose
+// threads then see the totals in tot[0..1].
+__device__ __forceinline__ bool cg_finish2(double a, double b, double* part, unsigned* ticket, double tot[2]) {
+    __shared__ bool last;
+    __shared__ double sums[2];
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = a;
+        part[CG_BLOCKS + blockIdx.x] = b;
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    double va = 0.0, vb = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+        va += __ldcg(&part[i]);
+        vb += __ldcg(&part[CG_BLOCKS + i]);
+    }
+    va = cg_block_sum(va);
+    vb = cg_block_sum(vb);
+    if (threadIdx.x == 0) {
+        sums[0] = va;
+        sums[1] = vb;
+        *ticket = 0u;
+    }
+    __syncthreads();
+    tot[0] = sums[0];
+    tot[1] = sums[1];
+    return true;
+}
+
+// x = 0, r = b, z = r / diag, p = z; S0 = r.z, S2 = S3 = r.r
+__global__ void __launch_bounds__(CG_THREADS) k_cg_start(const double* __restrict__ b, const double* __restrict__ dg,
+                                                         double* x, double* r, double* z, double* p, int64_t N,
+                                                         double* part, unsigned* ticket, double* S) {
+    double rz = 0.0, rr = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const double ri = b[i], zi = ri / dg[i];
+        x[i] = 0.0;
+        r[i] = ri;
+        z[i] = zi;
+        p[i] = zi;
+        rz += ri * zi;
+        rr += ri * ri;
+    }
+    double tot[2];
+    if (cg_finish2(cg_block_sum(rz), cg_block_sum(rr), part, ticket, tot) && threadIdx.x == 0) {
+        S[0] = tot[0];
+        S[2] = tot[1];
+        S[3] = tot[1];
+    }
+}
+
+// S1 = p.q
+__global__ void __launch_bounds__(CG_THREADS) k_cg_pq(const double* __restrict__ p, const double* __restrict__ q,
+                                                      int64_t N, double* part, unsigned* ticket, double* S) {
+    double s = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        s += p[i] * q[i];
+    double tot[2];
+    if (cg_finish2(cg_block_sum(s), 0.0, part, ticket, tot) && threadIdx.x == 0) S[1] = tot[0];
+}
+
+// alpha = S0 / S1; x += alpha p; r -= alpha q; z = r / diag; then beta = (r.z)_new / S0, S0 = (r.z)_new, S2 = r.r
+__global__ void __launch_bounds__(CG_THREADS) k_cg_update(double* x, double* r, const double* __restrict__ p,
+                                                          const double* __restrict__ q, const double* __restrict__ dg,
+                                                          double* z, int64_t N, double* part, unsigned* ticket,
+                                                          double* S) {
+    const double pq = S[1];
+    const double alpha = pq != 0.0 ? S[0] / pq : 0.0;
+    double rz = 0.0, rr = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        x[i] += alpha * p[i];
+        const double ri = r[i] - alpha * q[i];
+        const double zi = ri / dg[i];
+        r[i] = ri;
+        z[i] = zi;
+        rz += ri * zi;
+        rr += ri * ri;
+    }
+    double tot[2];
+    if (cg_finish2(cg_block_sum(rz), cg_block_sum(rr), part, ticket, tot) && threadIdx.x == 0) {
+        const double old = S[0];
+        S[4] = old != 0.0 ? tot[0] / old : 0.0;
+        S[0] = tot[0];
+        S[2] = tot[1];
+    }
+}
+
+// p = z + beta p
+__global__ void k_cg_dir(double* p, const double* __restrict__ z, int64_t N, const double* __restrict__ S) {
+    const double beta = S[4];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = z[i] + beta * p[i];
+}
+
+// *out = |a - b|^2
+__global__ void __launch_bounds__(CG_THREADS) k_diff_norm(const double* __restrict__ a, const double* __restrict__ b,
+                                                          int64_t N, double* part, unsigned* ticket, double* out) {
+    double s = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const double d = a[i] - b[i];
+        s += d * d;
+    }
+    double tot[2];
+    if (cg_finish2(cg_block_sum(s), 0.0, part, ticket, tot) && threadIdx.x == 0) *out = tot[0];
+}
+
+// Workspace: r, z, p, q [N_phi] + partials + scalars + ticket (allocated once per mesh).
+static int geo_workspace(evap_mesh* h) {
+    if (h->geo_ws) return EVAP_OK;
+    const int64_t Np = h->m.Nphi;
+    const size_t vec = ((size_t)Np * sizeof(double) + 255) & ~(size_t)255;
+    const size_t bytes = 9 * vec + (2 * CG_BLOCKS + 8) * sizeof(double) + 256;
+    EVAP_CUDA(cudaMalloc(&h->geo_ws, bytes));
+    EVAP_CUDA(cudaMemset(h->geo_ws, 0, bytes));
+    EVAP_CUDA(cudaMallocHost(&h->geo_host, 8 * sizeof(double)));
+    return EVAP_OK;
+}
+
+struct CgSpace {
+    double *r, *z, *p, *q, *b, *d, *t0, *t1, *t2, *part, *S;
+    unsigned* ticket;
+};
+
+static CgSpace cg_space(evap_mesh* h) {
+    const int64_t Np = h->m.Nphi;
+    const size_t vec = ((size_t)Np * sizeof(double) + 255) & ~(size_t)255;
+    char* base = (char*)h->geo_ws;
+    CgSpace w;
+    w.r = (double*)(base + 0 * vec);
+    w.z = (double*)(base + 1 * vec);
+    w.p = (double*)(base + 2 * vec);
+    w.q = (double*)(base + 3 * vec);
+    w.b = (double*)(base + 4 * vec);
+    w.d = (double*)(base + 5 * vec);
+    w.t0 = (double*)(base + 6 * vec);
+    w.t1 = (double*)(base + 7 * vec);
+    w.t2 = (double*)(base + 8 * vec);
+    w.part = (double*)(base + 9 * vec);
+    w.S = w.part + 2 * CG_BLOCKS;
+    w.ticket = (unsigned*)(w.S + 8);
+    return w;
+}
+
+// CG on A x = b (x0 = 0) with the Jacobi diagonal d; apply(p, q) computes q = A p.  Stops when
+// |r| <= max(rtol |r0|, atol), checked every CG_CHECK iterations, or after max_iter iterations.
+template <class Apply>
+static int cg_solve(evap_mesh* h, Apply apply, const double* b, const double* d, double* x, double rtol, double atol,
+                    int max_iter, int* iters, double* relres, cudaStream_t s) {
+    const int64_t N = h->m.Nphi;
+    CgSpace w = cg_space(h);
+    double* hs = h->geo_host;
+    k_cg_start<<<CG_BLOCKS, CG_THREADS, 0, s>>>(b, d, x, w.r, w.z, w.p, N, w.part, w.ticket, w.S);
+    EVAP_CHECK_LAUNCH("cg_start");
+    EVAP_CUDA(cudaMemcpyAsync(hs, w.S, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    EVAP_CUDA(cudaStreamSynchronize(s));
+    const double r0 = std::sqrt(hs[3]);
+    const double target = std::max(rtol * r0, atol);
+    double res = r0;
+    int it = 0;
+    const int G = blocks_for(N, 256, 152 * 8);
+    while (res > target && it < max_iter) {
+        for (int k = 0; k < CG_CHECK && it < max_iter; ++k, ++it) {
+            int rc = apply(w.p, w.q);
+            if (rc) return rc;
+            k_cg_pq<<<CG_BLOCKS, CG_THREADS, 0, s>>>(w.p, w.q, N, w.part, w.ticket, w.S);
+            EVAP_CHECK_LAUNCH("cg_pq");
+            k_cg_update<<<CG_BLOCKS, CG_THREADS, 0, s>>>(x, w.r, w.p, w.q, d, w.z, N, w.part, w.ticket, w.S);
+            EVAP_CHECK_LAUNCH("cg_update");
+            k_cg_dir<<<G, 256, 0, s>>>(w.p, w.z, N, w.S);
+            EVAP_CHECK_LAUNCH("cg_dir");
+        }
+        EVAP_CUDA(cudaMemcpyAsync(hs, w.S, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        EVAP_CUDA(cudaStreamSynchronize(s));
+        res = std::sqrt(hs[2]);
+    }
+    if (iters) *iters += it;
+    const double rel = r0 > 0.0 ? res / r0 : 0.0;
+    if (relres && rel > *relres) *relres = rel;
+    return res <= target ? EVAP_OK : EVAP_ENOTCONV;
+}
+
+static int helmholtz_apply(evap_mesh* h, double c, int ncomp, const double* x, double* y, cudaStream_t s) {
+    const int64_t total = h->m.Nphi * ncomp;
+    k_helmholtz<<<blocks_for(total, 256, 152 * 16), 256, 0, s>>>(h->m.n, h->m.h, c, ncomp, x, y);
+    EVAP_CHECK_LAUNCH("helmholtz");
+    return EVAP_OK;
+}
+
+int geo_helmholtz(evap_mesh* h, double c, int ncomp, const double* x, double* y, cudaStream_t s) {
+    return helmholtz_apply(h, c, ncomp, x, y, s);
+}
+
+int geo_projected_normal(evap_mesh* h, double* n, int* iters, double* relres, cudaStream_t s) {
+    int rc = geo_workspace(h);
+    if (rc) return rc;
+    CgSpace w = cg_space(h);
+    const int64_t Np = h->m.Nphi;
+    const int64_t stride = w.t1 - w.t0;  // right-hand sides of the three components in t0, t1, t2
+    const double c = h->prm.eta_n * h->m.h * h->m.h;
+    EVAP_CUDA(cudaMemsetAsync(w.t0, 0, 3 * stride * sizeof(double), s));
+    k_normal_rhs<<<blocks_for(h->m.ncell, 128, 1LL << 40), 128, 0, s>>>(h->m, h->b, h->phi, w.t0, stride);
+    EVAP_CHECK_LAUNCH("normal_rhs");
+    k_helmholtz_diag<<<blocks_for(Np, 256, 152 * 16), 256, 0, s>>>(h->m.n, h->m.h, c, w.d);
+    EVAP_CHECK_LAUNCH("helmholtz_diag");
+    if (iters) *iters = 0;
+    if (relres) *relres = 0.0;
+    int status = EVAP_OK;
+    auto apply = [&](const double* p, double* q) { return helmholtz_apply(h, c, 1, p, q, s); };
+    for (int d = 0; d < 3; ++d) {
+        rc = cg_solve(h, apply, w.t0 + d * stride, w.d, n + d * Np, 1e-12, 1e-20, 1000, iters, relres, s);
+        if (rc == EVAP_ENOTCONV) status = rc;
+        else if (rc) return rc;
+    }
+    return status;
+}
+
+int geo_curvature(evap_mesh* h, const double* nf, double* kappa, int* iters, double* relres, cudaStream_t s) {
+    int rc = geo_workspace(h);
+    if (rc) return rc;
+    CgSpace w = cg_space(h);
+    const int64_t Np = h->m.Nphi;
+    const double c = h->prm.eta_kappa * h->m.h * h->m.h;
+    EVAP_CUDA(cudaMemsetAsync(w.b, 0, Np * sizeof(double), s));
+    k_curvature_rhs<<<blocks_for(h->m.ncell, 128, 1LL << 40), 128, 0, s>>>(h->m, h->b, nf, w.b);
+    EVAP_CHECK_LAUNCH("curvature_rhs");
+    k_helmholtz_diag<<<blocks_for(Np, 256, 152 * 16), 256, 0, s>>>(h->m.n, h->m.h, c, w.d);
+    EVAP_CHECK_LAUNCH("helmholtz_diag");
+    if (iters) *iters = 0;
+    if (relres) *relres = 0.0;
+    auto apply = [&](const double* p, double* q) { return helmholtz_apply(h, c, 1, p, q, s); };
+    return cg_solve(h, apply, w.b, w.d, kappa, 1e-12, 1e-20, 1000, iters, relres, s);
+}
+
+// `steps` pseudo-time steps of the reinitialization with the frozen normal of the level-set operators.
+int geo_reinitialize(evap_mesh* h, double* psi, int steps, int* iters, double* last_change, cudaStream_t s) {
+    int rc = geo_workspace(h);
+    if (rc) return rc;
+    CgSpace w = cg_space(h);
+    const int64_t Np = h->m.Nphi;
+    EVAP_CUDA(cudaMemsetAsync(w.d, 0, Np * sizeof(double), s));
+    k_reinit_diag<<<blocks_for(h->m.ncell, 128, 1LL << 40), 128, 0, s>>>(h->m, h->b, h->phi, h->ls_normal, w.d);
+    EVAP_CHECK_LAUNCH("reinit_diag");
+    if (iters) *iters = 0;
+    double rel = 0.0;
+    int status = EVAP_OK;
+    auto apply = [&](const double* p, double* q) { return launch_levelset<double>(h, EVAP_REINIT, p, q, s); };
+    for (int k = 0; k < steps; ++k) {
+        rc = launch_levelset<double>(h, EVAP_REINIT_RHS, psi, w.b, s);
+        if (rc) return rc;
+        rc = cg_solve(h, apply, w.b, w.d, w.t0, 1e-12, 1e-20, 1000, iters, &rel, s);
+        if (rc == EVAP_ENOTCONV) status = rc;
+        else if (rc) return rc;
+        if (k == steps - 1 && last_change) {
+            k_diff_norm<<<CG_BLOCKS, CG_THREADS, 0, s>>>(w.t0, psi, Np, w.part, w.ticket, w.S + 5);
+            EVAP_CHECK_LAUNCH("reinit_change");
+        }
+        EVAP_CUDA(cudaMemcpyAsync(psi, w.t0, Np * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
+    if (last_change) {
+        *last_change = 0.0;
+        if (steps > 0) {
+            EVAP_CUDA(cudaMemcpyAsync(h->geo_host, w.S + 5, sizeof(double), cudaMemcpyDeviceToHost, s));
+            EVAP_CUDA(cudaStreamSynchronize(s));
+            *last_change = std::sqrt(h->geo_host[0]);
+        }
+    }
+    return status;
+}
+
+}  // namespace evap

@@ -2,14 +2,17 @@
 //   EVAP_ADVECT      y_i = sum_q W [ N_i x + theta dt N_i (u_Gamma . grad x) ]            Eq. (weakFormLevelSet), CN
 //   EVAP_REINIT      y_i = sum_q W [ N_i x / dtau + eps (grad N_i . n)(grad x . n) ]      Eq. (reinitialization)
 //   EVAP_REINIT_RHS  y_i = sum_q W [ N_i x / dtau + (grad N_i . n) (1 - x^2) / 2 ]        explicit compressive flux
-// with n = grad phi / |grad phi| of the level set at the quadrature point (Eq. normal_vector).
-#include "evap_internal.cuh"
+// with n the frozen normal at the quadrature point: grad phi / |grad phi| of the level set (Eq. normal_vector), or,
+// when a nodal normal field is set (e.g. the projected normal of Eq. normal_vector_regularized), its normalized
+// interpolant (ls_frozen_normal).
+#include "physics.cuh"
 
 namespace evap {
 
 template <typename T, int MODE>
 __global__ void __launch_bounds__(128) k_levelset(MeshArgs<T> m, Basis<T> bas, const T* __restrict__ phi,
-                                                  const T* __restrict__ ug, const T* __restrict__ x, T* __restrict__ y) {
+                                                  const T* __restrict__ nf, const T* __restrict__ ug,
+                                                  const T* __restrict__ x, T* __restrict__ y) {
     const int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (cell >= m.ncell) return;
     const int n = m.n;
@@ -24,6 +27,10 @@ __global__ void __launch_bounds__(128) k_levelset(MeshArgs<T> m, Basis<T> bas, c
         if (MODE == EVAP_ADVECT) {
 #pragma unroll
             for (int k = 0; k < 3; ++k) uv[k][j] = ug[k * m.Nphi + node[j]];
+        } else if (nf) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) uv[k][j] = nf[k * m.Nphi + node[j]];
+            pv[j] = T(0);
         } else {
             pv[j] = phi[node[j]];
         }
@@ -63,16 +70,8 @@ __global__ void __launch_bounds__(128) k_levelset(MeshArgs<T> m, Basis<T> bas, c
                 for (int k = 0; k < 3; ++k) U[k] += N[j] * uv[k][j];
             Fv = W * (X + m.theta * m.dt * (U[0] * GX[0] + U[1] * GX[1] + U[2] * GX[2]));
         } else {
-            T g[3] = {0, 0, 0};
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-#pragma unroll
-                for (int d = 0; d < 3; ++d) g[d] += dN[j][d] * pv[j];
-            const T gn = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
-            T nv[3] = {0, 0, 0};
-            if (gn * m.h > T(1e-4)) {  // normal taken as 0 where phi varies < 1e-4 across the cell (far field)
-                nv[0] = g[0] / gn; nv[1] = g[1] / gn; nv[2] = g[2] / gn;
-            }
+            T nv[3];
+            ls_frozen_normal<T>(nf ? uv : nullptr, pv, N, dN, m.h, nv);
             Fv = W * X / m.dtau;
             const T s = (MODE == EVAP_REINIT) ? W * m.eps * (GX[0] * nv[0] + GX[1] * nv[1] + GX[2] * nv[2])
                                               : W * T(0.5) * (T(1) - X * X);
@@ -93,16 +92,17 @@ int launch_levelset(evap_mesh* h, int mode, const T* x, T* y, cudaStream_t s) {
     const bool dbl = sizeof(T) == 8;
     const T* phi = dbl ? (const T*)h->phi : (const T*)h->phi32;
     const T* ug = dbl ? (const T*)h->ugamma : (const T*)h->ugamma32;
+    const T* nf = dbl ? (const T*)h->ls_normal : (const T*)h->ls_normal32;
     int rc = launch_fill<T>(y, m.Nphi, T(0), s);
     if (rc) return rc;
     const int threads = 128;
     const unsigned grid = (unsigned)((m.ncell + threads - 1) / threads);
     if (mode == EVAP_ADVECT)
-        k_levelset<T, EVAP_ADVECT><<<grid, threads, 0, s>>>(m, b, phi, ug, x, y);
+        k_levelset<T, EVAP_ADVECT><<<grid, threads, 0, s>>>(m, b, phi, nullptr, ug, x, y);
     else if (mode == EVAP_REINIT)
-        k_levelset<T, EVAP_REINIT><<<grid, threads, 0, s>>>(m, b, phi, ug, x, y);
+        k_levelset<T, EVAP_REINIT><<<grid, threads, 0, s>>>(m, b, phi, nf, ug, x, y);
     else
-        k_levelset<T, EVAP_REINIT_RHS><<<grid, threads, 0, s>>>(m, b, phi, ug, x, y);
+        k_levelset<T, EVAP_REINIT_RHS><<<grid, threads, 0, s>>>(m, b, phi, nf, ug, x, y);
     EVAP_CHECK_LAUNCH("levelset");
     return EVAP_OK;
 }

@@ -47,6 +47,36 @@ __device__ __forceinline__ Material material(double phi, double gx, double gy, d
     return r;
 }
 
+// Frozen normal of the reinitialization operators at a Q1 quadrature point (Eq. reinitialization): with a nodal
+// field nf (nf[c][j] at the cell's 8 nodes) the normalized interpolant n_h / |n_h| (zero where |n_h| <= 1e-4), else the
+// unit normal grad phi / |grad phi| (zero where |grad phi| h <= GRAD_TINY).  N[j], G[j][d]: Q1 values and
+// physical gradients at the point; pv[j]: phi at the nodes.
+constexpr double NODAL_NORMAL_TINY = 1e-4;
+template <typename T>
+__device__ __forceinline__ void ls_frozen_normal(const T (*nf)[8], const T pv[8], const T N[8], const T (*G)[3], T h,
+                                                 T nv[3]) {
+    T g[3] = {T(0), T(0), T(0)};
+    if (nf) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) g[d] += N[j] * nf[d][j];
+    } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) g[d] += G[j][d] * pv[j];
+    }
+    const T gn = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    const bool ok = nf ? gn > T(NODAL_NORMAL_TINY) : gn * h > T(GRAD_TINY);
+    nv[0] = nv[1] = nv[2] = T(0);
+    if (ok) {
+        nv[0] = g[0] / gn;
+        nv[1] = g[1] / gn;
+        nv[2] = g[2] / gn;
+    }
+}
+
 // Whether the corrected-strain term is active at a point (Sec. 2.4.2; zone gate or everywhere).
 __device__ __forceinline__ bool correction_on(const MeshArgs<double>& m, bool zone) {
     return m.stress != 0 && (m.corr_zone != 0 || zone);

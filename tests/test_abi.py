@@ -76,6 +76,12 @@ def test_invalid_arguments_are_rejected_on_the_host(L):
                      ("evap_apply_levelset", (None, 0, 64, None, None, None)),
                      ("evap_set_fields", (None, None, None, None, None)),
                      ("evap_apply_adjoint", (None,) * 9),
-                     ("evap_jacobi_diagonal", (None, None, None))):
+                     ("evap_jacobi_diagonal", (None, None, None)),
+                     ("evap_projected_normal", (None, None, None, None, None)),
+                     ("evap_curvature", (None, None, None, None, None, None)),
+                     ("evap_set_levelset_normal", (None, None, None)),
+                     ("evap_reinitialize", (None, None, 1, None, None, None)),
+                     ("evap_update_transport_velocity", (None, None)),
+                     ("evap_transport_stats", (None, None, None, None, None))):
         assert getattr(L, fn)(*args) == -1, fn
     assert L.evap_destroy(None) == 0

@@ -159,7 +159,7 @@ def default_params(n: int, L: float = 1.0, ratio: float = 1e3, **over) -> dict:
     dt = 1e-4
     prm = dict(rho_l=1000.0, rho_g=1000.0 / ratio, mu_l=1e-3, mu_g=1e-5, eps=eps, dt=dt, c_mass=1.0 / dt,
                theta=0.5, dtau=min(eps, dt), variant=2, stress=1, corr_zone=0, newton=1, dirichlet_faces=0x3F,
-               cpp_tol=1e-10, cpp_kmax=20)
+               cpp_tol=1e-10, cpp_kmax=20, eta_n=2.0, eta_kappa=2.0)
     prm.update(over)
     return prm
 
