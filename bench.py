@@ -325,6 +325,33 @@ def operator_applies(evap, torch, dev, op, d, counts, hbm):
     return out
 
 
+def geometry_subsolver(torch, op, phi):
+    """Level-set geometry sub-solver on the current fields (64^3 four spheres): projected normal (3 CG solves),
+    curvature (1 CG solve), 5 reinitialization steps with the projected normal frozen; each timed with CUDA events
+    after one untimed run."""
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), out
+
+    t_n, (n, info_n) = timed(op.projected_normal)
+    t_k, (kappa, info_k) = timed(lambda: op.curvature(n))
+    op.set_levelset_normal(n)
+    t_r, (psi, info_r) = timed(lambda: op.reinitialize(phi, 5))
+    op.set_levelset_normal(None)
+    return dict(projected_normal=dict(ms=t_n, cg_iters=info_n["iters"], relres=info_n["relres"]),
+                curvature=dict(ms=t_k, cg_iters=info_k["iters"], relres=info_k["relres"]),
+                reinit_5_steps=dict(ms=t_r, cg_iters=info_r["iters"], last_change=info_r["last_change"]),
+                level_set_dofs=op.n_phi)
+
+
 def large_case(evap, torch, dev, p: int):
     """deformed128: 128^3 cells, degree-p velocity (p = 2: 51 M DoFs, p = 3: 171 M DoFs), deformed sphere with
     spherical-harmonic noise up to l = 6 (seed 5), density ratio 1e4.  FP64 and FP32 applies, the adjoint apply, and
@@ -566,6 +593,7 @@ def main():
     applies = None
     if rank == 0 and not args.no_applies:
         applies = operator_applies(evap, torch, dev, op, d, counts, hbm)
+        applies["geometry"] = geometry_subsolver(torch, op, d["phi"])
     solves = None
     if rank == 0 and not args.no_solve_compare:
         solves = solve_comparison(evap, torch, dev)
