@@ -101,6 +101,8 @@ struct evap_mesh {
     // geometry sub-solver workspace (first use) and its pinned scalars
     void* geo_ws = nullptr;
     double* geo_host = nullptr;
+    double* geo_elem = nullptr;  // reinitialization element matrices [36][ncell] (first reinitialization)
+    int64_t geo_elem_len = 0;
     // Jacobi diagonal and Krylov workspace (allocated by the first solve)
     double* diag = nullptr;
     float* diag32 = nullptr;
