@@ -480,12 +480,14 @@ int launch_transport_velocity(evap_mesh* h, cudaStream_t s) {
                                                                             h->band_list, h->band_count);
     EVAP_CHECK_LAUNCH("transport_direct");
     if (h->m.variant != 1) {
-        // Persistent pass sized to about 4 band nodes per lane (lanes that finish early take the remaining entries,
+        // Persistent pass sized to about 2 band nodes per lane (lanes that finish early take the remaining entries,
         // so warps stay full until the tail), at most 8 warps per SM: the FP64 pipe, not occupancy, bounds it.
+        // Measured on the 64^3 four-sphere band (49 k nodes): 2 nodes per lane 3.9 ms, 4 nodes 5.0 ms, 1 node 4.3 ms;
+        // on the 128^3 deformed sphere (181 k nodes, capped at 8 warps per SM) 9.6 ms, and 10.6 ms at 16 warps.
         int32_t count = 0;
         EVAP_CUDA(cudaMemcpyAsync(&count, h->band_count, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         EVAP_CUDA(cudaStreamSynchronize(s));
-        const int grid = (int)std::min<int64_t>(std::max<int64_t>(((int64_t)count + 127) / 128, 1), 152 * 8);
+        const int grid = (int)std::min<int64_t>(std::max<int64_t>(((int64_t)count + 63) / 64, 1), 152 * 8);
         k_transport_band<<<grid, 32, 0, s>>>(e, h->prm.cpp_tol, h->prm.cpp_kmax, h->band_list, h->band_count,
                                              h->band_y, h->cpp_flags, h->flag_count, h->cpp_evals);
         EVAP_CHECK_LAUNCH("transport_band");
