@@ -91,9 +91,10 @@ def algorithmic_counts(n: int, p: int):
     # (testing); ~50 multiply-adds per point for the fluxes; an FMA counts 2 flops
     interp = 6 * sweep
     mom_flop = 2 * nc * (3 * interp + 3 * interp + 50 * nq)
-    # adjoint: interpolation of x, w, u0 (9 components), testing of g_x and g_u0 (6 components), ~300 multiply-adds
-    # per point for the adjoint fluxes and the material-law derivatives
-    adj_flop = 2 * nc * (9 * interp + 6 * interp + 300 * nq)
+    # adjoint: interpolation of x and w (6 components; the u0 terms come from the quadrature-point cache), testing
+    # of g_x and g_u0 (6 components), ~80 multiply-adds per point for the adjoint fluxes (the material-law
+    # derivatives of the interface-zone points are not counted: a lower bound)
+    adj_flop = 2 * nc * (6 * interp + 6 * interp + 80 * nq)
     # FP32 line kernel per cell (Q^2 line threads): z-sweeps (S, D on 3 components), y-sweeps (S, D on S-output,
     # S on D-output), x-lines (4 outputs per point and component, ~50 multiply-adds of fluxes per point, x-line
     # testing 4 per point, node and component), backward y- (3 per pair) and z-sweeps (2 per pair) of 3 components
