@@ -9,6 +9,11 @@
 
 namespace evap {
 
+// Points of the 2-point Gauss rule on [0, 1], (1 -+ 1/sqrt 3) / 2 (the literal of the host basis).
+__host__ __device__ constexpr double g2_point(int i) {
+    return i ? 0.5 * (1.0 + 0.5773502691896257645091488) : 0.5 * (1.0 - 0.5773502691896257645091488);
+}
+
 template <typename T, int MODE>
 __global__ void __launch_bounds__(128) k_levelset(MeshArgs<T> m, Basis<T> bas, const T* __restrict__ phi,
                                                   const T* __restrict__ nf, const T* __restrict__ ug,
@@ -38,48 +43,50 @@ __global__ void __launch_bounds__(128) k_levelset(MeshArgs<T> m, Basis<T> bas, c
     T out[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) out[j] = 0;
+    const T ih = m.inv_h;
+    const T W = T(0.125) * m.vol_w;  // 2-point Gauss weights 1/2 in each direction
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
+        // shape values and reference derivatives at the point: compile-time constants once the loops are unrolled
         const int qx = q & 1, qy = (q >> 1) & 1, qz = q >> 2;
-        const T tx = bas.g2t[qx], ty = bas.g2t[qy], tz = bas.g2t[qz];
-        const T W = bas.g2w[qx] * bas.g2w[qy] * bas.g2w[qz] * m.vol_w;
+        const T tx = T(g2_point(qx)), ty = T(g2_point(qy)), tz = T(g2_point(qz));
         const T Nx[2] = {T(1) - tx, tx}, Ny[2] = {T(1) - ty, ty}, Nz[2] = {T(1) - tz, tz};
         const T Dd[2] = {T(-1), T(1)};
-        T N[8], dN[8][3];
+        T N[8], dR[8][3];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const int ja = j & 1, jb = (j >> 1) & 1, jc = j >> 2;
             N[j] = Nx[ja] * Ny[jb] * Nz[jc];
-            dN[j][0] = Dd[ja] * Ny[jb] * Nz[jc] * m.inv_h;
-            dN[j][1] = Nx[ja] * Dd[jb] * Nz[jc] * m.inv_h;
-            dN[j][2] = Nx[ja] * Ny[jb] * Dd[jc] * m.inv_h;
+            dR[j][0] = Dd[ja] * Ny[jb] * Nz[jc];
+            dR[j][1] = Nx[ja] * Dd[jb] * Nz[jc];
+            dR[j][2] = Nx[ja] * Ny[jb] * Dd[jc];
         }
-        T X = 0, GX[3] = {0, 0, 0};
+        T X = 0, GX[3] = {0, 0, 0};  // value and reference gradient (physical gradient = GX / h)
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             X += N[j] * xv[j];
 #pragma unroll
-            for (int d = 0; d < 3; ++d) GX[d] += dN[j][d] * xv[j];
+            for (int d = 0; d < 3; ++d) GX[d] += dR[j][d] * xv[j];
         }
-        T Fv, Gf[3] = {0, 0, 0};
+        T Fv, Gf[3] = {0, 0, 0};  // Gf: flux tested with the reference gradients (physical flux / h)
         if (MODE == EVAP_ADVECT) {
             T U[3] = {0, 0, 0};
 #pragma unroll
             for (int j = 0; j < 8; ++j)
 #pragma unroll
                 for (int k = 0; k < 3; ++k) U[k] += N[j] * uv[k][j];
-            Fv = W * (X + m.theta * m.dt * (U[0] * GX[0] + U[1] * GX[1] + U[2] * GX[2]));
+            Fv = W * (X + m.theta * m.dt * ih * (U[0] * GX[0] + U[1] * GX[1] + U[2] * GX[2]));
         } else {
             T nv[3];
-            ls_frozen_normal<T>(nf ? uv : nullptr, pv, N, dN, m.h, nv);
+            ls_frozen_normal<T>(nf ? uv : nullptr, pv, N, dR, T(1), nv);  // |grad_ref phi| = |grad phi| h
             Fv = W * X / m.dtau;
-            const T s = (MODE == EVAP_REINIT) ? W * m.eps * (GX[0] * nv[0] + GX[1] * nv[1] + GX[2] * nv[2])
-                                              : W * T(0.5) * (T(1) - X * X);
+            const T s = (MODE == EVAP_REINIT) ? W * m.eps * ih * ih * (GX[0] * nv[0] + GX[1] * nv[1] + GX[2] * nv[2])
+                                              : W * T(0.5) * ih * (T(1) - X * X);
 #pragma unroll
             for (int d = 0; d < 3; ++d) Gf[d] = s * nv[d];
         }
 #pragma unroll
-        for (int j = 0; j < 8; ++j) out[j] += N[j] * Fv + dN[j][0] * Gf[0] + dN[j][1] * Gf[1] + dN[j][2] * Gf[2];
+        for (int j = 0; j < 8; ++j) out[j] += N[j] * Fv + dR[j][0] * Gf[0] + dR[j][1] * Gf[1] + dR[j][2] * Gf[2];
     }
 #pragma unroll
     for (int j = 0; j < 8; ++j) atomicAdd(&y[node[j]], out[j]);

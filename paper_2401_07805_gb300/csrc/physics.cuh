@@ -71,9 +71,10 @@ __device__ __forceinline__ void ls_frozen_normal(const T (*nf)[8], const T pv[8]
     const bool ok = nf ? gn > T(NODAL_NORMAL_TINY) : gn * h > T(GRAD_TINY);
     nv[0] = nv[1] = nv[2] = T(0);
     if (ok) {
-        nv[0] = g[0] / gn;
-        nv[1] = g[1] / gn;
-        nv[2] = g[2] / gn;
+        const T ig = T(1) / gn;
+        nv[0] = g[0] * ig;
+        nv[1] = g[1] * ig;
+        nv[2] = g[2] * ig;
     }
 }
 
