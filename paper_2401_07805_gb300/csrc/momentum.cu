@@ -258,11 +258,15 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
             for (int d = 0; d < 3; ++d) v += cf[1 + d] * G[k][d] + cf[4 + 3 * k + d] * X[d];
             F[k] = v;
         }
-        const T sm = cf[13] * tr;
+        const T sm = cf[13] * tr, hm = T(0.5) * cf[13];
 #pragma unroll
         for (int k = 0; k < 3; ++k)
 #pragma unroll
-            for (int l = 0; l < 3; ++l) Tf[k][l] = cf[13] * (T(0.5) * (G[k][l] + G[l][k])) - sm * cf[14 + k] * cf[14 + l];
+            for (int l = k; l < 3; ++l) {  // symmetric: 6 distinct entries
+                const T v = hm * (G[k][l] + G[l][k]) - sm * cf[14 + k] * cf[14 + l];
+                Tf[k][l] = v;
+                Tf[l][k] = v;
+            }
         rdiv = cf[17] * tr - cf[18];
     }
     __syncthreads();
