@@ -333,8 +333,8 @@ def operator_applies(evap, torch, dev, op, d, counts, hbm):
 
 def geometry_subsolver(torch, op, phi):
     """Level-set geometry sub-solver on the current fields (64^3 four spheres): projected normal (3 CG solves),
-    curvature (1 CG solve), 5 reinitialization steps with the projected normal frozen; each timed with CUDA events
-    after one untimed run."""
+    curvature (1 CG solve), the surface-tension force from them, 5 reinitialization steps with the projected normal
+    frozen; each timed with CUDA events after one untimed run."""
     stream = torch.cuda.current_stream()
 
     def timed(fn):
@@ -349,11 +349,13 @@ def geometry_subsolver(torch, op, phi):
 
     t_n, (n, info_n) = timed(op.projected_normal)
     t_k, (kappa, info_k) = timed(lambda: op.curvature(n))
+    t_s, _ = timed(lambda: op.surface_tension(n, kappa, 0.0728))
     op.set_levelset_normal(n)
     t_r, (psi, info_r) = timed(lambda: op.reinitialize(phi, 5))
     op.set_levelset_normal(None)
     return dict(projected_normal=dict(ms=t_n, cg_iters=info_n["iters"], relres=info_n["relres"]),
                 curvature=dict(ms=t_k, cg_iters=info_k["iters"], relres=info_k["relres"]),
+                surface_tension_force=dict(ms=t_s, velocity_dofs=3 * op.n_u),
                 reinit_5_steps=dict(ms=t_r, cg_iters=info_r["iters"], last_change=info_r["last_change"]),
                 level_set_dofs=op.n_phi)
 

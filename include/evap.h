@@ -154,6 +154,13 @@ int evap_set_levelset_normal(evap_handle h, const double* n, void* stream);
  * psi^(steps-1)|_2. */
 int evap_reinitialize(evap_handle h, double* psi, int steps, int* iters, double* last_change, void* stream);
 
+/* Surface-tension force f [3 N_u] of Eq. (surfaceTension) in the velocity test space (the right-hand side of the
+ * momentum equation): f_(i,c) = sum_q W_q N_i alpha kappa_h n_c delta(phi) rho(phi) c_rho with the density-scaled
+ * delta, c_rho = (rho_g - rho_l) / (rho_l rho_g ln(rho_g / rho_l)); kappa [N_phi] and n [3 N_phi] are Q1 fields (e.g.
+ * from evap_curvature and evap_projected_normal; n is normalized at each point, zero where |n_h| <= 1e-4), phi is the
+ * level set of evap_set_fields.  Dirichlet-constrained entries are 0.  EVAP_EINVAL if rho_l == rho_g. */
+int evap_surface_tension(evap_handle h, const double* n, const double* kappa, double alpha, double* f, void* stream);
+
 /* Adjoint of the momentum apply for L = w . A(phi, mdot, u) x + w_p . (B x - g(phi, mdot)):
  *   g_x = A^T w + B^T w_p,  g_u0 = dL/du [3 N_u],  g_phi = dL/dphi [N_phi],  g_mdot = dL/dmdot [N_phi],
  * with the quadrature-point coefficients of evap_set_fields and the material-law derivatives recomputed at the

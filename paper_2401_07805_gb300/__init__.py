@@ -56,6 +56,7 @@ SIGNATURES = {
     "evap_curvature": (_c_int, [_vp, _vp, _vp, ctypes.POINTER(_c_int), ctypes.POINTER(_c_dbl), _vp]),
     "evap_set_levelset_normal": (_c_int, [_vp, _vp, _vp]),
     "evap_reinitialize": (_c_int, [_vp, _vp, _c_int, ctypes.POINTER(_c_int), ctypes.POINTER(_c_dbl), _vp]),
+    "evap_surface_tension": (_c_int, [_vp, _vp, _vp, _c_dbl, _vp, _vp]),
     "evap_apply_momentum": (_c_int, [_vp, _c_int, _vp, _vp, _vp, _vp]),
     "evap_apply_levelset": (_c_int, [_vp, _c_int, _c_int, _vp, _vp, _vp]),
     "evap_apply_adjoint": (_c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
@@ -240,6 +241,15 @@ class Operator:
         rc = lib().evap_reinitialize(self._h, _ptr(out), int(steps), ctypes.byref(its), ctypes.byref(ch), _stream())
         _check(rc, "evap_reinitialize", allow=() if raise_on_notconv else (-3,))
         return out, dict(iters=its.value, last_change=ch.value, converged=rc == 0)
+
+    def surface_tension(self, n: torch.Tensor, kappa: torch.Tensor, alpha: float, out=None):
+        """Surface-tension force [3 N_u] (Eq. surfaceTension, density-scaled delta) from Q1 normal and curvature."""
+        n = self._dev(n, 3 * self.n_phi, torch.float64, "n")
+        kappa = self._dev(kappa, self.n_phi, torch.float64, "kappa")
+        f = self._out(out, 3 * self.n_u, torch.float64)
+        _check(lib().evap_surface_tension(self._h, _ptr(n), _ptr(kappa), float(alpha), _ptr(f), _stream()),
+               "evap_surface_tension")
+        return f
 
     def apply_momentum(self, x: torch.Tensor, prec: int = 64, with_divergence: bool = False, out=None, out_p=None):
         dt = torch.float64 if prec == 64 else torch.float32

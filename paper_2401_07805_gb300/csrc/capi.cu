@@ -331,6 +331,13 @@ int evap_reinitialize(evap_handle h, double* psi, int steps, int* iters, double*
     return geo_reinitialize(h, psi, steps, iters, last_change, (cudaStream_t)stream);
 }
 
+int evap_surface_tension(evap_handle h, const double* n, const double* kappa, double alpha, double* f, void* stream) {
+    if (!h || !n || !kappa || !f) return fail(EVAP_EINVAL, "evap_surface_tension: null argument");
+    if (!h->has_fields) return fail(EVAP_ENOFIELDS, "evap_surface_tension: call evap_set_fields first");
+    if (!(h->m.rho_l != h->m.rho_g)) return fail(EVAP_EINVAL, "evap_surface_tension: c_rho needs rho_l != rho_g");
+    return launch_surface_tension(h, n, kappa, alpha, f, (cudaStream_t)stream);
+}
+
 int evap_apply_momentum(evap_handle h, int prec, const void* x, void* y, void* y_p, void* stream) {
     if (!h || !x || !y) return fail(EVAP_EINVAL, "evap_apply_momentum: null argument");
     if (prec != 64 && prec != 32) return fail(EVAP_EINVAL, "evap_apply_momentum: prec must be 64 or 32");

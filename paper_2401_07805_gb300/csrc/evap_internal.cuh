@@ -152,6 +152,8 @@ int geo_helmholtz(evap_mesh* h, double c, int ncomp, const double* x, double* y,
 int geo_projected_normal(evap_mesh* h, double* n, int* iters, double* relres, cudaStream_t s);
 int geo_curvature(evap_mesh* h, const double* nf, double* kappa, int* iters, double* relres, cudaStream_t s);
 int geo_reinitialize(evap_mesh* h, double* psi, int steps, int* iters, double* last_change, cudaStream_t s);
+int launch_surface_tension(evap_mesh* h, const double* nf, const double* kappa, double alpha, double* out,
+                           cudaStream_t s);
 int launch_diagonal_into(evap_mesh* h, float* acc, double* out, cudaStream_t s);
 int solve_gmres(evap_mesh* h, const double* f, double* x, int mixed, int restart, double rtol, int max_iter,
                 int* iters, double* relres, cudaStream_t s);
