@@ -1,7 +1,11 @@
 """Level-set geometry sub-solver by assembled Gauss quadrature and direct sparse solves (test infrastructure).
 
-Steps 2 and 3 of Algorithm 2 (level_set_solver) on the Q1 level-set space with 2^3 Gauss points (Sec. 2.5),
+Steps 1 to 3 of Algorithm 2 (level_set_solver) on the Q1 level-set space with 2^3 Gauss points (Sec. 2.5),
 homogeneous Neumann conditions on every face (no constraint):
+
+  advection           Eqs. (transport), (weakFormLevelSet), Crank-Nicolson in time, step 1 of Algorithm 2: a fixed
+                      point phi^(k) -> u_Gamma(phi^(k)) (oracle.transport) -> phi^(k+1) solving
+                      (M + theta dt C) phi^(k+1) = (M - (1 - theta) dt C) phi^n, C_ij = sum_q W N_i (u_Gamma . grad N_j).
 
   projected normal    Eq. (normal_vector_regularized): n - eta_n h^2 Laplace n = nbar, nbar the unit normal of
                       Eq. (normal_vector) at the point (zero where phi is flat, physics.has_normal).  Weak form per
@@ -135,3 +139,28 @@ def reinitialize(mesh: fe.Mesh, phi: np.ndarray, n_field, eps: float, dtau: floa
         change = float(np.linalg.norm(new - psi))
         psi = new
     return psi, change
+
+
+def advect_levelset(mesh_u: fe.Mesh, phi_n: np.ndarray, u0: np.ndarray, mdot: np.ndarray, prm: dict,
+                    fp_iters: int):
+    """Step 1 of Algorithm 2: the fixed point between the transport velocity and the Crank-Nicolson advection
+    (Eqs. transport, weakFormLevelSet):  phi^(0) = phi^n;  for k: u_Gamma^(k) = u_Gamma(u0, mdot, phi^(k)) (the variant
+    of prm, closest-point projection of App. C for variants 2/3), then phi^(k+1) solves
+        (M + theta dt C(u_Gamma^(k))) phi^(k+1) = (M - (1 - theta) dt C(u_Gamma^(k))) phi^n,
+    C_ij = sum_q W N_i (u_Gamma . grad N_j).  phi^(k) is clamped to [-1, 1] before the transport velocity (as the
+    fields of set_fields are).  Returns (phi^(fp_iters), [|phi^(k+1) - phi^(k)|_2 for each k])."""
+    from . import levelset, transport
+    mesh1 = fe.Mesh(mesh_u.n, 1, mesh_u.L)
+    theta, dt = prm["theta"], prm["dt"]
+    M = helmholtz_matrix(mesh1, 0.0)
+    phi_k = np.array(phi_n, dtype=float)
+    changes = []
+    for _ in range(fp_iters):
+        ug, _ = transport.transport_velocity(mesh_u, np.clip(phi_k, -1.0, 1.0), u0, mdot, prm)
+        A = levelset.advection_matrix(mesh1, ug.ravel(), theta, dt)
+        C = (A - M) / (theta * dt)
+        rhs = M @ phi_n - (1.0 - theta) * dt * (C @ phi_n)
+        new = spla.spsolve(A.tocsc(), rhs)
+        changes.append(float(np.linalg.norm(new - phi_k)))
+        phi_k = new
+    return phi_k, changes

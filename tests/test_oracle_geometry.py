@@ -130,3 +130,63 @@ def test_reinit_with_the_unit_normal_matches_the_level_set_operators():
     r1 = geometry.reinit_rhs(mesh, phi, None, psi, dtau)
     r2 = levelset.reinit_rhs(mesh, phi, psi, dtau)
     assert np.abs(r1 - r2).max() < 1e-13 * np.abs(r2).max()
+
+
+def _advect_case(n, phi, u_const, variant=1, mdot_val=0.0):
+    import workloads
+    wl = workloads.random_workload(n, 2, 1, geom="sphere")
+    prm = dict(wl.params)
+    prm["variant"] = variant
+    mesh_u = fe.Mesh(n, 2, 1.0)
+    u0 = np.repeat(np.asarray(u_const, dtype=float)[:, None], mesh_u.n_u, axis=1).ravel()
+    mdot = np.full(mesh_u.n_phi, mdot_val)
+    return mesh_u, prm, u0, mdot
+
+
+def test_advection_of_a_linear_field_by_a_uniform_velocity_is_exact():
+    """phi = a . x + b with a uniform velocity U (variant 1, mdot = 0, so u_Gamma = U): C 1 = 0 and C phi = (U . a) M 1,
+    so Crank-Nicolson gives phi^(n+1) = phi^n - dt U . a exactly; the fixed point is reached after one pass."""
+    mesh_u, prm, u0, mdot = _advect_case(5, None, [0.3, -0.2, 0.5])
+    mesh1 = fe.Mesh(5, 1, 1.0)
+    x, y, z = q1_nodes(mesh1)
+    a = np.array([0.1, 0.05, -0.08])
+    phi = a[0] * x + a[1] * y + a[2] * z + 0.01
+    new, changes = geometry.advect_levelset(mesh_u, phi, u0, mdot, prm, 2)
+    shift = prm["dt"] * float(np.dot([0.3, -0.2, 0.5], a))
+    assert np.abs(new - (phi - shift)).max() < 1e-14
+    assert changes[1] < 1e-15
+
+
+def test_advection_with_zero_velocity_keeps_the_level_set():
+    mesh_u, prm, u0, mdot = _advect_case(4, None, [0.0, 0.0, 0.0])
+    mesh1 = fe.Mesh(4, 1, 1.0)
+    x, y, z = q1_nodes(mesh1)
+    phi = np.tanh((0.3 - np.sqrt((x - 0.5) ** 2 + (y - 0.5) ** 2 + (z - 0.5) ** 2)) / 0.5)
+    new, _ = geometry.advect_levelset(mesh_u, phi, u0, mdot, prm, 1)
+    assert np.abs(new - phi).max() < 1e-14
+
+
+def test_advection_fixed_point_converges_to_a_self_consistent_level_set():
+    """Variant 2 with an evaporation speed mdot / rho_l = 0.2 (0.06 cells per step): u_Gamma depends on phi^(k)
+    through the normal and the closest points, and the iteration contracts geometrically to a phi* whose own
+    transport velocity reproduces it, (M + theta dt C(u(phi*))) phi* = (M - (1 - theta) dt C(u(phi*))) phi^n.  Taking
+    the velocity from phi^n in every pass instead would stall the changes at zero after the second pass while the
+    self-consistency residual stayed at the size of the first change."""
+    from oracle import transport
+    mesh_u, prm, u0, mdot = _advect_case(6, None, [0.2, 0.1, -0.1], variant=2, mdot_val=200.0)
+    prm["dt"] = 0.05
+    import workloads
+    phi_n = workloads.random_workload(6, 2, 1, geom="sphere").phi
+    phi, changes = geometry.advect_levelset(mesh_u, phi_n, u0, mdot, prm, 7)
+    assert changes[1] > 1e-4 * changes[0]
+    for k in range(1, 6):
+        assert changes[k + 1] < 0.2 * changes[k]
+    assert changes[-1] < 1e-8
+    mesh1 = fe.Mesh(6, 1, 1.0)
+    ug, _ = transport.transport_velocity(mesh_u, np.clip(phi, -1.0, 1.0), u0, mdot, prm)
+    theta, dt = prm["theta"], prm["dt"]
+    A = levelset.advection_matrix(mesh1, ug.ravel(), theta, dt)
+    M = geometry.helmholtz_matrix(mesh1, 0.0)
+    B = M - (1.0 - theta) / theta * (A - M)
+    res = A @ phi - B @ phi_n
+    assert np.linalg.norm(res) < 1e-7 * np.linalg.norm(B @ phi_n)
