@@ -154,6 +154,21 @@ int evap_set_levelset_normal(evap_handle h, const double* n, void* stream);
  * psi^(steps-1)|_2. */
 int evap_reinitialize(evap_handle h, double* psi, int steps, int* iters, double* last_change, void* stream);
 
+/* Level-set advection, Eqs. (transport), (weakFormLevelSet) with Crank-Nicolson in time (Algorithm 2, step 1):
+ * phi^n is the (clamped) level set of evap_set_fields; phi^(0) = phi^n and pass k computes the transport velocity of
+ * clamp(phi^(k), -1, 1) (the mesh's variant, with the fields' u and mdot) and solves
+ *   (M + theta dt C(u_Gamma)) phi^(k+1) = (M - (1 - theta) dt C(u_Gamma)) phi^n,  C_ij = sum_q W N_i u_Gamma . grad N_j,
+ * by GMRES(30) with the diagonal preconditioner, started from phi^(k), to |r| <= max(1e-12 |b|, 1e-20) (b the
+ * right-hand side: the residual of a zero start).  The fixed point
+ * stops after max_iters passes or once |phi^(k+1) - phi^(k)|_2 <= tol (tol = 0: exactly max_iters passes).
+ * phi [N_phi] (device) receives phi^(k) of the last pass (phi^n when max_iters = 0).  The mesh's level set stays
+ * phi^n; its transport velocity (evap_get_transport_velocity, EVAP_ADVECT) is left as that of the last pass.
+ * fp_iters, lin_iters (GMRES operator applications, summed) and last_change (|phi^(k) - phi^(k-1)|_2 of the last
+ * pass) are host outputs and may be NULL.  Returns EVAP_ENOTCONV if a linear solve missed its tolerance (phi still
+ * written), EVAP_EINVAL for max_iters < 0 or tol < 0. */
+int evap_advect_levelset(evap_handle h, double* phi, int max_iters, double tol, int* fp_iters, int* lin_iters,
+                         double* last_change, void* stream);
+
 /* Surface-tension force f [3 N_u] of Eq. (surfaceTension) in the velocity test space (the right-hand side of the
  * momentum equation): f_(i,c) = sum_q W_q N_i alpha kappa_h n_c delta(phi) rho(phi) c_rho with the density-scaled
  * delta, c_rho = (rho_g - rho_l) / (rho_l rho_g ln(rho_g / rho_l)); kappa [N_phi] and n [3 N_phi] are Q1 fields (e.g.

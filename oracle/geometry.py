@@ -141,26 +141,31 @@ def reinitialize(mesh: fe.Mesh, phi: np.ndarray, n_field, eps: float, dtau: floa
     return psi, change
 
 
+def advection_step(mesh1: fe.Mesh, phi_n: np.ndarray, ug: np.ndarray, theta: float, dt: float) -> np.ndarray:
+    """One Crank-Nicolson step of Eq. (weakFormLevelSet) with the nodal transport velocity ug [3, N_phi]:
+    solves (M + theta dt C) phi = (M - (1 - theta) dt C) phi^n, C_ij = sum_q W N_i (u_Gamma . grad N_j)."""
+    from . import levelset
+    M = helmholtz_matrix(mesh1, 0.0)
+    A = levelset.advection_matrix(mesh1, np.asarray(ug).ravel(), theta, dt)
+    C = (A - M) / (theta * dt)
+    rhs = M @ phi_n - (1.0 - theta) * dt * (C @ phi_n)
+    return spla.spsolve(A.tocsc(), rhs)
+
+
 def advect_levelset(mesh_u: fe.Mesh, phi_n: np.ndarray, u0: np.ndarray, mdot: np.ndarray, prm: dict,
                     fp_iters: int):
     """Step 1 of Algorithm 2: the fixed point between the transport velocity and the Crank-Nicolson advection
     (Eqs. transport, weakFormLevelSet):  phi^(0) = phi^n;  for k: u_Gamma^(k) = u_Gamma(u0, mdot, phi^(k)) (the variant
-    of prm, closest-point projection of App. C for variants 2/3), then phi^(k+1) solves
-        (M + theta dt C(u_Gamma^(k))) phi^(k+1) = (M - (1 - theta) dt C(u_Gamma^(k))) phi^n,
-    C_ij = sum_q W N_i (u_Gamma . grad N_j).  phi^(k) is clamped to [-1, 1] before the transport velocity (as the
-    fields of set_fields are).  Returns (phi^(fp_iters), [|phi^(k+1) - phi^(k)|_2 for each k])."""
-    from . import levelset, transport
+    of prm, closest-point projection of App. C for variants 2/3), then phi^(k+1) = advection_step(phi^n, u_Gamma^(k)).
+    phi^(k) is clamped to [-1, 1] before the transport velocity (as the fields of set_fields are).  Returns
+    (phi^(fp_iters), [|phi^(k+1) - phi^(k)|_2 for each k])."""
+    from . import transport
     mesh1 = fe.Mesh(mesh_u.n, 1, mesh_u.L)
-    theta, dt = prm["theta"], prm["dt"]
-    M = helmholtz_matrix(mesh1, 0.0)
     phi_k = np.array(phi_n, dtype=float)
     changes = []
     for _ in range(fp_iters):
         ug, _ = transport.transport_velocity(mesh_u, np.clip(phi_k, -1.0, 1.0), u0, mdot, prm)
-        A = levelset.advection_matrix(mesh1, ug.ravel(), theta, dt)
-        C = (A - M) / (theta * dt)
-        rhs = M @ phi_n - (1.0 - theta) * dt * (C @ phi_n)
-        new = spla.spsolve(A.tocsc(), rhs)
+        new = advection_step(mesh1, phi_n, ug, prm["theta"], prm["dt"])
         changes.append(float(np.linalg.norm(new - phi_k)))
         phi_k = new
     return phi_k, changes

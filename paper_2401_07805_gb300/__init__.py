@@ -56,6 +56,8 @@ SIGNATURES = {
     "evap_curvature": (_c_int, [_vp, _vp, _vp, ctypes.POINTER(_c_int), ctypes.POINTER(_c_dbl), _vp]),
     "evap_set_levelset_normal": (_c_int, [_vp, _vp, _vp]),
     "evap_reinitialize": (_c_int, [_vp, _vp, _c_int, ctypes.POINTER(_c_int), ctypes.POINTER(_c_dbl), _vp]),
+    "evap_advect_levelset": (_c_int, [_vp, _vp, _c_int, _c_dbl, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int),
+                                      ctypes.POINTER(_c_dbl), _vp]),
     "evap_surface_tension": (_c_int, [_vp, _vp, _vp, _c_dbl, _vp, _vp]),
     "evap_apply_momentum": (_c_int, [_vp, _c_int, _vp, _vp, _vp, _vp]),
     "evap_apply_levelset": (_c_int, [_vp, _c_int, _c_int, _vp, _vp, _vp]),
@@ -241,6 +243,16 @@ class Operator:
         rc = lib().evap_reinitialize(self._h, _ptr(out), int(steps), ctypes.byref(its), ctypes.byref(ch), _stream())
         _check(rc, "evap_reinitialize", allow=() if raise_on_notconv else (-3,))
         return out, dict(iters=its.value, last_change=ch.value, converged=rc == 0)
+
+    def advect_levelset(self, max_iters: int, tol: float = 0.0, out=None, raise_on_notconv: bool = False):
+        """Algorithm 2 step 1: fixed point of transport velocity and Crank-Nicolson advection from the fields' level
+        set; returns (phi^(n+1) [N_phi], info)."""
+        phi = self._out(out, self.n_phi, torch.float64)
+        fp, lin, ch = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        rc = lib().evap_advect_levelset(self._h, _ptr(phi), int(max_iters), float(tol), ctypes.byref(fp),
+                                        ctypes.byref(lin), ctypes.byref(ch), _stream())
+        _check(rc, "evap_advect_levelset", allow=() if raise_on_notconv else (-3,))
+        return phi, dict(fp_iters=fp.value, lin_iters=lin.value, last_change=ch.value, converged=rc == 0)
 
     def surface_tension(self, n: torch.Tensor, kappa: torch.Tensor, alpha: float, out=None):
         """Surface-tension force [3 N_u] (Eq. surfaceTension, density-scaled delta) from Q1 normal and curvature."""

@@ -331,6 +331,14 @@ int evap_reinitialize(evap_handle h, double* psi, int steps, int* iters, double*
     return geo_reinitialize(h, psi, steps, iters, last_change, (cudaStream_t)stream);
 }
 
+int evap_advect_levelset(evap_handle h, double* phi, int max_iters, double tol, int* fp_iters, int* lin_iters,
+                         double* last_change, void* stream) {
+    if (!h || !phi) return fail(EVAP_EINVAL, "evap_advect_levelset: null argument");
+    if (max_iters < 0 || !(tol >= 0.0)) return fail(EVAP_EINVAL, "evap_advect_levelset: max_iters and tol must be >= 0");
+    if (!h->has_fields) return fail(EVAP_ENOFIELDS, "evap_advect_levelset: call evap_set_fields first");
+    return geo_advect_levelset(h, phi, max_iters, tol, fp_iters, lin_iters, last_change, (cudaStream_t)stream);
+}
+
 int evap_surface_tension(evap_handle h, const double* n, const double* kappa, double alpha, double* f, void* stream) {
     if (!h || !n || !kappa || !f) return fail(EVAP_EINVAL, "evap_surface_tension: null argument");
     if (!h->has_fields) return fail(EVAP_ENOFIELDS, "evap_surface_tension: call evap_set_fields first");

@@ -101,7 +101,7 @@ struct evap_mesh {
     // geometry sub-solver workspace (first use) and its pinned scalars
     void* geo_ws = nullptr;
     double* geo_host = nullptr;
-    double* geo_elem = nullptr;  // reinitialization element matrices [36][ncell] (first reinitialization)
+    double* geo_elem = nullptr;  // element matrices: reinitialization [36][ncell] or advection [64][ncell]
     int64_t geo_elem_len = 0;
     // Jacobi diagonal and Krylov workspace (allocated by the first solve)
     double* diag = nullptr;
@@ -138,7 +138,8 @@ MeshArgs<T> mesh_args(const evap_mesh* h);
 int launch_setup_coefficients(evap_mesh* h, cudaStream_t s);
 int launch_qp_coeffs(evap_mesh* h, cudaStream_t s);
 int launch_momentum32(evap_mesh* h, const float* x, float* y, float* yp, cudaStream_t s);
-int launch_transport_velocity(evap_mesh* h, cudaStream_t s);
+// u_Gamma of the mesh's level set, or of `phi` (a clamped Q1 field) when given, into h->ugamma / h->ugamma32.
+int launch_transport_velocity(evap_mesh* h, cudaStream_t s, const double* phi = nullptr);
 // y = A x (+ divergence row into yp if not null).  init = false: y already holds x on the Dirichlet DoFs and 0
 // elsewhere (and yp is null), e.g. written by the solver's fused preconditioner kernel.
 template <typename T>
@@ -152,11 +153,20 @@ int geo_helmholtz(evap_mesh* h, double c, int ncomp, const double* x, double* y,
 int geo_projected_normal(evap_mesh* h, double* n, int* iters, double* relres, cudaStream_t s);
 int geo_curvature(evap_mesh* h, const double* nf, double* kappa, int* iters, double* relres, cudaStream_t s);
 int geo_reinitialize(evap_mesh* h, double* psi, int steps, int* iters, double* last_change, cudaStream_t s);
+int geo_advect_levelset(evap_mesh* h, double* phi, int max_iters, double tol, int* fp_iters, int* lin_iters,
+                        double* last_change, cudaStream_t s);
+// y = A x with the advection element matrices of the current fixed-point pass (h->geo_elem, [64][ncell]).
+int geo_advect_elem_apply(evap_mesh* h, const double* x, double* y, cudaStream_t s);
 int launch_surface_tension(evap_mesh* h, const double* nf, const double* kappa, double alpha, double* out,
                            cudaStream_t s);
 int launch_diagonal_into(evap_mesh* h, float* acc, double* out, cudaStream_t s);
 int solve_gmres(evap_mesh* h, const double* f, double* x, int mixed, int restart, double rtol, int max_iter,
                 int* iters, double* relres, cudaStream_t s);
+// GMRES(restart) with the Jacobi diagonal `diag` on the Q1 advection system (the EVAP_ADVECT operator with the mesh's
+// transport velocity, applied through the element matrices of the pass), x the initial guess and the solution;
+// stops at |r| <= max(rtol |b|, atol).  *iters is incremented by the operator applications; *relres = |r| / |b|.
+int solve_advect_gmres(evap_mesh* h, const double* b, const double* diag, double* x, int restart, double rtol,
+                       double atol, int max_iter, int* iters, double* relres, cudaStream_t s);
 
 // small vector kernels used by several files
 template <typename T>

@@ -307,6 +307,14 @@ __global__ void __launch_bounds__(256) k_precond_init(int M, int64_t Nu, unsigne
     }
 }
 
+// z = sc v / diag for an operator without constrained rows (the Q1 advection operator zero-fills its output).
+template <typename T>
+__global__ void k_precond_plain(const T* __restrict__ v, const T* __restrict__ diag, T sc, T* __restrict__ z,
+                                int64_t N) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x)
+        z[k] = sc * v[k] / diag[k];
+}
+
 // x += diag^{-1} sum_i y[i] V_i   (x may be unaligned caller memory: scalar)
 template <typename T>
 __global__ void k_update(const T* __restrict__ V, int64_t ld, const double* __restrict__ y, int nv,
@@ -349,8 +357,12 @@ __global__ void k_refine(double* x, const float* __restrict__ d, const double* _
 // the outer FP64 residual is checked regardless).
 constexpr double REORTH64 = 0.5;
 constexpr double REORTH32 = 1e-2;
+// the operator of a solve: the momentum system, or the Q1 advection with the element matrices of the current
+// fixed-point pass (FP64 only)
+enum { OP_MOMENTUM = 0, OP_ADVECT = 1 };
 struct Ctx {
     evap_mesh* h;
+    int op;
     cudaStream_t s;
     int64_t N, ld;
     double* partial;   // [(m+2) * RED_BLOCKS]
@@ -364,12 +376,23 @@ struct Ctx {
 
 template <typename T>
 static int apply_op(Ctx& c, const T* x, T* y) {
+    if constexpr (sizeof(T) == 8)
+        if (c.op == OP_ADVECT) return geo_advect_elem_apply(c.h, x, y, c.s);
     return launch_momentum<T>(c.h, x, y, (T*)nullptr, c.s);
+}
+
+// Blocks of a reduction over N entries: RED_BLOCKS (one wave) for the velocity systems; for short vectors (the
+// Q1 level-set space) about 4 vector loads per thread, so that per-block overheads (ticket, partial sums) do not
+// dominate.  row_finish counts gridDim.x, so any grid up to RED_BLOCKS uses the same partial layout.
+template <typename T>
+static int red_grid(int64_t N) {
+    const int64_t per_block = (int64_t)RED_THREADS * V2<T>::w * 4;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(RED_BLOCKS, (N + per_block - 1) / per_block));
 }
 
 template <typename T>
 static int norm2_dev(Ctx& c, const T* v, double* out) {
-    k_norm2<T><<<RED_BLOCKS, RED_THREADS, 0, c.s>>>(v, c.N, c.partial, c.cnt, out);
+    k_norm2<T><<<red_grid<T>(c.N), RED_THREADS, 0, c.s>>>(v, c.N, c.partial, c.cnt, out);
     EVAP_CHECK_LAUNCH("norm");
     return EVAP_OK;
 }
@@ -385,9 +408,10 @@ static int fetch(Ctx& c, const double* dev, int n, double* host) {
 template <typename T>
 static int cgs_pass(Ctx& c, const T* V, T* w, int nv, double* h_out, bool with_pre) {
     const int rows = nv + (with_pre ? 1 : 0);
-    k_mdot<T><<<dim3(RED_BLOCKS, rows), RED_THREADS, 0, c.s>>>(V, c.ld, nv, w, c.N, c.partial, c.cnt, h_out);
+    const int gx = red_grid<T>(c.N);
+    k_mdot<T><<<dim3(gx, rows), RED_THREADS, 0, c.s>>>(V, c.ld, nv, w, c.N, c.partial, c.cnt, h_out);
     EVAP_CHECK_LAUNCH("mdot");
-    k_maxpy_norm<T><<<RED_BLOCKS, RED_THREADS, 0, c.s>>>(V, c.ld, h_out, c.dsc2, nv, w, c.N, c.partial, c.cnt,
+    k_maxpy_norm<T><<<gx, RED_THREADS, 0, c.s>>>(V, c.ld, h_out, c.dsc2, nv, w, c.N, c.partial, c.cnt,
                                                           c.dnorm);
     EVAP_CHECK_LAUNCH("maxpy");
     return EVAP_OK;
@@ -428,10 +452,10 @@ static int gmres(Ctx& c, int m, const T* b, T* x, bool x_zero, const T* diag, T*
             k_residual<T><<<G, 256, 0, c.s>>>(b, z, V, N);
             EVAP_CHECK_LAUNCH("residual");
         }
-        first = false;
         if ((rc = norm2_dev<T>(c, V, c.dnorm))) return rc;
         if ((rc = fetch(c, c.dnorm, 1, c.hcol))) return rc;
         beta = std::sqrt(c.hcol[0]);
+        first = false;
         *res_out = beta;
         if (beta <= tol_abs || used >= maxit || !(beta > 0.0)) break;
         sc[0] = 1.0 / beta;
@@ -442,13 +466,17 @@ static int gmres(Ctx& c, int m, const T* b, T* x, bool x_zero, const T* diag, T*
         for (; j < m; ++j) {
             T* Vj = V + (int64_t)j * c.ld;
             T* Wn = V + (int64_t)(j + 1) * c.ld;  // A z goes straight into the next basis slot
-            {
+            if (c.op == OP_ADVECT) {
+                k_precond_plain<T><<<G, 256, 0, c.s>>>(Vj, diag, (T)sc[j], z, N);
+                EVAP_CHECK_LAUNCH("precond");
+                if ((rc = apply_op<T>(c, z, Wn))) return rc;
+            } else {
                 const int M = c.h->m.M;
                 const unsigned gl = (unsigned)std::min<int64_t>((3 * (int64_t)M * M + 7) / 8, 152 * 16);
                 k_precond_init<T><<<gl, 256, 0, c.s>>>(M, c.h->m.Nu, c.h->m.faces, Vj, diag, (T)sc[j], z, Wn);
                 EVAP_CHECK_LAUNCH("precond");
+                if ((rc = launch_momentum<T>(c.h, z, Wn, (T*)nullptr, c.s, false))) return rc;
             }
-            if ((rc = launch_momentum<T>(c.h, z, Wn, (T*)nullptr, c.s, false))) return rc;
             ++used;
             const int nv = j + 1;
             double* col = &H[(size_t)j * (m + 1)];
@@ -509,18 +537,8 @@ static int gmres(Ctx& c, int m, const T* b, T* x, bool x_zero, const T* diag, T*
     return EVAP_OK;
 }
 
-int solve_gmres(evap_mesh* h, const double* f, double* x, int mixed, int m, double rtol, int max_iter, int* iters,
-                double* relres, cudaStream_t s) {
-    int rc = launch_diagonal(h, s);
-    if (rc) return rc;
-    const int64_t N = 3 * h->m.Nu;
-    const int64_t ld = (N + 63) / 64 * 64;
-    // workspace, every sub-array on a 256-byte boundary:
-    //   FP64: V [(m+1) ld], w [ld], z [ld] doubles;  mixed: V [(m+1) ld], w32, z32, r32, d32 [ld] floats, r64, Ax [ld]
-    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
-    const size_t fV = al((size_t)(m + 1) * ld * sizeof(float)), fN = al((size_t)ld * sizeof(float));
-    const size_t dV = al((size_t)(m + 1) * ld * sizeof(double)), dN = al((size_t)ld * sizeof(double));
-    const size_t bytes = mixed ? fV + 4 * fN + 2 * dN : dV + 2 * dN;
+// Grows the mesh's Krylov workspace to `bytes` and the reduction scratch to a GMRES(m) solve, and sets up c.
+static int prepare(evap_mesh* h, int op, int m, int64_t N, int64_t ld, size_t bytes, cudaStream_t s, Ctx& c) {
     if (h->ws_bytes < bytes) {
         if (h->ws) cudaFree(h->ws);
         h->ws = nullptr;
@@ -539,8 +557,8 @@ int solve_gmres(evap_mesh* h, const double* f, double* x, int mixed, int m, doub
         EVAP_CUDA(cudaMallocHost(&h->red_host, red_need * sizeof(double)));
         h->red_len = red_need;
     }
-    Ctx c;
     c.h = h;
+    c.op = op;
     c.s = s;
     c.N = N;
     c.ld = ld;
@@ -552,6 +570,24 @@ int solve_gmres(evap_mesh* h, const double* f, double* x, int mixed, int m, doub
     EVAP_CUDA(cudaMemsetAsync(c.cnt, 0, (size_t)(m + 2) * sizeof(unsigned), s));
     c.hcol = h->red_host;
     c.hsc2 = h->red_host + red_need - (m + 2);
+    return EVAP_OK;
+}
+
+static size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+int solve_gmres(evap_mesh* h, const double* f, double* x, int mixed, int m, double rtol, int max_iter, int* iters,
+                double* relres, cudaStream_t s) {
+    int rc = launch_diagonal(h, s);
+    if (rc) return rc;
+    const int64_t N = 3 * h->m.Nu;
+    const int64_t ld = (N + 63) / 64 * 64;
+    // workspace, every sub-array on a 256-byte boundary:
+    //   FP64: V [(m+1) ld], w [ld], z [ld] doubles;  mixed: V [(m+1) ld], w32, z32, r32, d32 [ld] floats, r64, Ax [ld]
+    const size_t fV = al256((size_t)(m + 1) * ld * sizeof(float)), fN = al256((size_t)ld * sizeof(float));
+    const size_t dV = al256((size_t)(m + 1) * ld * sizeof(double)), dN = al256((size_t)ld * sizeof(double));
+    const size_t bytes = mixed ? fV + 4 * fN + 2 * dN : dV + 2 * dN;
+    Ctx c;
+    if ((rc = prepare(h, OP_MOMENTUM, m, N, ld, bytes, s, c))) return rc;
     const int G = blocks_for(N, 256);
     // |f|, |x0|
     if ((rc = norm2_dev<double>(c, f, c.dnorm))) return rc;
@@ -620,6 +656,31 @@ int solve_gmres(evap_mesh* h, const double* f, double* x, int mixed, int m, doub
     if (iters) *iters = used;
     if (relres) *relres = res / fn;
     return res <= rtol * fn ? EVAP_OK : EVAP_ENOTCONV;
+}
+
+int solve_advect_gmres(evap_mesh* h, const double* b, const double* diag, double* x, int m, double rtol, double atol,
+                       int max_iter, int* iters, double* relres, cudaStream_t s) {
+    const int64_t N = h->m.Nphi;
+    const int64_t ld = (N + 63) / 64 * 64;
+    const size_t dV = al256((size_t)(m + 1) * ld * sizeof(double)), dN = al256((size_t)ld * sizeof(double));
+    Ctx c;
+    int rc = prepare(h, OP_ADVECT, m, N, ld, dV + dN, s, c);
+    if (rc) return rc;
+    double* V = (double*)h->ws;
+    double* z = (double*)((char*)h->ws + dV);
+    // the relative target is taken against |b|, the residual of a zero start, whatever the start x: it stays above
+    // the rounding level of the residual when x is already (nearly) the solution
+    if ((rc = norm2_dev<double>(c, b, c.dnorm))) return rc;
+    if ((rc = fetch(c, c.dnorm, 1, c.hcol))) return rc;
+    const double bn = std::sqrt(c.hcol[0]);
+    const double target = std::max(rtol * bn, atol);
+    int its = 0;
+    double res = 0.0;
+    if ((rc = gmres<double>(c, m, b, x, false, diag, V, nullptr, z, target, max_iter, &its, &res))) return rc;
+    EVAP_CUDA(cudaStreamSynchronize(s));
+    if (iters) *iters += its;
+    if (relres) *relres = bn > 0.0 ? res / bn : 0.0;
+    return res <= target ? EVAP_OK : EVAP_ENOTCONV;
 }
 
 }  // namespace evap

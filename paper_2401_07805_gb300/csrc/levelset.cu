@@ -9,11 +9,6 @@
 
 namespace evap {
 
-// Points of the 2-point Gauss rule on [0, 1], (1 -+ 1/sqrt 3) / 2 (the literal of the host basis).
-__host__ __device__ constexpr double g2_point(int i) {
-    return i ? 0.5 * (1.0 + 0.5773502691896257645091488) : 0.5 * (1.0 - 0.5773502691896257645091488);
-}
-
 template <typename T, int MODE>
 __global__ void __launch_bounds__(128) k_levelset(MeshArgs<T> m, Basis<T> bas, const T* __restrict__ phi,
                                                   const T* __restrict__ nf, const T* __restrict__ ug,

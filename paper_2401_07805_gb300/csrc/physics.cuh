@@ -5,6 +5,11 @@
 
 namespace evap {
 
+// Points of the 2-point Gauss rule on [0, 1], (1 -+ 1/sqrt 3) / 2 (the literal of the host basis).
+__host__ __device__ constexpr double g2_point(int i) {
+    return i ? 0.5 * (1.0 + 0.5773502691896257645091488) : 0.5 * (1.0 - 0.5773502691896257645091488);
+}
+
 // phi at d = 3 eps: tanh(3/2), the edge of the interface zone 0 < H < 1 (Eqs. initial_phi, heaviside).
 constexpr double PHI_BAND = 0x1.cf6f9786df577p-1;      // tanh(3/2), correctly rounded
 constexpr double PHI_GAS_BAND = 0x1.fd77d111a0b00p-1;  // tanh(3), correctly rounded (d = 6 eps)

@@ -461,9 +461,9 @@ __global__ void k_transport_band_finish(PointEval e, const double* __restrict__ 
     }
 }
 
-int launch_transport_velocity(evap_mesh* h, cudaStream_t s) {
+int launch_transport_velocity(evap_mesh* h, cudaStream_t s, const double* phi) {
     PointEval e;
-    e.phi = h->phi;
+    e.phi = phi ? phi : h->phi;
     e.u = h->u;
     e.m = h->m;
     const int P = h->m.P;

@@ -130,3 +130,100 @@ def test_full_size_geometry_properties():
     one = np.ones(mesh.n_phi)
     m0, m1 = one @ (M @ wl.phi), one @ (M @ host(psi))
     assert abs(m1 - m0) < 1e-11 * abs(m0)
+
+
+# ------------------------------------------------------------------------------------ advection (step 1)
+def _q1_xyz(n):
+    r = np.arange(n + 1) / n
+    Z, Y, X = np.meshgrid(r, r, r, indexing="ij")
+    return X.ravel(), Y.ravel(), Z.ravel()
+
+
+def test_advection_of_a_linear_field_is_exact():
+    """phi = a . x + b, uniform velocity U, variant 1 without evaporation: phi^(n+1) = phi^n - dt U . a exactly
+    (up to the GMRES tolerance |r| <= 1e-12 |b| of the step, about 1e-11 of max |phi| in the solution), and the
+    second pass (the same system: u_Gamma does not depend on phi) changes nothing beyond that."""
+    n = 9
+    wl = workloads.random_workload(n, 2, 1, geom="sphere", variant=1, dt=0.01)
+    U = np.array([0.3, -0.2, 0.5])
+    wl.u0 = np.repeat(U[:, None], (2 * n + 1) ** 3, axis=1).ravel()
+    wl.mdot = np.zeros((n + 1) ** 3)
+    x, y, z = _q1_xyz(n)
+    a = np.array([0.1, 0.05, -0.08])
+    wl.phi = a[0] * x + a[1] * y + a[2] * z + 0.01
+    op = make_op(wl)
+    phi, info = op.advect_levelset(2)
+    shift = wl.params["dt"] * float(U @ a)
+    assert info["converged"] and info["fp_iters"] == 2
+    assert np.abs(host(phi) - (wl.phi - shift)).max() < 1e-11
+    assert info["last_change"] < 1e-11 * np.sqrt(wl.phi.size)
+
+
+@pytest.mark.parametrize("n,geom,seed", [(8, "sphere", 3), (7, "spheres", 4)], ids=["sphere8", "ragged7"])
+def test_advection_fixed_point_variant1_against_oracle(n, geom, seed):
+    """Variant 1 (u_Gamma = u + mdot / rho(phi) n(phi) at the node: no iteration, GPU and oracle agree to 1e-13):
+    three fixed-point passes with dt = 0.01 (about 0.1 cells per step), element by element against the oracle's
+    direct solves.  Each GMRES solve stops at |r| <= 1e-12 |b| (b ~ M phi^n; the Jacobi-scaled operator is
+    mass-dominated, condition ~10), an error of about 1e-11 of |phi^n|: bar 1e-10 |phi^n| on phi^(n+1), and 1e-7
+    relative on the increment phi^(n+1) - phi^n (1 to 5 % of |phi^n|); the last change (a difference of two
+    solutions) to 1e-3."""
+    wl = workloads.random_workload(n, 2, seed, geom=geom, variant=1, dt=0.01)
+    op = make_op(wl)
+    phi, info = op.advect_levelset(3)
+    mesh_u = fe.Mesh(n, 2, 1.0)
+    ref, changes = geometry.advect_levelset(mesh_u, wl.phi, wl.u0, wl.mdot, wl.params, 3)
+    assert info["converged"] and info["fp_iters"] == 3
+    assert np.linalg.norm(host(phi) - ref) < 1e-10 * np.linalg.norm(wl.phi)
+    assert rel(host(phi) - wl.phi, ref - wl.phi) < 1e-7
+    assert info["last_change"] == pytest.approx(changes[-1], rel=1e-3, abs=1e-9)
+
+
+def test_advection_fixed_point_variant2_against_oracle():
+    """Variant 2 (closest points on the liquid-side isocontour, eps = h/2 so that it exists inside the drop; smooth
+    velocity): the closest-point iteration resolves u_Gamma only to its stopping resolution and may end on another
+    local minimum at a crease node, so the passes are checked one by one.  For K = 1, 2: the transport velocity of
+    pass K (left on the mesh) is the oracle's u_Gamma of clamp(phi^(K-1)) at the transport-velocity bar (flags agree
+    on >= 98 % of the nodes, >= 99 % of the nodes unflagged on both sides within 1e-6 of the velocity scale), and
+    phi^(K) is the oracle's Crank-Nicolson step with that velocity (the solve bar of the variant-1 test: 1e-10
+    |phi^n|, 1e-7 relative on the increment)."""
+    from oracle import transport
+    n = 8
+    wl = workloads.random_workload(n, 2, 9, geom="sphere", variant=2, dt=0.01, eps=0.5 / n)
+    X = workloads.node_coords(n, 2)
+    x, y, z = X[:, 0], X[:, 1], X[:, 2]
+    wl.u0 = np.concatenate([0.5 * np.sin(2 * np.pi * y), 0.4 * np.cos(2 * np.pi * x),
+                            0.3 * np.sin(2 * np.pi * (x + z))])
+    wl.mdot = np.full((n + 1) ** 3, 300.0)
+    op = make_op(wl)
+    mesh_u, mesh1 = fe.Mesh(n, 2, 1.0), fe.Mesh(n, 1, 1.0)
+    prev = np.clip(wl.phi, -1.0, 1.0)
+    for K in (1, 2):
+        phi, info = op.advect_levelset(K)
+        assert info["converged"] and info["fp_iters"] == K
+        ug, flags, _ = op.transport_velocity()
+        ug, flags = host(ug).reshape(3, -1), host(flags)
+        ugo, flo = transport.transport_velocity(mesh_u, np.clip(prev, -1.0, 1.0), wl.u0, wl.mdot, wl.params)
+        assert np.mean(flags == flo) >= 0.98
+        ok = (flags == 0) & (flo == 0)
+        diff = np.abs(ug[:, ok] - ugo[:, ok]).max(axis=0)
+        assert np.mean(diff <= 1e-6 * np.abs(ugo).max()) >= 0.99
+        ref = geometry.advection_step(mesh1, wl.phi, ug, wl.params["theta"], wl.params["dt"])
+        assert np.linalg.norm(host(phi) - ref) < 1e-10 * np.linalg.norm(wl.phi)
+        assert rel(host(phi) - wl.phi, ref - wl.phi) < 1e-7
+        prev = host(phi)
+
+
+def test_advection_tolerance_stops_the_fixed_point():
+    """With tol > 0 the passes stop once |phi^(k+1) - phi^(k)| <= tol, well before max_iters; the result is the
+    self-consistent level set of the oracle's fixed point (iterated to 1e-9) within the transport parity bar."""
+    n = 6
+    wl = workloads.random_workload(n, 2, 1, geom="sphere", variant=2, dt=0.05)
+    wl.u0 = np.repeat(np.array([0.2, 0.1, -0.1])[:, None], (2 * n + 1) ** 3, axis=1).ravel()
+    wl.mdot = np.full((n + 1) ** 3, 200.0)
+    op = make_op(wl)
+    phi, info = op.advect_levelset(20, tol=1e-9)
+    assert info["converged"] and 2 <= info["fp_iters"] < 20 and info["last_change"] <= 1e-9
+    ref, _ = geometry.advect_levelset(fe.Mesh(n, 2, 1.0), wl.phi, wl.u0, wl.mdot, wl.params, 8)
+    assert rel(host(phi) - wl.phi, ref - wl.phi) < 1e-4
+    phi0, info0 = op.advect_levelset(0)
+    assert info0["fp_iters"] == 0 and np.array_equal(host(phi0), np.clip(wl.phi, -1, 1))
