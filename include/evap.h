@@ -194,6 +194,28 @@ int evap_apply_adjoint(evap_handle h, const double* w, const double* w_p, const 
 int evap_solve(evap_handle h, const double* f, double* x, int mixed, int restart, double rtol, int max_iter,
                int* iters_out, double* relres_out, void* stream);
 
+/* Velocity-pressure system of Eq. (weakNavierStokes) with the Q1 pressure (Sec. 2.5, k_p = 1):
+ *   y   = A x - B^T p   [3 N_u]  (the pressure term -(div v, p); Dirichlet-constrained rows: y = x)
+ *   y_p = B x           [N_phi]  (the divergence row without its source: the continuity equation is B x = g with
+ *                                 g_j = sum_q W N1_j v_dil, Eq. continuity with the dilation rate of Eq. evaporDil)
+ * A the momentum operator of evap_apply_momentum, B its divergence row (Dirichlet entries of x read as 0).
+ * x [3 N_u], p [N_phi], y, y_p device arrays, FP64; x and y must not alias.  Faces that are not Dirichlet
+ * (dirichlet_faces) are open: the weak form's natural condition (zero traction) holds there. */
+int evap_apply_saddle(evap_handle h, const double* x, const double* p, double* y, double* y_p, void* stream);
+
+/* Solve [A, -B^T; B, 0] [x; p] = [f; g] (g the continuity right-hand side of the fields) by flexible GMRES(restart)
+ * with the block upper-triangular right preconditioner [A~, -B^T; 0, S~]: A~^(-1) a fixed budget of FP32 GMRES
+ * iterations on A with its Jacobi preconditioner, S~^(-1) = c_m K_(1/rho)^(-1) + M_(1/mu)^(-1) (Cahouet-Chabard, the
+ * pressure Laplacian weighted by 1/rho with p = 0 on the open faces, by CG, plus the lumped pressure mass weighted by
+ * 1/mu): the block-triangular preconditioner of Sec. 2.5 with its ILU velocity block replaced by the FP32 GMRES.
+ * x, p hold the initial guess on entry and the solution on exit.  Stops when ||[f; g] - K [x; p]|| <= rtol ||[f; g]||
+ * or after max_iter operator applications; iters (host, may be NULL): operator applications; relres (host, may be
+ * NULL): the final relative residual.  Synchronizes the stream.  EVAP_EINVAL if every face is Dirichlet (the pressure
+ * level is then undetermined), restart outside [1, 255], rtol <= 0 or max_iter < 1; EVAP_ENOTCONV if the cap was
+ * reached. */
+int evap_solve_saddle(evap_handle h, const double* f, double* x, double* p, int restart, double rtol, int max_iter,
+                      int* iters, double* relres, void* stream);
+
 /* Diagonal of the momentum operator [3 N_u] (1 on Dirichlet DoFs), the Jacobi preconditioner of evap_solve,
  * evaluated in FP32 arithmetic from the FP64 coefficient table and written as double. */
 int evap_jacobi_diagonal(evap_handle h, double* diag, void* stream);

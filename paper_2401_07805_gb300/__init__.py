@@ -58,6 +58,9 @@ SIGNATURES = {
     "evap_reinitialize": (_c_int, [_vp, _vp, _c_int, ctypes.POINTER(_c_int), ctypes.POINTER(_c_dbl), _vp]),
     "evap_advect_levelset": (_c_int, [_vp, _vp, _c_int, _c_dbl, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int),
                                       ctypes.POINTER(_c_dbl), _vp]),
+    "evap_apply_saddle": (_c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "evap_solve_saddle": (_c_int, [_vp, _vp, _vp, _vp, _c_int, _c_dbl, _c_int, ctypes.POINTER(_c_int),
+                                   ctypes.POINTER(_c_dbl), _vp]),
     "evap_surface_tension": (_c_int, [_vp, _vp, _vp, _c_dbl, _vp, _vp]),
     "evap_apply_momentum": (_c_int, [_vp, _c_int, _vp, _vp, _vp, _vp]),
     "evap_apply_levelset": (_c_int, [_vp, _c_int, _c_int, _vp, _vp, _vp]),
@@ -253,6 +256,29 @@ class Operator:
                                         ctypes.byref(lin), ctypes.byref(ch), _stream())
         _check(rc, "evap_advect_levelset", allow=() if raise_on_notconv else (-3,))
         return phi, dict(fp_iters=fp.value, lin_iters=lin.value, last_change=ch.value, converged=rc == 0)
+
+    def apply_saddle(self, x: torch.Tensor, p: torch.Tensor):
+        """(A x - B^T p, B x): the velocity-pressure operator of Eq. (weakNavierStokes) with the Q1 pressure."""
+        x = self._dev(x, 3 * self.n_u, torch.float64, "x")
+        p = self._dev(p, self.n_phi, torch.float64, "p")
+        y = torch.empty(3 * self.n_u, dtype=torch.float64, device=self.device)
+        yp = torch.empty(self.n_phi, dtype=torch.float64, device=self.device)
+        _check(lib().evap_apply_saddle(self._h, _ptr(x), _ptr(p), _ptr(y), _ptr(yp), _stream()), "evap_apply_saddle")
+        return y, yp
+
+    def solve_saddle(self, f: torch.Tensor, x0=None, p0=None, restart: int = 30, rtol: float = 1e-8,
+                     max_iter: int = 600, raise_on_notconv: bool = False):
+        """Solve [A, -B^T; B, 0] [x; p] = [f; g] (g from the fields' dilation rate); returns (x, p, info)."""
+        f = self._dev(f, 3 * self.n_u, torch.float64, "f")
+        x = (torch.zeros(3 * self.n_u, dtype=torch.float64, device=self.device) if x0 is None
+             else self._dev(x0, 3 * self.n_u, torch.float64, "x0").clone())
+        p = (torch.zeros(self.n_phi, dtype=torch.float64, device=self.device) if p0 is None
+             else self._dev(p0, self.n_phi, torch.float64, "p0").clone())
+        its, rel = ctypes.c_int(), ctypes.c_double()
+        rc = lib().evap_solve_saddle(self._h, _ptr(f), _ptr(x), _ptr(p), int(restart), float(rtol), int(max_iter),
+                                     ctypes.byref(its), ctypes.byref(rel), _stream())
+        _check(rc, "evap_solve_saddle", allow=() if raise_on_notconv else (-3,))
+        return x, p, dict(iters=its.value, relres=rel.value, converged=rc == 0)
 
     def surface_tension(self, n: torch.Tensor, kappa: torch.Tensor, alpha: float, out=None):
         """Surface-tension force [3 N_u] (Eq. surfaceTension, density-scaled delta) from Q1 normal and curvature."""

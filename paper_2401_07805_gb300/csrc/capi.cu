@@ -113,11 +113,12 @@ static void free_all(evap_mesh* h) {
     void* ptrs[] = {h->phi, h->u, h->mdot, h->u32, h->phi32, h->cell_code, h->table_index, h->table_count,
                     h->table, h->table32, h->qc, h->qc32, h->ugamma, h->ugamma32, h->cpp_flags, h->flag_count, h->band_list,
                     h->band_count, h->band_y, h->cpp_evals, h->ls_normal_store, h->ls_normal32_store, h->geo_ws, h->geo_elem, h->diag,
-                    h->diag32, h->ws, h->red};
+                    h->diag32, h->ws, h->red, h->cont_rhs, h->sd_ws, h->sd_red};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->red_host) cudaFreeHost(h->red_host);
     if (h->geo_host) cudaFreeHost(h->geo_host);
+    if (h->sd_host) cudaFreeHost(h->sd_host);
 }
 
 extern "C" {
@@ -238,6 +239,7 @@ int evap_set_fields(evap_handle h, const double* phi, const double* u, const dou
     if (rc) return rc;
     h->has_fields = true;
     h->diag_valid = false;
+    h->cont_valid = false;
     return EVAP_OK;
 }
 
@@ -337,6 +339,24 @@ int evap_advect_levelset(evap_handle h, double* phi, int max_iters, double tol, 
     if (max_iters < 0 || !(tol >= 0.0)) return fail(EVAP_EINVAL, "evap_advect_levelset: max_iters and tol must be >= 0");
     if (!h->has_fields) return fail(EVAP_ENOFIELDS, "evap_advect_levelset: call evap_set_fields first");
     return geo_advect_levelset(h, phi, max_iters, tol, fp_iters, lin_iters, last_change, (cudaStream_t)stream);
+}
+
+int evap_apply_saddle(evap_handle h, const double* x, const double* p, double* y, double* y_p, void* stream) {
+    if (!h || !x || !p || !y || !y_p) return fail(EVAP_EINVAL, "evap_apply_saddle: null argument");
+    if (x == y) return fail(EVAP_EINVAL, "evap_apply_saddle: x and y must not alias");
+    if (!h->has_fields) return fail(EVAP_ENOFIELDS, "evap_apply_saddle: call evap_set_fields first");
+    return launch_saddle_apply(h, x, p, y, y_p, (cudaStream_t)stream);
+}
+
+int evap_solve_saddle(evap_handle h, const double* f, double* x, double* p, int restart, double rtol, int max_iter,
+                      int* iters, double* relres, void* stream) {
+    if (!h || !f || !x || !p) return fail(EVAP_EINVAL, "evap_solve_saddle: null argument");
+    if (restart < 1 || restart > 255 || !(rtol > 0.0) || max_iter < 1)
+        return fail(EVAP_EINVAL, "evap_solve_saddle: need 1 <= restart <= 255, rtol > 0, max_iter >= 1");
+    if ((h->m.faces & 0x3Fu) == 0x3Fu)
+        return fail(EVAP_EINVAL, "evap_solve_saddle: every face is Dirichlet (the pressure level is undetermined)");
+    if (!h->has_fields) return fail(EVAP_ENOFIELDS, "evap_solve_saddle: call evap_set_fields first");
+    return solve_saddle(h, f, x, p, restart, rtol, max_iter, iters, relres, (cudaStream_t)stream);
 }
 
 int evap_surface_tension(evap_handle h, const double* n, const double* kappa, double alpha, double* f, void* stream) {

@@ -112,7 +112,18 @@ struct evap_mesh {
     double* red = nullptr;   // device reduction scratch
     double* red_host = nullptr;  // pinned host mirror
     size_t red_len = 0;
+    // velocity-pressure system: continuity right-hand side of the current fields, the flexible GMRES workspace
+    // (device) and its reduction scratch with a pinned host mirror
+    double* cont_rhs = nullptr;
+    bool cont_valid = false;
+    void* sd_ws = nullptr;
+    size_t sd_bytes = 0;
+    double* sd_red = nullptr;
+    double* sd_host = nullptr;
+    size_t sd_red_len = 0;
 };
+
+#include <functional>  // host-side declarations below
 
 namespace evap {
 
@@ -157,6 +168,20 @@ int geo_advect_levelset(evap_mesh* h, double* phi, int max_iters, double tol, in
                         double* last_change, cudaStream_t s);
 // y = A x with the advection element matrices of the current fixed-point pass (h->geo_elem, [64][ncell]).
 int geo_advect_elem_apply(evap_mesh* h, const double* x, double* y, cudaStream_t s);
+// Jacobi diagonal (in the geometry workspace, valid until the next geometry call) for CG on the pressure Schur
+// approximation B diag(A)^(-1) B^T, and the Q1 CG engine of the geometry sub-solver for an arbitrary SPD apply.
+int geo_schur_setup(evap_mesh* h, double** diag, cudaStream_t s);
+int geo_cg(evap_mesh* h, const std::function<int(const double*, double*)>& apply, const double* b, const double* d,
+           double* x, double rtol, double atol, int max_iter, int* iters, cudaStream_t s);
+// velocity-pressure coupling (saddle.cu)
+int launch_pressure_gradient(evap_mesh* h, const double* p, double scale, double* y, cudaStream_t s);
+int continuity_rhs(evap_mesh* h, const double** g, cudaStream_t s);
+int launch_saddle_apply(evap_mesh* h, const double* x, const double* p, double* y, double* yp, cudaStream_t s);
+// y_p += B x (the divergence row without its source; Dirichlet entries of x read as 0)
+int launch_divergence(evap_mesh* h, const double* x, double* yp, cudaStream_t s);
+// z = S~^(-1) r by at most cg_iters CG iterations on S~ = B diag(A)^(-1) B^T with the Jacobi diagonal d of
+// geo_schur_setup (t: velocity scratch [3 N_u])
+int schur_apply(evap_mesh* h, const double* r, double* z, const double* d, double* t, int cg_iters, cudaStream_t s);
 int launch_surface_tension(evap_mesh* h, const double* nf, const double* kappa, double alpha, double* out,
                            cudaStream_t s);
 int launch_diagonal_into(evap_mesh* h, float* acc, double* out, cudaStream_t s);
@@ -167,6 +192,9 @@ int solve_gmres(evap_mesh* h, const double* f, double* x, int mixed, int restart
 // stops at |r| <= max(rtol |b|, atol).  *iters is incremented by the operator applications; *relres = |r| / |b|.
 int solve_advect_gmres(evap_mesh* h, const double* b, const double* diag, double* x, int restart, double rtol,
                        double atol, int max_iter, int* iters, double* relres, cudaStream_t s);
+// Flexible GMRES on the velocity-pressure system K [x; p] = [f; g] (see evap_solve_saddle).
+int solve_saddle(evap_mesh* h, const double* f, double* x, double* p, int restart, double rtol, int max_iter,
+                 int* iters, double* relres, cudaStream_t s);
 
 // small vector kernels used by several files
 template <typename T>

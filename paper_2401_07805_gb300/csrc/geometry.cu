@@ -13,6 +13,7 @@
 // sums (x, then y, then z: 93 FMA per node) instead of per-cell quadrature.
 #include <algorithm>
 #include <cmath>
+#include <functional>
 
 #include "physics.cuh"
 
@@ -747,6 +748,60 @@ int geo_advect_levelset(evap_mesh* h, double* phi, int max_iters, double tol, in
     if (lin_iters) *lin_iters = lin;
     if (last_change) *last_change = change;
     return status;
+}
+
+// ------------------------------------------------------ pressure Schur complement of the velocity-pressure system
+// Jacobi diagonal for the CG on S~ = B diag(A)^(-1) B^T (the Schur approximation of the velocity-pressure solve):
+// with the velocity block dominated by rho c_m M, S~ ~ K_(1/rho) / c_m, so d_i = (K_(1/rho))_ii / c_m, K_(1/rho) the Q1
+// stiffness weighted by 1/rho(phi) at the 2-point Gauss points.
+__global__ void __launch_bounds__(128) k_schur_diag(MeshArgs<double> m, Basis<double> bas, const double* __restrict__ phi,
+                                                    double* __restrict__ d) {
+    const int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (cell >= m.ncell) return;
+    Q1Cell c;
+    int cx, cy, cz;
+    q1_cell_nodes(cell, m.n, c, cx, cy, cz);
+    double pv[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) pv[j] = phi[c.node[j]];
+    double out[8] = {};
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        double N[8], G[8][3];
+        q1_weights(bas.g2t, q, m.inv_h, N, G);
+        const double W = bas.g2w[q & 1] * bas.g2w[(q >> 1) & 1] * bas.g2w[q >> 2] * m.vol_w;
+        double ph = 0.0, g0 = 0.0, g1 = 0.0, g2 = 0.0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            ph += N[j] * pv[j];
+            g0 += G[j][0] * pv[j];
+            g1 += G[j][1] * pv[j];
+            g2 += G[j][2] * pv[j];
+        }
+        const double wr = W / (material(ph, g0, g1, g2, m).rho * m.c_mass);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) out[j] += wr * (G[j][0] * G[j][0] + G[j][1] * G[j][1] + G[j][2] * G[j][2]);
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) atomicAdd(&d[c.node[j]], out[j]);
+}
+
+int geo_schur_setup(evap_mesh* h, double** diag, cudaStream_t s) {
+    int rc = geo_workspace(h);
+    if (rc) return rc;
+    CgSpace w = cg_space(h);
+    EVAP_CUDA(cudaMemsetAsync(w.d, 0, h->m.Nphi * sizeof(double), s));
+    k_schur_diag<<<blocks_for(h->m.ncell, 128, 1LL << 40), 128, 0, s>>>(h->m, h->b, h->phi, w.d);
+    EVAP_CHECK_LAUNCH("schur_diag");
+    *diag = w.d;
+    return EVAP_OK;
+}
+
+int geo_cg(evap_mesh* h, const std::function<int(const double*, double*)>& apply, const double* b, const double* d,
+           double* x, double rtol, double atol, int max_iter, int* iters, cudaStream_t s) {
+    int rc = geo_workspace(h);
+    if (rc) return rc;
+    return cg_solve(h, apply, b, d, x, rtol, atol, max_iter, iters, nullptr, s);
 }
 
 }  // namespace evap

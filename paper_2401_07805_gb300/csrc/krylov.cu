@@ -683,4 +683,229 @@ int solve_advect_gmres(evap_mesh* h, const double* b, const double* diag, double
     return res <= target ? EVAP_OK : EVAP_ENOTCONV;
 }
 
+// ------------------------------------------------------------ velocity-pressure system: flexible GMRES
+// K [x; p] = [A x - B^T p; B x] = [f; g] with the block upper-triangular right preconditioner
+//   P = [[A~, -B^T], [0, S~]]:   z_p = S~^(-1) v_p,   z_u = A~^(-1) (v_u + B^T z_p)
+// (K P^(-1) is unit block lower-triangular for exact blocks).  A~^(-1): a fixed budget of FP32 GMRES iterations on the
+// momentum operator with its Jacobi preconditioner (the mixed solve's inner method); S~^(-1): CG on
+// B diag(A)^(-1) B^T (schur_apply).  Both are inexact and vary between applications, so the outer method stores the
+// preconditioned directions (flexible GMRES); the outer vectors are FP64 [x (3 N_u) | p (N_phi)].
+constexpr int SADDLE_INNER_M = 10;      // FP32 GMRES applications per velocity-block solve
+constexpr double SADDLE_INNER_TOL = 1e-2;
+constexpr int SADDLE_SCHUR_CG = 24;     // CG iterations per pressure Poisson solve
+
+// v = b - v
+__global__ void k_residual_inplace(const double* __restrict__ b, double* __restrict__ v, int64_t N) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x)
+        v[k] = b[k] - v[k];
+}
+
+__global__ void k_scale_vec(double* __restrict__ v, const double* __restrict__ nrm2, int64_t N) {
+    const double inv = 1.0 / sqrt(*nrm2);
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x)
+        v[k] *= inv;
+}
+
+// [x; p] += sum_i y[i] Z_i
+__global__ void k_update_split(const double* __restrict__ Z, int64_t ld, const double* __restrict__ y, int nv,
+                               double* x, double* p, int64_t Nu3, int64_t N) {
+    __shared__ double ys[256];
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) ys[i] = y[i];
+    __syncthreads();
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int i = 0; i < nv; ++i) s += ys[i] * Z[i * ld + k];
+        if (k < Nu3) x[k] += s;
+        else p[k - Nu3] += s;
+    }
+}
+
+struct SaddleSpace {
+    const double* sdiag;    // Jacobi diagonal of the pressure Schur approximation
+    double *V, *Z, *b, *t;  // outer basis [(m+1) ld], directions [m ld], right-hand side [ld], velocity scratch [3 N_u]
+    float *V32, *w32, *z32, *r32, *d32;  // inner FP32 workspace
+};
+
+// z = P^(-1) v
+static int saddle_precond(Ctx& inner, SaddleSpace& sp, const double* v, double* z) {
+    evap_mesh* h = inner.h;
+    cudaStream_t s = inner.s;
+    const int64_t Nu3 = 3 * h->m.Nu;
+    const int G = blocks_for(Nu3, 256);
+    int rc = schur_apply(h, v + Nu3, z + Nu3, sp.sdiag, sp.t, SADDLE_SCHUR_CG, s);
+    if (rc) return rc;
+    EVAP_CUDA(cudaMemcpyAsync(sp.t, v, Nu3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if ((rc = launch_pressure_gradient(h, z + Nu3, 1.0, sp.t, s))) return rc;
+    // velocity block: FP32 GMRES on t / |t| from zero, then z_u = |t| d
+    if ((rc = norm2_dev<double>(inner, sp.t, inner.dnorm))) return rc;
+    k_scaled_to_float<<<G, 256, 0, s>>>(sp.t, inner.dnorm, sp.r32, Nu3);
+    EVAP_CHECK_LAUNCH("saddle_to32");
+    EVAP_CUDA(cudaMemsetAsync(sp.d32, 0, Nu3 * sizeof(float), s));
+    int its = 0;
+    double res = 0.0;
+    if ((rc = gmres<float>(inner, SADDLE_INNER_M, sp.r32, sp.d32, true, h->diag32, sp.V32, sp.w32, sp.z32,
+                           SADDLE_INNER_TOL, SADDLE_INNER_M, &its, &res)))
+        return rc;
+    if ((rc = norm2_dev<double>(inner, sp.t, inner.dnorm))) return rc;
+    EVAP_CUDA(cudaMemsetAsync(z, 0, Nu3 * sizeof(double), s));
+    k_refine<<<G, 256, 0, s>>>(z, sp.d32, inner.dnorm, Nu3);
+    EVAP_CHECK_LAUNCH("saddle_velocity");
+    return EVAP_OK;
+}
+
+int solve_saddle(evap_mesh* h, const double* f, double* x, double* p, int m, double rtol, int max_iter, int* iters,
+                 double* relres, cudaStream_t s) {
+    int rc = launch_diagonal(h, s);
+    if (rc) return rc;
+    const double* g = nullptr;
+    if ((rc = continuity_rhs(h, &g, s))) return rc;
+    double* sdiag = nullptr;
+    if ((rc = geo_schur_setup(h, &sdiag, s))) return rc;
+    const int64_t Nu3 = 3 * h->m.Nu, Np = h->m.Nphi, N = Nu3 + Np;
+    const int64_t ld = (N + 63) / 64 * 64, ldu = (Nu3 + 63) / 64 * 64;
+    // inner (FP32 velocity GMRES) workspace and reduction scratch: the mesh's Krylov buffers
+    const size_t fV = al256((size_t)(SADDLE_INNER_M + 1) * ldu * sizeof(float)), fN = al256((size_t)ldu * sizeof(float));
+    Ctx inner;
+    if ((rc = prepare(h, OP_MOMENTUM, SADDLE_INNER_M, Nu3, ldu, fV + 4 * fN, s, inner))) return rc;
+    SaddleSpace sp;
+    sp.sdiag = sdiag;
+    char* ib = (char*)h->ws;
+    sp.V32 = (float*)ib;
+    sp.w32 = (float*)(ib + fV);
+    sp.z32 = (float*)(ib + fV + fN);
+    sp.r32 = (float*)(ib + fV + 2 * fN);
+    sp.d32 = (float*)(ib + fV + 3 * fN);
+    // outer workspace and its own reduction scratch (the inner solve reuses the mesh's)
+    const size_t dV = al256((size_t)(m + 1) * ld * sizeof(double)), dZ = al256((size_t)m * ld * sizeof(double));
+    const size_t dN = al256((size_t)ld * sizeof(double)), dU = al256((size_t)Nu3 * sizeof(double));
+    const size_t bytes = dV + dZ + dN + dU;
+    if (h->sd_bytes < bytes) {
+        if (h->sd_ws) cudaFree(h->sd_ws);
+        h->sd_ws = nullptr;
+        h->sd_bytes = 0;
+        EVAP_CUDA(cudaMalloc(&h->sd_ws, bytes));
+        h->sd_bytes = bytes;
+    }
+    char* ob = (char*)h->sd_ws;
+    sp.V = (double*)ob;
+    sp.Z = (double*)(ob + dV);
+    sp.b = (double*)(ob + dV + dZ);
+    sp.t = (double*)(ob + dV + dZ + dN);
+    const size_t red_need = (size_t)(m + 2) * RED_BLOCKS + 4 * (m + 2) + 8;
+    if (h->sd_red_len < red_need) {
+        if (h->sd_red) cudaFree(h->sd_red);
+        if (h->sd_host) cudaFreeHost(h->sd_host);
+        h->sd_red = nullptr;
+        h->sd_host = nullptr;
+        h->sd_red_len = 0;
+        EVAP_CUDA(cudaMalloc(&h->sd_red, red_need * sizeof(double)));
+        EVAP_CUDA(cudaMallocHost(&h->sd_host, red_need * sizeof(double)));
+        h->sd_red_len = red_need;
+    }
+    Ctx c;
+    c.h = h;
+    c.op = OP_MOMENTUM;  // not used: the outer operator is applied explicitly
+    c.s = s;
+    c.N = N;
+    c.ld = ld;
+    c.partial = h->sd_red;
+    c.dcol = h->sd_red + (size_t)(m + 2) * RED_BLOCKS;
+    c.dnorm = c.dcol + 2 * (m + 2);
+    c.dsc2 = c.dnorm + 8;
+    c.cnt = reinterpret_cast<unsigned*>(c.dsc2 + (m + 2));
+    c.hcol = h->sd_host;
+    c.hsc2 = h->sd_host + red_need - (m + 2);
+    EVAP_CUDA(cudaMemsetAsync(c.cnt, 0, (size_t)(m + 2) * sizeof(unsigned), s));
+    for (int i = 0; i < m + 2; ++i) c.hsc2[i] = 1.0;  // normalized basis: unit scales
+    EVAP_CUDA(cudaMemcpyAsync(c.dsc2, c.hsc2, (size_t)(m + 2) * sizeof(double), cudaMemcpyHostToDevice, s));
+    // b = [f; g]
+    EVAP_CUDA(cudaMemcpyAsync(sp.b, f, Nu3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    EVAP_CUDA(cudaMemcpyAsync(sp.b + Nu3, g, Np * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if ((rc = norm2_dev<double>(c, sp.b, c.dnorm))) return rc;
+    if ((rc = fetch(c, c.dnorm, 1, c.hcol))) return rc;
+    const double bn = std::sqrt(c.hcol[0]);
+    const double target = rtol * bn;
+    const int G = blocks_for(N, 256);
+    std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), yv(m);
+    int used = 0;
+    double beta = 0.0;
+    while (true) {
+        if ((rc = launch_saddle_apply(h, x, p, sp.V, sp.V + Nu3, s))) return rc;
+        ++used;
+        k_residual_inplace<<<G, 256, 0, s>>>(sp.b, sp.V, N);
+        EVAP_CHECK_LAUNCH("saddle_residual");
+        if ((rc = norm2_dev<double>(c, sp.V, c.dnorm))) return rc;
+        if ((rc = fetch(c, c.dnorm, 1, c.hcol))) return rc;
+        beta = std::sqrt(c.hcol[0]);
+        if (beta <= target || used >= max_iter || !(beta > 0.0)) break;
+        k_scale_vec<<<G, 256, 0, s>>>(sp.V, c.dnorm, N);
+        EVAP_CHECK_LAUNCH("saddle_scale");
+        std::fill(gv.begin(), gv.end(), 0.0);
+        gv[0] = beta;
+        int j = 0;
+        for (; j < m; ++j) {
+            double* Vj = sp.V + (int64_t)j * ld;
+            double* Zj = sp.Z + (int64_t)j * ld;
+            double* Wn = sp.V + (int64_t)(j + 1) * ld;
+            if ((rc = saddle_precond(inner, sp, Vj, Zj))) return rc;
+            if ((rc = launch_saddle_apply(h, Zj, Zj + Nu3, Wn, Wn + Nu3, s))) return rc;
+            ++used;
+            const int nv = j + 1;
+            double* col = &H[(size_t)j * (m + 1)];
+            if ((rc = cgs_pass<double>(c, sp.V, Wn, nv, c.dcol, true))) return rc;
+            EVAP_CUDA(cudaMemcpyAsync(c.hcol, c.dcol, (size_t)(nv + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
+            EVAP_CUDA(cudaMemcpyAsync(c.hcol + m + 2, c.dnorm, sizeof(double), cudaMemcpyDeviceToHost, s));
+            EVAP_CUDA(cudaStreamSynchronize(s));
+            for (int i = 0; i < nv; ++i) col[i] = c.hcol[i];
+            double after = c.hcol[m + 2];
+            if (after < REORTH64 * c.hcol[nv]) {
+                if ((rc = cgs_pass<double>(c, sp.V, Wn, nv, c.dcol + (m + 2), false))) return rc;
+                EVAP_CUDA(cudaMemcpyAsync(c.hcol, c.dcol + (m + 2), (size_t)nv * sizeof(double),
+                                          cudaMemcpyDeviceToHost, s));
+                EVAP_CUDA(cudaMemcpyAsync(c.hcol + m + 2, c.dnorm, sizeof(double), cudaMemcpyDeviceToHost, s));
+                EVAP_CUDA(cudaStreamSynchronize(s));
+                for (int i = 0; i < nv; ++i) col[i] += c.hcol[i];
+                after = c.hcol[m + 2];
+            }
+            const double hn = std::sqrt(after);
+            col[j + 1] = hn;
+            if (hn > 0.0) {
+                k_scale_vec<<<G, 256, 0, s>>>(Wn, c.dnorm, N);
+                EVAP_CHECK_LAUNCH("saddle_scale");
+            }
+            for (int i = 0; i < j; ++i) {
+                const double t0 = cs[i] * col[i] + sn[i] * col[i + 1];
+                col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+                col[i] = t0;
+            }
+            const double rr = std::hypot(col[j], col[j + 1]);
+            cs[j] = rr > 0.0 ? col[j] / rr : 1.0;
+            sn[j] = rr > 0.0 ? col[j + 1] / rr : 0.0;
+            col[j] = rr;
+            col[j + 1] = 0.0;
+            gv[j + 1] = -sn[j] * gv[j];
+            gv[j] = cs[j] * gv[j];
+            if (std::fabs(gv[j + 1]) <= target || used >= max_iter || !(hn > 0.0)) {
+                ++j;
+                break;
+            }
+        }
+        const int k = j;
+        for (int i = k - 1; i >= 0; --i) {
+            double sum = gv[i];
+            for (int l = i + 1; l < k; ++l) sum -= H[(size_t)l * (m + 1) + i] * yv[l];
+            yv[i] = sum / H[(size_t)i * (m + 1) + i];
+        }
+        for (int i = 0; i < k; ++i) c.hcol[i] = yv[i];
+        EVAP_CUDA(cudaMemcpyAsync(c.dcol, c.hcol, k * sizeof(double), cudaMemcpyHostToDevice, s));
+        k_update_split<<<G, 256, 0, s>>>(sp.Z, ld, c.dcol, k, x, p, Nu3, N);
+        EVAP_CHECK_LAUNCH("saddle_update");
+        EVAP_CUDA(cudaStreamSynchronize(s));
+    }
+    EVAP_CUDA(cudaStreamSynchronize(s));
+    if (iters) *iters = used;
+    if (relres) *relres = bn > 0.0 ? beta / bn : 0.0;
+    return beta <= target ? EVAP_OK : EVAP_ENOTCONV;
+}
+
 }  // namespace evap

@@ -14,14 +14,9 @@
 //   scatter  atomic add into y (constrained rows hold y = x, written by the init kernel)
 // Thread layout: one thread per quadrature point, CB cells per block; sweeps go through shared memory, each thread
 // keeps its rows/columns of the 1D matrices in registers.
-#include "evap_internal.cuh"
+#include "physics.cuh"
 
 namespace evap {
-
-__device__ __forceinline__ bool constrained_node(int gx, int gy, int gz, int M, unsigned f) {
-    return ((f & 1u) && gx == 0) || ((f & 2u) && gx == M - 1) || ((f & 4u) && gy == 0) ||
-           ((f & 8u) && gy == M - 1) || ((f & 16u) && gz == 0) || ((f & 32u) && gz == M - 1);
-}
 
 // y = x on Dirichlet DoFs, 0 elsewhere; y_p = 0.  Each warp walks whole x-lines (component c, gy, gz) of M nodes,
 // so the line's position is split once per warp and the lanes only test their own gx.

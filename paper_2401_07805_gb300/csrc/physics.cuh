@@ -5,6 +5,13 @@
 
 namespace evap {
 
+// Whether node (gx, gy, gz) of an M^3 grid lies on a face selected by the bit mask f (bit 2 axis: face 0, bit
+// 2 axis + 1: face M - 1).
+__device__ __forceinline__ bool constrained_node(int gx, int gy, int gz, int M, unsigned f) {
+    return ((f & 1u) && gx == 0) || ((f & 2u) && gx == M - 1) || ((f & 4u) && gy == 0) ||
+           ((f & 8u) && gy == M - 1) || ((f & 16u) && gz == 0) || ((f & 32u) && gz == M - 1);
+}
+
 // Points of the 2-point Gauss rule on [0, 1], (1 -+ 1/sqrt 3) / 2 (the literal of the host basis).
 __host__ __device__ constexpr double g2_point(int i) {
     return i ? 0.5 * (1.0 + 0.5773502691896257645091488) : 0.5 * (1.0 - 0.5773502691896257645091488);

@@ -1,0 +1,299 @@
+// Velocity-pressure coupling of Eq. (weakNavierStokes) with the Q1 pressure of Sec. 2.5 (k_p = 1), FP64:
+//   pressure term of the momentum row   y_(c,i) += s sum_q W p_h(x_q) d_c N_i(x_q)      (s = -1: -(div v, p))
+//   continuity right-hand side         g_j = sum_q W N1_j v_dil                           (Eq. continuity, evaporDil)
+//   saddle-point apply                 [y; y_p] = [A x - B^T p; B x]
+// with B the divergence row of the momentum apply (velocity Gauss rule, Dirichlet entries of x read as 0) and
+// Dirichlet-constrained velocity rows left to the momentum apply (identity), so B^T p vanishes there.
+#include "physics.cuh"
+
+namespace evap {
+
+// B^T p, scaled by s, added to y: one thread per velocity quadrature point, CB cells per block.  The pressure is
+// interpolated at the point from the cell's 8 Q1 nodes; the test with d_c N_i is the transpose of the momentum
+// apply's gradient (collocation derivative at the Gauss points along c, then S^T along z, y, x), so B^T here is
+// the exact transpose of the divergence row.
+template <int P, int CB>
+__global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
+    k_pressure_gradient(MeshArgs<double> m, Basis<double> bas, const double* __restrict__ p, double s,
+                        double* __restrict__ y) {
+    constexpr int Q = P + 1, NQ = Q * Q * Q;
+    __shared__ double sS[Q][Q], sDc[Q][Q], sN1[Q][2];
+    __shared__ double val[CB][NQ];
+    __shared__ double buf[2][CB][3][NQ];
+    const int tid = threadIdx.x;
+    const int lc = tid / NQ, t = tid % NQ;
+    const int64_t cell = (int64_t)blockIdx.x * CB + lc;
+    const bool active = cell < m.ncell;
+    if (tid < Q * Q) {
+        sS[tid / Q][tid % Q] = bas.S[tid / Q][tid % Q];
+        sDc[tid / Q][tid % Q] = bas.Dc[tid / Q][tid % Q] * m.inv_h;
+    }
+    if (tid < 2 * Q) sN1[tid / 2][tid % 2] = bas.N1[tid / 2][tid % 2];
+    __syncthreads();
+    const int a = t % Q, b = (t / Q) % Q, c = t / (Q * Q);
+    const int n = m.n;
+    int cx = 0, cy = 0, cz = 0;
+    if (active) {
+        cx = (int)(cell % n);
+        cy = (int)((cell / n) % n);
+        cz = (int)(cell / ((int64_t)n * n));
+        const int64_t m1 = n + 1;
+        double pq = 0.0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int ja = j & 1, jb = (j >> 1) & 1, jc = j >> 2;
+            pq += sN1[a][ja] * sN1[b][jb] * sN1[c][jc] * p[(cx + ja) + m1 * ((cy + jb) + m1 * (cz + jc))];
+        }
+        val[lc][t] = s * bas.w[a] * bas.w[b] * bas.w[c] * m.vol_w * pq;
+    }
+    __syncthreads();
+    if (active) {
+        double d0 = 0.0, d1 = 0.0, d2 = 0.0;
+#pragma unroll
+        for (int r = 0; r < Q; ++r) {
+            d0 += sDc[r][a] * val[lc][r + Q * (b + Q * c)];
+            d1 += sDc[r][b] * val[lc][a + Q * (r + Q * c)];
+            d2 += sDc[r][c] * val[lc][a + Q * (b + Q * r)];
+        }
+        buf[0][lc][0][t] = d0;
+        buf[0][lc][1][t] = d1;
+        buf[0][lc][2][t] = d2;
+    }
+    __syncthreads();
+    if (active)
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            double v = 0.0;
+#pragma unroll
+            for (int q = 0; q < Q; ++q) v += sS[q][c] * buf[0][lc][f][a + Q * (b + Q * q)];
+            buf[1][lc][f][t] = v;
+        }
+    __syncthreads();
+    if (active)
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            double v = 0.0;
+#pragma unroll
+            for (int q = 0; q < Q; ++q) v += sS[q][b] * buf[1][lc][f][a + Q * (q + Q * c)];
+            buf[0][lc][f][t] = v;
+        }
+    __syncthreads();
+    if (!active) return;
+    const int M = m.M;
+    const int gx = P * cx + a, gy = P * cy + b, gz = P * cz + c;
+    if (constrained_node(gx, gy, gz, M, m.faces)) return;
+    const int64_t gidx = gx + (int64_t)M * (gy + (int64_t)M * gz);
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+        double v = 0.0;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) v += sS[q][a] * buf[0][lc][f][q + Q * (b + Q * c)];
+        atomicAdd(&y[f * m.Nu + gidx], v);
+    }
+}
+
+// g_j += sum_q N1_j(x_q) (W v_dil)_q over the cell's velocity Gauss points, from the cached coefficient slot 18.
+template <int P>
+__global__ void __launch_bounds__(128) k_continuity_rhs(MeshArgs<double> m, Basis<double> bas,
+                                                        const double* __restrict__ qc, double* __restrict__ g) {
+    constexpr int Q = P + 1, NQ = Q * Q * Q;
+    const int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (cell >= m.ncell) return;
+    const int n = m.n;
+    const int cx = (int)(cell % n), cy = (int)((cell / n) % n), cz = (int)(cell / ((int64_t)n * n));
+    const double* v = qc + cell * QC_K * NQ + 18 * NQ;
+    double out[8] = {};
+    for (int t = 0; t < NQ; ++t) {
+        const int a = t % Q, b = (t / Q) % Q, c = t / (Q * Q);
+        const double vt = v[t];
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            out[j] += bas.N1[a][j & 1] * bas.N1[b][(j >> 1) & 1] * bas.N1[c][j >> 2] * vt;
+    }
+    const int64_t m1 = n + 1;
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+        atomicAdd(&g[(cx + (j & 1)) + m1 * ((cy + ((j >> 1) & 1)) + m1 * (cz + (j >> 2)))], out[j]);
+}
+
+// y_p += B x: the divergence row of the momentum apply without its source, sum_q W N1_j (div x)(x_q); values at the
+// points by S sweeps (x, y, z), the divergence by the collocation derivative, the Q1 test by three sweeps of N1.
+template <int P, int CB>
+__global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
+    k_divergence(MeshArgs<double> m, Basis<double> bas, const double* __restrict__ x, double* __restrict__ yp) {
+    constexpr int Q = P + 1, NQ = Q * Q * Q;
+    __shared__ double sS[Q][Q], sDc[Q][Q], sN1[Q][2];
+    __shared__ double buf[2][3][CB][NQ];
+    __shared__ double rbuf[CB][NQ], q1a[CB][2 * Q * Q], q1b[CB][4 * Q];
+    const int tid = threadIdx.x;
+    const int lc = tid / NQ, t = tid % NQ;
+    const int64_t cell = (int64_t)blockIdx.x * CB + lc;
+    const bool active = cell < m.ncell;
+    if (tid < Q * Q) {
+        sS[tid / Q][tid % Q] = bas.S[tid / Q][tid % Q];
+        sDc[tid / Q][tid % Q] = bas.Dc[tid / Q][tid % Q] * m.inv_h;
+    }
+    if (tid < 2 * Q) sN1[tid / 2][tid % 2] = bas.N1[tid / 2][tid % 2];
+    const int a = t % Q, b = (t / Q) % Q, c = t / (Q * Q);
+    const int n = m.n, M = m.M;
+    int cx = 0, cy = 0, cz = 0;
+    if (active) {
+        cx = (int)(cell % n);
+        cy = (int)((cell / n) % n);
+        cz = (int)(cell / ((int64_t)n * n));
+        const int gx = P * cx + a, gy = P * cy + b, gz = P * cz + c;
+        const int64_t gidx = gx + (int64_t)M * (gy + (int64_t)M * gz);
+        const bool cons = constrained_node(gx, gy, gz, M, m.faces);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) buf[0][k][lc][t] = cons ? 0.0 : x[k * m.Nu + gidx];
+    }
+    __syncthreads();
+    if (active)
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            double v = 0.0;
+#pragma unroll
+            for (int k = 0; k < Q; ++k) v += sS[a][k] * buf[0][f][lc][k + Q * (b + Q * c)];
+            buf[1][f][lc][t] = v;
+        }
+    __syncthreads();
+    if (active)
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            double v = 0.0;
+#pragma unroll
+            for (int k = 0; k < Q; ++k) v += sS[b][k] * buf[1][f][lc][a + Q * (k + Q * c)];
+            buf[0][f][lc][t] = v;
+        }
+    __syncthreads();
+    if (active)
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            double v = 0.0;
+#pragma unroll
+            for (int k = 0; k < Q; ++k) v += sS[c][k] * buf[0][f][lc][a + Q * (b + Q * k)];
+            buf[1][f][lc][t] = v;
+        }
+    __syncthreads();
+    if (active) {
+        double tr = 0.0;
+#pragma unroll
+        for (int r = 0; r < Q; ++r)
+            tr += sDc[a][r] * buf[1][0][lc][r + Q * (b + Q * c)] + sDc[b][r] * buf[1][1][lc][a + Q * (r + Q * c)] +
+                  sDc[c][r] * buf[1][2][lc][a + Q * (b + Q * r)];
+        rbuf[lc][t] = bas.w[a] * bas.w[b] * bas.w[c] * m.vol_w * tr;
+    }
+    __syncthreads();
+    if (active && t < 2 * Q * Q) {  // x-sweep: [jx][qy][qz]
+        const int jx = t & 1, qy = (t >> 1) % Q, qz = (t >> 1) / Q;
+        double v = 0.0;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) v += sN1[q][jx] * rbuf[lc][q + Q * (qy + Q * qz)];
+        q1a[lc][t] = v;
+    }
+    __syncthreads();
+    if (active && t < 4 * Q) {  // y-sweep: [jx][jy][qz]
+        const int jx = t & 1, jy = (t >> 1) & 1, qz = t >> 2;
+        double v = 0.0;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) v += sN1[q][jy] * q1a[lc][jx + 2 * (q + Q * qz)];
+        q1b[lc][t] = v;
+    }
+    __syncthreads();
+    if (active && t < 8) {  // z-sweep: Q1 node (jx, jy, jz)
+        const int jx = t & 1, jy = (t >> 1) & 1, jz = t >> 2;
+        double v = 0.0;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) v += sN1[q][jz] * q1b[lc][jx + 2 * (jy + 2 * q)];
+        const int64_t m1 = n + 1;
+        atomicAdd(&yp[(cx + jx) + m1 * ((cy + jy) + m1 * (cz + jz))], v);
+    }
+}
+
+// t /= diag (the FP64 Jacobi diagonal of the velocity block)
+__global__ void k_div_diag(double* __restrict__ t, const double* __restrict__ diag, int64_t N) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        t[i] /= diag[i];
+}
+
+__global__ void k_add_vec(double* __restrict__ y, const double* __restrict__ g, int64_t N) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] += g[i];
+}
+
+int launch_pressure_gradient(evap_mesh* h, const double* p, double s, double* y, cudaStream_t st) {
+    const MeshArgs<double>& m = h->m;
+    if (m.P == 2) {
+        constexpr int CB = 8;
+        k_pressure_gradient<2, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 27, 0, st>>>(m, h->b, p, s, y);
+    } else {
+        constexpr int CB = 4;
+        k_pressure_gradient<3, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 64, 0, st>>>(m, h->b, p, s, y);
+    }
+    EVAP_CHECK_LAUNCH("pressure_gradient");
+    return EVAP_OK;
+}
+
+int launch_divergence(evap_mesh* h, const double* x, double* yp, cudaStream_t st) {
+    const MeshArgs<double>& m = h->m;
+    if (m.P == 2) {
+        constexpr int CB = 8;
+        k_divergence<2, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 27, 0, st>>>(m, h->b, x, yp);
+    } else {
+        constexpr int CB = 4;
+        k_divergence<3, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 64, 0, st>>>(m, h->b, x, yp);
+    }
+    EVAP_CHECK_LAUNCH("divergence");
+    return EVAP_OK;
+}
+
+// z = S~^(-1) r, S~ = B diag(A)^(-1) B^T (a SIMPLE-type approximation of the Schur complement B A^(-1) B^T: it keeps
+// the discrete B, so the pressure nodes of open faces are treated like every other node), by CG with the Jacobi
+// diagonal d of geo_schur_setup, at most cg_iters iterations (an inexact solve: the outer method is flexible).
+int schur_apply(evap_mesh* h, const double* r, double* z, const double* d, double* t, int cg_iters, cudaStream_t st) {
+    const int64_t Nu3 = 3 * h->m.Nu, Np = h->m.Nphi;
+    const double* diag = h->diag;
+    auto apply = [&](const double* p, double* q) {
+        EVAP_CUDA(cudaMemsetAsync(t, 0, Nu3 * sizeof(double), st));
+        int e = launch_pressure_gradient(h, p, 1.0, t, st);
+        if (e) return e;
+        k_div_diag<<<blocks_for(Nu3, 256), 256, 0, st>>>(t, diag, Nu3);
+        EVAP_CHECK_LAUNCH("schur_scale");
+        EVAP_CUDA(cudaMemsetAsync(q, 0, Np * sizeof(double), st));
+        return launch_divergence(h, t, q, st);
+    };
+    const int rc = geo_cg(h, apply, r, d, z, 1e-6, 0.0, cg_iters, nullptr, st);
+    return rc == EVAP_ENOTCONV ? EVAP_OK : rc;
+}
+
+// g (the continuity right-hand side of the current fields), computed once per set_fields into h->cont_rhs.
+int continuity_rhs(evap_mesh* h, const double** g, cudaStream_t st) {
+    const MeshArgs<double>& m = h->m;
+    if (!h->cont_rhs) EVAP_CUDA(cudaMalloc(&h->cont_rhs, m.Nphi * sizeof(double)));
+    if (!h->cont_valid) {
+        EVAP_CUDA(cudaMemsetAsync(h->cont_rhs, 0, m.Nphi * sizeof(double), st));
+        const unsigned grid = (unsigned)blocks_for(m.ncell, 128, 1LL << 40);
+        if (m.P == 2)
+            k_continuity_rhs<2><<<grid, 128, 0, st>>>(m, h->b, h->qc, h->cont_rhs);
+        else
+            k_continuity_rhs<3><<<grid, 128, 0, st>>>(m, h->b, h->qc, h->cont_rhs);
+        EVAP_CHECK_LAUNCH("continuity_rhs");
+        h->cont_valid = true;
+    }
+    *g = h->cont_rhs;
+    return EVAP_OK;
+}
+
+// [y; y_p] = [A x - B^T p; B x]: the momentum apply (whose divergence row is B x - g) followed by + g and the
+// pressure term.
+int launch_saddle_apply(evap_mesh* h, const double* x, const double* p, double* y, double* yp, cudaStream_t st) {
+    const double* g = nullptr;
+    int rc = continuity_rhs(h, &g, st);
+    if (rc) return rc;
+    if ((rc = launch_momentum<double>(h, x, y, yp, st))) return rc;
+    k_add_vec<<<blocks_for(h->m.Nphi, 256, 152 * 8), 256, 0, st>>>(yp, g, h->m.Nphi);
+    EVAP_CHECK_LAUNCH("saddle_add_g");
+    return launch_pressure_gradient(h, p, -1.0, y, st);
+}
+
+}  // namespace evap
