@@ -365,6 +365,46 @@ def geometry_subsolver(torch, op, phi):
                 level_set_dofs=op.n_phi)
 
 
+def saddle_case(evap, torch, dev):
+    """Velocity-pressure system on the 64^3 four-sphere workload with the top face open (walls on the other five):
+    the FP64 saddle-point apply (20 back-to-back after 3) and flexible-GMRES solves of [A, -B^T; B, 0] [x; p] =
+    [f; g] from zero, f the workload's random vector (Dirichlet entries 0), g from the evaporation, to the paper's
+    relative tolerance 1e-4 of the Navier-Stokes solve and to 1e-8; each solve timed with CUDA events."""
+    wl = workloads.make_workload(WORKLOAD, dirichlet_faces=0x1F)
+    op = evap.Operator(wl.n, wl.p, wl.L, dict(wl.params))
+    cu = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    op.set_fields(cu(wl.phi), cu(wl.u0), cu(wl.mdot))
+    stream = torch.cuda.current_stream()
+    nu3 = 3 * op.n_u
+    f = wl.x.copy()
+    m = workloads.node_coords(wl.n, wl.p)
+    M = wl.p * wl.n + 1
+    idx = np.round(m * (M - 1)).astype(np.int64)
+    cons = np.zeros(len(m), dtype=bool)
+    for ax in range(3):
+        cons |= idx[:, ax] == 0
+        if ax < 2:
+            cons |= idx[:, ax] == M - 1
+    f[np.tile(cons, 3)] = 0.0
+    f = cu(f)
+    pr = cu(np.random.default_rng(3).uniform(-1, 1, op.n_phi))
+    t_apply = back_to_back(torch, lambda: op.apply_saddle(f, pr), 20, 3)
+    res = dict(workload=f"{WORKLOAD} with the face z = 1 open: {nu3 / 1e6:.2f} M velocity + {op.n_phi / 1e3:.0f} k "
+                        "pressure DoFs", apply_ms=t_apply, apply_gdofs=(nu3 + op.n_phi) / t_apply / 1e6)
+    for rtol in (1e-4, 1e-8):
+        op.solve_saddle(f, rtol=rtol)  # warm-up (workspace allocation)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, _, info = op.solve_saddle(f, rtol=rtol)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res[f"solve_rtol_{rtol:g}"] = dict(ms=e0.elapsed_time(e1), applies=info["iters"], relres=info["relres"],
+                                           converged=info["converged"])
+    op.close()
+    return res
+
+
 def large_case(evap, torch, dev, p: int):
     """deformed128: 128^3 cells, degree-p velocity (p = 2: 51 M DoFs, p = 3: 171 M DoFs), deformed sphere with
     spherical-harmonic noise up to l = 6 (seed 5), density ratio 1e4.  FP64 and FP32 applies, the adjoint apply, and
@@ -632,6 +672,7 @@ def main():
     if rank == 0 and not args.no_applies:
         applies = operator_applies(evap, torch, dev, op, d, counts, hbm)
         applies["geometry"] = geometry_subsolver(torch, op, d["phi"])
+        applies["saddle"] = saddle_case(evap, torch, dev)
     solves = None
     if rank == 0 and not args.no_solve_compare:
         solves = solve_comparison(evap, torch, dev)

@@ -154,7 +154,8 @@ int launch_transport_velocity(evap_mesh* h, cudaStream_t s, const double* phi = 
 // y = A x (+ divergence row into yp if not null).  init = false: y already holds x on the Dirichlet DoFs and 0
 // elsewhere (and yp is null), e.g. written by the solver's fused preconditioner kernel.
 template <typename T>
-int launch_momentum(evap_mesh* h, const T* x, T* y, T* yp, cudaStream_t s, bool init = true);
+// y = A x (+ the pressure term -B^T p when p is given, FP64 only), y_p = B x - g when yp is given.
+int launch_momentum(evap_mesh* h, const T* x, T* y, T* yp, cudaStream_t s, bool init = true, const T* p = nullptr);
 template <typename T>
 int launch_levelset(evap_mesh* h, int mode, const T* x, T* y, cudaStream_t s);
 int launch_adjoint(evap_mesh* h, const double* w, const double* wp, const double* x, double* gx, double* gu,
@@ -174,14 +175,17 @@ int geo_schur_setup(evap_mesh* h, double** diag, cudaStream_t s);
 int geo_cg(evap_mesh* h, const std::function<int(const double*, double*)>& apply, const double* b, const double* d,
            double* x, double rtol, double atol, int max_iter, int* iters, cudaStream_t s);
 // velocity-pressure coupling (saddle.cu)
-int launch_pressure_gradient(evap_mesh* h, const double* p, double scale, double* y, cudaStream_t s);
+template <typename T>
+int launch_pressure_gradient(evap_mesh* h, const T* p, T scale, T* y, cudaStream_t s);
 int continuity_rhs(evap_mesh* h, const double** g, cudaStream_t s);
 int launch_saddle_apply(evap_mesh* h, const double* x, const double* p, double* y, double* yp, cudaStream_t s);
 // y_p += B x (the divergence row without its source; Dirichlet entries of x read as 0)
-int launch_divergence(evap_mesh* h, const double* x, double* yp, cudaStream_t s);
-// z = S~^(-1) r by at most cg_iters CG iterations on S~ = B diag(A)^(-1) B^T with the Jacobi diagonal d of
-// geo_schur_setup (t: velocity scratch [3 N_u])
-int schur_apply(evap_mesh* h, const double* r, double* z, const double* d, double* t, int cg_iters, cudaStream_t s);
+template <typename T>
+int launch_divergence(evap_mesh* h, const T* x, T* yp, cudaStream_t s);
+// z = S~^(-1) r by at most cg_iters CG iterations on S~ = B diag(A)^(-1) B^T (applied in FP32) with the Jacobi
+// diagonal d of geo_schur_setup (scratch: t32 [3 N_u], pq32 [2 N_phi] floats)
+int schur_apply(evap_mesh* h, const double* r, double* z, const double* d, float* t32, float* pq32, int cg_iters,
+                cudaStream_t s);
 int launch_surface_tension(evap_mesh* h, const double* nf, const double* kappa, double alpha, double* out,
                            cudaStream_t s);
 int launch_diagonal_into(evap_mesh* h, float* acc, double* out, cudaStream_t s);
@@ -200,6 +204,7 @@ int solve_saddle(evap_mesh* h, const double* f, double* x, double* p, int restar
 template <typename T>
 int launch_fill(T* p, int64_t n, T v, cudaStream_t s);
 int launch_to_float(const double* a, float* b, int64_t n, cudaStream_t s);
+int launch_to_double(const float* a, double* b, int64_t n, cudaStream_t s);
 
 inline int blocks_for(int64_t n, int threads, int64_t cap = 152 * 64) {
     int64_t b = (n + threads - 1) / threads;

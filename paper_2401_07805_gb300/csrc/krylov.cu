@@ -720,6 +720,12 @@ __global__ void k_update_split(const double* __restrict__ Z, int64_t ld, const d
     }
 }
 
+// t = v + (double) w
+__global__ void k_add_float(const double* __restrict__ v, const float* __restrict__ w, double* __restrict__ t, int64_t N) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x)
+        t[k] = v[k] + (double)w[k];
+}
+
 struct SaddleSpace {
     const double* sdiag;    // Jacobi diagonal of the pressure Schur approximation
     double *V, *Z, *b, *t;  // outer basis [(m+1) ld], directions [m ld], right-hand side [ld], velocity scratch [3 N_u]
@@ -730,12 +736,17 @@ struct SaddleSpace {
 static int saddle_precond(Ctx& inner, SaddleSpace& sp, const double* v, double* z) {
     evap_mesh* h = inner.h;
     cudaStream_t s = inner.s;
-    const int64_t Nu3 = 3 * h->m.Nu;
+    const int64_t Nu3 = 3 * h->m.Nu, Np = h->m.Nphi;
     const int G = blocks_for(Nu3, 256);
-    int rc = schur_apply(h, v + Nu3, z + Nu3, sp.sdiag, sp.t, SADDLE_SCHUR_CG, s);
+    // the inner solve's FP32 scratch is free here: w32 [3 N_u] and z32 (>= 2 N_phi) for the Schur operator
+    int rc = schur_apply(h, v + Nu3, z + Nu3, sp.sdiag, sp.w32, sp.z32, SADDLE_SCHUR_CG, s);
     if (rc) return rc;
-    EVAP_CUDA(cudaMemcpyAsync(sp.t, v, Nu3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    if ((rc = launch_pressure_gradient(h, z + Nu3, 1.0, sp.t, s))) return rc;
+    // t = v_u + B^T z_p, the gradient in FP32 (it enters the FP32 velocity solve)
+    if ((rc = launch_to_float(z + Nu3, sp.z32, Np, s))) return rc;
+    EVAP_CUDA(cudaMemsetAsync(sp.w32, 0, Nu3 * sizeof(float), s));
+    if ((rc = launch_pressure_gradient<float>(h, sp.z32, 1.0f, sp.w32, s))) return rc;
+    k_add_float<<<G, 256, 0, s>>>(v, sp.w32, sp.t, Nu3);
+    EVAP_CHECK_LAUNCH("saddle_add_grad");
     // velocity block: FP32 GMRES on t / |t| from zero, then z_u = |t| d
     if ((rc = norm2_dev<double>(inner, sp.t, inner.dnorm))) return rc;
     k_scaled_to_float<<<G, 256, 0, s>>>(sp.t, inner.dnorm, sp.r32, Nu3);

@@ -152,10 +152,12 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
     for (int k = 0; k < QC32_K; ++k) dst[(int64_t)k * NQ * 32] = (float)(k < 3 ? v[1 + k] * m.inv_h : v[1 + k]);
 }
 
-template <typename T, int P, int CB>
+// PRES: the velocity-pressure apply, with the pressure term -(div v, p) of Eq. (weakNavierStokes) for the Q1 pressure
+// pin added to the gradient-tested flux (T_cc -= W p_h(x_q)).
+template <typename T, int P, int CB, bool PRES>
 __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
     k_momentum(MeshArgs<T> m, Basis<T> bas, const T* __restrict__ qc, const T* __restrict__ x, T* __restrict__ y,
-               T* __restrict__ yp) {
+               T* __restrict__ yp, const T* __restrict__ pin) {
     constexpr int Q = P + 1, NQ = Q * Q * Q;
     __shared__ T sS[Q][Q], sDc[Q][Q], sN1[Q][2];
     __shared__ T buf[2][6][CB][NQ];  // [half][slot][cell][point]: conflict-free lanes
@@ -263,6 +265,19 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
                 Tf[l][k] = v;
             }
         rdiv = cf[17] * tr - cf[18];
+        if constexpr (PRES) {
+            const int64_t m1 = n + 1;
+            T pq = 0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int ja = j & 1, jb = (j >> 1) & 1, jc = j >> 2;
+                pq += sN1[a][ja] * sN1[b][jb] * sN1[c][jc] * pin[(cx + ja) + m1 * ((cy + jb) + m1 * (cz + jc))];
+            }
+            const T wp = cf[17] * pq;
+            Tf[0][0] -= wp;
+            Tf[1][1] -= wp;
+            Tf[2][2] -= wp;
+        }
     }
     __syncthreads();
     if (active) {
@@ -381,7 +396,7 @@ int launch_qp_coeffs(evap_mesh* h, cudaStream_t s) {
 }
 
 template <typename T>
-int launch_momentum(evap_mesh* h, const T* x, T* y, T* yp, cudaStream_t s, bool init) {
+int launch_momentum(evap_mesh* h, const T* x, T* y, T* yp, cudaStream_t s, bool init, const T* p) {
     const MeshArgs<T> m = mesh_args<T>(h);
     const Basis<T> b = cast_basis<T>(h->b);
     const T* qc = (const T*)h->qc;  // FP64 only (the FP32 apply takes the line kernel)
@@ -394,22 +409,29 @@ int launch_momentum(evap_mesh* h, const T* x, T* y, T* yp, cudaStream_t s, bool 
     if constexpr (sizeof(T) == 4) {  // FP32: line-oriented kernel with u0 interpolated on the fly (momentum32.cu)
         (void)b;
         (void)qc;
+        if (p) return EVAP_EINVAL;  // the pressure term is FP64 only
         return launch_momentum32(h, x, y, yp, s);
     } else {
         if (m.P == 2) {
             constexpr int CB = 8;
-            const int64_t grid = (m.ncell + CB - 1) / CB;
-            k_momentum<T, 2, CB><<<(unsigned)grid, CB * 27, 0, s>>>(m, b, qc, x, y, yp);
+            const unsigned grid = (unsigned)((m.ncell + CB - 1) / CB);
+            if (p)
+                k_momentum<T, 2, CB, true><<<grid, CB * 27, 0, s>>>(m, b, qc, x, y, yp, p);
+            else
+                k_momentum<T, 2, CB, false><<<grid, CB * 27, 0, s>>>(m, b, qc, x, y, yp, nullptr);
         } else {
             constexpr int CB = 4;
-            const int64_t grid = (m.ncell + CB - 1) / CB;
-            k_momentum<T, 3, CB><<<(unsigned)grid, CB * 64, 0, s>>>(m, b, qc, x, y, yp);
+            const unsigned grid = (unsigned)((m.ncell + CB - 1) / CB);
+            if (p)
+                k_momentum<T, 3, CB, true><<<grid, CB * 64, 0, s>>>(m, b, qc, x, y, yp, p);
+            else
+                k_momentum<T, 3, CB, false><<<grid, CB * 64, 0, s>>>(m, b, qc, x, y, yp, nullptr);
         }
         EVAP_CHECK_LAUNCH("momentum");
         return EVAP_OK;
     }
 }
-template int launch_momentum<double>(evap_mesh*, const double*, double*, double*, cudaStream_t, bool);
-template int launch_momentum<float>(evap_mesh*, const float*, float*, float*, cudaStream_t, bool);
+template int launch_momentum<double>(evap_mesh*, const double*, double*, double*, cudaStream_t, bool, const double*);
+template int launch_momentum<float>(evap_mesh*, const float*, float*, float*, cudaStream_t, bool, const float*);
 
 }  // namespace evap

@@ -1,5 +1,6 @@
 // Velocity-pressure coupling of Eq. (weakNavierStokes) with the Q1 pressure of Sec. 2.5 (k_p = 1), FP64:
-//   pressure term of the momentum row   y_(c,i) += s sum_q W p_h(x_q) d_c N_i(x_q)      (s = -1: -(div v, p))
+//   pressure term of the momentum row   y_(c,i) += s sum_q W p_h(x_q) d_c N_i(x_q)      (s = -1: -(div v, p); the
+//                                       saddle-point apply folds it into the momentum kernel's stress flux)
 //   continuity right-hand side         g_j = sum_q W N1_j v_dil                           (Eq. continuity, evaporDil)
 //   saddle-point apply                 [y; y_p] = [A x - B^T p; B x]
 // with B the divergence row of the momentum apply (velocity Gauss rule, Dirichlet entries of x read as 0) and
@@ -12,14 +13,13 @@ namespace evap {
 // interpolated at the point from the cell's 8 Q1 nodes; the test with d_c N_i is the transpose of the momentum
 // apply's gradient (collocation derivative at the Gauss points along c, then S^T along z, y, x), so B^T here is
 // the exact transpose of the divergence row.
-template <int P, int CB>
+template <typename T, int P, int CB>
 __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
-    k_pressure_gradient(MeshArgs<double> m, Basis<double> bas, const double* __restrict__ p, double s,
-                        double* __restrict__ y) {
+    k_pressure_gradient(MeshArgs<T> m, Basis<T> bas, const T* __restrict__ p, T s, T* __restrict__ y) {
     constexpr int Q = P + 1, NQ = Q * Q * Q;
-    __shared__ double sS[Q][Q], sDc[Q][Q], sN1[Q][2];
-    __shared__ double val[CB][NQ];
-    __shared__ double buf[2][CB][3][NQ];
+    __shared__ T sS[Q][Q], sDc[Q][Q], sN1[Q][2];
+    __shared__ T val[CB][NQ];
+    __shared__ T buf[2][CB][3][NQ];
     const int tid = threadIdx.x;
     const int lc = tid / NQ, t = tid % NQ;
     const int64_t cell = (int64_t)blockIdx.x * CB + lc;
@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
         cy = (int)((cell / n) % n);
         cz = (int)(cell / ((int64_t)n * n));
         const int64_t m1 = n + 1;
-        double pq = 0.0;
+        T pq = 0;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const int ja = j & 1, jb = (j >> 1) & 1, jc = j >> 2;
@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
     }
     __syncthreads();
     if (active) {
-        double d0 = 0.0, d1 = 0.0, d2 = 0.0;
+        T d0 = 0, d1 = 0, d2 = 0;
 #pragma unroll
         for (int r = 0; r < Q; ++r) {
             d0 += sDc[r][a] * val[lc][r + Q * (b + Q * c)];
@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
     if (active)
 #pragma unroll
         for (int f = 0; f < 3; ++f) {
-            double v = 0.0;
+            T v = 0;
 #pragma unroll
             for (int q = 0; q < Q; ++q) v += sS[q][c] * buf[0][lc][f][a + Q * (b + Q * q)];
             buf[1][lc][f][t] = v;
@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
     if (active)
 #pragma unroll
         for (int f = 0; f < 3; ++f) {
-            double v = 0.0;
+            T v = 0;
 #pragma unroll
             for (int q = 0; q < Q; ++q) v += sS[q][b] * buf[1][lc][f][a + Q * (q + Q * c)];
             buf[0][lc][f][t] = v;
@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
     const int64_t gidx = gx + (int64_t)M * (gy + (int64_t)M * gz);
 #pragma unroll
     for (int f = 0; f < 3; ++f) {
-        double v = 0.0;
+        T v = 0;
 #pragma unroll
         for (int q = 0; q < Q; ++q) v += sS[q][a] * buf[0][lc][f][q + Q * (b + Q * c)];
         atomicAdd(&y[f * m.Nu + gidx], v);
@@ -118,13 +118,13 @@ __global__ void __launch_bounds__(128) k_continuity_rhs(MeshArgs<double> m, Basi
 
 // y_p += B x: the divergence row of the momentum apply without its source, sum_q W N1_j (div x)(x_q); values at the
 // points by S sweeps (x, y, z), the divergence by the collocation derivative, the Q1 test by three sweeps of N1.
-template <int P, int CB>
+template <typename T, int P, int CB>
 __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
-    k_divergence(MeshArgs<double> m, Basis<double> bas, const double* __restrict__ x, double* __restrict__ yp) {
+    k_divergence(MeshArgs<T> m, Basis<T> bas, const T* __restrict__ x, T* __restrict__ yp) {
     constexpr int Q = P + 1, NQ = Q * Q * Q;
-    __shared__ double sS[Q][Q], sDc[Q][Q], sN1[Q][2];
-    __shared__ double buf[2][3][CB][NQ];
-    __shared__ double rbuf[CB][NQ], q1a[CB][2 * Q * Q], q1b[CB][4 * Q];
+    __shared__ T sS[Q][Q], sDc[Q][Q], sN1[Q][2];
+    __shared__ T buf[2][3][CB][NQ];
+    __shared__ T rbuf[CB][NQ], q1a[CB][2 * Q * Q], q1b[CB][4 * Q];
     const int tid = threadIdx.x;
     const int lc = tid / NQ, t = tid % NQ;
     const int64_t cell = (int64_t)blockIdx.x * CB + lc;
@@ -145,13 +145,13 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
         const int64_t gidx = gx + (int64_t)M * (gy + (int64_t)M * gz);
         const bool cons = constrained_node(gx, gy, gz, M, m.faces);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) buf[0][k][lc][t] = cons ? 0.0 : x[k * m.Nu + gidx];
+        for (int k = 0; k < 3; ++k) buf[0][k][lc][t] = cons ? T(0) : x[k * m.Nu + gidx];
     }
     __syncthreads();
     if (active)
 #pragma unroll
         for (int f = 0; f < 3; ++f) {
-            double v = 0.0;
+            T v = 0;
 #pragma unroll
             for (int k = 0; k < Q; ++k) v += sS[a][k] * buf[0][f][lc][k + Q * (b + Q * c)];
             buf[1][f][lc][t] = v;
@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
     if (active)
 #pragma unroll
         for (int f = 0; f < 3; ++f) {
-            double v = 0.0;
+            T v = 0;
 #pragma unroll
             for (int k = 0; k < Q; ++k) v += sS[b][k] * buf[1][f][lc][a + Q * (k + Q * c)];
             buf[0][f][lc][t] = v;
@@ -169,14 +169,14 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
     if (active)
 #pragma unroll
         for (int f = 0; f < 3; ++f) {
-            double v = 0.0;
+            T v = 0;
 #pragma unroll
             for (int k = 0; k < Q; ++k) v += sS[c][k] * buf[0][f][lc][a + Q * (b + Q * k)];
             buf[1][f][lc][t] = v;
         }
     __syncthreads();
     if (active) {
-        double tr = 0.0;
+        T tr = 0;
 #pragma unroll
         for (int r = 0; r < Q; ++r)
             tr += sDc[a][r] * buf[1][0][lc][r + Q * (b + Q * c)] + sDc[b][r] * buf[1][1][lc][a + Q * (r + Q * c)] +
@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
     __syncthreads();
     if (active && t < 2 * Q * Q) {  // x-sweep: [jx][qy][qz]
         const int jx = t & 1, qy = (t >> 1) % Q, qz = (t >> 1) / Q;
-        double v = 0.0;
+        T v = 0;
 #pragma unroll
         for (int q = 0; q < Q; ++q) v += sN1[q][jx] * rbuf[lc][q + Q * (qy + Q * qz)];
         q1a[lc][t] = v;
@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
     __syncthreads();
     if (active && t < 4 * Q) {  // y-sweep: [jx][jy][qz]
         const int jx = t & 1, jy = (t >> 1) & 1, qz = t >> 2;
-        double v = 0.0;
+        T v = 0;
 #pragma unroll
         for (int q = 0; q < Q; ++q) v += sN1[q][jy] * q1a[lc][jx + 2 * (q + Q * qz)];
         q1b[lc][t] = v;
@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
     __syncthreads();
     if (active && t < 8) {  // z-sweep: Q1 node (jx, jy, jz)
         const int jx = t & 1, jy = (t >> 1) & 1, jz = t >> 2;
-        double v = 0.0;
+        T v = 0;
 #pragma unroll
         for (int q = 0; q < Q; ++q) v += sN1[q][jz] * q1b[lc][jx + 2 * (jy + 2 * q)];
         const int64_t m1 = n + 1;
@@ -210,8 +210,9 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
     }
 }
 
-// t /= diag (the FP64 Jacobi diagonal of the velocity block)
-__global__ void k_div_diag(double* __restrict__ t, const double* __restrict__ diag, int64_t N) {
+// t /= diag (the Jacobi diagonal of the velocity block)
+template <typename T>
+__global__ void k_div_diag(T* __restrict__ t, const T* __restrict__ diag, int64_t N) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
         t[i] /= diag[i];
 }
@@ -221,46 +222,61 @@ __global__ void k_add_vec(double* __restrict__ y, const double* __restrict__ g, 
         y[i] += g[i];
 }
 
-int launch_pressure_gradient(evap_mesh* h, const double* p, double s, double* y, cudaStream_t st) {
-    const MeshArgs<double>& m = h->m;
+template <typename T>
+int launch_pressure_gradient(evap_mesh* h, const T* p, T s, T* y, cudaStream_t st) {
+    const MeshArgs<T> m = mesh_args<T>(h);
+    const Basis<T> b = cast_basis<T>(h->b);
     if (m.P == 2) {
         constexpr int CB = 8;
-        k_pressure_gradient<2, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 27, 0, st>>>(m, h->b, p, s, y);
+        k_pressure_gradient<T, 2, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 27, 0, st>>>(m, b, p, s, y);
     } else {
         constexpr int CB = 4;
-        k_pressure_gradient<3, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 64, 0, st>>>(m, h->b, p, s, y);
+        k_pressure_gradient<T, 3, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 64, 0, st>>>(m, b, p, s, y);
     }
     EVAP_CHECK_LAUNCH("pressure_gradient");
     return EVAP_OK;
 }
+template int launch_pressure_gradient<float>(evap_mesh*, const float*, float, float*, cudaStream_t);
 
-int launch_divergence(evap_mesh* h, const double* x, double* yp, cudaStream_t st) {
-    const MeshArgs<double>& m = h->m;
+template <typename T>
+int launch_divergence(evap_mesh* h, const T* x, T* yp, cudaStream_t st) {
+    const MeshArgs<T> m = mesh_args<T>(h);
+    const Basis<T> b = cast_basis<T>(h->b);
     if (m.P == 2) {
         constexpr int CB = 8;
-        k_divergence<2, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 27, 0, st>>>(m, h->b, x, yp);
+        k_divergence<T, 2, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 27, 0, st>>>(m, b, x, yp);
     } else {
         constexpr int CB = 4;
-        k_divergence<3, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 64, 0, st>>>(m, h->b, x, yp);
+        k_divergence<T, 3, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 64, 0, st>>>(m, b, x, yp);
     }
     EVAP_CHECK_LAUNCH("divergence");
     return EVAP_OK;
 }
+template int launch_divergence<double>(evap_mesh*, const double*, double*, cudaStream_t);
+template int launch_divergence<float>(evap_mesh*, const float*, float*, cudaStream_t);
 
 // z = S~^(-1) r, S~ = B diag(A)^(-1) B^T (a SIMPLE-type approximation of the Schur complement B A^(-1) B^T: it keeps
 // the discrete B, so the pressure nodes of open faces are treated like every other node), by CG with the Jacobi
-// diagonal d of geo_schur_setup, at most cg_iters iterations (an inexact solve: the outer method is flexible).
-int schur_apply(evap_mesh* h, const double* r, double* z, const double* d, double* t, int cg_iters, cudaStream_t st) {
+// diagonal d of geo_schur_setup, at most cg_iters iterations (an inexact solve: the outer method is flexible).  The
+// CG runs in FP64; its operator is applied in FP32 (gradient, scaling by the FP32 Jacobi diagonal of A, divergence):
+// B and B^T are FP64-pipe bound at ~45 FMA per velocity point, and a preconditioner needs no FP64 operator.
+// Scratch: t32 [3 N_u] and pq32 [2 N_phi] floats.
+int schur_apply(evap_mesh* h, const double* r, double* z, const double* d, float* t32, float* pq32, int cg_iters,
+                cudaStream_t st) {
     const int64_t Nu3 = 3 * h->m.Nu, Np = h->m.Nphi;
-    const double* diag = h->diag;
+    float* p32 = pq32;
+    float* q32 = pq32 + Np;
+    const float* diag32 = h->diag32;
     auto apply = [&](const double* p, double* q) {
-        EVAP_CUDA(cudaMemsetAsync(t, 0, Nu3 * sizeof(double), st));
-        int e = launch_pressure_gradient(h, p, 1.0, t, st);
+        int e = launch_to_float(p, p32, Np, st);
         if (e) return e;
-        k_div_diag<<<blocks_for(Nu3, 256), 256, 0, st>>>(t, diag, Nu3);
+        EVAP_CUDA(cudaMemsetAsync(t32, 0, Nu3 * sizeof(float), st));
+        if ((e = launch_pressure_gradient<float>(h, p32, 1.0f, t32, st))) return e;
+        k_div_diag<float><<<blocks_for(Nu3, 256), 256, 0, st>>>(t32, diag32, Nu3);
         EVAP_CHECK_LAUNCH("schur_scale");
-        EVAP_CUDA(cudaMemsetAsync(q, 0, Np * sizeof(double), st));
-        return launch_divergence(h, t, q, st);
+        EVAP_CUDA(cudaMemsetAsync(q32, 0, Np * sizeof(float), st));
+        if ((e = launch_divergence<float>(h, t32, q32, st))) return e;
+        return launch_to_double(q32, q, Np, st);
     };
     const int rc = geo_cg(h, apply, r, d, z, 1e-6, 0.0, cg_iters, nullptr, st);
     return rc == EVAP_ENOTCONV ? EVAP_OK : rc;
@@ -284,16 +300,16 @@ int continuity_rhs(evap_mesh* h, const double** g, cudaStream_t st) {
     return EVAP_OK;
 }
 
-// [y; y_p] = [A x - B^T p; B x]: the momentum apply (whose divergence row is B x - g) followed by + g and the
-// pressure term.
+// [y; y_p] = [A x - B^T p; B x]: the momentum apply with the pressure term folded into its stress flux (whose
+// divergence row is B x - g), followed by + g.
 int launch_saddle_apply(evap_mesh* h, const double* x, const double* p, double* y, double* yp, cudaStream_t st) {
     const double* g = nullptr;
     int rc = continuity_rhs(h, &g, st);
     if (rc) return rc;
-    if ((rc = launch_momentum<double>(h, x, y, yp, st))) return rc;
+    if ((rc = launch_momentum<double>(h, x, y, yp, st, true, p))) return rc;
     k_add_vec<<<blocks_for(h->m.Nphi, 256, 152 * 8), 256, 0, st>>>(yp, g, h->m.Nphi);
     EVAP_CHECK_LAUNCH("saddle_add_g");
-    return launch_pressure_gradient(h, p, -1.0, y, st);
+    return EVAP_OK;
 }
 
 }  // namespace evap

@@ -32,6 +32,17 @@ int launch_to_float(const double* a, float* b, int64_t n, cudaStream_t s) {
     return EVAP_OK;
 }
 
+__global__ void k_to_double(const float* __restrict__ a, double* __restrict__ b, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = (double)a[i];
+}
+
+int launch_to_double(const float* a, double* b, int64_t n, cudaStream_t s) {
+    k_to_double<<<blocks_for(n, 256), 256, 0, s>>>(a, b, n);
+    EVAP_CHECK_LAUNCH("to_double");
+    return EVAP_OK;
+}
+
 // phi clamped to [-1, 1]; FP32 copies of phi and u.
 __global__ void k_prepare(double* phi, float* phi32, const double* __restrict__ u, float* __restrict__ u32,
                           int64_t Np, int64_t Nu3) {
