@@ -50,7 +50,9 @@ enum evap_status {
     EVAP_ECUDA = -2,       /* a CUDA call or kernel launch failed; evap_last_error() has the CUDA message */
     EVAP_ENOTCONV = -3,    /* solve hit its iteration cap; the last iterate and its residual are returned */
     EVAP_ENOFIELDS = -4,   /* an apply or solve was called before evap_set_fields */
-    EVAP_ENOMEM = -5       /* device allocation failed */
+    EVAP_ENOMEM = -5,      /* device allocation failed */
+    EVAP_ENONFINITE = -6   /* input checks on (evap_set_checks): an input array holds a NaN or an Inf; the check's
+                              reduction was enqueued and synchronized, the call's own work was not */
 };
 
 enum evap_levelset_mode {
@@ -89,6 +91,11 @@ int evap_destroy(evap_handle h);
 
 /* Number of Q_p velocity nodes (N_u; a velocity vector has 3 N_u entries) and of Q1 nodes (N_phi). */
 int evap_sizes(evap_handle h, int64_t* n_u, int64_t* n_phi);
+
+/* Input checks (off by default): with on != 0 every later call first counts the NaN and Inf entries of its input
+ * arrays (the fields of evap_set_fields, x / f / p / w / n / kappa / psi of the applies and solves) by one device
+ * reduction, synchronizes the stream, and returns EVAP_ENONFINITE without doing its work if any is found. */
+int evap_set_checks(evap_handle h, int on);
 
 /* Set the coefficient fields of the operators: phi [N_phi] (regularized level set, Eq. initial_phi; values are
  * clamped to [-1, 1]), u [3 N_u] (velocity about which the momentum operator is linearized; also the fluid

@@ -29,7 +29,7 @@ _LOCK = threading.Lock()
 
 LEVELSET_MODES = {"advect": 0, "reinit": 1, "reinit_rhs": 2}
 STATUS = {0: "EVAP_OK", -1: "EVAP_EINVAL", -2: "EVAP_ECUDA", -3: "EVAP_ENOTCONV", -4: "EVAP_ENOFIELDS",
-          -5: "EVAP_ENOMEM"}
+          -5: "EVAP_ENOMEM", -6: "EVAP_ENONFINITE"}
 
 # Exported symbols of include/evap.h with their ctypes signatures.
 _c_int, _c_dbl, _vp = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
@@ -58,6 +58,7 @@ SIGNATURES = {
     "evap_reinitialize": (_c_int, [_vp, _vp, _c_int, ctypes.POINTER(_c_int), ctypes.POINTER(_c_dbl), _vp]),
     "evap_advect_levelset": (_c_int, [_vp, _vp, _c_int, _c_dbl, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int),
                                       ctypes.POINTER(_c_dbl), _vp]),
+    "evap_set_checks": (_c_int, [_vp, _c_int]),
     "evap_apply_saddle": (_c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "evap_solve_saddle": (_c_int, [_vp, _vp, _vp, _vp, _c_int, _c_dbl, _c_int, ctypes.POINTER(_c_int),
                                    ctypes.POINTER(_c_dbl), _vp]),
@@ -256,6 +257,10 @@ class Operator:
                                         ctypes.byref(lin), ctypes.byref(ch), _stream())
         _check(rc, "evap_advect_levelset", allow=() if raise_on_notconv else (-3,))
         return phi, dict(fp_iters=fp.value, lin_iters=lin.value, last_change=ch.value, converged=rc == 0)
+
+    def set_checks(self, on: bool = True):
+        """Count NaN / Inf entries of every later call's inputs first (EVAP_ENONFINITE if any)."""
+        _check(lib().evap_set_checks(self._h, int(bool(on))), "evap_set_checks")
 
     def apply_saddle(self, x: torch.Tensor, p: torch.Tensor):
         """(A x - B^T p, B x): the velocity-pressure operator of Eq. (weakNavierStokes) with the Q1 pressure."""

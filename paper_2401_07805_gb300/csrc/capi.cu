@@ -3,6 +3,7 @@
 #include <cstdio>
 #include <cstring>
 #include <atomic>
+#include <initializer_list>
 #include <new>
 
 #include "evap_internal.cuh"
@@ -109,11 +110,49 @@ static int fail(int code, const char* msg) {
     return code;
 }
 
+// Input checks: the number of NaN / Inf entries of the listed arrays (one device counter, one synchronization).
+template <typename T>
+__global__ void k_count_nonfinite(const T* __restrict__ a, int64_t n, unsigned long long* cnt) {
+    unsigned long long c = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        c += isfinite(a[i]) ? 0ull : 1ull;
+    if (c) atomicAdd(cnt, c);
+}
+
+struct InArr {
+    const void* p;
+    int64_t n;
+    bool f32;
+};
+
+static int check_inputs(evap_mesh* h, const char* who, cudaStream_t s, std::initializer_list<InArr> arrs) {
+    if (!h->checks) return EVAP_OK;
+    if (!h->nonfinite) EVAP_CUDA(cudaMalloc(&h->nonfinite, sizeof(unsigned long long)));
+    EVAP_CUDA(cudaMemsetAsync(h->nonfinite, 0, sizeof(unsigned long long), s));
+    for (const InArr& a : arrs) {
+        if (!a.p || a.n <= 0) continue;
+        const int grid = blocks_for(a.n, 256, 152 * 8);
+        if (a.f32)
+            k_count_nonfinite<float><<<grid, 256, 0, s>>>((const float*)a.p, a.n, h->nonfinite);
+        else
+            k_count_nonfinite<double><<<grid, 256, 0, s>>>((const double*)a.p, a.n, h->nonfinite);
+        EVAP_CHECK_LAUNCH("count_nonfinite");
+    }
+    unsigned long long c = 0;
+    EVAP_CUDA(cudaMemcpyAsync(&c, h->nonfinite, sizeof(c), cudaMemcpyDeviceToHost, s));
+    EVAP_CUDA(cudaStreamSynchronize(s));
+    if (c) {
+        set_error(std::string(who) + ": " + std::to_string(c) + " non-finite input entries");
+        return EVAP_ENONFINITE;
+    }
+    return EVAP_OK;
+}
+
 static void free_all(evap_mesh* h) {
     void* ptrs[] = {h->phi, h->u, h->mdot, h->u32, h->phi32, h->cell_code, h->table_index, h->table_count,
                     h->table, h->table32, h->qc, h->qc32, h->ugamma, h->ugamma32, h->cpp_flags, h->flag_count, h->band_list,
                     h->band_count, h->band_y, h->cpp_evals, h->ls_normal_store, h->ls_normal32_store, h->geo_ws, h->geo_elem, h->diag,
-                    h->diag32, h->ws, h->red, h->cont_rhs, h->sd_ws, h->sd_red};
+                    h->diag32, h->ws, h->red, h->cont_rhs, h->sd_ws, h->sd_red, h->nonfinite};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->red_host) cudaFreeHost(h->red_host);
@@ -131,6 +170,7 @@ const char* evap_status_string(int status) {
         case EVAP_ENOTCONV: return "EVAP_ENOTCONV";
         case EVAP_ENOFIELDS: return "EVAP_ENOFIELDS";
         case EVAP_ENOMEM: return "EVAP_ENOMEM";
+        case EVAP_ENONFINITE: return "EVAP_ENONFINITE";
         default: return "EVAP_UNKNOWN";
     }
 }
@@ -224,10 +264,18 @@ int evap_sizes(evap_handle h, int64_t* n_u, int64_t* n_phi) {
     return EVAP_OK;
 }
 
+int evap_set_checks(evap_handle h, int on) {
+    if (!h) return fail(EVAP_EINVAL, "evap_set_checks: null handle");
+    h->checks = on != 0;
+    return EVAP_OK;
+}
+
 int evap_set_fields(evap_handle h, const double* phi, const double* u, const double* mdot, void* stream) {
     if (!h || !phi || !u || !mdot) return fail(EVAP_EINVAL, "evap_set_fields: null argument");
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t Nu = h->m.Nu, Np = h->m.Nphi;
+    int rc0 = check_inputs(h, "evap_set_fields", s, {{phi, Np, false}, {u, 3 * Nu, false}, {mdot, Np, false}});
+    if (rc0) return rc0;
     EVAP_CUDA(cudaMemcpyAsync(h->phi, phi, Np * sizeof(double), cudaMemcpyDeviceToDevice, s));
     EVAP_CUDA(cudaMemcpyAsync(h->u, u, 3 * Nu * sizeof(double), cudaMemcpyDeviceToDevice, s));
     EVAP_CUDA(cudaMemcpyAsync(h->mdot, mdot, Np * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -247,6 +295,8 @@ int evap_set_transport_velocity(evap_handle h, const double* u_gamma, void* stre
     if (!h || !u_gamma) return fail(EVAP_EINVAL, "evap_set_transport_velocity: null argument");
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t Np = h->m.Nphi;
+    int rc0 = check_inputs(h, "evap_set_transport_velocity", s, {{u_gamma, 3 * Np, false}});
+    if (rc0) return rc0;
     EVAP_CUDA(cudaMemcpyAsync(h->ugamma, u_gamma, 3 * Np * sizeof(double), cudaMemcpyDeviceToDevice, s));
     int rc = launch_to_float(h->ugamma, h->ugamma32, 3 * Np, s);
     if (rc) return rc;
@@ -304,6 +354,8 @@ int evap_projected_normal(evap_handle h, double* n, int* iters, double* relres, 
 int evap_curvature(evap_handle h, const double* n, double* kappa, int* iters, double* relres, void* stream) {
     if (!h || !n || !kappa) return fail(EVAP_EINVAL, "evap_curvature: null argument");
     if ((const void*)n == (const void*)kappa) return fail(EVAP_EINVAL, "evap_curvature: n and kappa must not alias");
+    int rc0 = check_inputs(h, "evap_curvature", (cudaStream_t)stream, {{n, 3 * h->m.Nphi, false}});
+    if (rc0) return rc0;
     return geo_curvature(h, n, kappa, iters, relres, (cudaStream_t)stream);
 }
 
@@ -316,6 +368,8 @@ int evap_set_levelset_normal(evap_handle h, const double* n, void* stream) {
         return EVAP_OK;
     }
     const int64_t Np = h->m.Nphi;
+    int rc0 = check_inputs(h, "evap_set_levelset_normal", s, {{n, 3 * Np, false}});
+    if (rc0) return rc0;
     if (!h->ls_normal_store) EVAP_CUDA(cudaMalloc(&h->ls_normal_store, 3 * Np * sizeof(double)));
     if (!h->ls_normal32_store) EVAP_CUDA(cudaMalloc(&h->ls_normal32_store, 3 * Np * sizeof(float)));
     EVAP_CUDA(cudaMemcpyAsync(h->ls_normal_store, n, 3 * Np * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -330,6 +384,8 @@ int evap_reinitialize(evap_handle h, double* psi, int steps, int* iters, double*
     if (!h || !psi) return fail(EVAP_EINVAL, "evap_reinitialize: null argument");
     if (steps < 0) return fail(EVAP_EINVAL, "evap_reinitialize: steps must be >= 0");
     if (!h->has_fields) return fail(EVAP_ENOFIELDS, "evap_reinitialize: call evap_set_fields first");
+    int rc0 = check_inputs(h, "evap_reinitialize", (cudaStream_t)stream, {{psi, h->m.Nphi, false}});
+    if (rc0) return rc0;
     return geo_reinitialize(h, psi, steps, iters, last_change, (cudaStream_t)stream);
 }
 
@@ -345,6 +401,9 @@ int evap_apply_saddle(evap_handle h, const double* x, const double* p, double* y
     if (!h || !x || !p || !y || !y_p) return fail(EVAP_EINVAL, "evap_apply_saddle: null argument");
     if (x == y) return fail(EVAP_EINVAL, "evap_apply_saddle: x and y must not alias");
     if (!h->has_fields) return fail(EVAP_ENOFIELDS, "evap_apply_saddle: call evap_set_fields first");
+    int rc0 = check_inputs(h, "evap_apply_saddle", (cudaStream_t)stream,
+                           {{x, 3 * h->m.Nu, false}, {p, h->m.Nphi, false}});
+    if (rc0) return rc0;
     return launch_saddle_apply(h, x, p, y, y_p, (cudaStream_t)stream);
 }
 
@@ -356,6 +415,9 @@ int evap_solve_saddle(evap_handle h, const double* f, double* x, double* p, int 
     if ((h->m.faces & 0x3Fu) == 0x3Fu)
         return fail(EVAP_EINVAL, "evap_solve_saddle: every face is Dirichlet (the pressure level is undetermined)");
     if (!h->has_fields) return fail(EVAP_ENOFIELDS, "evap_solve_saddle: call evap_set_fields first");
+    int rc0 = check_inputs(h, "evap_solve_saddle", (cudaStream_t)stream,
+                           {{f, 3 * h->m.Nu, false}, {x, 3 * h->m.Nu, false}, {p, h->m.Nphi, false}});
+    if (rc0) return rc0;
     return solve_saddle(h, f, x, p, restart, rtol, max_iter, iters, relres, (cudaStream_t)stream);
 }
 
@@ -363,6 +425,9 @@ int evap_surface_tension(evap_handle h, const double* n, const double* kappa, do
     if (!h || !n || !kappa || !f) return fail(EVAP_EINVAL, "evap_surface_tension: null argument");
     if (!h->has_fields) return fail(EVAP_ENOFIELDS, "evap_surface_tension: call evap_set_fields first");
     if (!(h->m.rho_l != h->m.rho_g)) return fail(EVAP_EINVAL, "evap_surface_tension: c_rho needs rho_l != rho_g");
+    int rc0 = check_inputs(h, "evap_surface_tension", (cudaStream_t)stream,
+                           {{n, 3 * h->m.Nphi, false}, {kappa, h->m.Nphi, false}});
+    if (rc0) return rc0;
     return launch_surface_tension(h, n, kappa, alpha, f, (cudaStream_t)stream);
 }
 
@@ -372,6 +437,8 @@ int evap_apply_momentum(evap_handle h, int prec, const void* x, void* y, void* y
     if (x == y) return fail(EVAP_EINVAL, "evap_apply_momentum: x and y must not alias");
     if (!h->has_fields) return fail(EVAP_ENOFIELDS, "evap_apply_momentum: call evap_set_fields first");
     cudaStream_t s = (cudaStream_t)stream;
+    int rc0 = check_inputs(h, "evap_apply_momentum", s, {{x, 3 * h->m.Nu, prec == 32}});
+    if (rc0) return rc0;
     if (prec == 64) return launch_momentum<double>(h, (const double*)x, (double*)y, (double*)y_p, s);
     return launch_momentum<float>(h, (const float*)x, (float*)y, (float*)y_p, s);
 }
@@ -383,6 +450,8 @@ int evap_apply_levelset(evap_handle h, int mode, int prec, const void* x, void* 
     if (x == y) return fail(EVAP_EINVAL, "evap_apply_levelset: x and y must not alias");
     if (!h->has_fields) return fail(EVAP_ENOFIELDS, "evap_apply_levelset: call evap_set_fields first");
     cudaStream_t s = (cudaStream_t)stream;
+    int rc0 = check_inputs(h, "evap_apply_levelset", s, {{x, h->m.Nphi, prec == 32}});
+    if (rc0) return rc0;
     if (prec == 64) return launch_levelset<double>(h, mode, (const double*)x, (double*)y, s);
     return launch_levelset<float>(h, mode, (const float*)x, (float*)y, s);
 }
@@ -391,6 +460,9 @@ int evap_apply_adjoint(evap_handle h, const double* w, const double* w_p, const 
                        double* g_u0, double* g_phi, double* g_mdot, void* stream) {
     if (!h || !w || !x) return fail(EVAP_EINVAL, "evap_apply_adjoint: null argument");
     if (!h->has_fields) return fail(EVAP_ENOFIELDS, "evap_apply_adjoint: call evap_set_fields first");
+    int rc0 = check_inputs(h, "evap_apply_adjoint", (cudaStream_t)stream,
+                           {{w, 3 * h->m.Nu, false}, {w_p, h->m.Nphi, false}, {x, 3 * h->m.Nu, false}});
+    if (rc0) return rc0;
     return launch_adjoint(h, w, w_p, x, g_x, g_u0, g_phi, g_mdot, (cudaStream_t)stream);
 }
 
@@ -411,6 +483,8 @@ int evap_solve(evap_handle h, const double* f, double* x, int mixed, int restart
     if (restart < 1 || restart > 200) return fail(EVAP_EINVAL, "evap_solve: restart must be in [1, 200]");
     if (!(rtol > 0.0) || max_iter < 1) return fail(EVAP_EINVAL, "evap_solve: rtol > 0 and max_iter >= 1 required");
     if (!h->has_fields) return fail(EVAP_ENOFIELDS, "evap_solve: call evap_set_fields first");
+    int rc0 = check_inputs(h, "evap_solve", (cudaStream_t)stream, {{f, 3 * h->m.Nu, false}, {x, 3 * h->m.Nu, false}});
+    if (rc0) return rc0;
     return solve_gmres(h, f, x, mixed ? 1 : 0, restart, rtol, max_iter, iters_out, relres_out, (cudaStream_t)stream);
 }
 

@@ -121,6 +121,9 @@ struct evap_mesh {
     double* sd_red = nullptr;
     double* sd_host = nullptr;
     size_t sd_red_len = 0;
+    // input checks (evap_set_checks): device counter of non-finite entries
+    bool checks = false;
+    unsigned long long* nonfinite = nullptr;
 };
 
 #include <functional>  // host-side declarations below

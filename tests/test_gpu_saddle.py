@@ -129,3 +129,34 @@ def test_saddle_solve_rejects_a_closed_box():
     op, _ = make(wl)
     with pytest.raises(EvapError):
         op.solve_saddle(cuda(np.zeros(3 * op.n_u)))
+
+
+def test_input_checks_report_non_finite_entries():
+    """With checks on, a NaN or Inf in an input array returns EVAP_ENONFINITE before any work (the output is left
+    untouched); with checks off the same call runs.  The check covers set_fields, the applies and the solves."""
+    from paper_2401_07805_gb300 import EvapError
+    wl = workloads.random_workload(5, 2, 3, geom="sphere", dirichlet_faces=0x1F)
+    op, _ = make(wl)
+    x = np.random.default_rng(1).uniform(-1, 1, 3 * op.n_u)
+    x[17] = np.nan
+    op.set_checks(True)
+    y = torch.full((3 * op.n_u,), 7.0, dtype=torch.float64, device="cuda")
+    with pytest.raises(EvapError, match="ENONFINITE"):
+        op.apply_momentum(cuda(x), prec=64, out=y)
+    assert bool((y == 7.0).all())
+    with pytest.raises(EvapError, match="ENONFINITE"):
+        op.apply_momentum(cuda(x).float(), prec=32)
+    f = np.zeros(3 * op.n_u)
+    f[5] = np.inf
+    with pytest.raises(EvapError, match="ENONFINITE"):
+        op.solve_saddle(cuda(f))
+    phi = wl.phi.copy()
+    phi[3] = np.nan
+    with pytest.raises(EvapError, match="ENONFINITE"):
+        op.set_fields(cuda(phi), cuda(wl.u0), cuda(wl.mdot))
+    x[17] = 0.0
+    op.apply_momentum(cuda(x), prec=64, out=y)  # finite again: runs
+    op.set_checks(False)
+    x[17] = np.nan
+    op.apply_momentum(cuda(x), prec=64, out=y)  # checks off: no error, NaN propagates
+    assert bool(torch.isnan(y).any())
