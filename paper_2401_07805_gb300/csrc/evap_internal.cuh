@@ -182,9 +182,10 @@ template <typename T>
 int launch_pressure_gradient(evap_mesh* h, const T* p, T scale, T* y, cudaStream_t s);
 int continuity_rhs(evap_mesh* h, const double** g, cudaStream_t s);
 int launch_saddle_apply(evap_mesh* h, const double* x, const double* p, double* y, double* yp, cudaStream_t s);
-// y_p += B x (the divergence row without its source; Dirichlet entries of x read as 0)
+// y_p += B D^(-1) x (the divergence row without its source; Dirichlet entries of x read as 0; D = diag, or the
+// identity when diag is null)
 template <typename T>
-int launch_divergence(evap_mesh* h, const T* x, T* yp, cudaStream_t s);
+int launch_divergence(evap_mesh* h, const T* x, const T* diag, T* yp, cudaStream_t s);
 // z = S~^(-1) r by at most cg_iters CG iterations on S~ = B diag(A)^(-1) B^T (applied in FP32) with the Jacobi
 // diagonal d of geo_schur_setup (scratch: t32 [3 N_u], pq32 [2 N_phi] floats)
 int schur_apply(evap_mesh* h, const double* r, double* z, const double* d, float* t32, float* pq32, int cg_iters,

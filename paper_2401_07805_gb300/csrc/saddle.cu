@@ -116,11 +116,13 @@ __global__ void __launch_bounds__(128) k_continuity_rhs(MeshArgs<double> m, Basi
         atomicAdd(&g[(cx + (j & 1)) + m1 * ((cy + ((j >> 1) & 1)) + m1 * (cz + (j >> 2)))], out[j]);
 }
 
-// y_p += B x: the divergence row of the momentum apply without its source, sum_q W N1_j (div x)(x_q); values at the
-// points by S sweeps (x, y, z), the divergence by the collocation derivative, the Q1 test by three sweeps of N1.
+// y_p += B D^(-1) x (D = diag when given, else the identity): the divergence row of the momentum apply without its
+// source, sum_q W N1_j (div x)(x_q); values at the points by S sweeps (x, y, z), the divergence by the collocation
+// derivative, the Q1 test by three sweeps of N1.
 template <typename T, int P, int CB>
 __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
-    k_divergence(MeshArgs<T> m, Basis<T> bas, const T* __restrict__ x, T* __restrict__ yp) {
+    k_divergence(MeshArgs<T> m, Basis<T> bas, const T* __restrict__ x, const T* __restrict__ diag,
+                 T* __restrict__ yp) {
     constexpr int Q = P + 1, NQ = Q * Q * Q;
     __shared__ T sS[Q][Q], sDc[Q][Q], sN1[Q][2];
     __shared__ T buf[2][3][CB][NQ];
@@ -145,7 +147,10 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
         const int64_t gidx = gx + (int64_t)M * (gy + (int64_t)M * gz);
         const bool cons = constrained_node(gx, gy, gz, M, m.faces);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) buf[0][k][lc][t] = cons ? T(0) : x[k * m.Nu + gidx];
+        for (int k = 0; k < 3; ++k) {
+            const int64_t i = k * m.Nu + gidx;
+            buf[0][k][lc][t] = cons ? T(0) : (diag ? x[i] / diag[i] : x[i]);
+        }
     }
     __syncthreads();
     if (active)
@@ -210,13 +215,6 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
     }
 }
 
-// t /= diag (the Jacobi diagonal of the velocity block)
-template <typename T>
-__global__ void k_div_diag(T* __restrict__ t, const T* __restrict__ diag, int64_t N) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
-        t[i] /= diag[i];
-}
-
 __global__ void k_add_vec(double* __restrict__ y, const double* __restrict__ g, int64_t N) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
         y[i] += g[i];
@@ -239,21 +237,20 @@ int launch_pressure_gradient(evap_mesh* h, const T* p, T s, T* y, cudaStream_t s
 template int launch_pressure_gradient<float>(evap_mesh*, const float*, float, float*, cudaStream_t);
 
 template <typename T>
-int launch_divergence(evap_mesh* h, const T* x, T* yp, cudaStream_t st) {
+int launch_divergence(evap_mesh* h, const T* x, const T* diag, T* yp, cudaStream_t st) {
     const MeshArgs<T> m = mesh_args<T>(h);
     const Basis<T> b = cast_basis<T>(h->b);
     if (m.P == 2) {
         constexpr int CB = 8;
-        k_divergence<T, 2, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 27, 0, st>>>(m, b, x, yp);
+        k_divergence<T, 2, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 27, 0, st>>>(m, b, x, diag, yp);
     } else {
         constexpr int CB = 4;
-        k_divergence<T, 3, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 64, 0, st>>>(m, b, x, yp);
+        k_divergence<T, 3, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 64, 0, st>>>(m, b, x, diag, yp);
     }
     EVAP_CHECK_LAUNCH("divergence");
     return EVAP_OK;
 }
-template int launch_divergence<double>(evap_mesh*, const double*, double*, cudaStream_t);
-template int launch_divergence<float>(evap_mesh*, const float*, float*, cudaStream_t);
+template int launch_divergence<float>(evap_mesh*, const float*, const float*, float*, cudaStream_t);
 
 // z = S~^(-1) r, S~ = B diag(A)^(-1) B^T (a SIMPLE-type approximation of the Schur complement B A^(-1) B^T: it keeps
 // the discrete B, so the pressure nodes of open faces are treated like every other node), by CG with the Jacobi
@@ -272,10 +269,8 @@ int schur_apply(evap_mesh* h, const double* r, double* z, const double* d, float
         if (e) return e;
         EVAP_CUDA(cudaMemsetAsync(t32, 0, Nu3 * sizeof(float), st));
         if ((e = launch_pressure_gradient<float>(h, p32, 1.0f, t32, st))) return e;
-        k_div_diag<float><<<blocks_for(Nu3, 256), 256, 0, st>>>(t32, diag32, Nu3);
-        EVAP_CHECK_LAUNCH("schur_scale");
         EVAP_CUDA(cudaMemsetAsync(q32, 0, Np * sizeof(float), st));
-        if ((e = launch_divergence<float>(h, t32, q32, st))) return e;
+        if ((e = launch_divergence<float>(h, t32, diag32, q32, st))) return e;  // B diag^(-1) t
         return launch_to_double(q32, q, Np, st);
     };
     const int rc = geo_cg(h, apply, r, d, z, 1e-6, 0.0, cg_iters, nullptr, st);
