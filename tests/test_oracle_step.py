@@ -1,0 +1,69 @@
+"""Pins of the oracle's coupled time step (oracle.step: BDF1 Picard Navier-Stokes step, then Algorithm 2) against
+closed forms.  CPU only."""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import fe, step
+
+pytestmark = pytest.mark.filterwarnings("ignore::scipy.sparse.SparseEfficiencyWarning")
+
+
+def slab_case(n, mdot_val, z0=0.55):
+    z = workloads.node_coords(n, 1)[:, 2]
+    prm = workloads.default_params(n, 1.0, ratio=10.0, dirichlet_faces=0x1F, dt=0.02, newton=0, variant=2)
+    prm["c_mass"] = 1.0 / prm["dt"]
+    prm["dtau"] = min(prm["eps"], prm["dt"])
+    phi = np.tanh((z0 - z) / (2 * prm["eps"]))
+    mesh = fe.Mesh(n, 2, 1.0)
+    return mesh, prm, phi, np.full(mesh.n_phi, float(mdot_val))
+
+
+def interface_height(phi, n):
+    """z of phi = 0 on the vertical line through the domain centre (linear interpolation between nodes)."""
+    m = n + 1
+    col = phi.reshape(m, m, m)[:, m // 2, m // 2]
+    zz = np.arange(m) / n
+    for k in range(m - 1):
+        if col[k] > 0 >= col[k + 1]:
+            return zz[k] + col[k] / (col[k] - col[k + 1]) * (zz[k + 1] - zz[k])
+    raise AssertionError("no interface on the centre line")
+
+
+def test_evaporating_slab_recedes_at_mdot_over_rho_l():
+    """Liquid at rest below a flat interface (walls on five faces, the top open), constant mdot: the liquid end of
+    the interface region does not move, so the variant-2 transport velocity is mdot / rho_l n and the interface
+    recedes into the liquid at mdot / rho_l (the sharp solution of the 1D phase-change problem with no inflow,
+    App. evapor_stefan).  Over three steps the displacement matches to 3 %; a dropped or sign-flipped evaporation
+    term gives 0 or -100 %."""
+    n = 6
+    mesh, prm, phi, mdot = slab_case(n, 50.0)
+    u = np.zeros(3 * mesh.n_u)
+    p = np.zeros(mesh.n_phi)
+    z0 = interface_height(phi, n)
+    for k in range(3):
+        phi, u, p = step.time_step(mesh, prm, phi, u, p, mdot, fp_iters=2, reinit_steps=2)
+        moved = z0 - interface_height(phi, n)
+        assert moved == pytest.approx((k + 1) * prm["dt"] * 50.0 / prm["rho_l"], rel=0.03)
+
+
+def test_rest_state_without_evaporation_stays_at_rest():
+    """No evaporation, no force, fluid at rest: f = 0 and g = 0, so the Navier-Stokes step returns exactly u = 0,
+    p = 0; the level set then only feels the reinitialization of the discrete tanh profile (a few 1e-3)."""
+    n = 6
+    mesh, prm, phi, _ = slab_case(n, 0.0)
+    ph, u, p = step.time_step(mesh, prm, phi, np.zeros(3 * mesh.n_u), np.zeros(mesh.n_phi), np.zeros(mesh.n_phi),
+                              fp_iters=1, reinit_steps=1)
+    assert np.abs(u).max() == 0.0 and np.abs(p).max() == 0.0
+    assert np.abs(ph - phi).max() < 5e-3
+
+
+def test_step_requires_bdf1_picard():
+    n = 3
+    mesh, prm, phi, mdot = slab_case(n, 1.0)
+    bad = dict(prm, newton=1)
+    with pytest.raises(ValueError):
+        step.time_step(mesh, bad, phi, np.zeros(3 * mesh.n_u), np.zeros(mesh.n_phi), mdot)
+    bad = dict(prm, c_mass=1.5 / prm["dt"])
+    with pytest.raises(ValueError):
+        step.time_step(mesh, bad, phi, np.zeros(3 * mesh.n_u), np.zeros(mesh.n_phi), mdot)
