@@ -152,7 +152,7 @@ static void free_all(evap_mesh* h) {
     void* ptrs[] = {h->phi, h->u, h->mdot, h->u32, h->phi32, h->cell_code, h->table_index, h->table_count,
                     h->table, h->table32, h->qc, h->qc32, h->ugamma, h->ugamma32, h->cpp_flags, h->flag_count, h->band_list,
                     h->band_count, h->band_y, h->cpp_evals, h->ls_normal_store, h->ls_normal32_store, h->geo_ws, h->geo_elem, h->diag,
-                    h->diag32, h->ws, h->red, h->cont_rhs, h->sd_ws, h->sd_red, h->nonfinite};
+                    h->diag32, h->ws, h->red, h->cont_rhs, h->sd_ws, h->sd_red, h->nonfinite, h->step_ws};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->red_host) cudaFreeHost(h->red_host);
@@ -419,6 +419,28 @@ int evap_solve_saddle(evap_handle h, const double* f, double* x, double* p, int 
                            {{f, 3 * h->m.Nu, false}, {x, 3 * h->m.Nu, false}, {p, h->m.Nphi, false}});
     if (rc0) return rc0;
     return solve_saddle(h, f, x, p, restart, rtol, max_iter, iters, relres, (cudaStream_t)stream);
+}
+
+int evap_time_step(evap_handle h, double* phi, double* u, double* p, const double* mdot, const double* gravity,
+                   int fp_iters, int reinit_steps, double ns_rtol, int* ns_iters, double* ns_relres, void* stream) {
+    if (!h || !phi || !u || !p || !mdot) return fail(EVAP_EINVAL, "evap_time_step: null argument");
+    if (h->m.newton != 0 || !(std::fabs(h->m.c_mass * h->m.dt - 1.0) <= 1e-12))
+        return fail(EVAP_EINVAL, "evap_time_step: the step is BDF1 with a Picard linearization (newton = 0, "
+                                 "c_mass = 1/dt)");
+    if ((h->m.faces & 0x3Fu) == 0x3Fu)
+        return fail(EVAP_EINVAL, "evap_time_step: every face is Dirichlet (the pressure level is undetermined)");
+    if (fp_iters < 1 || reinit_steps < 0 || !(ns_rtol > 0.0))
+        return fail(EVAP_EINVAL, "evap_time_step: need fp_iters >= 1, reinit_steps >= 0, ns_rtol > 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc0 = check_inputs(h, "evap_time_step", s, {{p, h->m.Nphi, false}});
+    if (rc0) return rc0;
+    double g[3] = {0.0, 0.0, 0.0};
+    if (gravity) {
+        g[0] = gravity[0];
+        g[1] = gravity[1];
+        g[2] = gravity[2];
+    }
+    return time_step(h, phi, u, p, mdot, g, fp_iters, reinit_steps, ns_rtol, ns_iters, ns_relres, s);
 }
 
 int evap_surface_tension(evap_handle h, const double* n, const double* kappa, double alpha, double* f, void* stream) {

@@ -124,6 +124,8 @@ struct evap_mesh {
     // input checks (evap_set_checks): device counter of non-finite entries
     bool checks = false;
     unsigned long long* nonfinite = nullptr;
+    // time step workspace: inertia load [3 N_u], advected level set [N_phi], projected normal [3 N_phi]
+    double* step_ws = nullptr;
 };
 
 #include <functional>  // host-side declarations below
@@ -182,6 +184,11 @@ template <typename T>
 int launch_pressure_gradient(evap_mesh* h, const T* p, T scale, T* y, cudaStream_t s);
 int continuity_rhs(evap_mesh* h, const double** g, cudaStream_t s);
 int launch_saddle_apply(evap_mesh* h, const double* x, const double* p, double* y, double* yp, cudaStream_t s);
+// f = sum_q W rho N_i (c_m u + g) (FP64; Dirichlet rows 0)
+int launch_mass_load(evap_mesh* h, const double* u, const double g[3], double* f, cudaStream_t s);
+// one coupled time step (step.cu; see evap_time_step)
+int time_step(evap_mesh* h, double* phi, double* u, double* p, const double* mdot, const double g[3], int fp_iters,
+              int reinit_steps, double ns_rtol, int* ns_iters, double* ns_relres, cudaStream_t s);
 // y_p += B D^(-1) x (the divergence row without its source; Dirichlet entries of x read as 0; D = diag, or the
 // identity when diag is null)
 template <typename T>

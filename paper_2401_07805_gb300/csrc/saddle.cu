@@ -215,6 +215,109 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
     }
 }
 
+// f += sum_q W rho c_m N_i (u_c + g_c / c_m) at the velocity Gauss points (the BDF1 inertia load of the old velocity
+// plus the body force), from the cached coefficient slot 0 (W rho c_m); Dirichlet entries of u are read as 0 and the
+// constrained rows of f are left untouched (zero).
+template <int P, int CB>
+__global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
+    k_mass_load(MeshArgs<double> m, Basis<double> bas, const double* __restrict__ qc, const double* __restrict__ u,
+                double g0, double g1, double g2, double* __restrict__ f) {
+    constexpr int Q = P + 1, NQ = Q * Q * Q;
+    __shared__ double sS[Q][Q];
+    __shared__ double buf[2][3][CB][NQ];
+    const int tid = threadIdx.x;
+    const int lc = tid / NQ, t = tid % NQ;
+    const int64_t cell = (int64_t)blockIdx.x * CB + lc;
+    const bool active = cell < m.ncell;
+    if (tid < Q * Q) sS[tid / Q][tid % Q] = bas.S[tid / Q][tid % Q];
+    const int a = t % Q, b = (t / Q) % Q, c = t / (Q * Q);
+    const int n = m.n, M = m.M;
+    int64_t gidx = 0;
+    bool cons = false;
+    if (active) {
+        const int cx = (int)(cell % n), cy = (int)((cell / n) % n), cz = (int)(cell / ((int64_t)n * n));
+        const int gx = P * cx + a, gy = P * cy + b, gz = P * cz + c;
+        gidx = gx + (int64_t)M * (gy + (int64_t)M * gz);
+        cons = constrained_node(gx, gy, gz, M, m.faces);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) buf[0][k][lc][t] = cons ? 0.0 : u[k * m.Nu + gidx];
+    }
+    __syncthreads();
+    if (active)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            double v = 0.0;
+#pragma unroll
+            for (int r = 0; r < Q; ++r) v += sS[a][r] * buf[0][k][lc][r + Q * (b + Q * c)];
+            buf[1][k][lc][t] = v;
+        }
+    __syncthreads();
+    if (active)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            double v = 0.0;
+#pragma unroll
+            for (int r = 0; r < Q; ++r) v += sS[b][r] * buf[1][k][lc][a + Q * (r + Q * c)];
+            buf[0][k][lc][t] = v;
+        }
+    __syncthreads();
+    if (active) {
+        const double cf0 = qc[cell * QC_K * NQ + t];  // W rho c_m
+        const double gc[3] = {g0 / m.c_mass, g1 / m.c_mass, g2 / m.c_mass};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            double v = 0.0;
+#pragma unroll
+            for (int r = 0; r < Q; ++r) v += sS[c][r] * buf[0][k][lc][a + Q * (b + Q * r)];
+            buf[1][k][lc][t] = cf0 * (v + gc[k]);
+        }
+    }
+    __syncthreads();
+    // test with N_i: transposed sweeps z, y, x
+    if (active)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            double v = 0.0;
+#pragma unroll
+            for (int q = 0; q < Q; ++q) v += sS[q][c] * buf[1][k][lc][a + Q * (b + Q * q)];
+            buf[0][k][lc][t] = v;
+        }
+    __syncthreads();
+    if (active)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            double v = 0.0;
+#pragma unroll
+            for (int q = 0; q < Q; ++q) v += sS[q][b] * buf[0][k][lc][a + Q * (q + Q * c)];
+            buf[1][k][lc][t] = v;
+        }
+    __syncthreads();
+    if (!active || cons) return;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        double v = 0.0;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) v += sS[q][a] * buf[1][k][lc][q + Q * (b + Q * c)];
+        atomicAdd(&f[k * m.Nu + gidx], v);
+    }
+}
+
+int launch_mass_load(evap_mesh* h, const double* u, const double g[3], double* f, cudaStream_t st) {
+    const MeshArgs<double>& m = h->m;
+    EVAP_CUDA(cudaMemsetAsync(f, 0, 3 * m.Nu * sizeof(double), st));
+    if (m.P == 2) {
+        constexpr int CB = 8;
+        k_mass_load<2, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 27, 0, st>>>(m, h->b, h->qc, u, g[0], g[1],
+                                                                                   g[2], f);
+    } else {
+        constexpr int CB = 4;
+        k_mass_load<3, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 64, 0, st>>>(m, h->b, h->qc, u, g[0], g[1],
+                                                                                   g[2], f);
+    }
+    EVAP_CHECK_LAUNCH("mass_load");
+    return EVAP_OK;
+}
+
 __global__ void k_add_vec(double* __restrict__ y, const double* __restrict__ g, int64_t N) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
         y[i] += g[i];
