@@ -224,9 +224,11 @@ int evap_solve_saddle(evap_handle h, const double* f, double* x, double* p, int 
                       int* iters, double* relres, void* stream);
 
 /* One time step of the coupled problem (the Navier-Stokes step, then Algorithm 2), for meshes created with
- * newton = 0 and c_mass = 1/dt (BDF1, one Picard linearization per step) and at least one open face:
- *   1. [A(u^n), -B^T; B, 0] [u^(n+1); p^(n+1)] = [f; g], f_(i,c) = sum_q W N_i rho (u^n_c / dt + gravity_c), by
- *      evap_solve_saddle (restart 30, ns_rtol, at most 2000 applications) from (u^n, p^n);
+ * newton = 0 (one Picard linearization per step) and at least one open face:
+ *   1. [A(u^n), -B^T; B, 0] [u^(n+1); p^(n+1)] = [f; g], f_(i,c) = sum_q W N_i rho (c_m u*_c + gravity_c): BDF1
+ *      (u_prev NULL: c_m = 1/dt, u* = u^n) or BDF2 (u_prev = u^(n-1): c_m = 3/(2 dt), u* = (4 u^n - u^(n-1)) / 3);
+ *      the mesh's c_mass is replaced by the scheme's for the step.  Solved by evap_solve_saddle (restart 30,
+ *      ns_rtol, at most 2000 applications) from (u^n, p^n);
  *   2. the advection fixed point (evap_advect_levelset, fp_iters passes, tol 0) with the transport velocity of
  *      u^(n+1), the result clamped to [-1, 1]; its projected normal; reinit_steps reinitialization steps with that
  *      normal frozen (evap_reinitialize), starting from the clamped field.
@@ -235,10 +237,11 @@ int evap_solve_saddle(evap_handle h, const double* f, double* x, double* p, int 
  * operator applications and relative residual of the velocity-pressure solve.  The call sets the fields from its
  * inputs first (as evap_set_fields) and leaves the mesh without fields afterwards (call evap_set_fields before the
  * next apply), with the unit-normal reinitialization operators restored.  Synchronizes the stream.  EVAP_EINVAL on
- * a mesh of another time scheme, a closed box, fp_iters < 1, reinit_steps < 0 or ns_rtol <= 0; EVAP_ENOTCONV if a
+ * a Newton mesh, dt <= 0, a closed box, fp_iters < 1, reinit_steps < 0 or ns_rtol <= 0; EVAP_ENOTCONV if a
  * sub-solve missed its tolerance (the step is still completed). */
-int evap_time_step(evap_handle h, double* phi, double* u, double* p, const double* mdot, const double* gravity,
-                   int fp_iters, int reinit_steps, double ns_rtol, int* ns_iters, double* ns_relres, void* stream);
+int evap_time_step(evap_handle h, double* phi, double* u, double* p, const double* mdot, const double* u_prev,
+                   const double* gravity, int fp_iters, int reinit_steps, double ns_rtol, int* ns_iters,
+                   double* ns_relres, void* stream);
 
 /* Diagonal of the momentum operator [3 N_u] (1 on Dirichlet DoFs), the Jacobi preconditioner of evap_solve,
  * evaluated in FP32 arithmetic from the FP64 coefficient table and written as double. */

@@ -3,10 +3,11 @@
 Algorithm 1 of the paper alternates the level-set solver (Algorithm 2) and the Navier-Stokes solver; the step here
 takes them in the order velocity first, then level set, each once:
 
-  1. Navier-Stokes, BDF1 with one Picard linearization about u^n (Eq. weakNavierStokes; App. D uses BDF2 and full
-     Newton, see the module readings): with A the momentum operator of oracle.momentum for u0 = u^n, newton = 0 and
-     c_m = 1/dt (so A u = rho u / dt + rho (u^n . grad) u + viscous(u)),
-        [A, -B^T; B, 0] [u^(n+1); p^(n+1)] = [f; g],   f_(i,c) = sum_q W N_i rho (u^n_c / dt + g_c),
+  1. Navier-Stokes with one Picard linearization about u^n per step (Eq. weakNavierStokes; App. D iterates Newton):
+     BDF1 (c_m = 1/dt, u* = u^n) or, given u^(n-1), BDF2 (c_m = 3/(2 dt), u* = (4 u^n - u^(n-1)) / 3); with A the
+     momentum operator of oracle.momentum for u0 = u^n, newton = 0 and that c_m (A u = rho c_m u + rho (u^n . grad) u
+     + viscous(u)),
+        [A, -B^T; B, 0] [u^(n+1); p^(n+1)] = [f; g],   f_(i,c) = sum_q W N_i rho (c_m u*_c + g_c),
      g the continuity right-hand side (oracle.saddle), Dirichlet rows of f zero (walls at rest).
   2. Level set, Algorithm 2: the advection fixed point (oracle.geometry.advect_levelset) with the velocity u^(n+1)
      and `fp_iters` passes; the advected field clamped to [-1, 1]; its projected normal (Eq.
@@ -36,13 +37,15 @@ def mass_load(pb: momentum.Problem, u: np.ndarray, gvec=(0.0, 0.0, 0.0)) -> np.n
 
 
 def time_step(mesh_u: fe.Mesh, params: dict, phi: np.ndarray, u: np.ndarray, p: np.ndarray, mdot: np.ndarray,
-              fp_iters: int = 2, reinit_steps: int = 2, gvec=(0.0, 0.0, 0.0)):
+              fp_iters: int = 2, reinit_steps: int = 2, gvec=(0.0, 0.0, 0.0), u_prev=None):
     prm = dict(params)
-    if int(prm.get("newton", 1)) != 0 or abs(prm["c_mass"] * prm["dt"] - 1.0) > 1e-12:
-        raise ValueError("the step is BDF1 with a Picard linearization: newton = 0 and c_mass = 1/dt")
+    if int(prm.get("newton", 1)) != 0:
+        raise ValueError("the step takes one Picard linearization: newton = 0")
+    prm["c_mass"] = (1.0 if u_prev is None else 1.5) / prm["dt"]
+    ustar = np.array(u, dtype=float) if u_prev is None else (4.0 * np.asarray(u) - np.asarray(u_prev)) / 3.0
     pb = momentum.Problem(mesh=mesh_u, params=prm, phi=np.clip(phi, -1.0, 1.0), u0=np.array(u, dtype=float),
                           mdot=np.array(mdot, dtype=float))
-    f = mass_load(pb, u, gvec)
+    f = mass_load(pb, ustar, gvec)
     u1, p1 = saddle.solve(pb, f)
     mesh1 = fe.Mesh(mesh_u.n, 1, mesh_u.L)
     adv, _ = geometry.advect_levelset(mesh_u, np.clip(phi, -1.0, 1.0), u1, mdot, prm, fp_iters)

@@ -59,7 +59,7 @@ SIGNATURES = {
     "evap_advect_levelset": (_c_int, [_vp, _vp, _c_int, _c_dbl, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int),
                                       ctypes.POINTER(_c_dbl), _vp]),
     "evap_set_checks": (_c_int, [_vp, _c_int]),
-    "evap_time_step": (_c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_c_dbl), _c_int, _c_int, _c_dbl,
+    "evap_time_step": (_c_int, [_vp, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_c_dbl), _c_int, _c_int, _c_dbl,
                                 ctypes.POINTER(_c_int), ctypes.POINTER(_c_dbl), _vp]),
     "evap_apply_saddle": (_c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "evap_solve_saddle": (_c_int, [_vp, _vp, _vp, _vp, _c_int, _c_dbl, _c_int, ctypes.POINTER(_c_int),
@@ -261,16 +261,18 @@ class Operator:
         return phi, dict(fp_iters=fp.value, lin_iters=lin.value, last_change=ch.value, converged=rc == 0)
 
     def time_step(self, phi: torch.Tensor, u: torch.Tensor, p: torch.Tensor, mdot: torch.Tensor, gravity=None,
-                  fp_iters: int = 2, reinit_steps: int = 2, ns_rtol: float = 1e-8, raise_on_notconv: bool = False):
-        """One coupled step (BDF1 Picard velocity-pressure solve, then Algorithm 2) from (phi, u, p) at t^n;
-        returns new tensors (phi, u, p) at t^(n+1) and info."""
+                  fp_iters: int = 2, reinit_steps: int = 2, ns_rtol: float = 1e-8, u_prev=None,
+                  raise_on_notconv: bool = False):
+        """One coupled step (Picard velocity-pressure solve, BDF1, or BDF2 given u_prev = u^(n-1); then Algorithm 2)
+        from (phi, u, p) at t^n; returns new tensors (phi, u, p) at t^(n+1) and info."""
         phi = self._dev(phi, self.n_phi, torch.float64, "phi").clone()
         u = self._dev(u, 3 * self.n_u, torch.float64, "u").clone()
         p = self._dev(p, self.n_phi, torch.float64, "p").clone()
         mdot = self._dev(mdot, self.n_phi, torch.float64, "mdot")
+        up = None if u_prev is None else self._dev(u_prev, 3 * self.n_u, torch.float64, "u_prev")
         g = None if gravity is None else (ctypes.c_double * 3)(*[float(v) for v in gravity])
         its, rel = ctypes.c_int(), ctypes.c_double()
-        rc = lib().evap_time_step(self._h, _ptr(phi), _ptr(u), _ptr(p), _ptr(mdot), g, int(fp_iters),
+        rc = lib().evap_time_step(self._h, _ptr(phi), _ptr(u), _ptr(p), _ptr(mdot), _ptr(up), g, int(fp_iters),
                                   int(reinit_steps), float(ns_rtol), ctypes.byref(its), ctypes.byref(rel), _stream())
         _check(rc, "evap_time_step", allow=() if raise_on_notconv else (-3,))
         return phi, u, p, dict(ns_iters=its.value, ns_relres=rel.value, converged=rc == 0)

@@ -421,18 +421,18 @@ int evap_solve_saddle(evap_handle h, const double* f, double* x, double* p, int 
     return solve_saddle(h, f, x, p, restart, rtol, max_iter, iters, relres, (cudaStream_t)stream);
 }
 
-int evap_time_step(evap_handle h, double* phi, double* u, double* p, const double* mdot, const double* gravity,
-                   int fp_iters, int reinit_steps, double ns_rtol, int* ns_iters, double* ns_relres, void* stream) {
+int evap_time_step(evap_handle h, double* phi, double* u, double* p, const double* mdot, const double* u_prev,
+                   const double* gravity, int fp_iters, int reinit_steps, double ns_rtol, int* ns_iters,
+                   double* ns_relres, void* stream) {
     if (!h || !phi || !u || !p || !mdot) return fail(EVAP_EINVAL, "evap_time_step: null argument");
-    if (h->m.newton != 0 || !(std::fabs(h->m.c_mass * h->m.dt - 1.0) <= 1e-12))
-        return fail(EVAP_EINVAL, "evap_time_step: the step is BDF1 with a Picard linearization (newton = 0, "
-                                 "c_mass = 1/dt)");
+    if (h->m.newton != 0) return fail(EVAP_EINVAL, "evap_time_step: the step takes a Picard linearization (newton = 0)");
+    if (!(h->m.dt > 0.0)) return fail(EVAP_EINVAL, "evap_time_step: dt must be > 0");
     if ((h->m.faces & 0x3Fu) == 0x3Fu)
         return fail(EVAP_EINVAL, "evap_time_step: every face is Dirichlet (the pressure level is undetermined)");
     if (fp_iters < 1 || reinit_steps < 0 || !(ns_rtol > 0.0))
         return fail(EVAP_EINVAL, "evap_time_step: need fp_iters >= 1, reinit_steps >= 0, ns_rtol > 0");
     cudaStream_t s = (cudaStream_t)stream;
-    int rc0 = check_inputs(h, "evap_time_step", s, {{p, h->m.Nphi, false}});
+    int rc0 = check_inputs(h, "evap_time_step", s, {{p, h->m.Nphi, false}, {u_prev, 3 * h->m.Nu, false}});
     if (rc0) return rc0;
     double g[3] = {0.0, 0.0, 0.0};
     if (gravity) {
@@ -440,7 +440,7 @@ int evap_time_step(evap_handle h, double* phi, double* u, double* p, const doubl
         g[1] = gravity[1];
         g[2] = gravity[2];
     }
-    return time_step(h, phi, u, p, mdot, g, fp_iters, reinit_steps, ns_rtol, ns_iters, ns_relres, s);
+    return time_step(h, phi, u, p, mdot, u_prev, g, fp_iters, reinit_steps, ns_rtol, ns_iters, ns_relres, s);
 }
 
 int evap_surface_tension(evap_handle h, const double* n, const double* kappa, double alpha, double* f, void* stream) {

@@ -66,6 +66,7 @@ def interface_height(phi, n):
 
 @pytest.mark.parametrize("geom", ["slab", "sphere"])
 def test_time_step_against_oracle(geom):
+    """Three steps (BDF1, then two BDF2 steps), element by element against the oracle's step."""
     n = 6
     prm, phi, mdot = slab(n, 1, 50.0)
     if geom == "sphere":
@@ -77,10 +78,15 @@ def test_time_step_against_oracle(geom):
     u = np.zeros(3 * mesh.n_u)
     p = np.zeros(mesh.n_phi)
     gphi, gu, gp = cuda(phi), cuda(u), cuda(p)
-    for k in range(2):
-        gphi, gu, gp, info = op.time_step(gphi, gu, gp, cuda(mdot), fp_iters=2, reinit_steps=2, ns_rtol=1e-10)
+    u_prev = gu_prev = None
+    for k in range(3):  # BDF1, then BDF2 with the previous velocity
+        nxt = op.time_step(gphi, gu, gp, cuda(mdot), fp_iters=2, reinit_steps=2, ns_rtol=1e-10, u_prev=gu_prev)
+        gu_prev = gu
+        gphi, gu, gp, info = nxt
         assert info["converged"], info
-        phi, u, p = step.time_step(mesh, prm, phi, u, p, mdot, fp_iters=2, reinit_steps=2)
+        u_old = u
+        phi, u, p = step.time_step(mesh, prm, phi, u, p, mdot, fp_iters=2, reinit_steps=2, u_prev=u_prev)
+        u_prev = u_old
         assert rel(host(gu), u) < 1e-6, k
         assert rel(host(gp), p) < 1e-5, k
         assert np.abs(host(gphi) - phi).max() < 1e-7, k
