@@ -3,10 +3,13 @@
 Algorithm 1 of the paper alternates the level-set solver (Algorithm 2) and the Navier-Stokes solver; the step here
 takes them in the order velocity first, then level set, each once:
 
-  1. Navier-Stokes with one Picard linearization about u^n per step (Eq. weakNavierStokes; App. D iterates Newton):
+  1. Navier-Stokes with Picard iterations (Eq. weakNavierStokes; App. D iterates Newton): the operator is linearized
+     about the latest iterate u^(k) (u^(0) = u^n), at most `picard_iters` solves, stopping before a solve once the
+     nonlinear residual |[f; g] - K(u^(k)) [u^(k); p^(k)]| is <= picard_atol (the table's 1e-10 for the Navier-Stokes
+     nonlinear solver); with picard_iters = 1 the step is semi-implicit. The time discretization is
      BDF1 (c_m = 1/dt, u* = u^n) or, given u^(n-1), BDF2 (c_m = 3/(2 dt), u* = (4 u^n - u^(n-1)) / 3); with A the
-     momentum operator of oracle.momentum for u0 = u^n, newton = 0 and that c_m (A u = rho c_m u + rho (u^n . grad) u
-     + viscous(u)),
+     momentum operator of oracle.momentum for u0 = u^(k), newton = 0 and that c_m (A u = rho c_m u + rho (u^(k) .
+     grad) u + viscous(u)),
         [A, -B^T; B, 0] [u^(n+1); p^(n+1)] = [f; g],   f_(i,c) = sum_q W N_i rho (c_m u*_c + g_c),
      g the continuity right-hand side (oracle.saddle), Dirichlet rows of f zero (walls at rest).
   2. Level set, Algorithm 2: the advection fixed point (oracle.geometry.advect_levelset) with the velocity u^(n+1)
@@ -37,7 +40,8 @@ def mass_load(pb: momentum.Problem, u: np.ndarray, gvec=(0.0, 0.0, 0.0)) -> np.n
 
 
 def time_step(mesh_u: fe.Mesh, params: dict, phi: np.ndarray, u: np.ndarray, p: np.ndarray, mdot: np.ndarray,
-              fp_iters: int = 2, reinit_steps: int = 2, gvec=(0.0, 0.0, 0.0), u_prev=None):
+              fp_iters: int = 2, reinit_steps: int = 2, gvec=(0.0, 0.0, 0.0), u_prev=None, picard_iters: int = 1,
+              picard_atol: float = 0.0, residuals=None):
     prm = dict(params)
     if int(prm.get("newton", 1)) != 0:
         raise ValueError("the step takes one Picard linearization: newton = 0")
@@ -46,7 +50,17 @@ def time_step(mesh_u: fe.Mesh, params: dict, phi: np.ndarray, u: np.ndarray, p: 
     pb = momentum.Problem(mesh=mesh_u, params=prm, phi=np.clip(phi, -1.0, 1.0), u0=np.array(u, dtype=float),
                           mdot=np.array(mdot, dtype=float))
     f = mass_load(pb, ustar, gvec)
-    u1, p1 = saddle.solve(pb, f)
+    u1, p1 = np.array(u, dtype=float), np.array(p, dtype=float)
+    for it in range(picard_iters):
+        pb.u0 = u1
+        if it > 0:
+            K, g = saddle.saddle_matrix(pb)
+            res = float(np.linalg.norm(np.concatenate([f, g]) - K @ np.concatenate([u1, p1])))
+            if residuals is not None:
+                residuals.append(res)
+            if res <= picard_atol:
+                break
+        u1, p1 = saddle.solve(pb, f)
     mesh1 = fe.Mesh(mesh_u.n, 1, mesh_u.L)
     adv, _ = geometry.advect_levelset(mesh_u, np.clip(phi, -1.0, 1.0), u1, mdot, prm, fp_iters)
     adv = np.clip(adv, -1.0, 1.0)

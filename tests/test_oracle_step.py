@@ -85,3 +85,26 @@ def test_step_requires_picard():
     bad = dict(prm, newton=1)
     with pytest.raises(ValueError):
         step.time_step(mesh, bad, phi, np.zeros(3 * mesh.n_u), np.zeros(mesh.n_phi), mdot)
+
+
+def test_picard_iterations_contract_the_nonlinear_residual():
+    """A strong convection (u^n = 0.3 in the gas, dt = 0.02, about 0.1 cells per step): the Picard iterations of a
+    step contract the nonlinear residual |[f; g] - K(u^(k)) [u^(k); p^(k)]| geometrically, and a tolerance stops them
+    early; one iteration leaves the semi-implicit step."""
+    n = 5
+    mesh, prm, phi, mdot = slab_case(n, 20.0)
+    rng = np.random.default_rng(3)
+    u = rng.uniform(-0.3, 0.3, 3 * mesh.n_u)
+    from oracle import momentum
+    pb = momentum.Problem(mesh=mesh, params=dict(prm), phi=phi, u0=u, mdot=mdot)
+    u[pb.constrained()] = 0.0
+    p = np.zeros(mesh.n_phi)
+    res = []
+    step.time_step(mesh, prm, phi, u, p, mdot, fp_iters=1, reinit_steps=0, picard_iters=5, residuals=res)
+    assert len(res) == 4
+    for a, b in zip(res, res[1:]):
+        assert b < 0.2 * a
+    res2 = []
+    step.time_step(mesh, prm, phi, u, p, mdot, fp_iters=1, reinit_steps=0, picard_iters=5, picard_atol=res[1] * 1.01,
+                   residuals=res2)
+    assert len(res2) == 2
