@@ -227,21 +227,26 @@ int evap_solve_saddle(evap_handle h, const double* f, double* x, double* p, int 
  * newton = 0 (one Picard linearization per step) and at least one open face:
  *   1. [A(u^n), -B^T; B, 0] [u^(n+1); p^(n+1)] = [f; g], f_(i,c) = sum_q W N_i rho (c_m u*_c + gravity_c): BDF1
  *      (u_prev NULL: c_m = 1/dt, u* = u^n) or BDF2 (u_prev = u^(n-1): c_m = 3/(2 dt), u* = (4 u^n - u^(n-1)) / 3);
- *      the mesh's c_mass is replaced by the scheme's for the step.  Solved by evap_solve_saddle (restart 30,
- *      ns_rtol, at most 2000 applications) from (u^n, p^n);
+ *      the mesh's c_mass is replaced by the scheme's for the step.  Picard iterations: A is linearized about the
+ *      latest iterate u^(k) (u^(0) = u^n), at most picard_iters solves by evap_solve_saddle (restart 30, ns_rtol, at
+ *      most 2000 applications each, from the latest iterate), stopping before a solve once the nonlinear residual
+ *      |[f; g] - K(u^(k)) [u^(k); p^(k)]| is <= picard_atol (the paper's Navier-Stokes nonlinear tolerance is 1e-10);
+ *      picard_iters = 1 gives the semi-implicit step;
  *   2. the advection fixed point (evap_advect_levelset, fp_iters passes, tol 0) with the transport velocity of
  *      u^(n+1), the result clamped to [-1, 1]; its projected normal; reinit_steps reinitialization steps with that
  *      normal frozen (evap_reinitialize), starting from the clamped field.
  * phi [N_phi], u [3 N_u], p [N_phi]: device arrays holding the state at t^n on entry and at t^(n+1) on exit;
  * mdot [N_phi] device; gravity: host double[3] or NULL (no body force).  ns_iters / ns_relres (host, may be NULL):
- * operator applications and relative residual of the velocity-pressure solve.  The call sets the fields from its
+ * operator applications of all velocity-pressure solves and the relative residual of the last; picard_res (host,
+ * may be NULL): the last nonlinear residual evaluated (-1 if none, i.e. picard_iters = 1).  The call sets the fields from its
  * inputs first (as evap_set_fields) and leaves the mesh without fields afterwards (call evap_set_fields before the
  * next apply), with the unit-normal reinitialization operators restored.  Synchronizes the stream.  EVAP_EINVAL on
- * a Newton mesh, dt <= 0, a closed box, fp_iters < 1, reinit_steps < 0 or ns_rtol <= 0; EVAP_ENOTCONV if a
+ * a Newton mesh, dt <= 0, a closed box, picard_iters < 1, picard_atol < 0, fp_iters < 1, reinit_steps < 0 or
+ * ns_rtol <= 0; EVAP_ENOTCONV if a
  * sub-solve missed its tolerance (the step is still completed). */
 int evap_time_step(evap_handle h, double* phi, double* u, double* p, const double* mdot, const double* u_prev,
-                   const double* gravity, int fp_iters, int reinit_steps, double ns_rtol, int* ns_iters,
-                   double* ns_relres, void* stream);
+                   const double* gravity, int picard_iters, double picard_atol, int fp_iters, int reinit_steps,
+                   double ns_rtol, int* ns_iters, double* ns_relres, double* picard_res, void* stream);
 
 /* Diagonal of the momentum operator [3 N_u] (1 on Dirichlet DoFs), the Jacobi preconditioner of evap_solve,
  * evaluated in FP32 arithmetic from the FP64 coefficient table and written as double. */

@@ -270,25 +270,37 @@ int evap_set_checks(evap_handle h, int on) {
     return EVAP_OK;
 }
 
+}  // extern "C"
+
+namespace evap {
+// The fields and every coefficient of the flow operators (no transport velocity).
+int set_fields_flow(evap_mesh* h, const double* phi, const double* u, const double* mdot, cudaStream_t s) {
+    const int64_t Nu = h->m.Nu, Np = h->m.Nphi;
+    if (phi != h->phi) EVAP_CUDA(cudaMemcpyAsync(h->phi, phi, Np * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (u != h->u) EVAP_CUDA(cudaMemcpyAsync(h->u, u, 3 * Nu * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (mdot != h->mdot) EVAP_CUDA(cudaMemcpyAsync(h->mdot, mdot, Np * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    int rc = launch_setup_coefficients(h, s);  // clamps phi, FP32 copies, coefficient table
+    if (rc) return rc;
+    rc = launch_qp_coeffs(h, s);  // quadrature-point coefficients of the momentum operator
+    if (rc) return rc;
+    h->has_fields = true;
+    h->diag_valid = false;
+    h->cont_valid = false;
+    return EVAP_OK;
+}
+}  // namespace evap
+
+extern "C" {
+
 int evap_set_fields(evap_handle h, const double* phi, const double* u, const double* mdot, void* stream) {
     if (!h || !phi || !u || !mdot) return fail(EVAP_EINVAL, "evap_set_fields: null argument");
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t Nu = h->m.Nu, Np = h->m.Nphi;
     int rc0 = check_inputs(h, "evap_set_fields", s, {{phi, Np, false}, {u, 3 * Nu, false}, {mdot, Np, false}});
     if (rc0) return rc0;
-    EVAP_CUDA(cudaMemcpyAsync(h->phi, phi, Np * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    EVAP_CUDA(cudaMemcpyAsync(h->u, u, 3 * Nu * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    EVAP_CUDA(cudaMemcpyAsync(h->mdot, mdot, Np * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    int rc = launch_setup_coefficients(h, s);  // clamps phi, FP32 copies, coefficient table
+    int rc = set_fields_flow(h, phi, u, mdot, s);
     if (rc) return rc;
-    rc = launch_qp_coeffs(h, s);  // quadrature-point coefficients of the momentum operator
-    if (rc) return rc;
-    rc = launch_transport_velocity(h, s);
-    if (rc) return rc;
-    h->has_fields = true;
-    h->diag_valid = false;
-    h->cont_valid = false;
-    return EVAP_OK;
+    return launch_transport_velocity(h, s);
 }
 
 int evap_set_transport_velocity(evap_handle h, const double* u_gamma, void* stream) {
@@ -422,15 +434,16 @@ int evap_solve_saddle(evap_handle h, const double* f, double* x, double* p, int 
 }
 
 int evap_time_step(evap_handle h, double* phi, double* u, double* p, const double* mdot, const double* u_prev,
-                   const double* gravity, int fp_iters, int reinit_steps, double ns_rtol, int* ns_iters,
-                   double* ns_relres, void* stream) {
+                   const double* gravity, int picard_iters, double picard_atol, int fp_iters, int reinit_steps,
+                   double ns_rtol, int* ns_iters, double* ns_relres, double* picard_res, void* stream) {
     if (!h || !phi || !u || !p || !mdot) return fail(EVAP_EINVAL, "evap_time_step: null argument");
     if (h->m.newton != 0) return fail(EVAP_EINVAL, "evap_time_step: the step takes a Picard linearization (newton = 0)");
     if (!(h->m.dt > 0.0)) return fail(EVAP_EINVAL, "evap_time_step: dt must be > 0");
     if ((h->m.faces & 0x3Fu) == 0x3Fu)
         return fail(EVAP_EINVAL, "evap_time_step: every face is Dirichlet (the pressure level is undetermined)");
-    if (fp_iters < 1 || reinit_steps < 0 || !(ns_rtol > 0.0))
-        return fail(EVAP_EINVAL, "evap_time_step: need fp_iters >= 1, reinit_steps >= 0, ns_rtol > 0");
+    if (picard_iters < 1 || !(picard_atol >= 0.0) || fp_iters < 1 || reinit_steps < 0 || !(ns_rtol > 0.0))
+        return fail(EVAP_EINVAL, "evap_time_step: need picard_iters >= 1, picard_atol >= 0, fp_iters >= 1, "
+                                 "reinit_steps >= 0, ns_rtol > 0");
     cudaStream_t s = (cudaStream_t)stream;
     int rc0 = check_inputs(h, "evap_time_step", s, {{p, h->m.Nphi, false}, {u_prev, 3 * h->m.Nu, false}});
     if (rc0) return rc0;
@@ -440,7 +453,8 @@ int evap_time_step(evap_handle h, double* phi, double* u, double* p, const doubl
         g[1] = gravity[1];
         g[2] = gravity[2];
     }
-    return time_step(h, phi, u, p, mdot, u_prev, g, fp_iters, reinit_steps, ns_rtol, ns_iters, ns_relres, s);
+    return time_step(h, phi, u, p, mdot, u_prev, g, picard_iters, picard_atol, fp_iters, reinit_steps, ns_rtol,
+                     ns_iters, ns_relres, picard_res, s);
 }
 
 int evap_surface_tension(evap_handle h, const double* n, const double* kappa, double alpha, double* f, void* stream) {

@@ -1,7 +1,8 @@
 // One time step of the coupled problem: the Navier-Stokes step, then Algorithm 2 (level-set solver).
-//   1. velocity-pressure solve with one Picard linearization about u^n (newton = 0): BDF1 (c_m = 1/dt, u* = u^n) or,
-//      given u^(n-1), BDF2 (c_m = 3/(2 dt), u* = (4 u^n - u^(n-1)) / 3):
-//        [A(u^n), -B^T; B, 0] [u^(n+1); p^(n+1)] = [f; g],  f = sum_q W N_i rho (c_m u* + g_body)
+//   1. velocity-pressure solve with Picard iterations (newton = 0): BDF1 (c_m = 1/dt, u* = u^n) or, given u^(n-1),
+//      BDF2 (c_m = 3/(2 dt), u* = (4 u^n - u^(n-1)) / 3); iteration k solves
+//        [A(u^(k)), -B^T; B, 0] [u^(k+1); p^(k+1)] = [f; g],  f = sum_q W N_i rho (c_m u* + g_body),  u^(0) = u^n,
+//      at most picard_iters times, stopping before a solve once |[f; g] - K(u^(k)) [u^(k); p^(k)]| <= picard_atol
 //   2. advection fixed point with the transport velocity of u^(n+1) (Algorithm 2 step 1), the result clamped to
 //      [-1, 1]; its projected normal (Eq. normal_vector_regularized); reinitialization steps with that normal frozen
 //      (Algorithm 2 step 2), starting from the clamped field.
@@ -24,6 +25,25 @@ __global__ void k_bdf2_star(const double* __restrict__ u, const double* __restri
         us[i] = (4.0 * u[i] - up[i]) / 3.0;
 }
 
+// *out += sum_i (b_i - a_i)^2 (one atomic per block)
+__global__ void __launch_bounds__(256) k_diff_sq(const double* __restrict__ a, const double* __restrict__ b,
+                                                 int64_t N, double* out) {
+    __shared__ double sh[8];
+    double s = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const double d = b[i] - a[i];
+        s += d * d;
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += sh[w];
+        atomicAdd(out, t);
+    }
+}
+
 // The mesh's mass coefficient set to the scheme's for the duration of a step.
 struct MassCoefficient {
     evap_mesh* h;
@@ -33,21 +53,24 @@ struct MassCoefficient {
 };
 
 int time_step(evap_mesh* h, double* phi, double* u, double* p, const double* mdot, const double* u_prev,
-              const double g[3], int fp_iters, int reinit_steps, double ns_rtol, int* ns_iters, double* ns_relres,
-              cudaStream_t s) {
+              const double g[3], int picard_iters, double picard_atol, int fp_iters, int reinit_steps, double ns_rtol,
+              int* ns_iters, double* ns_relres, double* picard_res, cudaStream_t s) {
     const int64_t Nu3 = 3 * h->m.Nu, Np = h->m.Nphi;
+    // workspace: f, u* [3 N_u]; residual [3 N_u + N_phi]; advected level set [N_phi]; normal [3 N_phi]; scalar
     if (!h->step_ws) {
-        EVAP_CUDA(cudaMalloc(&h->step_ws, (2 * Nu3 + 4 * Np) * sizeof(double)));
+        EVAP_CUDA(cudaMalloc(&h->step_ws, (3 * Nu3 + 5 * Np + 1) * sizeof(double)));
     }
     double* f = h->step_ws;
     double* ustar = f + Nu3;
-    double* adv = ustar + Nu3;
+    double* res = ustar + Nu3;
+    double* adv = res + Nu3 + Np;
     double* nrm = adv + Np;
+    double* sq = nrm + 3 * Np;
     MassCoefficient cm(h, (u_prev ? 1.5 : 1.0) / h->m.dt);
-    int rc = evap_set_fields(h, phi, u, mdot, s);
+    int rc = set_fields_flow(h, phi, u, mdot, s);  // the advection computes its own transport velocities
     if (rc) return rc;
     int status = EVAP_OK;
-    // 1. Navier-Stokes: the inertia load of u* (plus the body force), then the saddle solve from (u^n, p^n)
+    // 1. Navier-Stokes: the inertia load of u* (plus the body force), then Picard iterations from (u^n, p^n)
     const double* us = u;
     if (u_prev) {
         k_bdf2_star<<<blocks_for(Nu3, 256), 256, 0, s>>>(u, u_prev, ustar, Nu3);
@@ -55,9 +78,34 @@ int time_step(evap_mesh* h, double* phi, double* u, double* p, const double* mdo
         us = ustar;
     }
     if ((rc = launch_mass_load(h, us, g, f, s))) return rc;
-    rc = solve_saddle(h, f, u, p, 30, ns_rtol, 2000, ns_iters, ns_relres, s);
-    if (rc == EVAP_ENOTCONV) status = rc;
-    else if (rc) return rc;
+    int applies = 0;
+    double relres = 0.0, nl = -1.0;
+    for (int it = 0; it < picard_iters; ++it) {
+        if (it > 0) {  // relinearize about the latest iterate and evaluate the nonlinear residual
+            if ((rc = set_fields_flow(h, h->phi, u, h->mdot, s))) return rc;
+            const double* gc = nullptr;
+            if ((rc = continuity_rhs(h, &gc, s))) return rc;
+            if ((rc = launch_saddle_apply(h, u, p, res, res + Nu3, s))) return rc;
+            EVAP_CUDA(cudaMemsetAsync(sq, 0, sizeof(double), s));
+            k_diff_sq<<<blocks_for(Nu3, 256, 152 * 8), 256, 0, s>>>(res, f, Nu3, sq);
+            EVAP_CHECK_LAUNCH("picard_residual");
+            k_diff_sq<<<blocks_for(Np, 256, 152 * 8), 256, 0, s>>>(res + Nu3, gc, Np, sq);
+            EVAP_CHECK_LAUNCH("picard_residual");
+            double hs = 0.0;
+            EVAP_CUDA(cudaMemcpyAsync(&hs, sq, sizeof(double), cudaMemcpyDeviceToHost, s));
+            EVAP_CUDA(cudaStreamSynchronize(s));
+            nl = std::sqrt(hs);
+            if (nl <= picard_atol) break;
+        }
+        int its = 0;
+        rc = solve_saddle(h, f, u, p, 30, ns_rtol, 2000, &its, &relres, s);
+        applies += its;
+        if (rc == EVAP_ENOTCONV) status = rc;
+        else if (rc) return rc;
+    }
+    if (ns_iters) *ns_iters = applies;
+    if (ns_relres) *ns_relres = relres;
+    if (picard_res) *picard_res = nl;
     // 2. level set with the transport velocity of u^(n+1)
     EVAP_CUDA(cudaMemcpyAsync(h->u, u, Nu3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
     rc = geo_advect_levelset(h, adv, fp_iters, 0.0, nullptr, nullptr, nullptr, s);

@@ -119,3 +119,30 @@ def test_time_step_rest_state_and_arguments():
     bad = make_op(n, dict(prm, newton=1))
     with pytest.raises(EvapError):
         bad.time_step(cuda(phi), z, cuda(np.zeros(mesh.n_phi)), cuda(np.zeros(mesh.n_phi)))
+
+
+def test_time_step_picard_iterations_against_oracle():
+    """Three Picard iterations in a step with a strong random velocity: the state after the step and the last
+    nonlinear residual match the oracle's (residual to 1e-2 relative: it is a difference of near-equal vectors)."""
+    n = 5
+    prm, phi, mdot = slab(n, 1, 20.0)
+    mesh = fe.Mesh(n, 2, 1.0)
+    from oracle import momentum
+    u = np.random.default_rng(3).uniform(-0.3, 0.3, 3 * mesh.n_u)
+    u[momentum.Problem(mesh=mesh, params=dict(prm), phi=phi, u0=u, mdot=mdot).constrained()] = 0.0
+    p = np.zeros(mesh.n_phi)
+    op = make_op(n, prm)
+    gphi, gu, gp, info = op.time_step(cuda(phi), cuda(u), cuda(p), cuda(mdot), fp_iters=1, reinit_steps=1,
+                                      ns_rtol=1e-10, picard_iters=3, picard_atol=0.0)
+    res = []
+    ophi, ou, op_ = step.time_step(mesh, prm, phi, u, p, mdot, fp_iters=1, reinit_steps=1, picard_iters=3,
+                                   residuals=res)
+    assert info["converged"], info
+    assert rel(host(gu), ou) < 1e-6
+    assert rel(host(gp), op_) < 1e-5
+    assert np.abs(host(gphi) - ophi).max() < 1e-7
+    assert info["picard_res"] == pytest.approx(res[-1], rel=1e-2)
+    # a tolerance above the first residual stops after one solve
+    _, _, _, info1 = op.time_step(cuda(phi), cuda(u), cuda(p), cuda(mdot), fp_iters=1, reinit_steps=1,
+                                  ns_rtol=1e-10, picard_iters=3, picard_atol=10 * res[0])
+    assert info1["picard_res"] == pytest.approx(res[0], rel=1e-2)
