@@ -231,7 +231,8 @@ int evap_solve_saddle(evap_handle h, const double* f, double* x, double* p, int 
  *      latest iterate u^(k) (u^(0) = u^n), at most picard_iters solves by evap_solve_saddle (restart 30, ns_rtol, at
  *      most 2000 applications each, from the latest iterate), stopping before a solve once the nonlinear residual
  *      |[f; g] - K(u^(k)) [u^(k); p^(k)]| is <= picard_atol (the paper's Navier-Stokes nonlinear tolerance is 1e-10);
- *      picard_iters = 1 gives the semi-implicit step;
+ *      picard_iters = 1 gives the semi-implicit step; with alpha != 0 (surface tension coefficient) f also carries
+ *      the force of evap_surface_tension with the projected normal and regularized curvature of phi^n;
  *   2. the advection fixed point (evap_advect_levelset, fp_iters passes, tol 0) with the transport velocity of
  *      u^(n+1), the result clamped to [-1, 1]; its projected normal; reinit_steps reinitialization steps with that
  *      normal frozen (evap_reinitialize), starting from the clamped field.
@@ -241,12 +242,13 @@ int evap_solve_saddle(evap_handle h, const double* f, double* x, double* p, int 
  * may be NULL): the last nonlinear residual evaluated (-1 if none, i.e. picard_iters = 1).  The call sets the fields from its
  * inputs first (as evap_set_fields) and leaves the mesh without fields afterwards (call evap_set_fields before the
  * next apply), with the unit-normal reinitialization operators restored.  Synchronizes the stream.  EVAP_EINVAL on
- * a Newton mesh, dt <= 0, a closed box, picard_iters < 1, picard_atol < 0, fp_iters < 1, reinit_steps < 0 or
- * ns_rtol <= 0; EVAP_ENOTCONV if a
+ * a Newton mesh, dt <= 0, a closed box, alpha != 0 with rho_l == rho_g, picard_iters < 1, picard_atol < 0,
+ * fp_iters < 1, reinit_steps < 0 or ns_rtol <= 0; EVAP_ENOTCONV if a
  * sub-solve missed its tolerance (the step is still completed). */
 int evap_time_step(evap_handle h, double* phi, double* u, double* p, const double* mdot, const double* u_prev,
-                   const double* gravity, int picard_iters, double picard_atol, int fp_iters, int reinit_steps,
-                   double ns_rtol, int* ns_iters, double* ns_relres, double* picard_res, void* stream);
+                   const double* gravity, double alpha, int picard_iters, double picard_atol, int fp_iters,
+                   int reinit_steps, double ns_rtol, int* ns_iters, double* ns_relres, double* picard_res,
+                   void* stream);
 
 /* Diagonal of the momentum operator [3 N_u] (1 on Dirichlet DoFs), the Jacobi preconditioner of evap_solve,
  * evaluated in FP32 arithmetic from the FP64 coefficient table and written as double. */

@@ -11,7 +11,10 @@ takes them in the order velocity first, then level set, each once:
      momentum operator of oracle.momentum for u0 = u^(k), newton = 0 and that c_m (A u = rho c_m u + rho (u^(k) .
      grad) u + viscous(u)),
         [A, -B^T; B, 0] [u^(n+1); p^(n+1)] = [f; g],   f_(i,c) = sum_q W N_i rho (c_m u*_c + g_c),
-     g the continuity right-hand side (oracle.saddle), Dirichlet rows of f zero (walls at rest).
+     g the continuity right-hand side (oracle.saddle), Dirichlet rows of f zero (walls at rest).  With a surface
+     tension coefficient alpha != 0, f also carries the surface-tension force of Eq. (surfaceTension)
+     (oracle.surface) with the projected normal and the regularized curvature of phi^n (Algorithm 2 step 3 of the
+     previous step).
   2. Level set, Algorithm 2: the advection fixed point (oracle.geometry.advect_levelset) with the velocity u^(n+1)
      and `fp_iters` passes; the advected field clamped to [-1, 1]; its projected normal (Eq.
      normal_vector_regularized); `reinit_steps` reinitialization steps with that normal frozen, starting from the
@@ -22,7 +25,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import fe, geometry, momentum, saddle
+from . import fe, geometry, momentum, saddle, surface
 
 
 def mass_load(pb: momentum.Problem, u: np.ndarray, gvec=(0.0, 0.0, 0.0)) -> np.ndarray:
@@ -41,7 +44,7 @@ def mass_load(pb: momentum.Problem, u: np.ndarray, gvec=(0.0, 0.0, 0.0)) -> np.n
 
 def time_step(mesh_u: fe.Mesh, params: dict, phi: np.ndarray, u: np.ndarray, p: np.ndarray, mdot: np.ndarray,
               fp_iters: int = 2, reinit_steps: int = 2, gvec=(0.0, 0.0, 0.0), u_prev=None, picard_iters: int = 1,
-              picard_atol: float = 0.0, residuals=None):
+              picard_atol: float = 0.0, residuals=None, alpha: float = 0.0):
     prm = dict(params)
     if int(prm.get("newton", 1)) != 0:
         raise ValueError("the step takes one Picard linearization: newton = 0")
@@ -50,6 +53,12 @@ def time_step(mesh_u: fe.Mesh, params: dict, phi: np.ndarray, u: np.ndarray, p: 
     pb = momentum.Problem(mesh=mesh_u, params=prm, phi=np.clip(phi, -1.0, 1.0), u0=np.array(u, dtype=float),
                           mdot=np.array(mdot, dtype=float))
     f = mass_load(pb, ustar, gvec)
+    mesh1 = fe.Mesh(mesh_u.n, 1, mesh_u.L)
+    if alpha != 0.0:
+        n0 = geometry.projected_normal(mesh1, pb.phi, prm.get("eta_n", 2.0))
+        kappa = geometry.curvature(mesh1, n0, prm.get("eta_kappa", 2.0))
+        f = f + surface.surface_tension_rhs(pb, n0, kappa, alpha)
+        f[pb.constrained()] = 0.0
     u1, p1 = np.array(u, dtype=float), np.array(p, dtype=float)
     for it in range(picard_iters):
         pb.u0 = u1
@@ -61,7 +70,6 @@ def time_step(mesh_u: fe.Mesh, params: dict, phi: np.ndarray, u: np.ndarray, p: 
             if res <= picard_atol:
                 break
         u1, p1 = saddle.solve(pb, f)
-    mesh1 = fe.Mesh(mesh_u.n, 1, mesh_u.L)
     adv, _ = geometry.advect_levelset(mesh_u, np.clip(phi, -1.0, 1.0), u1, mdot, prm, fp_iters)
     adv = np.clip(adv, -1.0, 1.0)
     n = geometry.projected_normal(mesh1, adv, prm.get("eta_n", 2.0))

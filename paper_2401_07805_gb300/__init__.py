@@ -59,7 +59,7 @@ SIGNATURES = {
     "evap_advect_levelset": (_c_int, [_vp, _vp, _c_int, _c_dbl, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int),
                                       ctypes.POINTER(_c_dbl), _vp]),
     "evap_set_checks": (_c_int, [_vp, _c_int]),
-    "evap_time_step": (_c_int, [_vp, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_c_dbl), _c_int, _c_dbl, _c_int,
+    "evap_time_step": (_c_int, [_vp, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_c_dbl), _c_dbl, _c_int, _c_dbl, _c_int,
                                 _c_int, _c_dbl, ctypes.POINTER(_c_int), ctypes.POINTER(_c_dbl),
                                 ctypes.POINTER(_c_dbl), _vp]),
     "evap_apply_saddle": (_c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
@@ -263,7 +263,8 @@ class Operator:
 
     def time_step(self, phi: torch.Tensor, u: torch.Tensor, p: torch.Tensor, mdot: torch.Tensor, gravity=None,
                   fp_iters: int = 2, reinit_steps: int = 2, ns_rtol: float = 1e-8, u_prev=None,
-                  picard_iters: int = 1, picard_atol: float = 1e-10, raise_on_notconv: bool = False):
+                  picard_iters: int = 1, picard_atol: float = 1e-10, alpha: float = 0.0,
+                  raise_on_notconv: bool = False):
         """One coupled step (Picard velocity-pressure solve, BDF1, or BDF2 given u_prev = u^(n-1); then Algorithm 2)
         from (phi, u, p) at t^n; returns new tensors (phi, u, p) at t^(n+1) and info."""
         phi = self._dev(phi, self.n_phi, torch.float64, "phi").clone()
@@ -273,8 +274,9 @@ class Operator:
         up = None if u_prev is None else self._dev(u_prev, 3 * self.n_u, torch.float64, "u_prev")
         g = None if gravity is None else (ctypes.c_double * 3)(*[float(v) for v in gravity])
         its, rel, nl = ctypes.c_int(), ctypes.c_double(), ctypes.c_double()
-        rc = lib().evap_time_step(self._h, _ptr(phi), _ptr(u), _ptr(p), _ptr(mdot), _ptr(up), g, int(picard_iters),
-                                  float(picard_atol), int(fp_iters), int(reinit_steps), float(ns_rtol),
+        rc = lib().evap_time_step(self._h, _ptr(phi), _ptr(u), _ptr(p), _ptr(mdot), _ptr(up), g, float(alpha),
+                                  int(picard_iters), float(picard_atol), int(fp_iters), int(reinit_steps),
+                                  float(ns_rtol),
                                   ctypes.byref(its), ctypes.byref(rel), ctypes.byref(nl), _stream())
         _check(rc, "evap_time_step", allow=() if raise_on_notconv else (-3,))
         return phi, u, p, dict(ns_iters=its.value, ns_relres=rel.value, picard_res=nl.value, converged=rc == 0)

@@ -434,13 +434,16 @@ int evap_solve_saddle(evap_handle h, const double* f, double* x, double* p, int 
 }
 
 int evap_time_step(evap_handle h, double* phi, double* u, double* p, const double* mdot, const double* u_prev,
-                   const double* gravity, int picard_iters, double picard_atol, int fp_iters, int reinit_steps,
-                   double ns_rtol, int* ns_iters, double* ns_relres, double* picard_res, void* stream) {
+                   const double* gravity, double alpha, int picard_iters, double picard_atol, int fp_iters,
+                   int reinit_steps, double ns_rtol, int* ns_iters, double* ns_relres, double* picard_res,
+                   void* stream) {
     if (!h || !phi || !u || !p || !mdot) return fail(EVAP_EINVAL, "evap_time_step: null argument");
     if (h->m.newton != 0) return fail(EVAP_EINVAL, "evap_time_step: the step takes a Picard linearization (newton = 0)");
     if (!(h->m.dt > 0.0)) return fail(EVAP_EINVAL, "evap_time_step: dt must be > 0");
     if ((h->m.faces & 0x3Fu) == 0x3Fu)
         return fail(EVAP_EINVAL, "evap_time_step: every face is Dirichlet (the pressure level is undetermined)");
+    if (alpha != 0.0 && !(h->m.rho_l != h->m.rho_g))
+        return fail(EVAP_EINVAL, "evap_time_step: surface tension needs rho_l != rho_g (c_rho)");
     if (picard_iters < 1 || !(picard_atol >= 0.0) || fp_iters < 1 || reinit_steps < 0 || !(ns_rtol > 0.0))
         return fail(EVAP_EINVAL, "evap_time_step: need picard_iters >= 1, picard_atol >= 0, fp_iters >= 1, "
                                  "reinit_steps >= 0, ns_rtol > 0");
@@ -453,7 +456,7 @@ int evap_time_step(evap_handle h, double* phi, double* u, double* p, const doubl
         g[1] = gravity[1];
         g[2] = gravity[2];
     }
-    return time_step(h, phi, u, p, mdot, u_prev, g, picard_iters, picard_atol, fp_iters, reinit_steps, ns_rtol,
+    return time_step(h, phi, u, p, mdot, u_prev, g, alpha, picard_iters, picard_atol, fp_iters, reinit_steps, ns_rtol,
                      ns_iters, ns_relres, picard_res, s);
 }
 

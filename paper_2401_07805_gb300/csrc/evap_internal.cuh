@@ -190,8 +190,8 @@ int launch_mass_load(evap_mesh* h, const double* u, const double g[3], double* f
 int set_fields_flow(evap_mesh* h, const double* phi, const double* u, const double* mdot, cudaStream_t s);
 // one coupled time step (step.cu; see evap_time_step)
 int time_step(evap_mesh* h, double* phi, double* u, double* p, const double* mdot, const double* u_prev,
-              const double g[3], int picard_iters, double picard_atol, int fp_iters, int reinit_steps, double ns_rtol,
-              int* ns_iters, double* ns_relres, double* picard_res, cudaStream_t s);
+              const double g[3], double alpha, int picard_iters, double picard_atol, int fp_iters, int reinit_steps,
+              double ns_rtol, int* ns_iters, double* ns_relres, double* picard_res, cudaStream_t s);
 // y_p += B D^(-1) x (the divergence row without its source; Dirichlet entries of x read as 0; D = diag, or the
 // identity when diag is null)
 template <typename T>

@@ -2,7 +2,9 @@
 //   1. velocity-pressure solve with Picard iterations (newton = 0): BDF1 (c_m = 1/dt, u* = u^n) or, given u^(n-1),
 //      BDF2 (c_m = 3/(2 dt), u* = (4 u^n - u^(n-1)) / 3); iteration k solves
 //        [A(u^(k)), -B^T; B, 0] [u^(k+1); p^(k+1)] = [f; g],  f = sum_q W N_i rho (c_m u* + g_body),  u^(0) = u^n,
-//      at most picard_iters times, stopping before a solve once |[f; g] - K(u^(k)) [u^(k); p^(k)]| <= picard_atol
+//      at most picard_iters times, stopping before a solve once |[f; g] - K(u^(k)) [u^(k); p^(k)]| <= picard_atol;
+//      with alpha != 0 f also carries the surface-tension force (Eq. surfaceTension) of the projected normal and
+//      regularized curvature of phi^n
 //   2. advection fixed point with the transport velocity of u^(n+1) (Algorithm 2 step 1), the result clamped to
 //      [-1, 1]; its projected normal (Eq. normal_vector_regularized); reinitialization steps with that normal frozen
 //      (Algorithm 2 step 2), starting from the clamped field.
@@ -23,6 +25,12 @@ __global__ void k_bdf2_star(const double* __restrict__ u, const double* __restri
                             int64_t N) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
         us[i] = (4.0 * u[i] - up[i]) / 3.0;
+}
+
+// y += x
+__global__ void k_axpy1(double* __restrict__ y, const double* __restrict__ x, int64_t N) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] += x[i];
 }
 
 // *out += sum_i (b_i - a_i)^2 (one atomic per block)
@@ -53,8 +61,8 @@ struct MassCoefficient {
 };
 
 int time_step(evap_mesh* h, double* phi, double* u, double* p, const double* mdot, const double* u_prev,
-              const double g[3], int picard_iters, double picard_atol, int fp_iters, int reinit_steps, double ns_rtol,
-              int* ns_iters, double* ns_relres, double* picard_res, cudaStream_t s) {
+              const double g[3], double alpha, int picard_iters, double picard_atol, int fp_iters, int reinit_steps,
+              double ns_rtol, int* ns_iters, double* ns_relres, double* picard_res, cudaStream_t s) {
     const int64_t Nu3 = 3 * h->m.Nu, Np = h->m.Nphi;
     // workspace: f, u* [3 N_u]; residual [3 N_u + N_phi]; advected level set [N_phi]; normal [3 N_phi]; scalar
     if (!h->step_ws) {
@@ -78,6 +86,17 @@ int time_step(evap_mesh* h, double* phi, double* u, double* p, const double* mdo
         us = ustar;
     }
     if ((rc = launch_mass_load(h, us, g, f, s))) return rc;
+    if (alpha != 0.0) {  // surface tension of phi^n: projected normal (nrm), curvature (adv), force (res)
+        rc = geo_projected_normal(h, nrm, nullptr, nullptr, s);
+        if (rc == EVAP_ENOTCONV) status = rc;
+        else if (rc) return rc;
+        rc = geo_curvature(h, nrm, adv, nullptr, nullptr, s);
+        if (rc == EVAP_ENOTCONV) status = rc;
+        else if (rc) return rc;
+        if ((rc = launch_surface_tension(h, nrm, adv, alpha, res, s))) return rc;
+        k_axpy1<<<blocks_for(Nu3, 256), 256, 0, s>>>(f, res, Nu3);
+        EVAP_CHECK_LAUNCH("step_add_surface");
+    }
     int applies = 0;
     double relres = 0.0, nl = -1.0;
     for (int it = 0; it < picard_iters; ++it) {

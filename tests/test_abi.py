@@ -84,7 +84,7 @@ def test_invalid_arguments_are_rejected_on_the_host(L):
                      ("evap_surface_tension", (None, None, None, 1.0, None, None)),
                      ("evap_advect_levelset", (None, None, 1, 0.0, None, None, None, None)),
                      ("evap_set_checks", (None, 1)),
-                     ("evap_time_step", (None,) * 7 + (1, 0.0, 1, 1, 1e-8, None, None, None, None)),
+                     ("evap_time_step", (None,) * 7 + (0.0, 1, 0.0, 1, 1, 1e-8, None, None, None, None)),
                      ("evap_apply_saddle", (None,) * 6),
                      ("evap_solve_saddle", (None, None, None, None, 30, 1e-8, 10, None, None, None)),
                      ("evap_update_transport_velocity", (None, None)),

@@ -146,3 +146,48 @@ def test_time_step_picard_iterations_against_oracle():
     _, _, _, info1 = op.time_step(cuda(phi), cuda(u), cuda(p), cuda(mdot), fp_iters=1, reinit_steps=1,
                                   ns_rtol=1e-10, picard_iters=3, picard_atol=10 * res[0])
     assert info1["picard_res"] == pytest.approx(res[0], rel=1e-2)
+
+
+def test_time_step_with_surface_tension_against_oracle():
+    """alpha != 0: the force of the projected normal and curvature of phi^n enters f; a drop (no evaporation) after
+    one step against the oracle's step."""
+    n = 6
+    prm, _, _ = slab(n, 1, 0.0)
+    q1 = workloads.node_coords(n, 1)
+    phi = np.tanh(workloads.signed_distance("sphere", q1, radius=0.3) / (2 * prm["eps"]))
+    mdot = np.zeros((n + 1) ** 3)
+    mesh = fe.Mesh(n, 2, 1.0)
+    op = make_op(n, prm)
+    u = np.zeros(3 * mesh.n_u)
+    p = np.zeros(mesh.n_phi)
+    gphi, gu, gp, info = op.time_step(cuda(phi), cuda(u), cuda(p), cuda(mdot), fp_iters=1, reinit_steps=1,
+                                      ns_rtol=1e-10, alpha=0.07)
+    ophi, ou, op_ = step.time_step(mesh, prm, phi, u, p, mdot, fp_iters=1, reinit_steps=1, alpha=0.07)
+    assert info["converged"], info
+    assert rel(host(gu), ou) < 1e-6
+    assert rel(host(gp), op_) < 1e-5
+    assert np.abs(host(gphi) - ophi).max() < 1e-7
+
+
+def test_static_drop_laplace_pressure_jump():
+    """A drop of radius R = 0.3 at rest on 32^3 (eps = h, no evaporation, viscous fluid, density ratio 10): after one
+    step the pressure inside exceeds the pressure outside by the Laplace jump alpha kappa = 2 alpha / R within 10 %
+    (the regularized curvature and the diffuse force at this resolution); the spurious velocities stay far below
+    the capillary scale alpha / mu."""
+    n = 32
+    R, alpha = 0.3, 0.07
+    prm, _, _ = slab(n, 1, 0.0, mu_l=1e-2, mu_g=1e-3)
+    q1 = workloads.node_coords(n, 1)
+    phi = np.tanh(workloads.signed_distance("sphere", q1, radius=R) / (2 * prm["eps"]))
+    mesh = fe.Mesh(n, 2, 1.0)
+    op = make_op(n, prm)
+    _, gu, gp, info = op.time_step(cuda(phi), cuda(np.zeros(3 * mesh.n_u)), cuda(np.zeros(mesh.n_phi)),
+                                   cuda(np.zeros(mesh.n_phi)), fp_iters=1, reinit_steps=1, ns_rtol=1e-10, alpha=alpha)
+    assert info["converged"], info
+    p = host(gp)
+    r = np.linalg.norm(q1 - 0.5, axis=1)
+    band = 3 * prm["eps"]
+    inside = p[r < R - band - 0.02].mean()
+    outside = p[(r > R + band + 0.02) & (q1[:, 2] < 0.85)].mean()
+    assert inside - outside == pytest.approx(2 * alpha / R, rel=0.10)
+    assert float(gu.abs().max()) < 1e-2 * alpha / prm["mu_l"]
