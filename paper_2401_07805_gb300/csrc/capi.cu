@@ -152,7 +152,8 @@ static void free_all(evap_mesh* h) {
     void* ptrs[] = {h->phi, h->u, h->mdot, h->u32, h->phi32, h->cell_code, h->table_index, h->table_count,
                     h->table, h->table32, h->qc, h->qc32, h->ugamma, h->ugamma32, h->cpp_flags, h->flag_count, h->band_list,
                     h->band_count, h->band_y, h->cpp_evals, h->ls_normal_store, h->ls_normal32_store, h->geo_ws, h->geo_elem, h->diag,
-                    h->diag32, h->ws, h->red, h->cont_rhs, h->sd_ws, h->sd_red, h->nonfinite, h->step_ws};
+                    h->diag32, h->ws, h->red, h->cont_rhs, h->sd_ws, h->sd_red, h->nonfinite, h->step_ws,
+                    h->tp_fac, h->tp_sigma};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->red_host) cudaFreeHost(h->red_host);
@@ -285,6 +286,7 @@ int set_fields_flow(evap_mesh* h, const double* phi, const double* u, const doub
     if (rc) return rc;
     h->has_fields = true;
     h->diag_valid = false;
+    h->tp_valid = false;
     h->cont_valid = false;
     return EVAP_OK;
 }

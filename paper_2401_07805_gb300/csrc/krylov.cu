@@ -329,6 +329,25 @@ __global__ void k_update(const T* __restrict__ V, int64_t ld, const double* __re
     }
 }
 
+// u = sum_i y[i] V_i (FP32)
+__global__ void k_combine(const float* __restrict__ V, int64_t ld, const double* __restrict__ y, int nv,
+                          float* __restrict__ u, int64_t N) {
+    __shared__ float ys[256];
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) ys[i] = (float)y[i];
+    __syncthreads();
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
+        float s = 0.0f;
+        for (int i = 0; i < nv; ++i) s += ys[i] * V[i * ld + k];
+        u[k] = s;
+    }
+}
+
+// x += u (FP32)
+__global__ void k_add_to(float* x, const float* __restrict__ u, int64_t N) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x)
+        x[k] += u[k];
+}
+
 // r = b - Ax
 template <typename T>
 __global__ void k_residual(const T* __restrict__ b, const T* __restrict__ Ax, T* __restrict__ r, int64_t N) {
@@ -365,6 +384,7 @@ enum { OP_MOMENTUM = 0, OP_ADVECT = 1 };
 struct Ctx {
     evap_mesh* h;
     int op;
+    bool tp = false;   // FP32 momentum solves: the tensor-product mass preconditioner instead of Jacobi
     cudaStream_t s;
     int64_t N, ld;
     double* partial;   // [(m+2) * RED_BLOCKS]
@@ -473,10 +493,19 @@ static int gmres(Ctx& c, int m, const T* b, T* x, bool x_zero, const T* diag, T*
                 EVAP_CHECK_LAUNCH("precond");
                 if ((rc = apply_op<T>(c, z, Wn))) return rc;
             } else {
-                const int M = c.h->m.M;
-                const unsigned gl = (unsigned)std::min<int64_t>((3 * (int64_t)M * M + 7) / 8, 152 * 16);
-                k_precond_init<T><<<gl, 256, 0, c.s>>>(M, c.h->m.Nu, c.h->m.faces, Vj, diag, (T)sc[j], z, Wn);
-                EVAP_CHECK_LAUNCH("precond");
+                bool done = false;
+                if constexpr (sizeof(T) == 4) {
+                    if (c.tp) {  // z = P (sc V_j), Wn initialized on the Dirichlet rows; w is the sweeps' scratch
+                        if ((rc = tensor_prec_apply(c.h, Vj, (float)sc[j], w, z, Wn, c.s))) return rc;
+                        done = true;
+                    }
+                }
+                if (!done) {
+                    const int M = c.h->m.M;
+                    const unsigned gl = (unsigned)std::min<int64_t>((3 * (int64_t)M * M + 7) / 8, 152 * 16);
+                    k_precond_init<T><<<gl, 256, 0, c.s>>>(M, c.h->m.Nu, c.h->m.faces, Vj, diag, (T)sc[j], z, Wn);
+                    EVAP_CHECK_LAUNCH("precond");
+                }
                 if ((rc = launch_momentum<T>(c.h, z, Wn, (T*)nullptr, c.s, false))) return rc;
             }
             ++used;
@@ -531,8 +560,22 @@ static int gmres(Ctx& c, int m, const T* b, T* x, bool x_zero, const T* diag, T*
         }
         for (int i = 0; i < k; ++i) c.hcol[i] = y[i] * sc[i];
         EVAP_CUDA(cudaMemcpyAsync(c.dcol, c.hcol, k * sizeof(double), cudaMemcpyHostToDevice, c.s));
-        k_update<T><<<G, 256, 0, c.s>>>(V, c.ld, c.dcol, k, diag, x, N);
-        EVAP_CHECK_LAUNCH("update");
+        bool updated = false;
+        if constexpr (sizeof(T) == 4) {
+            if (c.tp && c.op == OP_MOMENTUM) {  // x += P (sum_i y_i sc_i V_i): combination in z, P into the free slot V_k
+                k_combine<<<G, 256, 0, c.s>>>(V, c.ld, c.dcol, k, z, N);
+                EVAP_CHECK_LAUNCH("combine");
+                T* Vk = V + (int64_t)k * c.ld;
+                if ((rc = tensor_prec_apply(c.h, z, 1.0f, w, Vk, nullptr, c.s))) return rc;
+                k_add_to<<<G, 256, 0, c.s>>>(x, Vk, N);
+                EVAP_CHECK_LAUNCH("update");
+                updated = true;
+            }
+        }
+        if (!updated) {
+            k_update<T><<<G, 256, 0, c.s>>>(V, c.ld, c.dcol, k, diag, x, N);
+            EVAP_CHECK_LAUNCH("update");
+        }
         EVAP_CUDA(cudaStreamSynchronize(c.s));  // c.hcol is reused by the next fetch
     }
     *its = used;
@@ -623,6 +666,11 @@ int solve_gmres(evap_mesh* h, const double* f, double* x, int mixed, int m, doub
         double* r64 = (double*)(base + fV + 4 * fN);
         double* Ax = (double*)(base + fV + 4 * fN + dN);
         const double inner_rtol = 1e-5;
+        if (!h->tp_valid) {
+            if ((rc = tensor_prec_setup(h, s))) return rc;
+            h->tp_valid = true;
+        }
+        c.tp = true;  // the inner FP32 solve takes the tensor-product mass preconditioner
         while (true) {
             if (x_zero) {  // r = f
                 EVAP_CUDA(cudaMemcpyAsync(r64, f, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -780,6 +828,11 @@ int solve_saddle(evap_mesh* h, const double* f, double* x, double* p, int m, dou
     const size_t fV = al256((size_t)(SADDLE_INNER_M + 1) * ldu * sizeof(float)), fN = al256((size_t)ldu * sizeof(float));
     Ctx inner;
     if ((rc = prepare(h, OP_MOMENTUM, SADDLE_INNER_M, Nu3, ldu, fV + 4 * fN, s, inner))) return rc;
+    if (!h->tp_valid) {
+        if ((rc = tensor_prec_setup(h, s))) return rc;
+        h->tp_valid = true;
+    }
+    inner.tp = true;
     SaddleSpace sp;
     sp.sdiag = sdiag;
     char* ib = (char*)h->ws;
