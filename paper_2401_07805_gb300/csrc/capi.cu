@@ -153,7 +153,7 @@ static void free_all(evap_mesh* h) {
                     h->table, h->table32, h->qc, h->qc32, h->ugamma, h->ugamma32, h->cpp_flags, h->flag_count, h->band_list,
                     h->band_count, h->band_y, h->cpp_evals, h->ls_normal_store, h->ls_normal32_store, h->geo_ws, h->geo_elem, h->diag,
                     h->diag32, h->ws, h->red, h->cont_rhs, h->sd_ws, h->sd_red, h->nonfinite, h->step_ws,
-                    h->tp_fac, h->tp_sigma};
+                    h->tp_fac, h->tp_sigma, h->tp_sigma64};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->red_host) cudaFreeHost(h->red_host);

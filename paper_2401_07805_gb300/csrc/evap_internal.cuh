@@ -126,11 +126,14 @@ struct evap_mesh {
     unsigned long long* nonfinite = nullptr;
     // time step workspace: inertia load [3 N_u], advected level set [N_phi], projected normal [3 N_phi]
     double* step_ws = nullptr;
-    // tensor-product mass preconditioner of the FP32 inner solve: banded LU factors of the three axes and the 1D
-    // mass diagonal (floats), Sigma [3 N_u]; valid with the FP32 Jacobi diagonal it was built from
-    float* tp_fac = nullptr;
+    // tensor-product mass preconditioner of the momentum solves: banded LU factors of the three axes (FP64 [nf],
+    // the 1D mass diagonal FP64 [M], FP32 copy of the factors [nf]), Sigma [3 N_u] in FP32 and FP64; valid with the
+    // Jacobi diagonal it was built from
+    void* tp_fac = nullptr;
     size_t tp_fac_len = 0;
+    int64_t tp_nf = 0;
     float* tp_sigma = nullptr;
+    double* tp_sigma64 = nullptr;
     int tp_lo[3] = {0, 0, 0}, tp_hi[3] = {0, 0, 0};
     int64_t tp_off[3] = {0, 0, 0};
     bool tp_valid = false;
@@ -211,10 +214,11 @@ int schur_apply(evap_mesh* h, const double* r, double* z, const double* d, float
 int launch_surface_tension(evap_mesh* h, const double* nf, const double* kappa, double alpha, double* out,
                            cudaStream_t s);
 int launch_diagonal_into(evap_mesh* h, float* acc, double* out, cudaStream_t s);
-// tensor-product mass preconditioner of the FP32 inner solve (precond.cu): setup after the Jacobi diagonal, apply
+// tensor-product mass preconditioner of the momentum solves (precond.cu): setup after the Jacobi diagonal, apply
 // z = P (sc v) with scratch t (and w = Dirichlet ? z : 0 when w is given)
 int tensor_prec_setup(evap_mesh* h, cudaStream_t s);
-int tensor_prec_apply(evap_mesh* h, const float* v, float sc, float* t, float* z, float* w, cudaStream_t s);
+template <typename T>
+int tensor_prec_apply(evap_mesh* h, const T* v, T sc, T* t, T* z, T* w, cudaStream_t s);
 int solve_gmres(evap_mesh* h, const double* f, double* x, int mixed, int restart, double rtol, int max_iter,
                 int* iters, double* relres, cudaStream_t s);
 // GMRES(restart) with the Jacobi diagonal `diag` on the Q1 advection system (the EVAP_ADVECT operator with the mesh's

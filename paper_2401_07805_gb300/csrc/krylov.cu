@@ -329,21 +329,23 @@ __global__ void k_update(const T* __restrict__ V, int64_t ld, const double* __re
     }
 }
 
-// u = sum_i y[i] V_i (FP32)
-__global__ void k_combine(const float* __restrict__ V, int64_t ld, const double* __restrict__ y, int nv,
-                          float* __restrict__ u, int64_t N) {
-    __shared__ float ys[256];
-    for (int i = threadIdx.x; i < nv; i += blockDim.x) ys[i] = (float)y[i];
+// u = sum_i y[i] V_i
+template <typename T>
+__global__ void k_combine(const T* __restrict__ V, int64_t ld, const double* __restrict__ y, int nv,
+                          T* __restrict__ u, int64_t N) {
+    __shared__ T ys[256];
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) ys[i] = (T)y[i];
     __syncthreads();
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
-        float s = 0.0f;
+        T s = 0;
         for (int i = 0; i < nv; ++i) s += ys[i] * V[i * ld + k];
         u[k] = s;
     }
 }
 
-// x += u (FP32)
-__global__ void k_add_to(float* x, const float* __restrict__ u, int64_t N) {
+// x += u
+template <typename T>
+__global__ void k_add_to(T* x, const T* __restrict__ u, int64_t N) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x)
         x[k] += u[k];
 }
@@ -384,7 +386,7 @@ enum { OP_MOMENTUM = 0, OP_ADVECT = 1 };
 struct Ctx {
     evap_mesh* h;
     int op;
-    bool tp = false;   // FP32 momentum solves: the tensor-product mass preconditioner instead of Jacobi
+    bool tp = false;   // momentum solves: the tensor-product mass preconditioner instead of Jacobi
     cudaStream_t s;
     int64_t N, ld;
     double* partial;   // [(m+2) * RED_BLOCKS]
@@ -494,11 +496,9 @@ static int gmres(Ctx& c, int m, const T* b, T* x, bool x_zero, const T* diag, T*
                 if ((rc = apply_op<T>(c, z, Wn))) return rc;
             } else {
                 bool done = false;
-                if constexpr (sizeof(T) == 4) {
-                    if (c.tp) {  // z = P (sc V_j), Wn initialized on the Dirichlet rows; w is the sweeps' scratch
-                        if ((rc = tensor_prec_apply(c.h, Vj, (float)sc[j], w, z, Wn, c.s))) return rc;
-                        done = true;
-                    }
+                if (c.tp) {  // z = P (sc V_j), Wn initialized on the Dirichlet rows; w is the sweeps' scratch
+                    if ((rc = tensor_prec_apply<T>(c.h, Vj, (T)sc[j], w, z, Wn, c.s))) return rc;
+                    done = true;
                 }
                 if (!done) {
                     const int M = c.h->m.M;
@@ -561,16 +561,14 @@ static int gmres(Ctx& c, int m, const T* b, T* x, bool x_zero, const T* diag, T*
         for (int i = 0; i < k; ++i) c.hcol[i] = y[i] * sc[i];
         EVAP_CUDA(cudaMemcpyAsync(c.dcol, c.hcol, k * sizeof(double), cudaMemcpyHostToDevice, c.s));
         bool updated = false;
-        if constexpr (sizeof(T) == 4) {
-            if (c.tp && c.op == OP_MOMENTUM) {  // x += P (sum_i y_i sc_i V_i): combination in z, P into the free slot V_k
-                k_combine<<<G, 256, 0, c.s>>>(V, c.ld, c.dcol, k, z, N);
-                EVAP_CHECK_LAUNCH("combine");
-                T* Vk = V + (int64_t)k * c.ld;
-                if ((rc = tensor_prec_apply(c.h, z, 1.0f, w, Vk, nullptr, c.s))) return rc;
-                k_add_to<<<G, 256, 0, c.s>>>(x, Vk, N);
-                EVAP_CHECK_LAUNCH("update");
-                updated = true;
-            }
+        if (c.tp && c.op == OP_MOMENTUM) {  // x += P (sum_i y_i sc_i V_i): combination in z, P into the free slot V_k
+            k_combine<T><<<G, 256, 0, c.s>>>(V, c.ld, c.dcol, k, z, N);
+            EVAP_CHECK_LAUNCH("combine");
+            T* Vk = V + (int64_t)k * c.ld;
+            if ((rc = tensor_prec_apply<T>(c.h, z, T(1), w, Vk, (T*)nullptr, c.s))) return rc;
+            k_add_to<T><<<G, 256, 0, c.s>>>(x, Vk, N);
+            EVAP_CHECK_LAUNCH("update");
+            updated = true;
         }
         if (!updated) {
             k_update<T><<<G, 256, 0, c.s>>>(V, c.ld, c.dcol, k, diag, x, N);
@@ -655,6 +653,11 @@ int solve_gmres(evap_mesh* h, const double* f, double* x, int mixed, int m, doub
         double* w = (double*)(base + dV);
         double* z = (double*)(base + dV + dN);
         int its = 0;
+        if (!h->tp_valid) {
+            if ((rc = tensor_prec_setup(h, s))) return rc;
+            h->tp_valid = true;
+        }
+        c.tp = true;  // the same preconditioner as the mixed solve's inner iterations
         if ((rc = gmres<double>(c, m, f, x, x_zero, h->diag, V, w, z, rtol * fn, max_iter, &its, &res))) return rc;
         used = its;
     } else {

@@ -27,12 +27,11 @@ constexpr int TP_THREADS = 256;  // threads of a block: all load and store the t
 
 // Factor layout per axis (floats, Mf = hi - lo + 1 free nodes): rows k = 0..P-1 hold L[i][i-1-k], rows P..2P-1 hold
 // U[i][i+1+(k-P)], row 2P holds 1 / U[i][i].
-template <int P>
-__device__ __forceinline__ void tp_solve_line(const float* __restrict__ fac, int Mf, float* __restrict__ col,
-                                              int stride) {
+template <typename T, int P>
+__device__ __forceinline__ void tp_solve_line(const T* __restrict__ fac, int Mf, T* __restrict__ col, int stride) {
     // forward: L y = d (unit lower)
     for (int i = 0; i < Mf; ++i) {
-        float v = col[i * stride];
+        T v = col[i * stride];
 #pragma unroll
         for (int k = 0; k < P; ++k)
             if (i - 1 - k >= 0) v -= fac[k * Mf + i] * col[(i - 1 - k) * stride];
@@ -40,7 +39,7 @@ __device__ __forceinline__ void tp_solve_line(const float* __restrict__ fac, int
     }
     // backward: U x = y
     for (int i = Mf - 1; i >= 0; --i) {
-        float v = col[i * stride];
+        T v = col[i * stride];
 #pragma unroll
         for (int k = 0; k < P; ++k)
             if (i + 1 + k < Mf) v -= fac[(P + k) * Mf + i] * col[(i + 1 + k) * stride];
@@ -52,15 +51,16 @@ __device__ __forceinline__ void tp_solve_line(const float* __restrict__ fac, int
 // MODE 1: t = M_axis^(-1) t; MODE 2: z = Sigma M_axis^(-1) t on the free DoFs, z = sc v on the Dirichlet ones, and
 // w = (Dirichlet ? z : 0) (the initialization of the operator apply that follows).  One block per tile of TP_LANES
 // lines; lines whose transverse position is constrained are all-Dirichlet and are solved only as a copy in MODE 2.
-template <int P, int AXIS, int MODE>
-__global__ void __launch_bounds__(TP_THREADS) k_tp_sweep(int M, int64_t Nu, unsigned faces, const float* __restrict__ fac_all,
-                                                     int lo, int hi, const float* __restrict__ sigma,
-                                                     const float* __restrict__ v, float sc, float* __restrict__ t,
-                                                     float* __restrict__ z, float* __restrict__ w) {
-    extern __shared__ float smem[];
+template <typename T, int P, int AXIS, int MODE>
+__global__ void __launch_bounds__(TP_THREADS) k_tp_sweep(int M, int64_t Nu, unsigned faces, const T* __restrict__ fac_all,
+                                                     int lo, int hi, const T* __restrict__ sigma,
+                                                     const T* __restrict__ v, T sc, T* __restrict__ t,
+                                                     T* __restrict__ z, T* __restrict__ w) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* smem = reinterpret_cast<T*>(smem_raw);
     const int Mf = hi - lo + 1;
-    float* fac = smem;                     // (2P + 1) Mf
-    float* tile = smem + (2 * P + 1) * Mf;  // [M][TP_LANES + 1]
+    T* fac = smem;                     // (2P + 1) Mf
+    T* tile = smem + (2 * P + 1) * Mf;  // [M][TP_LANES + 1]
     const int tid = threadIdx.x;
     for (int i = tid; i < (2 * P + 1) * Mf; i += TP_THREADS) fac[i] = fac_all[i];
     // tile -> (component, first line); line l of the tile has transverse coordinates (ta, tb) and base address
@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(TP_THREADS) k_tp_sweep(int M, int64_t Nu, unsi
         else { l = k % nlines; e = k / nlines; }
         bool cons;
         const int64_t a = line_base(l, cons) + (int64_t)(lo + e) * es;
-        float val = 0.0f;
+        T val = 0;
         if (!cons) val = MODE == 0 ? sc * v[a] * sigma[a] : t[a];
         tile[e * (TP_LANES + 1) + l] = val;
     }
@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(TP_THREADS) k_tp_sweep(int M, int64_t Nu, unsi
     bool my_cons = true;
     if (tid < nlines) {
         line_base(tid, my_cons);
-        if (!my_cons) tp_solve_line<P>(fac, Mf, tile + tid, TP_LANES + 1);
+        if (!my_cons) tp_solve_line<T, P>(fac, Mf, tile + tid, TP_LANES + 1);
     }
     __syncthreads();
     if (MODE < 2) {
@@ -140,21 +140,22 @@ __global__ void __launch_bounds__(TP_THREADS) k_tp_sweep(int M, int64_t Nu, unsi
             bool cons;
             const int64_t a = line_base(l, cons) + (int64_t)e * es;
             const bool dir = cons || e < lo || e > hi;
-            const float zz = dir ? sc * v[a] : sigma[a] * tile[(e - lo) * (TP_LANES + 1) + l];
+            const T zz = dir ? sc * v[a] : sigma[a] * tile[(e - lo) * (TP_LANES + 1) + l];
             z[a] = zz;
-            if (w) w[a] = dir ? zz : 0.0f;
+            if (w) w[a] = dir ? zz : T(0);
         }
     }
 }
 
 // Sigma = sqrt(diag(M) / diag(A)) on the free DoFs (1 on the Dirichlet ones); md: the 1D mass diagonal [M].
-__global__ void k_tp_sigma(int M, int64_t Nu, unsigned faces, const float* __restrict__ md,
-                           const float* __restrict__ diag, float* __restrict__ sigma) {
+template <typename T>
+__global__ void k_tp_sigma(int M, int64_t Nu, unsigned faces, const double* __restrict__ md,
+                           const T* __restrict__ diag, T* __restrict__ sigma) {
     const int64_t N = 3 * Nu;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t node = i % Nu;
         const int x = (int)(node % M), y = (int)((node / M) % M), zc = (int)(node / ((int64_t)M * M));
-        sigma[i] = constrained_node(x, y, zc, M, faces) ? 1.0f : sqrtf(md[x] * md[y] * md[zc] / diag[i]);
+        sigma[i] = constrained_node(x, y, zc, M, faces) ? T(1) : (T)sqrt(md[x] * md[y] * md[zc] / (double)diag[i]);
     }
 }
 
@@ -172,7 +173,7 @@ static void mass_1d(const Basis<double>& b, int n, double h, std::vector<double>
             }
 }
 
-static void factor_band(const std::vector<double>& Mg, int M, int P, int lo, int hi, std::vector<float>& out) {
+static void factor_band(const std::vector<double>& Mg, int M, int P, int lo, int hi, std::vector<double>& out) {
     const int Mf = hi - lo + 1;
     std::vector<double> A((size_t)Mf * Mf);
     for (int i = 0; i < Mf; ++i)
@@ -183,82 +184,97 @@ static void factor_band(const std::vector<double>& Mg, int M, int P, int lo, int
             A[(size_t)i * Mf + j] = l;
             for (int c = j + 1; c <= std::min(j + P, Mf - 1); ++c) A[(size_t)i * Mf + c] -= l * A[(size_t)j * Mf + c];
         }
-    out.assign((size_t)(2 * P + 1) * Mf, 0.0f);
+    out.assign((size_t)(2 * P + 1) * Mf, 0.0);
     for (int i = 0; i < Mf; ++i) {
         for (int k = 0; k < P; ++k) {
-            if (i - 1 - k >= 0) out[(size_t)k * Mf + i] = (float)A[(size_t)i * Mf + (i - 1 - k)];
-            if (i + 1 + k < Mf) out[(size_t)(P + k) * Mf + i] = (float)A[(size_t)i * Mf + (i + 1 + k)];
+            if (i - 1 - k >= 0) out[(size_t)k * Mf + i] = A[(size_t)i * Mf + (i - 1 - k)];
+            if (i + 1 + k < Mf) out[(size_t)(P + k) * Mf + i] = A[(size_t)i * Mf + (i + 1 + k)];
         }
-        out[(size_t)2 * P * Mf + i] = (float)(1.0 / A[(size_t)i * Mf + i]);
+        out[(size_t)2 * P * Mf + i] = 1.0 / A[(size_t)i * Mf + i];
     }
 }
 
-// Factors of the three axes and Sigma for the current Jacobi diagonal (h->diag32 valid).
+// Factors of the three axes (FP64 and FP32 copies, then the 1D mass diagonal in FP64) and Sigma for the current
+// Jacobi diagonal (h->diag and h->diag32 valid) in both precisions.
 int tensor_prec_setup(evap_mesh* h, cudaStream_t s) {
     const MeshArgs<double>& m = h->m;
     const int P = m.P, M = m.M;
     const int64_t N = 3 * m.Nu;
     std::vector<double> Mg;
     mass_1d(h->b, m.n, m.h, Mg);
-    std::vector<float> all, md(M);
-    for (int i = 0; i < M; ++i) md[i] = (float)Mg[(size_t)i * M + i];
+    std::vector<double> all;
     for (int a = 0; a < 3; ++a) {
         const int lo = (m.faces & (1u << (2 * a))) ? 1 : 0;
         const int hi = (m.faces & (1u << (2 * a + 1))) ? M - 2 : M - 1;
         h->tp_lo[a] = lo;
         h->tp_hi[a] = hi;
         h->tp_off[a] = (int64_t)all.size();
-        std::vector<float> f;
+        std::vector<double> f;
         factor_band(Mg, M, P, lo, hi, f);
         all.insert(all.end(), f.begin(), f.end());
     }
-    const size_t need = all.size() + (size_t)M;
+    const size_t nf = all.size();
+    for (int i = 0; i < M; ++i) all.push_back(Mg[(size_t)i * M + i]);
+    // device layout (bytes): factors FP64 [nf], mass diagonal FP64 [M], factors FP32 [nf]
+    const size_t need = (nf + M) * sizeof(double) + nf * sizeof(float);
     if (h->tp_fac_len < need) {
         if (h->tp_fac) cudaFree(h->tp_fac);
         h->tp_fac = nullptr;
         h->tp_fac_len = 0;
-        EVAP_CUDA(cudaMalloc(&h->tp_fac, need * sizeof(float)));
+        EVAP_CUDA(cudaMalloc(&h->tp_fac, need));
         h->tp_fac_len = need;
     }
+    std::vector<float> f32(all.begin(), all.begin() + nf);
+    double* fac64 = (double*)h->tp_fac;
+    float* fac32 = (float*)(fac64 + nf + M);
+    h->tp_nf = (int64_t)nf;
+    EVAP_CUDA(cudaMemcpyAsync(fac64, all.data(), all.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    EVAP_CUDA(cudaMemcpyAsync(fac32, f32.data(), nf * sizeof(float), cudaMemcpyHostToDevice, s));
     if (!h->tp_sigma) EVAP_CUDA(cudaMalloc(&h->tp_sigma, N * sizeof(float)));
-    all.insert(all.end(), md.begin(), md.end());
-    EVAP_CUDA(cudaMemcpyAsync(h->tp_fac, all.data(), all.size() * sizeof(float), cudaMemcpyHostToDevice, s));
-    const float* mdd = h->tp_fac + (all.size() - M);
-    k_tp_sigma<<<blocks_for(N, 256), 256, 0, s>>>(M, m.Nu, m.faces, mdd, h->diag32, h->tp_sigma);
+    if (!h->tp_sigma64) EVAP_CUDA(cudaMalloc(&h->tp_sigma64, N * sizeof(double)));
+    k_tp_sigma<float><<<blocks_for(N, 256), 256, 0, s>>>(M, m.Nu, m.faces, fac64 + nf, h->diag32, h->tp_sigma);
     EVAP_CHECK_LAUNCH("tp_sigma");
-    EVAP_CUDA(cudaStreamSynchronize(s));  // the host staging vector goes out of scope
+    k_tp_sigma<double><<<blocks_for(N, 256), 256, 0, s>>>(M, m.Nu, m.faces, fac64 + nf, h->diag, h->tp_sigma64);
+    EVAP_CHECK_LAUNCH("tp_sigma");
+    EVAP_CUDA(cudaStreamSynchronize(s));  // the host staging vectors go out of scope
     return EVAP_OK;
 }
 
-template <int P, int AXIS, int MODE>
-static int tp_launch(evap_mesh* h, const float* v, float sc, float* t, float* z, float* w, cudaStream_t s) {
+template <typename T, int P, int AXIS, int MODE>
+static int tp_launch(evap_mesh* h, const T* v, T sc, T* t, T* z, T* w, cudaStream_t s) {
     const MeshArgs<double>& m = h->m;
     const int M = m.M;
     const int lo = h->tp_lo[AXIS], hi = h->tp_hi[AXIS], Mf = hi - lo + 1;
-    const size_t smem = ((size_t)(2 * P + 1) * Mf + (size_t)M * (TP_LANES + 1)) * sizeof(float);
+    const size_t smem = ((size_t)(2 * P + 1) * Mf + (size_t)M * (TP_LANES + 1)) * sizeof(T);
     if (smem > 48 * 1024)
-        EVAP_CUDA(cudaFuncSetAttribute(k_tp_sweep<P, AXIS, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        EVAP_CUDA(cudaFuncSetAttribute(k_tp_sweep<T, P, AXIS, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem));
+    const double* fac64 = (const double*)h->tp_fac;
+    const T* fac = sizeof(T) == 8 ? (const T*)fac64 : (const T*)(const void*)((const float*)(fac64 + h->tp_nf + M));
+    const T* sigma = sizeof(T) == 8 ? (const T*)h->tp_sigma64 : (const T*)h->tp_sigma;
     const int64_t M2 = (int64_t)M * M;
     const int64_t blocks = AXIS == 1 ? 3 * (int64_t)((M + TP_LANES - 1) / TP_LANES) * M
                                      : 3 * ((M2 + TP_LANES - 1) / TP_LANES);
-    k_tp_sweep<P, AXIS, MODE><<<(unsigned)blocks, TP_THREADS, smem, s>>>(M, m.Nu, m.faces, h->tp_fac + h->tp_off[AXIS],
-                                                                      lo, hi, h->tp_sigma, v, sc, t, z, w);
+    k_tp_sweep<T, P, AXIS, MODE><<<(unsigned)blocks, TP_THREADS, smem, s>>>(M, m.Nu, m.faces, fac + h->tp_off[AXIS],
+                                                                         lo, hi, sigma, v, sc, t, z, w);
     EVAP_CHECK_LAUNCH("tp_sweep");
     return EVAP_OK;
 }
 
 // z = P (sc v) (and w = Dirichlet ? z : 0 when w is given); t: scratch [3 N_u]; z must not alias v or t.
-int tensor_prec_apply(evap_mesh* h, const float* v, float sc, float* t, float* z, float* w, cudaStream_t s) {
+template <typename T>
+int tensor_prec_apply(evap_mesh* h, const T* v, T sc, T* t, T* z, T* w, cudaStream_t s) {
     int rc;
     if (h->m.P == 2) {
-        if ((rc = tp_launch<2, 0, 0>(h, v, sc, t, z, w, s))) return rc;
-        if ((rc = tp_launch<2, 1, 1>(h, v, sc, t, z, w, s))) return rc;
-        return tp_launch<2, 2, 2>(h, v, sc, t, z, w, s);
+        if ((rc = tp_launch<T, 2, 0, 0>(h, v, sc, t, z, w, s))) return rc;
+        if ((rc = tp_launch<T, 2, 1, 1>(h, v, sc, t, z, w, s))) return rc;
+        return tp_launch<T, 2, 2, 2>(h, v, sc, t, z, w, s);
     }
-    if ((rc = tp_launch<3, 0, 0>(h, v, sc, t, z, w, s))) return rc;
-    if ((rc = tp_launch<3, 1, 1>(h, v, sc, t, z, w, s))) return rc;
-    return tp_launch<3, 2, 2>(h, v, sc, t, z, w, s);
+    if ((rc = tp_launch<T, 3, 0, 0>(h, v, sc, t, z, w, s))) return rc;
+    if ((rc = tp_launch<T, 3, 1, 1>(h, v, sc, t, z, w, s))) return rc;
+    return tp_launch<T, 3, 2, 2>(h, v, sc, t, z, w, s);
 }
+template int tensor_prec_apply<float>(evap_mesh*, const float*, float, float*, float*, float*, cudaStream_t);
+template int tensor_prec_apply<double>(evap_mesh*, const double*, double, double*, double*, double*, cudaStream_t);
 
 }  // namespace evap
