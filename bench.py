@@ -45,8 +45,13 @@ def load_peaks():
 # sources are unchanged: {(kernel, workload): (bytes, sha256 prefix of the sources, profile summary)}.
 MEASURED_TRAFFIC = {
     ("k_momentum32", "spheres64"): (431_719_680, "a39b9c808096dfb6", "profiles/k_momentum32_spheres64.md"),
+    ("k_momentum64", "spheres64"): (1_228_852_224, "9de9670fb8e2d3b1", "profiles/k_momentum64_spheres64.md"),
 }
 TRAFFIC_SOURCES = {"k_momentum32": ("paper_2401_07805_gb300/csrc/momentum32.cu",
+                                    "paper_2401_07805_gb300/csrc/basis_ct.cuh",
+                                    "paper_2401_07805_gb300/csrc/evap_internal.cuh"),
+                   "k_momentum64": ("paper_2401_07805_gb300/csrc/momentum.cu",
+                                    "paper_2401_07805_gb300/csrc/physics.cuh",
                                     "paper_2401_07805_gb300/csrc/basis_ct.cuh",
                                     "paper_2401_07805_gb300/csrc/evap_internal.cuh")}
 
@@ -667,29 +672,37 @@ def main():
                         fp64_tflops=counts["adj_flop"] / (part["adjoint"] * 1e-3) / 1e12),
         "solve_mixed": dict(ms=part["solve"], iters=solve_info.get("iters"), relres=solve_info.get("relres")),
     }
-    # dominant kernel of the step: the FP32 momentum apply (the inner operator, ~60 launches per step in the solve).
-    # Its roofline bound is the larger of (algorithmic bytes / HBM peak) and (flops / FP32 peak): with the u0
-    # coefficients streamed (1.3 KB per Q2 cell) that is the HBM time; the FP32-pipe fraction is reported beside it.
+    # Dominant kernel of the step (largest share of the launch list): the FP64 momentum apply, launched three times
+    # per step (the step's own apply and the two FP64 residuals of the mixed solve).  It is bound by the FP64 pipe
+    # (~90 % active; its ~1.9 flop per algorithmic byte is ten times GB300's FP64 machine balance), so its roofline
+    # is the FP64 rate; its HBM fraction is reported beside it.  The FP32 apply inside the mixed solve (HBM-bound:
+    # its roof is the larger of bytes / HBM peak and flops / FP32 peak) follows as the second kernel.
+    g64 = counts["mom64_bytes"] / t_mom / 1e9
     t32 = part["mom32"] * 1e-3
     f32 = counts["mom32_flop"] / t32 / 1e12
     g32 = counts["mom32_bytes"] / t32 / 1e9
     hbm_bound = counts["mom32_bytes"] / (hbm * 1e9) >= counts["mom32_flop"] / (FP32_PEAK_TFLOPS * 1e12)
-    alu = dict(achieved=f32, peak=FP32_PEAK_TFLOPS, unit="TFLOP/s", frac=f32 / FP32_PEAK_TFLOPS,
-               flop_per_launch=counts["mom32_flop"],
-               peak_source="FP32 peak from the recipe's unit counts and max clock (152 SM x 128 lanes x 2 x 2.07 GHz); "
-                           "the FMA probe measured 73 TFLOP/s")
-    mem = dict(achieved=g32, peak=hbm, unit="GB/s", frac=g32 / hbm, bytes_per_launch=counts["mom32_bytes"],
-               peak_source=peak_src)
-    main, other = (mem, alu) if hbm_bound else (alu, mem)
-    roofline = dict(bound="hbm" if hbm_bound else "alu",
-                    kernel="k_momentum32<2,32,3> (FP32 momentum apply inside the mixed solve)",
-                    achieved=main["achieved"], peak=main["peak"], unit=main["unit"], frac=main["frac"],
-                    traffic=measured_traffic("k_momentum32", WORKLOAD),
-                    peak_source=main["peak_source"],
-                    **{"alu" if hbm_bound else "hbm": other},
-                    fp64_kernel=dict(kernel="k_momentum<double,2,8>", bound="alu", achieved=mom_tflops,
-                                     peak=FP64_PEAK_TFLOPS, unit="TFLOP/s", frac=mom_tflops / FP64_PEAK_TFLOPS,
-                                     peak_source="nominal FP64 rate (profiling recipe); FMA probe measured 1.19"))
+    alu32 = dict(achieved=f32, peak=FP32_PEAK_TFLOPS, unit="TFLOP/s", frac=f32 / FP32_PEAK_TFLOPS,
+                 flop_per_launch=counts["mom32_flop"],
+                 peak_source="FP32 peak from the recipe's unit counts and max clock (152 SM x 128 lanes x 2 x 2.07 "
+                             "GHz); the FMA probe measured 73 TFLOP/s")
+    mem32 = dict(achieved=g32, peak=hbm, unit="GB/s", frac=g32 / hbm, bytes_per_launch=counts["mom32_bytes"],
+                 peak_source=peak_src)
+    main32, other32 = (mem32, alu32) if hbm_bound else (alu32, mem32)
+    roofline = dict(bound="alu",
+                    kernel="k_momentum<double,2,8> (FP64 momentum apply: the step's apply and the two FP64 residuals "
+                           "of the mixed solve)",
+                    achieved=mom_tflops, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s", frac=mom_tflops / FP64_PEAK_TFLOPS,
+                    traffic=measured_traffic("k_momentum64", WORKLOAD), flop_per_launch=counts["mom_flop"],
+                    peak_source="nominal FP64 rate of the profiling recipe's table; an FMA probe measured 1.19 TFLOP/s",
+                    hbm=dict(achieved=g64, peak=hbm, unit="GB/s", frac=g64 / hbm,
+                             bytes_per_launch=counts["mom64_bytes"], peak_source=peak_src),
+                    fp32_kernel=dict(kernel="k_momentum32<2,32,3> (FP32 momentum apply inside the mixed solve)",
+                                     bound="hbm" if hbm_bound else "alu",
+                                     achieved=main32["achieved"], peak=main32["peak"], unit=main32["unit"],
+                                     frac=main32["frac"], traffic=measured_traffic("k_momentum32", WORKLOAD),
+                                     peak_source=main32["peak_source"],
+                                     **{"alu" if hbm_bound else "hbm": other32}))
     applies = None
     if rank == 0 and not args.no_applies:
         applies = operator_applies(evap, torch, dev, op, d, counts, hbm)
