@@ -29,21 +29,35 @@ constexpr int TP_THREADS = 256;  // threads of a block: all load and store the t
 // U[i][i+1+(k-P)], row 2P holds 1 / U[i][i].
 template <typename T, int P>
 __device__ __forceinline__ void tp_solve_line(const T* __restrict__ fac, int Mf, T* __restrict__ col, int stride) {
+    // The last P values of each recurrence stay in registers (win[0] the nearest), so a step waits on FMAs only; the
+    // factor rows are zero where a neighbour falls outside the line, so no step needs a branch.
+    T win[P];
+#pragma unroll
+    for (int k = 0; k < P; ++k) win[k] = T(0);
     // forward: L y = d (unit lower)
+#pragma unroll 4
     for (int i = 0; i < Mf; ++i) {
         T v = col[i * stride];
 #pragma unroll
-        for (int k = 0; k < P; ++k)
-            if (i - 1 - k >= 0) v -= fac[k * Mf + i] * col[(i - 1 - k) * stride];
+        for (int k = 0; k < P; ++k) v -= fac[k * Mf + i] * win[k];
         col[i * stride] = v;
+#pragma unroll
+        for (int k = P - 1; k > 0; --k) win[k] = win[k - 1];
+        win[0] = v;
     }
     // backward: U x = y
+#pragma unroll
+    for (int k = 0; k < P; ++k) win[k] = T(0);
+#pragma unroll 4
     for (int i = Mf - 1; i >= 0; --i) {
         T v = col[i * stride];
 #pragma unroll
-        for (int k = 0; k < P; ++k)
-            if (i + 1 + k < Mf) v -= fac[(P + k) * Mf + i] * col[(i + 1 + k) * stride];
-        col[i * stride] = v * fac[2 * P * Mf + i];
+        for (int k = 0; k < P; ++k) v -= fac[(P + k) * Mf + i] * win[k];
+        v *= fac[2 * P * Mf + i];
+        col[i * stride] = v;
+#pragma unroll
+        for (int k = P - 1; k > 0; --k) win[k] = win[k - 1];
+        win[0] = v;
     }
 }
 
@@ -104,45 +118,59 @@ __global__ void __launch_bounds__(TP_THREADS) k_tp_sweep(int M, int64_t Nu, unsi
         return cbase + base;
     };
     const int64_t es = AXIS == 0 ? 1 : (AXIS == 1 ? M : M2);  // element stride along the line
-    __syncthreads();
-    // load the free range of the tile's lines (coalesced: along the line for x-lines, across lines otherwise)
-    for (int k = tid; k < nlines * Mf; k += TP_THREADS) {
-        int l, e;
-        if (AXIS == 0) { l = k / Mf; e = k % Mf; }
-        else { l = k % nlines; e = k / nlines; }
-        bool cons;
-        const int64_t a = line_base(l, cons) + (int64_t)(lo + e) * es;
-        T val = 0;
-        if (!cons) val = MODE == 0 ? sc * v[a] * sigma[a] : t[a];
-        tile[e * (TP_LANES + 1) + l] = val;
-    }
-    __syncthreads();
-    bool my_cons = true;
+    // per-line base address and constraint flag, once per tile (the element loops below divide nothing)
+    __shared__ int64_t s_base[TP_LANES];
+    __shared__ int s_cons[TP_LANES];
     if (tid < nlines) {
-        line_base(tid, my_cons);
-        if (!my_cons) tp_solve_line<T, P>(fac, Mf, tile + tid, TP_LANES + 1);
+        bool cons;
+        s_base[tid] = line_base(tid, cons);
+        s_cons[tid] = cons ? 1 : 0;
     }
+    __syncthreads();
+    // element loops: x-lines are contiguous, so each line is read by consecutive threads; for y- and z-lines a warp
+    // reads one element of 32 neighbouring lines (contiguous in memory) and the eight warps take every eighth element
+    constexpr int ROWS = TP_THREADS / TP_LANES;
+    const int lane = tid % TP_LANES, row = tid / TP_LANES;
+    auto load = [&](int64_t a) -> T { return MODE == 0 ? sc * v[a] * sigma[a] : t[a]; };
+    if (AXIS == 0) {
+        for (int l = 0; l < nlines; ++l) {
+            if (s_cons[l]) continue;
+            const int64_t b = s_base[l] + lo;
+            for (int e = tid; e < Mf; e += TP_THREADS) tile[e * (TP_LANES + 1) + l] = load(b + e);
+        }
+    } else if (lane < nlines && !s_cons[lane]) {
+        const int64_t b = s_base[lane] + (int64_t)lo * es;
+        for (int e = row; e < Mf; e += ROWS) tile[e * (TP_LANES + 1) + lane] = load(b + (int64_t)e * es);
+    }
+    __syncthreads();
+    if (tid < nlines && !s_cons[tid]) tp_solve_line<T, P>(fac, Mf, tile + tid, TP_LANES + 1);
     __syncthreads();
     if (MODE < 2) {
-        for (int k = tid; k < nlines * Mf; k += TP_THREADS) {
-            int l, e;
-            if (AXIS == 0) { l = k / Mf; e = k % Mf; }
-            else { l = k % nlines; e = k / nlines; }
-            bool cons;
-            const int64_t a = line_base(l, cons) + (int64_t)(lo + e) * es;
-            if (!cons) t[a] = tile[e * (TP_LANES + 1) + l];
+        if (AXIS == 0) {
+            for (int l = 0; l < nlines; ++l) {
+                if (s_cons[l]) continue;
+                const int64_t b = s_base[l] + lo;
+                for (int e = tid; e < Mf; e += TP_THREADS) t[b + e] = tile[e * (TP_LANES + 1) + l];
+            }
+        } else if (lane < nlines && !s_cons[lane]) {
+            const int64_t b = s_base[lane] + (int64_t)lo * es;
+            for (int e = row; e < Mf; e += ROWS) t[b + (int64_t)e * es] = tile[e * (TP_LANES + 1) + lane];
         }
-    } else {  // every node of the tile's lines: free -> Sigma t, Dirichlet -> v; w = Dirichlet ? z : 0
-        for (int k = tid; k < nlines * M; k += TP_THREADS) {
-            int l, e;
-            if (AXIS == 0) { l = k / M; e = k % M; }
-            else { l = k % nlines; e = k / nlines; }
-            bool cons;
-            const int64_t a = line_base(l, cons) + (int64_t)e * es;
-            const bool dir = cons || e < lo || e > hi;
+    } else {  // every node of the tile's lines: free -> Sigma t, Dirichlet -> sc v; w = Dirichlet ? z : 0
+        auto put = [&](int l, int e, int64_t a) {
+            const bool dir = s_cons[l] || e < lo || e > hi;
             const T zz = dir ? sc * v[a] : sigma[a] * tile[(e - lo) * (TP_LANES + 1) + l];
             z[a] = zz;
             if (w) w[a] = dir ? zz : T(0);
+        };
+        if (AXIS == 0) {
+            for (int l = 0; l < nlines; ++l) {
+                const int64_t b = s_base[l];
+                for (int e = tid; e < M; e += TP_THREADS) put(l, e, b + e);
+            }
+        } else if (lane < nlines) {
+            const int64_t b = s_base[lane];
+            for (int e = row; e < M; e += ROWS) put(lane, e, b + (int64_t)e * es);
         }
     }
 }
