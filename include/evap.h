@@ -191,8 +191,10 @@ int evap_surface_tension(evap_handle h, const double* n, const double* kappa, do
 int evap_apply_adjoint(evap_handle h, const double* w, const double* w_p, const double* x, double* g_x,
                        double* g_u0, double* g_phi, double* g_mdot, void* stream);
 
-/* Solve A x = f for the momentum operator with restarted GMRES(restart) and right Jacobi preconditioning
- * (Table tab:solver_settings: GMRES with a diagonal preconditioner).  mixed = 0: FP64 throughout; mixed = 1:
+/* Solve A x = f for the momentum operator with restarted GMRES(restart) and a right preconditioner: the
+ * tensor-product mass inverse P = Sigma (Mx (x) My (x) Mz)^(-1) Sigma, Sigma = sqrt(diag(M) / diag(A)) on the free
+ * DoFs (the 1D Q_p mass matrices of the uniform mesh; the identity on Dirichlet DoFs), which fits the operator's
+ * dominant inertia term rho c_m M better than its diagonal alone.  mixed = 0: FP64 throughout; mixed = 1:
  * FP32 operator and Krylov basis inside FP64 iterative refinement (outer residual r = f - A x, norms and dot
  * products in FP64).  x holds the initial guess on entry and the solution on exit.  Stops when ||f - A x|| <=
  * rtol ||f|| (FP64 residual) or after max_iter operator applications.  iters_out (host, may be NULL): operator
@@ -211,10 +213,11 @@ int evap_solve(evap_handle h, const double* f, double* x, int mixed, int restart
 int evap_apply_saddle(evap_handle h, const double* x, const double* p, double* y, double* y_p, void* stream);
 
 /* Solve [A, -B^T; B, 0] [x; p] = [f; g] (g the continuity right-hand side of the fields) by flexible GMRES(restart)
- * with the block upper-triangular right preconditioner [A~, -B^T; 0, S~]: A~^(-1) a fixed budget of FP32 GMRES
- * iterations on A with its Jacobi preconditioner, S~^(-1) = c_m K_(1/rho)^(-1) + M_(1/mu)^(-1) (Cahouet-Chabard, the
- * pressure Laplacian weighted by 1/rho with p = 0 on the open faces, by CG, plus the lumped pressure mass weighted by
- * 1/mu): the block-triangular preconditioner of Sec. 2.5 with its ILU velocity block replaced by the FP32 GMRES.
+ * with the block upper-triangular right preconditioner [A~, -B^T; 0, S~]: A~^(-1) a fixed budget of 10 FP32 GMRES
+ * applications on A with the preconditioner of evap_solve, S~ = B diag(A)^(-1) B^T (an approximation of the Schur
+ * complement B A^(-1) B^T that keeps the discrete B and so the pressure nodes of open faces) solved by 24 CG
+ * iterations with its operator applied in FP32: the block-triangular preconditioner of Sec. 2.5 with its ILU velocity
+ * block and its Cahouet-Chabard Schur approximation replaced.
  * x, p hold the initial guess on entry and the solution on exit.  Stops when ||[f; g] - K [x; p]|| <= rtol ||[f; g]||
  * or after max_iter operator applications; iters (host, may be NULL): operator applications; relres (host, may be
  * NULL): the final relative residual.  Synchronizes the stream.  EVAP_EINVAL if every face is Dirichlet (the pressure
@@ -250,8 +253,8 @@ int evap_time_step(evap_handle h, double* phi, double* u, double* p, const doubl
                    int reinit_steps, double ns_rtol, int* ns_iters, double* ns_relres, double* picard_res,
                    void* stream);
 
-/* Diagonal of the momentum operator [3 N_u] (1 on Dirichlet DoFs), the Jacobi preconditioner of evap_solve,
- * evaluated in FP32 arithmetic from the FP64 coefficient table and written as double. */
+/* Diagonal of the momentum operator [3 N_u] (1 on Dirichlet DoFs; it sets the scale Sigma of evap_solve's
+ * preconditioner), evaluated in FP32 arithmetic from the FP64 coefficient table and written as double. */
 int evap_jacobi_diagonal(evap_handle h, double* diag, void* stream);
 
 /* Allocation-free variant of evap_jacobi_diagonal, for callers that cannot let the library call cudaMalloc when
