@@ -130,13 +130,13 @@ struct evap_mesh {
     // the 1D mass diagonal FP64 [M], FP32 copy of the factors [nf]), Sigma [3 N_u] in FP32 and FP64; valid with the
     // Jacobi diagonal it was built from
     void* tp_fac = nullptr;
-    size_t tp_fac_len = 0;
     int64_t tp_nf = 0;
     float* tp_sigma = nullptr;
     double* tp_sigma64 = nullptr;
     int tp_lo[3] = {0, 0, 0}, tp_hi[3] = {0, 0, 0};
     int64_t tp_off[3] = {0, 0, 0};
-    bool tp_valid = false;
+    bool tp_valid = false;    // FP32 Sigma of the current diagonal
+    bool tp64_valid = false;  // FP64 Sigma of the current diagonal
 };
 
 #include <functional>  // host-side declarations below
@@ -216,7 +216,7 @@ int launch_surface_tension(evap_mesh* h, const double* nf, const double* kappa, 
 int launch_diagonal_into(evap_mesh* h, float* acc, double* out, cudaStream_t s);
 // tensor-product mass preconditioner of the momentum solves (precond.cu): setup after the Jacobi diagonal, apply
 // z = P (sc v) with scratch t (and w = Dirichlet ? z : 0 when w is given)
-int tensor_prec_setup(evap_mesh* h, cudaStream_t s);
+int tensor_prec_setup(evap_mesh* h, bool fp64, cudaStream_t s);
 template <typename T>
 int tensor_prec_apply(evap_mesh* h, const T* v, T sc, T* t, T* z, T* w, cudaStream_t s);
 int solve_gmres(evap_mesh* h, const double* f, double* x, int mixed, int restart, double rtol, int max_iter,

@@ -653,10 +653,7 @@ int solve_gmres(evap_mesh* h, const double* f, double* x, int mixed, int m, doub
         double* w = (double*)(base + dV);
         double* z = (double*)(base + dV + dN);
         int its = 0;
-        if (!h->tp_valid) {
-            if ((rc = tensor_prec_setup(h, s))) return rc;
-            h->tp_valid = true;
-        }
+        if ((rc = tensor_prec_setup(h, true, s))) return rc;
         c.tp = true;  // the same preconditioner as the mixed solve's inner iterations
         if ((rc = gmres<double>(c, m, f, x, x_zero, h->diag, V, w, z, rtol * fn, max_iter, &its, &res))) return rc;
         used = its;
@@ -669,10 +666,7 @@ int solve_gmres(evap_mesh* h, const double* f, double* x, int mixed, int m, doub
         double* r64 = (double*)(base + fV + 4 * fN);
         double* Ax = (double*)(base + fV + 4 * fN + dN);
         const double inner_rtol = 1e-5;
-        if (!h->tp_valid) {
-            if ((rc = tensor_prec_setup(h, s))) return rc;
-            h->tp_valid = true;
-        }
+        if ((rc = tensor_prec_setup(h, false, s))) return rc;
         c.tp = true;  // the inner FP32 solve takes the tensor-product mass preconditioner
         while (true) {
             if (x_zero) {  // r = f
@@ -831,10 +825,7 @@ int solve_saddle(evap_mesh* h, const double* f, double* x, double* p, int m, dou
     const size_t fV = al256((size_t)(SADDLE_INNER_M + 1) * ldu * sizeof(float)), fN = al256((size_t)ldu * sizeof(float));
     Ctx inner;
     if ((rc = prepare(h, OP_MOMENTUM, SADDLE_INNER_M, Nu3, ldu, fV + 4 * fN, s, inner))) return rc;
-    if (!h->tp_valid) {
-        if ((rc = tensor_prec_setup(h, s))) return rc;
-        h->tp_valid = true;
-    }
+    if ((rc = tensor_prec_setup(h, false, s))) return rc;
     inner.tp = true;
     SaddleSpace sp;
     sp.sdiag = sdiag;

@@ -222,49 +222,53 @@ static void factor_band(const std::vector<double>& Mg, int M, int P, int lo, int
     }
 }
 
-// Factors of the three axes (FP64 and FP32 copies, then the 1D mass diagonal in FP64) and Sigma for the current
-// Jacobi diagonal (h->diag and h->diag32 valid) in both precisions.
-int tensor_prec_setup(evap_mesh* h, cudaStream_t s) {
+// Factors of the three axes (FP64 and FP32 copies, then the 1D mass diagonal in FP64): they depend on the mesh
+// and its Dirichlet faces only, so they are built and uploaded once per mesh (a synchronous copy).  Sigma follows
+// the Jacobi diagonal: the FP32 scale after every new diagonal, the FP64 one only when an FP64 solve asks for it;
+// both are enqueued on the stream without a host synchronization.
+int tensor_prec_setup(evap_mesh* h, bool fp64, cudaStream_t s) {
     const MeshArgs<double>& m = h->m;
     const int P = m.P, M = m.M;
     const int64_t N = 3 * m.Nu;
-    std::vector<double> Mg;
-    mass_1d(h->b, m.n, m.h, Mg);
-    std::vector<double> all;
-    for (int a = 0; a < 3; ++a) {
-        const int lo = (m.faces & (1u << (2 * a))) ? 1 : 0;
-        const int hi = (m.faces & (1u << (2 * a + 1))) ? M - 2 : M - 1;
-        h->tp_lo[a] = lo;
-        h->tp_hi[a] = hi;
-        h->tp_off[a] = (int64_t)all.size();
-        std::vector<double> f;
-        factor_band(Mg, M, P, lo, hi, f);
-        all.insert(all.end(), f.begin(), f.end());
+    if (!h->tp_fac) {
+        std::vector<double> Mg;
+        mass_1d(h->b, m.n, m.h, Mg);
+        std::vector<double> all;
+        for (int a = 0; a < 3; ++a) {
+            const int lo = (m.faces & (1u << (2 * a))) ? 1 : 0;
+            const int hi = (m.faces & (1u << (2 * a + 1))) ? M - 2 : M - 1;
+            h->tp_lo[a] = lo;
+            h->tp_hi[a] = hi;
+            h->tp_off[a] = (int64_t)all.size();
+            std::vector<double> f;
+            factor_band(Mg, M, P, lo, hi, f);
+            all.insert(all.end(), f.begin(), f.end());
+        }
+        const size_t nf = all.size();
+        for (int i = 0; i < M; ++i) all.push_back(Mg[(size_t)i * M + i]);
+        // device layout (bytes): factors FP64 [nf], mass diagonal FP64 [M], factors FP32 [nf]
+        const size_t bytes = (nf + M) * sizeof(double) + nf * sizeof(float);
+        EVAP_CUDA(cudaMalloc(&h->tp_fac, bytes));
+        std::vector<float> f32(all.begin(), all.begin() + nf);
+        double* fac64 = (double*)h->tp_fac;
+        EVAP_CUDA(cudaMemcpy(fac64, all.data(), all.size() * sizeof(double), cudaMemcpyHostToDevice));
+        EVAP_CUDA(cudaMemcpy(fac64 + nf + M, f32.data(), nf * sizeof(float), cudaMemcpyHostToDevice));
+        h->tp_nf = (int64_t)nf;
     }
-    const size_t nf = all.size();
-    for (int i = 0; i < M; ++i) all.push_back(Mg[(size_t)i * M + i]);
-    // device layout (bytes): factors FP64 [nf], mass diagonal FP64 [M], factors FP32 [nf]
-    const size_t need = (nf + M) * sizeof(double) + nf * sizeof(float);
-    if (h->tp_fac_len < need) {
-        if (h->tp_fac) cudaFree(h->tp_fac);
-        h->tp_fac = nullptr;
-        h->tp_fac_len = 0;
-        EVAP_CUDA(cudaMalloc(&h->tp_fac, need));
-        h->tp_fac_len = need;
+    const double* md = (const double*)h->tp_fac + h->tp_nf;
+    if (!h->tp_valid) {
+        if (!h->tp_sigma) EVAP_CUDA(cudaMalloc(&h->tp_sigma, N * sizeof(float)));
+        k_tp_sigma<float><<<blocks_for(N, 256), 256, 0, s>>>(M, m.Nu, m.faces, md, h->diag32, h->tp_sigma);
+        EVAP_CHECK_LAUNCH("tp_sigma");
+        h->tp_valid = true;
+        h->tp64_valid = false;
     }
-    std::vector<float> f32(all.begin(), all.begin() + nf);
-    double* fac64 = (double*)h->tp_fac;
-    float* fac32 = (float*)(fac64 + nf + M);
-    h->tp_nf = (int64_t)nf;
-    EVAP_CUDA(cudaMemcpyAsync(fac64, all.data(), all.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-    EVAP_CUDA(cudaMemcpyAsync(fac32, f32.data(), nf * sizeof(float), cudaMemcpyHostToDevice, s));
-    if (!h->tp_sigma) EVAP_CUDA(cudaMalloc(&h->tp_sigma, N * sizeof(float)));
-    if (!h->tp_sigma64) EVAP_CUDA(cudaMalloc(&h->tp_sigma64, N * sizeof(double)));
-    k_tp_sigma<float><<<blocks_for(N, 256), 256, 0, s>>>(M, m.Nu, m.faces, fac64 + nf, h->diag32, h->tp_sigma);
-    EVAP_CHECK_LAUNCH("tp_sigma");
-    k_tp_sigma<double><<<blocks_for(N, 256), 256, 0, s>>>(M, m.Nu, m.faces, fac64 + nf, h->diag, h->tp_sigma64);
-    EVAP_CHECK_LAUNCH("tp_sigma");
-    EVAP_CUDA(cudaStreamSynchronize(s));  // the host staging vectors go out of scope
+    if (fp64 && !h->tp64_valid) {
+        if (!h->tp_sigma64) EVAP_CUDA(cudaMalloc(&h->tp_sigma64, N * sizeof(double)));
+        k_tp_sigma<double><<<blocks_for(N, 256), 256, 0, s>>>(M, m.Nu, m.faces, md, h->diag, h->tp_sigma64);
+        EVAP_CHECK_LAUNCH("tp_sigma");
+        h->tp64_valid = true;
+    }
     return EVAP_OK;
 }
 
