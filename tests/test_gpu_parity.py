@@ -250,9 +250,16 @@ def test_jacobi_diagonal():
     np.testing.assert_allclose(d, do, rtol=2e-5)
 
 
+SOLVE_CASES = [(6, 2, None), (4, 3, 0x2A), (5, 2, 0), (5, 2, 0x1F)]
+
+
+@pytest.mark.parametrize("n,p,faces", SOLVE_CASES, ids=["q2_box", "q3_mixed_faces", "q2_no_faces", "q2_open_top"])
 @pytest.mark.parametrize("mixed", [False, True])
-def test_solve_against_direct(mixed):
-    wl = workloads.make_workload("sphere8", n=6)
+def test_solve_against_direct(mixed, n, p, faces):
+    """Both solves (FP64 GMRES and the mixed one) with the tensor-product mass preconditioner, whose line solves
+    run over the free node range of each axis (set by the Dirichlet faces) and whose factors have bandwidth p."""
+    over = {} if faces is None else dict(dirichlet_faces=faces)
+    wl = workloads.make_workload("sphere8", n=n, p=p, **over)
     op = make_op(wl)
     rng = np.random.default_rng(3)
     f = rng.uniform(-1, 1, wl.x.shape)
