@@ -108,3 +108,27 @@ def test_picard_iterations_contract_the_nonlinear_residual():
     step.time_step(mesh, prm, phi, u, p, mdot, fp_iters=1, reinit_steps=0, picard_iters=5, picard_atol=res[1] * 1.01,
                    residuals=res2)
     assert len(res2) == 2
+
+
+def test_uniform_translation_is_preserved():
+    """No walls (every face open), two phases, no evaporation or force: a uniform velocity U is an exact solution of
+    the Picard step (no convection, stress or pressure), so a BDF1 step and a BDF2 step (u^(n-1) = U) both return
+    u = U and p = 0; an inertia load of the wrong size or BDF2 weights that do not sum to one move it.  The interface
+    is carried with the transport velocity U (variant 1 without evaporation) by about U_z dt."""
+    n = 4
+    z = workloads.node_coords(n, 1)[:, 2]
+    prm = workloads.default_params(n, 1.0, ratio=10.0, dirichlet_faces=0, dt=0.02, newton=0, variant=1)
+    prm["c_mass"] = 1.0 / prm["dt"]
+    prm["dtau"] = min(prm["eps"], prm["dt"])
+    phi = np.tanh((0.55 - z) / (2 * prm["eps"]))
+    mesh = fe.Mesh(n, 2, 1.0)
+    U = np.array([0.2, -0.1, 0.5])
+    u = np.repeat(U[:, None], mesh.n_u, axis=1).ravel()
+    mdot = np.zeros(mesh.n_phi)
+    for u_prev in (None, u):
+        ph, u1, p1 = step.time_step(mesh, prm, phi, u, np.zeros(mesh.n_phi), mdot, fp_iters=1, reinit_steps=0,
+                                    u_prev=u_prev)
+        assert np.abs(u1 - u).max() < 1e-9 * np.abs(u).max()
+        # p = 0 up to the rounding of the direct solve, relative to the inertia pressure scale rho_l c_m |U| h
+        assert np.abs(p1).max() < 1e-11 * prm["rho_l"] * prm["c_mass"] * np.abs(U).max() * mesh.h
+    assert interface_height(ph, n) - interface_height(phi, n) == pytest.approx(U[2] * prm["dt"], rel=0.05)
