@@ -41,8 +41,8 @@ def rel(a, b):
 
 def slab(n, variant, mdot_val, z0=0.55, **over):
     z = workloads.node_coords(n, 1)[:, 2]
-    prm = workloads.default_params(n, 1.0, ratio=10.0, dirichlet_faces=0x1F, dt=0.02, newton=0, variant=variant,
-                                   **over)
+    over = dict(dict(dirichlet_faces=0x1F), **over)
+    prm = workloads.default_params(n, 1.0, ratio=10.0, dt=0.02, newton=0, variant=variant, **over)
     prm["c_mass"] = 1.0 / prm["dt"]
     prm["dtau"] = min(prm["eps"], prm["dt"])
     phi = np.tanh((z0 - z) / (2 * prm["eps"]))
@@ -191,3 +191,20 @@ def test_static_drop_laplace_pressure_jump():
     outside = p[(r > R + band + 0.02) & (q1[:, 2] < 0.85)].mean()
     assert inside - outside == pytest.approx(2 * alpha / R, rel=0.10)
     assert float(gu.abs().max()) < 1e-2 * alpha / prm["mu_l"]
+
+
+def test_time_step_preserves_a_uniform_translation():
+    """Every face open, no evaporation or force: u = U is an exact solution of the BDF1 and BDF2 steps (the
+    oracle's Galilean pin), to the velocity-pressure solve tolerance."""
+    n = 6
+    prm, phi, _ = slab(n, 1, 0.0, dirichlet_faces=0)
+    mesh = fe.Mesh(n, 2, 1.0)
+    op = make_op(n, prm)
+    U = np.array([0.2, -0.1, 0.5])
+    u = cuda(np.repeat(U[:, None], mesh.n_u, axis=1).ravel())
+    zero = cuda(np.zeros(mesh.n_phi))
+    for u_prev in (None, u):
+        _, gu, gp, info = op.time_step(cuda(phi), u, zero, zero, fp_iters=1, reinit_steps=0, ns_rtol=1e-12,
+                                       u_prev=u_prev)
+        assert float((gu - u).abs().max()) < 1e-8 * float(np.abs(U).max())
+        assert float(gp.abs().max()) < 1e-9 * prm["rho_l"] * prm["c_mass"] * float(np.abs(U).max()) * mesh.h
