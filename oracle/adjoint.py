@@ -48,7 +48,8 @@ def param_gradients(pb: momentum.Problem, x, w, w_p=None):
     cm = prm["c_mass"]
     newton = float(int(prm.get("newton", 1)))
     eps = prm["eps"]
-    k_rho = 1.0 / prm["rho_l"] - 1.0 / prm["rho_g"]
+    k_rho = 1.0 / prm["rho_l"] - 1.0 / prm["rho_g"]                 # d(1/rho)/dH, Eq. (rhoEff)
+    k_dil = physics.dilation_coefficient(prm["rho_l"], prm["rho_g"])  # v = mdot k_dil delta, Eq. (evaporDil)
     cells = mesh.cells()
     for sl in momentum._chunks(len(cells)):
         q = momentum.qp_fields(pb, cells[sl])
@@ -93,10 +94,10 @@ def param_gradients(pb: momentum.Problem, x, w, w_p=None):
             wp_q = w_p[d1] @ b1.N
             dL_dv = -Wq * wp_q
             delta = np.where(zone, dH * dd * gnorm, 0.0)
-            dL_dm = dL_dv * k_rho * delta
+            dL_dm = dL_dv * k_dil * delta
             mq = q["mdot"]
-            dL_dphi = dL_dphi + dL_dv * mq * k_rho * (d2H * dd * dd + dH * d2d) * gnorm
-            dL_dg = dL_dg + (dL_dv * mq * k_rho * dH * dd)[..., None] * n
+            dL_dphi = dL_dphi + dL_dv * mq * k_dil * (d2H * dd * dd + dH * d2d) * gnorm
+            dL_dg = dL_dg + (dL_dv * mq * k_dil * dH * dd)[..., None] * n
         gp = np.einsum("jq,nq->nj", b1.N, dL_dphi) + np.einsum("bjq,nqb->nj", b1.G, dL_dg)
         np.add.at(g_phi, d1.ravel(), gp.ravel())
         np.add.at(g_mdot, d1.ravel(), np.einsum("jq,nq->nj", b1.N, dL_dm).ravel())

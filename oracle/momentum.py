@@ -166,8 +166,9 @@ def constrain(A: sp.csr_matrix, mask: np.ndarray) -> sp.csr_matrix:
     return (keep @ A @ keep + sp.diags(mask.astype(float))).tocsr()
 
 
-def divergence(pb: Problem) -> tuple[sp.csr_matrix, np.ndarray]:
-    """B[N_phi, 3 N_u] (constrained velocity columns removed) and source g[N_phi] of the divergence row."""
+def divergence(pb: Problem, remove_constrained: bool = True) -> tuple[sp.csr_matrix, np.ndarray]:
+    """B[N_phi, 3 N_u] (constrained velocity columns removed unless remove_constrained is False) and source g[N_phi]
+    of the divergence row."""
     mesh = pb.mesh
     cells = mesh.cells()
     Nu = mesh.n_u
@@ -186,6 +187,8 @@ def divergence(pb: Problem) -> tuple[sp.csr_matrix, np.ndarray]:
         np.add.at(g, d1.ravel(), np.einsum("q,jq,nq->nj", W, b1.N, q["vdil"]).ravel())
     B = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
                       shape=(mesh.n_phi, 3 * Nu)).tocsr()
+    if not remove_constrained:
+        return B, g
     keep = sp.diags((~pb.constrained()).astype(float))
     return (B @ keep).tocsr(), g
 

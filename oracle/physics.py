@@ -7,7 +7,7 @@ Every function evaluates the paper's formula literally, on arrays of level-set v
   density    1/rho = H/rho_l + (1 - H)/rho_g  (reciprocal)                             Eq. (rhoEff)
   viscosity  mu = H mu_l + (1 - H) mu_g                                                Eq. (muEff)
   normal     n = grad phi / |grad phi|                                                 Eq. (normal_vector)
-  dilation   v = mdot (1/rho_l - 1/rho_g) delta                                        Eq. (evaporDil)
+  dilation   v = mdot (1/rho_g - 1/rho_l) delta          Eq. (evaporDil), sign of App. A (see dilation_rate)
 
 Reading of the branch boundaries (the paper's cases are in d; d(phi) is increasing): the interface zone
 0 < H < 1 is |phi| < tanh(3/2), i.e. -3 eps < d < 3 eps.  Outside it H is 0 or 1, its derivatives vanish and the
@@ -114,9 +114,20 @@ def delta(phi, grad_phi, eps):
     return out
 
 
+def dilation_coefficient(rho_l, rho_g):
+    """c_1 = 1/rho_g - 1/rho_l, the factor of mdot delta in div u.
+
+    Reading of the sign: Eq. (evaporDil) prints mdot (1/rho_l - 1/rho_g) delta, but the paper's own 1D solution
+    (App. A, Eq. stefan_diffuse_velocity: u = u_bar + mdot (1 - H)(1/rho_g - 1/rho_l) with the liquid where H = 1)
+    has div u = mdot (1/rho_g - 1/rho_l) delta, the derivation of variant 1 (Sec. 2.3.2) names c_1 = 1/rho_g -
+    1/rho_l with c_1 mdot delta = div u, and evaporation (mdot > 0, liquid turning into the lighter gas) expands the
+    volume.  The printed bracket is taken as reversed: v > 0 for mdot > 0 and rho_g < rho_l."""
+    return 1.0 / rho_g - 1.0 / rho_l
+
+
 def dilation_rate(mdot, phi, grad_phi, eps, rho_l, rho_g):
-    """Regularized evaporative dilation rate, Eq. (evaporDil)."""
-    return np.asarray(mdot, dtype=float) * (1.0 / rho_l - 1.0 / rho_g) * delta(phi, grad_phi, eps)
+    """Regularized evaporative dilation rate, Eq. (evaporDil) with the sign of App. A: mdot c_1 delta."""
+    return np.asarray(mdot, dtype=float) * dilation_coefficient(rho_l, rho_g) * delta(phi, grad_phi, eps)
 
 
 def corrected_strain(eps_tensor, n, active=True):

@@ -12,6 +12,11 @@ Faces whose bit is not set in `dirichlet_faces` are open: the natural condition 
 holds there, which also fixes the pressure level.  With every face Dirichlet the pressure is determined only up to a
 constant and K is singular; the solves here require an open face.
 
+Dirichlet data.  The solves take the entries of f on the constrained DoFs as the prescribed velocity there (walls at
+rest: 0; an inflow: its value) and lift them: they solve the system K_D [x; p] = [f; g] of `lifted_matrix`, whose
+constrained rows are identity rows and whose free rows keep the constrained columns of the unconstrained A and B,
+so x_c = f_c and the free rows see A_fc f_c and B_c f_c.  For f_c = 0 (homogeneous data) this is the system K.
+
 Also the consistent load of a body force, f_(i,c) = sum_q W N_i rho(phi) g_c (the rho g term of Eq. momentum_balance),
 and the outflow sum_(top face) of x . n, evaluated by face quadrature of the Q_p field (independently of B).
 """
@@ -32,6 +37,19 @@ def saddle_matrix(pb: momentum.Problem):
     return K, g
 
 
+def lifted_matrix(pb: momentum.Problem):
+    """K_D = [A_D, -B^T; B_full, 0] and g: A_D is the unconstrained velocity block with its constrained rows replaced
+    by identity rows (constrained columns kept), B_full the divergence matrix with every velocity column, and B
+    (constrained columns removed) in the pressure term, which therefore vanishes on the constrained rows."""
+    mask = pb.constrained()
+    A = momentum.assemble(pb, apply_dirichlet=False)
+    free = sp.diags((~mask).astype(float))
+    A_D = (free @ A + sp.diags(mask.astype(float))).tocsr()
+    B, g = momentum.divergence(pb)
+    B_full, _ = momentum.divergence(pb, remove_constrained=False)
+    return sp.bmat([[A_D, -B.T], [B_full, None]]).tocsr(), g
+
+
 def apply(pb: momentum.Problem, x: np.ndarray, p: np.ndarray):
     """(A x - B^T p, B x)."""
     A = momentum.assemble(pb)
@@ -44,10 +62,11 @@ def continuity_rhs(pb: momentum.Problem) -> np.ndarray:
 
 
 def solve(pb: momentum.Problem, f: np.ndarray):
-    """Direct solve of K [x; p] = [f; g]; returns (x, p).  Needs an open face (else K is singular)."""
+    """Direct solve of K_D [x; p] = [f; g] (`lifted_matrix`: x = f on the constrained DoFs, lifted into the free
+    rows); returns (x, p).  Needs an open face (else K is singular)."""
     if int(pb.params.get("dirichlet_faces", 0x3F)) & 0x3F == 0x3F:
         raise ValueError("the saddle-point system needs at least one open face")
-    K, g = saddle_matrix(pb)
+    K, g = lifted_matrix(pb)
     nu3 = 3 * pb.mesh.n_u
     sol = spla.spsolve(K.tocsc(), np.concatenate([f, g]))
     return sol[:nu3], sol[nu3:]

@@ -11,7 +11,9 @@ takes them in the order velocity first, then level set, each once:
      momentum operator of oracle.momentum for u0 = u^(k), newton = 0 and that c_m (A u = rho c_m u + rho (u^(k) .
      grad) u + viscous(u)),
         [A, -B^T; B, 0] [u^(n+1); p^(n+1)] = [f; g],   f_(i,c) = sum_q W N_i rho (c_m u*_c + g_c),
-     g the continuity right-hand side (oracle.saddle), Dirichlet rows of f zero (walls at rest).  With a surface
+     g the continuity right-hand side (oracle.saddle), Dirichlet rows of f equal to those of u^n: the velocity on
+     the Dirichlet faces keeps its value (walls at rest where u^n is 0 there, an inflow where it is not; the data
+     are lifted into the free rows, oracle.saddle.lifted_matrix).  With a surface
      tension coefficient alpha != 0, f also carries the surface-tension force of Eq. (surfaceTension)
      (oracle.surface) with the projected normal and the regularized curvature of phi^n (Algorithm 2 step 3 of the
      previous step).
@@ -59,11 +61,13 @@ def time_step(mesh_u: fe.Mesh, params: dict, phi: np.ndarray, u: np.ndarray, p: 
         kappa = geometry.curvature(mesh1, n0, prm.get("eta_kappa", 2.0))
         f = f + surface.surface_tension_rhs(pb, n0, kappa, alpha)
         f[pb.constrained()] = 0.0
+    mask = pb.constrained()
+    f[mask] = np.asarray(u, dtype=float)[mask]  # Dirichlet data: the boundary values of u^n
     u1, p1 = np.array(u, dtype=float), np.array(p, dtype=float)
     for it in range(picard_iters):
         pb.u0 = u1
         if it > 0:
-            K, g = saddle.saddle_matrix(pb)
+            K, g = saddle.lifted_matrix(pb)
             res = float(np.linalg.norm(np.concatenate([f, g]) - K @ np.concatenate([u1, p1])))
             if residuals is not None:
                 residuals.append(res)

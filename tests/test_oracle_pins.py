@@ -244,14 +244,15 @@ def test_convection_and_newton_terms():
 
 def test_divergence_row():
     """First line of Eq. (weakNavierStokes): (q, div x) = (q, v_dil).  For x = X, sum_j y_p[j] = 3 - int v_dil;
-    without evaporation exactly 3; on a flat interface int v_dil -> mdot (1/rho_l - 1/rho_g) since int delta dz = 1."""
+    without evaporation exactly 3; on a flat interface int v_dil -> mdot (1/rho_g - 1/rho_l) since int delta dz = 1
+    (the sign of App. A: div u = mdot (1/rho_g - 1/rho_l) delta, evaporation expands the volume)."""
     n = 4
     X = workloads.node_coords(n, 2)
     x = X.T.ravel().copy()
     pb = make_problem(n, phi=slab_phi(n, 0.1), mdot=np.zeros((n + 1) ** 3), dirichlet_faces=0, eps=0.1)
     B, g = momentum.divergence(pb)
     np.testing.assert_allclose((B @ x - g).sum(), 3.0, rtol=1e-13)
-    kr = 1.0 / 1000.0 - 1.0
+    kr = 1.0 / 1.0 - 1.0 / 1000.0
     errs = []
     for n in (8, 16):
         X = workloads.node_coords(n, 2)
@@ -354,7 +355,7 @@ def _naive_apply(wl_n, p, prm, phi, u0, mdot, x, w_p=None):
                             for i in range(len(loc)):
                                 for c in range(3):
                                     y[c * Nu + gidx[i]] += W * (Nv[i] * F[c] + Ng[i] @ T[c])
-                            vdil = md * (1 / prm["rho_l"] - 1 / prm["rho_g"]) * delta
+                            vdil = md * (1 / prm["rho_g"] - 1 / prm["rho_l"]) * delta  # App. A sign of Eq. (evaporDil)
                             for j in range(8):
                                 yp[gidx1[j]] += W * M1[j] * (np.trace(GX) - vdil)
     return y, yp

@@ -36,8 +36,8 @@ def test_evaporating_slab_recedes_at_mdot_over_rho_l():
     recedes into the liquid at mdot / rho_l (the sharp solution of the 1D phase-change problem with no inflow,
     App. evapor_stefan).  Over three steps the displacement matches to 3 %; a dropped or sign-flipped evaporation
     term gives 0 or -100 %."""
-    n = 6
-    mesh, prm, phi, mdot = slab_case(n, 50.0)
+    n = 8  # eps = h: the interface zone |d| < 3 eps stays one cell away from the bottom wall and the top face
+    mesh, prm, phi, mdot = slab_case(n, 50.0, z0=0.5)
     u = np.zeros(3 * mesh.n_u)
     p = np.zeros(mesh.n_phi)
     z0 = interface_height(phi, n)
@@ -61,8 +61,8 @@ def test_rest_state_without_evaporation_stays_at_rest():
 def test_bdf2_steps_recede_at_the_same_rate():
     """One BDF1 step, then BDF2 steps with u^(n-1): the recession rate stays mdot / rho_l (3 %), and the BDF2 load
     (4 u^n - u^(n-1)) / 3 reduces to u^n for a steady velocity, so the rest state stays exactly at rest."""
-    n = 6
-    mesh, prm, phi, mdot = slab_case(n, 50.0)
+    n = 8
+    mesh, prm, phi, mdot = slab_case(n, 50.0, z0=0.5)
     u_prev = np.zeros(3 * mesh.n_u)
     u = np.zeros(3 * mesh.n_u)
     p = np.zeros(mesh.n_phi)
@@ -73,7 +73,7 @@ def test_bdf2_steps_recede_at_the_same_rate():
         u, u1 = u1, u2
         moved = z0 - interface_height(phi, n)
         assert moved == pytest.approx((k + 2) * prm["dt"] * 50.0 / prm["rho_l"], rel=0.03)
-    _, ur, pr = step.time_step(mesh, prm, np.tanh((0.55 - workloads.node_coords(n, 1)[:, 2]) / (2 * prm["eps"])),
+    _, ur, pr = step.time_step(mesh, prm, np.tanh((0.5 - workloads.node_coords(n, 1)[:, 2]) / (2 * prm["eps"])),
                                np.zeros(3 * mesh.n_u), np.zeros(mesh.n_phi), np.zeros(mesh.n_phi),
                                u_prev=np.zeros(3 * mesh.n_u))
     assert np.abs(ur).max() == 0.0 and np.abs(pr).max() == 0.0
@@ -132,3 +132,18 @@ def test_uniform_translation_is_preserved():
         # p = 0 up to the rounding of the direct solve, relative to the inertia pressure scale rho_l c_m |U| h
         assert np.abs(p1).max() < 1e-11 * prm["rho_l"] * prm["c_mass"] * np.abs(U).max() * mesh.h
     assert interface_height(ph, n) - interface_height(phi, n) == pytest.approx(U[2] * prm["dt"], rel=0.05)
+
+
+def test_stationary_1d_phase_change_step():
+    """App. A through the whole step (Navier-Stokes step with two Picard iterations, then Algorithm 2): from the exact
+    diffuse state with the static inflow u_bar = mdot / rho_l, the step returns the closed-form velocity and pressure
+    (Eqs. stefan_diffuse_velocity, stefan_diffuse_pressure) within the discretization error of the 6^3 mesh, and the
+    interface does not move (variant 2: u(x_l) + mdot / rho_l n = u_bar - mdot / rho_l = 0)."""
+    from test_oracle_saddle import STEFAN, stefan_case
+    n = 6
+    mesh, prm, phi, u, md, pex, jump = stefan_case(n)
+    ph1, u1, p1 = step.time_step(mesh, prm, phi, u, np.zeros(mesh.n_phi), md, fp_iters=2, reinit_steps=2,
+                                 picard_iters=2)
+    assert np.abs(u1 - u).max() < 0.06 * jump
+    assert np.abs(p1 - pex).max() < 0.17 * STEFAN["mdot"] * jump
+    assert abs(interface_height(ph1, n) - interface_height(phi, n)) < 0.01 * mesh.h
