@@ -74,7 +74,8 @@ typedef struct {
     int stress;            /* 0 standard Stokes (Eq. stokesLaw), 1 corrected (Eq. modified_viscous_stress) */
     int corr_zone;         /* 0: correction only in the interface zone 0 < H < 1 (Sec. 2.4.2); 1: everywhere */
     int newton;            /* 1: Newton linearization (x . grad) u0 included (App. D); 0: Picard */
-    unsigned dirichlet_faces; /* homogeneous velocity Dirichlet faces, bit 2a: x_a = 0, bit 2a+1: x_a = L */
+    unsigned dirichlet_faces; /* velocity Dirichlet faces, bit 2a: x_a = 0, bit 2a+1: x_a = L (applies: homogeneous;
+                                 data in evap_solve_saddle, evap_time_step) */
     double cpp_tol;        /* closest-point tolerance in cell units (App. C) */
     int cpp_kmax;          /* closest-point outer iteration cap (App. C) */
     double eta_n;          /* normal filter constant, Eq. (normal_vector_regularized): radius eta_n h^2 (default 2) */
@@ -114,6 +115,13 @@ int evap_set_transport_velocity(evap_handle h, const double* u_gamma, void* stre
  * the number of flagged nodes is written to it (host pointer; this synchronizes the stream). */
 int evap_get_transport_velocity(evap_handle h, double* u_gamma, int32_t* flags, int64_t* n_flagged, void* stream);
 
+/* Points whose fluid velocity the last transport-velocity pass took (evap_set_fields, evap_update_transport_velocity,
+ * or the last fixed-point pass of evap_advect_levelset), y [3 N_phi] in physical coordinates, component-major: the
+ * closest point on the isocontour d = 3 eps (variant 2) or d = -3 eps (variant 3) of every node of the projection
+ * band (App. C; for a flagged node the last iterate), the node itself elsewhere and for variant 1.  Lets a caller
+ * check each projection on its own terms.  Not meaningful after evap_set_transport_velocity. */
+int evap_get_closest_points(evap_handle h, double* y, void* stream);
+
 /* Recompute the transport velocity (variant of the parameters; App. C closest-point projection for variants 2/3)
  * from the fields of the last evap_set_fields, replacing any u_Gamma given by evap_set_transport_velocity.  The
  * same pass evap_set_fields runs; separate so that it can be rerun or timed alone.  Synchronizes the stream once. */
@@ -127,7 +135,10 @@ int evap_transport_stats(evap_handle h, int64_t* band_nodes, int64_t* evaluation
 /* Momentum apply y = A x (velocity block of Eq. weakNavierStokes linearized about u, App. D):
  *   y_(i,c) = sum_q W_q [ N_i rho (c_mass x_c + (u . grad) x_c + newton (x . grad) u_c) + grad N_i . 2 mu eps_mod(x)_c ]
  * on unconstrained DoFs; on Dirichlet DoFs y = x and x does not enter other rows.  If y_p is not NULL the
- * divergence row y_p [N_phi] = sum_q W_q N^1_j (div x - v_dil) is written too (same precision).
+ * divergence row y_p [N_phi] = sum_q W_q N^1_j (div x - v_dil) is written too (same precision), with the dilation rate
+ * v_dil = mdot (1/rho_g - 1/rho_l) delta (Eq. evaporDil with the sign of the paper's 1D solution, App. A
+ * Eq. stefan_diffuse_velocity: evaporation, mdot > 0, expands the volume; the printed Eq. evaporDil has the bracket
+ * reversed).
  * prec 64: x, y, y_p double*;  prec 32: float*.  x [3 N_u], y [3 N_u]. */
 int evap_apply_momentum(evap_handle h, int prec, const void* x, void* y, void* y_p, void* stream);
 
@@ -218,9 +229,14 @@ int evap_apply_saddle(evap_handle h, const double* x, const double* p, double* y
  * complement B A^(-1) B^T that keeps the discrete B and so the pressure nodes of open faces) solved by 24 CG
  * iterations with its operator applied in FP32: the block-triangular preconditioner of Sec. 2.5 with its ILU velocity
  * block and its Cahouet-Chabard Schur approximation replaced.
- * x, p hold the initial guess on entry and the solution on exit.  Stops when ||[f; g] - K [x; p]|| <= rtol ||[f; g]||
- * or after max_iter operator applications; iters (host, may be NULL): operator applications; relres (host, may be
- * NULL): the final relative residual.  Synchronizes the stream.  EVAP_EINVAL if every face is Dirichlet (the pressure
+ * Dirichlet data: the entries of f on the Dirichlet DoFs are the prescribed velocity there (0 for walls at rest, an
+ * inflow otherwise); they are lifted, i.e. the system solved is K_D [x; p] = [f; g], whose constrained rows are x = f
+ * and whose free rows keep the columns of the Dirichlet DoFs (A_ff x_f + A_fc f_c - B^T p = f_f, B_f x_f + B_c f_c = g);
+ * with f = 0 there (homogeneous data) K_D is K.  The lifting costs one more velocity-pressure application and is
+ * skipped when f vanishes on the Dirichlet DoFs.
+ * x, p hold the initial guess on entry and the solution on exit.  Stops when ||b - K [x; p]|| <= rtol ||b|| (b the
+ * lifted right-hand side, [f; g] for homogeneous data) or after max_iter operator applications; iters (host, may be
+ * NULL): operator applications; relres (host, may be NULL): the final relative residual.  Synchronizes the stream.  EVAP_EINVAL if every face is Dirichlet (the pressure
  * level is then undetermined), restart outside [1, 255], rtol <= 0 or max_iter < 1; EVAP_ENOTCONV if the cap was
  * reached. */
 int evap_solve_saddle(evap_handle h, const double* f, double* x, double* p, int restart, double rtol, int max_iter,
@@ -228,7 +244,9 @@ int evap_solve_saddle(evap_handle h, const double* f, double* x, double* p, int 
 
 /* One time step of the coupled problem (the Navier-Stokes step, then Algorithm 2), for meshes created with
  * newton = 0 (one Picard linearization per step) and at least one open face:
- *   1. [A(u^n), -B^T; B, 0] [u^(n+1); p^(n+1)] = [f; g], f_(i,c) = sum_q W N_i rho (c_m u*_c + gravity_c): BDF1
+ *   1. [A(u^n), -B^T; B, 0] [u^(n+1); p^(n+1)] = [f; g], f_(i,c) = sum_q W N_i rho (c_m u*_c + gravity_c), with the
+ *      Dirichlet data of u^n (the velocity on the Dirichlet faces keeps its value of u^n: walls at rest where it is 0,
+ *      an inflow where it is not; lifted as in evap_solve_saddle, also in the nonlinear residual): BDF1
  *      (u_prev NULL: c_m = 1/dt, u* = u^n) or BDF2 (u_prev = u^(n-1): c_m = 3/(2 dt), u* = (4 u^n - u^(n-1)) / 3);
  *      the mesh's c_mass is replaced by the scheme's for the step.  Picard iterations: A is linearized about the
  *      latest iterate u^(k) (u^(0) = u^n), at most picard_iters solves by evap_solve_saddle (restart 30, ns_rtol, at

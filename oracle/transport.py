@@ -162,8 +162,10 @@ def closest_point(ev: PointEval, sx: np.ndarray, d_target: float, eps: float, to
 
 
 def transport_velocity(mesh: fe.Mesh, phi: np.ndarray, u0: np.ndarray, mdot: np.ndarray, prm: dict,
-                       nodes: np.ndarray | None = None):
-    """u_Gamma[3, len(nodes)] and the non-converged flag per node (all Q1 nodes if ``nodes`` is None)."""
+                       nodes: np.ndarray | None = None, return_points: bool = False):
+    """u_Gamma[3, len(nodes)] and the non-converged flag per node (all Q1 nodes if ``nodes`` is None); with
+    return_points also the point y[3, len(nodes)] (cell units) whose velocity was taken (the closest point for the
+    band nodes of variants 2/3, else the node)."""
     ev = PointEval(mesh, phi, u0)
     m1 = mesh.n + 1
     nodes = np.arange(mesh.n_phi) if nodes is None else np.asarray(nodes)
@@ -172,6 +174,7 @@ def transport_velocity(mesh: fe.Mesh, phi: np.ndarray, u0: np.ndarray, mdot: np.
     tol, kmax = prm.get("cpp_tol", 1e-10), int(prm.get("cpp_kmax", 50))
     ug = np.zeros((3, len(nodes)))
     flags = np.zeros(len(nodes), dtype=np.int32)
+    pts = np.zeros((3, len(nodes)))
     u0v = u0.reshape(3, -1)
     for t, node in enumerate(nodes):
         i, j, k = node % m1, (node // m1) % m1, node // (m1 * m1)
@@ -185,6 +188,7 @@ def transport_velocity(mesh: fe.Mesh, phi: np.ndarray, u0: np.ndarray, mdot: np.
             rho = physics.density(H, prm["rho_l"], prm["rho_g"])
             vnode = (mesh.p * i) + mesh.m * ((mesh.p * j) + mesh.m * (mesh.p * k))
             ug[:, t] = u0v[:, vnode] + mx / rho * nx
+            pts[:, t] = sx
             continue
         if variant == 2:
             band = (-physics.PHI_GAS_BAND < phx) and (phx < physics.PHI_BAND)
@@ -197,4 +201,7 @@ def transport_velocity(mesh: fe.Mesh, phi: np.ndarray, u0: np.ndarray, mdot: np.
             y, ok = closest_point(ev, sx, d_t, eps, tol, kmax)
             flags[t] = 0 if ok else 1
         ug[:, t] = ev.velocity(y) + mx / rho_t * nx
+        pts[:, t] = y
+    if return_points:
+        return ug, flags, pts
     return ug, flags

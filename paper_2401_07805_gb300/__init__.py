@@ -49,6 +49,7 @@ SIGNATURES = {
     "evap_set_fields": (_c_int, [_vp, _vp, _vp, _vp, _vp]),
     "evap_set_transport_velocity": (_c_int, [_vp, _vp, _vp]),
     "evap_get_transport_velocity": (_c_int, [_vp, _vp, _vp, ctypes.POINTER(ctypes.c_int64), _vp]),
+    "evap_get_closest_points": (_c_int, [_vp, _vp, _vp]),
     "evap_update_transport_velocity": (_c_int, [_vp, _vp]),
     "evap_transport_stats": (_c_int, [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                       ctypes.POINTER(ctypes.c_int64), _vp]),
@@ -159,6 +160,7 @@ class Operator:
         nu, nphi = ctypes.c_int64(), ctypes.c_int64()
         _check(lib().evap_sizes(self._h, ctypes.byref(nu), ctypes.byref(nphi)), "evap_sizes")
         self.n_u, self.n_phi = nu.value, nphi.value
+        self.fields_version = 0  # bumped by every call that replaces (or drops) the mesh's fields
 
     # ------------------------------------------------------------------------------------------------- helpers
     def close(self):
@@ -195,6 +197,7 @@ class Operator:
         phi = self._dev(phi, self.n_phi, torch.float64, "phi")
         u = self._dev(u, 3 * self.n_u, torch.float64, "u")
         mdot = self._dev(mdot, self.n_phi, torch.float64, "mdot")
+        self.fields_version += 1
         _check(lib().evap_set_fields(self._h, _ptr(phi), _ptr(u), _ptr(mdot), _stream()), "evap_set_fields")
 
     def set_transport_velocity(self, u_gamma: torch.Tensor):
@@ -208,6 +211,13 @@ class Operator:
         _check(lib().evap_get_transport_velocity(self._h, _ptr(ug), _ptr(flags), ctypes.byref(nf), _stream()),
                "evap_get_transport_velocity")
         return ug, flags, nf.value
+
+    def closest_points(self):
+        """Points y [3, N_phi] (physical coordinates) whose velocity the last transport-velocity pass took: the
+        closest point of each projection-band node (App. C), the node itself elsewhere."""
+        y = torch.empty(3 * self.n_phi, dtype=torch.float64, device=self.device)
+        _check(lib().evap_get_closest_points(self._h, _ptr(y), _stream()), "evap_get_closest_points")
+        return y.view(3, self.n_phi)
 
     def update_transport_velocity(self):
         """Recompute u_Gamma from the current fields (the pass set_fields runs)."""
@@ -274,6 +284,7 @@ class Operator:
         up = None if u_prev is None else self._dev(u_prev, 3 * self.n_u, torch.float64, "u_prev")
         g = None if gravity is None else (ctypes.c_double * 3)(*[float(v) for v in gravity])
         its, rel, nl = ctypes.c_int(), ctypes.c_double(), ctypes.c_double()
+        self.fields_version += 1  # the step leaves the mesh without fields
         rc = lib().evap_time_step(self._h, _ptr(phi), _ptr(u), _ptr(p), _ptr(mdot), _ptr(up), g, float(alpha),
                                   int(picard_iters), float(picard_atol), int(fp_iters), int(reinit_steps),
                                   float(ns_rtol),
@@ -372,20 +383,26 @@ class MomentumFunction(torch.autograd.Function):
     """(y, y_p) = (A(phi, u0) x, B x - g(phi, mdot)) with gradients from the adjoint kernel.
 
     forward(op, x, phi, u0, mdot) sets the operator's fields, applies the FP64 momentum operator with the
-    divergence row; backward calls evap_apply_adjoint with (w, w_p) = (grad_y, grad_y_p)."""
+    divergence row; backward calls evap_apply_adjoint with (w, w_p) = (grad_y, grad_y_p) at the fields of its own
+    forward: if the operator's fields were replaced since (another forward or set_fields), backward sets the saved
+    ones again first."""
 
     @staticmethod
     def forward(ctx, op: Operator, x, phi, u0, mdot):
         op.set_fields(phi.detach(), u0.detach(), mdot.detach())
         y, yp = op.apply_momentum(x.detach(), prec=64, with_divergence=True)
         ctx.op = op
-        ctx.save_for_backward(x)
+        ctx.version = op.fields_version
+        ctx.save_for_backward(x, phi, u0, mdot)
         return y, yp
 
     @staticmethod
     def backward(ctx, gy, gyp):
-        (x,) = ctx.saved_tensors
+        x, phi, u0, mdot = ctx.saved_tensors
         op = ctx.op
+        if op.fields_version != ctx.version:  # linearize about this forward's fields, not the latest ones
+            op.set_fields(phi.detach(), u0.detach(), mdot.detach())
+            ctx.version = op.fields_version
         gy = torch.zeros(3 * op.n_u, dtype=torch.float64, device=op.device) if gy is None else gy.contiguous()
         gyp = None if gyp is None else gyp.contiguous()
         g = op.apply_adjoint(gy, x.detach(), gyp)

@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1), 2)
                 for (int j = 0; j < 3; ++j) sacc += (OmG[i][j] + OmG[j][i]) * nv[j];
                 dL_dn[i] = -wm * zg * tr * sacc;
             }
-            const double krho = 1.0 / m.rho_l - 1.0 / m.rho_g;
+            const double krho = 1.0 / m.rho_l - 1.0 / m.rho_g;  // d(1/rho)/dH, Eq. (rhoEff)
             const double drho_dH = -rho * rho * krho;
             const double dmu_dH = m.mu_l - m.mu_g;
             dphi = (dL_drho * drho_dH + dL_dmu * dmu_dH) * dH * dd;
@@ -240,13 +240,14 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1), 2)
 #pragma unroll
                 for (int i = 0; i < 3; ++i) dg[i] = (dL_dn[i] - pn * nv[i]) / gn;
             }
-            if (wp) {
+            if (wp) {  // through v_dil = mdot c_1 delta (Eq. evaporDil)
+                const double kdil = dilation_coefficient(m);
                 const double dL_dv = -W * pi;
                 const double delta = mat.zone ? dH * dd * gn : 0.0;
-                dm = dL_dv * krho * delta;
-                dphi += dL_dv * md * krho * (d2H * dd * dd + dH * d2d) * gn;
+                dm = dL_dv * kdil * delta;
+                dphi += dL_dv * md * kdil * (d2H * dd * dd + dH * d2d) * gn;
 #pragma unroll
-                for (int i = 0; i < 3; ++i) dg[i] += dL_dv * md * krho * dH * dd * nv[i];
+                for (int i = 0; i < 3; ++i) dg[i] += dL_dv * md * kdil * dH * dd * nv[i];
             }
         }
     }

@@ -336,6 +336,12 @@ int evap_get_transport_velocity(evap_handle h, double* u_gamma, int32_t* flags, 
     return EVAP_OK;
 }
 
+int evap_get_closest_points(evap_handle h, double* y, void* stream) {
+    if (!h || !y) return fail(EVAP_EINVAL, "evap_get_closest_points: null argument");
+    if (!h->has_fields) return fail(EVAP_ENOFIELDS, "evap_get_closest_points: fields not set");
+    return launch_closest_points(h, y, (cudaStream_t)stream);
+}
+
 int evap_update_transport_velocity(evap_handle h, void* stream) {
     if (!h) return fail(EVAP_EINVAL, "evap_update_transport_velocity: null handle");
     if (!h->has_fields) return fail(EVAP_ENOFIELDS, "evap_update_transport_velocity: fields not set");

@@ -167,11 +167,20 @@ int launch_qp_coeffs(evap_mesh* h, cudaStream_t s);
 int launch_momentum32(evap_mesh* h, const float* x, float* y, float* yp, cudaStream_t s);
 // u_Gamma of the mesh's level set, or of `phi` (a clamped Q1 field) when given, into h->ugamma / h->ugamma32.
 int launch_transport_velocity(evap_mesh* h, cudaStream_t s, const double* phi = nullptr);
+// the points of the last transport-velocity pass, y [3 N_phi] physical coordinates (evap_get_closest_points)
+int launch_closest_points(evap_mesh* h, double* y, cudaStream_t s);
 // y = A x (+ divergence row into yp if not null).  init = false: y already holds x on the Dirichlet DoFs and 0
 // elsewhere (and yp is null), e.g. written by the solver's fused preconditioner kernel.
 template <typename T>
 // y = A x (+ the pressure term -B^T p when p is given, FP64 only), y_p = B x - g when yp is given.
-int launch_momentum(evap_mesh* h, const T* x, T* y, T* yp, cudaStream_t s, bool init = true, const T* p = nullptr);
+// all_columns (FP64 only, with init): the Dirichlet entries of x are read as they are, so the free rows are those of
+// the unconstrained operator (the lifting of Dirichlet data); the constrained rows are still y = x.
+int launch_momentum(evap_mesh* h, const T* x, T* y, T* yp, cudaStream_t s, bool init = true, const T* p = nullptr,
+                    bool all_columns = false);
+// dst = src on the Dirichlet DoFs of the mesh's faces (other entries untouched); [3 N_u] vectors
+int launch_constrained_copy(evap_mesh* h, const double* src, double* dst, cudaStream_t s);
+// *any (host) = whether src has a nonzero entry on a Dirichlet DoF (synchronizes the stream)
+int constrained_nonzero(evap_mesh* h, const double* src, bool* any, cudaStream_t s);
 template <typename T>
 int launch_levelset(evap_mesh* h, int mode, const T* x, T* y, cudaStream_t s);
 int launch_adjoint(evap_mesh* h, const double* w, const double* wp, const double* x, double* gx, double* gu,
@@ -194,7 +203,10 @@ int geo_cg(evap_mesh* h, const std::function<int(const double*, double*)>& apply
 template <typename T>
 int launch_pressure_gradient(evap_mesh* h, const T* p, T scale, T* y, cudaStream_t s);
 int continuity_rhs(evap_mesh* h, const double** g, cudaStream_t s);
-int launch_saddle_apply(evap_mesh* h, const double* x, const double* p, double* y, double* yp, cudaStream_t s);
+// [y; y_p] = K [x; p]; lifted: the system K_D of non-homogeneous Dirichlet data, whose free rows keep the columns of
+// the Dirichlet DoFs (y = A_full x - B^T p on free rows, x on constrained rows; y_p = B_full x)
+int launch_saddle_apply(evap_mesh* h, const double* x, const double* p, double* y, double* yp, cudaStream_t s,
+                        bool lifted = false);
 // f = sum_q W rho N_i (c_m u + g) (FP64; Dirichlet rows 0)
 int launch_mass_load(evap_mesh* h, const double* u, const double g[3], double* f, cudaStream_t s);
 // copy the fields and compute the flow operators' coefficients (evap_set_fields without the transport velocity)

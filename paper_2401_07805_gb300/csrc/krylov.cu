@@ -742,6 +742,13 @@ constexpr double SADDLE_INNER_TOL = 1e-2;
 constexpr int SADDLE_SCHUR_CG = 24;     // CG iterations per pressure Poisson solve
 
 // v = b - v
+// b += xd - kd: the lifting of Dirichlet data xd (K_D [xd] = kd) into the right-hand side.
+__global__ void k_lift_rhs(double* __restrict__ b, const double* __restrict__ xd, const double* __restrict__ kd,
+                           int64_t N) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] += xd[i] - kd[i];
+}
+
 __global__ void k_residual_inplace(const double* __restrict__ b, double* __restrict__ v, int64_t N) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x)
         v[k] = b[k] - v[k];
@@ -881,11 +888,25 @@ int solve_saddle(evap_mesh* h, const double* f, double* x, double* p, int m, dou
     // b = [f; g]
     EVAP_CUDA(cudaMemcpyAsync(sp.b, f, Nu3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
     EVAP_CUDA(cudaMemcpyAsync(sp.b + Nu3, g, Np * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    const int G = blocks_for(N, 256);
+    // Dirichlet data (f nonzero on a Dirichlet DoF): solve K_D [x; p] = [f; g], whose free rows keep the Dirichlet
+    // columns, as K [x; p] = b with b = [f; g] - K_D [f_D; 0] + [f_D; 0] (f_D: f on the Dirichlet DoFs, else 0); the
+    // first two basis vectors are scratch here
+    bool data = false;
+    if ((rc = constrained_nonzero(h, f, &data, s))) return rc;
+    if (data) {
+        double* xd = sp.V;
+        double* kd = sp.V + ld;
+        EVAP_CUDA(cudaMemsetAsync(xd, 0, N * sizeof(double), s));
+        if ((rc = launch_constrained_copy(h, f, xd, s))) return rc;
+        if ((rc = launch_saddle_apply(h, xd, xd + Nu3, kd, kd + Nu3, s, true))) return rc;
+        k_lift_rhs<<<G, 256, 0, s>>>(sp.b, xd, kd, N);
+        EVAP_CHECK_LAUNCH("saddle_lift");
+    }
     if ((rc = norm2_dev<double>(c, sp.b, c.dnorm))) return rc;
     if ((rc = fetch(c, c.dnorm, 1, c.hcol))) return rc;
     const double bn = std::sqrt(c.hcol[0]);
     const double target = rtol * bn;
-    const int G = blocks_for(N, 256);
     std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), yv(m);
     int used = 0;
     double beta = 0.0;

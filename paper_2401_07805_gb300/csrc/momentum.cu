@@ -395,9 +395,76 @@ int launch_qp_coeffs(evap_mesh* h, cudaStream_t s) {
     return EVAP_OK;
 }
 
+// dst = src on the DoFs of the Dirichlet faces, one warp per x-line as k_momentum_init.
+__global__ void __launch_bounds__(256) k_constrained_copy(int M, int64_t Nu, unsigned faces,
+                                                          const double* __restrict__ src, double* __restrict__ dst) {
+    const int lines = 3 * M * M;
+    const int wpb = blockDim.x / 32, warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    for (int line = blockIdx.x * wpb + warp; line < lines; line += gridDim.x * wpb) {
+        const int c = line / (M * M), rem = line - c * M * M, gz = rem / M, gy = rem - gz * M;
+        const bool cyz = ((faces & 4u) && gy == 0) || ((faces & 8u) && gy == M - 1) || ((faces & 16u) && gz == 0) ||
+                         ((faces & 32u) && gz == M - 1);
+        const int64_t off = c * Nu + (int64_t)M * (gy + (int64_t)M * gz);
+        for (int gx = lane; gx < M; gx += 32)
+            if (cyz || ((faces & 1u) && gx == 0) || ((faces & 2u) && gx == M - 1)) dst[off + gx] = src[off + gx];
+    }
+}
+
+// *flag = 1 if src is nonzero on a Dirichlet DoF.
+__global__ void __launch_bounds__(256) k_constrained_nonzero(int M, int64_t Nu, unsigned faces,
+                                                             const double* __restrict__ src, unsigned* flag) {
+    const int lines = 3 * M * M;
+    const int wpb = blockDim.x / 32, warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    bool any = false;
+    for (int line = blockIdx.x * wpb + warp; line < lines; line += gridDim.x * wpb) {
+        const int c = line / (M * M), rem = line - c * M * M, gz = rem / M, gy = rem - gz * M;
+        const bool cyz = ((faces & 4u) && gy == 0) || ((faces & 8u) && gy == M - 1) || ((faces & 16u) && gz == 0) ||
+                         ((faces & 32u) && gz == M - 1);
+        const int64_t off = c * Nu + (int64_t)M * (gy + (int64_t)M * gz);
+        for (int gx = lane; gx < M; gx += 32)
+            if ((cyz || ((faces & 1u) && gx == 0) || ((faces & 2u) && gx == M - 1)) && src[off + gx] != 0.0) any = true;
+    }
+    if (__any_sync(0xffffffffu, any) && lane == 0) atomicOr(flag, 1u);
+}
+
+static unsigned constrained_grid(const MeshArgs<double>& m) {
+    const int64_t lines = 3 * (int64_t)m.M * m.M;
+    return (unsigned)std::min<int64_t>((lines + 7) / 8, 152 * 16);
+}
+
+int launch_constrained_copy(evap_mesh* h, const double* src, double* dst, cudaStream_t s) {
+    const MeshArgs<double>& m = h->m;
+    if (!m.faces) return EVAP_OK;
+    k_constrained_copy<<<constrained_grid(m), 256, 0, s>>>(m.M, m.Nu, m.faces, src, dst);
+    EVAP_CHECK_LAUNCH("constrained_copy");
+    return EVAP_OK;
+}
+
+int constrained_nonzero(evap_mesh* h, const double* src, bool* any, cudaStream_t s) {
+    const MeshArgs<double>& m = h->m;
+    *any = false;
+    if (!m.faces) return EVAP_OK;
+    // the input-check counter doubles as the flag (it is only read right after its own reduction)
+    if (!h->nonfinite) EVAP_CUDA(cudaMalloc(&h->nonfinite, sizeof(unsigned long long)));
+    unsigned* flag = reinterpret_cast<unsigned*>(h->nonfinite);
+    EVAP_CUDA(cudaMemsetAsync(flag, 0, sizeof(unsigned), s));
+    k_constrained_nonzero<<<constrained_grid(m), 256, 0, s>>>(m.M, m.Nu, m.faces, src, flag);
+    EVAP_CHECK_LAUNCH("constrained_nonzero");
+    unsigned hv = 0;
+    EVAP_CUDA(cudaMemcpyAsync(&hv, flag, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    EVAP_CUDA(cudaStreamSynchronize(s));
+    *any = hv != 0;
+    return EVAP_OK;
+}
+
 template <typename T>
-int launch_momentum(evap_mesh* h, const T* x, T* y, T* yp, cudaStream_t s, bool init, const T* p) {
-    const MeshArgs<T> m = mesh_args<T>(h);
+int launch_momentum(evap_mesh* h, const T* x, T* y, T* yp, cudaStream_t s, bool init, const T* p, bool all_columns) {
+    MeshArgs<T> m = mesh_args<T>(h);
+    if (all_columns) {
+        // the unconstrained operator (no face read as 0), then the identity rows of the real faces
+        if (sizeof(T) != 8 || !init) return EVAP_EINVAL;
+        m.faces = 0u;
+    }
     const Basis<T> b = cast_basis<T>(h->b);
     const T* qc = (const T*)h->qc;  // FP64 only (the FP32 apply takes the line kernel)
     if (init) {
@@ -428,10 +495,12 @@ int launch_momentum(evap_mesh* h, const T* x, T* y, T* yp, cudaStream_t s, bool 
                 k_momentum<T, 3, CB, false><<<grid, CB * 64, 0, s>>>(m, b, qc, x, y, yp, nullptr);
         }
         EVAP_CHECK_LAUNCH("momentum");
+        if (all_columns) return launch_constrained_copy(h, (const double*)x, (double*)y, s);
         return EVAP_OK;
     }
 }
-template int launch_momentum<double>(evap_mesh*, const double*, double*, double*, cudaStream_t, bool, const double*);
-template int launch_momentum<float>(evap_mesh*, const float*, float*, float*, cudaStream_t, bool, const float*);
+template int launch_momentum<double>(evap_mesh*, const double*, double*, double*, cudaStream_t, bool, const double*,
+                                     bool);
+template int launch_momentum<float>(evap_mesh*, const float*, float*, float*, cudaStream_t, bool, const float*, bool);
 
 }  // namespace evap

@@ -90,6 +90,14 @@ __device__ __forceinline__ void ls_frozen_normal(const T (*nf)[8], const T pv[8]
     }
 }
 
+// c_1 = 1/rho_g - 1/rho_l, the factor of mdot delta in the dilation rate v = div u (Eq. evaporDil).  Sign: the
+// printed Eq. (evaporDil) has the bracket reversed with respect to the paper's 1D solution (App. A,
+// Eq. stefan_diffuse_velocity: div u = mdot (1/rho_g - 1/rho_l) delta) and to the c_1 of the variant-1 derivation;
+// the latter is taken, so evaporation (mdot > 0, rho_g < rho_l) expands the volume.
+__device__ __forceinline__ double dilation_coefficient(const MeshArgs<double>& m) {
+    return 1.0 / m.rho_g - 1.0 / m.rho_l;
+}
+
 // Whether the corrected-strain term is active at a point (Sec. 2.4.2; zone gate or everywhere).
 __device__ __forceinline__ bool correction_on(const MeshArgs<double>& m, bool zone) {
     return m.stress != 0 && (m.corr_zone != 0 || zone);

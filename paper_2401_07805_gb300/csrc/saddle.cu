@@ -400,11 +400,12 @@ int continuity_rhs(evap_mesh* h, const double** g, cudaStream_t st) {
 
 // [y; y_p] = [A x - B^T p; B x]: the momentum apply with the pressure term folded into its stress flux (whose
 // divergence row is B x - g), followed by + g.
-int launch_saddle_apply(evap_mesh* h, const double* x, const double* p, double* y, double* yp, cudaStream_t st) {
+int launch_saddle_apply(evap_mesh* h, const double* x, const double* p, double* y, double* yp, cudaStream_t st,
+                        bool lifted) {
     const double* g = nullptr;
     int rc = continuity_rhs(h, &g, st);
     if (rc) return rc;
-    if ((rc = launch_momentum<double>(h, x, y, yp, st, true, p))) return rc;
+    if ((rc = launch_momentum<double>(h, x, y, yp, st, true, p, lifted))) return rc;
     k_add_vec<<<blocks_for(h->m.Nphi, 256, 152 * 8), 256, 0, st>>>(yp, g, h->m.Nphi);
     EVAP_CHECK_LAUNCH("saddle_add_g");
     return EVAP_OK;

@@ -104,7 +104,8 @@ __global__ void k_classify(MeshArgs<double> m, Basis<double> b, const double* __
     tindex[cell] = c == CELL_TABLE ? atomicAdd(counter, 1) : -1;
 }
 
-// Table entries at one quadrature point of a table cell: rho, mu, z n (z = correction gate), v_dil (Eq. evaporDil).
+// Table entries at one quadrature point of a table cell: rho, mu, z n (z = correction gate), v_dil (Eq. evaporDil
+// with the sign of App. A, dilation_coefficient).
 __global__ void k_fill_table(MeshArgs<double> m, Basis<double> b, const double* __restrict__ phi,
                              const double* __restrict__ mdot, const int8_t* __restrict__ code,
                              const int32_t* __restrict__ tindex, double* table, float* table32) {
@@ -122,7 +123,7 @@ __global__ void k_fill_table(MeshArgs<double> m, Basis<double> b, const double* 
     const Material mat = material(ph, g[0], g[1], g[2], m);
     const double z = correction_on(m, mat.zone) ? 1.0 : 0.0;
     const double vals[TAB_K] = {mat.rho, mat.mu, z * mat.n[0], z * mat.n[1], z * mat.n[2],
-                                md * (1.0 / m.rho_l - 1.0 / m.rho_g) * mat.delta};
+                                md * dilation_coefficient(m) * mat.delta};
     const int64_t base = (int64_t)tindex[cell] * TAB_K * nq + q;
 #pragma unroll
     for (int k = 0; k < TAB_K; ++k) {
@@ -470,6 +471,39 @@ __global__ void k_transport_band_finish(PointEval e, const double* __restrict__ 
         const double y[3] = {band_y[3 * (int64_t)b], band_y[3 * (int64_t)b + 1], band_y[3 * (int64_t)b + 2]};
         transport_finish(e, mdot, band[b], y, rho_t, ug);
     }
+}
+
+// Points whose velocity the last pass took, y [3][N_phi] (physical coordinates, component-major): the node itself,
+// then (second kernel) the closest point of every band node.
+__global__ void k_node_points(int n, int64_t Np, double h, double* __restrict__ y) {
+    const int m1 = n + 1;
+    for (int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; node < Np;
+         node += (int64_t)gridDim.x * blockDim.x) {
+        y[node] = h * (double)(node % m1);
+        y[Np + node] = h * (double)((node / m1) % m1);
+        y[2 * Np + node] = h * (double)(node / ((int64_t)m1 * m1));
+    }
+}
+
+__global__ void k_band_points(const int32_t* __restrict__ band, const int32_t* __restrict__ band_count,
+                              const double* __restrict__ band_y, double h, int64_t Np, double* __restrict__ y) {
+    const int count = band_count[0];
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < count; b += gridDim.x * blockDim.x) {
+        const int64_t node = band[b];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) y[a * Np + node] = h * band_y[3 * (int64_t)b + a];
+    }
+}
+
+int launch_closest_points(evap_mesh* h, double* y, cudaStream_t s) {
+    const MeshArgs<double>& m = h->m;
+    k_node_points<<<blocks_for(m.Nphi, 256), 256, 0, s>>>(m.n, m.Nphi, m.h, y);
+    EVAP_CHECK_LAUNCH("node_points");
+    if (m.variant != 1) {
+        k_band_points<<<blocks_for(m.Nphi, 256), 256, 0, s>>>(h->band_list, h->band_count, h->band_y, m.h, m.Nphi, y);
+        EVAP_CHECK_LAUNCH("band_points");
+    }
+    return EVAP_OK;
 }
 
 int launch_transport_velocity(evap_mesh* h, cudaStream_t s, const double* phi) {

@@ -2,6 +2,7 @@
 //   1. velocity-pressure solve with Picard iterations (newton = 0): BDF1 (c_m = 1/dt, u* = u^n) or, given u^(n-1),
 //      BDF2 (c_m = 3/(2 dt), u* = (4 u^n - u^(n-1)) / 3); iteration k solves
 //        [A(u^(k)), -B^T; B, 0] [u^(k+1); p^(k+1)] = [f; g],  f = sum_q W N_i rho (c_m u* + g_body),  u^(0) = u^n,
+//      with the Dirichlet data of u^n (f = u^n on the Dirichlet DoFs, lifted by the solve),
 //      at most picard_iters times, stopping before a solve once |[f; g] - K(u^(k)) [u^(k); p^(k)]| <= picard_atol;
 //      with alpha != 0 f also carries the surface-tension force (Eq. surfaceTension) of the projected normal and
 //      regularized curvature of phi^n
@@ -97,6 +98,8 @@ int time_step(evap_mesh* h, double* phi, double* u, double* p, const double* mdo
         k_axpy1<<<blocks_for(Nu3, 256), 256, 0, s>>>(f, res, Nu3);
         EVAP_CHECK_LAUNCH("step_add_surface");
     }
+    // Dirichlet data: the velocity on the Dirichlet faces keeps its value of u^n (walls at rest, or an inflow)
+    if ((rc = launch_constrained_copy(h, u, f, s))) return rc;
     int applies = 0;
     double relres = 0.0, nl = -1.0;
     for (int it = 0; it < picard_iters; ++it) {
@@ -104,7 +107,7 @@ int time_step(evap_mesh* h, double* phi, double* u, double* p, const double* mdo
             if ((rc = set_fields_flow(h, h->phi, u, h->mdot, s))) return rc;
             const double* gc = nullptr;
             if ((rc = continuity_rhs(h, &gc, s))) return rc;
-            if ((rc = launch_saddle_apply(h, u, p, res, res + Nu3, s))) return rc;
+            if ((rc = launch_saddle_apply(h, u, p, res, res + Nu3, s, true))) return rc;  // K_D (lifted data)
             EVAP_CUDA(cudaMemsetAsync(sq, 0, sizeof(double), s));
             k_diff_sq<<<blocks_for(Nu3, 256, 152 * 8), 256, 0, s>>>(res, f, Nu3, sq);
             EVAP_CHECK_LAUNCH("picard_residual");

@@ -105,6 +105,8 @@ def test_transport_velocity_sampled_64(big):
     diff = np.abs(ug[:, nodes][:, ok] - ugo[:, ok]).max(axis=0)
     assert np.mean(diff <= 1e-6 * np.abs(ugo).max()) >= 0.99
     assert nflag <= 0.02 * len(band)
+    from test_gpu_parity import check_closest_points
+    check_closest_points(op, wl, np.asarray(band), sample=1500)
 
 
 def test_adjoint_finite_differences_48():

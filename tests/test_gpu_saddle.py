@@ -105,7 +105,8 @@ def test_saddle_solve_hydrostatic():
 
 def test_saddle_solve_evaporating_slab_outflow():
     """Flat evaporating interface, top open, no force: the outflow through the top face equals sum_j g_j (the
-    continuity row, to the solve tolerance) and mdot (1/rho_l - 1/rho_g) per unit area within 2 %."""
+    continuity row, to the solve tolerance) and mdot (1/rho_g - 1/rho_l) > 0 per unit area within 2 % (the gas
+    leaves: App. A)."""
     n = 8
     N1 = (n + 1) ** 3
     wl = workloads.random_workload(n, 2, 1, geom="sphere", dirichlet_faces=0x1F)
@@ -120,7 +121,32 @@ def test_saddle_solve_evaporating_slab_outflow():
     g = saddle.continuity_rhs(pb)
     assert out == pytest.approx(g.sum(), rel=1e-6)
     prm = pb.params
-    assert out == pytest.approx(mdot * (1.0 / prm["rho_l"] - 1.0 / prm["rho_g"]), rel=0.02)
+    closed = mdot * (1.0 / prm["rho_g"] - 1.0 / prm["rho_l"])
+    assert closed > 0.0
+    assert out == pytest.approx(closed, rel=0.02)
+
+
+def test_saddle_solve_dirichlet_data_against_oracle():
+    """Non-homogeneous Dirichlet data (the 1D phase change of App. A: inflow through the bottom face, the exact
+    profile on the side faces) lifted into the free rows, against the oracle's direct solve of the same system K_D;
+    the Dirichlet entries of the solution are the data exactly."""
+    from oracle import step
+    from test_oracle_saddle import stefan_case
+    n = 6
+    mesh, prm, phi, u, md, _, _ = stefan_case(n)
+    from paper_2401_07805_gb300 import Operator
+    op = Operator(n, 2, 1.0, dict(prm))
+    op.set_fields(cuda(phi), cuda(u), cuda(md))
+    pb = momentum.Problem(mesh=mesh, params=prm, phi=phi, u0=u, mdot=md)
+    f = step.mass_load(pb, u)
+    mask = pb.constrained()
+    f[mask] = u[mask]
+    x, pr, info = op.solve_saddle(cuda(f), rtol=1e-12, max_iter=3000)
+    assert info["converged"], info
+    xr, prr = saddle.solve(pb, f)
+    assert np.array_equal(host(x)[mask], u[mask])
+    assert rel(host(x), xr) < 1e-7
+    assert rel(host(pr), prr) < 1e-6
 
 
 def test_saddle_solve_rejects_a_closed_box():

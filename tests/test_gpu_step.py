@@ -208,3 +208,47 @@ def test_time_step_preserves_a_uniform_translation():
                                        u_prev=u_prev)
         assert float((gu - u).abs().max()) < 1e-8 * float(np.abs(U).max())
         assert float(gp.abs().max()) < 1e-9 * prm["rho_l"] * prm["c_mass"] * float(np.abs(U).max()) * mesh.h
+
+
+def test_stationary_1d_phase_change_step_against_oracle():
+    """App. A case (inflow mdot / rho_l through the bottom face, the exact 1D velocity as Dirichlet data on the side
+    faces, top open) on 6^3: the step with its lifted Dirichlet data, element by element against the oracle's step."""
+    from test_oracle_saddle import stefan_case
+    n = 6
+    mesh, prm, phi, u, md, _, _ = stefan_case(n)
+    op = make_op(n, prm)
+    gphi, gu, gp, info = op.time_step(cuda(phi), cuda(u), cuda(np.zeros(mesh.n_phi)), cuda(md), fp_iters=2,
+                                      reinit_steps=2, ns_rtol=1e-10, picard_iters=2, picard_atol=0.0)
+    assert info["converged"], info
+    ph1, u1, p1 = step.time_step(mesh, prm, phi, u, np.zeros(mesh.n_phi), md, fp_iters=2, reinit_steps=2,
+                                 picard_iters=2)
+    assert rel(host(gu), u1) < 1e-6
+    assert rel(host(gp), p1) < 1e-5
+    assert np.abs(host(gphi) - ph1).max() < 1e-7
+
+
+def test_stationary_1d_phase_change_converges_to_the_closed_form():
+    """App. A through evap_time_step on 8^3, 16^3 and 32^3 cells at fixed eps = 1/8: the velocity and pressure of the
+    step from the exact diffuse state approach Eqs. (stefan_diffuse_velocity), (stefan_diffuse_pressure) (the max
+    nodal error at least halves per refinement; the oracle's 6^3 -> 8^3 rates are ~h^3 for the velocity and ~h^2 for
+    the pressure; below 1 % of the velocity jump and 2 % of the pressure jump at 32^3), the transverse velocity stays
+    at the discretization error and the interface stays put."""
+    from test_oracle_saddle import STEFAN, stefan_case
+    eu, ep = [], []
+    for n in (8, 16, 32):
+        mesh, prm, phi, u, md, pex, jump = stefan_case(n)
+        op = make_op(n, prm)
+        gphi, gu, gp, info = op.time_step(cuda(phi), cuda(u), cuda(np.zeros(mesh.n_phi)), cuda(md), fp_iters=2,
+                                          reinit_steps=2, ns_rtol=1e-10, picard_iters=2, picard_atol=0.0)
+        assert info["converged"], info
+        u1, p1 = host(gu), host(gp)
+        eu.append(np.abs(u1 - u).max() / jump)
+        ep.append(np.abs(p1 - pex).max() / (STEFAN["mdot"] * jump))
+        assert np.abs(u1[:2 * mesh.n_u]).max() < 2.0 * eu[-1] * jump
+        assert abs(interface_height(host(gphi), n) - interface_height(phi, n)) < 0.02 * mesh.h
+        print(f"stefan {n}^3: velocity error {eu[-1]:.3e}, pressure error {ep[-1]:.3e} (relative to the jumps)")
+    for a, b in zip(eu, eu[1:]):
+        assert b < a / 2.0
+    for a, b in zip(ep, ep[1:]):
+        assert b < a / 2.0
+    assert eu[-1] < 0.01 and ep[-1] < 0.02

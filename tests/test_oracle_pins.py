@@ -539,3 +539,44 @@ def test_closest_point_rounding_sensitivity():
     d = np.abs(ug - ug2).max(axis=0)[ok]
     assert np.mean(fl == fl2) >= 0.98
     assert np.mean(d <= 1e-6 * np.abs(ug).max()) >= 0.99
+
+
+@pytest.mark.parametrize("name", ["sphere8", "spheres64", "sphere48", "slab96", "deformed128"])
+def test_normal_cutoff_is_inactive_near_the_interface(name):
+    """The reading that sets n = 0 where |grad phi_h| h <= 1e-4 (physics.has_normal) changes nothing where the normal
+    matters: on every workload (phi = tanh(d / 2 eps), eps = h) |grad phi_h| h exceeds the cut-off at every velocity
+    quadrature point of the interface zone |phi_h| < tanh(3/2) (where the corrected stress and the delta use n) and at
+    every Q1 node of the closest-point band -tanh(3) < phi < tanh(3) of variants 2 and 3 (n(x) of the transport
+    velocity), by a margin of at least 10.  (For the tanh profile |grad phi| h = (1 - phi^2) |grad d| h / (2 eps), at
+    least 0.09 in the zone and 0.005 at the band edge; the cut-off acts only ~9 eps or more from an interface.)"""
+    wl = workloads.make_workload(name)
+    mesh = fe.Mesh(wl.n, 1, wl.L)
+    h = mesh.h
+    assert wl.params["eps"] == pytest.approx(h)
+    t, _ = fe.gauss_rule(wl.p + 1)
+    b1 = fe.tensor_basis(1, t, h)
+    cells = mesh.cells()
+    worst = np.inf
+    for s in range(0, len(cells), 65536):
+        ph = wl.phi[mesh.dofs_phi(cells[s:s + 65536])]                 # [nc, 8]
+        pq = ph @ b1.N                                                 # [nc, nq]
+        gq = np.linalg.norm(np.einsum("nj,bjq->nqb", ph, b1.G), axis=-1)
+        zone = physics.in_zone(pq)
+        if zone.any():
+            assert np.all(physics.has_normal(gq[zone], h))
+            worst = min(worst, float(gq[zone].min() * h))
+    # node gradients as the transport velocity takes them: the point-located cell's trilinear interpolant at the node
+    m1 = wl.n + 1
+    P = wl.phi.reshape(m1, m1, m1)                                     # [z, y, x]
+    band = (-physics.PHI_GAS_BAND < P) & (P < physics.PHI_GAS_BAND)
+    g = np.zeros((3,) + P.shape)
+    for ax, axis in ((0, 2), (1, 1), (2, 0)):                          # x, y, z derivative along array axes 2, 1, 0
+        fwd = np.diff(P, axis=axis) / h                                # cell of the node = floor, clamped to n - 1
+        last = np.take(fwd, [-1], axis=axis)
+        g[ax] = np.concatenate([fwd, last], axis=axis)
+    # the trilinear gradient at a cell corner is the edge difference along that axis (the other coordinates at the
+    # corner), so the node's gradient is the forward difference (backward on the last node)
+    gn = np.linalg.norm(g, axis=0)
+    assert np.all(physics.has_normal(gn[band], h))
+    worst = min(worst, float(gn[band].min() * h))
+    assert worst > 10 * physics.GRAD_TINY, worst
