@@ -1,16 +1,19 @@
 """Benchmark of the matrix-free evaporation hot path on GB300.
 
-One step = one pass of the whole hot path over the 64^3-cell four-sphere workload (Q2 velocity, 6.44 M velocity
-DoFs, 275 k level-set DoFs, density ratio 1e3, random-Fourier velocity):
-  set_fields (material law table + variant-2 transport velocity with closest-point projection)
-  -> momentum apply FP64 with divergence row -> momentum apply FP32 -> level-set advect / reinit / reinit RHS (FP64)
-  -> adjoint apply (all four gradients) -> mixed-precision GMRES(16) solve to 1e-10.
-value = velocity DoFs per step / step time (GDoF/s of the whole pass); per-operator GDoF/s, bytes and the roofline
-of the dominant kernel are reported beside it.  Inputs (~0.5 GB touched per step) exceed the 129 MB L2.
+Workload: the 64^3-cell four-sphere case (Q2 velocity, 6.44 M velocity DoFs, 275 k level-set DoFs, density ratio
+1e3, random-Fourier velocity).  One step = one pass of the whole hot path:
+  set_fields (material-law table + variant-2 transport velocity with closest-point projection)
+  -> 100 back-to-back FP64 momentum applies with the divergence row (the 64^3 configuration's "100 repeated applies")
+  -> 100 FP32 momentum applies -> 100 level-set advection applies -> reinitialization operator and right-hand side
+  -> adjoint apply (all four gradients) -> mixed-precision GMRES solve to 1e-10.
+value = FP64 momentum operator-apply GDoF/s (velocity DoFs x applies / time of the 100 back-to-back applies, CUDA
+events, max over ranks); the FP32 apply, the adjoint and the level-set apply are first-class keys beside it, each
+with its roofline fractions; the whole-step rate is an extra.  Inputs (~0.5 GB touched per apply) exceed the 129 MB
+L2.  Denominators: HBM from MEASURED_PEAKS.json, FP64 and FP32 from FMA probes run in this process.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Under torchrun every rank runs an independent replica (weak scaling, no collective on the data path); rank 0 prints
-one JSON line.  --impl reference times the CPU oracle on a bounded sample of the same workload instead.
+one JSON line.  --impl reference times the CPU oracle (assembled CSR operator) on the host cores instead.
 """
 from __future__ import annotations
 
@@ -42,10 +45,10 @@ def load_peaks():
 
 
 # DRAM bytes (read + write) per launch of a kernel from an ncu capture of this bench, valid only while the kernel's
-# sources are unchanged: {(kernel, workload): (bytes, sha256 prefix of the sources, profile summary)}.
+# sources are unchanged: {(kernel, workload): (bytes, sha256 prefix of the sources)}.
 MEASURED_TRAFFIC = {
-    ("k_momentum32", "spheres64"): (431_719_680, "a39b9c808096dfb6", "profiles/k_momentum32_spheres64.md"),
-    ("k_momentum64", "spheres64"): (1_228_852_224, "9de9670fb8e2d3b1", "profiles/k_momentum64_spheres64.md"),
+    ("k_momentum32", "spheres64"): (431_719_680, "a39b9c808096dfb6"),
+    ("k_momentum64", "spheres64"): (1_228_852_224, "9de9670fb8e2d3b1"),
 }
 TRAFFIC_SOURCES = {"k_momentum32": ("paper_2401_07805_gb300/csrc/momentum32.cu",
                                     "paper_2401_07805_gb300/csrc/basis_ct.cuh",
@@ -76,11 +79,11 @@ def measured_traffic(kernel, workload):
     return rec[0]
 
 
-# Nominal FP64 rate of GB300 (profiling recipe table: 1.25 TFLOP/s); the FP64 FMA probe measured 1.19 TFLOP/s.
-FP64_PEAK_TFLOPS = 1.25
-# FP32 peak from the unit counts and clocks of the profiling recipe: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x
-# 2.07 GHz maximum SM clock = 80.5 TFLOP/s (the FMA probe measured 73 TFLOP/s at the clocks it saw).
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# Nominal rates, quoted beside the probes' measurements: FP64 1.25 TFLOP/s (the profiling recipe's table); FP32
+# 152 SMs x 128 lanes x 2 flop x 2.07 GHz = 80.5 TFLOP/s (the recipe's unit counts and maximum SM clock).
+FP64_NOMINAL_TFLOPS = 1.25
+FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+REPS = 100  # back-to-back applies per operator and step (the 64^3 configuration's 100 repeated applies)
 
 
 def algorithmic_counts(n: int, p: int):
@@ -109,9 +112,13 @@ def algorithmic_counts(n: int, p: int):
     mom32_flop = 2 * nc * mom32_fma
     return dict(
         Nu=Nu, Np=Np, ncell=nc,
-        # FP64 apply: x in, y and y_p out, the 19 cached FP64 coefficients per quadrature point streamed in
+        # algorithmic bytes of the method (every nodal vector read or written once, no quadrature data stored):
+        # FP64 apply: x, u0 and y [3 N_u] plus phi and mdot [N_phi]; FP32 apply: x, u0, y in FP32, phi, mdot in FP64
+        mom64_alg_bytes=8 * (9 * Nu + 2 * Np),
+        mom32_alg_bytes=4 * 9 * Nu + 8 * 2 * Np,
+        # bytes the kernels stream: FP64 apply x in, y and y_p out, the 19 cached FP64 coefficients per quadrature
+        # point; FP32 apply x in, y out, 12 FP32 u0 coefficients per quadrature point, cell code and table index
         mom64_bytes=8 * (3 * Nu * 2 + Np) + 8 * nc * 19 * nq,
-        # FP32 apply: x in, y out, 12 FP32 u0 coefficients per quadrature point, cell code and table index
         mom32_bytes=4 * (3 * Nu * 2) + 4 * nc * 12 * nq + 5 * nc,
         mom_flop=mom_flop,
         mom32_flop=mom32_flop,
@@ -187,56 +194,78 @@ def cpu_info():
     return cores, model
 
 
-def oracle_sample(wl, nb: int = 8, reps: int = 1):
-    """Time the CPU oracle on a bounded sample: every hot-path row of an nb^3-cell sub-block of the workload
-    (momentum element matrices and apply with divergence rows, transport velocity of the sub-block's band nodes,
-    level-set advect/reinit/reinit-RHS, adjoint parameter gradients).  Returns (seconds, velocity DoFs covered)."""
-    from oracle import adjoint, fe, levelset, momentum, transport
-    n = wl.n
-    mesh = fe.Mesh(n, wl.p, wl.L)
-    pb = momentum.Problem.from_workload(wl)
-    c0 = n // 2 - nb // 2
-    r = np.arange(c0, c0 + nb)
-    Z, Y, X = np.meshgrid(r, r, r, indexing="ij")
-    cells = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
-    du = np.unique(mesh.dofs_u(cells))
-    d1 = np.unique(mesh.dofs_phi(cells))
-    rng = np.random.default_rng(0)
-    w = rng.uniform(-1, 1, wl.x.shape)
+def _oracle_block(args):
+    """One host core's share of the CPU baseline (runs in a spawned process): the oracle's assembled FP64 momentum
+    operator with its divergence rows on an nb^3-cell sub-block of the workload (no Dirichlet faces; the workload's
+    fields restricted to the block), CSR assembly timed once, then `reps` applies (y = A x, y_p = B x - g) each
+    timed, after all workers reached the barrier.  Returns (assembly s, list of apply s, velocity DoFs)."""
+    name, nb, corner, reps, barrier = args
+    sys.path.insert(0, ROOT)
+    import workloads as wlmod
+    from oracle import fe, momentum
+    wl = wlmod.make_workload(name)
+    n, p = wl.n, wl.p
+    M, m1, mb, m1b = p * n + 1, n + 1, p * nb + 1, nb + 1
+    cx, cy, cz = corner
+    iu = np.arange(mb)
+    K, J, I = np.meshgrid(p * cz + iu, p * cy + iu, p * cx + iu, indexing="ij")
+    gu = (I + M * (J + M * K)).ravel()
+    i1 = np.arange(m1b)
+    K1, J1, I1 = np.meshgrid(cz + i1, cy + i1, cx + i1, indexing="ij")
+    g1 = (I1 + m1 * (J1 + m1 * K1)).ravel()
+    sub = lambda v: np.concatenate([v.reshape(3, -1)[c][gu] for c in range(3)])
+    prm = dict(wl.params, dirichlet_faces=0)
+    pb = momentum.Problem(mesh=fe.Mesh(nb, p, nb * wl.L / n), params=prm, phi=wl.phi[g1].copy(),
+                          u0=sub(wl.u0), mdot=wl.mdot[g1].copy())
+    x = sub(wl.x)
     t0 = time.perf_counter()
+    A = momentum.assemble(pb)
+    B, g = momentum.divergence(pb)
+    t_asm = time.perf_counter() - t0
+    barrier.wait()
+    ts = []
     for _ in range(reps):
-        momentum.apply_rows(pb, wl.x, du)
-        momentum.divergence_rows(pb, wl.x, d1)
-        band = d1[(wl.phi[d1] > -workloads_tanh3()) & (wl.phi[d1] < np.tanh(1.5))]
-        transport.transport_velocity(mesh, wl.phi, wl.u0, wl.mdot, wl.params, nodes=band[: max(1, len(band) // 4)])
-        sub = fe.Mesh(nb, 1, nb * mesh.h)
-        ug = np.zeros(3 * sub.n_phi)
-        phis = rng.uniform(-1, 1, sub.n_phi)
-        for mode in ("advect", "reinit", "reinit_rhs"):
-            levelset.apply(sub, mode, phis, phis, ug, wl.params)
-        sub_wl = workloads.random_workload(nb, p=wl.p, seed=1)
-        sub_pb = momentum.Problem.from_workload(sub_wl)
-        adjoint.param_gradients(sub_pb, sub_wl.x, sub_wl.x, np.ones(sub_pb.mesh.n_phi))
-    dt = (time.perf_counter() - t0) / reps
-    return dt, 3 * len(du)
+        t0 = time.perf_counter()
+        y = A @ x
+        yp = B @ x - g
+        ts.append(time.perf_counter() - t0)
+    del y, yp
+    return t_asm, ts, 3 * pb.mesh.n_u
 
 
-def workloads_tanh3():
-    return float.fromhex("0x1.fd77d111a0b00p-1")
-
-
-def oracle_sample_subprocess(nb: int, reps: int = 1):
-    """Run oracle_sample in a fresh single-threaded interpreter (BLAS/OpenMP pinned to 1 thread, so the reported
-    core count is the number actually used; a new process is spawned, never forked from one that holds a GPU
-    context).  Returns (seconds, velocity DoFs covered, cores)."""
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
-               CUDA_VISIBLE_DEVICES="")
-    code = ("import json, sys; sys.path.insert(0, %r); import bench, workloads; "
-            "wl = workloads.make_workload(bench.WORKLOAD); dt, dofs = bench.oracle_sample(wl, nb=%d, reps=%d); "
-            "print(json.dumps([dt, dofs]))" % (ROOT, nb, reps))
-    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, check=True)
-    dt, dofs = json.loads(out.stdout.strip().splitlines()[-1])
-    return dt, dofs, 1
+def oracle_baseline(name: str = "spheres64", nb: int = 12, reps: int = 10, workers: int | None = None):
+    """The CPU oracle as it stands on all host cores: one spawned process per core, each assembling the oracle's
+    CSR momentum operator (full Gauss quadrature) on its own nb^3-cell sub-block of the workload and timing `reps`
+    applies with the divergence rows; the aggregate rate is the sum over workers of block DoFs / median apply time
+    (the applies of all workers run at the same time, after a barrier).  Spawned, so no process inherits a GPU
+    context."""
+    import multiprocessing as mp
+    workers = workers or os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    wl = workloads.make_workload(name)
+    per = max(1, wl.n // nb)
+    corners = [((k % per) * nb, ((k // per) % per) * nb, ((k // (per * per)) % per) * nb) for k in range(workers)]
+    # one thread per worker process (the spawned interpreters read these at import): cores = workers
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    os.environ.update({k: "1" for k in saved})
+    try:
+        with ctx.Manager() as mgr:
+            barrier = mgr.Barrier(workers)
+            with ctx.Pool(workers) as pool:
+                res = pool.map(_oracle_block, [(name, nb, c, reps, barrier) for c in corners])
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    rate = sum(dofs / float(np.median(ts)) for _, ts, dofs in res)
+    return dict(value=rate / 1e9, unit="GDoF/s", cores=workers, kind="oracle",
+                assembly_s=float(np.median([r[0] for r in res])),
+                apply_ms_median=1e3 * float(np.median([np.median(r[1]) for r in res])),
+                sample=f"the oracle's assembled FP64 momentum operator with divergence rows (CSR, full Gauss "
+                       f"quadrature) on {workers} disjoint {nb}^3-cell sub-blocks of the {name} workload, one process "
+                       f"per host core; median of {reps} applies after CSR assembly (assembly reported separately)")
 
 
 def solve_comparison(evap, torch, dev):
@@ -296,33 +325,14 @@ def back_to_back(torch, fn, reps, warm):
 
 
 def operator_applies(evap, torch, dev, op, d, counts, hbm):
-    """Per-operator throughput on the 64^3 four-sphere workload: 100 back-to-back applies after 10 warm-ups each
-    (momentum FP64 with the divergence row, momentum FP32, level-set advection FP64), the closest-point transport
-    pass alone (20 repeats: band nodes/s, point evaluations, flags), and the adjoint on the 48^3 sphere
-    (2.74 M DoFs, 20 applies).  Inputs are larger than the L2 for every operator except the level set."""
-    nu3, nphi = 3 * op.n_u, op.n_phi
-    x, x32, psi = d["x"], d["x32"], d["psi"]
-    y64 = torch.empty(nu3, dtype=torch.float64, device=dev)
-    yp64 = torch.empty(nphi, dtype=torch.float64, device=dev)
-    y32 = torch.empty(nu3, dtype=torch.float32, device=dev)
-    yl = torch.empty(nphi, dtype=torch.float64, device=dev)
+    """Extras beside the step: the closest-point transport pass alone on the 64^3 workload (20 repeats: band nodes/s,
+    point evaluations, flags) and the adjoint on the 48^3 sphere (2.74 M DoFs, 20 applies after 3)."""
     out = {}
-    t = back_to_back(torch, lambda: op.apply_momentum(x, prec=64, with_divergence=True, out=y64, out_p=yp64), 100, 10)
-    out["momentum_fp64"] = dict(ms=t, gdofs=nu3 / t / 1e6, gbs=counts["mom64_bytes"] / t / 1e6,
-                                fp64_tflops=counts["mom_flop"] / t / 1e9)
-    t = back_to_back(torch, lambda: op.apply_momentum(x32, prec=32, out=y32), 100, 10)
-    out["momentum_fp32"] = dict(ms=t, gdofs=nu3 / t / 1e6, gbs=counts["mom32_bytes"] / t / 1e6,
-                                hbm_frac=counts["mom32_bytes"] / t / 1e6 / hbm,
-                                fp32_tflops=counts["mom32_flop"] / t / 1e9,
-                                rel_err_vs_fp64=float((y32.double() - y64).norm() / y64.norm()))
-    t = back_to_back(torch, lambda: op.apply_levelset(psi, mode="advect", out=yl), 100, 10)
-    out["levelset_advect_fp64"] = dict(ms=t, gdofs=nphi / t / 1e6, gbs=counts["ls_adv_bytes"] / t / 1e6)
     t = back_to_back(torch, op.update_transport_velocity, 20, 2)
     st = op.transport_stats()
     out["transport_velocity"] = dict(ms=t, band_nodes=st["band_nodes"], band_nodes_per_s=st["band_nodes"] / t * 1e3,
                                      evaluations_per_node=st["evaluations"] / max(st["band_nodes"], 1),
                                      flagged=st["flagged"])
-    # adjoint on the 48^3 sphere
     wl = workloads.make_workload("sphere48")
     op4 = evap.Operator(wl.n, wl.p, wl.L, dict(wl.params))
     cu = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
@@ -332,7 +342,6 @@ def operator_applies(evap, torch, dev, op, d, counts, hbm):
     c4 = algorithmic_counts(wl.n, wl.p)
     out["adjoint_sphere48"] = dict(ms=t, gdofs=3 * op4.n_u / t / 1e6, fp64_tflops=c4["adj_flop"] / t / 1e9)
     op4.close()
-    out["note"] = "100 back-to-back applies after 10 warm-ups (transport 20 after 2, adjoint 20 after 3)"
     return out
 
 
@@ -479,41 +488,46 @@ def large_case(evap, torch, dev, p: int):
 
 
 def run_reference(args):
-    """--impl reference: the CPU oracle, timed on a bounded sample per step (rank 0 only)."""
+    """--impl reference: the CPU oracle's FP64 momentum apply on all host cores (rank 0 only): every step is one
+    apply on each core's sub-block (oracle_baseline), the warm-up steps untimed."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    # each step is a bounded sample of the workload (all hot-path rows of a 10^3-cell sub-block), timed in a
-    # single-threaded interpreter; the whole --steps K --warmup W run stays within a few minutes
-    oracle_sample_subprocess(nb=4, reps=max(1, args.warmup))
-    dt, dofs, _ = oracle_sample_subprocess(nb=10, reps=args.steps)
-    t = dt * args.steps
-    value = dofs * args.steps / t / 1e9
+    base = oracle_baseline(WORKLOAD, nb=12, reps=args.warmup + args.steps)
+    value = base["value"]
     cores, model = cpu_info()
     out = dict(impl="reference", metric=METRIC, value=value, unit="GDoF/s", n_gpus=args.gpus, steps=args.steps,
-               warmup=args.warmup, ms_per_step=1e3 * t / args.steps, higher_is_better=True, scaling="weak",
+               warmup=args.warmup, ms_per_step=base["apply_ms_median"], higher_is_better=True, scaling="weak",
                vs_baseline=None, dtype="f64", data="synthetic",
                config=dict(workload="spheres64: 64^3 cells, Q2 velocity, 4 random spheres, density ratio 1e3, "
-                                    "random-Fourier velocity (seed 2)", sample="10^3-cell sub-block per step",
-                           l2="sample fits in host caches (CPU)"),
-               cpu_baseline=dict(value=value, unit="GDoF/s", cores=1, kind="oracle",
-                                 sample="all hot-path rows of a 10^3-cell sub-block of the 64^3 workload "
-                                        "(single thread)", cpu=model),
+                                    "random-Fourier velocity (seed 2)",
+                           sample=f"{base['cores']} disjoint 12^3-cell sub-blocks, one per host core",
+                           l2="CSR blocks of ~0.2 GB per core exceed the host caches"),
+               cpu_baseline=dict(base, value=value, cpu=model),
                e2e=dict(value=value, unit="GDoF/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(out), flush=True)
+
+
+def rates(t_ms, dofs, alg_bytes, stream_bytes, flop, hbm, alu_peak):
+    """Per-apply figures of an operator: GDoF/s, %HBM against the algorithmic bytes of the method and against the
+    bytes the kernel streams, and the arithmetic rate against the measured FMA peak of its pipe."""
+    t = t_ms * 1e-3
+    return dict(ms=t_ms, gdofs=dofs / t / 1e9, alg_bytes=alg_bytes, hbm_frac=alg_bytes / t / 1e9 / hbm,
+                stream_bytes=stream_bytes, hbm_frac_streamed=stream_bytes / t / 1e9 / hbm,
+                tflops=flop / t / 1e12, alu_frac=flop / t / 1e12 / alu_peak)
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-solve-compare", action="store_true", help="skip the 96^3 FP64-vs-mixed solve comparison")
     ap.add_argument("--no-large", action="store_true", help="skip the 128^3 Q2/Q3 large case")
-    ap.add_argument("--no-applies", action="store_true", help="skip the per-operator back-to-back apply timings")
+    ap.add_argument("--no-applies", action="store_true", help="skip the extra per-operator timings")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -524,6 +538,12 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    # the CPU baseline's worker processes are spawned before this process touches the GPU
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = oracle_baseline(WORKLOAD)
+        cores, model = cpu_info()
+        cpu.update(cpu=model, host_cores=cores)
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl")
@@ -543,8 +563,17 @@ def main():
     d = {k: torch.from_numpy(v).to(dev) for k, v in host.items()}
     d["x32"] = d["x"].float()
     stream = torch.cuda.current_stream()
-    names = ["set_fields", "mom64", "mom32", "ls_advect", "ls_reinit", "ls_rhs", "adjoint", "solve"]
+    nu3, nphi = 3 * op.n_u, op.n_phi
+    y64 = torch.empty(nu3, dtype=torch.float64, device=dev)
+    yp64 = torch.empty(nphi, dtype=torch.float64, device=dev)
+    y32 = torch.empty(nu3, dtype=torch.float32, device=dev)
+    yl = torch.empty(nphi, dtype=torch.float64, device=dev)
+    names = ["set_fields", "mom64", "mom32", "ls_advect", "ls_reinit", "adjoint", "solve"]
     solve_info = {}
+
+    # arithmetic peaks of this GPU at its current clocks (probes of the library, before the timed region)
+    fp64_peak = evap.fma_probe(64)
+    fp32_peak = evap.fma_probe(32)
 
     def step(dd, ev=None):
         def mark(i):
@@ -553,28 +582,31 @@ def main():
         mark(0)
         op.set_fields(dd["phi"], dd["u0"], dd["mdot"])
         mark(1)
-        y, yp = op.apply_momentum(dd["x"], prec=64, with_divergence=True)
+        for _ in range(REPS):
+            op.apply_momentum(dd["x"], prec=64, with_divergence=True, out=y64, out_p=yp64)
         mark(2)
-        y32 = op.apply_momentum(dd["x32"], prec=32)
+        for _ in range(REPS):
+            op.apply_momentum(dd["x32"], prec=32, out=y32)
         mark(3)
-        la = op.apply_levelset(dd["psi"], mode="advect")
+        for _ in range(REPS):
+            op.apply_levelset(dd["psi"], mode="advect", out=yl)
         mark(4)
         lr = op.apply_levelset(dd["psi"], mode="reinit")
-        mark(5)
         lh = op.apply_levelset(dd["psi"], mode="reinit_rhs")
-        mark(6)
+        mark(5)
         g = op.apply_adjoint(dd["w"], dd["x"], dd["wp"])
-        mark(7)
+        mark(6)
         xs, info = op.solve(dd["f"], mixed=True, restart=16, rtol=1e-10, max_iter=400)
-        mark(8)
+        mark(7)
         solve_info.update(info)
-        return dict(y=y, yp=yp, y32=y32, la=la, lr=lr, lh=lh, gx=g["x"], gu=g["u0"], gphi=g["phi"], gm=g["mdot"], xs=xs)
+        return dict(y=y64, yp=yp64, y32=y32, la=yl, lr=lr, lh=lh, gx=g["x"], gu=g["u0"], gphi=g["phi"], gm=g["mdot"],
+                    xs=xs)
 
     for _ in range(args.warmup):
         step(d)
     torch.cuda.synchronize()
     K = args.steps
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(9)] for _ in range(K)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)] for _ in range(K)]
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
@@ -593,116 +625,105 @@ def main():
     if world > 1:
         dist.barrier()
     clocks = sampler.stop()
-    ms_total = job_time_ms(torch, dist, t_start.elapsed_time(t_end), dev, world)
-    ms_step = ms_total / K
-    part = {nm: float(np.mean([evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(K)])) for i, nm in enumerate(names)}
-    Nu3 = 3 * counts["Nu"]
-    value = aggregate_gdofs(world, Nu3, ms_step)
+    ms_step = job_time_ms(torch, dist, t_start.elapsed_time(t_end), dev, world) / K
+    part = {nm: float(np.mean([evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(K)]))
+            for i, nm in enumerate(names)}
+    # the headline: FP64 momentum applies, the max over ranks of the 100-apply group's time
+    ms_mom64 = job_time_ms(torch, dist, part["mom64"], dev, world) / REPS
+    value = aggregate_gdofs(world, nu3, ms_mom64)
 
-    # end to end: pinned host inputs copied in and all results copied out inside the timed region.  The copies run on
-    # two copy streams (host-to-device for step k+1 while step k computes; device-to-host of step k's results after
-    # its compute), as a streaming pipeline would; every step still moves all of its inputs and results.
+    # end to end through the public API with host buffers: every apply copies its input x from pinned host memory
+    # in and its results y, y_p out inside the timed region (copy streams overlap the copies of neighbouring
+    # applies with compute, as a streaming caller would)
     e2e = None
     if not args.no_e2e:
-        pinned = {k: torch.from_numpy(v).pin_memory() for k, v in host.items()}
-        outs_host = None
-        h2d = sum(v.numel() * v.element_size() for v in pinned.values())
+        xh = torch.from_numpy(wl.x).pin_memory()
+        yh = [torch.empty(nu3, dtype=torch.float64, pin_memory=True) for _ in range(2)]
+        yph = [torch.empty(nphi, dtype=torch.float64, pin_memory=True) for _ in range(2)]
+        xd = [torch.empty(nu3, dtype=torch.float64, device=dev) for _ in range(2)]
+        yd = [torch.empty(nu3, dtype=torch.float64, device=dev) for _ in range(2)]
+        ypd = [torch.empty(nphi, dtype=torch.float64, device=dev) for _ in range(2)]
         cin, cout = torch.cuda.Stream(), torch.cuda.Stream()
+        op.set_fields(d["phi"], d["u0"], d["mdot"])
+        n_e2e = REPS * K
+        in_ev = [None, None]
+        out_ev = [None, None]
 
-        def fetch_inputs():
+        def copy_in(i):
             with torch.cuda.stream(cin):
-                nxt = {k: v.to(dev, non_blocking=True) for k, v in pinned.items()}
-                return nxt, cin.record_event()
+                if out_ev[i % 2] is not None:
+                    cin.wait_event(out_ev[i % 2])  # the buffer's previous apply has been read out
+                xd[i % 2].copy_(xh, non_blocking=True)
+                in_ev[i % 2] = cin.record_event()
 
-        total = args.warmup + K
-        nxt, ev_in = fetch_inputs()
-        ev_out = None
-        for it in range(total):
-            if it == args.warmup:
-                torch.cuda.synchronize()
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                nxt, ev_in = fetch_inputs()  # the timed steps copy their own inputs
-            stream.wait_event(ev_in)
-            dd = nxt
-            for v in dd.values():
-                v.record_stream(stream)
-            if it + 1 < total and it + 1 != args.warmup:
-                nxt, ev_in = fetch_inputs()
-            dd["x32"] = dd["x"].float()
-            outs = step(dd)
-            if outs_host is None:
-                outs_host = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in outs.items()}
-            done = stream.record_event()
-            with torch.cuda.stream(cout):
-                cout.wait_event(done)
-                for k, v in outs.items():
-                    v.record_stream(cout)
-                    outs_host[k].copy_(v, non_blocking=True)
-                ev_out = cout.record_event()
-        stream.wait_event(ev_out)
+        def run(n):
+            copy_in(0)
+            for i in range(n):
+                b = i % 2
+                stream.wait_event(in_ev[b])
+                if i + 1 < n:
+                    copy_in(i + 1)
+                op.apply_momentum(xd[b], prec=64, with_divergence=True, out=yd[b], out_p=ypd[b])
+                done = stream.record_event()
+                with torch.cuda.stream(cout):
+                    cout.wait_event(done)
+                    yh[b].copy_(yd[b], non_blocking=True)
+                    yph[b].copy_(ypd[b], non_blocking=True)
+                    out_ev[b] = cout.record_event()
+            stream.wait_event(out_ev[(n - 1) % 2])
+
+        run(10)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        run(n_e2e)
         e1.record(stream)
         torch.cuda.synchronize()
-        d2h = sum(v.numel() * v.element_size() for v in outs_host.values())
-        e_ms = job_time_ms(torch, dist, e0.elapsed_time(e1) / K, dev, world)
-        e2e = dict(value=aggregate_gdofs(world, Nu3, e_ms), unit="GDoF/s", ms_per_step=e_ms,
-                   h2d_bytes_per_step=int(h2d), d2h_bytes_per_step=int(d2h),
-                   note="inputs of step k+1 copied in while step k computes; results copied out after each step")
+        e_ms = job_time_ms(torch, dist, e0.elapsed_time(e1), dev, world) / n_e2e
+        e2e = dict(value=aggregate_gdofs(world, nu3, e_ms), unit="GDoF/s", ms_per_apply=e_ms,
+                   h2d_bytes_per_step=int(8 * nu3 * REPS), d2h_bytes_per_step=int(8 * (nu3 + nphi) * REPS),
+                   note="FP64 momentum applies through the C ABI with the input x copied in from pinned host memory "
+                        "and y, y_p copied out for every apply (100 applies per step); copies of neighbouring "
+                        "applies overlap with compute on two copy streams")
+        del xd, yd, ypd
 
     peaks, peak_src = load_peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
-    # FP64 momentum apply: FP64-pipe bound (its FP64-pipe roofline is reported beside the dominant kernel's)
-    t_mom = part["mom64"] * 1e-3
-    mom_tflops = counts["mom_flop"] / t_mom / 1e12
-    breakdown = {
-        "set_fields_ms": part["set_fields"],
-        "momentum_fp64": dict(ms=part["mom64"], gdofs=Nu3 / (part["mom64"] * 1e-3) / 1e9,
-                              gbs=counts["mom64_bytes"] / (part["mom64"] * 1e-3) / 1e9,
-                              hbm_frac=counts["mom64_bytes"] / (part["mom64"] * 1e-3) / 1e9 / hbm,
-                              fp64_tflops=mom_tflops),
-        "momentum_fp32": dict(ms=part["mom32"], gdofs=Nu3 / (part["mom32"] * 1e-3) / 1e9,
-                              fp32_tflops=counts["mom32_flop"] / (part["mom32"] * 1e-3) / 1e12,
-                              gbs=counts["mom32_bytes"] / (part["mom32"] * 1e-3) / 1e9,
-                              hbm_frac=counts["mom32_bytes"] / (part["mom32"] * 1e-3) / 1e9 / hbm),
-        "levelset_advect": dict(ms=part["ls_advect"], gdofs=counts["Np"] / (part["ls_advect"] * 1e-3) / 1e9),
-        "levelset_reinit": dict(ms=part["ls_reinit"], gdofs=counts["Np"] / (part["ls_reinit"] * 1e-3) / 1e9),
-        "levelset_reinit_rhs": dict(ms=part["ls_rhs"], gdofs=counts["Np"] / (part["ls_rhs"] * 1e-3) / 1e9),
-        "adjoint": dict(ms=part["adjoint"], gdofs=Nu3 / (part["adjoint"] * 1e-3) / 1e9,
-                        fp64_tflops=counts["adj_flop"] / (part["adjoint"] * 1e-3) / 1e12),
-        "solve_mixed": dict(ms=part["solve"], iters=solve_info.get("iters"), relres=solve_info.get("relres")),
-    }
-    # Dominant kernel of the step (largest share of the launch list): the FP64 momentum apply, launched three times
-    # per step (the step's own apply and the two FP64 residuals of the mixed solve).  It is bound by the FP64 pipe
-    # (~90 % active; its ~1.9 flop per algorithmic byte is ten times GB300's FP64 machine balance), so its roofline
-    # is the FP64 rate; its HBM fraction is reported beside it.  The FP32 apply inside the mixed solve (HBM-bound:
-    # its roof is the larger of bytes / HBM peak and flops / FP32 peak) follows as the second kernel.
-    g64 = counts["mom64_bytes"] / t_mom / 1e9
-    t32 = part["mom32"] * 1e-3
-    f32 = counts["mom32_flop"] / t32 / 1e12
-    g32 = counts["mom32_bytes"] / t32 / 1e9
-    hbm_bound = counts["mom32_bytes"] / (hbm * 1e9) >= counts["mom32_flop"] / (FP32_PEAK_TFLOPS * 1e12)
-    alu32 = dict(achieved=f32, peak=FP32_PEAK_TFLOPS, unit="TFLOP/s", frac=f32 / FP32_PEAK_TFLOPS,
-                 flop_per_launch=counts["mom32_flop"],
-                 peak_source="FP32 peak from the recipe's unit counts and max clock (152 SM x 128 lanes x 2 x 2.07 "
-                             "GHz); the FMA probe measured 73 TFLOP/s")
-    mem32 = dict(achieved=g32, peak=hbm, unit="GB/s", frac=g32 / hbm, bytes_per_launch=counts["mom32_bytes"],
-                 peak_source=peak_src)
-    main32, other32 = (mem32, alu32) if hbm_bound else (alu32, mem32)
+    mom64 = rates(ms_mom64, nu3, counts["mom64_alg_bytes"], counts["mom64_bytes"], counts["mom_flop"], hbm,
+                  fp64_peak)
+    mom32 = rates(part["mom32"] / REPS, nu3, counts["mom32_alg_bytes"], counts["mom32_bytes"], counts["mom32_flop"],
+                  hbm, fp32_peak)
+    y32_err = float((y32.double() - y64).norm() / y64.norm())
+    mom32["rel_err_vs_fp64"] = y32_err
+    adj = rates(part["adjoint"], nu3, counts["adj_bytes"], counts["adj_bytes"] + counts["mom64_bytes"]
+                - 8 * (3 * counts["Nu"] * 2 + counts["Np"]), counts["adj_flop"], hbm, fp64_peak)
+    ls = dict(ms=part["ls_advect"] / REPS, gdofs=nphi / (part["ls_advect"] / REPS * 1e-3) / 1e9,
+              alg_bytes=counts["ls_adv_bytes"],
+              hbm_frac=counts["ls_adv_bytes"] / (part["ls_advect"] / REPS * 1e-3) / 1e9 / hbm,
+              note="275 k Q1 DoFs: the 11 MB of vectors stay in L2 across back-to-back applies")
+    # Dominant kernel of the step (largest share of its launch list): the FP64 momentum apply, 100 launches per step
+    # plus the FP64 residuals of the mixed solve.  Bound by the FP64 pipe (its ~14 flop per algorithmic byte is ~70
+    # times GB300's FP64 machine balance), so the roofline is the measured FP64 FMA rate; its HBM fractions (against
+    # the method's algorithmic bytes and against the bytes it streams with its quadrature-point cache) are beside it.
     roofline = dict(bound="alu",
-                    kernel="k_momentum<double,2,8> (FP64 momentum apply: the step's apply and the two FP64 residuals "
-                           "of the mixed solve)",
-                    achieved=mom_tflops, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s", frac=mom_tflops / FP64_PEAK_TFLOPS,
+                    kernel="k_momentum<double,2,8> (FP64 momentum apply with divergence row, 100 per step)",
+                    achieved=mom64["tflops"], peak=fp64_peak, unit="TFLOP/s", frac=mom64["alu_frac"],
                     traffic=measured_traffic("k_momentum64", WORKLOAD), flop_per_launch=counts["mom_flop"],
-                    peak_source="nominal FP64 rate of the profiling recipe's table; an FMA probe measured 1.19 TFLOP/s",
-                    hbm=dict(achieved=g64, peak=hbm, unit="GB/s", frac=g64 / hbm,
-                             bytes_per_launch=counts["mom64_bytes"], peak_source=peak_src),
-                    fp32_kernel=dict(kernel="k_momentum32<2,32,3> (FP32 momentum apply inside the mixed solve)",
-                                     bound="hbm" if hbm_bound else "alu",
-                                     achieved=main32["achieved"], peak=main32["peak"], unit=main32["unit"],
-                                     frac=main32["frac"], traffic=measured_traffic("k_momentum32", WORKLOAD),
-                                     peak_source=main32["peak_source"],
-                                     **{"alu" if hbm_bound else "hbm": other32}))
+                    peak_source=f"FP64 FMA probe in this process (evap_fma_probe), nominal "
+                                f"{FP64_NOMINAL_TFLOPS} TFLOP/s",
+                    hbm=dict(achieved=mom64["alg_bytes"] / ms_mom64 / 1e6, peak=hbm, unit="GB/s",
+                             frac=mom64["hbm_frac"], bytes_per_launch=counts["mom64_alg_bytes"],
+                             frac_streamed=mom64["hbm_frac_streamed"], streamed_bytes=counts["mom64_bytes"],
+                             peak_source=f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"),
+                    fp32_kernel=dict(kernel="k_momentum32<2,32,3> (FP32 momentum apply)", bound="hbm",
+                                     achieved=mom32["alg_bytes"] / (mom32["ms"] * 1e6), peak=hbm, unit="GB/s",
+                                     frac=mom32["hbm_frac"], frac_streamed=mom32["hbm_frac_streamed"],
+                                     traffic=measured_traffic("k_momentum32", WORKLOAD),
+                                     fp32_tflops=mom32["tflops"], fp32_frac=mom32["alu_frac"]))
+    whole = dict(ms=ms_step, gdofs=aggregate_gdofs(world, nu3, ms_step),
+                 parts_ms=part, solve=dict(iters=solve_info.get("iters"), relres=solve_info.get("relres")),
+                 note="velocity DoFs per whole step (set_fields, 100 FP64 + 100 FP32 momentum applies, 100 level-set "
+                      "advections, reinitialization operators, adjoint, mixed solve)")
     applies = None
     if rank == 0 and not args.no_applies:
         applies = operator_applies(evap, torch, dev, op, d, counts, hbm)
@@ -715,25 +736,23 @@ def main():
     if rank == 0 and not args.no_large:
         op.close()
         large = {f"q{p}": large_case(evap, torch, dev, p) for p in (2, 3)}
-    cpu = None
-    if rank == 0 and not args.no_cpu:
-        dt, dofs, used = oracle_sample_subprocess(nb=20)
-        cores, model = cpu_info()
-        cpu = dict(value=dofs / dt / 1e9, unit="GDoF/s", cores=used, kind="oracle",
-                   sample="all hot-path rows (momentum + divergence rows, transport velocity of a quarter of the "
-                          "band nodes, 3 level-set operators, adjoint gradients) of a 20^3-cell sub-block of the 64^3 "
-                          "workload, numpy in a single-threaded process", seconds=dt, cpu=model, host_cores=cores)
     if rank == 0:
         out = dict(metric=METRIC, value=value, unit="GDoF/s", n_gpus=world, steps=K, warmup=args.warmup,
                    ms_per_step=ms_step, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
                    data="synthetic",
                    config=dict(workload="spheres64: 64^3 cells, Q2 velocity (6.44 M DoFs), Q1 level set (275 k "
                                         "DoFs), 4 random spheres, density ratio 1e3, random-Fourier velocity",
-                               step="set_fields + FP64/FP32 momentum + 3 level-set applies + adjoint + mixed solve",
+                               value="FP64 momentum operator apply with divergence row, 100 back-to-back applies "
+                                     "per step",
+                               step="set_fields + 100 FP64 + 100 FP32 momentum applies + 100 level-set advections + "
+                                    "reinitialization operators + adjoint + mixed solve",
                                l2="inputs larger than L2 (no flush)", parallelism=f"replicas x{world}"),
-                   roofline=roofline, breakdown=breakdown, applies=applies, solve_comparison=solves, large_case=large,
-                   cpu_baseline=cpu, e2e=e2e,
-                   gpu_launches=int(launches), clocks=clocks)
+                   momentum_fp64=mom64, momentum_fp32=mom32, adjoint=adj, levelset_advect=ls,
+                   peaks=dict(fp64_tflops_measured=fp64_peak, fp64_tflops_nominal=FP64_NOMINAL_TFLOPS,
+                              fp32_tflops_measured=fp32_peak, fp32_tflops_nominal=FP32_NOMINAL_TFLOPS,
+                              hbm_gbs=hbm, hbm_source=peak_src),
+                   roofline=roofline, whole_step=whole, applies=applies, solve_comparison=solves, large_case=large,
+                   cpu_baseline=cpu, e2e=e2e, gpu_launches=int(launches), clocks=clocks)
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -287,6 +287,12 @@ int evap_jacobi_diagonal(evap_handle h, double* diag, void* stream);
  * serialized by the caller.  Calls no cudaMalloc, cudaFree or allocating library routine. */
 int evap_jacobi_diagonal_noalloc(evap_handle h, double* diag, void* stream);
 
+/* Measured FMA throughput of the current device in TFLOP/s (prec 64: FP64, 32: FP32), *tflops a host pointer: about
+ * 50 ms of independent FMA chains on every SM, timed with CUDA events after one warm-up launch (synchronizes the
+ * stream).  The denominator of the roofline fractions of ALU-bound kernels.  The paper has no counterpart
+ * (instrumentation). */
+int evap_fma_probe(int prec, double* tflops, void* stream);
+
 const char* evap_status_string(int status);
 const char* evap_last_error(void);
 

@@ -77,6 +77,7 @@ SIGNATURES = {
     "evap_status_string": (ctypes.c_char_p, [_c_int]),
     "evap_last_error": (ctypes.c_char_p, []),
     "evap_launch_count": (ctypes.c_int64, []),
+    "evap_fma_probe": (_c_int, [_c_int, ctypes.POINTER(_c_dbl), _vp]),
 }
 
 DEFAULT_PARAMS = dict(rho_l=1000.0, rho_g=1.0, mu_l=1e-3, mu_g=1e-5, eps=None, dt=1e-4, c_mass=None, theta=0.5,
@@ -111,6 +112,13 @@ class EvapError(RuntimeError):
         msg = lib().evap_last_error().decode()
         super().__init__(f"{where}: {STATUS.get(status, status)}: {msg}")
         self.status = status
+
+
+def fma_probe(prec: int = 64) -> float:
+    """Measured FMA throughput (TFLOP/s) of the current device in FP64 (prec 64) or FP32 (prec 32)."""
+    t = ctypes.c_double()
+    _check(lib().evap_fma_probe(int(prec), ctypes.byref(t), _stream()), "evap_fma_probe")
+    return t.value
 
 
 def launch_count() -> int:
