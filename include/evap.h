@@ -242,30 +242,36 @@ int evap_apply_saddle(evap_handle h, const double* x, const double* p, double* y
 int evap_solve_saddle(evap_handle h, const double* f, double* x, double* p, int restart, double rtol, int max_iter,
                       int* iters, double* relres, void* stream);
 
-/* One time step of the coupled problem (the Navier-Stokes step, then Algorithm 2), for meshes created with
- * newton = 0 (one Picard linearization per step) and at least one open face:
- *   1. [A(u^n), -B^T; B, 0] [u^(n+1); p^(n+1)] = [f; g], f_(i,c) = sum_q W N_i rho (c_m u*_c + gravity_c), with the
- *      Dirichlet data of u^n (the velocity on the Dirichlet faces keeps its value of u^n: walls at rest where it is 0,
- *      an inflow where it is not; lifted as in evap_solve_saddle, also in the nonlinear residual): BDF1
- *      (u_prev NULL: c_m = 1/dt, u* = u^n) or BDF2 (u_prev = u^(n-1): c_m = 3/(2 dt), u* = (4 u^n - u^(n-1)) / 3);
- *      the mesh's c_mass is replaced by the scheme's for the step.  Picard iterations: A is linearized about the
- *      latest iterate u^(k) (u^(0) = u^n), at most picard_iters solves by evap_solve_saddle (restart 30, ns_rtol, at
- *      most 2000 applications each, from the latest iterate), stopping before a solve once the nonlinear residual
- *      |[f; g] - K(u^(k)) [u^(k); p^(k)]| is <= picard_atol (the paper's Navier-Stokes nonlinear tolerance is 1e-10);
- *      picard_iters = 1 gives the semi-implicit step; with alpha != 0 (surface tension coefficient) f also carries
- *      the force of evap_surface_tension with the projected normal and regularized curvature of phi^n;
+/* One time step of the coupled problem (the Navier-Stokes step, then Algorithm 2), for meshes with at least one open
+ * face:
+ *   1. the nonlinear velocity-pressure system [A(u), -B^T; B, 0] [u; p] = [f; g], A(u) the Picard operator (the
+ *      momentum operator linearized about u without the Newton term), f_(i,c) = sum_q W N_i rho (c_m u*_c +
+ *      gravity_c), with the Dirichlet data of u^n (the velocity on the Dirichlet faces keeps its value of u^n: walls
+ *      at rest where it is 0, an inflow where it is not; lifted as in evap_solve_saddle, also in the nonlinear
+ *      residual): BDF1 (u_prev NULL: c_m = 1/dt, u* = u^n) or BDF2 (u_prev = u^(n-1): c_m = 3/(2 dt),
+ *      u* = (4 u^n - u^(n-1)) / 3); the mesh's c_mass is replaced by the scheme's for the step.  Nonlinear
+ *      iterations from u^(0) = u^n, at most picard_iters of them, stopping before an iteration k >= 1 once the
+ *      nonlinear residual R^(k) = [f; g] - K(u^(k)) [u^(k); p^(k)] has |R^(k)| <= picard_atol (the paper's
+ *      Navier-Stokes nonlinear tolerance is 1e-10); each solve by evap_solve_saddle (restart 30, ns_rtol, at most 2000
+ *      applications):
+ *        mesh newton = 0, Picard: solve K(u^(k)) [u^(k+1); p^(k+1)] = [f; g] from the latest iterate; picard_iters = 1
+ *          gives the semi-implicit step;
+ *        mesh newton = 1, Newton (App. D): solve J(u^(k)) [du; dp] = R^(k) from zero with the Jacobian J, the operator
+ *          with the Newton term (x . grad) u^(k), and add the correction (zero Dirichlet data);
+ *      with alpha != 0 (surface tension coefficient) f also carries the force of evap_surface_tension with the
+ *      projected normal and regularized curvature of phi^n;
  *   2. the advection fixed point (evap_advect_levelset, fp_iters passes, tol 0) with the transport velocity of
  *      u^(n+1), the result clamped to [-1, 1]; its projected normal; reinit_steps reinitialization steps with that
  *      normal frozen (evap_reinitialize), starting from the clamped field.
  * phi [N_phi], u [3 N_u], p [N_phi]: device arrays holding the state at t^n on entry and at t^(n+1) on exit;
  * mdot [N_phi] device; gravity: host double[3] or NULL (no body force).  ns_iters / ns_relres (host, may be NULL):
  * operator applications of all velocity-pressure solves and the relative residual of the last; picard_res (host,
- * may be NULL): the last nonlinear residual evaluated (-1 if none, i.e. picard_iters = 1).  The call sets the fields from its
- * inputs first (as evap_set_fields) and leaves the mesh without fields afterwards (call evap_set_fields before the
- * next apply), with the unit-normal reinitialization operators restored.  Synchronizes the stream.  EVAP_EINVAL on
- * a Newton mesh, dt <= 0, a closed box, alpha != 0 with rho_l == rho_g, picard_iters < 1, picard_atol < 0,
- * fp_iters < 1, reinit_steps < 0 or ns_rtol <= 0; EVAP_ENOTCONV if a
- * sub-solve missed its tolerance (the step is still completed). */
+ * may be NULL): the last nonlinear residual evaluated (-1 if none, i.e. picard_iters = 1).  The call sets the fields
+ * from its inputs first (as evap_set_fields) and leaves the mesh without fields afterwards (call evap_set_fields
+ * before the next apply), with the unit-normal reinitialization operators restored.  Synchronizes the stream.
+ * EVAP_EINVAL on dt <= 0, a closed box, alpha != 0 with rho_l == rho_g, picard_iters < 1, picard_atol < 0,
+ * fp_iters < 1, reinit_steps < 0 or ns_rtol <= 0; EVAP_ENOTCONV if a sub-solve missed its tolerance (the step is still
+ * completed). */
 int evap_time_step(evap_handle h, double* phi, double* u, double* p, const double* mdot, const double* u_prev,
                    const double* gravity, double alpha, int picard_iters, double picard_atol, int fp_iters,
                    int reinit_steps, double ns_rtol, int* ns_iters, double* ns_relres, double* picard_res,

@@ -61,12 +61,14 @@ def continuity_rhs(pb: momentum.Problem) -> np.ndarray:
     return momentum.divergence(pb)[1]
 
 
-def solve(pb: momentum.Problem, f: np.ndarray):
+def solve(pb: momentum.Problem, f: np.ndarray, g=None):
     """Direct solve of K_D [x; p] = [f; g] (`lifted_matrix`: x = f on the constrained DoFs, lifted into the free
-    rows); returns (x, p).  Needs an open face (else K is singular)."""
+    rows; g the continuity right-hand side of the fields unless given); returns (x, p).  Needs an open face (else K
+    is singular)."""
     if int(pb.params.get("dirichlet_faces", 0x3F)) & 0x3F == 0x3F:
         raise ValueError("the saddle-point system needs at least one open face")
-    K, g = lifted_matrix(pb)
+    K, g_fields = lifted_matrix(pb)
+    g = g_fields if g is None else g
     nu3 = 3 * pb.mesh.n_u
     sol = spla.spsolve(K.tocsc(), np.concatenate([f, g]))
     return sol[:nu3], sol[nu3:]

@@ -3,10 +3,13 @@
 Algorithm 1 of the paper alternates the level-set solver (Algorithm 2) and the Navier-Stokes solver; the step here
 takes them in the order velocity first, then level set, each once:
 
-  1. Navier-Stokes with Picard iterations (Eq. weakNavierStokes; App. D iterates Newton): the operator is linearized
-     about the latest iterate u^(k) (u^(0) = u^n), at most `picard_iters` solves, stopping before a solve once the
-     nonlinear residual |[f; g] - K(u^(k)) [u^(k); p^(k)]| is <= picard_atol (the table's 1e-10 for the Navier-Stokes
-     nonlinear solver); with picard_iters = 1 the step is semi-implicit. The time discretization is
+  1. Navier-Stokes with Picard iterations (params newton = 0) or Newton's method (newton = 1, App. D: "consistently
+     linearized ... full Newton"): the Picard operator K(u^(k)) is linearized about the latest iterate u^(k)
+     (u^(0) = u^n) and gives the nonlinear residual R^(k) = [f; g] - K(u^(k)) [u^(k); p^(k)]; a Picard iteration solves
+     K(u^(k)) [u^(k+1); p^(k+1)] = [f; g], a Newton iteration solves J(u^(k)) [du; dp] = R^(k) with the Jacobian J,
+     the operator with the Newton term (x . grad) u^(k), and adds the correction.  At most `picard_iters` iterations,
+     stopping before an iteration k >= 1 once |R^(k)| <= picard_atol (the table's 1e-10 for the Navier-Stokes
+     nonlinear solver); with picard_iters = 1 the Picard step is semi-implicit. The time discretization is
      BDF1 (c_m = 1/dt, u* = u^n) or, given u^(n-1), BDF2 (c_m = 3/(2 dt), u* = (4 u^n - u^(n-1)) / 3); with A the
      momentum operator of oracle.momentum for u0 = u^(k), newton = 0 and that c_m (A u = rho c_m u + rho (u^(k) .
      grad) u + viscous(u)),
@@ -48,8 +51,8 @@ def time_step(mesh_u: fe.Mesh, params: dict, phi: np.ndarray, u: np.ndarray, p: 
               fp_iters: int = 2, reinit_steps: int = 2, gvec=(0.0, 0.0, 0.0), u_prev=None, picard_iters: int = 1,
               picard_atol: float = 0.0, residuals=None, alpha: float = 0.0):
     prm = dict(params)
-    if int(prm.get("newton", 1)) != 0:
-        raise ValueError("the step takes one Picard linearization: newton = 0")
+    newton = int(prm.get("newton", 1)) != 0
+    prm["newton"] = 0  # the Picard operator: residuals, and the Picard iterations' solves
     prm["c_mass"] = (1.0 if u_prev is None else 1.5) / prm["dt"]
     ustar = np.array(u, dtype=float) if u_prev is None else (4.0 * np.asarray(u) - np.asarray(u_prev)) / 3.0
     pb = momentum.Problem(mesh=mesh_u, params=prm, phi=np.clip(phi, -1.0, 1.0), u0=np.array(u, dtype=float),
@@ -64,16 +67,26 @@ def time_step(mesh_u: fe.Mesh, params: dict, phi: np.ndarray, u: np.ndarray, p: 
     mask = pb.constrained()
     f[mask] = np.asarray(u, dtype=float)[mask]  # Dirichlet data: the boundary values of u^n
     u1, p1 = np.array(u, dtype=float), np.array(p, dtype=float)
+    nu3 = 3 * mesh_u.n_u
     for it in range(picard_iters):
         pb.u0 = u1
-        if it > 0:
+        if it > 0 or newton:
             K, g = saddle.lifted_matrix(pb)
-            res = float(np.linalg.norm(np.concatenate([f, g]) - K @ np.concatenate([u1, p1])))
-            if residuals is not None:
-                residuals.append(res)
-            if res <= picard_atol:
-                break
-        u1, p1 = saddle.solve(pb, f)
+            rvec = np.concatenate([f, g]) - K @ np.concatenate([u1, p1])
+            res = float(np.linalg.norm(rvec))
+            if it > 0:
+                if residuals is not None:
+                    residuals.append(res)
+                if res <= picard_atol:
+                    break
+        if newton:
+            # Newton: the Jacobian of the residual is the operator with the (x . grad) u^(k) term (App. D); the
+            # correction has zero Dirichlet data (u^(k) already carries the boundary values)
+            pn = momentum.Problem(mesh=mesh_u, params=dict(prm, newton=1), phi=pb.phi, u0=u1, mdot=pb.mdot)
+            du, dp = saddle.solve(pn, rvec[:nu3], g=rvec[nu3:])
+            u1, p1 = u1 + du, p1 + dp
+        else:
+            u1, p1 = saddle.solve(pb, f)
     adv, _ = geometry.advect_levelset(mesh_u, np.clip(phi, -1.0, 1.0), u1, mdot, prm, fp_iters)
     adv = np.clip(adv, -1.0, 1.0)
     n = geometry.projected_normal(mesh1, adv, prm.get("eta_n", 2.0))

@@ -283,8 +283,9 @@ class Operator:
                   fp_iters: int = 2, reinit_steps: int = 2, ns_rtol: float = 1e-8, u_prev=None,
                   picard_iters: int = 1, picard_atol: float = 1e-10, alpha: float = 0.0,
                   raise_on_notconv: bool = False):
-        """One coupled step (Picard velocity-pressure solve, BDF1, or BDF2 given u_prev = u^(n-1); then Algorithm 2)
-        from (phi, u, p) at t^n; returns new tensors (phi, u, p) at t^(n+1) and info."""
+        """One coupled step (velocity-pressure solve with Picard iterations, or Newton iterations on a mesh created
+        with newton = 1; BDF1, or BDF2 given u_prev = u^(n-1); then Algorithm 2) from (phi, u, p) at t^n; returns new
+        tensors (phi, u, p) at t^(n+1) and info (picard_res: the last nonlinear residual)."""
         phi = self._dev(phi, self.n_phi, torch.float64, "phi").clone()
         u = self._dev(u, 3 * self.n_u, torch.float64, "u").clone()
         p = self._dev(p, self.n_phi, torch.float64, "p").clone()

@@ -150,7 +150,7 @@ static int check_inputs(evap_mesh* h, const char* who, cudaStream_t s, std::init
 
 static void free_all(evap_mesh* h) {
     void* ptrs[] = {h->phi, h->u, h->mdot, h->u32, h->phi32, h->cell_code, h->table_index, h->table_count,
-                    h->table, h->table32, h->qc, h->qc32, h->ugamma, h->ugamma32, h->cpp_flags, h->flag_count, h->band_list,
+                    h->table, h->table32, h->qc, h->qcdf, h->qc32, h->ugamma, h->ugamma32, h->cpp_flags, h->flag_count, h->band_list,
                     h->band_count, h->band_y, h->cpp_evals, h->ls_normal_store, h->ls_normal32_store, h->geo_ws, h->geo_elem, h->diag,
                     h->diag32, h->ws, h->red, h->cont_rhs, h->sd_ws, h->sd_red, h->nonfinite, h->step_ws,
                     h->tp_fac, h->tp_sigma, h->tp_sigma64};
@@ -446,7 +446,6 @@ int evap_time_step(evap_handle h, double* phi, double* u, double* p, const doubl
                    int reinit_steps, double ns_rtol, int* ns_iters, double* ns_relres, double* picard_res,
                    void* stream) {
     if (!h || !phi || !u || !p || !mdot) return fail(EVAP_EINVAL, "evap_time_step: null argument");
-    if (h->m.newton != 0) return fail(EVAP_EINVAL, "evap_time_step: the step takes a Picard linearization (newton = 0)");
     if (!(h->m.dt > 0.0)) return fail(EVAP_EINVAL, "evap_time_step: dt must be > 0");
     if ((h->m.faces & 0x3Fu) == 0x3Fu)
         return fail(EVAP_EINVAL, "evap_time_step: every face is Dirichlet (the pressure level is undetermined)");

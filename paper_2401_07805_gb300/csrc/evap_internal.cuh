@@ -80,6 +80,9 @@ struct evap_mesh {
     float* table32 = nullptr;
     // quadrature-point coefficients of the FP64 momentum operator, all cells [ncell][QC_K][nq]
     double* qc = nullptr;
+    // the same coefficients as double-float pairs (hi, lo) [ncell][QC_K][nq] for the double-float FP64 apply
+    float* qcdf = nullptr;
+    int64_t qcdf_len = 0;  // floats
     // FP32 copy of the u0 coefficients (slots 1..12 of qc) in the 32-cell block layout of the FP32 apply
     float* qc32 = nullptr;
     int64_t qc32_len = 0;
@@ -165,6 +168,9 @@ MeshArgs<T> mesh_args(const evap_mesh* h);
 int launch_setup_coefficients(evap_mesh* h, cudaStream_t s);
 int launch_qp_coeffs(evap_mesh* h, cudaStream_t s);
 int launch_momentum32(evap_mesh* h, const float* x, float* y, float* yp, cudaStream_t s);
+// the FP64-accurate apply in double-float arithmetic (momentum_df.cu), after the init kernel; m carries the faces
+int launch_momentum_df(evap_mesh* h, const MeshArgs<double>& m, const double* x, double* y, double* yp,
+                       const double* p, cudaStream_t s);
 // u_Gamma of the mesh's level set, or of `phi` (a clamped Q1 field) when given, into h->ugamma / h->ugamma32.
 int launch_transport_velocity(evap_mesh* h, cudaStream_t s, const double* phi = nullptr);
 // the points of the last transport-velocity pass, y [3 N_phi] physical coordinates (evap_get_closest_points)
@@ -238,9 +244,10 @@ int solve_gmres(evap_mesh* h, const double* f, double* x, int mixed, int restart
 // stops at |r| <= max(rtol |b|, atol).  *iters is incremented by the operator applications; *relres = |r| / |b|.
 int solve_advect_gmres(evap_mesh* h, const double* b, const double* diag, double* x, int restart, double rtol,
                        double atol, int max_iter, int* iters, double* relres, cudaStream_t s);
-// Flexible GMRES on the velocity-pressure system K [x; p] = [f; g] (see evap_solve_saddle).
+// Flexible GMRES on the velocity-pressure system K [x; p] = [f; g] (see evap_solve_saddle); g is the continuity
+// right-hand side of the fields unless g_rhs is given.
 int solve_saddle(evap_mesh* h, const double* f, double* x, double* p, int restart, double rtol, int max_iter,
-                 int* iters, double* relres, cudaStream_t s);
+                 int* iters, double* relres, cudaStream_t s, const double* g_rhs = nullptr);
 
 // small vector kernels used by several files
 template <typename T>

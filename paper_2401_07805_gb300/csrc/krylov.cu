@@ -819,11 +819,12 @@ static int saddle_precond(Ctx& inner, SaddleSpace& sp, const double* v, double* 
 }
 
 int solve_saddle(evap_mesh* h, const double* f, double* x, double* p, int m, double rtol, int max_iter, int* iters,
-                 double* relres, cudaStream_t s) {
+                 double* relres, cudaStream_t s, const double* g_rhs) {
     int rc = launch_diagonal(h, s);
     if (rc) return rc;
     const double* g = nullptr;
     if ((rc = continuity_rhs(h, &g, s))) return rc;
+    if (g_rhs) g = g_rhs;
     double* sdiag = nullptr;
     if ((rc = geo_schur_setup(h, &sdiag, s))) return rc;
     const int64_t Nu3 = 3 * h->m.Nu, Np = h->m.Nphi, N = Nu3 + Np;

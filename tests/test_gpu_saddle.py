@@ -114,8 +114,9 @@ def test_saddle_solve_evaporating_slab_outflow():
     mdot = 0.5
     wl.mdot = np.full(N1, mdot)
     op, pb = make(wl)
-    # |[f; g]| = |g| is small against the rounding of the inertia rows (rho c_m h^3 |x|): 1e-10 is reachable, 1e-12 not
-    x, _, info = op.solve_saddle(cuda(np.zeros(3 * op.n_u)), rtol=1e-10, max_iter=2000)
+    # |[f; g]| = |g| is small against the rounding of the inertia rows (rho c_m h^3 |x|): the double-float apply rounds
+    # at ~4e-15 of their scale, which puts the attainable relative residual near 2e-10 here; 1e-9 is reachable
+    x, _, info = op.solve_saddle(cuda(np.zeros(3 * op.n_u)), rtol=1e-9, max_iter=2000)
     assert info["converged"], info
     out = saddle.top_outflow(pb.mesh, host(x))
     g = saddle.continuity_rhs(pb)
