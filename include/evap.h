@@ -16,9 +16,12 @@
  *     iterative refinement.
  *
  * Conventions shared by every entry point
- *   Mesh:     n cells per axis, h = L / n.  Velocity (Q_p) nodes: M = p n + 1 per axis, N_u = M^3; level-set /
- *             mass-flux / pressure-space (Q1) nodes: N_phi = (n + 1)^3.  Node index i + M (j + M k), i fastest
- *             (x), then y, then z.  Inside a cell the Q_p nodes sit at the Gauss-Lobatto points of [0, 1].
+ *   Mesh:     n cells per axis, h = L / n.  Velocity (Q_p) nodes: M = p n + 1 per axis, N_u = M^3; pressure-space
+ *             (Q1) nodes: N_p = (n + 1)^3; level-set / mass-flux (Q1) nodes on the level-set mesh (the velocity
+ *             mesh subdivided n_sub times, cell size h / n_sub): N_phi = (n_sub n + 1)^3 (N_phi = N_p for n_sub = 1).
+ *             Node index i + M (j + M k), i fastest (x), then y, then z.  Inside a cell the Q_p nodes sit at the
+ *             Gauss-Lobatto points of [0, 1].  At a velocity quadrature point the level set is the Q1 interpolant of
+ *             the level-set cell containing it (a point on a sub-cell face takes the upper sub-cell).
  *   Vectors:  component-major: v[c * N + node] for c = 0, 1, 2 (x, y, z components).
  *   Pointers: every array argument is a DEVICE pointer owned by the caller (e.g. a contiguous torch CUDA
  *             tensor).  The library keeps no reference to caller arrays after a call returns on the host:
@@ -80,6 +83,9 @@ typedef struct {
     int cpp_kmax;          /* closest-point outer iteration cap (App. C) */
     double eta_n;          /* normal filter constant, Eq. (normal_vector_regularized): radius eta_n h^2 (default 2) */
     double eta_kappa;      /* curvature filter constant, Eq. (curvature_regularized) (default 2) */
+    int n_sub;             /* level-set mesh: the velocity mesh subdivided n_sub times per direction (Sec. 2.5; 1 or 2,
+                              0 reads as 1): the level set and the mass flux are Q1 on it, N_phi = (n_sub n + 1)^3
+                              nodes; the pressure stays Q1 on the velocity mesh, N_p = (n + 1)^3 nodes */
 } evap_params;
 
 /* Create the mesh/operator object.  n_cells >= 1, degree_u in {2, 3}, L > 0, prm not NULL with rho_l, rho_g,
@@ -90,8 +96,11 @@ int evap_create_mesh(int n_cells, int degree_u, double L, const evap_params* prm
 /* Release all device memory of the handle (synchronizes the device). NULL is accepted and ignored. */
 int evap_destroy(evap_handle h);
 
-/* Number of Q_p velocity nodes (N_u; a velocity vector has 3 N_u entries) and of Q1 nodes (N_phi). */
+/* Number of Q_p velocity nodes (N_u; a velocity vector has 3 N_u entries) and of level-set nodes (N_phi). */
 int evap_sizes(evap_handle h, int64_t* n_u, int64_t* n_phi);
+
+/* Number of Q1 pressure nodes N_p (the space of the divergence row y_p, the pressure p and w_p). */
+int evap_pressure_size(evap_handle h, int64_t* n_p);
 
 /* Input checks (off by default): with on != 0 every later call first counts the NaN and Inf entries of its input
  * arrays (the fields of evap_set_fields, x / f / p / w / n / kappa / psi of the applies and solves) by one device
@@ -135,7 +144,7 @@ int evap_transport_stats(evap_handle h, int64_t* band_nodes, int64_t* evaluation
 /* Momentum apply y = A x (velocity block of Eq. weakNavierStokes linearized about u, App. D):
  *   y_(i,c) = sum_q W_q [ N_i rho (c_mass x_c + (u . grad) x_c + newton (x . grad) u_c) + grad N_i . 2 mu eps_mod(x)_c ]
  * on unconstrained DoFs; on Dirichlet DoFs y = x and x does not enter other rows.  If y_p is not NULL the
- * divergence row y_p [N_phi] = sum_q W_q N^1_j (div x - v_dil) is written too (same precision), with the dilation rate
+ * divergence row y_p [N_p] = sum_q W_q N^1_j (div x - v_dil) is written too (same precision), with the dilation rate
  * v_dil = mdot (1/rho_g - 1/rho_l) delta (Eq. evaporDil with the sign of the paper's 1D solution, App. A
  * Eq. stefan_diffuse_velocity: evaporation, mdot > 0, expands the volume; the printed Eq. evaporDil has the bracket
  * reversed).
@@ -197,7 +206,7 @@ int evap_surface_tension(evap_handle h, const double* n, const double* kappa, do
 /* Adjoint of the momentum apply for L = w . A(phi, mdot, u) x + w_p . (B x - g(phi, mdot)):
  *   g_x = A^T w + B^T w_p,  g_u0 = dL/du [3 N_u],  g_phi = dL/dphi [N_phi],  g_mdot = dL/dmdot [N_phi],
  * with the quadrature-point coefficients of evap_set_fields and the material-law derivatives recomputed at the
- * points of the interface zone.  w [3 N_u] and x [3 N_u] required; w_p may be
+ * points of the interface zone.  w [3 N_u] and x [3 N_u] required; w_p [N_p] may be
  * NULL (no divergence row); any g_* may be NULL (not computed).  FP64 only. */
 int evap_apply_adjoint(evap_handle h, const double* w, const double* w_p, const double* x, double* g_x,
                        double* g_u0, double* g_phi, double* g_mdot, void* stream);
@@ -216,10 +225,10 @@ int evap_solve(evap_handle h, const double* f, double* x, int mixed, int restart
 
 /* Velocity-pressure system of Eq. (weakNavierStokes) with the Q1 pressure (Sec. 2.5, k_p = 1):
  *   y   = A x - B^T p   [3 N_u]  (the pressure term -(div v, p); Dirichlet-constrained rows: y = x)
- *   y_p = B x           [N_phi]  (the divergence row without its source: the continuity equation is B x = g with
+ *   y_p = B x           [N_p]    (the divergence row without its source: the continuity equation is B x = g with
  *                                 g_j = sum_q W N1_j v_dil, Eq. continuity with the dilation rate of Eq. evaporDil)
  * A the momentum operator of evap_apply_momentum, B its divergence row (Dirichlet entries of x read as 0).
- * x [3 N_u], p [N_phi], y, y_p device arrays, FP64; x and y must not alias.  Faces that are not Dirichlet
+ * x [3 N_u], p [N_p], y, y_p device arrays, FP64; x and y must not alias.  Faces that are not Dirichlet
  * (dirichlet_faces) are open: the weak form's natural condition (zero traction) holds there. */
 int evap_apply_saddle(evap_handle h, const double* x, const double* p, double* y, double* y_p, void* stream);
 
@@ -263,7 +272,7 @@ int evap_solve_saddle(evap_handle h, const double* f, double* x, double* p, int 
  *   2. the advection fixed point (evap_advect_levelset, fp_iters passes, tol 0) with the transport velocity of
  *      u^(n+1), the result clamped to [-1, 1]; its projected normal; reinit_steps reinitialization steps with that
  *      normal frozen (evap_reinitialize), starting from the clamped field.
- * phi [N_phi], u [3 N_u], p [N_phi]: device arrays holding the state at t^n on entry and at t^(n+1) on exit;
+ * phi [N_phi], u [3 N_u], p [N_p]: device arrays holding the state at t^n on entry and at t^(n+1) on exit;
  * mdot [N_phi] device; gravity: host double[3] or NULL (no body force).  ns_iters / ns_relres (host, may be NULL):
  * operator applications of all velocity-pressure solves and the relative residual of the last; picard_res (host,
  * may be NULL): the last nonlinear residual evaluated (-1 if none, i.e. picard_iters = 1).  The call sets the fields

@@ -54,6 +54,7 @@ def param_gradients(pb: momentum.Problem, x, w, w_p=None):
     for sl in momentum._chunks(len(cells)):
         q = momentum.qp_fields(pb, cells[sl])
         W, bu, b1, du, d1 = q["W"], q["bu"], q["b1"], q["du"], q["d1"]
+        bl, dl = q["bl"], q["dl"]  # level-set space (phi, mdot); b1, d1: pressure space (w_p)
         X = np.einsum("nci,iq->nqc", np.stack([xt[c][du] for c in range(3)], 1), bu.N)
         G = np.einsum("nci,biq->nqcb", np.stack([xt[c][du] for c in range(3)], 1), bu.G)
         Om = np.einsum("nci,iq->nqc", np.stack([wt[c][du] for c in range(3)], 1), bu.N)
@@ -98,7 +99,7 @@ def param_gradients(pb: momentum.Problem, x, w, w_p=None):
             mq = q["mdot"]
             dL_dphi = dL_dphi + dL_dv * mq * k_dil * (d2H * dd * dd + dH * d2d) * gnorm
             dL_dg = dL_dg + (dL_dv * mq * k_dil * dH * dd)[..., None] * n
-        gp = np.einsum("jq,nq->nj", b1.N, dL_dphi) + np.einsum("bjq,nqb->nj", b1.G, dL_dg)
-        np.add.at(g_phi, d1.ravel(), gp.ravel())
-        np.add.at(g_mdot, d1.ravel(), np.einsum("jq,nq->nj", b1.N, dL_dm).ravel())
+        gp = np.einsum("jq,nq->nj", bl.N, dL_dphi) + np.einsum("bjq,nqb->nj", bl.G, dL_dg)
+        np.add.at(g_phi, dl.ravel(), gp.ravel())
+        np.add.at(g_mdot, dl.ravel(), np.einsum("jq,nq->nj", bl.N, dL_dm).ravel())
     return g_u0.ravel(), g_phi, g_mdot

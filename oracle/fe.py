@@ -71,6 +71,37 @@ def tensor_basis(p: int, pts: np.ndarray, h: float) -> TensorBasis:
     return TensorBasis(p=p, N=N, G=np.stack([Gx, Gy, Gz]))
 
 
+def iso_q1_1d(x: np.ndarray, n_sub: int) -> tuple[np.ndarray, np.ndarray]:
+    """V[a, q], D[a, q] (reference derivative) of the n_sub + 1 piecewise-linear hat functions of [0, 1] subdivided
+    n_sub times (nodes a / n_sub) at the points x.  A point lies in the sub-interval floor(n_sub x), clamped to
+    n_sub - 1: on an interior node it takes the upper sub-interval's slopes.  For n_sub = 1 these are the Q1 shape
+    functions 1 - x, x."""
+    x = np.asarray(x, dtype=float)
+    V = np.zeros((n_sub + 1, x.size))
+    D = np.zeros((n_sub + 1, x.size))
+    k = np.clip(np.floor(n_sub * x).astype(int), 0, n_sub - 1)
+    xi = n_sub * x - k
+    for q in range(x.size):
+        V[k[q], q] += 1.0 - xi[q]
+        V[k[q] + 1, q] += xi[q]
+        D[k[q], q] -= n_sub
+        D[k[q] + 1, q] += n_sub
+    return V, D
+
+
+def levelset_basis(n_sub: int, pts: np.ndarray, h: float) -> TensorBasis:
+    """Level-set shape functions on one velocity cell of size h at the tensor points (reference coords ``pts``): Q1
+    on each of the n_sub^3 sub-cells of the cell (the level-set mesh subdivided n_sub times per direction, Sec. 2.5),
+    (n_sub + 1)^3 local nodes, local index a + (n_sub + 1)(b + (n_sub + 1)c); n_sub = 1 is the Q1 basis."""
+    V, D = iso_q1_1d(pts, n_sub)
+    m, nq = V.shape
+    N = np.einsum("ax,by,cz->cbazyx", V, V, V).reshape(m ** 3, nq ** 3)
+    Gx = np.einsum("ax,by,cz->cbazyx", D, V, V).reshape(m ** 3, nq ** 3) / h
+    Gy = np.einsum("ax,by,cz->cbazyx", V, D, V).reshape(m ** 3, nq ** 3) / h
+    Gz = np.einsum("ax,by,cz->cbazyx", V, V, D).reshape(m ** 3, nq ** 3) / h
+    return TensorBasis(p=1, N=N, G=np.stack([Gx, Gy, Gz]))
+
+
 def tensor_weights(w1: np.ndarray, h: float) -> np.ndarray:
     """W_q = w_x w_y w_z h^3 for q = qx + nq (qy + nq qz)."""
     return np.einsum("x,y,z->zyx", w1, w1, w1).ravel() * h ** 3
@@ -84,11 +115,13 @@ def tensor_points(t1: np.ndarray) -> np.ndarray:
 
 @dataclass
 class Mesh:
-    """Uniform n^3 hex mesh of [0, L]^3 with Q_p velocity nodes and Q1 level-set nodes."""
+    """Uniform n^3 hex mesh of [0, L]^3 with Q_p velocity nodes, Q1 pressure nodes, and Q1 level-set nodes on the mesh
+    subdivided n_sub times per direction (Sec. 2.5; n_sub = 1: the level set shares the pressure nodes)."""
 
     n: int
     p: int
     L: float
+    n_sub: int = 1
 
     @property
     def h(self) -> float:
@@ -103,7 +136,11 @@ class Mesh:
         return self.m ** 3
 
     @property
-    def n_phi(self) -> int:
+    def n_phi(self) -> int:  # level-set (and mass-flux) nodes
+        return (self.n_sub * self.n + 1) ** 3
+
+    @property
+    def n_p(self) -> int:  # pressure nodes (Q1 on the velocity mesh)
         return (self.n + 1) ** 3
 
     def cells(self) -> np.ndarray:
@@ -124,14 +161,24 @@ class Mesh:
         gz = p * cells[:, 2:3] + C[None]
         return gx + m * (gy + m * gz)
 
-    def dofs_phi(self, cells: np.ndarray | None = None) -> np.ndarray:
-        """(ncell, 8) global Q1 node indices of each cell."""
+    def dofs_p(self, cells: np.ndarray | None = None) -> np.ndarray:
+        """(ncell, 8) global Q1 pressure node indices of each cell."""
         cells = self.cells() if cells is None else cells
         m1 = self.n + 1
         r = np.arange(2)
         C, B, A = np.meshgrid(r, r, r, indexing="ij")
         A, B, C = A.ravel(), B.ravel(), C.ravel()
         return (cells[:, 0:1] + A[None]) + m1 * ((cells[:, 1:2] + B[None]) + m1 * (cells[:, 2:3] + C[None]))
+
+    def dofs_phi(self, cells: np.ndarray | None = None) -> np.ndarray:
+        """(ncell, (n_sub+1)^3) global level-set node indices of each cell (local order a + (n_sub+1)(b + ...));
+        for n_sub = 1 the 8 Q1 nodes (the pressure nodes)."""
+        cells = self.cells() if cells is None else cells
+        k, ml = self.n_sub, self.n_sub * self.n + 1
+        r = np.arange(k + 1)
+        C, B, A = np.meshgrid(r, r, r, indexing="ij")
+        A, B, C = A.ravel(), B.ravel(), C.ravel()
+        return (k * cells[:, 0:1] + A[None]) + ml * ((k * cells[:, 1:2] + B[None]) + ml * (k * cells[:, 2:3] + C[None]))
 
     def dirichlet_nodes(self, faces: int) -> np.ndarray:
         """Boolean [n_u] mask of Q_p nodes on the selected faces; bit 2*axis is the face x_axis = 0, bit 2*axis+1

@@ -160,7 +160,7 @@ def advect_levelset(mesh_u: fe.Mesh, phi_n: np.ndarray, u0: np.ndarray, mdot: np
     phi^(k) is clamped to [-1, 1] before the transport velocity (as the fields of set_fields are).  Returns
     (phi^(fp_iters), [|phi^(k+1) - phi^(k)|_2 for each k])."""
     from . import transport
-    mesh1 = fe.Mesh(mesh_u.n, 1, mesh_u.L)
+    mesh1 = fe.Mesh(mesh_u.n * mesh_u.n_sub, 1, mesh_u.L)  # the level-set mesh
     phi_k = np.array(phi_n, dtype=float)
     changes = []
     for _ in range(fp_iters):

@@ -43,7 +43,8 @@ class Problem:
     def from_workload(cls, wl, **over) -> "Problem":
         prm = dict(wl.params)
         prm.update(over)
-        return cls(mesh=fe.Mesh(wl.n, wl.p, wl.L), params=prm, phi=np.array(wl.phi, dtype=float),
+        return cls(mesh=fe.Mesh(wl.n, wl.p, wl.L, int(prm.get("n_sub", 1))), params=prm,
+                   phi=np.array(wl.phi, dtype=float),
                    u0=np.array(wl.u0, dtype=float), mdot=np.array(wl.mdot, dtype=float))
 
     def constrained(self) -> np.ndarray:
@@ -58,17 +59,22 @@ def velocity_rule(mesh: fe.Mesh):
 
 
 def qp_fields(pb: Problem, cells: np.ndarray):
-    """Coefficient fields at the velocity quadrature points of ``cells`` (arrays [ncell, nq, ...])."""
+    """Coefficient fields at the velocity quadrature points of ``cells`` (arrays [ncell, nq, ...]).
+
+    phi and mdot are interpolated from the level-set space (bl, dl: Q1 on the cell's n_sub^3 sub-cells, Sec. 2.5);
+    b1, d1 are the Q1 pressure-space shape functions and nodes (the divergence row's test functions)."""
     mesh, prm = pb.mesh, pb.params
     t, W = velocity_rule(mesh)
     bu = fe.tensor_basis(mesh.p, t, mesh.h)
     b1 = fe.tensor_basis(1, t, mesh.h)
+    bl = fe.levelset_basis(mesh.n_sub, t, mesh.h)
     du = mesh.dofs_u(cells)
-    d1 = mesh.dofs_phi(cells)
-    phin = pb.phi[d1]                                          # [nc, 8]
-    phi_q = phin @ b1.N                                        # [nc, nq]
-    gphi = np.einsum("nj,bjq->nqb", phin, b1.G)               # [nc, nq, 3]
-    mdot_q = pb.mdot[d1] @ b1.N
+    d1 = mesh.dofs_p(cells)
+    dl = mesh.dofs_phi(cells)
+    phin = pb.phi[dl]                                          # [nc, (n_sub+1)^3]
+    phi_q = phin @ bl.N                                        # [nc, nq]
+    gphi = np.einsum("nj,bjq->nqb", phin, bl.G)               # [nc, nq, 3]
+    mdot_q = pb.mdot[dl] @ bl.N
     u0 = pb.u0.reshape(3, -1)
     un = np.stack([u0[c][du] for c in range(3)], axis=1)      # [nc, 3, nloc]
     U = np.einsum("nci,iq->nqc", un, bu.N)                     # [nc, nq, 3]
@@ -84,8 +90,8 @@ def qp_fields(pb: Problem, cells: np.ndarray):
         z = np.ones_like(phi_q)
     else:
         z = zone.astype(float)
-    return dict(W=W, bu=bu, b1=b1, du=du, d1=d1, phi=phi_q, gphi=gphi, mdot=mdot_q, U=U, GU=GU, H=H, rho=rho,
-                mu=mu, n=n, z=z, vdil=vdil, zone=zone)
+    return dict(W=W, bu=bu, b1=b1, bl=bl, du=du, d1=d1, dl=dl, phi=phi_q, gphi=gphi, mdot=mdot_q, U=U, GU=GU, H=H,
+                rho=rho, mu=mu, n=n, z=z, vdil=vdil, zone=zone)
 
 
 def flux_jacobian(q: dict, prm: dict) -> np.ndarray:
@@ -173,7 +179,7 @@ def divergence(pb: Problem, remove_constrained: bool = True) -> tuple[sp.csr_mat
     cells = mesh.cells()
     Nu = mesh.n_u
     rows, cols, vals = [], [], []
-    g = np.zeros(mesh.n_phi)
+    g = np.zeros(mesh.n_p)
     for sl in _chunks(len(cells)):
         q = qp_fields(pb, cells[sl])
         W, bu, b1 = q["W"], q["bu"], q["b1"]
@@ -186,7 +192,7 @@ def divergence(pb: Problem, remove_constrained: bool = True) -> tuple[sp.csr_mat
         vals.append(np.broadcast_to(Be[None], (nc, 8, 3, nloc)).ravel())
         np.add.at(g, d1.ravel(), np.einsum("q,jq,nq->nj", W, b1.N, q["vdil"]).ravel())
     B = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
-                      shape=(mesh.n_phi, 3 * Nu)).tocsr()
+                      shape=(mesh.n_p, 3 * Nu)).tocsr()
     if not remove_constrained:
         return B, g
     keep = sp.diags((~pb.constrained()).astype(float))
@@ -242,12 +248,12 @@ def apply_rows(pb: Problem, x: np.ndarray, nodes: np.ndarray) -> np.ndarray:
 
 
 def divergence_rows(pb: Problem, x: np.ndarray, q1nodes: np.ndarray) -> np.ndarray:
-    """Rows y_p[j] = (B x - g)[j] of the given Q1 nodes, from the cells around them only."""
+    """Rows y_p[j] = (B x - g)[j] of the given Q1 pressure nodes, from the cells around them only."""
     mesh = pb.mesh
     Nu = mesh.n_u
     xt = np.where(pb.constrained(), 0.0, x)
     cells = cells_touching_nodes(mesh, q1nodes, 1)
-    yp = np.zeros(mesh.n_phi)
+    yp = np.zeros(mesh.n_p)
     for sl in _chunks(len(cells)):
         q = qp_fields(pb, cells[sl])
         W, bu, b1, du, d1 = q["W"], q["bu"], q["b1"], q["du"], q["d1"]

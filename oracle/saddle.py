@@ -82,12 +82,12 @@ def body_force_load(pb: momentum.Problem, gvec) -> np.ndarray:
     t, w = fe.gauss_rule(mesh.p + 1)
     W = fe.tensor_weights(w, mesh.h)
     bu = fe.tensor_basis(mesh.p, t, mesh.h)
-    b1 = fe.tensor_basis(1, t, mesh.h)
+    bl = fe.levelset_basis(mesh.n_sub, t, mesh.h)
     prm = pb.params
     for sl in momentum._chunks(len(cells)):
         c = cells[sl]
-        du, d1 = mesh.dofs_u(c), mesh.dofs_phi(c)
-        phi_q = pb.phi[d1] @ b1.N
+        du, dl = mesh.dofs_u(c), mesh.dofs_phi(c)
+        phi_q = pb.phi[dl] @ bl.N
         H = physics.heaviside_parts(phi_q, prm["eps"])[0]
         rho = physics.density(H, prm["rho_l"], prm["rho_g"], pb.rho_mode)
         fi = np.einsum("q,iq,nq->ni", W, bu.N, rho)                  # [nc, nloc]

@@ -58,7 +58,7 @@ def time_step(mesh_u: fe.Mesh, params: dict, phi: np.ndarray, u: np.ndarray, p: 
     pb = momentum.Problem(mesh=mesh_u, params=prm, phi=np.clip(phi, -1.0, 1.0), u0=np.array(u, dtype=float),
                           mdot=np.array(mdot, dtype=float))
     f = mass_load(pb, ustar, gvec)
-    mesh1 = fe.Mesh(mesh_u.n, 1, mesh_u.L)
+    mesh1 = fe.Mesh(mesh_u.n * mesh_u.n_sub, 1, mesh_u.L)  # the level-set mesh
     if alpha != 0.0:
         n0 = geometry.projected_normal(mesh1, pb.phi, prm.get("eta_n", 2.0))
         kappa = geometry.curvature(mesh1, n0, prm.get("eta_kappa", 2.0))

@@ -37,7 +37,7 @@ def surface_tension_rhs(pb: Problem, n_field: np.ndarray, kappa: np.ndarray, alp
     mesh, prm = pb.mesh, pb.params
     t, W = velocity_rule(mesh)
     bu = fe.tensor_basis(mesh.p, t, mesh.h)
-    b1 = fe.tensor_basis(1, t, mesh.h)
+    b1 = fe.levelset_basis(mesh.n_sub, t, mesh.h)  # kappa, n and phi live on the level-set space
     nf = np.asarray(n_field).reshape(3, -1)
     out = np.zeros((3, mesh.n_u))
     cells = mesh.cells()

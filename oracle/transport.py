@@ -26,9 +26,10 @@ Readings where App. C leaves details open (the same on the GPU):
     so this pins y to ~1e-6 cells; it ends the zigzag along creases of the piecewise-trilinear isocontour).
     A node is flagged as not converged when the first projection does not reach the isocontour (e.g. it does not
     exist inside a thin droplet) or after kmax outer iterations.
-  * positions are handled in cell units s = y / h and clamped to the domain [0, n]^3; point location takes
-    cell = clamp(floor(s), 0, n - 1) per axis; phi and grad phi are the trilinear Q1 interpolant of that cell,
-    u the Q_p interpolant; d(phi) uses phi clamped to |phi| <= 1 - 2^-40.
+  * positions are handled in cell units s = y / h of the level-set mesh (the velocity mesh subdivided n_sub times,
+    h = h_u / n_sub) and clamped to the domain [0, n]^3; point location takes cell = clamp(floor(s), 0, n - 1) per
+    axis; phi and grad phi are the trilinear Q1 interpolant of that cell, u the Q_p interpolant of the velocity cell
+    located the same way at s / n_sub; d(phi) uses phi clamped to |phi| <= 1 - 2^-40.
   * n(x) is the normalised gradient of the Q1 interpolant at the node (point-located as above), 0 where it is
     negligible (physics.has_normal).
 """
@@ -47,24 +48,27 @@ STALL = 1e-12  # an accepted step shortening |y - x| by less than this fraction 
 
 
 class PointEval:
-    """Point evaluation of the Q1 level set and the Q_p velocity on the uniform mesh (cell-unit coordinates)."""
+    """Point evaluation of the Q1 level set (on the level-set mesh: the velocity mesh subdivided n_sub times) and of
+    the Q_p velocity, at positions s in level-set cell units (s = x / h_ls, h_ls = h / n_sub)."""
 
     def __init__(self, mesh: fe.Mesh, phi: np.ndarray, u0: np.ndarray):
         self.mesh = mesh
         self.phi = phi
         self.u0 = u0.reshape(3, -1)
         self.nodes = fe.gauss_lobatto_points(mesh.p)
+        self.n_cells = mesh.n * mesh.n_sub  # level-set cells per axis
+        self.h = mesh.h / mesh.n_sub        # level-set cell size
 
-    def locate(self, s):
-        n = self.mesh.n
+    def locate(self, s, n=None):
+        n = self.n_cells if n is None else n
         k = [min(max(int(math.floor(s[a])), 0), n - 1) for a in range(3)]
         xi = [s[a] - k[a] for a in range(3)]
         return k, xi
 
     def phi_grad(self, s):
         (kx, ky, kz), (x, y, z) = self.locate(s)
-        m1 = self.mesh.n + 1
-        h = self.mesh.h
+        m1 = self.n_cells + 1
+        h = self.h
         val = 0.0
         g = [0.0, 0.0, 0.0]
         for c in range(2):
@@ -80,7 +84,7 @@ class PointEval:
         return val, np.array(g)
 
     def velocity(self, s):
-        (kx, ky, kz), xi = self.locate(s)
+        (kx, ky, kz), xi = self.locate(np.asarray(s, dtype=float) / self.mesh.n_sub, self.mesh.n)
         p, m = self.mesh.p, self.mesh.m
         Vs = [fe.lagrange_1d(self.nodes, np.array([xi[a]]))[0][:, 0] for a in range(3)]
         out = np.zeros(3)
@@ -100,9 +104,10 @@ def _unit(g):
 def project(ev: PointEval, y: np.ndarray, d_target: float, eps: float, tol: float, max_steps: int = 20):
     """Normal steps y <- y - (d(y) - d*) / |grad d(y)| n(y) (App. C), in cell units, clamped to the domain.
 
-    Returns (y, reached) with reached = |d(y) - d*| <= tol h at the returned point."""
-    n = ev.mesh.n
-    h = ev.mesh.h
+    Returns (y, reached) with reached = |d(y) - d*| <= tol h at the returned point (h, cell units: the level-set
+    mesh's)."""
+    n = ev.n_cells
+    h = ev.h
     y = y.copy()
     for _ in range(max_steps):
         ph, g = ev.phi_grad(y)
@@ -135,7 +140,7 @@ def tangential_part(ev: PointEval, sx: np.ndarray, y: np.ndarray) -> np.ndarray:
 
 def closest_point(ev: PointEval, sx: np.ndarray, d_target: float, eps: float, tol: float, kmax: int):
     """Closest point (cell units) of node position sx on the isocontour d(phi) = d_target; returns (y, converged)."""
-    n = float(ev.mesh.n)
+    n = float(ev.n_cells)
     y, on = project(ev, sx.astype(float), d_target, eps, tol)
     if not on:
         return y, False
@@ -167,7 +172,7 @@ def transport_velocity(mesh: fe.Mesh, phi: np.ndarray, u0: np.ndarray, mdot: np.
     return_points also the point y[3, len(nodes)] (cell units) whose velocity was taken (the closest point for the
     band nodes of variants 2/3, else the node)."""
     ev = PointEval(mesh, phi, u0)
-    m1 = mesh.n + 1
+    m1 = ev.n_cells + 1  # level-set nodes per axis
     nodes = np.arange(mesh.n_phi) if nodes is None else np.asarray(nodes)
     variant = int(prm.get("variant", 2))
     eps = prm["eps"]
@@ -181,13 +186,17 @@ def transport_velocity(mesh: fe.Mesh, phi: np.ndarray, u0: np.ndarray, mdot: np.
         sx = np.array([i, j, k], dtype=float)
         phx = float(phi[node])
         _, g = ev.phi_grad(sx)
-        nx = physics.normal(g, mesh.h)
+        nx = physics.normal(g, ev.h)
         mx = float(mdot[node])
         if variant == 1:
             H = physics.heaviside(np.array([phx]), eps)[0]
             rho = physics.density(H, prm["rho_l"], prm["rho_g"])
-            vnode = (mesh.p * i) + mesh.m * ((mesh.p * j) + mesh.m * (mesh.p * k))
-            ug[:, t] = u0v[:, vnode] + mx / rho * nx
+            if mesh.n_sub == 1:  # the node is a velocity node
+                vnode = (mesh.p * i) + mesh.m * ((mesh.p * j) + mesh.m * (mesh.p * k))
+                uval = u0v[:, vnode]
+            else:
+                uval = ev.velocity(sx)
+            ug[:, t] = uval + mx / rho * nx
             pts[:, t] = sx
             continue
         if variant == 2:

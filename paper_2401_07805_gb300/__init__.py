@@ -39,13 +39,14 @@ class EvapParams(ctypes.Structure):
     _fields_ = [("rho_l", _c_dbl), ("rho_g", _c_dbl), ("mu_l", _c_dbl), ("mu_g", _c_dbl), ("eps", _c_dbl),
                 ("dt", _c_dbl), ("c_mass", _c_dbl), ("theta", _c_dbl), ("dtau", _c_dbl), ("variant", _c_int),
                 ("stress", _c_int), ("corr_zone", _c_int), ("newton", _c_int), ("dirichlet_faces", ctypes.c_uint),
-                ("cpp_tol", _c_dbl), ("cpp_kmax", _c_int), ("eta_n", _c_dbl), ("eta_kappa", _c_dbl)]
+                ("cpp_tol", _c_dbl), ("cpp_kmax", _c_int), ("eta_n", _c_dbl), ("eta_kappa", _c_dbl), ("n_sub", _c_int)]
 
 
 SIGNATURES = {
     "evap_create_mesh": (_c_int, [_c_int, _c_int, _c_dbl, ctypes.POINTER(EvapParams), ctypes.POINTER(_vp)]),
     "evap_destroy": (_c_int, [_vp]),
     "evap_sizes": (_c_int, [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+    "evap_pressure_size": (_c_int, [_vp, ctypes.POINTER(ctypes.c_int64)]),
     "evap_set_fields": (_c_int, [_vp, _vp, _vp, _vp, _vp]),
     "evap_set_transport_velocity": (_c_int, [_vp, _vp, _vp]),
     "evap_get_transport_velocity": (_c_int, [_vp, _vp, _vp, ctypes.POINTER(ctypes.c_int64), _vp]),
@@ -82,7 +83,7 @@ SIGNATURES = {
 
 DEFAULT_PARAMS = dict(rho_l=1000.0, rho_g=1.0, mu_l=1e-3, mu_g=1e-5, eps=None, dt=1e-4, c_mass=None, theta=0.5,
                       dtau=None, variant=2, stress=1, corr_zone=0, newton=1, dirichlet_faces=0x3F, cpp_tol=1e-10,
-                      cpp_kmax=20, eta_n=2.0, eta_kappa=2.0)
+                      cpp_kmax=20, eta_n=2.0, eta_kappa=2.0, n_sub=1)
 
 
 def library_path() -> str:
@@ -167,7 +168,10 @@ class Operator:
                "evap_create_mesh")
         nu, nphi = ctypes.c_int64(), ctypes.c_int64()
         _check(lib().evap_sizes(self._h, ctypes.byref(nu), ctypes.byref(nphi)), "evap_sizes")
-        self.n_u, self.n_phi = nu.value, nphi.value
+        self.n_u, self.n_phi = nu.value, nphi.value  # velocity nodes, level-set nodes
+        npr = ctypes.c_int64()
+        _check(lib().evap_pressure_size(self._h, ctypes.byref(npr)), "evap_pressure_size")
+        self.n_p = npr.value  # pressure nodes (the divergence row, p, w_p)
         self.fields_version = 0  # bumped by every call that replaces (or drops) the mesh's fields
 
     # ------------------------------------------------------------------------------------------------- helpers
@@ -288,7 +292,7 @@ class Operator:
         tensors (phi, u, p) at t^(n+1) and info (picard_res: the last nonlinear residual)."""
         phi = self._dev(phi, self.n_phi, torch.float64, "phi").clone()
         u = self._dev(u, 3 * self.n_u, torch.float64, "u").clone()
-        p = self._dev(p, self.n_phi, torch.float64, "p").clone()
+        p = self._dev(p, self.n_p, torch.float64, "p").clone()
         mdot = self._dev(mdot, self.n_phi, torch.float64, "mdot")
         up = None if u_prev is None else self._dev(u_prev, 3 * self.n_u, torch.float64, "u_prev")
         g = None if gravity is None else (ctypes.c_double * 3)(*[float(v) for v in gravity])
@@ -308,9 +312,9 @@ class Operator:
     def apply_saddle(self, x: torch.Tensor, p: torch.Tensor):
         """(A x - B^T p, B x): the velocity-pressure operator of Eq. (weakNavierStokes) with the Q1 pressure."""
         x = self._dev(x, 3 * self.n_u, torch.float64, "x")
-        p = self._dev(p, self.n_phi, torch.float64, "p")
+        p = self._dev(p, self.n_p, torch.float64, "p")
         y = torch.empty(3 * self.n_u, dtype=torch.float64, device=self.device)
-        yp = torch.empty(self.n_phi, dtype=torch.float64, device=self.device)
+        yp = torch.empty(self.n_p, dtype=torch.float64, device=self.device)
         _check(lib().evap_apply_saddle(self._h, _ptr(x), _ptr(p), _ptr(y), _ptr(yp), _stream()), "evap_apply_saddle")
         return y, yp
 
@@ -320,8 +324,8 @@ class Operator:
         f = self._dev(f, 3 * self.n_u, torch.float64, "f")
         x = (torch.zeros(3 * self.n_u, dtype=torch.float64, device=self.device) if x0 is None
              else self._dev(x0, 3 * self.n_u, torch.float64, "x0").clone())
-        p = (torch.zeros(self.n_phi, dtype=torch.float64, device=self.device) if p0 is None
-             else self._dev(p0, self.n_phi, torch.float64, "p0").clone())
+        p = (torch.zeros(self.n_p, dtype=torch.float64, device=self.device) if p0 is None
+             else self._dev(p0, self.n_p, torch.float64, "p0").clone())
         its, rel = ctypes.c_int(), ctypes.c_double()
         rc = lib().evap_solve_saddle(self._h, _ptr(f), _ptr(x), _ptr(p), int(restart), float(rtol), int(max_iter),
                                      ctypes.byref(its), ctypes.byref(rel), _stream())
@@ -341,7 +345,7 @@ class Operator:
         dt = torch.float64 if prec == 64 else torch.float32
         x = self._dev(x, 3 * self.n_u, dt, "x")
         y = self._out(out, 3 * self.n_u, dt)
-        yp = self._out(out_p, self.n_phi, dt) if with_divergence else None
+        yp = self._out(out_p, self.n_p, dt) if with_divergence else None
         _check(lib().evap_apply_momentum(self._h, prec, _ptr(x), _ptr(y), _ptr(yp), _stream()), "evap_apply_momentum")
         return (y, yp) if with_divergence else y
 
@@ -357,7 +361,7 @@ class Operator:
                       need=("x", "u0", "phi", "mdot")):
         w = self._dev(w, 3 * self.n_u, torch.float64, "w")
         x = self._dev(x, 3 * self.n_u, torch.float64, "x")
-        wp = None if w_p is None else self._dev(w_p, self.n_phi, torch.float64, "w_p")
+        wp = None if w_p is None else self._dev(w_p, self.n_p, torch.float64, "w_p")
         f64 = dict(dtype=torch.float64, device=self.device)
         out = {k: None for k in ("x", "u0", "phi", "mdot")}
         if "x" in need:

@@ -14,7 +14,8 @@
 //     d delta/dphi = (H''(d) d'(phi)^2 + H'(d) d''(phi)) |grad phi|, d delta/d grad phi = H'(d) d'(phi) n,
 //     dn/d grad phi = (I - n n^T)/|grad phi|; the zone gate is piecewise constant.
 // The value/gradient sensitivities are tested like the forward operator (S^T and Dc^T sweeps); the Q1 sensitivities
-// are integrated against N^1_j and grad N^1_j.
+// are integrated against the level-set shape functions N_j and grad N_j (Q1 on the level-set mesh: the velocity
+// cell subdivided n_sub times per direction).
 #include "physics.cuh"
 
 namespace evap {
@@ -41,16 +42,18 @@ __global__ void k_adjoint_init(int M, int64_t Nu, int64_t Np, unsigned faces, co
     }
 }
 
-template <int P, int CB>
+// K = n_sub + 1: level-set shape functions per direction on a velocity cell (Q1 on its n_sub sub-intervals).
+template <int P, int CB, int K>
 __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1), 2)
     k_adjoint(MeshArgs<double> m, Basis<double> bas, const double* __restrict__ phi, const double* __restrict__ mdot,
               const int8_t* __restrict__ code, const int32_t* __restrict__ tindex, const double* __restrict__ table,
               const double* __restrict__ qc, const double* __restrict__ w, const double* __restrict__ wp,
               const double* __restrict__ x, double* gx, double* gu, double* gphi, double* gm) {
     constexpr int Q = P + 1, NQ = Q * Q * Q;
-    __shared__ double sS[Q][Q], sDc[Q][Q], sN1[Q][2];
+    static_assert(K * Q * Q <= NQ && K * K * K <= NQ, "one thread per entry of each level-set test sweep");
+    __shared__ double sS[Q][Q], sDc[Q][Q], sN1[Q][2], sNL[Q][K], sDL[Q][K];
     __shared__ double buf[2][CB][12][NQ];
-    __shared__ double q1a[CB][5][2 * Q * Q], q1b[CB][5][4 * Q];  // Q1 test sweeps of the phi / mdot sensitivities
+    __shared__ double q1a[CB][5][K * Q * Q], q1b[CB][5][K * K * Q];  // level-set test sweeps of the phi / mdot sensitivities
     const int tid = threadIdx.x;
     const int lc = tid / NQ, t = tid % NQ;
     const int64_t cell = (int64_t)blockIdx.x * CB + lc;
@@ -60,9 +63,14 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1), 2)
         sDc[tid / Q][tid % Q] = bas.Dc[tid / Q][tid % Q] * m.inv_h;  // physical collocation derivative
     }
     if (tid < 2 * Q) sN1[tid / 2][tid % 2] = bas.N1[tid / 2][tid % 2];
+    if (tid < K * Q) {
+        sNL[tid / K][tid % K] = bas.NL[tid / K][tid % K];
+        sDL[tid / K][tid % K] = bas.DL[tid / K][tid % K];
+    }
     const int a = t % Q, b = (t / Q) % Q, c = t / (Q * Q);
     const int n = m.n, M = m.M;
-    const int64_t m1 = n + 1;
+    const int64_t m1 = n + 1;       // pressure nodes per axis (w_p)
+    const int64_t ml = m.nl + 1;    // level-set nodes per axis
     int cx = 0, cy = 0, cz = 0;
     int64_t gidx = 0;
     bool cons = false;
@@ -140,37 +148,29 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1), 2)
         const double rho_c = tcell ? table[(int64_t)tindex[cell] * TAB_K * NQ + t]
                                    : (cc == CELL_LIQUID ? m.rho_H1 : m.rho_H0);
         const double wr = W * rho_c;  // the W rho of the forward apply
-        // Q1 fields at the point: trilinear weights of the 8 cell nodes (phi only in table cells)
+        // w_p (pressure space, Q1 on the cell) and the level set (its own, possibly subdivided, mesh; only in table
+        // cells) at the point
         const double tx = bas.t[a], ty = bas.t[b], tz = bas.t[c];
-        double wq[8];
         double ph = 0, pi = 0;
+        if (wp) {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int ja = j & 1, jb = (j >> 1) & 1, jc = j >> 2;
-            const int64_t nd = (cx + ja) + m1 * ((cy + jb) + m1 * (cz + jc));
-            wq[j] = (ja ? tx : 1.0 - tx) * (jb ? ty : 1.0 - ty) * (jc ? tz : 1.0 - tz);
-            if (tcell) ph += wq[j] * phi[nd];
-            if (wp) pi += wq[j] * wp[nd];
+            for (int j = 0; j < 8; ++j) {
+                const int ja = j & 1, jb = (j >> 1) & 1, jc = j >> 2;
+                const int64_t nd = (cx + ja) + m1 * ((cy + jb) + m1 * (cz + jc));
+                pi += (ja ? tx : 1.0 - tx) * (jb ? ty : 1.0 - ty) * (jc ? tz : 1.0 - tz) * wp[nd];
+            }
         }
+        double gp[3] = {0, 0, 0}, md = 0.0;
+        if (tcell) ls_at(phi, m, cx, cy, cz, tx, ty, tz, ph, gp);
         // the phi / mdot sensitivities and the normal are needed only in the interface zone (or with the correction
         // applied everywhere), which lies in table cells; elsewhere H is 0 or 1 and its derivatives vanish
         const bool zone = tcell && fabs(ph) < PHI_BAND;
         const bool full = zone || (tcell && m.stress != 0 && m.corr_zone != 0);
         const double nw = m.newton ? 1.0 : 0.0;
         Material mat;
-        double gp[3] = {0, 0, 0}, md = 0.0;
         if (full) {
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int ja = j & 1, jb = (j >> 1) & 1, jc = j >> 2;
-                const int64_t nd = (cx + ja) + m1 * ((cy + jb) + m1 * (cz + jc));
-                const double pv = phi[nd];
-                gp[0] += (ja ? 1.0 : -1.0) * (jb ? ty : 1.0 - ty) * (jc ? tz : 1.0 - tz) * pv;
-                gp[1] += (ja ? tx : 1.0 - tx) * (jb ? 1.0 : -1.0) * (jc ? tz : 1.0 - tz) * pv;
-                gp[2] += (ja ? tx : 1.0 - tx) * (jb ? ty : 1.0 - ty) * (jc ? 1.0 : -1.0) * pv;
-                md += wq[j] * mdot[nd];
-            }
-            gp[0] *= m.inv_h; gp[1] *= m.inv_h; gp[2] *= m.inv_h;
+            double gm_[3];
+            ls_at(mdot, m, cx, cy, cz, tx, ty, tz, md, gm_);
             mat = material(ph, gp[0], gp[1], gp[2], m);
         }
         const double wm = qv[13];
@@ -283,17 +283,18 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1), 2)
             tx3[k] = gxv[k] + (s0 + s1 + s2);
             tu3[k] = guv[k] + (u0s + u1s + u2s);
         }
-        // Q1 sensitivities: g_phi[j] = sum_q N1_j dL/dphi + grad N1_j . dL/dgrad phi, g_mdot[j] = sum_q N1_j dL/dmdot,
-        // by three sweeps; field f: 0 dL/dphi, 1..3 dL/dgrad phi (x, y, z), 4 dL/dmdot.  Along direction d the 1D
-        // factor is d N1/dt = (-1, 1) for field 1 + d, N1(t_q) otherwise.  x-sweep: [jx][qy][qz].
-        if (t < 2 * Q * Q) {
-            const int jx = t & 1, qy = (t >> 1) % Q, qz = (t >> 1) / Q;
-            const double dj = jx ? 1.0 : -1.0;
+        // level-set sensitivities: g_phi[j] = sum_q N_j dL/dphi + grad N_j . dL/dgrad phi, g_mdot[j] = sum_q N_j
+        // dL/dmdot with the level-set shape functions N_j of the cell (K per direction), by three sweeps; field f:
+        // 0 dL/dphi, 1..3 dL/dgrad phi (x, y, z), 4 dL/dmdot.  Along direction d the 1D factor is the reference
+        // derivative DL for field 1 + d, NL otherwise.  x-sweep: [jx][qy][qz].
+        if (t < K * Q * Q) {
+            const int jx = t % K, qy = (t / K) % Q, qz = (t / K) / Q;
 #pragma unroll
             for (int f = 0; f < 5; ++f) {
                 double sacc = 0.0;
 #pragma unroll
-                for (int q = 0; q < Q; ++q) sacc += (f == 1 ? dj : sN1[q][jx]) * buf[1][lc][6 + f][q + Q * (qy + Q * qz)];
+                for (int q = 0; q < Q; ++q)
+                    sacc += (f == 1 ? sDL[q][jx] : sNL[q][jx]) * buf[1][lc][6 + f][q + Q * (qy + Q * qz)];
                 q1a[lc][f][t] = sacc;
             }
         }
@@ -305,31 +306,31 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1), 2)
             buf[0][lc][k][t] = tx3[k];
             buf[0][lc][3 + k][t] = tu3[k];
         }
-        if (t < 4 * Q) {  // Q1 y-sweep: [jx][jy][qz]
-            const int jx = t & 1, jy = (t >> 1) & 1, qz = t >> 2;
-            const double dj = jy ? 1.0 : -1.0;
+        if (t < K * K * Q) {  // y-sweep: [jx][jy][qz]
+            const int jx = t % K, jy = (t / K) % K, qz = t / (K * K);
 #pragma unroll
             for (int f = 0; f < 5; ++f) {
                 double sacc = 0.0;
 #pragma unroll
-                for (int q = 0; q < Q; ++q) sacc += (f == 2 ? dj : sN1[q][jy]) * q1a[lc][f][jx + 2 * (q + Q * qz)];
+                for (int q = 0; q < Q; ++q)
+                    sacc += (f == 2 ? sDL[q][jy] : sNL[q][jy]) * q1a[lc][f][jx + K * (q + Q * qz)];
                 q1b[lc][f][t] = sacc;
             }
         }
     }
     __syncthreads();
-    if (active && t < 8) {  // Q1 z-sweep and scatter of node (jx, jy, jz)
-        const int jx = t & 1, jy = (t >> 1) & 1, jz = t >> 2;
-        const double dj = jz ? 1.0 : -1.0;
+    if (active && t < K * K * K) {  // z-sweep and scatter of level-set node (jx, jy, jz) of the cell
+        const int jx = t % K, jy = (t / K) % K, jz = t / (K * K);
         double r[5];
 #pragma unroll
         for (int f = 0; f < 5; ++f) {
             double sacc = 0.0;
 #pragma unroll
-            for (int q = 0; q < Q; ++q) sacc += (f == 3 ? dj : sN1[q][jz]) * q1b[lc][f][jx + 2 * (jy + 2 * q)];
+            for (int q = 0; q < Q; ++q) sacc += (f == 3 ? sDL[q][jz] : sNL[q][jz]) * q1b[lc][f][jx + K * (jy + K * q)];
             r[f] = sacc;
         }
-        const int64_t nd = (cx + jx) + m1 * ((cy + jy) + m1 * (cz + jz));
+        const int ks = K - 1;  // n_sub
+        const int64_t nd = (ks * cx + jx) + ml * ((ks * cy + jy) + ml * (ks * cz + jz));
         if (gphi) atomicAdd(&gphi[nd], r[0] + m.inv_h * (r[1] + r[2] + r[3]));
         if (gm) atomicAdd(&gm[nd], r[4]);
     }
@@ -368,15 +369,23 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1), 2)
 int launch_adjoint(evap_mesh* h, const double* w, const double* wp, const double* x, double* gx, double* gu,
                    double* gphi, double* gm, cudaStream_t s) {
     const MeshArgs<double>& m = h->m;
-    k_adjoint_init<<<blocks_for(3 * m.Nu, 256), 256, 0, s>>>(m.M, m.Nu, m.Nphi, m.faces, w, gx, gu, gphi, gm);
+    k_adjoint_init<<<blocks_for(3 * m.Nu, 256), 256, 0, s>>>(m.M, m.Nu, m.Nphi, m.faces, w, gx, gu, gphi, gm);  // level set
     EVAP_CHECK_LAUNCH("adjoint_init");
-    if (m.P == 2) {
+    if (m.P == 2 && m.nsub == 1) {
         constexpr int CB = 7;  // 189 threads: 98 % of the lanes of 6 warps (4 cells: 108 threads, 84 %)
-        k_adjoint<2, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 27, 0, s>>>(
+        k_adjoint<2, CB, 2><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 27, 0, s>>>(
+            m, h->b, h->phi, h->mdot, h->cell_code, h->table_index, h->table, h->qc, w, wp, x, gx, gu, gphi, gm);
+    } else if (m.P == 2) {
+        constexpr int CB = 6;  // the subdivided level set's larger test-sweep buffers (static shared memory <= 48 KB)
+        k_adjoint<2, CB, 3><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 27, 0, s>>>(
+            m, h->b, h->phi, h->mdot, h->cell_code, h->table_index, h->table, h->qc, w, wp, x, gx, gu, gphi, gm);
+    } else if (m.nsub == 1) {
+        constexpr int CB = 2;
+        k_adjoint<3, CB, 2><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 64, 0, s>>>(
             m, h->b, h->phi, h->mdot, h->cell_code, h->table_index, h->table, h->qc, w, wp, x, gx, gu, gphi, gm);
     } else {
         constexpr int CB = 2;
-        k_adjoint<3, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 64, 0, s>>>(
+        k_adjoint<3, CB, 3><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 64, 0, s>>>(
             m, h->b, h->phi, h->mdot, h->cell_code, h->table_index, h->table, h->qc, w, wp, x, gx, gu, gphi, gm);
     }
     EVAP_CHECK_LAUNCH("adjoint");

@@ -1,6 +1,7 @@
 // C ABI entry points: argument validation, library-owned state, dispatch to the kernel launchers.
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <atomic>
 #include <initializer_list>
@@ -47,7 +48,7 @@ static void copy_ct_basis(Basis<double>& b) {
 }
 
 // The mesh's basis: the compile-time tables of basis_ct.cuh (also used as immediates by the FP32 apply).
-void host_basis(int P, Basis<double>& b) {
+void host_basis(int P, Basis<double>& b, int nsub) {
     std::memset(&b, 0, sizeof(b));
     b.P = P;
     b.Q = P + 1;
@@ -56,6 +57,15 @@ void host_basis(int P, Basis<double>& b) {
     else
         copy_ct_basis<3>(b);
     gauss_rule2(b.g2t, b.g2w);
+    for (int q = 0; q < b.Q; ++q) {  // level-set hats of the n_sub times subdivided interval
+        const double s = nsub * b.t[q];
+        const int k = std::min(std::max((int)std::floor(s), 0), nsub - 1);
+        const double xi = s - k;
+        b.NL[q][k] = 1.0 - xi;
+        b.NL[q][k + 1] = xi;
+        b.DL[q][k] = -(double)nsub;
+        b.DL[q][k + 1] = (double)nsub;
+    }
 }
 
 template <typename T>
@@ -74,6 +84,10 @@ Basis<T> cast_basis(const Basis<double>& b) {
         o.t[i] = (T)b.t[i];
         o.N1[i][0] = (T)b.N1[i][0];
         o.N1[i][1] = (T)b.N1[i][1];
+        for (int j = 0; j < 3; ++j) {
+            o.NL[i][j] = (T)b.NL[i][j];
+            o.DL[i][j] = (T)b.DL[i][j];
+        }
     }
     for (int i = 0; i < 2; ++i) {
         o.g2t[i] = (T)b.g2t[i];
@@ -96,10 +110,25 @@ MeshArgs<T> mesh_args(const evap_mesh* h) {
     o.eps = (T)m.eps; o.dt = (T)m.dt; o.theta = (T)m.theta; o.dtau = (T)m.dtau;
     o.newton = m.newton; o.stress = m.stress; o.corr_zone = m.corr_zone; o.variant = m.variant;
     o.faces = m.faces;
+    o.nsub = m.nsub; o.nl = m.nl; o.Np = m.Np;
     return o;
 }
 template MeshArgs<double> mesh_args<double>(const evap_mesh*);
 template MeshArgs<float> mesh_args<float>(const evap_mesh*);
+
+template <typename T>
+MeshArgs<T> ls_args(const evap_mesh* h) {
+    MeshArgs<T> o = mesh_args<T>(h);
+    const double hl = h->m.h / h->m.nsub;
+    o.n = h->m.nl;
+    o.ncell = (int64_t)o.n * o.n * o.n;
+    o.h = (T)hl;
+    o.inv_h = (T)(1.0 / hl);
+    o.vol_w = (T)(hl * hl * hl);
+    return o;
+}
+template MeshArgs<double> ls_args<double>(const evap_mesh*);
+template MeshArgs<float> ls_args<float>(const evap_mesh*);
 
 }  // namespace evap
 
@@ -193,6 +222,8 @@ int evap_create_mesh(int n_cells, int degree_u, double L, const evap_params* prm
         return fail(EVAP_EINVAL, "evap_create_mesh: cpp_tol must be > 0 and cpp_kmax >= 0");
     if (!(prm->eta_n >= 0.0) || !(prm->eta_kappa >= 0.0))
         return fail(EVAP_EINVAL, "evap_create_mesh: eta_n and eta_kappa must be >= 0");
+    const int nsub = prm->n_sub == 0 ? 1 : prm->n_sub;
+    if (nsub != 1 && nsub != 2) return fail(EVAP_EINVAL, "evap_create_mesh: n_sub must be 1 or 2");
     evap_mesh* h = new (std::nothrow) evap_mesh();
     if (!h) return fail(EVAP_ENOMEM, "evap_create_mesh: host allocation failed");
     cudaGetDevice(&h->device);
@@ -202,7 +233,10 @@ int evap_create_mesh(int n_cells, int degree_u, double L, const evap_params* prm
     m.P = degree_u;
     m.M = degree_u * n_cells + 1;
     m.Nu = (int64_t)m.M * m.M * m.M;
-    m.Nphi = (int64_t)(n_cells + 1) * (n_cells + 1) * (n_cells + 1);
+    m.nsub = nsub;
+    m.nl = nsub * n_cells;
+    m.Nphi = (int64_t)(m.nl + 1) * (m.nl + 1) * (m.nl + 1);
+    m.Np = (int64_t)(n_cells + 1) * (n_cells + 1) * (n_cells + 1);
     m.ncell = (int64_t)n_cells * n_cells * n_cells;
     m.h = L / n_cells;
     m.inv_h = 1.0 / m.h;
@@ -218,7 +252,7 @@ int evap_create_mesh(int n_cells, int degree_u, double L, const evap_params* prm
     m.corr_zone = prm->corr_zone ? 1 : 0;
     m.variant = prm->variant;
     m.faces = prm->dirichlet_faces & 0x3Fu;
-    host_basis(degree_u, h->b);
+    host_basis(degree_u, h->b, nsub);
     const int64_t Nu = m.Nu, Np = m.Nphi;
     cudaError_t e = cudaSuccess;
     auto al = [&](void** p, size_t bytes) {
@@ -262,6 +296,12 @@ int evap_sizes(evap_handle h, int64_t* n_u, int64_t* n_phi) {
     if (!h) return fail(EVAP_EINVAL, "evap_sizes: null handle");
     if (n_u) *n_u = h->m.Nu;
     if (n_phi) *n_phi = h->m.Nphi;
+    return EVAP_OK;
+}
+
+int evap_pressure_size(evap_handle h, int64_t* n_p) {
+    if (!h) return fail(EVAP_EINVAL, "evap_pressure_size: null handle");
+    if (n_p) *n_p = h->m.Np;
     return EVAP_OK;
 }
 
@@ -422,7 +462,7 @@ int evap_apply_saddle(evap_handle h, const double* x, const double* p, double* y
     if (x == y) return fail(EVAP_EINVAL, "evap_apply_saddle: x and y must not alias");
     if (!h->has_fields) return fail(EVAP_ENOFIELDS, "evap_apply_saddle: call evap_set_fields first");
     int rc0 = check_inputs(h, "evap_apply_saddle", (cudaStream_t)stream,
-                           {{x, 3 * h->m.Nu, false}, {p, h->m.Nphi, false}});
+                           {{x, 3 * h->m.Nu, false}, {p, h->m.Np, false}});
     if (rc0) return rc0;
     return launch_saddle_apply(h, x, p, y, y_p, (cudaStream_t)stream);
 }
@@ -436,7 +476,7 @@ int evap_solve_saddle(evap_handle h, const double* f, double* x, double* p, int 
         return fail(EVAP_EINVAL, "evap_solve_saddle: every face is Dirichlet (the pressure level is undetermined)");
     if (!h->has_fields) return fail(EVAP_ENOFIELDS, "evap_solve_saddle: call evap_set_fields first");
     int rc0 = check_inputs(h, "evap_solve_saddle", (cudaStream_t)stream,
-                           {{f, 3 * h->m.Nu, false}, {x, 3 * h->m.Nu, false}, {p, h->m.Nphi, false}});
+                           {{f, 3 * h->m.Nu, false}, {x, 3 * h->m.Nu, false}, {p, h->m.Np, false}});
     if (rc0) return rc0;
     return solve_saddle(h, f, x, p, restart, rtol, max_iter, iters, relres, (cudaStream_t)stream);
 }
@@ -455,7 +495,7 @@ int evap_time_step(evap_handle h, double* phi, double* u, double* p, const doubl
         return fail(EVAP_EINVAL, "evap_time_step: need picard_iters >= 1, picard_atol >= 0, fp_iters >= 1, "
                                  "reinit_steps >= 0, ns_rtol > 0");
     cudaStream_t s = (cudaStream_t)stream;
-    int rc0 = check_inputs(h, "evap_time_step", s, {{p, h->m.Nphi, false}, {u_prev, 3 * h->m.Nu, false}});
+    int rc0 = check_inputs(h, "evap_time_step", s, {{p, h->m.Np, false}, {u_prev, 3 * h->m.Nu, false}});
     if (rc0) return rc0;
     double g[3] = {0.0, 0.0, 0.0};
     if (gravity) {
@@ -507,7 +547,7 @@ int evap_apply_adjoint(evap_handle h, const double* w, const double* w_p, const 
     if (!h || !w || !x) return fail(EVAP_EINVAL, "evap_apply_adjoint: null argument");
     if (!h->has_fields) return fail(EVAP_ENOFIELDS, "evap_apply_adjoint: call evap_set_fields first");
     int rc0 = check_inputs(h, "evap_apply_adjoint", (cudaStream_t)stream,
-                           {{w, 3 * h->m.Nu, false}, {w_p, h->m.Nphi, false}, {x, 3 * h->m.Nu, false}});
+                           {{w, 3 * h->m.Nu, false}, {w_p, h->m.Np, false}, {x, 3 * h->m.Nu, false}});
     if (rc0) return rc0;
     return launch_adjoint(h, w, w_p, x, g_x, g_u0, g_phi, g_mdot, (cudaStream_t)stream);
 }

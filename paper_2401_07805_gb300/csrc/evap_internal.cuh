@@ -23,8 +23,12 @@ struct Basis {
     T Dc[MAXQ][MAXQ];  // Dc[q][r] = L_r'(t_q), L_r the Lagrange polynomials through the Gauss points (collocation)
     T w[MAXQ];         // Gauss weights on [0, 1]
     T t[MAXQ];         // Gauss points on [0, 1]
-    T N1[MAXQ][2];     // Q1 shape values (1 - t_q, t_q)
+    T N1[MAXQ][2];     // Q1 shape values (1 - t_q, t_q) (pressure space)
     T g2t[2], g2w[2];  // 2-point Gauss rule of the Q1 operators
+    // level-set space on one velocity cell (Q1 on the n_sub sub-intervals per direction, Sec. 2.5): the n_sub + 1
+    // piecewise-linear hats at the Gauss points, NL[q][a], and their reference derivatives DL[q][a] (d/dt; divide by
+    // h for physical units); a Gauss point on a sub-interval boundary takes the upper sub-interval's slopes
+    T NL[MAXQ][3], DL[MAXQ][3];
 };
 
 // Scalars every kernel needs (passed by value).
@@ -32,6 +36,8 @@ template <typename T>
 struct MeshArgs {
     int n, P, M;
     int64_t Nu, Nphi, ncell;
+    int nsub, nl;  // level-set mesh: the velocity mesh subdivided nsub times per direction, nl = nsub n cells per axis
+    int64_t Np;    // Q1 pressure nodes (n + 1)^3; Nphi = (nl + 1)^3 level-set nodes
     T h, inv_h, vol_w;  // cell size, 1/h, h^3
     T rho_l, rho_g, mu_l, mu_g, c_mass;
     T rho_H1, rho_H0, mu_H1, mu_H0;  // Eqs. (rhoEff), (muEff) evaluated at H = 1 and H = 0
@@ -53,7 +59,7 @@ struct Coeffs {            // quadrature-point coefficients of the momentum oper
     const T* u0;           // [3 N_u]
 };
 
-void host_basis(int P, Basis<double>& b);
+void host_basis(int P, Basis<double>& b, int nsub = 1);
 template <typename T>
 Basis<T> cast_basis(const Basis<double>& b);
 
@@ -163,6 +169,10 @@ void count_launch();
 
 template <typename T>
 MeshArgs<T> mesh_args(const evap_mesh* h);
+// The same arguments for kernels that work on the level-set mesh alone (Q1 level-set operators, geometry): n, h, inv_h,
+// vol_w and ncell of the subdivided mesh (identical to mesh_args for n_sub = 1).
+template <typename T>
+MeshArgs<T> ls_args(const evap_mesh* h);
 
 // kernels launchers (each returns an evap_status)
 int launch_setup_coefficients(evap_mesh* h, cudaStream_t s);

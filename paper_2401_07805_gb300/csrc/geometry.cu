@@ -387,8 +387,8 @@ static CgSpace cg_space(evap_mesh* h) {
 // |r| <= max(rtol |r0|, atol), checked every CG_CHECK iterations, or after max_iter iterations.
 template <class Apply>
 static int cg_solve(evap_mesh* h, Apply apply, const double* b, const double* d, double* x, double rtol, double atol,
-                    int max_iter, int* iters, double* relres, cudaStream_t s) {
-    const int64_t N = h->m.Nphi;
+                    int max_iter, int* iters, double* relres, cudaStream_t s, int64_t N = -1) {
+    if (N < 0) N = h->m.Nphi;  // level-set vectors unless given (the pressure space of the Schur solve)
     CgSpace w = cg_space(h);
     double* hs = h->geo_host;
     k_cg_start<<<CG_BLOCKS, CG_THREADS, 0, s>>>(b, d, x, w.r, w.z, w.p, N, w.part, w.ticket, w.S);
@@ -422,8 +422,9 @@ static int cg_solve(evap_mesh* h, Apply apply, const double* b, const double* d,
 }
 
 static int helmholtz_apply(evap_mesh* h, double c, int ncomp, const double* x, double* y, cudaStream_t s) {
-    const int64_t total = h->m.Nphi * ncomp;
-    k_helmholtz<<<blocks_for(total, 256, 152 * 16), 256, 0, s>>>(h->m.n, h->m.h, c, ncomp, x, y);
+    const MeshArgs<double> lm = ls_args<double>(h);  // the level-set mesh
+    const int64_t total = lm.Nphi * ncomp;
+    k_helmholtz<<<blocks_for(total, 256, 152 * 16), 256, 0, s>>>(lm.n, lm.h, c, ncomp, x, y);
     EVAP_CHECK_LAUNCH("helmholtz");
     return EVAP_OK;
 }
@@ -433,16 +434,17 @@ int geo_helmholtz(evap_mesh* h, double c, int ncomp, const double* x, double* y,
 }
 
 int geo_projected_normal(evap_mesh* h, double* n, int* iters, double* relres, cudaStream_t s) {
+    const MeshArgs<double> lm = ls_args<double>(h);  // the level-set mesh
     int rc = geo_workspace(h);
     if (rc) return rc;
     CgSpace w = cg_space(h);
-    const int64_t Np = h->m.Nphi;
+    const int64_t Np = lm.Nphi;
     const int64_t stride = w.t1 - w.t0;  // right-hand sides of the three components in t0, t1, t2
-    const double c = h->prm.eta_n * h->m.h * h->m.h;
+    const double c = h->prm.eta_n * lm.h * lm.h;
     EVAP_CUDA(cudaMemsetAsync(w.t0, 0, 3 * stride * sizeof(double), s));
-    k_normal_rhs<<<blocks_for(h->m.ncell, 128, 1LL << 40), 128, 0, s>>>(h->m, h->b, h->phi, w.t0, stride);
+    k_normal_rhs<<<blocks_for(lm.ncell, 128, 1LL << 40), 128, 0, s>>>(lm, h->b, h->phi, w.t0, stride);
     EVAP_CHECK_LAUNCH("normal_rhs");
-    k_helmholtz_diag<<<blocks_for(Np, 256, 152 * 16), 256, 0, s>>>(h->m.n, h->m.h, c, w.d);
+    k_helmholtz_diag<<<blocks_for(Np, 256, 152 * 16), 256, 0, s>>>(lm.n, lm.h, c, w.d);
     EVAP_CHECK_LAUNCH("helmholtz_diag");
     if (iters) *iters = 0;
     if (relres) *relres = 0.0;
@@ -457,15 +459,16 @@ int geo_projected_normal(evap_mesh* h, double* n, int* iters, double* relres, cu
 }
 
 int geo_curvature(evap_mesh* h, const double* nf, double* kappa, int* iters, double* relres, cudaStream_t s) {
+    const MeshArgs<double> lm = ls_args<double>(h);  // the level-set mesh
     int rc = geo_workspace(h);
     if (rc) return rc;
     CgSpace w = cg_space(h);
-    const int64_t Np = h->m.Nphi;
-    const double c = h->prm.eta_kappa * h->m.h * h->m.h;
+    const int64_t Np = lm.Nphi;
+    const double c = h->prm.eta_kappa * lm.h * lm.h;
     EVAP_CUDA(cudaMemsetAsync(w.b, 0, Np * sizeof(double), s));
-    k_curvature_rhs<<<blocks_for(h->m.ncell, 128, 1LL << 40), 128, 0, s>>>(h->m, h->b, nf, w.b);
+    k_curvature_rhs<<<blocks_for(lm.ncell, 128, 1LL << 40), 128, 0, s>>>(lm, h->b, nf, w.b);
     EVAP_CHECK_LAUNCH("curvature_rhs");
-    k_helmholtz_diag<<<blocks_for(Np, 256, 152 * 16), 256, 0, s>>>(h->m.n, h->m.h, c, w.d);
+    k_helmholtz_diag<<<blocks_for(Np, 256, 152 * 16), 256, 0, s>>>(lm.n, lm.h, c, w.d);
     EVAP_CHECK_LAUNCH("helmholtz_diag");
     if (iters) *iters = 0;
     if (relres) *relres = 0.0;
@@ -536,7 +539,8 @@ __global__ void __launch_bounds__(128) k_elem_apply(int n, int64_t ncell, const 
 
 // Grows the element-matrix buffer of the mesh to `entries` per cell.
 static int geo_elem_reserve(evap_mesh* h, int entries) {
-    const int64_t need = entries * h->m.ncell;
+    const MeshArgs<double> lm = ls_args<double>(h);  // the level-set mesh
+    const int64_t need = entries * lm.ncell;
     if (h->geo_elem_len >= need) return EVAP_OK;
     if (h->geo_elem) cudaFree(h->geo_elem);
     h->geo_elem = nullptr;
@@ -548,23 +552,24 @@ static int geo_elem_reserve(evap_mesh* h, int entries) {
 
 // `steps` pseudo-time steps of the reinitialization with the frozen normal of the level-set operators.
 int geo_reinitialize(evap_mesh* h, double* psi, int steps, int* iters, double* last_change, cudaStream_t s) {
+    const MeshArgs<double> lm = ls_args<double>(h);  // the level-set mesh
     int rc = geo_workspace(h);
     if (rc) return rc;
     CgSpace w = cg_space(h);
-    const int64_t Np = h->m.Nphi;
+    const int64_t Np = lm.Nphi;
     EVAP_CUDA(cudaMemsetAsync(w.d, 0, Np * sizeof(double), s));
-    k_reinit_diag<<<blocks_for(h->m.ncell, 128, 1LL << 40), 128, 0, s>>>(h->m, h->b, h->phi, h->ls_normal, w.d);
+    k_reinit_diag<<<blocks_for(lm.ncell, 128, 1LL << 40), 128, 0, s>>>(lm, h->b, h->phi, h->ls_normal, w.d);
     EVAP_CHECK_LAUNCH("reinit_diag");
     if ((rc = geo_elem_reserve(h, 36))) return rc;
-    const unsigned gc = (unsigned)blocks_for(h->m.ncell, 128, 1LL << 40);
-    k_reinit_elem<<<gc, 128, 0, s>>>(h->m, h->b, h->phi, h->ls_normal, h->geo_elem);
+    const unsigned gc = (unsigned)blocks_for(lm.ncell, 128, 1LL << 40);
+    k_reinit_elem<<<gc, 128, 0, s>>>(lm, h->b, h->phi, h->ls_normal, h->geo_elem);
     EVAP_CHECK_LAUNCH("reinit_elem");
     if (iters) *iters = 0;
     double rel = 0.0;
     int status = EVAP_OK;
     auto apply = [&](const double* p, double* q) {
         EVAP_CUDA(cudaMemsetAsync(q, 0, Np * sizeof(double), s));
-        k_elem_apply<<<gc, 128, 0, s>>>(h->m.n, h->m.ncell, h->geo_elem, p, q);
+        k_elem_apply<<<gc, 128, 0, s>>>(lm.n, lm.ncell, h->geo_elem, p, q);
         EVAP_CHECK_LAUNCH("reinit_apply");
         return (int)EVAP_OK;
     };
@@ -673,8 +678,9 @@ __global__ void __launch_bounds__(128) k_elem_apply_full(int n, int64_t ncell, c
 }
 
 int geo_advect_elem_apply(evap_mesh* h, const double* x, double* y, cudaStream_t s) {
-    EVAP_CUDA(cudaMemsetAsync(y, 0, h->m.Nphi * sizeof(double), s));
-    k_elem_apply_full<<<(unsigned)blocks_for(h->m.ncell, 128, 1LL << 40), 128, 0, s>>>(h->m.n, h->m.ncell,
+    const MeshArgs<double> lm = ls_args<double>(h);  // the level-set mesh
+    EVAP_CUDA(cudaMemsetAsync(y, 0, lm.Nphi * sizeof(double), s));
+    k_elem_apply_full<<<(unsigned)blocks_for(lm.ncell, 128, 1LL << 40), 128, 0, s>>>(lm.n, lm.ncell,
                                                                                       h->geo_elem, x, y);
     EVAP_CHECK_LAUNCH("advect_apply");
     return EVAP_OK;
@@ -705,12 +711,13 @@ __global__ void k_clamp_unit(const double* __restrict__ phi, double* __restrict_
 constexpr int ADVECT_RESTART = 30;
 int geo_advect_levelset(evap_mesh* h, double* phi, int max_iters, double tol, int* fp_iters, int* lin_iters,
                         double* last_change, cudaStream_t s) {
+    const MeshArgs<double> lm = ls_args<double>(h);  // the level-set mesh
     int rc = geo_workspace(h);
     if (rc) return rc;
     CgSpace w = cg_space(h);
-    const int64_t Np = h->m.Nphi;
+    const int64_t Np = lm.Nphi;
     const int G = blocks_for(Np, 256, 152 * 8);
-    const unsigned gc = (unsigned)blocks_for(h->m.ncell, 128, 1LL << 40);
+    const unsigned gc = (unsigned)blocks_for(lm.ncell, 128, 1LL << 40);
     if ((rc = geo_elem_reserve(h, 64))) return rc;
     EVAP_CUDA(cudaMemcpyAsync(phi, h->phi, Np * sizeof(double), cudaMemcpyDeviceToDevice, s));
     int k = 0, lin = 0, status = EVAP_OK;
@@ -725,10 +732,10 @@ int geo_advect_levelset(evap_mesh* h, double* phi, int max_iters, double tol, in
         if ((rc = launch_transport_velocity(h, s, cur))) return rc;
         if ((rc = helmholtz_apply(h, 0.0, 1, h->phi, w.t1, s))) return rc;
         if ((rc = launch_levelset<double>(h, EVAP_ADVECT, h->phi, w.t2, s))) return rc;
-        k_advect_rhs<<<G, 256, 0, s>>>(w.t1, w.t2, h->m.theta, w.b, Np);
+        k_advect_rhs<<<G, 256, 0, s>>>(w.t1, w.t2, lm.theta, w.b, Np);
         EVAP_CHECK_LAUNCH("advect_rhs");
         EVAP_CUDA(cudaMemsetAsync(w.d, 0, Np * sizeof(double), s));
-        k_advect_elem<<<gc, 128, 0, s>>>(h->m, h->ugamma, h->geo_elem, w.d);
+        k_advect_elem<<<gc, 128, 0, s>>>(lm, h->ugamma, h->geo_elem, w.d);
         EVAP_CHECK_LAUNCH("advect_elem");
         EVAP_CUDA(cudaMemcpyAsync(w.r, phi, Np * sizeof(double), cudaMemcpyDeviceToDevice, s));
         double rel = 0.0;
@@ -761,24 +768,15 @@ __global__ void __launch_bounds__(128) k_schur_diag(MeshArgs<double> m, Basis<do
     Q1Cell c;
     int cx, cy, cz;
     q1_cell_nodes(cell, m.n, c, cx, cy, cz);
-    double pv[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) pv[j] = phi[c.node[j]];
     double out[8] = {};
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         double N[8], G[8][3];
         q1_weights(bas.g2t, q, m.inv_h, N, G);
         const double W = bas.g2w[q & 1] * bas.g2w[(q >> 1) & 1] * bas.g2w[q >> 2] * m.vol_w;
-        double ph = 0.0, g0 = 0.0, g1 = 0.0, g2 = 0.0;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            ph += N[j] * pv[j];
-            g0 += G[j][0] * pv[j];
-            g1 += G[j][1] * pv[j];
-            g2 += G[j][2] * pv[j];
-        }
-        const double wr = W / (material(ph, g0, g1, g2, m).rho * m.c_mass);
+        double ph, gp[3];  // the level set at the point (its own, possibly subdivided, mesh)
+        ls_at(phi, m, cx, cy, cz, bas.g2t[q & 1], bas.g2t[(q >> 1) & 1], bas.g2t[q >> 2], ph, gp);
+        const double wr = W / (material(ph, gp[0], gp[1], gp[2], m).rho * m.c_mass);
 #pragma unroll
         for (int j = 0; j < 8; ++j) out[j] += wr * (G[j][0] * G[j][0] + G[j][1] * G[j][1] + G[j][2] * G[j][2]);
     }
@@ -790,7 +788,7 @@ int geo_schur_setup(evap_mesh* h, double** diag, cudaStream_t s) {
     int rc = geo_workspace(h);
     if (rc) return rc;
     CgSpace w = cg_space(h);
-    EVAP_CUDA(cudaMemsetAsync(w.d, 0, h->m.Nphi * sizeof(double), s));
+    EVAP_CUDA(cudaMemsetAsync(w.d, 0, h->m.Np * sizeof(double), s));  // pressure space
     k_schur_diag<<<blocks_for(h->m.ncell, 128, 1LL << 40), 128, 0, s>>>(h->m, h->b, h->phi, w.d);
     EVAP_CHECK_LAUNCH("schur_diag");
     *diag = w.d;
@@ -801,7 +799,7 @@ int geo_cg(evap_mesh* h, const std::function<int(const double*, double*)>& apply
            double* x, double rtol, double atol, int max_iter, int* iters, cudaStream_t s) {
     int rc = geo_workspace(h);
     if (rc) return rc;
-    return cg_solve(h, apply, b, d, x, rtol, atol, max_iter, iters, nullptr, s);
+    return cg_solve(h, apply, b, d, x, rtol, atol, max_iter, iters, nullptr, s, h->m.Np);
 }
 
 }  // namespace evap

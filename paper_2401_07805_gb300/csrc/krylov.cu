@@ -790,7 +790,7 @@ struct SaddleSpace {
 static int saddle_precond(Ctx& inner, SaddleSpace& sp, const double* v, double* z) {
     evap_mesh* h = inner.h;
     cudaStream_t s = inner.s;
-    const int64_t Nu3 = 3 * h->m.Nu, Np = h->m.Nphi;
+    const int64_t Nu3 = 3 * h->m.Nu, Np = h->m.Np;
     const int G = blocks_for(Nu3, 256);
     // the inner solve's FP32 scratch is free here: w32 [3 N_u] and z32 (>= 2 N_phi) for the Schur operator
     int rc = schur_apply(h, v + Nu3, z + Nu3, sp.sdiag, sp.w32, sp.z32, SADDLE_SCHUR_CG, s);
@@ -827,7 +827,7 @@ int solve_saddle(evap_mesh* h, const double* f, double* x, double* p, int m, dou
     if (g_rhs) g = g_rhs;
     double* sdiag = nullptr;
     if ((rc = geo_schur_setup(h, &sdiag, s))) return rc;
-    const int64_t Nu3 = 3 * h->m.Nu, Np = h->m.Nphi, N = Nu3 + Np;
+    const int64_t Nu3 = 3 * h->m.Nu, Np = h->m.Np, N = Nu3 + Np;
     const int64_t ld = (N + 63) / 64 * 64, ldu = (Nu3 + 63) / 64 * 64;
     // inner (FP32 velocity GMRES) workspace and reduction scratch: the mesh's Krylov buffers
     const size_t fV = al256((size_t)(SADDLE_INNER_M + 1) * ldu * sizeof(float)), fN = al256((size_t)ldu * sizeof(float));

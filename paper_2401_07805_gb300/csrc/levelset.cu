@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(128) k_levelset(MeshArgs<T> m, Basis<T> bas, c
 
 template <typename T>
 int launch_levelset(evap_mesh* h, int mode, const T* x, T* y, cudaStream_t s) {
-    const MeshArgs<T> m = mesh_args<T>(h);
+    const MeshArgs<T> m = ls_args<T>(h);  // Q1 on the level-set mesh
     const Basis<T> b = cast_basis<T>(h->b);
     const bool dbl = sizeof(T) == 8;
     const T* phi = dbl ? (const T*)h->phi : (const T*)h->phi32;

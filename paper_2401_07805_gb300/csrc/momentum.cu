@@ -262,7 +262,7 @@ int launch_momentum(evap_mesh* h, const T* x, T* y, T* yp, cudaStream_t s, bool 
     if (init) {
         const int64_t lines = 3 * (int64_t)m.M * m.M;
         const unsigned grid = (unsigned)std::min<int64_t>((lines + 7) / 8, 152 * 16);
-        k_momentum_init<T><<<grid, 256, 0, s>>>(m.M, m.Nu, m.faces, x, y, yp, m.Nphi);
+        k_momentum_init<T><<<grid, 256, 0, s>>>(m.M, m.Nu, m.faces, x, y, yp, m.Np);  // y_p: pressure space
         EVAP_CHECK_LAUNCH("momentum_init");
     }
     if constexpr (sizeof(T) == 4) {  // FP32: line-oriented kernel (momentum32.cu)

@@ -98,6 +98,54 @@ __device__ __forceinline__ double dilation_coefficient(const MeshArgs<double>& m
     return 1.0 / m.rho_g - 1.0 / m.rho_l;
 }
 
+// Q1 field value and physical gradient at reference point (t[qx], t[qy], t[qz]) of cell (cx, cy, cz).
+__device__ __forceinline__ void q1_at(const double* __restrict__ f, int n, int cx, int cy, int cz, double x, double y,
+                                      double z, double inv_h, double& val, double g[3]) {
+    const int m1 = n + 1;
+    val = 0.0;
+    g[0] = g[1] = g[2] = 0.0;
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                const double v = f[(cx + a) + (int64_t)m1 * ((cy + b) + (int64_t)m1 * (cz + c))];
+                const double wx = a ? x : 1.0 - x, wy = b ? y : 1.0 - y, wz = c ? z : 1.0 - z;
+                const double dx = a ? 1.0 : -1.0, dy = b ? 1.0 : -1.0, dz = c ? 1.0 : -1.0;
+                val += wx * wy * wz * v;
+                g[0] += dx * wy * wz * v;
+                g[1] += wx * dy * wz * v;
+                g[2] += wx * wy * dz * v;
+            }
+    g[0] *= inv_h;
+    g[1] *= inv_h;
+    g[2] *= inv_h;
+}
+
+// Level-set field (value and physical gradient) at the reference point (x, y, z) of velocity cell (cx, cy, cz): the
+// Q1 interpolant of the level-set cell containing it, the velocity cell subdivided nsub times per direction (Sec.
+// 2.5; sub-cell floor(nsub t) clamped, so a point on a sub-cell face takes the upper sub-cell).
+__device__ __forceinline__ void ls_at(const double* __restrict__ f, const MeshArgs<double>& m, int cx, int cy, int cz,
+                                      double x, double y, double z, double& val, double g[3]) {
+    const int k = m.nsub;
+    if (k == 1) {
+        q1_at(f, m.n, cx, cy, cz, x, y, z, m.inv_h, val, g);
+        return;
+    }
+    const double s[3] = {x * k, y * k, z * k};
+    int sub[3];
+    double loc[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        int c = (int)floor(s[a]);
+        c = c < 0 ? 0 : (c > k - 1 ? k - 1 : c);
+        sub[a] = c;
+        loc[a] = s[a] - c;
+    }
+    q1_at(f, m.nl, k * cx + sub[0], k * cy + sub[1], k * cz + sub[2], loc[0], loc[1], loc[2], m.inv_h * k, val, g);
+}
+
 // Whether the corrected-strain term is active at a point (Sec. 2.4.2; zone gate or everywhere).
 __device__ __forceinline__ bool correction_on(const MeshArgs<double>& m, bool zone) {
     return m.stress != 0 && (m.corr_zone != 0 || zone);

@@ -360,10 +360,10 @@ template int launch_divergence<float>(evap_mesh*, const float*, const float*, fl
 // diagonal d of geo_schur_setup, at most cg_iters iterations (an inexact solve: the outer method is flexible).  The
 // CG runs in FP64; its operator is applied in FP32 (gradient, scaling by the FP32 Jacobi diagonal of A, divergence):
 // B and B^T are FP64-pipe bound at ~45 FMA per velocity point, and a preconditioner needs no FP64 operator.
-// Scratch: t32 [3 N_u] and pq32 [2 N_phi] floats.
+// Scratch: t32 [3 N_u] and pq32 [2 N_p] floats.
 int schur_apply(evap_mesh* h, const double* r, double* z, const double* d, float* t32, float* pq32, int cg_iters,
                 cudaStream_t st) {
-    const int64_t Nu3 = 3 * h->m.Nu, Np = h->m.Nphi;
+    const int64_t Nu3 = 3 * h->m.Nu, Np = h->m.Np;
     float* p32 = pq32;
     float* q32 = pq32 + Np;
     const float* diag32 = h->diag32;
@@ -383,9 +383,9 @@ int schur_apply(evap_mesh* h, const double* r, double* z, const double* d, float
 // g (the continuity right-hand side of the current fields), computed once per set_fields into h->cont_rhs.
 int continuity_rhs(evap_mesh* h, const double** g, cudaStream_t st) {
     const MeshArgs<double>& m = h->m;
-    if (!h->cont_rhs) EVAP_CUDA(cudaMalloc(&h->cont_rhs, m.Nphi * sizeof(double)));
+    if (!h->cont_rhs) EVAP_CUDA(cudaMalloc(&h->cont_rhs, m.Np * sizeof(double)));
     if (!h->cont_valid) {
-        EVAP_CUDA(cudaMemsetAsync(h->cont_rhs, 0, m.Nphi * sizeof(double), st));
+        EVAP_CUDA(cudaMemsetAsync(h->cont_rhs, 0, m.Np * sizeof(double), st));
         const unsigned grid = (unsigned)blocks_for(m.ncell, 128, 1LL << 40);
         if (m.P == 2)
             k_continuity_rhs<2><<<grid, 128, 0, st>>>(m, h->b, h->qc, h->cont_rhs);
@@ -406,7 +406,7 @@ int launch_saddle_apply(evap_mesh* h, const double* x, const double* p, double* 
     int rc = continuity_rhs(h, &g, st);
     if (rc) return rc;
     if ((rc = launch_momentum<double>(h, x, y, yp, st, true, p, lifted))) return rc;
-    k_add_vec<<<blocks_for(h->m.Nphi, 256, 152 * 8), 256, 0, st>>>(yp, g, h->m.Nphi);
+    k_add_vec<<<blocks_for(h->m.Np, 256, 152 * 8), 256, 0, st>>>(yp, g, h->m.Np);
     EVAP_CHECK_LAUNCH("saddle_add_g");
     return EVAP_OK;
 }

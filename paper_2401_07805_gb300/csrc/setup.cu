@@ -56,31 +56,6 @@ __global__ void k_prepare(double* phi, float* phi32, const double* __restrict__ 
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < Nu3; i += stride) u32[i] = (float)u[i];
 }
 
-// Q1 field value and physical gradient at reference point (t[qx], t[qy], t[qz]) of cell (cx, cy, cz).
-__device__ __forceinline__ void q1_at(const double* __restrict__ f, int n, int cx, int cy, int cz, double x, double y,
-                                      double z, double inv_h, double& val, double g[3]) {
-    const int m1 = n + 1;
-    val = 0.0;
-    g[0] = g[1] = g[2] = 0.0;
-#pragma unroll
-    for (int c = 0; c < 2; ++c)
-#pragma unroll
-        for (int b = 0; b < 2; ++b)
-#pragma unroll
-            for (int a = 0; a < 2; ++a) {
-                const double v = f[(cx + a) + (int64_t)m1 * ((cy + b) + (int64_t)m1 * (cz + c))];
-                const double wx = a ? x : 1.0 - x, wy = b ? y : 1.0 - y, wz = c ? z : 1.0 - z;
-                const double dx = a ? 1.0 : -1.0, dy = b ? 1.0 : -1.0, dz = c ? 1.0 : -1.0;
-                val += wx * wy * wz * v;
-                g[0] += dx * wy * wz * v;
-                g[1] += wx * dy * wz * v;
-                g[2] += wx * wy * dz * v;
-            }
-    g[0] *= inv_h;
-    g[1] *= inv_h;
-    g[2] *= inv_h;
-}
-
 // Cell classification: all quadrature points liquid (H = 1), all gas (H = 0), or a table cell (interface zone,
 // mixed phases, or correction applied everywhere).  Table cells get a slot by an atomic counter.
 __global__ void k_classify(MeshArgs<double> m, Basis<double> b, const double* __restrict__ phi, int8_t* code,
@@ -94,7 +69,7 @@ __global__ void k_classify(MeshArgs<double> m, Basis<double> b, const double* __
         for (int qy = 0; qy < b.Q; ++qy)
             for (int qx = 0; qx < b.Q; ++qx) {
                 double v, g[3];
-                q1_at(phi, n, cx, cy, cz, b.t[qx], b.t[qy], b.t[qz], m.inv_h, v, g);
+                ls_at(phi, m, cx, cy, cz, b.t[qx], b.t[qy], b.t[qz], v, g);
                 all_liq = all_liq && (v >= PHI_BAND);
                 all_gas = all_gas && (v <= -PHI_BAND);
             }
@@ -118,8 +93,8 @@ __global__ void k_fill_table(MeshArgs<double> m, Basis<double> b, const double* 
     const int n = m.n;
     const int cx = (int)(cell % n), cy = (int)((cell / n) % n), cz = (int)(cell / ((int64_t)n * n));
     double ph, g[3], md, gm[3];
-    q1_at(phi, n, cx, cy, cz, b.t[qx], b.t[qy], b.t[qz], m.inv_h, ph, g);
-    q1_at(mdot, n, cx, cy, cz, b.t[qx], b.t[qy], b.t[qz], m.inv_h, md, gm);
+    ls_at(phi, m, cx, cy, cz, b.t[qx], b.t[qy], b.t[qz], ph, g);
+    ls_at(mdot, m, cx, cy, cz, b.t[qx], b.t[qy], b.t[qz], md, gm);
     const Material mat = material(ph, g[0], g[1], g[2], m);
     const double z = correction_on(m, mat.zone) ? 1.0 : 0.0;
     const double vals[TAB_K] = {mat.rho, mat.mu, z * mat.n[0], z * mat.n[1], z * mat.n[2],
@@ -165,11 +140,15 @@ int launch_setup_coefficients(evap_mesh* h, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------------------------------------ transport velocity
-// Point evaluation in cell units s = y / h: cell = clamp(floor(s), 0, n - 1), trilinear phi, Q_p velocity.
+// Point evaluation in cell units s = y / h of the level-set mesh (m: the level-set view of the mesh, ls_args):
+// cell = clamp(floor(s), 0, n - 1), trilinear phi; the Q_p velocity from the velocity cell located the same way at
+// s / n_sub (nu cells per axis).
 struct PointEval {
     const double* phi;
     const double* u;
     MeshArgs<double> m;
+    int nu;           // velocity cells per axis
+    double inv_sub;   // 1 / n_sub
     double gl[MAXQ];  // Gauss-Lobatto support points of the velocity element
 
     __device__ void locate(const double s[3], int k[3], double xi[3]) const {
@@ -187,10 +166,17 @@ struct PointEval {
         locate(s, k, xi);
         q1_at(phi, m.n, k[0], k[1], k[2], xi[0], xi[1], xi[2], m.inv_h, val, g);
     }
-    __device__ void velocity(const double s[3], double out[3]) const {
+    __device__ void velocity(const double s_ls[3], double out[3]) const {
         int k[3];
         double xi[3];
-        locate(s, k, xi);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const double s = s_ls[a] * inv_sub;
+            int c = (int)floor(s);
+            c = c < 0 ? 0 : (c > nu - 1 ? nu - 1 : c);
+            k[a] = c;
+            xi[a] = s - c;
+        }
         const int P = m.P, Q = P + 1;
         double l[3][MAXQ];
         for (int d = 0; d < 3; ++d)
@@ -320,11 +306,20 @@ __global__ void k_transport_direct(PointEval e, const double* __restrict__ mdot,
         double nx[3] = {0.0, 0.0, 0.0};
         if (nrm * m.h > GRAD_TINY) { nx[0] = g[0] / nrm; nx[1] = g[1] / nrm; nx[2] = g[2] / nrm; }
         const Material mat = material(phx, 0.0, 0.0, 0.0, m);
-        const int64_t vn = (int64_t)(m.P * i) + (int64_t)m.M * ((int64_t)(m.P * j) + (int64_t)m.M * (m.P * k));
+        double uv[3];
+        if (m.nsub == 1 || m.nsub == m.P) {  // the node is a velocity node
+            const int st = m.nsub == 1 ? m.P : 1;
+            const int64_t vn = (int64_t)(st * i) + (int64_t)m.M * ((int64_t)(st * j) + (int64_t)m.M * (st * k));
+            uv[0] = e.u[vn];
+            uv[1] = e.u[m.Nu + vn];
+            uv[2] = e.u[2 * m.Nu + vn];
+        } else {
+            e.velocity(sx, uv);
+        }
         const double c = mdot[node] / mat.rho;
-        ug[node] = e.u[vn] + c * nx[0];
-        ug[m.Nphi + node] = e.u[m.Nu + vn] + c * nx[1];
-        ug[2 * m.Nphi + node] = e.u[2 * m.Nu + vn] + c * nx[2];
+        ug[node] = uv[0] + c * nx[0];
+        ug[m.Nphi + node] = uv[1] + c * nx[1];
+        ug[2 * m.Nphi + node] = uv[2] + c * nx[2];
         return;
     }
     if (in_projection_band(m.variant, phx)) {
@@ -496,7 +491,7 @@ __global__ void k_band_points(const int32_t* __restrict__ band, const int32_t* _
 }
 
 int launch_closest_points(evap_mesh* h, double* y, cudaStream_t s) {
-    const MeshArgs<double>& m = h->m;
+    const MeshArgs<double> m = ls_args<double>(h);
     k_node_points<<<blocks_for(m.Nphi, 256), 256, 0, s>>>(m.n, m.Nphi, m.h, y);
     EVAP_CHECK_LAUNCH("node_points");
     if (m.variant != 1) {
@@ -510,7 +505,9 @@ int launch_transport_velocity(evap_mesh* h, cudaStream_t s, const double* phi) {
     PointEval e;
     e.phi = phi ? phi : h->phi;
     e.u = h->u;
-    e.m = h->m;
+    e.m = ls_args<double>(h);
+    e.nu = h->m.n;
+    e.inv_sub = 1.0 / h->m.nsub;
     const int P = h->m.P;
     if (P == 2) {
         e.gl[0] = 0.0; e.gl[1] = 0.5; e.gl[2] = 1.0; e.gl[3] = 0.0;

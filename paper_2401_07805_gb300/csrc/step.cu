@@ -103,20 +103,20 @@ __global__ void k_add2(double* __restrict__ u, const double* __restrict__ du, in
 int time_step(evap_mesh* h, double* phi, double* u, double* p, const double* mdot, const double* u_prev,
               const double g[3], double alpha, int picard_iters, double picard_atol, int fp_iters, int reinit_steps,
               double ns_rtol, int* ns_iters, double* ns_relres, double* picard_res, cudaStream_t s) {
-    const int64_t Nu3 = 3 * h->m.Nu, Np = h->m.Nphi;
+    const int64_t Nu3 = 3 * h->m.Nu, Np = h->m.Np, Nl = h->m.Nphi;  // pressure, level-set nodes
     const bool newton = h->m.newton != 0;
-    // workspace: f, u* [3 N_u]; residual [3 N_u + N_phi]; Newton correction [3 N_u + N_phi]; advected level set
+    // workspace: f, u* [3 N_u]; residual [3 N_u + N_p]; Newton correction [3 N_u + N_p]; advected level set
     // [N_phi]; normal [3 N_phi]; scalar
     if (!h->step_ws) {
-        EVAP_CUDA(cudaMalloc(&h->step_ws, (4 * Nu3 + 6 * Np + 1) * sizeof(double)));
+        EVAP_CUDA(cudaMalloc(&h->step_ws, (4 * Nu3 + 2 * Np + 4 * Nl + 1) * sizeof(double)));
     }
     double* f = h->step_ws;
     double* ustar = f + Nu3;
     double* res = ustar + Nu3;
     double* corr = res + Nu3 + Np;
     double* adv = corr + Nu3 + Np;
-    double* nrm = adv + Np;
-    double* sq = nrm + 3 * Np;
+    double* nrm = adv + Nl;
+    double* sq = nrm + 3 * Nl;
     StepCoefficients cm(h, (u_prev ? 1.5 : 1.0) / h->m.dt);
     int rc = set_fields_flow(h, phi, u, mdot, s);  // the advection computes its own transport velocities
     if (rc) return rc;
@@ -189,13 +189,13 @@ int time_step(evap_mesh* h, double* phi, double* u, double* p, const double* mdo
     rc = geo_advect_levelset(h, adv, fp_iters, 0.0, nullptr, nullptr, nullptr, s);
     if (rc == EVAP_ENOTCONV) status = rc;
     else if (rc) return rc;
-    k_clamp_copy<<<blocks_for(Np, 256, 152 * 8), 256, 0, s>>>(adv, h->phi, Np);
+    k_clamp_copy<<<blocks_for(Nl, 256, 152 * 8), 256, 0, s>>>(adv, h->phi, Nl);
     EVAP_CHECK_LAUNCH("step_clamp");
     rc = geo_projected_normal(h, nrm, nullptr, nullptr, s);
     if (rc == EVAP_ENOTCONV) status = rc;
     else if (rc) return rc;
     if ((rc = evap_set_levelset_normal(h, nrm, s))) return rc;
-    EVAP_CUDA(cudaMemcpyAsync(phi, h->phi, Np * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    EVAP_CUDA(cudaMemcpyAsync(phi, h->phi, Nl * sizeof(double), cudaMemcpyDeviceToDevice, s));
     rc = geo_reinitialize(h, phi, reinit_steps, nullptr, nullptr, s);
     if (rc == EVAP_ENOTCONV) status = rc;
     else if (rc) return rc;

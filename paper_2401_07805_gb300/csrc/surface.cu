@@ -1,8 +1,9 @@
 // Surface-tension force of Eq. (surfaceTension) as the right-hand side of the momentum equation, FP64:
 //   b_(i,c) = sum_q W_q N_i(x_q) alpha kappa_h(x_q) n_c(x_q) delta(x_q) rho(x_q) c_rho,
 //   c_rho = (rho_g - rho_l) / (rho_l rho_g ln(rho_g / rho_l))  (the density-scaled delta, same section),
-// kappa_h and n_h the caller's Q1 curvature and normal fields (normalized at the point: n_h / |n_h|, zero where
-// |n_h| <= 1e-4), delta (Eq. delta) and the reciprocal rho (Eq. rhoEff) from the level set at the point.  One thread
+// kappa_h and n_h the caller's Q1 curvature and normal fields on the level-set mesh (normalized at the point:
+// n_h / |n_h|, zero where |n_h| <= 1e-4), delta (Eq. delta) and the reciprocal rho (Eq. rhoEff) from the level set at
+// the point.  One thread
 // per velocity quadrature point; the test with the Q_p shape functions runs as three transposed 1D sweeps
 // (z, y, x) through shared memory.  Dirichlet-constrained entries stay zero.
 #include <cmath>
@@ -31,25 +32,13 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
         cx = (int)(cell % n);
         cy = (int)((cell / n) % n);
         cz = (int)(cell / ((int64_t)n * n));
-        // Q1 fields at the point (trilinear weights of the 8 cell nodes)
-        const int64_t m1 = n + 1;
+        // level-set-space fields at the point (the Q1 interpolant of the level-set cell containing it)
         const double tx = bas.t[a], ty = bas.t[b], tz = bas.t[c];
-        double ph = 0.0, gp[3] = {0.0, 0.0, 0.0}, kq = 0.0, nh[3] = {0.0, 0.0, 0.0};
+        double ph, gp[3], kq, nh[3], gdum[3];
+        ls_at(phi, m, cx, cy, cz, tx, ty, tz, ph, gp);
+        ls_at(kappa, m, cx, cy, cz, tx, ty, tz, kq, gdum);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int ja = j & 1, jb = (j >> 1) & 1, jc = j >> 2;
-            const int64_t nd = (cx + ja) + m1 * ((cy + jb) + m1 * (cz + jc));
-            const double wx = ja ? tx : 1.0 - tx, wy = jb ? ty : 1.0 - ty, wz = jc ? tz : 1.0 - tz;
-            const double w = wx * wy * wz, pv = phi[nd];
-            ph += w * pv;
-            gp[0] += (ja ? 1.0 : -1.0) * wy * wz * pv;
-            gp[1] += wx * (jb ? 1.0 : -1.0) * wz * pv;
-            gp[2] += wx * wy * (jc ? 1.0 : -1.0) * pv;
-            kq += w * kappa[nd];
-#pragma unroll
-            for (int d = 0; d < 3; ++d) nh[d] += w * nf[d * m.Nphi + nd];
-        }
-        gp[0] *= m.inv_h; gp[1] *= m.inv_h; gp[2] *= m.inv_h;
+        for (int d = 0; d < 3; ++d) ls_at(nf + d * m.Nphi, m, cx, cy, cz, tx, ty, tz, nh[d], gdum);
         const Material mat = material(ph, gp[0], gp[1], gp[2], m);
         const double W = bas.w[a] * bas.w[b] * bas.w[c] * m.vol_w;
         const double nn = sqrt(nh[0] * nh[0] + nh[1] * nh[1] + nh[2] * nh[2]);

@@ -1,0 +1,154 @@
+"""GPU parity with the subdivided level-set mesh (n_sub = 2, Sec. 2.5: the level set and the mass flux are Q1 on the
+velocity mesh subdivided twice per direction; the pressure stays Q1 on the velocity mesh), through the C ABI,
+against the oracle (tests/test_oracle_nsub.py pins it).  Tolerances as in test_gpu_parity: FP64 applies and the
+adjoint 1e-12 relative l2, FP32 apply 2e-5, level-set operators 1e-12, transport velocity variant 1 to 1e-13 of the
+velocity scale and variants 2/3 at the closest-point iteration's resolution with every GPU point checked."""
+import numpy as np
+import pytest
+import torch
+
+import workloads
+from oracle import adjoint, fe, levelset, momentum, physics, step, transport
+
+pytestmark = [pytest.mark.gpu, pytest.mark.filterwarnings("ignore::scipy.sparse.SparseEfficiencyWarning")]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import os
+    import paper_2401_07805_gb300 as evap
+    from paper_2401_07805_gb300 import build
+    if not os.path.exists(evap.library_path()):
+        build.build()
+    evap.lib()
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def rel(a, b):
+    a = host(a) if isinstance(a, torch.Tensor) else a
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def make(wl):
+    from paper_2401_07805_gb300 import Operator
+    op = Operator(wl.n, wl.p, wl.L, dict(wl.params))
+    op.set_fields(cuda(wl.phi), cuda(wl.u0), cuda(wl.mdot))
+    return op, momentum.Problem.from_workload(wl)
+
+
+CASES = [(5, 2, "sphere", {}), (3, 3, "sphere", {}), (4, 2, "spheres", dict(corr_zone=1, newton=0)),
+         (6, 2, "slab", dict(stress=0))]
+
+
+@pytest.mark.parametrize("n,p,geom,over", CASES, ids=["q2_sphere", "q3_sphere", "q2_everywhere", "q2_slab_stokes"])
+def test_momentum_and_adjoint(n, p, geom, over):
+    wl = workloads.random_workload(n, p=p, seed=n + 3, geom=geom, dirichlet_faces=0x1D, n_sub=2, **over)
+    op, pb = make(wl)
+    assert op.n_phi == (2 * n + 1) ** 3 and op.n_p == (n + 1) ** 3
+    y, yp = op.apply_momentum(cuda(wl.x), prec=64, with_divergence=True)
+    yo, ypo = momentum.apply(pb, wl.x, with_divergence=True)
+    assert rel(y, yo) <= 1e-12 and rel(yp, ypo) <= 1e-12
+    x32 = wl.x.astype(np.float32)
+    y32, yp32 = op.apply_momentum(cuda(x32), prec=32, with_divergence=True)
+    yo32, ypo32 = momentum.apply(pb, x32.astype(np.float64), with_divergence=True)
+    assert rel(y32.double(), yo32) <= 2e-5 and rel(yp32.double(), ypo32) <= 2e-5
+    rng = np.random.default_rng(n)
+    w = rng.uniform(-1, 1, wl.x.shape)
+    wp = rng.uniform(-1, 1, op.n_p)
+    g = op.apply_adjoint(cuda(w), cuda(wl.x), cuda(wp))
+    gu, gphi, gm = adjoint.param_gradients(pb, wl.x, w, wp)
+    errs = dict(x=rel(g["x"], adjoint.grad_x(pb, w, wp)), u0=rel(g["u0"], gu), phi=rel(g["phi"], gphi),
+                mdot=rel(g["mdot"], gm))
+    print("n_sub 2 adjoint", n, p, geom, " ".join(f"{k} {v:.2e}" for k, v in errs.items()))
+    for k, v in errs.items():
+        assert v <= 1e-12, (k, v)
+
+
+def test_levelset_operators_on_the_fine_mesh():
+    n = 5
+    wl = workloads.random_workload(n, seed=2, geom="sphere", n_sub=2)
+    op, _ = make(wl)
+    mesh1 = fe.Mesh(2 * n, 1, 1.0)
+    rng = np.random.default_rng(3)
+    ug = rng.uniform(-1, 1, 3 * op.n_phi)
+    op.set_transport_velocity(cuda(ug))
+    x = rng.uniform(-1, 1, op.n_phi)
+    for mode in ("advect", "reinit", "reinit_rhs"):
+        xin = wl.phi if mode == "reinit_rhs" else x
+        assert rel(op.apply_levelset(cuda(xin), mode=mode), levelset.apply(mesh1, mode, xin, wl.phi, ug,
+                                                                           wl.params)) <= 1e-12
+
+
+@pytest.mark.parametrize("variant", [1, 2, 3])
+def test_transport_velocity(variant):
+    from test_gpu_parity import check_closest_points
+    n = 8
+    wl = workloads.random_workload(n, seed=5, geom="sphere", variant=variant, n_sub=2)
+    q1 = workloads.node_coords(2 * n, 1)
+    wl.phi = np.tanh(workloads.signed_distance("sphere", q1, radius=0.3) / (2 * wl.params["eps"]))
+    op, _ = make(wl)
+    ug, flags, nflag = op.transport_velocity()
+    ug = host(ug).reshape(3, -1)
+    flags = host(flags)
+    mesh = fe.Mesh(n, 2, 1.0, 2)
+    ugo, flo = transport.transport_velocity(mesh, wl.phi, wl.u0, wl.mdot, wl.params)
+    assert np.mean(flags == flo) >= 0.98
+    ok = (flags == 0) & (flo == 0)
+    scale = np.abs(ugo).max()
+    diff = np.abs(ug[:, ok] - ugo[:, ok]).max(axis=0)
+    if variant == 1:
+        assert nflag == 0 and diff.max() <= 1e-13 * scale
+    else:
+        assert np.mean(diff <= 1e-6 * scale) >= 0.99
+        check_closest_points(op, wl, np.arange(op.n_phi))
+
+
+def test_sampled_rows_64():
+    """The 64^3 four-sphere workload with its level set on the 128^3 level-set mesh (2.15 M level-set DoFs): sampled
+    momentum rows and divergence rows against the oracle, the adjoint's phi gradient on sampled fine nodes through the
+    oracle's directional derivative is covered by the small cases."""
+    wl = workloads.make_workload("spheres64", n_sub=2)
+    op, pb = make(wl)
+    y, yp = op.apply_momentum(cuda(wl.x), prec=64, with_divergence=True)
+    y = host(y).reshape(3, -1)
+    rng = np.random.default_rng(1)
+    m = wl.p * wl.n + 1
+    # half of the sampled velocity nodes in interface cells (a fine level-set node in the zone at that position)
+    zone = np.nonzero(np.abs(wl.phi) < physics.PHI_BAND)[0]
+    nodes = np.unique(np.concatenate([rng.integers(0, m ** 3, 48), rng.choice(zone, 48, replace=False),
+                                      [0, m - 1, m ** 3 - 1]]))
+    yo = momentum.apply_rows(pb, wl.x, nodes)
+    assert rel(y[:, nodes], yo) <= 1e-12
+    q1n = np.unique(rng.integers(0, op.n_p, 64))
+    assert rel(host(yp)[q1n], momentum.divergence_rows(pb, wl.x, q1n)) <= 1e-12
+    op.close()
+
+
+def test_time_step_against_oracle():
+    """One BDF1 step with the subdivided level set (velocity-pressure solve on the pressure space of the velocity
+    mesh, Algorithm 2 on the fine level-set mesh), against the oracle's step."""
+    n = 4
+    z = workloads.node_coords(2 * n, 1)[:, 2]
+    prm = workloads.default_params(n, 1.0, ratio=10.0, dirichlet_faces=0x1F, dt=0.02, newton=0, variant=1, n_sub=2)
+    prm["c_mass"] = 1.0 / prm["dt"]
+    prm["dtau"] = min(prm["eps"], prm["dt"])
+    phi = np.tanh((0.55 - z) / (2 * prm["eps"]))
+    mdot = np.full(phi.size, 50.0)
+    mesh = fe.Mesh(n, 2, 1.0, 2)
+    from paper_2401_07805_gb300 import Operator
+    op = Operator(n, 2, 1.0, dict(prm))
+    u = np.zeros(3 * mesh.n_u)
+    p = np.zeros(mesh.n_p)
+    gphi, gu, gp, info = op.time_step(cuda(phi), cuda(u), cuda(p), cuda(mdot), fp_iters=2, reinit_steps=2,
+                                      ns_rtol=1e-10)
+    assert info["converged"], info
+    ophi, ou, op_ = step.time_step(mesh, prm, phi, u, p, mdot, fp_iters=2, reinit_steps=2)
+    assert rel(gu, ou) < 1e-6 and rel(gp, op_) < 1e-5
+    assert np.abs(host(gphi) - ophi).max() < 1e-7

@@ -9,7 +9,9 @@ Layouts (identical on both sides):
   * Q_p velocity nodes: (p*n+1)^3 points per component, lexicographic index i + M*(j + M*k), i fastest, M = p*n+1;
     the 1D node positions inside a cell are the Gauss-Lobatto points of degree p.
   * Vector fields are component-major: v[c*N + idx].
-  * Q1 nodes (level set, mass flux, pressure space): (n+1)^3, same lexicographic order.
+  * Q1 nodes (level set, mass flux, pressure space): (n+1)^3, same lexicographic order; with params "n_sub" = 2 the
+    level set and the mass flux live on the Q1 nodes of the mesh subdivided twice per direction, (2n+1)^3 of them
+    (the pressure stays on the (n+1)^3 nodes).
 
 Workload recipes (domain [0, L]^3, L = 1, eps = one cell width h unless stated):
   * sphere:   d = R - |x - c|, R = 0.25, c = (0.5, 0.5, 0.5)                   (droplet, Sec. 3.2)
@@ -147,8 +149,8 @@ class Workload:
         return (self.p * self.n + 1) ** 3
 
     @property
-    def n_phi(self) -> int:
-        return (self.n + 1) ** 3
+    def n_phi(self) -> int:  # level-set nodes: Q1 on the mesh subdivided n_sub times (params "n_sub", default 1)
+        return (int(self.params.get("n_sub", 1)) * self.n + 1) ** 3
 
 
 def default_params(n: int, L: float = 1.0, ratio: float = 1e3, **over) -> dict:
@@ -189,7 +191,8 @@ def make_workload(name: str, n: int | None = None, p: int = 2, seed: int | None 
     n = cfg["n"]
     rng = np.random.default_rng(cfg["seed"])
     prm = default_params(n, L, ratio=cfg["ratio"], **over)
-    q1 = node_coords(n, 1, L)
+    ns = int(prm.get("n_sub", 1))
+    q1 = node_coords(ns * n, 1, L)  # level-set nodes
     d = signed_distance(cfg["geom"], q1, rng)
     phi = np.tanh(d / (2.0 * prm["eps"]))
     n_u = (p * n + 1) ** 3
@@ -206,7 +209,7 @@ def make_workload(name: str, n: int | None = None, p: int = 2, seed: int | None 
     else:
         u0 = fourier_velocity(n, p, rng, L=L)
         x = rng.uniform(-1.0, 1.0, 3 * n_u)
-    mdot = np.ones((n + 1) ** 3)
+    mdot = np.ones((ns * n + 1) ** 3)
     return Workload(n=n, p=p, L=L, params=prm, phi=phi, u0=u0, mdot=mdot, x=x, extra=extra)
 
 
@@ -215,11 +218,12 @@ def random_workload(n: int, p: int = 2, seed: int = 0, geom: str = "sphere", rat
     L = 1.0
     rng = np.random.default_rng(seed)
     prm = default_params(n, L, ratio=ratio, **over)
-    q1 = node_coords(n, 1, L)
+    ns = int(prm.get("n_sub", 1))
+    q1 = node_coords(ns * n, 1, L)  # level-set nodes
     d = signed_distance(geom, q1, rng)
     phi = np.tanh(d / (2.0 * prm["eps"]))
     n_u = (p * n + 1) ** 3
     u0 = rng.uniform(-1.0, 1.0, 3 * n_u)
     x = rng.uniform(-1.0, 1.0, 3 * n_u)
-    mdot = rng.uniform(0.5, 1.5, (n + 1) ** 3)
+    mdot = rng.uniform(0.5, 1.5, (ns * n + 1) ** 3)
     return Workload(n=n, p=p, L=L, params=prm, phi=phi, u0=u0, mdot=mdot, x=x)
