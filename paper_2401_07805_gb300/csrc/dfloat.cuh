@@ -14,6 +14,8 @@
 
 #include <cuda_runtime.h>
 
+#include "evap_internal.cuh"
+
 namespace evap {
 
 struct dfl {
@@ -87,5 +89,27 @@ __host__ __device__ __forceinline__ dfl df_from_double(double v) {
     return {hi, (float)(v - (double)hi)};
 }
 __device__ __forceinline__ double df_to_double(dfl a) { return (double)a.hi + (double)a.lo; }
+
+// Double-float copies of the 1D tables of the velocity element (built on the host from the FP64 basis).
+struct DfBasis {
+    dfl S[MAXQ][MAXQ];   // S[q][a] = l_a(t_q)
+    dfl Dc[MAXQ][MAXQ];  // physical collocation derivative Dc[q][r] / h
+    dfl N1[MAXQ][2];     // Q1 shape values at the Gauss points
+};
+DfBasis make_df_basis(const Basis<double>& b, double inv_h);
+
+__device__ __forceinline__ dfl ld_df(const float2* p) {
+    const float2 v = *p;
+    return {v.x, v.y};
+}
+
+// dot product of Q double-float constants with Q values of a shared buffer (stride in dfl entries)
+template <int Q>
+__device__ __forceinline__ dfl df_dot(const dfl* c, const dfl* v, int stride) {
+    dfl s = df_prod(c[0], v[0]);
+#pragma unroll
+    for (int k = 1; k < Q; ++k) df_fma(s, c[k], v[k * stride]);
+    return df_norm(s);
+}
 
 }  // namespace evap

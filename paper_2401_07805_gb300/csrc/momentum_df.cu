@@ -28,26 +28,6 @@
 
 namespace evap {
 
-struct DfBasis {
-    dfl S[MAXQ][MAXQ];   // S[q][a] = l_a(t_q)
-    dfl Dc[MAXQ][MAXQ];  // physical collocation derivative Dc[q][r] / h
-    dfl N1[MAXQ][2];     // Q1 shape values at the Gauss points
-};
-
-__device__ __forceinline__ dfl ld_df(const float2* p) {
-    const float2 v = *p;
-    return {v.x, v.y};
-}
-
-// dot product of Q double-float constants with Q values of the shared buffer (stride in dfl entries)
-template <int Q>
-__device__ __forceinline__ dfl df_dot(const dfl* c, const dfl* v, int stride) {
-    dfl s = df_prod(c[0], v[0]);
-#pragma unroll
-    for (int k = 1; k < Q; ++k) df_fma(s, c[k], v[k * stride]);
-    return df_norm(s);
-}
-
 // 8-byte asynchronous copy global -> shared (cp.async, completion tracked per thread by commit / wait groups)
 __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);

@@ -91,6 +91,8 @@ def test_transport_velocity(variant):
     from test_gpu_parity import check_closest_points
     n = 8
     wl = workloads.random_workload(n, seed=5, geom="sphere", variant=variant, n_sub=2)
+    wl.params["eps"] = 1.0 / (2 * n)  # one level-set cell: both ends of the zone (d = +-3 eps) exist in the box
+    wl.params["dtau"] = min(wl.params["eps"], wl.params["dt"])
     q1 = workloads.node_coords(2 * n, 1)
     wl.phi = np.tanh(workloads.signed_distance("sphere", q1, radius=0.3) / (2 * wl.params["eps"]))
     op, _ = make(wl)

@@ -204,17 +204,17 @@ def check_closest_points(op, wl, nodes, every_oracle=True, sample=None):
           points; the share of such nodes is at most the oracle's own share plus 1 %.
     (c) and (d) compare with the oracle's points on all band nodes, or on a random sample of ``sample`` of them."""
     from oracle import physics
-    mesh = fe.Mesh(wl.n, wl.p, wl.L)
     prm = wl.params
+    mesh = fe.Mesh(wl.n, wl.p, wl.L, int(prm.get("n_sub", 1)))
     variant = int(prm["variant"])
-    eps, h = prm["eps"], mesh.h
+    eps, h = prm["eps"], mesh.h / mesh.n_sub  # cell units of the level-set mesh
     d_t = 3.0 * eps if variant == 2 else -3.0 * eps
     rho_t = prm["rho_l"] if variant == 2 else prm["rho_g"]
     ug, flags, _ = op.transport_velocity()
     ug = ug.cpu().numpy().reshape(3, -1)
     flags = flags.cpu().numpy()
     y = op.closest_points().cpu().numpy() / h                      # cell units
-    m1 = mesh.n + 1
+    m1 = mesh.n * mesh.n_sub + 1
     phi = wl.phi
     if variant == 2:
         band = (-physics.PHI_GAS_BAND < phi) & (phi < physics.PHI_BAND)
