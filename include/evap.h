@@ -54,8 +54,10 @@ enum evap_status {
     EVAP_ENOTCONV = -3,    /* solve hit its iteration cap; the last iterate and its residual are returned */
     EVAP_ENOFIELDS = -4,   /* an apply or solve was called before evap_set_fields */
     EVAP_ENOMEM = -5,      /* device allocation failed */
-    EVAP_ENONFINITE = -6   /* input checks on (evap_set_checks): an input array holds a NaN or an Inf; the check's
+    EVAP_ENONFINITE = -6,  /* input checks on (evap_set_checks): an input array holds a NaN or an Inf; the check's
                               reduction was enqueued and synchronized, the call's own work was not */
+    EVAP_ETIMEOUT = -7     /* a bounded device-side wait gave up (the grid barrier of a single-launch solver): the
+                              kernel returned without finishing, the context stays usable, the output is undefined */
 };
 
 enum evap_levelset_mode {

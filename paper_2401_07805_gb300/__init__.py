@@ -29,7 +29,7 @@ _LOCK = threading.Lock()
 
 LEVELSET_MODES = {"advect": 0, "reinit": 1, "reinit_rhs": 2}
 STATUS = {0: "EVAP_OK", -1: "EVAP_EINVAL", -2: "EVAP_ECUDA", -3: "EVAP_ENOTCONV", -4: "EVAP_ENOFIELDS",
-          -5: "EVAP_ENOMEM", -6: "EVAP_ENONFINITE"}
+          -5: "EVAP_ENOMEM", -6: "EVAP_ENONFINITE", -7: "EVAP_ETIMEOUT"}
 
 # Exported symbols of include/evap.h with their ctypes signatures.
 _c_int, _c_dbl, _vp = ctypes.c_int, ctypes.c_double, ctypes.c_void_p

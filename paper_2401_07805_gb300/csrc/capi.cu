@@ -179,7 +179,7 @@ static int check_inputs(evap_mesh* h, const char* who, cudaStream_t s, std::init
 
 static void free_all(evap_mesh* h) {
     void* ptrs[] = {h->phi, h->u, h->mdot, h->u32, h->phi32, h->cell_code, h->table_index, h->table_count,
-                    h->table, h->table32, h->qc, h->qcdf, h->qc32, h->ugamma, h->ugamma32, h->cpp_flags, h->flag_count, h->band_list,
+                    h->table, h->table32, h->qc, h->qcdf, h->qc32, h->ugamma, h->ugamma32, h->ugammadf, h->cpp_flags, h->flag_count, h->band_list,
                     h->band_count, h->band_y, h->cpp_evals, h->ls_normal_store, h->ls_normal32_store, h->geo_ws, h->geo_elem, h->diag,
                     h->diag32, h->ws, h->red, h->cont_rhs, h->sd_ws, h->sd_red, h->nonfinite, h->step_ws,
                     h->tp_fac, h->tp_sigma, h->tp_sigma64};
@@ -201,6 +201,7 @@ const char* evap_status_string(int status) {
         case EVAP_ENOFIELDS: return "EVAP_ENOFIELDS";
         case EVAP_ENOMEM: return "EVAP_ENOMEM";
         case EVAP_ENONFINITE: return "EVAP_ENONFINITE";
+        case EVAP_ETIMEOUT: return "EVAP_ETIMEOUT";
         default: return "EVAP_UNKNOWN";
     }
 }
@@ -268,6 +269,7 @@ int evap_create_mesh(int n_cells, int degree_u, double L, const evap_params* prm
     al((void**)&h->table_count, sizeof(int32_t));
     al((void**)&h->ugamma, 3 * Np * sizeof(double));
     al((void**)&h->ugamma32, 3 * Np * sizeof(float));
+    al((void**)&h->ugammadf, 3 * Np * 2 * sizeof(float));
     al((void**)&h->cpp_flags, Np * sizeof(int32_t));
     al((void**)&h->flag_count, sizeof(unsigned long long));
     al((void**)&h->band_list, Np * sizeof(int32_t));
@@ -352,7 +354,7 @@ int evap_set_transport_velocity(evap_handle h, const double* u_gamma, void* stre
     int rc0 = check_inputs(h, "evap_set_transport_velocity", s, {{u_gamma, 3 * Np, false}});
     if (rc0) return rc0;
     EVAP_CUDA(cudaMemcpyAsync(h->ugamma, u_gamma, 3 * Np * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    int rc = launch_to_float(h->ugamma, h->ugamma32, 3 * Np, s);
+    int rc = refresh_ugamma_copies(h, s);
     if (rc) return rc;
     EVAP_CUDA(cudaMemsetAsync(h->cpp_flags, 0, Np * sizeof(int32_t), s));
     EVAP_CUDA(cudaMemsetAsync(h->flag_count, 0, sizeof(unsigned long long), s));

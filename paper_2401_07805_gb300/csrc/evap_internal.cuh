@@ -96,6 +96,7 @@ struct evap_mesh {
     // transport velocity
     double* ugamma = nullptr;
     float* ugamma32 = nullptr;
+    float* ugammadf = nullptr;  // double-float pairs (hi, lo) [3][N_phi] of u_Gamma for the double-float advection
     int32_t* cpp_flags = nullptr;
     unsigned long long* flag_count = nullptr;
     int32_t* band_list = nullptr;   // Q1 nodes that run the closest-point iteration
@@ -182,6 +183,8 @@ int launch_momentum32(evap_mesh* h, const float* x, float* y, float* yp, cudaStr
 int launch_momentum_df(evap_mesh* h, const MeshArgs<double>& m, const double* x, double* y, double* yp,
                        const double* p, cudaStream_t s);
 // u_Gamma of the mesh's level set, or of `phi` (a clamped Q1 field) when given, into h->ugamma / h->ugamma32.
+// The FP32 and double-float copies of h->ugamma (after every change of it).
+int refresh_ugamma_copies(evap_mesh* h, cudaStream_t s);
 int launch_transport_velocity(evap_mesh* h, cudaStream_t s, const double* phi = nullptr);
 // the points of the last transport-velocity pass, y [3 N_phi] physical coordinates (evap_get_closest_points)
 int launch_closest_points(evap_mesh* h, double* y, cudaStream_t s);

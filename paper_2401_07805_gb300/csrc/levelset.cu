@@ -4,7 +4,9 @@
 //   EVAP_REINIT_RHS  y_i = sum_q W [ N_i x / dtau + (grad N_i . n) (1 - x^2) / 2 ]        explicit compressive flux
 // with n the frozen normal at the quadrature point: grad phi / |grad phi| of the level set (Eq. normal_vector), or,
 // when a nodal normal field is set (e.g. the projected normal of Eq. normal_vector_regularized), its normalized
-// interpolant (ls_frozen_normal).
+// interpolant (ls_frozen_normal).  The FP64 advection runs in double-float arithmetic (k_levelset_advect_df: the FP64
+// pipe bounds the FP64 version); the reinitialization operators stay in FP64.
+#include "dfloat.cuh"
 #include "physics.cuh"
 
 namespace evap {
@@ -87,6 +89,72 @@ __global__ void __launch_bounds__(128) k_levelset(MeshArgs<T> m, Basis<T> bas, c
     for (int j = 0; j < 8; ++j) atomicAdd(&y[node[j]], out[j]);
 }
 
+// EVAP_ADVECT for the FP64 applies in double-float arithmetic (dfloat.cuh): the same sums with x converted per node,
+// u_Gamma read from its double-float copy, every product and sum on hi + lo FP32 pairs, the scatter in FP64.  The
+// shape values at the Gauss points are compile-time doubles split into pairs.
+__global__ void __launch_bounds__(128) k_levelset_advect_df(MeshArgs<double> m, dfl W, dfl thdt_ih,
+                                                            const float2* __restrict__ ug, const double* __restrict__ x,
+                                                            double* __restrict__ y) {
+    const int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (cell >= m.ncell) return;
+    const int n = m.n;
+    const int64_t m1 = n + 1;
+    const int cx = (int)(cell % n), cy = (int)((cell / n) % n), cz = (int)(cell / ((int64_t)n * n));
+    int64_t node[8];
+    dfl xv[8], uv[3][8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        node[j] = (cx + (j & 1)) + m1 * ((cy + ((j >> 1) & 1)) + m1 * (cz + (j >> 2)));
+        xv[j] = df_from_double(x[node[j]]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) uv[k][j] = ld_df(ug + k * m.Nphi + node[j]);
+    }
+    dfl out[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) out[j] = dfl{0.f, 0.f};
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int qx = q & 1, qy = (q >> 1) & 1, qz = q >> 2;
+        const double tx = g2_point(qx), ty = g2_point(qy), tz = g2_point(qz);
+        const double Nx[2] = {1.0 - tx, tx}, Ny[2] = {1.0 - ty, ty}, Nz[2] = {1.0 - tz, tz};
+        dfl N[8], dR[8][3];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int ja = j & 1, jb = (j >> 1) & 1, jc = j >> 2;
+            const double sx = ja ? 1.0 : -1.0, sy = jb ? 1.0 : -1.0, sz = jc ? 1.0 : -1.0;
+            N[j] = df_from_double(Nx[ja] * Ny[jb] * Nz[jc]);
+            dR[j][0] = df_from_double(sx * Ny[jb] * Nz[jc]);
+            dR[j][1] = df_from_double(Nx[ja] * sy * Nz[jc]);
+            dR[j][2] = df_from_double(Nx[ja] * Ny[jb] * sz);
+        }
+        dfl X = df_prod(N[0], xv[0]), GX[3], U[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            GX[d] = df_prod(dR[0][d], xv[0]);
+            U[d] = df_prod(N[0], uv[d][0]);
+        }
+#pragma unroll
+        for (int j = 1; j < 8; ++j) {
+            df_fma(X, N[j], xv[j]);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                df_fma(GX[d], dR[j][d], xv[j]);
+                df_fma(U[d], N[j], uv[d][j]);
+            }
+        }
+        dfl ug_gx = df_prod(df_norm(U[0]), df_norm(GX[0]));
+        df_fma(ug_gx, df_norm(U[1]), df_norm(GX[1]));
+        df_fma(ug_gx, df_norm(U[2]), df_norm(GX[2]));
+        dfl v = df_norm(X);
+        df_fma(v, thdt_ih, df_norm(ug_gx));
+        const dfl Fv = df_mul(W, df_norm(v));
+#pragma unroll
+        for (int j = 0; j < 8; ++j) df_fma(out[j], N[j], Fv);
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) atomicAdd(&y[node[j]], df_to_double(df_norm(out[j])));
+}
+
 template <typename T>
 int launch_levelset(evap_mesh* h, int mode, const T* x, T* y, cudaStream_t s) {
     const MeshArgs<T> m = ls_args<T>(h);  // Q1 on the level-set mesh
@@ -99,6 +167,16 @@ int launch_levelset(evap_mesh* h, int mode, const T* x, T* y, cudaStream_t s) {
     if (rc) return rc;
     const int threads = 128;
     const unsigned grid = (unsigned)((m.ncell + threads - 1) / threads);
+    if constexpr (sizeof(T) == 8) {
+        if (mode == EVAP_ADVECT) {  // FP64-accurate advection in double-float arithmetic
+            const dfl W = df_from_double(0.125 * (double)m.vol_w);  // 2-point Gauss weights 1/2 per direction
+            const dfl thdt_ih = df_from_double((double)m.theta * (double)m.dt * (double)m.inv_h);
+            k_levelset_advect_df<<<grid, threads, 0, s>>>(m, W, thdt_ih, (const float2*)h->ugammadf, (const double*)x,
+                                                          (double*)y);
+            EVAP_CHECK_LAUNCH("levelset_advect_df");
+            return EVAP_OK;
+        }
+    }
     if (mode == EVAP_ADVECT)
         k_levelset<T, EVAP_ADVECT><<<grid, threads, 0, s>>>(m, b, phi, nullptr, ug, x, y);
     else if (mode == EVAP_REINIT)

@@ -37,6 +37,23 @@ __global__ void k_to_double(const float* __restrict__ a, double* __restrict__ b,
         b[i] = (double)a[i];
 }
 
+// b = (float)a and c = (hi, lo) of a
+__global__ void k_to_float_df(const double* __restrict__ a, float* __restrict__ b, float2* __restrict__ c, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = a[i];
+        const float hi = (float)v;
+        b[i] = hi;
+        c[i] = make_float2(hi, (float)(v - (double)hi));
+    }
+}
+
+int refresh_ugamma_copies(evap_mesh* h, cudaStream_t s) {
+    const int64_t n = 3 * h->m.Nphi;
+    k_to_float_df<<<blocks_for(n, 256), 256, 0, s>>>(h->ugamma, h->ugamma32, (float2*)h->ugammadf, n);
+    EVAP_CHECK_LAUNCH("ugamma_copies");
+    return EVAP_OK;
+}
+
 int launch_to_double(const float* a, double* b, int64_t n, cudaStream_t s) {
     k_to_double<<<blocks_for(n, 256), 256, 0, s>>>(a, b, n);
     EVAP_CHECK_LAUNCH("to_double");
@@ -538,7 +555,7 @@ int launch_transport_velocity(evap_mesh* h, cudaStream_t s, const double* phi) {
                                                                                       h->ugamma);
         EVAP_CHECK_LAUNCH("transport_band_finish");
     }
-    return launch_to_float(h->ugamma, h->ugamma32, 3 * h->m.Nphi, s);
+    return refresh_ugamma_copies(h, s);
 }
 
 }  // namespace evap
