@@ -113,6 +113,8 @@ struct evap_mesh {
     double* geo_host = nullptr;
     double* geo_elem = nullptr;  // element matrices: reinitialization [36][ncell] or advection [64][ncell]
     int64_t geo_elem_len = 0;
+    void* geo_kry = nullptr;     // single-launch Krylov solvers: pair vectors, inverse diagonal, partials, barrier
+    size_t geo_kry_bytes = 0;
     // Jacobi diagonal and Krylov workspace (allocated by the first solve)
     double* diag = nullptr;
     float* diag32 = nullptr;
@@ -211,8 +213,6 @@ int geo_curvature(evap_mesh* h, const double* nf, double* kappa, int* iters, dou
 int geo_reinitialize(evap_mesh* h, double* psi, int steps, int* iters, double* last_change, cudaStream_t s);
 int geo_advect_levelset(evap_mesh* h, double* phi, int max_iters, double tol, int* fp_iters, int* lin_iters,
                         double* last_change, cudaStream_t s);
-// y = A x with the advection element matrices of the current fixed-point pass (h->geo_elem, [64][ncell]).
-int geo_advect_elem_apply(evap_mesh* h, const double* x, double* y, cudaStream_t s);
 // Jacobi diagonal (in the geometry workspace, valid until the next geometry call) for CG on the pressure Schur
 // approximation B diag(A)^(-1) B^T, and the Q1 CG engine of the geometry sub-solver for an arbitrary SPD apply.
 int geo_schur_setup(evap_mesh* h, double** diag, cudaStream_t s);
@@ -252,11 +252,6 @@ template <typename T>
 int tensor_prec_apply(evap_mesh* h, const T* v, T sc, T* t, T* z, T* w, cudaStream_t s);
 int solve_gmres(evap_mesh* h, const double* f, double* x, int mixed, int restart, double rtol, int max_iter,
                 int* iters, double* relres, cudaStream_t s);
-// GMRES(restart) with the Jacobi diagonal `diag` on the Q1 advection system (the EVAP_ADVECT operator with the mesh's
-// transport velocity, applied through the element matrices of the pass), x the initial guess and the solution;
-// stops at |r| <= max(rtol |b|, atol).  *iters is incremented by the operator applications; *relres = |r| / |b|.
-int solve_advect_gmres(evap_mesh* h, const double* b, const double* diag, double* x, int restart, double rtol,
-                       double atol, int max_iter, int* iters, double* relres, cudaStream_t s);
 // Flexible GMRES on the velocity-pressure system K [x; p] = [f; g] (see evap_solve_saddle); g is the continuity
 // right-hand side of the fields unless g_rhs is given.
 int solve_saddle(evap_mesh* h, const double* f, double* x, double* p, int restart, double rtol, int max_iter,

@@ -17,6 +17,7 @@
 #include <functional>
 
 #include "dfloat.cuh"
+#include "fused_krylov.cuh"
 #include "physics.cuh"
 
 namespace evap {
@@ -92,91 +93,37 @@ __global__ void k_helmholtz_diag(int n, double h, double c, double* __restrict__
 // The operators of the CG solves in double-float arithmetic (dfloat.cuh): GB300's FP64 pipe bounds the FP64 stencil
 // (93 FMA per node: ~40 us at 64^3), the FP32 pipe runs the same sums on hi + lo pairs several times faster.  The
 // CG keeps its direction p as pairs beside the FP64 copy, so the operators read their neighbours without converting.
-// Row `node` of (M + c K) x for one field, x given as pairs: the separable sums of k_helmholtz in double-float.
-// The 1D rows are h/6, 2h/3, h/6 (mass) and -1/h, 2/h, -1/h (stiffness), with h/3 and 1/h as the centre entry on a
-// boundary node, so only the three centre entries depend on the node.  Node indices fit 32 bits (checked on the host).
-struct HelmholtzDf {
-    int n;
-    dfl h6, h3, h3x2, ih, ih2, nih, c;
-    __device__ __forceinline__ dfl row(int64_t node, const float2* x) const {
-        const unsigned m1 = (unsigned)n + 1u, nd = (unsigned)node;
-        const unsigned t = nd / m1, i = nd - t * m1, kz = t / m1, j = t - kz * m1;
-        const bool xin = i > 0u && i < (unsigned)n, yin = j > 0u && j < (unsigned)n, zin = kz > 0u && kz < (unsigned)n;
-        const dfl mcx = xin ? h3x2 : h3, kcx = xin ? ih2 : ih;
-        const dfl mcy = yin ? h3x2 : h3, kcy = yin ? ih2 : ih;
-        const dfl mcz = zin ? h3x2 : h3, kcz = zin ? ih2 : ih;
-        dfl acc{0.f, 0.f};
+// The node stencil of sum_e A_e from symmetric element matrices stored as pairs, entry (a <= b) of cell e at
+// E[(b (b + 1) / 2 + a) ncell + e] (k_reinit_elem): per node, the rows of the (up to 8) cells around it summed by
+// offset in double-float; offsets without a cell get 0.  One thread per node, so no atomics and a fixed sum order.
+__global__ void __launch_bounds__(256) k_stencil_from_elem(int n, int64_t ncell, int64_t N, const float2* __restrict__ E,
+                                                           float2* __restrict__ C) {
+    const int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (node >= N) return;
+    const unsigned m1 = (unsigned)n + 1u, nd = (unsigned)node;
+    const unsigned t = nd / m1;
+    const int i = (int)(nd - t * m1), k = (int)(t / m1), j = (int)(t - (unsigned)k * m1);
+    dfl acc[27];
 #pragma unroll
-        for (int dz = -1; dz <= 1; ++dz) {
-            if ((dz < 0 && kz == 0u) || (dz > 0 && kz == (unsigned)n)) continue;
-            dfl smm{0.f, 0.f}, skm{0.f, 0.f}, smk{0.f, 0.f};
+    for (int s = 0; s < 27; ++s) acc[s] = dfl{0.f, 0.f};
 #pragma unroll
-            for (int dy = -1; dy <= 1; ++dy) {
-                if ((dy < 0 && j == 0u) || (dy > 0 && j == (unsigned)n)) continue;
-                const float2* xr = x + (nd + (unsigned)(dy * (int)m1 + dz * (int)(m1 * m1)));
-                dfl sm{0.f, 0.f}, sk{0.f, 0.f};
+    for (int cc = 0; cc < 8; ++cc) {
+        const int ox = cc & 1, oy = (cc >> 1) & 1, oz = cc >> 2;  // the node's corner in the cell
+        const int cx = i - ox, cy = j - oy, cz = k - oz;
+        if (cx < 0 || cy < 0 || cz < 0 || cx >= n || cy >= n || cz >= n) continue;
+        const int64_t cell = cx + (int64_t)n * (cy + (int64_t)n * cz);
+        const int li = ox + 2 * oy + 4 * oz;
 #pragma unroll
-                for (int dx = -1; dx <= 1; ++dx) {
-                    if ((dx < 0 && i == 0u) || (dx > 0 && i == (unsigned)n)) continue;
-                    const dfl v = ld_df(xr + dx);
-                    df_fma(sm, dx == 0 ? mcx : h6, v);
-                    df_fma(sk, dx == 0 ? kcx : nih, v);
-                }
-                sm = df_norm(sm);
-                sk = df_norm(sk);
-                const dfl my = dy == 0 ? mcy : h6, ky = dy == 0 ? kcy : nih;
-                df_fma(smm, my, sm);
-                df_fma(skm, my, sk);
-                df_fma(smk, ky, sm);
-            }
-            smm = df_norm(smm);
-            const dfl inner = df_add(smm, df_mul(c, df_add(df_norm(skm), df_norm(smk))));
-            df_fma(acc, dz == 0 ? mcz : h6, inner);
-            df_fma(acc, df_mul(c, dz == 0 ? kcz : nih), smm);
+        for (int lj = 0; lj < 8; ++lj) {
+            const int a = li < lj ? li : lj, b = li < lj ? lj : li;
+            const int sx = (lj & 1) - ox, sy = ((lj >> 1) & 1) - oy, sz = (lj >> 2) - oz;
+            const int s = 9 * (sz + 1) + 3 * (sy + 1) + (sx + 1);
+            acc[s] = df_add(acc[s], ld_df(E + (int64_t)(b * (b + 1) / 2 + a) * ncell + cell));
         }
-        return df_norm(acc);
     }
-};
-
-static HelmholtzDf helmholtz_df_op(int n, double h, double c) {
-    return HelmholtzDf{n,
-                       df_from_double(h / 6.0),
-                       df_from_double(h / 3.0),
-                       df_from_double(2.0 * h / 3.0),
-                       df_from_double(1.0 / h),
-                       df_from_double(2.0 / h),
-                       df_from_double(-1.0 / h),
-                       df_from_double(c)};
+#pragma unroll
+    for (int s = 0; s < 27; ++s) C[s * N + node] = make_float2(acc[s].hi, acc[s].lo);
 }
-
-// Row `node` of sum_e A_e x_e, gathered per node from the (up to 8) cells around it: each cell's 36 distinct
-// entries of its symmetric 8x8 matrix as pairs, layout [36][ncell] (k_reinit_elem), x as pairs.
-struct ElemGatherDf {
-    int n;
-    int64_t ncell;
-    const float2* E;
-    __device__ __forceinline__ dfl row(int64_t node, const float2* x) const {
-        const unsigned m1 = (unsigned)n + 1u, nd = (unsigned)node;
-        const unsigned t = nd / m1;
-        const int i = (int)(nd - t * m1), k = (int)(t / m1), j = (int)(t - (unsigned)k * m1);
-        dfl acc{0.f, 0.f};
-#pragma unroll
-        for (int cc = 0; cc < 8; ++cc) {
-            const int cx = i - 1 + (cc & 1), cy = j - 1 + ((cc >> 1) & 1), cz = k - 1 + (cc >> 2);
-            if (cx < 0 || cy < 0 || cz < 0 || cx >= n || cy >= n || cz >= n) continue;
-            const unsigned cell = (unsigned)cx + (unsigned)n * ((unsigned)cy + (unsigned)n * (unsigned)cz);
-            const int li = (i - cx) + 2 * (j - cy) + 4 * (k - cz);  // the node's local index in the cell
-            const unsigned n0 = (unsigned)cx + m1 * ((unsigned)cy + m1 * (unsigned)cz);
-#pragma unroll
-            for (int lj = 0; lj < 8; ++lj) {
-                const int a = li < lj ? li : lj, b = li < lj ? lj : li;
-                const unsigned nj = n0 + (unsigned)(lj & 1) + m1 * ((unsigned)((lj >> 1) & 1) + m1 * (unsigned)(lj >> 2));
-                df_fma(acc, ld_df(E + (int64_t)(b * (b + 1) / 2 + a) * ncell + cell), ld_df(x + nj));
-            }
-        }
-        return df_norm(acc);
-    }
-};
 
 
 
@@ -439,209 +386,12 @@ __global__ void __launch_bounds__(CG_THREADS) k_diff_norm(const double* __restri
     if (cg_finish2(cg_block_sum(s), 0.0, part, ticket, tot) && threadIdx.x == 0) *out = tot[0];
 }
 
-// ------------------------------------------------------------------------ fused conjugate gradients (one launch)
-// The whole Jacobi-preconditioned CG of a level-set solve in one cooperative launch: every block keeps its share of
-// the nodes for all iterations, and the grid meets at a barrier after the operator (p.q), after the update (r.z,
-// r.r) and after the new direction.  The scalar products are summed from the blocks' partials by every block in the
-// same order, so all blocks take the same alpha, beta and stopping decision and the result does not depend on the
-// arrival order.  The barrier's wait is bounded: a block that waits longer than CG_SPIN_LIMIT polls sets the error
-// word and every block returns at its next barrier (the host reports EVAP_ETIMEOUT); the cooperative launch makes
-// all blocks co-resident, so the limit is only a guard.
-constexpr int CGF_THREADS = 512;
-constexpr unsigned CG_SPIN_LIMIT = 1u << 22;  // polls of ~0.1 us: ~0.4 s
-
-struct GridBarrier {
-    unsigned count, gen;
-    int err, pad;
-};
-
-__device__ __forceinline__ bool grid_barrier(GridBarrier* gb) {
-    __shared__ int ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        volatile unsigned* gen = &gb->gen;
-        volatile int* err = &gb->err;
-        const unsigned g = *gen;  // cannot advance before this block arrives
-        __threadfence();
-        int good = 1;
-        if (atomicAdd(&gb->count, 1u) == gridDim.x - 1) {
-            atomicExch(&gb->count, 0u);
-            __threadfence();
-            atomicAdd(&gb->gen, 1u);
-        } else {
-            unsigned polls = 0;
-            while (*gen == g) {
-                if (*err || ++polls > CG_SPIN_LIMIT) {
-                    atomicExch(&gb->err, 1);
-                    good = 0;
-                    break;
-                }
-                __nanosleep(64);
-            }
-        }
-        __threadfence();  // the other blocks' writes before the barrier are visible after it
-        if (*err) good = 0;
-        ok = good;
-    }
-    __syncthreads();
-    return ok != 0;
-}
-
-__device__ __forceinline__ void st_df(float2* p, dfl a) { *p = make_float2(a.hi, a.lo); }
-
-// Block sum of a double-float value, valid in every thread (blockDim.x = CGF_THREADS); the warps' sums are added
-// in warp order, so the result does not depend on timing.
-__device__ __forceinline__ dfl cgf_block_sum(dfl v, float2* sh) {
-    v = df_norm(v);
-    for (int o = 16; o > 0; o >>= 1) {
-        const dfl u{__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};
-        v = df_add(v, u);
-    }
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) st_df(sh + wid, v);
-    __syncthreads();
-    dfl r = ld_df(sh);
-    for (int i = 1; i < CGF_THREADS / 32; ++i) r = df_add(r, ld_df(sh + i));
-    return r;
-}
-
-// Sum of the grid's partials part[0..gridDim.x), the same order in every block.
-__device__ __forceinline__ dfl cgf_grid_sum(const float2* part, float2* sh) {
-    dfl v{0.f, 0.f};
-    for (int i = threadIdx.x; i < (int)gridDim.x; i += CGF_THREADS) {
-        const float2 u = __ldcg(part + i);
-        v = df_add(v, dfl{u.x, u.y});
-    }
-    return cgf_block_sum(v, sh);
-}
-
-// 1/d for the Jacobi scaling: the FP32 reciprocal refined by one Newton step y + y (1 - d y) in double-float.
-__device__ __forceinline__ dfl df_recip(dfl d) {
-    const float y = 1.0f / d.hi;
-    const dfl e = df_sub(dfl{1.f, 0.f}, df_mul(d, dfl{y, 0.f}));
-    return df_add(dfl{y, 0.f}, df_mul(dfl{y, 0.f}, e));
-}
-
-// A x = b from x = 0 with the Jacobi diagonal dg, the vectors in double-float arithmetic (the FP64 pipe only
-// converts b and dg in and x out, and forms the scalars alpha, beta and |r| from the grid's sums).  Scratch vectors
-// of N pairs: xd (the iterate), dinv, r, p (read by op.row, which sees the other blocks' writes through the
-// barrier), q.  part holds 3 gridDim.x pairs.  out[0] = iterations, out[1] = |r|, out[2] = |r0|, written by block 0.
-template <class Op>
-__global__ void __launch_bounds__(CGF_THREADS) k_cg_fused(Op op, int64_t N, const double* __restrict__ b,
-                                                          const double* __restrict__ dg, double* x, float2* xd,
-                                                          float2* dinv, float2* r, float2* p, float2* q, double rtol,
-                                                          double atol, int max_iter, float2* part, GridBarrier* gb,
-                                                          double* out) {
-    __shared__ float2 sh[CGF_THREADS / 32];
-    __shared__ double s_rz, s_res, s_target;
-    __shared__ dfl s_alpha, s_beta;
-    __shared__ int s_go;
-    const int64_t i0 = blockIdx.x * (int64_t)CGF_THREADS + threadIdx.x, stride = (int64_t)gridDim.x * CGF_THREADS;
-    float2* part_pq = part;
-    float2* part_rz = part + gridDim.x;
-    float2* part_rr = part + 2 * gridDim.x;
-    dfl rz{0.f, 0.f}, rr{0.f, 0.f};
-    for (int64_t i = i0; i < N; i += stride) {
-        const dfl ri = df_from_double(b[i]), di = df_recip(df_from_double(dg[i])), zi = df_mul(ri, di);
-        st_df(xd + i, dfl{0.f, 0.f});
-        st_df(r + i, ri);
-        st_df(dinv + i, di);
-        st_df(p + i, zi);
-        df_fma(rz, ri, zi);
-        df_fma(rr, ri, ri);
-    }
-    rz = cgf_block_sum(rz, sh);
-    rr = cgf_block_sum(rr, sh);
-    if (threadIdx.x == 0) {
-        st_df(part_rz + blockIdx.x, rz);
-        st_df(part_rr + blockIdx.x, rr);
-    }
-    if (!grid_barrier(gb)) return;
-    rz = cgf_grid_sum(part_rz, sh);
-    rr = cgf_grid_sum(part_rr, sh);
-    double r0 = 0.0;
-    if (threadIdx.x == 0) {
-        s_rz = df_to_double(rz);
-        r0 = sqrt(fmax(df_to_double(rr), 0.0));
-        s_res = r0;
-        s_target = fmax(rtol * r0, atol);
-        s_go = s_res > s_target && max_iter > 0;
-    }
-    __syncthreads();
-    int it = 0;
-    while (s_go) {
-        dfl pq{0.f, 0.f};
-        for (int64_t i = i0; i < N; i += stride) {
-            const dfl qi = op.row(i, p);
-            st_df(q + i, qi);
-            df_fma(pq, ld_df(p + i), qi);
-        }
-        pq = cgf_block_sum(pq, sh);
-        if (threadIdx.x == 0) st_df(part_pq + blockIdx.x, pq);
-        if (!grid_barrier(gb)) return;
-        pq = cgf_grid_sum(part_pq, sh);
-        if (threadIdx.x == 0) {
-            const double pqd = df_to_double(pq);
-            s_alpha = df_from_double(pqd != 0.0 ? s_rz / pqd : 0.0);
-        }
-        __syncthreads();
-        const dfl alpha = s_alpha, nalpha = df_neg(s_alpha);
-        dfl rzn{0.f, 0.f};
-        rr = dfl{0.f, 0.f};
-        for (int64_t i = i0; i < N; i += stride) {
-            dfl xi = ld_df(xd + i), ri = ld_df(r + i);
-            df_fma(xi, alpha, ld_df(p + i));
-            df_fma(ri, nalpha, ld_df(q + i));
-            xi = df_norm(xi);
-            ri = df_norm(ri);
-            st_df(xd + i, xi);
-            st_df(r + i, ri);
-            const dfl zi = df_mul(ri, ld_df(dinv + i));
-            df_fma(rzn, ri, zi);
-            df_fma(rr, ri, ri);
-        }
-        rzn = cgf_block_sum(rzn, sh);
-        rr = cgf_block_sum(rr, sh);
-        if (threadIdx.x == 0) {
-            st_df(part_rz + blockIdx.x, rzn);
-            st_df(part_rr + blockIdx.x, rr);
-        }
-        if (!grid_barrier(gb)) return;
-        rzn = cgf_grid_sum(part_rz, sh);
-        rr = cgf_grid_sum(part_rr, sh);
-        ++it;
-        if (threadIdx.x == 0) {  // the same scalars and decision in every block
-            const double rznd = df_to_double(rzn);
-            s_beta = df_from_double(s_rz != 0.0 ? rznd / s_rz : 0.0);
-            s_rz = rznd;
-            s_res = sqrt(fmax(df_to_double(rr), 0.0));
-            s_go = s_res > s_target && it < max_iter;
-        }
-        __syncthreads();
-        if (!s_go) break;
-        const dfl beta = s_beta;
-        for (int64_t i = i0; i < N; i += stride) {
-            dfl pi = df_mul(ld_df(r + i), ld_df(dinv + i));
-            df_fma(pi, beta, ld_df(p + i));
-            st_df(p + i, df_norm(pi));
-        }
-        if (!grid_barrier(gb)) return;
-    }
-    for (int64_t i = i0; i < N; i += stride) x[i] = df_to_double(ld_df(xd + i));
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        out[0] = (double)it;
-        out[1] = s_res;
-        out[2] = r0;
-    }
-}
-
 // Workspace: r, z, p, q [N_phi] + partials + scalars + ticket (allocated once per mesh).
 static int geo_workspace(evap_mesh* h) {
     if (h->geo_ws) return EVAP_OK;
     const int64_t Np = h->m.Nphi;
     const size_t vec = ((size_t)Np * sizeof(double) + 255) & ~(size_t)255;
-    const size_t bytes = 10 * vec + (3 * CG_BLOCKS + 16) * sizeof(double) + 256;
+    const size_t bytes = 10 * vec + (2 * CG_BLOCKS + 8) * sizeof(double) + 256;
     EVAP_CUDA(cudaMalloc(&h->geo_ws, bytes));
     EVAP_CUDA(cudaMemset(h->geo_ws, 0, bytes));
     EVAP_CUDA(cudaMallocHost(&h->geo_host, 8 * sizeof(double)));
@@ -649,10 +399,8 @@ static int geo_workspace(evap_mesh* h) {
 }
 
 struct CgSpace {
-    double *r, *z, *p, *q, *b, *d, *t0, *t1, *t2, *part, *S, *out;
-    float2* pdf;  // the CG iterate as double-float pairs (the operators read it without converting)
+    double *r, *z, *p, *q, *b, *d, *t0, *t1, *t2, *part, *S;
     unsigned* ticket;
-    GridBarrier* gb;
 };
 
 static CgSpace cg_space(evap_mesh* h) {
@@ -669,12 +417,9 @@ static CgSpace cg_space(evap_mesh* h) {
     w.t0 = (double*)(base + 6 * vec);
     w.t1 = (double*)(base + 7 * vec);
     w.t2 = (double*)(base + 8 * vec);
-    w.pdf = (float2*)(base + 9 * vec);
     w.part = (double*)(base + 10 * vec);
-    w.S = w.part + 3 * CG_BLOCKS;
-    w.out = w.S + 8;
-    w.ticket = (unsigned*)(w.S + 12);
-    w.gb = (GridBarrier*)(w.S + 14);
+    w.S = w.part + 2 * CG_BLOCKS;
+    w.ticket = (unsigned*)(w.S + 8);
     return w;
 }
 
@@ -716,52 +461,139 @@ static int cg_solve(evap_mesh* h, Apply apply, const double* b, const double* d,
     return res <= target ? EVAP_OK : EVAP_ENOTCONV;
 }
 
-// The fused CG (k_cg_fused) on a level-set system: one cooperative launch and one host read per solve, stopping at
-// |r| <= max(rtol |r0|, atol) or after max_iter iterations.  The grid is as many blocks as can be co-resident (at
-// most 2 per SM and CG_BLOCKS in all).
+// Workspace of the single-launch solvers (fused_krylov.cuh): nvec pair vectors of N entries, the FP32 inverse
+// diagonal, (GM_MAX + 2) CG_BLOCKS partial pairs, the barrier, 4 result words and the Helmholtz coefficient table;
+// grown on demand, kept with the mesh.
+struct FusedSpace {
+    float2* vec;  // vector k at vec + k N
+    float* dinv;
+    float2* part;
+    GridBarrier* gb;
+    double* out;
+    float2* table;
+};
+
+static size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+static int fused_space(evap_mesh* h, int nvec, FusedSpace& f) {
+    const int64_t N = ls_args<double>(h).Nphi;
+    const size_t vbytes = al256((size_t)nvec * N * sizeof(float2)), dbytes = al256((size_t)N * sizeof(float));
+    const size_t pbytes = al256((size_t)(GM_MAX + 2) * CG_BLOCKS * sizeof(float2));
+    const size_t tail = al256(sizeof(GridBarrier) + 4 * sizeof(double)) + HelmholtzStencil::SMEM * sizeof(float2);
+    const size_t need = vbytes + dbytes + pbytes + tail;
+    if (h->geo_kry_bytes < need) {
+        if (h->geo_kry) cudaFree(h->geo_kry);
+        h->geo_kry = nullptr;
+        h->geo_kry_bytes = 0;
+        EVAP_CUDA(cudaMalloc(&h->geo_kry, need));
+        h->geo_kry_bytes = need;
+    }
+    char* base = (char*)h->geo_kry;
+    const size_t vcap = h->geo_kry_bytes - dbytes - pbytes - tail;  // the vectors keep whatever room they had
+    f.vec = (float2*)base;
+    f.dinv = (float*)(base + vcap);
+    f.part = (float2*)(base + vcap + dbytes);
+    f.gb = (GridBarrier*)(base + vcap + dbytes + pbytes);
+    f.out = (double*)(f.gb + 1);
+    f.table = (float2*)(base + vcap + dbytes + pbytes + al256(sizeof(GridBarrier) + 4 * sizeof(double)));
+    return EVAP_OK;
+}
+
+// Grid of a single-launch solver: as many blocks as can be co-resident, at most 2 per SM and CG_BLOCKS in all.
+template <class K>
+static int fused_grid(K kernel, size_t smem, int& G) {
+    int dev = 0, sms = 0, per_sm = 0;
+    EVAP_CUDA(cudaGetDevice(&dev));
+    EVAP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    EVAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, FK_THREADS, smem));
+    G = std::min(std::min(per_sm, 2) * sms, CG_BLOCKS);
+    if (G < 1) {
+        set_error("single-launch solver: no block of " + std::to_string(FK_THREADS) + " threads fits on an SM");
+        return EVAP_ECUDA;
+    }
+    return EVAP_OK;
+}
+
+// Reads the solver's result words and the barrier's error word after the launch (one synchronization).
+static int fused_result(evap_mesh* h, const FusedSpace& f, cudaStream_t s, double res[3]) {
+    double* hs = h->geo_host;
+    EVAP_CUDA(cudaMemcpyAsync(hs, f.out, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    EVAP_CUDA(cudaMemcpyAsync(hs + 4, f.gb, sizeof(GridBarrier), cudaMemcpyDeviceToHost, s));
+    EVAP_CUDA(cudaStreamSynchronize(s));
+    GridBarrier hb;
+    std::memcpy(&hb, hs + 4, sizeof(GridBarrier));
+    if (hb.err) {
+        set_error("single-launch solver: a block gave up waiting at the grid barrier");
+        return EVAP_ETIMEOUT;
+    }
+    res[0] = hs[0];
+    res[1] = hs[1];
+    res[2] = hs[2];
+    return EVAP_OK;
+}
+
+// The single-launch CG (k_cg_fused) on a level-set system: one cooperative launch and one host read per solve,
+// stopping at |r| <= max(rtol |r0|, atol) or after max_iter iterations.
 template <class Op>
 static int cg_solve_fused(evap_mesh* h, Op op, const double* b, const double* d, double* x, double rtol, double atol,
                           int max_iter, int* iters, double* relres, cudaStream_t s) {
     int64_t N = ls_args<double>(h).Nphi;
     if (N >= (int64_t)1 << 32) {
-        set_error("fused CG: the level-set operators index nodes with 32 bits");
+        set_error("single-launch CG: the level-set stencils index nodes with 32 bits");
         return EVAP_EINVAL;
     }
-    CgSpace w = cg_space(h);
-    int dev = 0, sms = 0, per_sm = 0;
-    EVAP_CUDA(cudaGetDevice(&dev));
-    EVAP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    EVAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg_fused<Op>, CGF_THREADS, 0));
-    const int G = std::min(std::min(per_sm, 2) * sms, CG_BLOCKS);
-    if (G < 1) {
-        set_error("fused CG: no block of " + std::to_string(CGF_THREADS) + " threads fits on an SM");
-        return EVAP_ECUDA;
-    }
-    EVAP_CUDA(cudaMemsetAsync(w.gb, 0, sizeof(GridBarrier), s));
+    FusedSpace f;
+    int rc = fused_space(h, 6, f), G = 0;
+    if (rc) return rc;
+    const size_t smem = Op::SMEM * sizeof(float2);
+    if ((rc = fused_grid(k_cg_fused<Op>, smem, G))) return rc;
+    EVAP_CUDA(cudaMemsetAsync(f.gb, 0, sizeof(GridBarrier), s));
     double* xx = x;
-    float2 *xd = (float2*)w.p, *dinv = (float2*)w.z, *r = (float2*)w.r, *p = w.pdf, *q = (float2*)w.q;
-    float2* part = (float2*)w.part;
-    double* out = w.out;
-    GridBarrier* gb = w.gb;
-    void* args[] = {&op, &N, &b, &d, &xx, &xd, &dinv, &r, &p, &q, &rtol, &atol, &max_iter, &part, &gb, &out};
-    EVAP_CUDA(cudaLaunchCooperativeKernel((const void*)k_cg_fused<Op>, dim3(G), dim3(CGF_THREADS), args, 0, s));
+    float2 *xd = f.vec, *r = f.vec + N, *u = f.vec + 2 * N, *p = f.vec + 3 * N, *sv = f.vec + 4 * N, *w = f.vec + 5 * N;
+    float* dinv = f.dinv;
+    float2* part = f.part;
+    GridBarrier* gb = f.gb;
+    double* out = f.out;
+    void* args[] = {&op, &N, &b, &d, &xx, &xd, &dinv, &r, &u, &p, &sv, &w, &rtol, &atol, &max_iter, &part, &gb, &out};
+    EVAP_CUDA(cudaLaunchCooperativeKernel((const void*)k_cg_fused<Op>, dim3(G), dim3(FK_THREADS), args, smem, s));
     EVAP_CHECK_LAUNCH("cg_fused");
-    double* hs = h->geo_host;
-    EVAP_CUDA(cudaMemcpyAsync(hs, w.out, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
-    EVAP_CUDA(cudaMemcpyAsync(hs + 4, w.gb, sizeof(GridBarrier), cudaMemcpyDeviceToHost, s));
-    EVAP_CUDA(cudaStreamSynchronize(s));
-    GridBarrier hb;
-    std::memcpy(&hb, hs + 4, sizeof(GridBarrier));
-    if (hb.err) {
-        set_error("fused CG: a block gave up waiting at the grid barrier");
-        return EVAP_ETIMEOUT;
-    }
-    const int it = (int)hs[0];
-    const double res = hs[1], r0 = hs[2];
-    if (iters) *iters += it;
-    const double rel = r0 > 0.0 ? res / r0 : 0.0;
+    double res[3];
+    if ((rc = fused_result(h, f, s, res))) return rc;
+    if (iters) *iters += (int)res[0];
+    const double rel = res[2] > 0.0 ? res[1] / res[2] : 0.0;
     if (relres && rel > *relres) *relres = rel;
-    return res <= std::max(rtol * r0, atol) ? EVAP_OK : EVAP_ENOTCONV;
+    return res[1] <= std::max(rtol * res[2], atol) ? EVAP_OK : EVAP_ENOTCONV;
+}
+
+// The single-launch GMRES(m) (k_gmres_fused) with the right Jacobi preconditioner, started from x.
+template <class Op>
+static int gmres_solve_fused(evap_mesh* h, Op op, int m, const double* b, const double* d, double* x, double rtol,
+                             double atol, int max_iter, double reorth, int* iters, double* relres, cudaStream_t s) {
+    int64_t N = ls_args<double>(h).Nphi;
+    if (N >= (int64_t)1 << 32 || m < 1 || m > GM_MAX) {
+        set_error("single-launch GMRES: restart must be in [1, 30] and node indices fit 32 bits");
+        return EVAP_EINVAL;
+    }
+    FusedSpace f;
+    int rc = fused_space(h, m + 3, f), G = 0;
+    if (rc) return rc;
+    const size_t smem = Op::SMEM * sizeof(float2);
+    if ((rc = fused_grid(k_gmres_fused<Op>, smem, G))) return rc;
+    EVAP_CUDA(cudaMemsetAsync(f.gb, 0, sizeof(GridBarrier), s));
+    double* xx = x;
+    float2 *xd = f.vec, *z = f.vec + N, *V = f.vec + 2 * N;
+    float* dinv = f.dinv;
+    float2* part = f.part;
+    GridBarrier* gb = f.gb;
+    double* out = f.out;
+    void* args[] = {&op, &N, &m, &b, &d, &xx, &xd, &dinv, &z, &V, &rtol, &atol, &max_iter, &reorth, &part, &gb, &out};
+    EVAP_CUDA(cudaLaunchCooperativeKernel((const void*)k_gmres_fused<Op>, dim3(G), dim3(FK_THREADS), args, smem, s));
+    EVAP_CHECK_LAUNCH("gmres_fused");
+    double res[3];
+    if ((rc = fused_result(h, f, s, res))) return rc;
+    if (iters) *iters += (int)res[0];
+    if (relres) *relres = res[2] > 0.0 ? res[1] / res[2] : 0.0;
+    return res[1] <= std::max(rtol * res[2], atol) ? EVAP_OK : EVAP_ENOTCONV;
 }
 
 static int helmholtz_apply(evap_mesh* h, double c, int ncomp, const double* x, double* y, cudaStream_t s) {
@@ -769,6 +601,20 @@ static int helmholtz_apply(evap_mesh* h, double c, int ncomp, const double* x, d
     const int64_t total = lm.Nphi * ncomp;
     k_helmholtz<<<blocks_for(total, 256, 152 * 16), 256, 0, s>>>(lm.n, lm.h, c, ncomp, x, y);
     EVAP_CHECK_LAUNCH("helmholtz");
+    return EVAP_OK;
+}
+
+// The Helmholtz stencil of the level-set mesh with its coefficient table uploaded to the workspace (the copy is
+// ordered before the solve on the stream; the host table is copied out before cudaMemcpyAsync returns).
+static int helmholtz_stencil(evap_mesh* h, const MeshArgs<double>& lm, double c, HelmholtzStencil& op, cudaStream_t s) {
+    FusedSpace f;
+    int rc = fused_space(h, 6, f);
+    if (rc) return rc;
+    float2 tab[HelmholtzStencil::SMEM];
+    helmholtz_table(lm.h, c, tab);
+    EVAP_CUDA(cudaMemcpyAsync(f.table, tab, sizeof(tab), cudaMemcpyHostToDevice, s));
+    op.n = lm.n;
+    op.table = f.table;
     return EVAP_OK;
 }
 
@@ -792,7 +638,8 @@ int geo_projected_normal(evap_mesh* h, double* n, int* iters, double* relres, cu
     if (iters) *iters = 0;
     if (relres) *relres = 0.0;
     int status = EVAP_OK;
-    const HelmholtzDf op = helmholtz_df_op(lm.n, lm.h, c);
+    HelmholtzStencil op;
+    if ((rc = helmholtz_stencil(h, lm, c, op, s))) return rc;
     for (int d = 0; d < 3; ++d) {
         rc = cg_solve_fused(h, op, w.t0 + d * stride, w.d, n + d * Np, 1e-12, 1e-20, 1000, iters, relres, s);
         if (rc == EVAP_ENOTCONV) status = rc;
@@ -815,17 +662,18 @@ int geo_curvature(evap_mesh* h, const double* nf, double* kappa, int* iters, dou
     EVAP_CHECK_LAUNCH("helmholtz_diag");
     if (iters) *iters = 0;
     if (relres) *relres = 0.0;
-    return cg_solve_fused(h, helmholtz_df_op(lm.n, lm.h, c), w.b, w.d, kappa, 1e-12, 1e-20, 1000, iters, relres, s);
+    HelmholtzStencil op;
+    if ((rc = helmholtz_stencil(h, lm, c, op, s))) return rc;
+    return cg_solve_fused(h, op, w.b, w.d, kappa, 1e-12, 1e-20, 1000, iters, relres, s);
 }
 
 // Element matrices of the reinitialization operator with the frozen normal, A_e[i][j] = sum_q W (N_i N_j / dtau +
-// eps (grad N_i . n)(grad N_j . n)): the normal does not change over the pseudo-time loop, so the 36 distinct entries
-// of each symmetric 8x8 matrix are formed once and every CG iteration is a per-cell matrix-vector product (64 FMA
-// instead of re-evaluating the 8 points).  Layout [36][ncell] (consecutive cells adjacent), entry k of (i <= j)
-// at k = j (j + 1) / 2 + i.
+// eps (grad N_i . n)(grad N_j . n)): the normal does not change over a pseudo-time step, so the 36 distinct entries
+// of each symmetric 8x8 matrix are formed once (in FP64, stored as pairs) and assembled into the 27-point node
+// stencil the CG iterations apply (k_stencil_from_elem).  Layout [36][ncell] (consecutive cells adjacent), entry k of
+// (i <= j) at k = j (j + 1) / 2 + i.
 __global__ void __launch_bounds__(128) k_reinit_elem(MeshArgs<double> m, Basis<double> bas, const double* __restrict__ phi,
-                                                     const double* __restrict__ nf, double* __restrict__ E,
-                                                     float2* __restrict__ Edf) {
+                                                     const double* __restrict__ nf, float2* __restrict__ Edf) {
     const int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (cell >= m.ncell) return;
     Q1Cell c;
@@ -855,16 +703,13 @@ __global__ void __launch_bounds__(128) k_reinit_elem(MeshArgs<double> m, Basis<d
     }
 #pragma unroll
     for (int k = 0; k < 36; ++k) {
-        E[k * m.ncell + cell] = a[k];
         const float hi = (float)a[k];
         Edf[k * m.ncell + cell] = make_float2(hi, (float)(a[k] - (double)hi));
     }
 }
 
-// Grows the element-matrix buffer of the mesh to `entries` per cell.
-static int geo_elem_reserve(evap_mesh* h, int entries) {
-    const MeshArgs<double> lm = ls_args<double>(h);  // the level-set mesh
-    const int64_t need = entries * lm.ncell;
+// Grows the element-matrix buffer of the mesh to `need` 8-byte words.
+static int geo_elem_reserve(evap_mesh* h, int64_t need) {
     if (h->geo_elem_len >= need) return EVAP_OK;
     if (h->geo_elem) cudaFree(h->geo_elem);
     h->geo_elem = nullptr;
@@ -884,15 +729,18 @@ int geo_reinitialize(evap_mesh* h, double* psi, int steps, int* iters, double* l
     EVAP_CUDA(cudaMemsetAsync(w.d, 0, Np * sizeof(double), s));
     k_reinit_diag<<<blocks_for(lm.ncell, 128, 1LL << 40), 128, 0, s>>>(lm, h->b, h->phi, h->ls_normal, w.d);
     EVAP_CHECK_LAUNCH("reinit_diag");
-    if ((rc = geo_elem_reserve(h, 36 + 36))) return rc;  // 36 FP64 entries per cell, then their 36 pairs
-    float2* Edf = reinterpret_cast<float2*>(h->geo_elem + 36 * lm.ncell);
+    if ((rc = geo_elem_reserve(h, 36 * lm.ncell + 27 * Np))) return rc;  // 36 pairs per cell, then 27 per node
+    float2* Edf = reinterpret_cast<float2*>(h->geo_elem);
+    float2* Cn = Edf + 36 * lm.ncell;
     const unsigned gc = (unsigned)blocks_for(lm.ncell, 128, 1LL << 40);
-    k_reinit_elem<<<gc, 128, 0, s>>>(lm, h->b, h->phi, h->ls_normal, h->geo_elem, Edf);
+    k_reinit_elem<<<gc, 128, 0, s>>>(lm, h->b, h->phi, h->ls_normal, Edf);
     EVAP_CHECK_LAUNCH("reinit_elem");
+    k_stencil_from_elem<<<(unsigned)blocks_for(Np, 256, 1LL << 40), 256, 0, s>>>(lm.n, lm.ncell, Np, Edf, Cn);
+    EVAP_CHECK_LAUNCH("reinit_stencil");
     if (iters) *iters = 0;
     double rel = 0.0;
     int status = EVAP_OK;
-    const ElemGatherDf op{lm.n, lm.ncell, Edf};  // q = sum_e A_e p_e, gathered per node in double-float
+    const NodeStencil op{lm.n, Np, Cn};  // q = sum_e A_e p_e, assembled per node
     for (int k = 0; k < steps; ++k) {
         rc = launch_levelset<double>(h, EVAP_REINIT_RHS, psi, w.b, s);
         if (rc) return rc;
@@ -977,33 +825,37 @@ __global__ void __launch_bounds__(128) k_advect_elem(MeshArgs<double> m, const d
     }
 }
 
-// y += A_e x_e over all cells for general 8x8 element matrices [64][ncell] (y zeroed by the caller).
-__global__ void __launch_bounds__(128) k_elem_apply_full(int n, int64_t ncell, const double* __restrict__ E,
-                                                         const double* __restrict__ x, double* __restrict__ y) {
-    const int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (cell >= ncell) return;
-    Q1Cell c;
-    int cx, cy, cz;
-    q1_cell_nodes(cell, n, c, cx, cy, cz);
-    double xv[8];
+// The node stencil of sum_e A_e from general element matrices in FP64, entry (i, j) of cell e at E[(8 i + j) ncell + e]
+// (k_advect_elem): per node, the rows of the (up to 8) cells around it summed by offset in FP64, then stored as pairs
+// C[s N + node]; offsets without a cell get 0.  One thread per node: no atomics, a fixed sum order.
+__global__ void __launch_bounds__(128) k_stencil_from_elem_full(int n, int64_t ncell, int64_t N,
+                                                                const double* __restrict__ E, float2* __restrict__ C) {
+    const int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (node >= N) return;
+    const unsigned m1 = (unsigned)n + 1u, nd = (unsigned)node;
+    const unsigned t = nd / m1;
+    const int i = (int)(nd - t * m1), k = (int)(t / m1), j = (int)(t - (unsigned)k * m1);
+    double acc[27];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) xv[j] = x[c.node[j]];
+    for (int q = 0; q < 27; ++q) acc[q] = 0.0;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        double v = 0.0;
+    for (int cc = 0; cc < 8; ++cc) {
+        const int ox = cc & 1, oy = (cc >> 1) & 1, oz = cc >> 2;  // the node's corner in the cell
+        const int cx = i - ox, cy = j - oy, cz = k - oz;
+        if (cx < 0 || cy < 0 || cz < 0 || cx >= n || cy >= n || cz >= n) continue;
+        const int64_t cell = cx + (int64_t)n * (cy + (int64_t)n * cz);
+        const int li = ox + 2 * oy + 4 * oz;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) v += E[(i * 8 + j) * ncell + cell] * xv[j];
-        atomicAdd(&y[c.node[i]], v);
+        for (int lj = 0; lj < 8; ++lj) {
+            const int sx = (lj & 1) - ox, sy = ((lj >> 1) & 1) - oy, sz = (lj >> 2) - oz;
+            acc[9 * (sz + 1) + 3 * (sy + 1) + (sx + 1)] += E[(int64_t)(8 * li + lj) * ncell + cell];
+        }
     }
-}
-
-int geo_advect_elem_apply(evap_mesh* h, const double* x, double* y, cudaStream_t s) {
-    const MeshArgs<double> lm = ls_args<double>(h);  // the level-set mesh
-    EVAP_CUDA(cudaMemsetAsync(y, 0, lm.Nphi * sizeof(double), s));
-    k_elem_apply_full<<<(unsigned)blocks_for(lm.ncell, 128, 1LL << 40), 128, 0, s>>>(lm.n, lm.ncell,
-                                                                                      h->geo_elem, x, y);
-    EVAP_CHECK_LAUNCH("advect_apply");
-    return EVAP_OK;
+#pragma unroll
+    for (int q = 0; q < 27; ++q) {
+        const float hi = (float)acc[q];
+        C[q * N + node] = make_float2(hi, (float)(acc[q] - (double)hi));
+    }
 }
 
 // b = M phi^n / theta - (1 - theta) / theta A phi^n  (= (M - (1 - theta) dt C) phi^n / theta with A = M + theta dt C)
@@ -1029,6 +881,7 @@ __global__ void k_clamp_unit(const double* __restrict__ phi, double* __restrict_
 // the relative one taken against the residual of a zero start).  Stops after max_iters passes or once
 // |phi^(k+1) - phi^(k)|_2 <= tol.
 constexpr int ADVECT_RESTART = 30;
+constexpr double ADVECT_REORTH = 1e-2;  // second Gram-Schmidt pass where the first one cancelled 99 % of |w|^2
 int geo_advect_levelset(evap_mesh* h, double* phi, int max_iters, double tol, int* fp_iters, int* lin_iters,
                         double* last_change, cudaStream_t s) {
     const MeshArgs<double> lm = ls_args<double>(h);  // the level-set mesh
@@ -1038,7 +891,12 @@ int geo_advect_levelset(evap_mesh* h, double* phi, int max_iters, double tol, in
     const int64_t Np = lm.Nphi;
     const int G = blocks_for(Np, 256, 152 * 8);
     const unsigned gc = (unsigned)blocks_for(lm.ncell, 128, 1LL << 40);
-    if ((rc = geo_elem_reserve(h, 64))) return rc;
+    if ((rc = geo_elem_reserve(h, 64 * lm.ncell + 27 * Np))) return rc;  // FP64 element matrices, node stencil
+    float2* Cn = reinterpret_cast<float2*>(h->geo_elem + 64 * lm.ncell);
+    if (Np >= (int64_t)1 << 32) {
+        set_error("level-set advection: the node stencil indexes nodes with 32 bits");
+        return EVAP_EINVAL;
+    }
     EVAP_CUDA(cudaMemcpyAsync(phi, h->phi, Np * sizeof(double), cudaMemcpyDeviceToDevice, s));
     int k = 0, lin = 0, status = EVAP_OK;
     double change = 0.0;
@@ -1057,9 +915,13 @@ int geo_advect_levelset(evap_mesh* h, double* phi, int max_iters, double tol, in
         EVAP_CUDA(cudaMemsetAsync(w.d, 0, Np * sizeof(double), s));
         k_advect_elem<<<gc, 128, 0, s>>>(lm, h->ugamma, h->geo_elem, w.d);
         EVAP_CHECK_LAUNCH("advect_elem");
+        k_stencil_from_elem_full<<<(unsigned)blocks_for(Np, 128, 1LL << 40), 128, 0, s>>>(lm.n, lm.ncell, Np,
+                                                                                         h->geo_elem, Cn);
+        EVAP_CHECK_LAUNCH("advect_stencil");
         EVAP_CUDA(cudaMemcpyAsync(w.r, phi, Np * sizeof(double), cudaMemcpyDeviceToDevice, s));
         double rel = 0.0;
-        rc = solve_advect_gmres(h, w.b, w.d, phi, ADVECT_RESTART, 1e-12, 1e-20, 1000, &lin, &rel, s);
+        rc = gmres_solve_fused(h, NodeStencil{lm.n, Np, Cn}, ADVECT_RESTART, w.b, w.d, phi, 1e-12, 1e-20, 1000,
+                               ADVECT_REORTH, &lin, &rel, s);
         if (rc == EVAP_ENOTCONV) status = rc;
         else if (rc) return rc;
         ++k;

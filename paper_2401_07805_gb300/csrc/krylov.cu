@@ -307,14 +307,6 @@ __global__ void __launch_bounds__(256) k_precond_init(int M, int64_t Nu, unsigne
     }
 }
 
-// z = sc v / diag for an operator without constrained rows (the Q1 advection operator zero-fills its output).
-template <typename T>
-__global__ void k_precond_plain(const T* __restrict__ v, const T* __restrict__ diag, T sc, T* __restrict__ z,
-                                int64_t N) {
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x)
-        z[k] = sc * v[k] / diag[k];
-}
-
 // x += diag^{-1} sum_i y[i] V_i   (x may be unaligned caller memory: scalar)
 template <typename T>
 __global__ void k_update(const T* __restrict__ V, int64_t ld, const double* __restrict__ y, int nv,
@@ -375,14 +367,11 @@ __global__ void k_refine(double* x, const float* __restrict__ d, const double* _
 // solve re-orthogonalizes only after a cancellation of 99 % of |w|^2 (the mass-dominated operator makes A v nearly
 // parallel to v, so the DGKS test fires on almost every step; measured on the 64^3 and 96^3 workloads the second
 // pass changed neither the iteration count nor the accuracy of the refined solution, and cost ~25 % of the solve;
-// the outer FP64 residual is checked regardless).  The Q1 advection solve (FP64, Crank-Nicolson operator dominated by
-// the mass matrix) takes the same 1e-2: with 1/2 it re-orthogonalized every step; with 1e-2 the 64^3 fixed point
-// (3 passes) needed the same 114 applications, ended at the same iterate and took 28.2 ms instead of 34.6 ms.
+// the outer FP64 residual is checked regardless).
 constexpr double REORTH64 = 0.5;
 constexpr double REORTH32 = 1e-2;
-// the operator of a solve: the momentum system, or the Q1 advection with the element matrices of the current
-// fixed-point pass (FP64 only)
-enum { OP_MOMENTUM = 0, OP_ADVECT = 1 };
+// the operator of a solve (the momentum system; the level-set solves run in fused_krylov.cuh)
+enum { OP_MOMENTUM = 0 };
 struct Ctx {
     evap_mesh* h;
     int op;
@@ -400,8 +389,6 @@ struct Ctx {
 
 template <typename T>
 static int apply_op(Ctx& c, const T* x, T* y) {
-    if constexpr (sizeof(T) == 8)
-        if (c.op == OP_ADVECT) return geo_advect_elem_apply(c.h, x, y, c.s);
     return launch_momentum<T>(c.h, x, y, (T*)nullptr, c.s);
 }
 
@@ -490,24 +477,15 @@ static int gmres(Ctx& c, int m, const T* b, T* x, bool x_zero, const T* diag, T*
         for (; j < m; ++j) {
             T* Vj = V + (int64_t)j * c.ld;
             T* Wn = V + (int64_t)(j + 1) * c.ld;  // A z goes straight into the next basis slot
-            if (c.op == OP_ADVECT) {
-                k_precond_plain<T><<<G, 256, 0, c.s>>>(Vj, diag, (T)sc[j], z, N);
-                EVAP_CHECK_LAUNCH("precond");
-                if ((rc = apply_op<T>(c, z, Wn))) return rc;
+            if (c.tp) {  // z = P (sc V_j), Wn initialized on the Dirichlet rows; w is the sweeps' scratch
+                if ((rc = tensor_prec_apply<T>(c.h, Vj, (T)sc[j], w, z, Wn, c.s))) return rc;
             } else {
-                bool done = false;
-                if (c.tp) {  // z = P (sc V_j), Wn initialized on the Dirichlet rows; w is the sweeps' scratch
-                    if ((rc = tensor_prec_apply<T>(c.h, Vj, (T)sc[j], w, z, Wn, c.s))) return rc;
-                    done = true;
-                }
-                if (!done) {
-                    const int M = c.h->m.M;
-                    const unsigned gl = (unsigned)std::min<int64_t>((3 * (int64_t)M * M + 7) / 8, 152 * 16);
-                    k_precond_init<T><<<gl, 256, 0, c.s>>>(M, c.h->m.Nu, c.h->m.faces, Vj, diag, (T)sc[j], z, Wn);
-                    EVAP_CHECK_LAUNCH("precond");
-                }
-                if ((rc = launch_momentum<T>(c.h, z, Wn, (T*)nullptr, c.s, false))) return rc;
+                const int M = c.h->m.M;
+                const unsigned gl = (unsigned)std::min<int64_t>((3 * (int64_t)M * M + 7) / 8, 152 * 16);
+                k_precond_init<T><<<gl, 256, 0, c.s>>>(M, c.h->m.Nu, c.h->m.faces, Vj, diag, (T)sc[j], z, Wn);
+                EVAP_CHECK_LAUNCH("precond");
             }
+            if ((rc = launch_momentum<T>(c.h, z, Wn, (T*)nullptr, c.s, false))) return rc;
             ++used;
             const int nv = j + 1;
             double* col = &H[(size_t)j * (m + 1)];
@@ -518,7 +496,7 @@ static int gmres(Ctx& c, int m, const T* b, T* x, bool x_zero, const T* diag, T*
             for (int i = 0; i < nv; ++i) col[i] = sc[i] * c.hcol[i];
             double after = c.hcol[m + 2];
             const double before = c.hcol[nv];
-            if (after < ((sizeof(T) == 4 || c.op == OP_ADVECT) ? REORTH32 : REORTH64) * before) {  // cancellation: re-orthogonalize once
+            if (after < (sizeof(T) == 4 ? REORTH32 : REORTH64) * before) {  // cancellation: re-orthogonalize once
                 if ((rc = cgs_pass<T>(c, V, Wn, nv, c.dcol + (m + 2), false))) return rc;
                 EVAP_CUDA(cudaMemcpyAsync(c.hcol, c.dcol + (m + 2), (size_t)nv * sizeof(double), cudaMemcpyDeviceToHost, c.s));
                 EVAP_CUDA(cudaMemcpyAsync(c.hcol + m + 2, c.dnorm, sizeof(double), cudaMemcpyDeviceToHost, c.s));
@@ -703,31 +681,6 @@ int solve_gmres(evap_mesh* h, const double* f, double* x, int mixed, int m, doub
     if (iters) *iters = used;
     if (relres) *relres = res / fn;
     return res <= rtol * fn ? EVAP_OK : EVAP_ENOTCONV;
-}
-
-int solve_advect_gmres(evap_mesh* h, const double* b, const double* diag, double* x, int m, double rtol, double atol,
-                       int max_iter, int* iters, double* relres, cudaStream_t s) {
-    const int64_t N = h->m.Nphi;
-    const int64_t ld = (N + 63) / 64 * 64;
-    const size_t dV = al256((size_t)(m + 1) * ld * sizeof(double)), dN = al256((size_t)ld * sizeof(double));
-    Ctx c;
-    int rc = prepare(h, OP_ADVECT, m, N, ld, dV + dN, s, c);
-    if (rc) return rc;
-    double* V = (double*)h->ws;
-    double* z = (double*)((char*)h->ws + dV);
-    // the relative target is taken against |b|, the residual of a zero start, whatever the start x: it stays above
-    // the rounding level of the residual when x is already (nearly) the solution
-    if ((rc = norm2_dev<double>(c, b, c.dnorm))) return rc;
-    if ((rc = fetch(c, c.dnorm, 1, c.hcol))) return rc;
-    const double bn = std::sqrt(c.hcol[0]);
-    const double target = std::max(rtol * bn, atol);
-    int its = 0;
-    double res = 0.0;
-    if ((rc = gmres<double>(c, m, b, x, false, diag, V, nullptr, z, target, max_iter, &its, &res))) return rc;
-    EVAP_CUDA(cudaStreamSynchronize(s));
-    if (iters) *iters += its;
-    if (relres) *relres = bn > 0.0 ? res / bn : 0.0;
-    return res <= target ? EVAP_OK : EVAP_ENOTCONV;
 }
 
 // ------------------------------------------------------------ velocity-pressure system: flexible GMRES

@@ -12,7 +12,7 @@ import pytest
 import torch
 
 import workloads
-from oracle import fe, step
+from oracle import fe, geometry, step
 
 pytestmark = [pytest.mark.gpu, pytest.mark.filterwarnings("ignore::scipy.sparse.SparseEfficiencyWarning")]
 
@@ -248,6 +248,28 @@ def test_time_step_preserves_a_uniform_translation():
         assert float(gp.abs().max()) < 1e-9 * prm["rho_l"] * prm["c_mass"] * float(np.abs(U).max()) * mesh.h
 
 
+def level_set_spread(mesh, prm, phi, mdot, u1, seeds=(0, 1)):
+    """How the oracle's level-set part of the step (advection fixed point with 2 passes, clamp, projected normal, 2
+    reinitialization steps) responds to a change d of the velocity u1, over seeded random and uniform d:
+    jump = max |psi(u1 + d) - psi(u1)| for |d| = 1e-12 and 1e-10 max|u1| (the closest point of a node on a crease of the
+    piecewise-trilinear isocontour is not unique, and which of the valid points App. C's iteration ends at can switch
+    under any perturbation), and gain = max |psi(u1 + d) - psi(u1)| / |d| for |d| = 1e-5 max|u1|."""
+    mesh1 = fe.Mesh(mesh.n, 1, mesh.L)
+
+    def level_set(uu):
+        adv, _ = geometry.advect_levelset(mesh, np.clip(phi, -1.0, 1.0), uu, mdot, prm, 2)
+        adv = np.clip(adv, -1.0, 1.0)
+        nf = geometry.projected_normal(mesh1, adv, prm.get("eta_n", 2.0))
+        return geometry.reinitialize(mesh1, adv, nf, prm["eps"], prm["dtau"], 2, psi0=adv)[0]
+
+    base = level_set(u1)
+    perts = [np.random.default_rng(sd).uniform(-1.0, 1.0, u1.shape) for sd in seeds] + [np.ones_like(u1)]
+    umax = np.abs(u1).max()
+    jump = max(np.abs(level_set(u1 + size * umax * d) - base).max() for d in perts for size in (1e-12, 1e-10))
+    gain = max(np.abs(level_set(u1 + 1e-5 * umax * d) - base).max() / (1e-5 * umax) for d in perts)
+    return jump, gain
+
+
 def test_stationary_1d_phase_change_step_against_oracle():
     """App. A case (inflow mdot / rho_l through the bottom face, the exact 1D velocity as Dirichlet data on the side
     faces, top open) on 6^3: the step with its lifted Dirichlet data, element by element against the oracle's step."""
@@ -262,10 +284,12 @@ def test_stationary_1d_phase_change_step_against_oracle():
                                  picard_iters=2)
     assert rel(host(gu), u1) < 1e-6
     assert rel(host(gp), p1) < 1e-5
-    # the level-set part carries the velocity difference of the two solves (both within their tolerances) into phi,
-    # multiplied by dt |grad phi| (dt = 1 here, |grad phi| <= 1 / (2 eps) = 4)
+    # the level-set part carries the velocity difference of the two solves (both within their tolerances) into phi;
+    # how much is measured on the oracle itself (level_set_spread: here a jump of ~1.2e-5 at the crease nodes of the
+    # domain's centre column, whose closest points switch between valid ones, and a gain of ~7)
     du = np.abs(host(gu) - u1).max()
-    assert np.abs(host(gphi) - ph1).max() < 1e-7 + 2.0 * prm["dt"] * du / (2.0 * prm["eps"])
+    jump, gain = level_set_spread(mesh, prm, phi, md, u1)
+    assert np.abs(host(gphi) - ph1).max() < 1e-7 + 2.0 * (jump + gain * du)
 
 
 def test_stationary_1d_phase_change_converges_to_the_closed_form():
