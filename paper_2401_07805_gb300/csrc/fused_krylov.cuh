@@ -167,6 +167,15 @@ struct HelmholtzStencil {
             return ld_df(sm + 27u * (9u * cz + 3u * cy + cx) + (unsigned)s);
         });
     }
+    // the diagonal entry (offset 13 = (0, 0, 0)) to FP32, for the Jacobi scaling
+    __device__ __forceinline__ float diag(int64_t node, const float2* sm) const {
+        const unsigned m1 = (unsigned)n + 1u, nd = (unsigned)node;
+        const unsigned t = nd / m1, i = nd - t * m1, k = t / m1, j = t - k * m1;
+        const unsigned cx = i == 0u ? 0u : (i == (unsigned)n ? 2u : 1u);
+        const unsigned cy = j == 0u ? 0u : (j == (unsigned)n ? 2u : 1u);
+        const unsigned cz = k == 0u ? 0u : (k == (unsigned)n ? 2u : 1u);
+        return sm[27u * (9u * cz + 3u * cy + cx) + 13u].x;
+    }
 };
 
 // Host: the 27 x 27 coefficient table of (M + c K) on a lattice of spacing h, formed in FP64 from the 1D rows
@@ -208,11 +217,12 @@ struct NodeStencil {
         const int64_t NN = N;
         return stencil27(n, node, x, [&](unsigned, unsigned, unsigned, int s) { return ld_df(c + s * NN); });
     }
+    __device__ __forceinline__ float diag(int64_t node, const float2*) const { return C[13 * N + node].x; }
 };
 
 // ------------------------------------------------------------------------------------ conjugate gradients
-// A x = b from x = 0, Jacobi-preconditioned CG in the Chronopoulos-Gear arrangement (Chronopoulos and Gear, J. Comput.
-// Appl. Math. 25, 1989): the two scalar products of an iteration, (r, u) and (A u, u), are formed in the same pass as
+// A x = b from x = 0, CG preconditioned by the operator's diagonal D (op.diag, in FP32), in the Chronopoulos-Gear
+// arrangement (Chronopoulos and Gear, J. Comput. Appl. Math. 25, 1989): the two scalar products of an iteration, (r, u) and (A u, u), are formed in the same pass as
 // the operator, with s = A p carried by its own recurrence, so an iteration needs two grid barriers (after the
 // operator and its products; after the vector updates) instead of three.  With u = D^-1 r, w = A u:
 //   gamma = (r, u), delta = (w, u), beta = gamma / gamma_old, alpha = gamma / (delta - beta gamma / alpha_old)
@@ -222,8 +232,8 @@ struct NodeStencil {
 // preconditioner; FP32 changes only the iteration count).  part holds 3 gridDim.x pairs.  out[0] = updates,
 // out[1] = |r|, out[2] = |r0| (block 0).
 template <class Op>
-__global__ void __launch_bounds__(FK_THREADS) k_cg_fused(Op op, int64_t N, const double* __restrict__ b,
-                                                         const double* __restrict__ dg, double* x, float2* xd,
+__global__ void __launch_bounds__(FK_THREADS) k_cg_fused(Op op, int64_t N, const double* __restrict__ b, double* x,
+                                                         float2* xd,
                                                          float* dinv, float2* r, float2* u, float2* p, float2* sv,
                                                          float2* w, double rtol, double atol, int max_iter,
                                                          float2* part, GridBarrier* gb, double* out) {
@@ -234,11 +244,12 @@ __global__ void __launch_bounds__(FK_THREADS) k_cg_fused(Op op, int64_t N, const
     __shared__ int s_go;
     unsigned long long bar = 0;
     const int64_t i0 = blockIdx.x * (int64_t)FK_THREADS + threadIdx.x, stride = (int64_t)gridDim.x * FK_THREADS;
-    op.load(op_sm);  // visible to the block after the barrier below
+    op.load(op_sm);
+    __syncthreads();
     const dfl zero{0.f, 0.f};
     for (int64_t i = i0; i < N; i += stride) {
         const dfl ri = df_from_double(b[i]);
-        const float di = 1.0f / (float)dg[i];
+        const float di = 1.0f / op.diag(i, op_sm);
         st_df(xd + i, zero);
         st_df(r + i, ri);
         st_df(u + i, df_norm(dfl{ri.hi * di, __fmaf_rn(ri.hi, di, -ri.hi * di) + ri.lo * di}));
@@ -314,8 +325,8 @@ __global__ void __launch_bounds__(FK_THREADS) k_cg_fused(Op op, int64_t N, const
 }
 
 // ------------------------------------------------------------------------------------------------- GMRES
-// GMRES(m) for A x = b with the right Jacobi preconditioner D^-1 (A D^-1 y = b, x = D^-1 y), started from x, with
-// classical Gram-Schmidt and a second pass where the first one cancelled more than `reorth` of the vector
+// GMRES(m) for A x = b with the right Jacobi preconditioner D^-1 (D = op.diag in FP32; A D^-1 y = b, x = D^-1 y),
+// started from x, with classical Gram-Schmidt and a second pass where the first one cancelled more than `reorth` of the vector
 // (|w_after|^2 < reorth |w_before|^2).  The Hessenberg matrix, its Givens rotations and the least-squares solve are
 // kept by thread 0 of every block (the same FP64 arithmetic on the same sums, so the same values everywhere).  It
 // stops when the true residual |b - A x| (formed at the start of each cycle) is <= max(rtol |b|, atol), or once
@@ -325,7 +336,7 @@ __global__ void __launch_bounds__(FK_THREADS) k_cg_fused(Op op, int64_t N, const
 // (GM_MAX + 2) gridDim.x pairs.  out[0] = applications, out[1] = the last true |r|, out[2] = |b| (block 0).
 template <class Op>
 __global__ void __launch_bounds__(FK_THREADS) k_gmres_fused(Op op, int64_t N, int m, const double* __restrict__ b,
-                                                            const double* __restrict__ dg, double* x, float2* xd,
+                                                            double* x, float2* xd,
                                                             float* dinv, float2* z, float2* V, double rtol, double atol,
                                                             int max_iter, double reorth, float2* part, GridBarrier* gb,
                                                             double* out) {
@@ -341,6 +352,7 @@ __global__ void __launch_bounds__(FK_THREADS) k_gmres_fused(Op op, int64_t N, in
     const int64_t i0 = blockIdx.x * (int64_t)FK_THREADS + threadIdx.x, stride = (int64_t)gridDim.x * FK_THREADS;
     const dfl zero{0.f, 0.f};
     op.load(op_sm);
+    __syncthreads();
     // per-warp sums of K values (sh[k FK_WARPS + warp]) written as block partials part[k G + b]: warp q reduces values
     // q, q + FK_WARPS, ... by a shuffle tree
     auto partials = [&](int K) {
@@ -380,7 +392,7 @@ __global__ void __launch_bounds__(FK_THREADS) k_gmres_fused(Op op, int64_t N, in
     {
         dfl bb = zero;
         for (int64_t i = i0; i < N; i += stride) {
-            dinv[i] = 1.0f / (float)dg[i];
+            dinv[i] = 1.0f / op.diag(i, op_sm);
             st_df(xd + i, df_from_double(x[i]));
             const dfl bi = df_from_double(b[i]);
             df_fma(bb, bi, bi);

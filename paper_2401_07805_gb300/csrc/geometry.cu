@@ -75,21 +75,6 @@ __global__ void __launch_bounds__(256) k_helmholtz(int n, double h, double c, in
     }
 }
 
-// Diagonal of M + c K (the same for every component).
-__global__ void k_helmholtz_diag(int n, double h, double c, double* __restrict__ d) {
-    const int m1 = n + 1;
-    const int64_t Np = (int64_t)m1 * m1 * m1;
-    const double ih = 1.0 / h;
-    for (int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; node < Np; node += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(node % m1), j = (int)((node / m1) % m1), kz = (int)(node / ((int64_t)m1 * m1));
-        double mx[3], kx[3], my[3], ky[3], mz[3], kzr[3];
-        q1_rows(i, n, h, ih, mx, kx);
-        q1_rows(j, n, h, ih, my, ky);
-        q1_rows(kz, n, h, ih, mz, kzr);
-        d[node] = mx[1] * my[1] * mz[1] + c * (kx[1] * my[1] * mz[1] + mx[1] * ky[1] * mz[1] + mx[1] * my[1] * kzr[1]);
-    }
-}
-
 // The operators of the CG solves in double-float arithmetic (dfloat.cuh): GB300's FP64 pipe bounds the FP64 stencil
 // (93 FMA per node: ~40 us at 64^3), the FP32 pipe runs the same sums on hi + lo pairs several times faster.  The
 // CG keeps its direction p as pairs beside the FP64 copy, so the operators read their neighbours without converting.
@@ -222,38 +207,6 @@ __global__ void __launch_bounds__(128) k_curvature_rhs(MeshArgs<double> m, Basis
     }
 #pragma unroll
     for (int j = 0; j < 8; ++j) atomicAdd(&b[c.node[j]], out[j]);
-}
-
-// diag_i += sum_q W (N_i^2 / dtau + eps (grad N_i . n)^2), the diagonal of the reinitialization operator.
-__global__ void __launch_bounds__(128) k_reinit_diag(MeshArgs<double> m, Basis<double> bas, const double* __restrict__ phi,
-                                                     const double* __restrict__ nf, double* __restrict__ d) {
-    const int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (cell >= m.ncell) return;
-    Q1Cell c;
-    int cx, cy, cz;
-    q1_cell_nodes(cell, m.n, c, cx, cy, cz);
-    double pv[8], nloc[3][8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        pv[j] = phi[c.node[j]];
-#pragma unroll
-        for (int e = 0; e < 3; ++e) nloc[e][j] = nf ? nf[e * m.Nphi + c.node[j]] : 0.0;
-    }
-    double out[8] = {};
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        double N[8], G[8][3], nv[3];
-        q1_weights(bas.g2t, q, m.inv_h, N, G);
-        const double W = bas.g2w[q & 1] * bas.g2w[(q >> 1) & 1] * bas.g2w[q >> 2] * m.vol_w;
-        ls_frozen_normal<double>(nf ? nloc : nullptr, pv, N, G, m.h, nv);
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const double gn = G[j][0] * nv[0] + G[j][1] * nv[1] + G[j][2] * nv[2];
-            out[j] += W * (N[j] * N[j] / m.dtau + m.eps * gn * gn);
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < 8; ++j) atomicAdd(&d[c.node[j]], out[j]);
 }
 
 // ------------------------------------------------------------------------------- conjugate gradients (FP64)
@@ -535,8 +488,8 @@ static int fused_result(evap_mesh* h, const FusedSpace& f, cudaStream_t s, doubl
 // The single-launch CG (k_cg_fused) on a level-set system: one cooperative launch and one host read per solve,
 // stopping at |r| <= max(rtol |r0|, atol) or after max_iter iterations.
 template <class Op>
-static int cg_solve_fused(evap_mesh* h, Op op, const double* b, const double* d, double* x, double rtol, double atol,
-                          int max_iter, int* iters, double* relres, cudaStream_t s) {
+static int cg_solve_fused(evap_mesh* h, Op op, const double* b, double* x, double rtol, double atol, int max_iter,
+                          int* iters, double* relres, cudaStream_t s) {
     int64_t N = ls_args<double>(h).Nphi;
     if (N >= (int64_t)1 << 32) {
         set_error("single-launch CG: the level-set stencils index nodes with 32 bits");
@@ -554,7 +507,7 @@ static int cg_solve_fused(evap_mesh* h, Op op, const double* b, const double* d,
     float2* part = f.part;
     GridBarrier* gb = f.gb;
     double* out = f.out;
-    void* args[] = {&op, &N, &b, &d, &xx, &xd, &dinv, &r, &u, &p, &sv, &w, &rtol, &atol, &max_iter, &part, &gb, &out};
+    void* args[] = {&op, &N, &b, &xx, &xd, &dinv, &r, &u, &p, &sv, &w, &rtol, &atol, &max_iter, &part, &gb, &out};
     EVAP_CUDA(cudaLaunchCooperativeKernel((const void*)k_cg_fused<Op>, dim3(G), dim3(FK_THREADS), args, smem, s));
     EVAP_CHECK_LAUNCH("cg_fused");
     double res[3];
@@ -567,8 +520,8 @@ static int cg_solve_fused(evap_mesh* h, Op op, const double* b, const double* d,
 
 // The single-launch GMRES(m) (k_gmres_fused) with the right Jacobi preconditioner, started from x.
 template <class Op>
-static int gmres_solve_fused(evap_mesh* h, Op op, int m, const double* b, const double* d, double* x, double rtol,
-                             double atol, int max_iter, double reorth, int* iters, double* relres, cudaStream_t s) {
+static int gmres_solve_fused(evap_mesh* h, Op op, int m, const double* b, double* x, double rtol, double atol,
+                             int max_iter, double reorth, int* iters, double* relres, cudaStream_t s) {
     int64_t N = ls_args<double>(h).Nphi;
     if (N >= (int64_t)1 << 32 || m < 1 || m > GM_MAX) {
         set_error("single-launch GMRES: restart must be in [1, 30] and node indices fit 32 bits");
@@ -586,7 +539,7 @@ static int gmres_solve_fused(evap_mesh* h, Op op, int m, const double* b, const 
     float2* part = f.part;
     GridBarrier* gb = f.gb;
     double* out = f.out;
-    void* args[] = {&op, &N, &m, &b, &d, &xx, &xd, &dinv, &z, &V, &rtol, &atol, &max_iter, &reorth, &part, &gb, &out};
+    void* args[] = {&op, &N, &m, &b, &xx, &xd, &dinv, &z, &V, &rtol, &atol, &max_iter, &reorth, &part, &gb, &out};
     EVAP_CUDA(cudaLaunchCooperativeKernel((const void*)k_gmres_fused<Op>, dim3(G), dim3(FK_THREADS), args, smem, s));
     EVAP_CHECK_LAUNCH("gmres_fused");
     double res[3];
@@ -633,15 +586,13 @@ int geo_projected_normal(evap_mesh* h, double* n, int* iters, double* relres, cu
     EVAP_CUDA(cudaMemsetAsync(w.t0, 0, 3 * stride * sizeof(double), s));
     k_normal_rhs<<<blocks_for(lm.ncell, 128, 1LL << 40), 128, 0, s>>>(lm, h->b, h->phi, w.t0, stride);
     EVAP_CHECK_LAUNCH("normal_rhs");
-    k_helmholtz_diag<<<blocks_for(Np, 256, 152 * 16), 256, 0, s>>>(lm.n, lm.h, c, w.d);
-    EVAP_CHECK_LAUNCH("helmholtz_diag");
     if (iters) *iters = 0;
     if (relres) *relres = 0.0;
     int status = EVAP_OK;
     HelmholtzStencil op;
     if ((rc = helmholtz_stencil(h, lm, c, op, s))) return rc;
     for (int d = 0; d < 3; ++d) {
-        rc = cg_solve_fused(h, op, w.t0 + d * stride, w.d, n + d * Np, 1e-12, 1e-20, 1000, iters, relres, s);
+        rc = cg_solve_fused(h, op, w.t0 + d * stride, n + d * Np, 1e-12, 1e-20, 1000, iters, relres, s);
         if (rc == EVAP_ENOTCONV) status = rc;
         else if (rc) return rc;
     }
@@ -658,13 +609,11 @@ int geo_curvature(evap_mesh* h, const double* nf, double* kappa, int* iters, dou
     EVAP_CUDA(cudaMemsetAsync(w.b, 0, Np * sizeof(double), s));
     k_curvature_rhs<<<blocks_for(lm.ncell, 128, 1LL << 40), 128, 0, s>>>(lm, h->b, nf, w.b);
     EVAP_CHECK_LAUNCH("curvature_rhs");
-    k_helmholtz_diag<<<blocks_for(Np, 256, 152 * 16), 256, 0, s>>>(lm.n, lm.h, c, w.d);
-    EVAP_CHECK_LAUNCH("helmholtz_diag");
     if (iters) *iters = 0;
     if (relres) *relres = 0.0;
     HelmholtzStencil op;
     if ((rc = helmholtz_stencil(h, lm, c, op, s))) return rc;
-    return cg_solve_fused(h, op, w.b, w.d, kappa, 1e-12, 1e-20, 1000, iters, relres, s);
+    return cg_solve_fused(h, op, w.b, kappa, 1e-12, 1e-20, 1000, iters, relres, s);
 }
 
 // Element matrices of the reinitialization operator with the frozen normal, A_e[i][j] = sum_q W (N_i N_j / dtau +
@@ -726,9 +675,6 @@ int geo_reinitialize(evap_mesh* h, double* psi, int steps, int* iters, double* l
     if (rc) return rc;
     CgSpace w = cg_space(h);
     const int64_t Np = lm.Nphi;
-    EVAP_CUDA(cudaMemsetAsync(w.d, 0, Np * sizeof(double), s));
-    k_reinit_diag<<<blocks_for(lm.ncell, 128, 1LL << 40), 128, 0, s>>>(lm, h->b, h->phi, h->ls_normal, w.d);
-    EVAP_CHECK_LAUNCH("reinit_diag");
     if ((rc = geo_elem_reserve(h, 36 * lm.ncell + 27 * Np))) return rc;  // 36 pairs per cell, then 27 per node
     float2* Edf = reinterpret_cast<float2*>(h->geo_elem);
     float2* Cn = Edf + 36 * lm.ncell;
@@ -744,7 +690,7 @@ int geo_reinitialize(evap_mesh* h, double* psi, int steps, int* iters, double* l
     for (int k = 0; k < steps; ++k) {
         rc = launch_levelset<double>(h, EVAP_REINIT_RHS, psi, w.b, s);
         if (rc) return rc;
-        rc = cg_solve_fused(h, op, w.b, w.d, w.t0, 1e-12, 1e-20, 1000, iters, &rel, s);
+        rc = cg_solve_fused(h, op, w.b, w.t0, 1e-12, 1e-20, 1000, iters, &rel, s);
         if (rc == EVAP_ENOTCONV) status = rc;
         else if (rc) return rc;
         if (k == steps - 1 && last_change) {
@@ -767,11 +713,10 @@ int geo_reinitialize(evap_mesh* h, double* psi, int steps, int* iters, double* l
 // ------------------------------------------------------------------------------ level-set advection (step 1)
 // Element matrices of the Crank-Nicolson advection operator (EVAP_ADVECT) with the mesh's nodal transport velocity
 // interpolated at the point, A_e[i][j] = sum_q W N_i (N_j + theta dt u_Gamma . grad N_j): u_Gamma is fixed within a
-// fixed-point pass, so every GMRES apply of the pass is a per-cell 8x8 product (64 FMA) instead of the 8-point
-// quadrature (about 10x the FP64 work).  Layout [64][ncell], entry i * 8 + j; the diagonal d_i += A_e[i][i] (the
-// Jacobi preconditioner) is accumulated on the way.
+// fixed-point pass, so the matrices are formed once per pass and assembled into the node stencil that every GMRES
+// iteration of the pass applies (k_stencil_from_elem_full).  Layout [64][ncell], entry i * 8 + j.
 __global__ void __launch_bounds__(128) k_advect_elem(MeshArgs<double> m, const double* __restrict__ ug,
-                                                     double* __restrict__ E, double* __restrict__ d) {
+                                                     double* __restrict__ E) {
     const int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (cell >= m.ncell) return;
     Q1Cell c;
@@ -821,7 +766,6 @@ __global__ void __launch_bounds__(128) k_advect_elem(MeshArgs<double> m, const d
     for (int i = 0; i < 8; ++i) {
 #pragma unroll
         for (int j = 0; j < 8; ++j) E[(i * 8 + j) * m.ncell + cell] = m.vol_w * a[i * 8 + j];
-        atomicAdd(&d[c.node[i]], m.vol_w * a[i * 9]);
     }
 }
 
@@ -912,15 +856,14 @@ int geo_advect_levelset(evap_mesh* h, double* phi, int max_iters, double tol, in
         if ((rc = launch_levelset<double>(h, EVAP_ADVECT, h->phi, w.t2, s))) return rc;
         k_advect_rhs<<<G, 256, 0, s>>>(w.t1, w.t2, lm.theta, w.b, Np);
         EVAP_CHECK_LAUNCH("advect_rhs");
-        EVAP_CUDA(cudaMemsetAsync(w.d, 0, Np * sizeof(double), s));
-        k_advect_elem<<<gc, 128, 0, s>>>(lm, h->ugamma, h->geo_elem, w.d);
+        k_advect_elem<<<gc, 128, 0, s>>>(lm, h->ugamma, h->geo_elem);
         EVAP_CHECK_LAUNCH("advect_elem");
         k_stencil_from_elem_full<<<(unsigned)blocks_for(Np, 128, 1LL << 40), 128, 0, s>>>(lm.n, lm.ncell, Np,
                                                                                          h->geo_elem, Cn);
         EVAP_CHECK_LAUNCH("advect_stencil");
         EVAP_CUDA(cudaMemcpyAsync(w.r, phi, Np * sizeof(double), cudaMemcpyDeviceToDevice, s));
         double rel = 0.0;
-        rc = gmres_solve_fused(h, NodeStencil{lm.n, Np, Cn}, ADVECT_RESTART, w.b, w.d, phi, 1e-12, 1e-20, 1000,
+        rc = gmres_solve_fused(h, NodeStencil{lm.n, Np, Cn}, ADVECT_RESTART, w.b, phi, 1e-12, 1e-20, 1000,
                                ADVECT_REORTH, &lin, &rel, s);
         if (rc == EVAP_ENOTCONV) status = rc;
         else if (rc) return rc;
