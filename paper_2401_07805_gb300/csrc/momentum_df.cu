@@ -41,8 +41,17 @@ constexpr size_t df_coeff_smem() {
     return sizeof(float2) * CB * QC_K * (P + 1) * (P + 1) * (P + 1);
 }
 
-template <int P, int CB, bool PRES>
-__global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
+// Block shape: CB cells per block (one thread per point), at least MINB blocks per SM.  Measured at 64^3 Q2 on
+// GB300 (100 back-to-back applies): see the launcher.
+#ifndef EVAP_DF_CB2
+#define EVAP_DF_CB2 8
+#endif
+#ifndef EVAP_DF_MINB2
+#define EVAP_DF_MINB2 1
+#endif
+
+template <int P, int CB, bool PRES, int MINB = 1>
+__global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1), MINB)
     k_momentum_df(MeshArgs<double> m, DfBasis bas, const float2* __restrict__ qc, const double* __restrict__ x,
                   double* __restrict__ y, double* __restrict__ yp, const double* __restrict__ pin) {
     constexpr int Q = P + 1, NQ = Q * Q * Q;
@@ -290,17 +299,17 @@ int launch_momentum_df(evap_mesh* h, const MeshArgs<double>& m, const double* x,
     const DfBasis b = make_df_basis(h->b, m.inv_h);
     const float2* qc = reinterpret_cast<const float2*>(h->qcdf);
     if (m.P == 2) {
-        constexpr int CB = 8;
+        constexpr int CB = EVAP_DF_CB2, MINB = EVAP_DF_MINB2;
         constexpr size_t dyn = df_coeff_smem<2, CB>();
         const unsigned grid = (unsigned)((m.ncell + CB - 1) / CB);
         if (p) {
-            EVAP_CUDA(cudaFuncSetAttribute(k_momentum_df<2, CB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)dyn));
-            k_momentum_df<2, CB, true><<<grid, CB * 27, dyn, s>>>(m, b, qc, x, y, yp, p);
+            EVAP_CUDA(cudaFuncSetAttribute(k_momentum_df<2, CB, true, MINB>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+            k_momentum_df<2, CB, true, MINB><<<grid, CB * 27, dyn, s>>>(m, b, qc, x, y, yp, p);
         } else {
-            EVAP_CUDA(cudaFuncSetAttribute(k_momentum_df<2, CB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)dyn));
-            k_momentum_df<2, CB, false><<<grid, CB * 27, dyn, s>>>(m, b, qc, x, y, yp, nullptr);
+            EVAP_CUDA(cudaFuncSetAttribute(k_momentum_df<2, CB, false, MINB>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+            k_momentum_df<2, CB, false, MINB><<<grid, CB * 27, dyn, s>>>(m, b, qc, x, y, yp, nullptr);
         }
     } else {
         constexpr int CB = 4;
