@@ -41,13 +41,15 @@ constexpr size_t df_coeff_smem() {
     return sizeof(float2) * CB * QC_K * (P + 1) * (P + 1) * (P + 1);
 }
 
-// Block shape: CB cells per block (one thread per point), at least MINB blocks per SM.  Measured at 64^3 Q2 on
-// GB300 (100 back-to-back applies): see the launcher.
+// Block shape for Q2: CB cells per block (one thread per point), at least MINB blocks per SM (which caps the
+// registers).  Measured at 64^3 on GB300, 100 back-to-back applies with the divergence row (ms per apply):
+// CB 4 / MINB 8 (64 registers) 0.685; CB 4 / 6 0.699; CB 8 / 4 0.700; CB 8 without a minimum (72 registers) 0.691;
+// CB 8 / 3 0.722; CB 4 / 1 (89 registers) 0.738; CB 8 / 1 0.848; CB 12 / 1 1.207.
 #ifndef EVAP_DF_CB2
-#define EVAP_DF_CB2 8
+#define EVAP_DF_CB2 4
 #endif
 #ifndef EVAP_DF_MINB2
-#define EVAP_DF_MINB2 1
+#define EVAP_DF_MINB2 8
 #endif
 
 template <int P, int CB, bool PRES, int MINB = 1>
