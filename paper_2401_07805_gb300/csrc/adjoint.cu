@@ -48,8 +48,18 @@ __global__ void k_adjoint_init(int M, int64_t Nu, int64_t Np, unsigned faces, co
 // (dfloat.cuh) on the FP32 pipe, with the coefficients of the double-float cache (the pairs of the FP64 values the
 // forward apply uses); the material-law derivatives of the interface-zone points and the level-set test sweeps run in
 // FP64 (only table cells carry them: blocks without a table cell skip the sweeps).
-template <int P, int CB, int K>
-__global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1), 2)
+// Block shape for Q2 on the velocity mesh's level set: CB cells per block, at least MINB blocks per SM (a register
+// cap).  Measured at 64^3 on GB300 (20 back-to-back adjoints, ms): CB 7 / MINB 3 (96 registers, some spills) 2.995;
+// 8 / 2 3.158; 7 / 2 (168 registers) 3.261; 4 / 4 3.403; 4 / 3 3.526; 6 / 2 3.696.
+#ifndef EVAP_ADJ_CB2
+#define EVAP_ADJ_CB2 7
+#endif
+#ifndef EVAP_ADJ_MINB2
+#define EVAP_ADJ_MINB2 3
+#endif
+
+template <int P, int CB, int K, int MINB = 2>
+__global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1), MINB)
     k_adjoint(MeshArgs<double> m, DfBasis dfb, Basis<double> bas, const double* __restrict__ phi,
               const double* __restrict__ mdot, const int8_t* __restrict__ code, const int32_t* __restrict__ tindex,
               const double* __restrict__ table, const float2* __restrict__ qcd, const double* __restrict__ w,
@@ -416,10 +426,11 @@ int launch_adjoint(evap_mesh* h, const double* w, const double* wp, const double
     EVAP_CHECK_LAUNCH("adjoint_init");
     const DfBasis dfb = make_df_basis(h->b, m.inv_h);
     const float2* qcd = reinterpret_cast<const float2*>(h->qcdf);
-    const unsigned g7 = (unsigned)((m.ncell + 6) / 7), g6 = (unsigned)((m.ncell + 5) / 6);
+    constexpr int CA = EVAP_ADJ_CB2, MA = EVAP_ADJ_MINB2;
+    const unsigned g7 = (unsigned)((m.ncell + CA - 1) / CA), g6 = (unsigned)((m.ncell + 5) / 6);
     const unsigned g2 = (unsigned)((m.ncell + 1) / 2);
     if (m.P == 2 && m.nsub == 1)  // 7 cells: 189 threads, 98 % of the lanes of 6 warps
-        k_adjoint<2, 7, 2><<<g7, 7 * 27, 0, s>>>(m, dfb, h->b, h->phi, h->mdot, h->cell_code, h->table_index, h->table,
+        k_adjoint<2, CA, 2, MA><<<g7, CA * 27, 0, s>>>(m, dfb, h->b, h->phi, h->mdot, h->cell_code, h->table_index, h->table,
                                                   qcd, w, wp, x, gx, gu, gphi, gm);
     else if (m.P == 2)  // the subdivided level set's larger test-sweep buffers (static shared memory <= 48 KB)
         k_adjoint<2, 6, 3><<<g6, 6 * 27, 0, s>>>(m, dfb, h->b, h->phi, h->mdot, h->cell_code, h->table_index, h->table,
