@@ -330,8 +330,20 @@ def back_to_back(torch, fn, reps, warm):
 
 def operator_applies(evap, torch, dev, op, d, counts, hbm):
     """Extras beside the step: the closest-point transport pass alone on the 64^3 workload (20 repeats: band nodes/s,
-    point evaluations, flags) and the adjoint on the 48^3 sphere (2.74 M DoFs, 20 applies after 3)."""
+    point evaluations, flags), the applies and the adjoint in the deterministic mode (8 colour passes instead of
+    atomic adds: 20 applies after 3 each), and the adjoint on the 48^3 sphere (2.74 M DoFs, 20 applies after 3)."""
     out = {}
+    x, x32 = d["x"], d["x32"]
+    y, yp = torch.empty_like(x), torch.empty(op.n_p, dtype=torch.float64, device=dev)
+    det = {}
+    for mode in (False, True):
+        op.set_deterministic(mode)
+        t64 = back_to_back(torch, lambda: op.apply_momentum(x, prec=64, with_divergence=True, out=y, out_p=yp), 20, 3)
+        t32 = back_to_back(torch, lambda: op.apply_momentum(x32, prec=32), 20, 3)
+        ta = back_to_back(torch, lambda: op.apply_adjoint(d["w"], x, d["wp"]), 20, 3)
+        det["deterministic" if mode else "atomic"] = dict(momentum_fp64_ms=t64, momentum_fp32_ms=t32, adjoint_ms=ta)
+    op.set_deterministic(False)
+    out["accumulation"] = det
     t = back_to_back(torch, op.update_transport_velocity, 20, 2)
     st = op.transport_stats()
     out["transport_velocity"] = dict(ms=t, band_nodes=st["band_nodes"], band_nodes_per_s=st["band_nodes"] / t * 1e3,

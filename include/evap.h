@@ -109,6 +109,15 @@ int evap_pressure_size(evap_handle h, int64_t* n_p);
  * reduction, synchronizes the stream, and returns EVAP_ENONFINITE without doing its work if any is found. */
 int evap_set_checks(evap_handle h, int on);
 
+/* Deterministic accumulation (off by default).  With on != 0 the operator applies (evap_apply_momentum at both
+ * precisions with its divergence row, the velocity-pressure apply, evap_apply_levelset, evap_apply_adjoint) and the
+ * Jacobi diagonal of the solves add the cells' contributions in 8 passes, one per parity class of the cell
+ * coordinates (cells of one class share no node), with plain loads and stores instead of atomic adds: every entry
+ * is summed in a fixed order, so these results, and the iterates and iteration counts of evap_solve, are bitwise
+ * reproducible from run to run.  Costs 8 launches per apply instead of one.  Section 2.5's y = sum_i R_i^T A_i R_i x
+ * is the same sum in another order. */
+int evap_set_deterministic(evap_handle h, int on);
+
 /* Set the coefficient fields of the operators: phi [N_phi] (regularized level set, Eq. initial_phi; values are
  * clamped to [-1, 1]), u [3 N_u] (velocity about which the momentum operator is linearized; also the fluid
  * velocity of the transport velocity), mdot [N_phi] (evaporative mass flux, Eq. evaporDil).  Copies the fields,

@@ -61,6 +61,7 @@ SIGNATURES = {
     "evap_advect_levelset": (_c_int, [_vp, _vp, _c_int, _c_dbl, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int),
                                       ctypes.POINTER(_c_dbl), _vp]),
     "evap_set_checks": (_c_int, [_vp, _c_int]),
+    "evap_set_deterministic": (_c_int, [_vp, _c_int]),
     "evap_time_step": (_c_int, [_vp, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_c_dbl), _c_dbl, _c_int, _c_dbl, _c_int,
                                 _c_int, _c_dbl, ctypes.POINTER(_c_int), ctypes.POINTER(_c_dbl),
                                 ctypes.POINTER(_c_dbl), _vp]),
@@ -308,6 +309,10 @@ class Operator:
     def set_checks(self, on: bool = True):
         """Count NaN / Inf entries of every later call's inputs first (EVAP_ENONFINITE if any)."""
         _check(lib().evap_set_checks(self._h, int(bool(on))), "evap_set_checks")
+
+    def set_deterministic(self, on: bool = True):
+        """Cells accumulated in 8 parity-class passes without atomics: bitwise reproducible applies and solves."""
+        _check(lib().evap_set_deterministic(self._h, int(bool(on))), "evap_set_deterministic")
 
     def apply_saddle(self, x: torch.Tensor, p: torch.Tensor):
         """(A x - B^T p, B x): the velocity-pressure operator of Eq. (weakNavierStokes) with the Q1 pressure."""

@@ -16,6 +16,8 @@
 // The value/gradient sensitivities are tested like the forward operator (S^T and Dc^T sweeps); the Q1 sensitivities
 // are integrated against the level-set shape functions N_j and grad N_j (Q1 on the level-set mesh: the velocity
 // cell subdivided n_sub times per direction).
+#include <algorithm>
+
 #include "dfloat.cuh"
 #include "physics.cuh"
 
@@ -64,7 +66,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1), MINB)
               const double* __restrict__ mdot, const int8_t* __restrict__ code, const int32_t* __restrict__ tindex,
               const double* __restrict__ table, const float2* __restrict__ qcd, const double* __restrict__ w,
               const double* __restrict__ wp, const double* __restrict__ x, double* gx, double* gu, double* gphi,
-              double* gm) {
+              double* gm, int colour) {
     constexpr int Q = P + 1, NQ = Q * Q * Q;
     static_assert(K * Q * Q <= NQ && K * K * K <= NQ, "one thread per entry of each level-set test sweep");
     __shared__ dfl sS[Q][Q], sDc[Q][Q];
@@ -73,8 +75,10 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1), MINB)
     __shared__ double q1a[CB][5][K * Q * Q], q1b[CB][5][K * K * Q];  // level-set test sweeps (FP64)
     const int tid = threadIdx.x;
     const int lc = tid / NQ, t = tid % NQ;
-    const int64_t cell = (int64_t)blockIdx.x * CB + lc;
-    const bool active = cell < m.ncell;
+    int cx = 0, cy = 0, cz = 0;
+    const bool active = colour_cell((int64_t)blockIdx.x * CB + lc, m.n, colour, cx, cy, cz);
+    const int64_t cell = cx + (int64_t)m.n * (cy + (int64_t)m.n * cz);
+    const bool plain = colour >= 0;  // a colour pass: no other cell of the launch touches this cell's nodes
     if (tid < Q * Q) {
         sS[tid / Q][tid % Q] = dfb.S[tid / Q][tid % Q];
         sDc[tid / Q][tid % Q] = dfb.Dc[tid / Q][tid % Q];
@@ -87,13 +91,9 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1), MINB)
     const int n = m.n, M = m.M;
     const int64_t m1 = n + 1;     // pressure nodes per axis (w_p)
     const int64_t ml = m.nl + 1;  // level-set nodes per axis
-    int cx = 0, cy = 0, cz = 0;
     int64_t gidx = 0;
     bool cons = false, tcell = false;
     if (active) {
-        cx = (int)(cell % n);
-        cy = (int)((cell / n) % n);
-        cz = (int)(cell / ((int64_t)n * n));
         const int gxi = P * cx + a, gyi = P * cy + b, gzi = P * cz + c;
         gidx = gxi + (int64_t)M * (gyi + (int64_t)M * gzi);
         cons = cons_node(gxi, gyi, gzi, M, m.faces);
@@ -388,8 +388,8 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1), MINB)
         }
         const int ks = K - 1;  // n_sub
         const int64_t nd = (ks * cx + jx) + ml * ((ks * cy + jy) + ml * (ks * cz + jz));
-        if (gphi) atomicAdd(&gphi[nd], r[0] + m.inv_h * (r[1] + r[2] + r[3]));
-        if (gm) atomicAdd(&gm[nd], r[4]);
+        if (gphi) acc_add(&gphi[nd], r[0] + m.inv_h * (r[1] + r[2] + r[3]), plain);
+        if (gm) acc_add(&gm[nd], r[4], plain);
     }
     // transposed sweeps S^T of the 6 value fields (g_x, g_u0): z, y, x
     if (active) {
@@ -416,9 +416,9 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1), MINB)
         for (int f = 0; f < 6; ++f) {
             const double s = df_to_double(df_dot<Q>(Ta, &buf[0][lc][f][Q * (b + Q * c)], 1));
             if (f < 3) {
-                if (gx && !cons) atomicAdd(&gx[f * m.Nu + gidx], s);
+                if (gx && !cons) acc_add(&gx[f * m.Nu + gidx], s, plain);
             } else if (gu) {
-                atomicAdd(&gu[(f - 3) * m.Nu + gidx], s);
+                acc_add(&gu[(f - 3) * m.Nu + gidx], s, plain);
             }
         }
     }
@@ -431,23 +431,25 @@ int launch_adjoint(evap_mesh* h, const double* w, const double* wp, const double
     EVAP_CHECK_LAUNCH("adjoint_init");
     const DfBasis dfb = make_df_basis(h->b, m.inv_h);
     const float2* qcd = reinterpret_cast<const float2*>(h->qcdf);
+    const int c0 = h->deterministic ? 0 : -1, c1 = h->deterministic ? 8 : 0;  // colour passes, or one atomic pass
+    auto run = [&](auto kern, int CB, int threads) -> int {
+        for (int colour = c0; colour < std::max(c1, c0 + 1); ++colour) {
+            const int64_t cells = colour_cells(m.n, colour);
+            if (cells == 0) continue;
+            kern<<<(unsigned)((cells + CB - 1) / CB), threads, 0, s>>>(m, dfb, h->b, h->phi, h->mdot, h->cell_code,
+                                                                       h->table_index, h->table, qcd, w, wp, x, gx,
+                                                                       gu, gphi, gm, colour);
+            EVAP_CHECK_LAUNCH("adjoint");
+        }
+        return EVAP_OK;
+    };
     constexpr int CA = EVAP_ADJ_CB2, MA = EVAP_ADJ_MINB2;
-    const unsigned g7 = (unsigned)((m.ncell + CA - 1) / CA), g6 = (unsigned)((m.ncell + 5) / 6);
-    const unsigned g2 = (unsigned)((m.ncell + 1) / 2);
     if (m.P == 2 && m.nsub == 1)  // 7 cells: 189 threads, 98 % of the lanes of 6 warps
-        k_adjoint<2, CA, 2, MA><<<g7, CA * 27, 0, s>>>(m, dfb, h->b, h->phi, h->mdot, h->cell_code, h->table_index, h->table,
-                                                  qcd, w, wp, x, gx, gu, gphi, gm);
-    else if (m.P == 2)  // the subdivided level set's larger test-sweep buffers (static shared memory <= 48 KB)
-        k_adjoint<2, 6, 3><<<g6, 6 * 27, 0, s>>>(m, dfb, h->b, h->phi, h->mdot, h->cell_code, h->table_index, h->table,
-                                                  qcd, w, wp, x, gx, gu, gphi, gm);
-    else if (m.nsub == 1)
-        k_adjoint<3, 2, 2><<<g2, 2 * 64, 0, s>>>(m, dfb, h->b, h->phi, h->mdot, h->cell_code, h->table_index, h->table,
-                                                  qcd, w, wp, x, gx, gu, gphi, gm);
-    else
-        k_adjoint<3, 2, 3><<<g2, 2 * 64, 0, s>>>(m, dfb, h->b, h->phi, h->mdot, h->cell_code, h->table_index, h->table,
-                                                  qcd, w, wp, x, gx, gu, gphi, gm);
-    EVAP_CHECK_LAUNCH("adjoint");
-    return EVAP_OK;
+        return run(k_adjoint<2, CA, 2, MA>, CA, CA * 27);
+    if (m.P == 2)  // the subdivided level set's larger test-sweep buffers (static shared memory <= 48 KB)
+        return run(k_adjoint<2, 6, 3>, 6, 6 * 27);
+    if (m.nsub == 1) return run(k_adjoint<3, 2, 2>, 2, 2 * 64);
+    return run(k_adjoint<3, 2, 3>, 2, 2 * 64);
 }
 
 }  // namespace evap

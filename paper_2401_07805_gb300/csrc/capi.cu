@@ -313,6 +313,13 @@ int evap_set_checks(evap_handle h, int on) {
     return EVAP_OK;
 }
 
+int evap_set_deterministic(evap_handle h, int on) {
+    if (!h) return fail(EVAP_EINVAL, "evap_set_deterministic: null handle");
+    h->deterministic = on != 0;
+    h->diag_valid = false;  // the Jacobi diagonal is rebuilt the chosen way
+    return EVAP_OK;
+}
+
 }  // extern "C"
 
 namespace evap {

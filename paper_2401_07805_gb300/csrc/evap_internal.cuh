@@ -59,6 +59,42 @@ struct Coeffs {            // quadrature-point coefficients of the momentum oper
     const T* u0;           // [3 N_u]
 };
 
+// Deterministic accumulation (evap_set_deterministic): the cells are taken in 8 passes, one per parity class
+// colour = px + 2 py + 4 pz (cx = px, cy = py, cz = pz mod 2).  Two cells of one class differ by at least 2 in some
+// coordinate, so they share no node of any of the meshes' spaces (velocity, pressure, level set): within a pass every
+// entry is written by at most one cell, with a plain load and store, and every entry sums its cells in class order.
+// colour < 0: all cells at once, accumulated by atomic adds (the default).
+__host__ __device__ inline int64_t colour_cells(int n, int colour) {
+    if (colour < 0) return (int64_t)n * n * n;
+    const int64_t hx = (n - (colour & 1) + 1) / 2, hy = (n - ((colour >> 1) & 1) + 1) / 2, hz = (n - (colour >> 2) + 1) / 2;
+    return hx * hy * hz;
+}
+// Cell (cx, cy, cz) of launch index idx in the pass `colour`, lexicographic within the class; false past its end.
+__device__ __forceinline__ bool colour_cell(int64_t idx, int n, int colour, int& cx, int& cy, int& cz) {
+    if (colour < 0) {
+        if (idx >= (int64_t)n * n * n) return false;
+        cx = (int)(idx % n);
+        cy = (int)((idx / n) % n);
+        cz = (int)(idx / ((int64_t)n * n));
+        return true;
+    }
+    const int px = colour & 1, py = (colour >> 1) & 1, pz = colour >> 2;
+    const int hx = (n - px + 1) >> 1, hy = (n - py + 1) >> 1, hz = (n - pz + 1) >> 1;
+    if (idx >= (int64_t)hx * hy * hz) return false;
+    cx = 2 * (int)(idx % hx) + px;
+    cy = 2 * (int)((idx / hx) % hy) + py;
+    cz = 2 * (int)(idx / ((int64_t)hx * hy)) + pz;
+    return true;
+}
+// y += v: a plain read-modify-write inside a colour pass, else an atomic add
+template <typename T>
+__device__ __forceinline__ void acc_add(T* y, T v, bool plain) {
+    if (plain)
+        *y += v;
+    else
+        atomicAdd(y, v);
+}
+
 void host_basis(int P, Basis<double>& b, int nsub = 1);
 template <typename T>
 Basis<T> cast_basis(const Basis<double>& b);
@@ -135,6 +171,8 @@ struct evap_mesh {
     size_t sd_red_len = 0;
     // input checks (evap_set_checks): device counter of non-finite entries
     bool checks = false;
+    // deterministic accumulation (evap_set_deterministic): 8 colour passes instead of atomic adds
+    bool deterministic = false;
     unsigned long long* nonfinite = nullptr;
     // time step workspace: inertia load [3 N_u], advected level set [N_phi], projected normal [3 N_phi]
     double* step_ws = nullptr;

@@ -7,6 +7,7 @@
 //              reductions carry FP64-level accuracy without using the (slow) FP64 pipe per element.
 // The Hessenberg matrix, Givens rotations and the small triangular solve run on the host in FP64; one
 // device-to-host copy per Arnoldi step carries the new column.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -20,13 +21,15 @@ namespace evap {
 // in FP32 from the quadrature-point cache of set_fields (k_qp_coeffs); one thread per (cell, local node).
 template <int P, int CB>
 __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
-    k_diagonal(MeshArgs<float> m, Basis<float> bas, const double* __restrict__ qc, float* __restrict__ diag) {
+    k_diagonal(MeshArgs<float> m, Basis<float> bas, const double* __restrict__ qc, float* __restrict__ diag,
+               int colour) {
     constexpr int Q = P + 1, NQ = Q * Q * Q;
     __shared__ float sS[Q][Q], sD[Q][Q];
     __shared__ float qd[CB][11][NQ];  // per point: W rho c_m, W rho U(3), newton W rho d_c u0_c (3), 2 W mu, z n(3)
     const int tid = threadIdx.x, lc = tid / NQ, t = tid % NQ;
-    const int64_t cell = (int64_t)blockIdx.x * CB + lc;
-    const bool active = cell < m.ncell;
+    int cx = 0, cy = 0, cz = 0;
+    const bool active = colour_cell((int64_t)blockIdx.x * CB + lc, m.n, colour, cx, cy, cz);
+    const int64_t cell = cx + (int64_t)m.n * (cy + (int64_t)m.n * cz);
     if (tid < Q * Q) {
         sS[tid / Q][tid % Q] = bas.S[tid / Q][tid % Q];
         sD[tid / Q][tid % Q] = bas.D[tid / Q][tid % Q];
@@ -40,8 +43,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
     }
     __syncthreads();
     if (!active) return;
-    const int n = m.n, M = m.M;
-    const int cx = (int)(cell % n), cy = (int)((cell / n) % n), cz = (int)(cell / ((int64_t)n * n));
+    const int M = m.M;
     const int64_t gidx = (P * cx + a) + (int64_t)M * ((P * cy + b) + (int64_t)M * (P * cz + c));
     float dsum[3] = {0.f, 0.f, 0.f};
     for (int q = 0; q < NQ; ++q) {
@@ -58,7 +60,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
             dsum[k] += qd[lc][0][q] * NN + N * conv + NN * qd[lc][4 + k][q] +
                        wm * (0.5f * (gg + g[k] * g[k]) - qd[lc][8 + k][q] * g[k] * ng);
     }
-    for (int k = 0; k < 3; ++k) atomicAdd(&diag[k * m.Nu + gidx], dsum[k]);
+    for (int k = 0; k < 3; ++k) acc_add(&diag[k * m.Nu + gidx], dsum[k], colour >= 0);
 }
 
 __device__ __forceinline__ bool dnode(int64_t node, int M, unsigned f) {
@@ -76,6 +78,25 @@ __global__ void k_diag_finish(int M, int64_t Nu, unsigned faces, float* d32, dou
     }
 }
 
+// The cells' diagonal contributions added into acc (zeroed by the caller): one atomic pass, or the 8 colour passes
+// of the deterministic mode.
+static int diagonal_passes(evap_mesh* h, const MeshArgs<float>& m, const Basis<float>& b, float* acc, cudaStream_t s) {
+    const int c0 = h->deterministic ? 0 : -1, c1 = h->deterministic ? 8 : 0;
+    for (int colour = c0; colour < std::max(c1, c0 + 1); ++colour) {
+        const int64_t cells = colour_cells(m.n, colour);
+        if (cells == 0) continue;
+        if (m.P == 2) {
+            constexpr int CB = 8;
+            k_diagonal<2, CB><<<(unsigned)((cells + CB - 1) / CB), CB * 27, 0, s>>>(m, b, h->qc, acc, colour);
+        } else {
+            constexpr int CB = 4;
+            k_diagonal<3, CB><<<(unsigned)((cells + CB - 1) / CB), CB * 64, 0, s>>>(m, b, h->qc, acc, colour);
+        }
+        EVAP_CHECK_LAUNCH("diagonal");
+    }
+    return EVAP_OK;
+}
+
 int launch_diagonal(evap_mesh* h, cudaStream_t s) {
     if (h->diag_valid) return EVAP_OK;
     const int64_t N = 3 * h->m.Nu;
@@ -84,14 +105,8 @@ int launch_diagonal(evap_mesh* h, cudaStream_t s) {
     EVAP_CUDA(cudaMemsetAsync(h->diag32, 0, N * sizeof(float), s));
     const MeshArgs<float> m = mesh_args<float>(h);
     const Basis<float> b = cast_basis<float>(h->b);
-    if (m.P == 2) {
-        constexpr int CB = 8;
-        k_diagonal<2, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 27, 0, s>>>(m, b, h->qc, h->diag32);
-    } else {
-        constexpr int CB = 4;
-        k_diagonal<3, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 64, 0, s>>>(m, b, h->qc, h->diag32);
-    }
-    EVAP_CHECK_LAUNCH("diagonal");
+    int rc = diagonal_passes(h, m, b, h->diag32, s);
+    if (rc) return rc;
     k_diag_finish<<<blocks_for(N, 256), 256, 0, s>>>(m.M, m.Nu, m.faces, h->diag32, h->diag);
     EVAP_CHECK_LAUNCH("diag_finish");
     h->diag_valid = true;
@@ -105,14 +120,8 @@ int launch_diagonal_into(evap_mesh* h, float* acc, double* out, cudaStream_t s) 
     EVAP_CUDA(cudaMemsetAsync(acc, 0, N * sizeof(float), s));
     const MeshArgs<float> m = mesh_args<float>(h);
     const Basis<float> b = cast_basis<float>(h->b);
-    if (m.P == 2) {
-        constexpr int CB = 8;
-        k_diagonal<2, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 27, 0, s>>>(m, b, h->qc, acc);
-    } else {
-        constexpr int CB = 4;
-        k_diagonal<3, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 64, 0, s>>>(m, b, h->qc, acc);
-    }
-    EVAP_CHECK_LAUNCH("diagonal_into");
+    int rc = diagonal_passes(h, m, b, acc, s);
+    if (rc) return rc;
     k_diag_finish<<<blocks_for(N, 256), 256, 0, s>>>(m.M, m.Nu, m.faces, acc, out);
     EVAP_CHECK_LAUNCH("diag_finish_into");
     return EVAP_OK;

@@ -14,12 +14,11 @@ namespace evap {
 template <typename T, int MODE>
 __global__ void __launch_bounds__(128) k_levelset(MeshArgs<T> m, Basis<T> bas, const T* __restrict__ phi,
                                                   const T* __restrict__ nf, const T* __restrict__ ug,
-                                                  const T* __restrict__ x, T* __restrict__ y) {
-    const int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (cell >= m.ncell) return;
+                                                  const T* __restrict__ x, T* __restrict__ y, int colour) {
+    int cx, cy, cz;
+    if (!colour_cell(blockIdx.x * (int64_t)blockDim.x + threadIdx.x, m.n, colour, cx, cy, cz)) return;
     const int n = m.n;
     const int64_t m1 = n + 1;
-    const int cx = (int)(cell % n), cy = (int)((cell / n) % n), cz = (int)(cell / ((int64_t)n * n));
     int64_t node[8];
     T xv[8], pv[8], uv[3][8];
 #pragma unroll
@@ -86,7 +85,7 @@ __global__ void __launch_bounds__(128) k_levelset(MeshArgs<T> m, Basis<T> bas, c
         for (int j = 0; j < 8; ++j) out[j] += N[j] * Fv + dR[j][0] * Gf[0] + dR[j][1] * Gf[1] + dR[j][2] * Gf[2];
     }
 #pragma unroll
-    for (int j = 0; j < 8; ++j) atomicAdd(&y[node[j]], out[j]);
+    for (int j = 0; j < 8; ++j) acc_add(&y[node[j]], out[j], colour >= 0);
 }
 
 // EVAP_ADVECT for the FP64 applies in double-float arithmetic (dfloat.cuh): the same sums with x converted per node,
@@ -94,12 +93,11 @@ __global__ void __launch_bounds__(128) k_levelset(MeshArgs<T> m, Basis<T> bas, c
 // shape values at the Gauss points are compile-time doubles split into pairs.
 __global__ void __launch_bounds__(128) k_levelset_advect_df(MeshArgs<double> m, dfl W, dfl thdt_ih,
                                                             const float2* __restrict__ ug, const double* __restrict__ x,
-                                                            double* __restrict__ y) {
-    const int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (cell >= m.ncell) return;
+                                                            double* __restrict__ y, int colour) {
+    int cx, cy, cz;
+    if (!colour_cell(blockIdx.x * (int64_t)blockDim.x + threadIdx.x, m.n, colour, cx, cy, cz)) return;
     const int n = m.n;
     const int64_t m1 = n + 1;
-    const int cx = (int)(cell % n), cy = (int)((cell / n) % n), cz = (int)(cell / ((int64_t)n * n));
     int64_t node[8];
     dfl xv[8], uv[3][8];
 #pragma unroll
@@ -152,7 +150,7 @@ __global__ void __launch_bounds__(128) k_levelset_advect_df(MeshArgs<double> m, 
         for (int j = 0; j < 8; ++j) df_fma(out[j], N[j], Fv);
     }
 #pragma unroll
-    for (int j = 0; j < 8; ++j) atomicAdd(&y[node[j]], df_to_double(df_norm(out[j])));
+    for (int j = 0; j < 8; ++j) acc_add(&y[node[j]], df_to_double(df_norm(out[j])), colour >= 0);
 }
 
 template <typename T>
@@ -166,24 +164,31 @@ int launch_levelset(evap_mesh* h, int mode, const T* x, T* y, cudaStream_t s) {
     int rc = launch_fill<T>(y, m.Nphi, T(0), s);
     if (rc) return rc;
     const int threads = 128;
-    const unsigned grid = (unsigned)((m.ncell + threads - 1) / threads);
-    if constexpr (sizeof(T) == 8) {
-        if (mode == EVAP_ADVECT) {  // FP64-accurate advection in double-float arithmetic
-            const dfl W = df_from_double(0.125 * (double)m.vol_w);  // 2-point Gauss weights 1/2 per direction
-            const dfl thdt_ih = df_from_double((double)m.theta * (double)m.dt * (double)m.inv_h);
-            k_levelset_advect_df<<<grid, threads, 0, s>>>(m, W, thdt_ih, (const float2*)h->ugammadf, (const double*)x,
-                                                          (double*)y);
-            EVAP_CHECK_LAUNCH("levelset_advect_df");
-            return EVAP_OK;
+    const int c0 = h->deterministic ? 0 : -1, c1 = h->deterministic ? 8 : 0;  // colour passes, or one atomic pass
+    for (int colour = c0; colour < (c1 > c0 + 1 ? c1 : c0 + 1); ++colour) {
+        const int64_t cells = colour_cells(m.n, colour);
+        if (cells == 0) continue;
+        const unsigned grid = (unsigned)((cells + threads - 1) / threads);
+        bool done = false;
+        if constexpr (sizeof(T) == 8) {
+            if (mode == EVAP_ADVECT) {  // FP64-accurate advection in double-float arithmetic
+                const dfl W = df_from_double(0.125 * (double)m.vol_w);  // 2-point Gauss weights 1/2 per direction
+                const dfl thdt_ih = df_from_double((double)m.theta * (double)m.dt * (double)m.inv_h);
+                k_levelset_advect_df<<<grid, threads, 0, s>>>(m, W, thdt_ih, (const float2*)h->ugammadf,
+                                                              (const double*)x, (double*)y, colour);
+                done = true;
+            }
         }
+        if (done) {
+        } else if (mode == EVAP_ADVECT) {
+            k_levelset<T, EVAP_ADVECT><<<grid, threads, 0, s>>>(m, b, phi, nullptr, ug, x, y, colour);
+        } else if (mode == EVAP_REINIT) {
+            k_levelset<T, EVAP_REINIT><<<grid, threads, 0, s>>>(m, b, phi, nf, ug, x, y, colour);
+        } else {
+            k_levelset<T, EVAP_REINIT_RHS><<<grid, threads, 0, s>>>(m, b, phi, nf, ug, x, y, colour);
+        }
+        EVAP_CHECK_LAUNCH("levelset");
     }
-    if (mode == EVAP_ADVECT)
-        k_levelset<T, EVAP_ADVECT><<<grid, threads, 0, s>>>(m, b, phi, nullptr, ug, x, y);
-    else if (mode == EVAP_REINIT)
-        k_levelset<T, EVAP_REINIT><<<grid, threads, 0, s>>>(m, b, phi, nf, ug, x, y);
-    else
-        k_levelset<T, EVAP_REINIT_RHS><<<grid, threads, 0, s>>>(m, b, phi, nf, ug, x, y);
-    EVAP_CHECK_LAUNCH("levelset");
     return EVAP_OK;
 }
 template int launch_levelset<double>(evap_mesh*, int, const double*, double*, cudaStream_t);

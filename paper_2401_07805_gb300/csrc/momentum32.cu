@@ -34,7 +34,7 @@ template <int P, int CB, int MINB>
 __global__ void __launch_bounds__(CB*(P + 1) * (P + 1), MINB)
     k_momentum32(MeshArgs<float> m, Scale32 hs, const int8_t* __restrict__ code,
                  const int32_t* __restrict__ tindex, const float* __restrict__ table, const float* __restrict__ qc32,
-                 const float* __restrict__ x, float* __restrict__ y, float* __restrict__ yp) {
+                 const float* __restrict__ x, float* __restrict__ y, float* __restrict__ yp, int colour) {
     static_assert(CB == 32, "the qc32 layout is for 32-cell blocks");
     constexpr int Q = P + 1, NQ = Q * Q * Q, L = Q * Q;
     constexpr int OFF_Z = 3 * NQ, OFF_Y = 6 * NQ, OFF_PD = 9 * NQ, OFF_QD = OFF_PD + 2 * L;
@@ -44,12 +44,30 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1), MINB)
     const int tid = threadIdx.x;
     const int lc = tid % CB, l = tid / CB;
     const int n = m.n, M = m.M;
-    // A block holds CB consecutive cells of one x-row: (cx, cy, cz) = (CB * xb + lc, row % n, row / n).
+    // A block holds CB consecutive cells of one x-row: (cx, cy, cz) = (CB * xb + lc, row % n, row / n).  In a colour
+    // pass (colour = pb + 2 py + 4 pz >= 0) the blocks with xb = pb mod 2 of the rows with cy = py, cz = pz mod 2:
+    // two such blocks share no node, and inside a block the even cells scatter before the odd ones.
     const int nxc = (n + CB - 1) / CB;
-    const int row = (int)(blockIdx.x / (unsigned)nxc);
-    const int cx = ((int)blockIdx.x - row * nxc) * CB + lc, cy = row % n, cz = row / n;
-    const bool active = cx < n;
-    const int64_t cell = cx + (int64_t)n * row;
+    int cx, cy, cz;
+    bool active;
+    if (colour < 0) {
+        const int row = (int)(blockIdx.x / (unsigned)nxc);
+        cx = ((int)blockIdx.x - row * nxc) * CB + lc;
+        cy = row % n;
+        cz = row / n;
+        active = cx < n;
+    } else {
+        const int pb = colour & 1, py = (colour >> 1) & 1, pz = colour >> 2;
+        const int hy = (n - py + 1) >> 1, hxb = (nxc - pb + 1) >> 1;
+        const int rowc = (int)(blockIdx.x / (unsigned)hxb);
+        const int xb = 2 * ((int)blockIdx.x - rowc * hxb) + pb;
+        cx = xb * CB + lc;
+        cy = 2 * (rowc % hy) + py;
+        cz = 2 * (rowc / hy) + pz;
+        active = cx < n;
+    }
+    const bool plain = colour >= 0;
+    const int64_t cell = cx + (int64_t)n * (cy + (int64_t)n * cz);
     float* cs = sm + lc;
     auto S_ = [cs](int slot) -> float& { return cs[slot * CB]; };
     auto at = [](int z, int yy, int xx) { return xx + Q * (yy + Q * z); };
@@ -137,7 +155,9 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1), MINB)
                 }
             const int8_t cc = code[cell];
             const float* tb = cc == CELL_TABLE ? table + (int64_t)tindex[cell] * TAB_K * NQ : nullptr;
-            const float* cq = qc32 + (int64_t)blockIdx.x * QC32_K * NQ * 32 + lc;
+            // the cache's block of 32 x-consecutive cells holding this cell, and its place in it
+            const int64_t cblk = (int64_t)(cy + n * cz) * nxc + cx / CB;
+            const float* cq = qc32 + cblk * QC32_K * NQ * 32 + cx % CB;
             const float wyz = B.wf[qy] * B.wf[qz];
             float Pv[3][Q], Py[3][Q], Pz[3][Q], Pd[2];
 #pragma unroll
@@ -256,6 +276,9 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1), MINB)
     // ---------------------------------------------------------------- z-lines backwards and scatter
     {
         const int i = l % Q, j = l / Q;
+        float o[3][Q], s0 = 0.f, s1 = 0.f;
+        const bool div = yp && l < 4;  // divergence row: z-sweep, Q1 node (jx, jy, jz)
+        const int jx = l % 2, jy = l / 2;
         if (active) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
@@ -267,38 +290,65 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1), MINB)
                 }
 #pragma unroll
                 for (int k = 0; k < Q; ++k) {
-                    float o = 0.f;
+                    float v = 0.f;
 #pragma unroll
-                    for (int q = 0; q < Q; ++q) o += (float)B.S[q][k] * r[q] + (float)B.D[q][k] * rz[q];
-                    if (keep[k]) atomicAdd(&y[c * m.Nu + zbase + k * MM], o);
+                    for (int q = 0; q < Q; ++q) v += (float)B.S[q][k] * r[q] + (float)B.D[q][k] * rz[q];
+                    o[c][k] = v;
                 }
             }
-            if (yp && l < 4) {  // divergence row: z-sweep, Q1 node (jx, jy, jz)
-                const int jx = l % 2, jy = l / 2;
-                float s0 = 0.f, s1 = 0.f;
+            if (div) {
 #pragma unroll
                 for (int q = 0; q < Q; ++q) {
                     const float v = S_(OFF_QD + jx + 2 * (jy + 2 * q));
                     s0 += (float)B.N1[q][0] * v;
                     s1 += (float)B.N1[q][1] * v;
                 }
-                const int64_t m1 = n + 1;
-                atomicAdd(&yp[(cx + jx) + m1 * ((cy + jy) + m1 * (cz + 0))], s0);
-                atomicAdd(&yp[(cx + jx) + m1 * ((cy + jy) + m1 * (cz + 1))], s1);
+            }
+        }
+        // atomic adds in one go; in a colour pass the even cells of the block first, then (after a block barrier)
+        // the odd ones, so that the two cells of a shared x-face never write at once
+        for (int par = 0; par < (plain ? 2 : 1); ++par) {
+            if (plain && par == 1) __syncthreads();
+            if (active && (!plain || (lc & 1) == par)) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+#pragma unroll
+                    for (int k = 0; k < Q; ++k)
+                        if (keep[k]) acc_add(&y[c * m.Nu + zbase + k * MM], o[c][k], plain);
+                if (div) {
+                    const int64_t m1 = n + 1;
+                    acc_add(&yp[(cx + jx) + m1 * ((cy + jy) + m1 * (cz + 0))], s0, plain);
+                    acc_add(&yp[(cx + jx) + m1 * ((cy + jy) + m1 * (cz + 1))], s1, plain);
+                }
             }
         }
     }
 }
 
 template <int P>
-static void launch32(const evap_mesh* h, const MeshArgs<float>& m, const Scale32& hs, const float* x, float* y,
-                     float* yp, cudaStream_t s) {
+static int launch32(const evap_mesh* h, const MeshArgs<float>& m, const Scale32& hs, const float* x, float* y,
+                    float* yp, cudaStream_t s) {
     constexpr int L = (P + 1) * (P + 1);
     constexpr int CB = 32;                // one warp per line: 288 / 512 threads
     constexpr int MINB = P == 2 ? 3 : 1;  // 35 KB / 80 KB of shared memory per block
-    const unsigned grid = (unsigned)(((m.n + CB - 1) / CB) * (int64_t)m.n * m.n);
-    k_momentum32<P, CB, MINB><<<grid, CB * L, 0, s>>>(m, hs, h->cell_code, h->table_index, h->table32, h->qc32, x, y,
-                                                       yp);
+    if (!h->deterministic) {
+        const unsigned grid = (unsigned)(((m.n + CB - 1) / CB) * (int64_t)m.n * m.n);
+        k_momentum32<P, CB, MINB><<<grid, CB * L, 0, s>>>(m, hs, h->cell_code, h->table_index, h->table32, h->qc32, x,
+                                                           y, yp, -1);
+        EVAP_CHECK_LAUNCH("momentum32");
+        return EVAP_OK;
+    }
+    const int64_t nxc = (m.n + CB - 1) / CB;
+    for (int colour = 0; colour < 8; ++colour) {  // block parity along x and row parities, one launch each
+        const int pb = colour & 1, py = (colour >> 1) & 1, pz = colour >> 2;
+        const int64_t hxb = (nxc - pb + 1) / 2, hy = (m.n - py + 1) / 2, hz = (m.n - pz + 1) / 2;
+        const int64_t grid = hxb * hy * hz;
+        if (grid == 0) continue;
+        k_momentum32<P, CB, MINB><<<(unsigned)grid, CB * L, 0, s>>>(m, hs, h->cell_code, h->table_index, h->table32,
+                                                                     h->qc32, x, y, yp, colour);
+        EVAP_CHECK_LAUNCH("momentum32");
+    }
+    return EVAP_OK;
 }
 
 int launch_momentum32(evap_mesh* h, const float* x, float* y, float* yp, cudaStream_t s) {
@@ -309,12 +359,7 @@ int launch_momentum32(evap_mesh* h, const float* x, float* y, float* yp, cudaStr
     hs.h3 = (float)(hh * hh * hh);
     hs.c2h = (float)(2.0 * hh);
     hs.hcm = (float)(hh * hh * hh * h->m.c_mass);
-    if (m.P == 2)
-        launch32<2>(h, m, hs, x, y, yp, s);
-    else
-        launch32<3>(h, m, hs, x, y, yp, s);
-    EVAP_CHECK_LAUNCH("momentum32");
-    return EVAP_OK;
+    return m.P == 2 ? launch32<2>(h, m, hs, x, y, yp, s) : launch32<3>(h, m, hs, x, y, yp, s);
 }
 
 }  // namespace evap

@@ -23,6 +23,8 @@
 // so that their HBM latency is hidden behind the interpolation sweeps (without it, waits on these loads were the top
 // stall).  The correction term is skipped at points where its
 // gate z n is zero (outside the interface zone), and the Newton terms on Picard meshes.
+#include <algorithm>
+
 #include "dfloat.cuh"
 #include "physics.cuh"
 
@@ -55,7 +57,7 @@ constexpr size_t df_coeff_smem() {
 template <int P, int CB, bool PRES, int MINB = 1>
 __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1), MINB)
     k_momentum_df(MeshArgs<double> m, DfBasis bas, const float2* __restrict__ qc, const double* __restrict__ x,
-                  double* __restrict__ y, double* __restrict__ yp, const double* __restrict__ pin) {
+                  double* __restrict__ y, double* __restrict__ yp, const double* __restrict__ pin, int colour) {
     constexpr int Q = P + 1, NQ = Q * Q * Q;
     __shared__ dfl sS[Q][Q], sDc[Q][Q], sN1[Q][2];
     __shared__ dfl buf[2][6][CB][NQ];  // [half][slot][cell][point]
@@ -63,8 +65,10 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1), MINB)
     extern __shared__ float2 sqc[];  // [cell][QC_K][point]: this block's coefficients, copied while the sweeps run
     const int tid = threadIdx.x;
     const int lc = tid / NQ, t = tid % NQ;
-    const int64_t cell = (int64_t)blockIdx.x * CB + lc;
-    const bool active = cell < m.ncell;
+    int cx = 0, cy = 0, cz = 0;
+    const bool active = colour_cell((int64_t)blockIdx.x * CB + lc, m.n, colour, cx, cy, cz);
+    const int64_t cell = cx + (int64_t)m.n * (cy + (int64_t)m.n * cz);
+    const bool plain = colour >= 0;  // a colour pass: no other cell of the launch touches this cell's nodes
     float2* myq = sqc + (int64_t)lc * QC_K * NQ + t;
     if (active) {  // each thread fetches (and later reads) only its own point's coefficients
         const float2* src = qc + cell * QC_K * NQ + t;
@@ -80,13 +84,9 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1), MINB)
     if (tid < 2 * Q) sN1[tid / 2][tid % 2] = bas.N1[tid / 2][tid % 2];
     const int a = t % Q, b = (t / Q) % Q, c = t / (Q * Q);
     const int n = m.n, M = m.M;
-    int cx = 0, cy = 0, cz = 0;
     int64_t gidx = 0;
     bool cons = false;
     if (active) {
-        cx = (int)(cell % n);
-        cy = (int)((cell / n) % n);
-        cz = (int)(cell / ((int64_t)n * n));
         const int gx = P * cx + a, gy = P * cy + b, gz = P * cz + c;
         gidx = gx + (int64_t)M * (gy + (int64_t)M * gz);
         cons = constrained_node(gx, gy, gz, M, m.faces);
@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1), MINB)
 #pragma unroll
             for (int qq = 1; qq < Q; ++qq) df_fma(s, sN1[qq][jz], q1b[lc][jx + 2 * (jy + 2 * qq)]);
             const int64_t m1 = n + 1;
-            atomicAdd(&yp[(cx + jx) + m1 * ((cy + jy) + m1 * (cz + jz))], df_to_double(df_norm(s)));
+            acc_add(&yp[(cx + jx) + m1 * ((cy + jy) + m1 * (cz + jz))], df_to_double(df_norm(s)), plain);
         }
     }
     __syncthreads();
@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1), MINB)
         for (int k = 0; k < Q; ++k) Ta[k] = sS[k][a];
 #pragma unroll
         for (int k = 0; k < 3; ++k)
-            atomicAdd(&y[k * m.Nu + gidx], df_to_double(df_dot<Q>(Ta, &buf[0][k][lc][Q * (b + Q * c)], 1)));
+            acc_add(&y[k * m.Nu + gidx], df_to_double(df_dot<Q>(Ta, &buf[0][k][lc][Q * (b + Q * c)], 1)), plain);
     }
 }
 
@@ -300,35 +300,30 @@ int launch_momentum_df(evap_mesh* h, const MeshArgs<double>& m, const double* x,
                        const double* p, cudaStream_t s) {
     const DfBasis b = make_df_basis(h->b, m.inv_h);
     const float2* qc = reinterpret_cast<const float2*>(h->qcdf);
+    const int c0 = h->deterministic ? 0 : -1, c1 = h->deterministic ? 8 : 0;  // colour passes, or one atomic pass
+    auto run = [&](auto kern, int CB, int threads, size_t dyn) -> int {
+        EVAP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+        for (int colour = c0; colour < std::max(c1, c0 + 1); ++colour) {
+            const int64_t cells = colour_cells(m.n, colour);
+            if (cells == 0) continue;
+            const unsigned grid = (unsigned)((cells + CB - 1) / CB);
+            kern<<<grid, threads, dyn, s>>>(m, b, qc, x, y, yp, p, colour);
+            EVAP_CHECK_LAUNCH("momentum_df");
+        }
+        return EVAP_OK;
+    };
+    int rc;
     if (m.P == 2) {
         constexpr int CB = EVAP_DF_CB2, MINB = EVAP_DF_MINB2;
         constexpr size_t dyn = df_coeff_smem<2, CB>();
-        const unsigned grid = (unsigned)((m.ncell + CB - 1) / CB);
-        if (p) {
-            EVAP_CUDA(cudaFuncSetAttribute(k_momentum_df<2, CB, true, MINB>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
-            k_momentum_df<2, CB, true, MINB><<<grid, CB * 27, dyn, s>>>(m, b, qc, x, y, yp, p);
-        } else {
-            EVAP_CUDA(cudaFuncSetAttribute(k_momentum_df<2, CB, false, MINB>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
-            k_momentum_df<2, CB, false, MINB><<<grid, CB * 27, dyn, s>>>(m, b, qc, x, y, yp, nullptr);
-        }
+        rc = p ? run(k_momentum_df<2, CB, true, MINB>, CB, CB * 27, dyn)
+               : run(k_momentum_df<2, CB, false, MINB>, CB, CB * 27, dyn);
     } else {
         constexpr int CB = 4;
         constexpr size_t dyn = df_coeff_smem<3, CB>();
-        const unsigned grid = (unsigned)((m.ncell + CB - 1) / CB);
-        if (p) {
-            EVAP_CUDA(cudaFuncSetAttribute(k_momentum_df<3, CB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)dyn));
-            k_momentum_df<3, CB, true><<<grid, CB * 64, dyn, s>>>(m, b, qc, x, y, yp, p);
-        } else {
-            EVAP_CUDA(cudaFuncSetAttribute(k_momentum_df<3, CB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)dyn));
-            k_momentum_df<3, CB, false><<<grid, CB * 64, dyn, s>>>(m, b, qc, x, y, yp, nullptr);
-        }
+        rc = p ? run(k_momentum_df<3, CB, true>, CB, CB * 64, dyn) : run(k_momentum_df<3, CB, false>, CB, CB * 64, dyn);
     }
-    EVAP_CHECK_LAUNCH("momentum_df");
-    return EVAP_OK;
+    return rc;
 }
 
 }  // namespace evap
