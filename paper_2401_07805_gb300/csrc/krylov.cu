@@ -699,9 +699,21 @@ int solve_gmres(evap_mesh* h, const double* f, double* x, int mixed, int m, doub
 // momentum operator with its Jacobi preconditioner (the mixed solve's inner method); S~^(-1): CG on
 // B diag(A)^(-1) B^T (schur_apply).  Both are inexact and vary between applications, so the outer method stores the
 // preconditioned directions (flexible GMRES); the outer vectors are FP64 [x (3 N_u) | p (N_phi)].
-constexpr int SADDLE_INNER_M = 10;      // FP32 GMRES applications per velocity-block solve
+// Budgets of the two inexact inner solves.  Measured on the 64^3 four-sphere case with the top face open (GB300; ms
+// and outer applications: solve to 1e-4 / solve to 1e-8 / three consecutive time steps to 1e-8):
+//   velocity 10, Schur CG 24: 43.7 (6) / 405 (42) / 99.6, 90.4, 70.0
+//   velocity 10, Schur CG 12: 30.1 (6) / 408 (60) / 70.1, 76.1, 70.1
+//   velocity 10, Schur CG 8:  25.5 (6) / 478 (84) / 74.3, 86.5, 129.3
+//   velocity 14, Schur CG 12: 30.1 (6) / 407 (60) / 62.9, 63.0, 63.6
+#ifndef EVAP_SADDLE_INNER_M
+#define EVAP_SADDLE_INNER_M 14
+#endif
+#ifndef EVAP_SADDLE_SCHUR_CG
+#define EVAP_SADDLE_SCHUR_CG 12
+#endif
+constexpr int SADDLE_INNER_M = EVAP_SADDLE_INNER_M;    // FP32 GMRES applications per velocity-block solve
 constexpr double SADDLE_INNER_TOL = 1e-2;
-constexpr int SADDLE_SCHUR_CG = 24;     // CG iterations per pressure Poisson solve
+constexpr int SADDLE_SCHUR_CG = EVAP_SADDLE_SCHUR_CG;  // CG iterations per pressure Poisson solve
 
 // v = b - v
 // b += xd - kd: the lifting of Dirichlet data xd (K_D [xd] = kd) into the right-hand side.
