@@ -246,7 +246,7 @@ int evap_apply_saddle(evap_handle h, const double* x, const double* p, double* y
 /* Solve [A, -B^T; B, 0] [x; p] = [f; g] (g the continuity right-hand side of the fields) by flexible GMRES(restart)
  * with the block upper-triangular right preconditioner [A~, -B^T; 0, S~]: A~^(-1) a fixed budget of 14 FP32 GMRES
  * applications on A with the preconditioner of evap_solve, S~ = B diag(A)^(-1) B^T (an approximation of the Schur
- * complement B A^(-1) B^T that keeps the discrete B and so the pressure nodes of open faces) solved by 12 CG
+ * complement B A^(-1) B^T that keeps the discrete B and so the pressure nodes of open faces) solved by 24 CG
  * iterations with its operator applied in FP32: the block-triangular preconditioner of Sec. 2.5 with its ILU velocity
  * block and its Cahouet-Chabard Schur approximation replaced.
  * Dirichlet data: the entries of f on the Dirichlet DoFs are the prescribed velocity there (0 for walls at rest, an

@@ -361,6 +361,9 @@ template int launch_divergence<float>(evap_mesh*, const float*, const float*, fl
 // CG runs in FP64; its operator is applied in FP32 (gradient, scaling by the FP32 Jacobi diagonal of A, divergence):
 // B and B^T are FP64-pipe bound at ~45 FMA per velocity point, and a preconditioner needs no FP64 operator.
 // Scratch: t32 [3 N_u] and pq32 [2 N_p] floats.
+#ifndef EVAP_SADDLE_SCHUR_RTOL
+#define EVAP_SADDLE_SCHUR_RTOL 1e-6
+#endif
 int schur_apply(evap_mesh* h, const double* r, double* z, const double* d, float* t32, float* pq32, int cg_iters,
                 cudaStream_t st) {
     const int64_t Nu3 = 3 * h->m.Nu, Np = h->m.Np;
@@ -376,7 +379,7 @@ int schur_apply(evap_mesh* h, const double* r, double* z, const double* d, float
         if ((e = launch_divergence<float>(h, t32, diag32, q32, st))) return e;  // B diag^(-1) t
         return launch_to_double(q32, q, Np, st);
     };
-    const int rc = geo_cg(h, apply, r, d, z, 1e-6, 0.0, cg_iters, nullptr, st);
+    const int rc = geo_cg(h, apply, r, d, z, EVAP_SADDLE_SCHUR_RTOL, 0.0, cg_iters, nullptr, st);
     return rc == EVAP_ENOTCONV ? EVAP_OK : rc;
 }
 
