@@ -243,6 +243,12 @@ int evap_solve(evap_handle h, const double* f, double* x, int mixed, int restart
  * (dirichlet_faces) are open: the weak form's natural condition (zero traction) holds there. */
 int evap_apply_saddle(evap_handle h, const double* x, const double* p, double* y, double* y_p, void* stream);
 
+/* y = S~ x with S~ = B diag(A)^(-1) B^T, the Schur approximation of the velocity-pressure preconditioner (B the
+ * divergence row, diag(A) the FP32 Jacobi diagonal of the momentum operator, the velocity DoFs of Dirichlet faces left
+ * out), assembled as a symmetric 125-point stencil on the Q1 pressure lattice and applied in FP32 arithmetic.
+ * x, y [N_p] device arrays, FP64.  Exposed to check the assembled operator against B diag(A)^(-1) B^T. */
+int evap_apply_schur(evap_handle h, const double* x, double* y, void* stream);
+
 /* Solve [A, -B^T; B, 0] [x; p] = [f; g] (g the continuity right-hand side of the fields) by flexible GMRES(restart)
  * with the block upper-triangular right preconditioner [A~, -B^T; 0, S~]: A~^(-1) a fixed budget of 14 FP32 GMRES
  * applications on A with the preconditioner of evap_solve, S~ = B diag(A)^(-1) B^T (an approximation of the Schur

@@ -66,6 +66,7 @@ SIGNATURES = {
                                 _c_int, _c_dbl, ctypes.POINTER(_c_int), ctypes.POINTER(_c_dbl),
                                 ctypes.POINTER(_c_dbl), _vp]),
     "evap_apply_saddle": (_c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "evap_apply_schur": (_c_int, [_vp, _vp, _vp, _vp]),
     "evap_solve_saddle": (_c_int, [_vp, _vp, _vp, _vp, _c_int, _c_dbl, _c_int, ctypes.POINTER(_c_int),
                                    ctypes.POINTER(_c_dbl), _vp]),
     "evap_surface_tension": (_c_int, [_vp, _vp, _vp, _c_dbl, _vp, _vp]),
@@ -322,6 +323,14 @@ class Operator:
         yp = torch.empty(self.n_p, dtype=torch.float64, device=self.device)
         _check(lib().evap_apply_saddle(self._h, _ptr(x), _ptr(p), _ptr(y), _ptr(yp), _stream()), "evap_apply_saddle")
         return y, yp
+
+    def apply_schur(self, x: torch.Tensor):
+        """S~ x, S~ = B diag(A)^-1 B^T assembled on the pressure lattice (the velocity-pressure preconditioner's Schur
+        approximation), in FP32 arithmetic."""
+        x = self._dev(x, self.n_p, torch.float64, "x")
+        y = torch.empty(self.n_p, dtype=torch.float64, device=self.device)
+        _check(lib().evap_apply_schur(self._h, _ptr(x), _ptr(y), _stream()), "evap_apply_schur")
+        return y
 
     def solve_saddle(self, f: torch.Tensor, x0=None, p0=None, restart: int = 30, rtol: float = 1e-8,
                      max_iter: int = 600, raise_on_notconv: bool = False):

@@ -173,6 +173,10 @@ struct evap_mesh {
     bool checks = false;
     // deterministic accumulation (evap_set_deterministic): 8 colour passes instead of atomic adds
     bool deterministic = false;
+    // assembled Schur approximation of the velocity-pressure preconditioner (schur.cu): [63][N_p] FP32, valid while
+    // schur_stamp equals diag_stamp (incremented whenever the Jacobi diagonal of A is rebuilt)
+    float* schur_S = nullptr;
+    unsigned long long schur_stamp = 0, diag_stamp = 0;
     unsigned long long* nonfinite = nullptr;
     // time step workspace: inertia load [3 N_u], advected level set [N_phi], projected normal [3 N_phi]
     double* step_ws = nullptr;
@@ -252,10 +256,6 @@ int geo_reinitialize(evap_mesh* h, double* psi, int steps, int* iters, double* l
 int geo_advect_levelset(evap_mesh* h, double* phi, int max_iters, double tol, int* fp_iters, int* lin_iters,
                         double* last_change, cudaStream_t s);
 // Jacobi diagonal (in the geometry workspace, valid until the next geometry call) for CG on the pressure Schur
-// approximation B diag(A)^(-1) B^T, and the Q1 CG engine of the geometry sub-solver for an arbitrary SPD apply.
-int geo_schur_setup(evap_mesh* h, double** diag, cudaStream_t s);
-int geo_cg(evap_mesh* h, const std::function<int(const double*, double*)>& apply, const double* b, const double* d,
-           double* x, double rtol, double atol, int max_iter, int* iters, cudaStream_t s);
 // velocity-pressure coupling (saddle.cu)
 template <typename T>
 int launch_pressure_gradient(evap_mesh* h, const T* p, T scale, T* y, cudaStream_t s);
@@ -277,9 +277,13 @@ int time_step(evap_mesh* h, double* phi, double* u, double* p, const double* mdo
 template <typename T>
 int launch_divergence(evap_mesh* h, const T* x, const T* diag, T* yp, cudaStream_t s);
 // z = S~^(-1) r by at most cg_iters CG iterations on S~ = B diag(A)^(-1) B^T (applied in FP32) with the Jacobi
-// diagonal d of geo_schur_setup (scratch: t32 [3 N_u], pq32 [2 N_phi] floats)
-int schur_apply(evap_mesh* h, const double* r, double* z, const double* d, float* t32, float* pq32, int cg_iters,
-                cudaStream_t s);
+// The assembled Schur approximation S~ = B diag(A)^-1 B^T (schur.cu): assembly for the current diagonal of A, y = S~ x,
+// and z ~ S~^-1 r by the FP32 single-launch CG (at most max_iter iterations or |r| <= rtol |r0|).
+int schur_assemble(evap_mesh* h, cudaStream_t s);
+int launch_schur_apply(evap_mesh* h, const double* x, double* y, cudaStream_t s);
+int schur_solve(evap_mesh* h, const double* r, double* z, double rtol, int max_iter, int* iters, cudaStream_t s);
+// z ~ S~^-1 r for the velocity-pressure preconditioner (saddle.cu): schur_solve with the preconditioner's tolerance
+int schur_apply(evap_mesh* h, const double* r, double* z, int cg_iters, cudaStream_t st);
 int launch_surface_tension(evap_mesh* h, const double* nf, const double* kappa, double alpha, double* out,
                            cudaStream_t s);
 int launch_diagonal_into(evap_mesh* h, float* acc, double* out, cudaStream_t s);

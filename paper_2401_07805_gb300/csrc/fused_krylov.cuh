@@ -23,6 +23,7 @@ constexpr int FK_THREADS = 512;
 constexpr int FK_WARPS = FK_THREADS / 32;
 constexpr unsigned FK_SPIN_LIMIT = 1u << 24;  // polls of one L2 round trip each: ~0.5 s
 constexpr int GM_MAX = 30;                    // largest GMRES restart length
+constexpr int FK_MAX_BLOCKS = 304;            // largest grid (2 blocks per SM of a 152-SM GPU): sizes the partials
 
 struct GridBarrier {
     unsigned long long count;  // arrivals since the launch (zeroed by the host before it)
@@ -546,6 +547,144 @@ __global__ void __launch_bounds__(FK_THREADS) k_gmres_fused(Op op, int64_t N, in
         out[1] = s_res;
         out[2] = s_bn;
     }
+}
+
+// ------------------------------------------------------------------------------------- FP32 conjugate gradients
+// The same Chronopoulos-Gear CG in FP32 for operators whose solve only has to be approximate (the Schur solve inside
+// the velocity-pressure preconditioner): vectors and coefficients in FP32, the scalar products summed in FP32 in a
+// fixed order (warp shuffle trees, then the blocks' partials), the scalars formed in FP64 by thread 0.  Op::row
+// returns float.  b and x are FP64 (converted once in and out).  Same out[] convention as k_cg_fused.
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;  // valid in lane 0
+}
+
+template <class Op>
+__global__ void __launch_bounds__(FK_THREADS) k_cg_fused32(Op op, int64_t N, const double* __restrict__ b, double* x,
+                                                           float* xs, float* dinv, float* r, float* u, float* p,
+                                                           float* sv, float* w, double rtol, double atol, int max_iter,
+                                                           float* part, GridBarrier* gb, double* out) {
+    extern __shared__ float op_sm32[];
+    __shared__ float sh[3 * FK_WARPS];
+    __shared__ double s_res, s_r0;
+    __shared__ float s_alpha, s_beta;
+    __shared__ int s_go;
+    unsigned long long bar = 0;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t i0 = blockIdx.x * (int64_t)FK_THREADS + threadIdx.x, stride = (int64_t)gridDim.x * FK_THREADS;
+    op.load(op_sm32);
+    __syncthreads();
+    for (int64_t i = i0; i < N; i += stride) {
+        const float ri = (float)b[i], di = 1.0f / op.diag(i, op_sm32);
+        xs[i] = 0.f;
+        r[i] = ri;
+        u[i] = ri * di;
+        p[i] = 0.f;
+        sv[i] = 0.f;
+        dinv[i] = di;
+    }
+    if (!grid_barrier(gb, bar)) return;
+    double gamma_old = 0.0, alpha_old = 1.0, target = 0.0;  // thread 0's copies (the same in every block)
+    int it = 0;
+    for (;;) {
+        float acc[3] = {0.f, 0.f, 0.f};  // (r, u), (w, u), (r, r)
+        for (int64_t i = i0; i < N; i += stride) {
+            const float wi = op.row(i, u, op_sm32), ui = u[i], ri = r[i];
+            w[i] = wi;
+            acc[0] = fmaf(ri, ui, acc[0]);
+            acc[1] = fmaf(wi, ui, acc[1]);
+            acc[2] = fmaf(ri, ri, acc[2]);
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) acc[k] = warp_sum_f(acc[k]);
+        __syncthreads();
+        if (lane == 0)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) sh[k * FK_WARPS + wid] = acc[k];
+        __syncthreads();
+        if (wid < 3) {
+            float t = lane < FK_WARPS ? sh[wid * FK_WARPS + lane] : 0.f;
+            t = warp_sum_f(t);
+            if (lane == 0) part[wid * gridDim.x + blockIdx.x] = t;
+        }
+        if (!grid_barrier(gb, bar)) return;
+        if (wid < 3) {
+            float t = 0.f;
+            for (int q = lane; q < (int)gridDim.x; q += 32) t += __ldcg(part + wid * gridDim.x + q);
+            t = warp_sum_f(t);
+            if (lane == 0) sh[wid] = t;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const double gam = sh[0], del = sh[1], res = sqrt(fmax((double)sh[2], 0.0));
+            if (it == 0) {
+                s_r0 = res;
+                target = fmax(rtol * res, atol);
+            }
+            s_res = res;
+            s_go = res > target && it < max_iter;
+            const double beta = it == 0 ? 0.0 : (gamma_old != 0.0 ? gam / gamma_old : 0.0);
+            const double den = it == 0 ? del : del - beta * gam / alpha_old;
+            const double alpha = den != 0.0 ? gam / den : 0.0;
+            s_alpha = (float)alpha;
+            s_beta = (float)beta;
+            gamma_old = gam;
+            alpha_old = alpha;
+        }
+        __syncthreads();
+        if (!s_go) break;
+        ++it;
+        const float alpha = s_alpha, beta = s_beta;
+        for (int64_t i = i0; i < N; i += stride) {
+            const float pi = fmaf(beta, p[i], u[i]), si = fmaf(beta, sv[i], w[i]);
+            const float ri = fmaf(-alpha, si, r[i]);
+            p[i] = pi;
+            sv[i] = si;
+            xs[i] = fmaf(alpha, pi, xs[i]);
+            r[i] = ri;
+            u[i] = ri * dinv[i];
+        }
+        if (!grid_barrier(gb, bar)) return;
+    }
+    for (int64_t i = i0; i < N; i += stride) x[i] = (double)xs[i];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        out[0] = (double)it;
+        out[1] = s_res;
+        out[2] = s_r0;
+    }
+}
+
+// ------------------------------------------------------------------------------------------ host-side workspace
+// Workspace of the single-launch solvers, kept with the mesh (geometry.cu): nvec pair vectors of N_phi entries (or,
+// read as floats, 2 nvec float vectors), an FP32 vector, (GM_MAX + 2) CG_BLOCKS partial pairs, the barrier, 4 result
+// words and the Helmholtz coefficient table.
+struct FusedSpace {
+    float2* vec;  // vector k at vec + k N
+    float* dinv;
+    float2* part;
+    GridBarrier* gb;
+    double* out;
+    float2* table;
+};
+int fused_space(evap_mesh* h, int nvec, FusedSpace& f);
+// the launch's result words (iterations, |r|, |r0|) and its barrier's error word, after one synchronization
+int fused_result(evap_mesh* h, const FusedSpace& f, cudaStream_t s, double res[3]);
+
+// Grid of a single-launch solver: as many blocks as can be co-resident, at most 2 per SM and `cap` in all.
+template <class K>
+inline int fused_grid(K kernel, size_t smem, int cap, int& G) {
+    int dev = 0, sms = 0, per_sm = 0;
+    EVAP_CUDA(cudaGetDevice(&dev));
+    EVAP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    EVAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, FK_THREADS, smem));
+    G = per_sm < 2 ? per_sm * sms : 2 * sms;
+    if (G > cap) G = cap;
+    if (G < 1) {
+        set_error("single-launch solver: no block of " + std::to_string(FK_THREADS) + " threads fits on an SM");
+        return EVAP_ECUDA;
+    }
+    return EVAP_OK;
 }
 
 }  // namespace evap

@@ -209,13 +209,11 @@ __global__ void __launch_bounds__(128) k_curvature_rhs(MeshArgs<double> m, Basis
     for (int j = 0; j < 8; ++j) atomicAdd(&b[c.node[j]], out[j]);
 }
 
-// ------------------------------------------------------------------------------- conjugate gradients (FP64)
-// Scalars on the device: S[0] r.z, S[1] p.q, S[2] r.r, S[3] r0.r0, S[4] beta.  Every reduction is finished by
-// the last block to arrive (memory fence + atomic ticket; no block waits on another), so an iteration needs no
-// host round trip; the host reads |r| every CG_CHECK iterations.
+// ------------------------------------------------------------------------------- norms of level-set changes
+// |a - b|^2 into a device scalar (the advection fixed point's and the reinitialization's change): block sums, then
+// the last block to arrive (memory fence + atomic ticket; no block waits on another) adds the partials.
 constexpr int CG_THREADS = 256;
 constexpr int CG_BLOCKS = 304;
-constexpr int CG_CHECK = 8;
 
 __device__ __forceinline__ double cg_block_sum(double v) {
     __shared__ double sh[CG_THREADS / 32];
@@ -262,71 +260,6 @@ __device__ __forceinline__ bool cg_finish2(double a, double b, double* part, uns
     return true;
 }
 
-// x = 0, r = b, z = r / diag, p = z; S0 = r.z, S2 = S3 = r.r
-__global__ void __launch_bounds__(CG_THREADS) k_cg_start(const double* __restrict__ b, const double* __restrict__ dg,
-                                                         double* x, double* r, double* z, double* p, int64_t N,
-                                                         double* part, unsigned* ticket, double* S) {
-    double rz = 0.0, rr = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-        const double ri = b[i], zi = ri / dg[i];
-        x[i] = 0.0;
-        r[i] = ri;
-        z[i] = zi;
-        p[i] = zi;
-        rz += ri * zi;
-        rr += ri * ri;
-    }
-    double tot[2];
-    if (cg_finish2(cg_block_sum(rz), cg_block_sum(rr), part, ticket, tot) && threadIdx.x == 0) {
-        S[0] = tot[0];
-        S[2] = tot[1];
-        S[3] = tot[1];
-    }
-}
-
-// S1 = p.q
-__global__ void __launch_bounds__(CG_THREADS) k_cg_pq(const double* __restrict__ p, const double* __restrict__ q,
-                                                      int64_t N, double* part, unsigned* ticket, double* S) {
-    double s = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
-        s += p[i] * q[i];
-    double tot[2];
-    if (cg_finish2(cg_block_sum(s), 0.0, part, ticket, tot) && threadIdx.x == 0) S[1] = tot[0];
-}
-
-// alpha = S0 / S1; x += alpha p; r -= alpha q; z = r / diag; then beta = (r.z)_new / S0, S0 = (r.z)_new, S2 = r.r
-__global__ void __launch_bounds__(CG_THREADS) k_cg_update(double* x, double* r, const double* __restrict__ p,
-                                                          const double* __restrict__ q, const double* __restrict__ dg,
-                                                          double* z, int64_t N, double* part, unsigned* ticket,
-                                                          double* S) {
-    const double pq = S[1];
-    const double alpha = pq != 0.0 ? S[0] / pq : 0.0;
-    double rz = 0.0, rr = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-        x[i] += alpha * p[i];
-        const double ri = r[i] - alpha * q[i];
-        const double zi = ri / dg[i];
-        r[i] = ri;
-        z[i] = zi;
-        rz += ri * zi;
-        rr += ri * ri;
-    }
-    double tot[2];
-    if (cg_finish2(cg_block_sum(rz), cg_block_sum(rr), part, ticket, tot) && threadIdx.x == 0) {
-        const double old = S[0];
-        S[4] = old != 0.0 ? tot[0] / old : 0.0;
-        S[0] = tot[0];
-        S[2] = tot[1];
-    }
-}
-
-// p = z + beta p
-__global__ void k_cg_dir(double* p, const double* __restrict__ z, int64_t N, const double* __restrict__ S) {
-    const double beta = S[4];
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
-        p[i] = z[i] + beta * p[i];
-}
-
 // *out = |a - b|^2
 __global__ void __launch_bounds__(CG_THREADS) k_diff_norm(const double* __restrict__ a, const double* __restrict__ b,
                                                           int64_t N, double* part, unsigned* ticket, double* out) {
@@ -347,7 +280,7 @@ static int geo_workspace(evap_mesh* h) {
     const size_t bytes = 10 * vec + (2 * CG_BLOCKS + 8) * sizeof(double) + 256;
     EVAP_CUDA(cudaMalloc(&h->geo_ws, bytes));
     EVAP_CUDA(cudaMemset(h->geo_ws, 0, bytes));
-    EVAP_CUDA(cudaMallocHost(&h->geo_host, 8 * sizeof(double)));
+    if (!h->geo_host) EVAP_CUDA(cudaMallocHost(&h->geo_host, 8 * sizeof(double)));
     return EVAP_OK;
 }
 
@@ -376,62 +309,14 @@ static CgSpace cg_space(evap_mesh* h) {
     return w;
 }
 
-// CG on A x = b (x0 = 0) with the Jacobi diagonal d; apply(p, q) computes q = A p.  Stops when
-// |r| <= max(rtol |r0|, atol), checked every CG_CHECK iterations, or after max_iter iterations.
-template <class Apply>
-static int cg_solve(evap_mesh* h, Apply apply, const double* b, const double* d, double* x, double rtol, double atol,
-                    int max_iter, int* iters, double* relres, cudaStream_t s, int64_t N = -1) {
-    if (N < 0) N = h->m.Nphi;  // level-set vectors unless given (the pressure space of the Schur solve)
-    CgSpace w = cg_space(h);
-    double* hs = h->geo_host;
-    k_cg_start<<<CG_BLOCKS, CG_THREADS, 0, s>>>(b, d, x, w.r, w.z, w.p, N, w.part, w.ticket, w.S);
-    EVAP_CHECK_LAUNCH("cg_start");
-    EVAP_CUDA(cudaMemcpyAsync(hs, w.S, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
-    EVAP_CUDA(cudaStreamSynchronize(s));
-    const double r0 = std::sqrt(hs[3]);
-    const double target = std::max(rtol * r0, atol);
-    double res = r0;
-    int it = 0;
-    const int G = blocks_for(N, 256, 152 * 8);
-    while (res > target && it < max_iter) {
-        for (int k = 0; k < CG_CHECK && it < max_iter; ++k, ++it) {
-            int rc = apply(w.p, w.q);
-            if (rc) return rc;
-            k_cg_pq<<<CG_BLOCKS, CG_THREADS, 0, s>>>(w.p, w.q, N, w.part, w.ticket, w.S);
-            EVAP_CHECK_LAUNCH("cg_pq");
-            k_cg_update<<<CG_BLOCKS, CG_THREADS, 0, s>>>(x, w.r, w.p, w.q, d, w.z, N, w.part, w.ticket, w.S);
-            EVAP_CHECK_LAUNCH("cg_update");
-            k_cg_dir<<<G, 256, 0, s>>>(w.p, w.z, N, w.S);
-            EVAP_CHECK_LAUNCH("cg_dir");
-        }
-        EVAP_CUDA(cudaMemcpyAsync(hs, w.S, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
-        EVAP_CUDA(cudaStreamSynchronize(s));
-        res = std::sqrt(hs[2]);
-    }
-    if (iters) *iters += it;
-    const double rel = r0 > 0.0 ? res / r0 : 0.0;
-    if (relres && rel > *relres) *relres = rel;
-    return res <= target ? EVAP_OK : EVAP_ENOTCONV;
-}
-
-// Workspace of the single-launch solvers (fused_krylov.cuh): nvec pair vectors of N entries, the FP32 inverse
-// diagonal, (GM_MAX + 2) CG_BLOCKS partial pairs, the barrier, 4 result words and the Helmholtz coefficient table;
-// grown on demand, kept with the mesh.
-struct FusedSpace {
-    float2* vec;  // vector k at vec + k N
-    float* dinv;
-    float2* part;
-    GridBarrier* gb;
-    double* out;
-    float2* table;
-};
-
+// Workspace of the single-launch solvers (FusedSpace, fused_krylov.cuh), grown on demand.
 static size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-static int fused_space(evap_mesh* h, int nvec, FusedSpace& f) {
+int fused_space(evap_mesh* h, int nvec, FusedSpace& f) {
+    if (!h->geo_host) EVAP_CUDA(cudaMallocHost(&h->geo_host, 8 * sizeof(double)));  // the result words' mirror
     const int64_t N = ls_args<double>(h).Nphi;
     const size_t vbytes = al256((size_t)nvec * N * sizeof(float2)), dbytes = al256((size_t)N * sizeof(float));
-    const size_t pbytes = al256((size_t)(GM_MAX + 2) * CG_BLOCKS * sizeof(float2));
+    const size_t pbytes = al256((size_t)(GM_MAX + 2) * FK_MAX_BLOCKS * sizeof(float2));
     const size_t tail = al256(sizeof(GridBarrier) + 4 * sizeof(double)) + HelmholtzStencil::SMEM * sizeof(float2);
     const size_t need = vbytes + dbytes + pbytes + tail;
     if (h->geo_kry_bytes < need) {
@@ -452,23 +337,8 @@ static int fused_space(evap_mesh* h, int nvec, FusedSpace& f) {
     return EVAP_OK;
 }
 
-// Grid of a single-launch solver: as many blocks as can be co-resident, at most 2 per SM and CG_BLOCKS in all.
-template <class K>
-static int fused_grid(K kernel, size_t smem, int& G) {
-    int dev = 0, sms = 0, per_sm = 0;
-    EVAP_CUDA(cudaGetDevice(&dev));
-    EVAP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    EVAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, FK_THREADS, smem));
-    G = std::min(std::min(per_sm, 2) * sms, CG_BLOCKS);
-    if (G < 1) {
-        set_error("single-launch solver: no block of " + std::to_string(FK_THREADS) + " threads fits on an SM");
-        return EVAP_ECUDA;
-    }
-    return EVAP_OK;
-}
-
 // Reads the solver's result words and the barrier's error word after the launch (one synchronization).
-static int fused_result(evap_mesh* h, const FusedSpace& f, cudaStream_t s, double res[3]) {
+int fused_result(evap_mesh* h, const FusedSpace& f, cudaStream_t s, double res[3]) {
     double* hs = h->geo_host;
     EVAP_CUDA(cudaMemcpyAsync(hs, f.out, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
     EVAP_CUDA(cudaMemcpyAsync(hs + 4, f.gb, sizeof(GridBarrier), cudaMemcpyDeviceToHost, s));
@@ -499,7 +369,7 @@ static int cg_solve_fused(evap_mesh* h, Op op, const double* b, double* x, doubl
     int rc = fused_space(h, 6, f), G = 0;
     if (rc) return rc;
     const size_t smem = Op::SMEM * sizeof(float2);
-    if ((rc = fused_grid(k_cg_fused<Op>, smem, G))) return rc;
+    if ((rc = fused_grid(k_cg_fused<Op>, smem, FK_MAX_BLOCKS, G))) return rc;
     EVAP_CUDA(cudaMemsetAsync(f.gb, 0, sizeof(GridBarrier), s));
     double* xx = x;
     float2 *xd = f.vec, *r = f.vec + N, *u = f.vec + 2 * N, *p = f.vec + 3 * N, *sv = f.vec + 4 * N, *w = f.vec + 5 * N;
@@ -531,7 +401,7 @@ static int gmres_solve_fused(evap_mesh* h, Op op, int m, const double* b, double
     int rc = fused_space(h, m + 3, f), G = 0;
     if (rc) return rc;
     const size_t smem = Op::SMEM * sizeof(float2);
-    if ((rc = fused_grid(k_gmres_fused<Op>, smem, G))) return rc;
+    if ((rc = fused_grid(k_gmres_fused<Op>, smem, FK_MAX_BLOCKS, G))) return rc;
     EVAP_CUDA(cudaMemsetAsync(f.gb, 0, sizeof(GridBarrier), s));
     double* xx = x;
     float2 *xd = f.vec, *z = f.vec + N, *V = f.vec + 2 * N;
@@ -880,51 +750,6 @@ int geo_advect_levelset(evap_mesh* h, double* phi, int max_iters, double tol, in
     if (lin_iters) *lin_iters = lin;
     if (last_change) *last_change = change;
     return status;
-}
-
-// ------------------------------------------------------ pressure Schur complement of the velocity-pressure system
-// Jacobi diagonal for the CG on S~ = B diag(A)^(-1) B^T (the Schur approximation of the velocity-pressure solve):
-// with the velocity block dominated by rho c_m M, S~ ~ K_(1/rho) / c_m, so d_i = (K_(1/rho))_ii / c_m, K_(1/rho) the Q1
-// stiffness weighted by 1/rho(phi) at the 2-point Gauss points.
-__global__ void __launch_bounds__(128) k_schur_diag(MeshArgs<double> m, Basis<double> bas, const double* __restrict__ phi,
-                                                    double* __restrict__ d) {
-    const int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (cell >= m.ncell) return;
-    Q1Cell c;
-    int cx, cy, cz;
-    q1_cell_nodes(cell, m.n, c, cx, cy, cz);
-    double out[8] = {};
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        double N[8], G[8][3];
-        q1_weights(bas.g2t, q, m.inv_h, N, G);
-        const double W = bas.g2w[q & 1] * bas.g2w[(q >> 1) & 1] * bas.g2w[q >> 2] * m.vol_w;
-        double ph, gp[3];  // the level set at the point (its own, possibly subdivided, mesh)
-        ls_at(phi, m, cx, cy, cz, bas.g2t[q & 1], bas.g2t[(q >> 1) & 1], bas.g2t[q >> 2], ph, gp);
-        const double wr = W / (material(ph, gp[0], gp[1], gp[2], m).rho * m.c_mass);
-#pragma unroll
-        for (int j = 0; j < 8; ++j) out[j] += wr * (G[j][0] * G[j][0] + G[j][1] * G[j][1] + G[j][2] * G[j][2]);
-    }
-#pragma unroll
-    for (int j = 0; j < 8; ++j) atomicAdd(&d[c.node[j]], out[j]);
-}
-
-int geo_schur_setup(evap_mesh* h, double** diag, cudaStream_t s) {
-    int rc = geo_workspace(h);
-    if (rc) return rc;
-    CgSpace w = cg_space(h);
-    EVAP_CUDA(cudaMemsetAsync(w.d, 0, h->m.Np * sizeof(double), s));  // pressure space
-    k_schur_diag<<<blocks_for(h->m.ncell, 128, 1LL << 40), 128, 0, s>>>(h->m, h->b, h->phi, w.d);
-    EVAP_CHECK_LAUNCH("schur_diag");
-    *diag = w.d;
-    return EVAP_OK;
-}
-
-int geo_cg(evap_mesh* h, const std::function<int(const double*, double*)>& apply, const double* b, const double* d,
-           double* x, double rtol, double atol, int max_iter, int* iters, cudaStream_t s) {
-    int rc = geo_workspace(h);
-    if (rc) return rc;
-    return cg_solve(h, apply, b, d, x, rtol, atol, max_iter, iters, nullptr, s, h->m.Np);
 }
 
 }  // namespace evap

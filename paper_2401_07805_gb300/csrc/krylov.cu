@@ -110,6 +110,7 @@ int launch_diagonal(evap_mesh* h, cudaStream_t s) {
     k_diag_finish<<<blocks_for(N, 256), 256, 0, s>>>(m.M, m.Nu, m.faces, h->diag32, h->diag);
     EVAP_CHECK_LAUNCH("diag_finish");
     h->diag_valid = true;
+    ++h->diag_stamp;
     return EVAP_OK;
 }
 
@@ -700,13 +701,16 @@ int solve_gmres(evap_mesh* h, const double* f, double* x, int mixed, int m, doub
 // B diag(A)^(-1) B^T (schur_apply).  Both are inexact and vary between applications, so the outer method stores the
 // preconditioned directions (flexible GMRES); the outer vectors are FP64 [x (3 N_u) | p (N_phi)].
 // Budgets of the two inexact inner solves.  Measured on the 64^3 four-sphere case with the top face open (GB300; ms
-// and outer applications: solve to 1e-4 / solve to 1e-8 / three consecutive time steps to 1e-8):
-//   velocity 10, Schur CG 24: 43.7 (6) / 405 (42) / 70.0, 70.0, 80.4
-//   velocity 14, Schur CG 24: 43.7 (6) / 405 (42) / 70.2, 69.9, 80.3
-//   velocity 14, Schur CG 12: 30.1 (6) / 407 (60) / 62.9, 63.0, 63.6
-//   velocity 14, Schur CG 32 to 1e-2: 46.0 (6) / 260 (23) / 91.4, 91.4, 79.3
-// The 12-iteration Schur budget does not converge the stationary 1D phase change of App. A (density ratio 1e3,
-// 4002 applications short of 1e-10), so the budget stays at 24; the Schur CG rarely stops before its cap.
+// and outer applications: solve to 1e-4 / solve to 1e-8 / three consecutive time steps to 1e-8).  With the Schur CG
+// on the assembled stencil (schur.cu):
+//   velocity 14, Schur CG 24 to 1e-6:   19.7 (6) / 111 (26) / 48.3, 48.4, 48.7
+//   velocity 14, Schur CG 60 to 1e-4:   25.3 (6) /  61 (12) / 54.2, 53.9, 54.0
+//   velocity 14, Schur CG 120 to 1e-4:  33.9 (6) /  81 (12) / 63.2, 63.4, 63.4
+//   velocity 10, Schur CG 60 to 1e-3:   23.9 (6) /  59 (12) / 54.2, 54.0, 54.4
+// and before it, with a matrix-free gradient and divergence per Schur CG iteration and an approximate diagonal:
+//   velocity 10, Schur CG 24: 43.7 (6) / 405 (42) / 70.0, 70.0, 80.4;  velocity 14, Schur CG 12: 30.1 (6) /
+//   407 (60) / 62.9, 63.0, 63.6, but 12 iterations did not converge the stationary 1D phase change of App. A
+//   (density ratio 1e3, 4002 applications short of 1e-10).
 #ifndef EVAP_SADDLE_INNER_M
 #define EVAP_SADDLE_INNER_M 14
 #endif
@@ -757,7 +761,6 @@ __global__ void k_add_float(const double* __restrict__ v, const float* __restric
 }
 
 struct SaddleSpace {
-    const double* sdiag;    // Jacobi diagonal of the pressure Schur approximation
     double *V, *Z, *b, *t;  // outer basis [(m+1) ld], directions [m ld], right-hand side [ld], velocity scratch [3 N_u]
     float *V32, *w32, *z32, *r32, *d32;  // inner FP32 workspace
 };
@@ -768,8 +771,7 @@ static int saddle_precond(Ctx& inner, SaddleSpace& sp, const double* v, double* 
     cudaStream_t s = inner.s;
     const int64_t Nu3 = 3 * h->m.Nu, Np = h->m.Np;
     const int G = blocks_for(Nu3, 256);
-    // the inner solve's FP32 scratch is free here: w32 [3 N_u] and z32 (>= 2 N_phi) for the Schur operator
-    int rc = schur_apply(h, v + Nu3, z + Nu3, sp.sdiag, sp.w32, sp.z32, SADDLE_SCHUR_CG, s);
+    int rc = schur_apply(h, v + Nu3, z + Nu3, SADDLE_SCHUR_CG, s);
     if (rc) return rc;
     // t = v_u + B^T z_p, the gradient in FP32 (it enters the FP32 velocity solve)
     if ((rc = launch_to_float(z + Nu3, sp.z32, Np, s))) return rc;
@@ -801,8 +803,7 @@ int solve_saddle(evap_mesh* h, const double* f, double* x, double* p, int m, dou
     const double* g = nullptr;
     if ((rc = continuity_rhs(h, &g, s))) return rc;
     if (g_rhs) g = g_rhs;
-    double* sdiag = nullptr;
-    if ((rc = geo_schur_setup(h, &sdiag, s))) return rc;
+    if ((rc = schur_assemble(h, s))) return rc;
     const int64_t Nu3 = 3 * h->m.Nu, Np = h->m.Np, N = Nu3 + Np;
     const int64_t ld = (N + 63) / 64 * 64, ldu = (Nu3 + 63) / 64 * 64;
     // inner (FP32 velocity GMRES) workspace and reduction scratch: the mesh's Krylov buffers
@@ -812,7 +813,6 @@ int solve_saddle(evap_mesh* h, const double* f, double* x, double* p, int m, dou
     if ((rc = tensor_prec_setup(h, false, s))) return rc;
     inner.tp = true;
     SaddleSpace sp;
-    sp.sdiag = sdiag;
     char* ib = (char*)h->ws;
     sp.V32 = (float*)ib;
     sp.w32 = (float*)(ib + fV);

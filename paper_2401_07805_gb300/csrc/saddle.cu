@@ -356,31 +356,14 @@ int launch_divergence(evap_mesh* h, const T* x, const T* diag, T* yp, cudaStream
 template int launch_divergence<float>(evap_mesh*, const float*, const float*, float*, cudaStream_t);
 
 // z = S~^(-1) r, S~ = B diag(A)^(-1) B^T (a SIMPLE-type approximation of the Schur complement B A^(-1) B^T: it keeps
-// the discrete B, so the pressure nodes of open faces are treated like every other node), by CG with the Jacobi
-// diagonal d of geo_schur_setup, at most cg_iters iterations (an inexact solve: the outer method is flexible).  The
-// CG runs in FP64; its operator is applied in FP32 (gradient, scaling by the FP32 Jacobi diagonal of A, divergence):
-// B and B^T are FP64-pipe bound at ~45 FMA per velocity point, and a preconditioner needs no FP64 operator.
-// Scratch: t32 [3 N_u] and pq32 [2 N_p] floats.
+// the discrete B, so the pressure nodes of open faces are treated like every other node): at most cg_iters iterations
+// of the FP32 single-launch CG on the assembled stencil (schur.cu), or |r| <= EVAP_SADDLE_SCHUR_RTOL |r0| (an inexact
+// solve: the outer method is flexible).
 #ifndef EVAP_SADDLE_SCHUR_RTOL
 #define EVAP_SADDLE_SCHUR_RTOL 1e-6
 #endif
-int schur_apply(evap_mesh* h, const double* r, double* z, const double* d, float* t32, float* pq32, int cg_iters,
-                cudaStream_t st) {
-    const int64_t Nu3 = 3 * h->m.Nu, Np = h->m.Np;
-    float* p32 = pq32;
-    float* q32 = pq32 + Np;
-    const float* diag32 = h->diag32;
-    auto apply = [&](const double* p, double* q) {
-        int e = launch_to_float(p, p32, Np, st);
-        if (e) return e;
-        EVAP_CUDA(cudaMemsetAsync(t32, 0, Nu3 * sizeof(float), st));
-        if ((e = launch_pressure_gradient<float>(h, p32, 1.0f, t32, st))) return e;
-        EVAP_CUDA(cudaMemsetAsync(q32, 0, Np * sizeof(float), st));
-        if ((e = launch_divergence<float>(h, t32, diag32, q32, st))) return e;  // B diag^(-1) t
-        return launch_to_double(q32, q, Np, st);
-    };
-    const int rc = geo_cg(h, apply, r, d, z, EVAP_SADDLE_SCHUR_RTOL, 0.0, cg_iters, nullptr, st);
-    return rc == EVAP_ENOTCONV ? EVAP_OK : rc;
+int schur_apply(evap_mesh* h, const double* r, double* z, int cg_iters, cudaStream_t st) {
+    return schur_solve(h, r, z, EVAP_SADDLE_SCHUR_RTOL, cg_iters, nullptr, st);
 }
 
 // g (the continuity right-hand side of the current fields), computed once per set_fields into h->cont_rhs.
