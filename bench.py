@@ -457,6 +457,32 @@ def saddle_case(evap, torch, dev):
     return res
 
 
+def subdivided_case(evap, torch, dev):
+    """The four-sphere workload with the level set on the twice-subdivided mesh (n_sub = 2: 64^3 velocity cells, Q2,
+    6.44 M velocity DoFs; 129^3 = 2.15 M level-set DoFs): set_fields (with the closest-point transport velocity on
+    the fine lattice), the FP64-accurate momentum apply with its divergence row, the level-set advection apply, the
+    adjoint (20 back-to-back calls after 3 each), and one projected normal and curvature."""
+    wl = workloads.make_workload(WORKLOAD, n_sub=2)
+    op = evap.Operator(wl.n, wl.p, wl.L, dict(wl.params))
+    cu = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    phi, u0, md, x = cu(wl.phi), cu(wl.u0), cu(wl.mdot), cu(wl.x)
+    rng = np.random.default_rng(7)
+    w, wp = cu(rng.uniform(-1, 1, wl.x.shape)), cu(rng.uniform(-1, 1, op.n_p))
+    ts = back_to_back(torch, lambda: op.set_fields(phi, u0, md), 3, 1)
+    y, yp = torch.empty_like(x), torch.empty(op.n_p, dtype=torch.float64, device=dev)
+    t64 = back_to_back(torch, lambda: op.apply_momentum(x, prec=64, with_divergence=True, out=y, out_p=yp), 20, 3)
+    t_ls = back_to_back(torch, lambda: op.apply_levelset(phi, mode="advect"), 20, 3)
+    t_adj = back_to_back(torch, lambda: op.apply_adjoint(w, x, wp), 20, 3)
+    t_n = back_to_back(torch, op.projected_normal, 2, 1)
+    nu3 = 3 * op.n_u
+    out = dict(workload="spheres64 with n_sub = 2: 6.44 M velocity DoFs, 2.15 M level-set DoFs, 275 k pressure DoFs",
+               set_fields_ms=ts, momentum_fp64=dict(ms=t64, gdofs=nu3 / t64 / 1e6),
+               levelset_advect=dict(ms=t_ls, gdofs=op.n_phi / t_ls / 1e6),
+               adjoint=dict(ms=t_adj, gdofs=nu3 / t_adj / 1e6), projected_normal_ms=t_n)
+    op.close()
+    return out
+
+
 def large_case(evap, torch, dev, p: int):
     """deformed128: 128^3 cells, degree-p velocity (p = 2: 51 M DoFs, p = 3: 171 M DoFs), deformed sphere with
     spherical-harmonic noise up to l = 6 (seed 5), density ratio 1e4.  FP64 and FP32 applies, the adjoint apply, and
@@ -751,6 +777,7 @@ def main():
         applies = operator_applies(evap, torch, dev, op, d, counts, hbm)
         applies["geometry"] = geometry_subsolver(torch, op, d["phi"])
         applies["saddle"] = saddle_case(evap, torch, dev)
+        applies["n_sub_2"] = subdivided_case(evap, torch, dev)
     solves = None
     if rank == 0 and not args.no_solve_compare:
         solves = solve_comparison(evap, torch, dev)
