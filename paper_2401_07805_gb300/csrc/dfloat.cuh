@@ -95,6 +95,7 @@ struct DfBasis {
     dfl S[MAXQ][MAXQ];   // S[q][a] = l_a(t_q)
     dfl Dc[MAXQ][MAXQ];  // physical collocation derivative Dc[q][r] / h
     dfl N1[MAXQ][2];     // Q1 shape values at the Gauss points
+    double t[MAXQ];      // the Gauss points on [0, 1] in FP64 (linear interpolation of nodal FP64 data)
 };
 DfBasis make_df_basis(const Basis<double>& b, double inv_h);
 

@@ -53,6 +53,9 @@ constexpr size_t df_coeff_smem() {
 #ifndef EVAP_DF_MINB2
 #define EVAP_DF_MINB2 8
 #endif
+#ifndef EVAP_DF_MINB2_PRES
+#define EVAP_DF_MINB2_PRES 8
+#endif
 
 template <int P, int CB, bool PRES, int MINB = 1>
 __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1), MINB)
@@ -181,16 +184,20 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1), MINB)
             r.lo = __fadd_rn(r.lo, __fsub_rn(s2.lo, src.lo));
             rdiv = df_norm(r);
         }
-        if constexpr (PRES) {
+        if constexpr (PRES) {  // p at the point: trilinear interpolation by successive linear ones, in FP64
             const int64_t m1 = n + 1;
-            dfl pq{0.f, 0.f};
+            const double* p0 = pin + cx + m1 * (cy + m1 * cz);
+            const double tx = bas.t[a], ty = bas.t[b], tz = bas.t[c];
+            double e[2][2];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int ja = j & 1, jb = (j >> 1) & 1, jc = j >> 2;
-                const dfl nw = df_mul(df_mul(sN1[a][ja], sN1[b][jb]), sN1[c][jc]);
-                df_fma(pq, nw, df_from_double(pin[(cx + ja) + m1 * ((cy + jb) + m1 * (cz + jc))]));
-            }
-            const dfl wp = df_mul(ld_df(q + 17 * NQ), df_norm(pq));
+            for (int jc = 0; jc < 2; ++jc)
+#pragma unroll
+                for (int jb = 0; jb < 2; ++jb) {
+                    const double* r = p0 + m1 * (jb + m1 * jc);
+                    e[jc][jb] = fma(tx, r[1] - r[0], r[0]);
+                }
+            const double f0 = fma(ty, e[0][1] - e[0][0], e[0][0]), f1 = fma(ty, e[1][1] - e[1][0], e[1][0]);
+            const dfl wp = df_mul(ld_df(q + 17 * NQ), df_from_double(fma(tz, f1 - f0, f0)));
 #pragma unroll
             for (int k = 0; k < 3; ++k) Tf[k][k] = df_sub(Tf[k][k], wp);
         }
@@ -290,6 +297,7 @@ DfBasis make_df_basis(const Basis<double>& b, double inv_h) {
         }
         d.N1[q][0] = df_from_double(b.N1[q][0]);
         d.N1[q][1] = df_from_double(b.N1[q][1]);
+        d.t[q] = b.t[q];
     }
     return d;
 }
@@ -314,9 +322,9 @@ int launch_momentum_df(evap_mesh* h, const MeshArgs<double>& m, const double* x,
     };
     int rc;
     if (m.P == 2) {
-        constexpr int CB = EVAP_DF_CB2, MINB = EVAP_DF_MINB2;
+        constexpr int CB = EVAP_DF_CB2, MINB = EVAP_DF_MINB2, MINBP = EVAP_DF_MINB2_PRES;
         constexpr size_t dyn = df_coeff_smem<2, CB>();
-        rc = p ? run(k_momentum_df<2, CB, true, MINB>, CB, CB * 27, dyn)
+        rc = p ? run(k_momentum_df<2, CB, true, MINBP>, CB, CB * 27, dyn)
                : run(k_momentum_df<2, CB, false, MINB>, CB, CB * 27, dyn);
     } else {
         constexpr int CB = 4;
