@@ -325,12 +325,17 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1), MINB)
     }
 }
 
+// blocks per SM for Q2 (a register cap): measured at 64^3 (100 applies, ms) 3 blocks (72 registers) 0.174, 2 (90)
+// 0.180, 4 (56, spills) 0.230
+#ifndef EVAP_M32_MINB2
+#define EVAP_M32_MINB2 3
+#endif
 template <int P>
 static int launch32(const evap_mesh* h, const MeshArgs<float>& m, const Scale32& hs, const float* x, float* y,
                     float* yp, cudaStream_t s) {
     constexpr int L = (P + 1) * (P + 1);
     constexpr int CB = 32;                // one warp per line: 288 / 512 threads
-    constexpr int MINB = P == 2 ? 3 : 1;  // 35 KB / 80 KB of shared memory per block
+    constexpr int MINB = P == 2 ? EVAP_M32_MINB2 : 1;  // 35 KB / 80 KB of shared memory per block
     if (!h->deterministic) {
         const unsigned grid = (unsigned)(((m.n + CB - 1) / CB) * (int64_t)m.n * m.n);
         k_momentum32<P, CB, MINB><<<grid, CB * L, 0, s>>>(m, hs, h->cell_code, h->table_index, h->table32, h->qc32, x,

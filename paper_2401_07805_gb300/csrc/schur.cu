@@ -80,7 +80,9 @@ __global__ void __launch_bounds__(128) k_schur_assemble(int n, int P, int M, uns
     S[idx] = acc;
 }
 
-// Row `node` of S~ x and its diagonal, from the stored half stencil (FP32).
+// Row `node` of S~ x and its diagonal, from the stored half stencil (FP32).  Nodes at least two layers inside the
+// lattice take an unrolled path with compile-time offsets and no bounds tests (83 % of the nodes at 64^3); the others
+// test each neighbour.  Entries are indexed with 32 bits (63 N_p < 2^32, checked on the host).
 struct SchurStencil {
     static constexpr int SMEM = 0;
     int n;
@@ -89,9 +91,23 @@ struct SchurStencil {
     __device__ __forceinline__ void load(float*) const {}
     template <class X>
     __device__ __forceinline__ float row(int64_t node, const X* x, const float*) const {
-        const unsigned m1 = (unsigned)n + 1u, nd = (unsigned)node;
+        const unsigned m1 = (unsigned)n + 1u, m2 = m1 * m1, nd = (unsigned)node, np = (unsigned)Np;
         const unsigned t = nd / m1, i = nd - t * m1, k = t / m1, j = t - k * m1;
         float acc = 0.f;
+        if (i >= 2u && j >= 2u && k >= 2u && i + 2u <= (unsigned)n && j + 2u <= (unsigned)n && k + 2u <= (unsigned)n) {
+#pragma unroll
+            for (int dz = -2; dz <= 2; ++dz)
+#pragma unroll
+                for (int dy = -2; dy <= 2; ++dy)
+#pragma unroll
+                    for (int dx = -2; dx <= 2; ++dx) {
+                        const int lin = 25 * (dz + 2) + 5 * (dy + 2) + (dx + 2);
+                        const unsigned nb = nd + (unsigned)dx + (unsigned)dy * m1 + (unsigned)dz * m2;
+                        const float c = lin >= 62 ? S[(unsigned)(lin - 62) * np + nd] : S[(unsigned)(62 - lin) * np + nb];
+                        acc = fmaf(c, (float)x[nb], acc);
+                    }
+            return acc;
+        }
 #pragma unroll
         for (int dz = -2; dz <= 2; ++dz) {
             if ((int)k + dz < 0 || (int)k + dz > n) continue;
@@ -102,10 +118,9 @@ struct SchurStencil {
                 for (int dx = -2; dx <= 2; ++dx) {
                     if ((int)i + dx < 0 || (int)i + dx > n) continue;
                     const int lin = 25 * (dz + 2) + 5 * (dy + 2) + (dx + 2);
-                    const unsigned nb = nd + (unsigned)(dx + (int)m1 * (dy + (int)m1 * dz));
-                    const unsigned owner = lin >= 62 ? nd : nb;
-                    const int ent = lin >= 62 ? lin - 62 : 62 - lin;
-                    acc = fmaf(S[(int64_t)ent * Np + owner], (float)x[nb], acc);
+                    const unsigned nb = nd + (unsigned)dx + (unsigned)dy * m1 + (unsigned)dz * m2;
+                    const float c = lin >= 62 ? S[(unsigned)(lin - 62) * np + nd] : S[(unsigned)(62 - lin) * np + nb];
+                    acc = fmaf(c, (float)x[nb], acc);
                 }
             }
         }
@@ -126,8 +141,8 @@ int schur_assemble(evap_mesh* h, cudaStream_t s) {
     if (rc) return rc;
     if (h->schur_S && h->schur_stamp == h->diag_stamp) return EVAP_OK;
     const MeshArgs<double>& m = h->m;
-    if (m.Np >= (int64_t)1 << 32) {
-        set_error("Schur stencil: pressure node indices must fit 32 bits");
+    if (63 * m.Np >= (int64_t)1 << 32) {
+        set_error("Schur stencil: its 63 N_p entries must be indexable with 32 bits");
         return EVAP_EINVAL;
     }
     if (!h->schur_S) EVAP_CUDA(cudaMalloc(&h->schur_S, 63 * m.Np * sizeof(float)));
