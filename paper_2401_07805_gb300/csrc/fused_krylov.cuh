@@ -327,7 +327,9 @@ __global__ void __launch_bounds__(FK_THREADS) k_cg_fused(Op op, int64_t N, const
 
 // ------------------------------------------------------------------------------------------------- GMRES
 // GMRES(m) for A x = b with the right Jacobi preconditioner D^-1 (D = op.diag in FP32; A D^-1 y = b, x = D^-1 y),
-// started from x, with classical Gram-Schmidt and a second pass where the first one cancelled more than `reorth` of the vector
+// started from x, with classical Gram-Schmidt: the norm of the orthogonalized vector by the Pythagorean form |w|^2 -
+// sum h_k^2 (its subtraction then shares the pass that normalizes it: two grid barriers per Arnoldi step), unless
+// that cancels more than `reorth` of |w|^2, when the subtraction and its norm are explicit and a second pass follows
 // (|w_after|^2 < reorth |w_before|^2).  The Hessenberg matrix, its Givens rotations and the least-squares solve are
 // kept by thread 0 of every block (the same FP64 arithmetic on the same sums, so the same values everywhere).  It
 // stops when the true residual |b - A x| (formed at the start of each cycle) is <= max(rtol |b|, atol), or once
@@ -347,7 +349,7 @@ __global__ void __launch_bounds__(FK_THREADS) k_gmres_fused(Op op, int64_t N, in
     __shared__ double H[(GM_MAX + 1) * GM_MAX], cs[GM_MAX], sn[GM_MAX], g[GM_MAX + 1];
     __shared__ dfl s_y[GM_MAX], s_scale;
     __shared__ double s_res, s_bn;
-    __shared__ int s_go, s_more, s_norm, s_pass2;
+    __shared__ int s_go, s_more, s_norm, s_pass2, s_fast;
     unsigned long long bar = 0;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t i0 = blockIdx.x * (int64_t)FK_THREADS + threadIdx.x, stride = (int64_t)gridDim.x * FK_THREADS;
@@ -454,7 +456,21 @@ __global__ void __launch_bounds__(FK_THREADS) k_gmres_fused(Op op, int64_t N, in
             grid_sums(j + 2);
             double hk[GM_MAX + 1];  // thread 0: the column before the rotations
             const double before = df_to_double(s_h[j + 1]);
-            for (int pass = 0; pass < 2; ++pass) {
+            // |w - sum_k h_k v_k|^2 = |w|^2 - sum_k h_k^2 for orthonormal v_k (the Pythagorean form of classical
+            // Gram-Schmidt): taken unless it cancels more than `reorth` of |w|^2, when the subtraction is done
+            // explicitly, its norm summed, and a second pass follows as before
+            if (threadIdx.x == 0) {
+                dfl a = s_h[j + 1];
+                for (int k = 0; k <= j; ++k) df_fma(a, df_neg(s_h[k]), s_h[k]);
+                const double after = df_to_double(df_norm(a));
+                s_fast = after > 0.0 && after >= reorth * before;
+                if (s_fast) {
+                    for (int k = 0; k <= j; ++k) hk[k] = df_to_double(s_h[k]);
+                    hk[j + 1] = sqrt(after);
+                }
+            }
+            __syncthreads();
+            for (int pass = 0; pass < 2 && !s_fast; ++pass) {
                 // w -= sum_k h_k v_k, |w|^2
                 dfl aft = zero;
                 for (int64_t i = i0; i < N; i += stride) {
@@ -506,7 +522,12 @@ __global__ void __launch_bounds__(FK_THREADS) k_gmres_fused(Op op, int64_t N, in
             __syncthreads();
             if (s_norm && s_more) {  // v_{j+1} = w / |w|, z = D^-1 v_{j+1}: the next operator reads z
                 for (int64_t i = i0; i < N; i += stride) {
-                    const dfl vi = df_mul(ld_df(W + i), s_scale);
+                    dfl wi = ld_df(W + i);
+                    if (s_fast) {  // the subtraction of the Pythagorean path, in the same pass
+                        for (int k = 0; k <= j; ++k) df_fma(wi, df_neg(s_h[k]), ld_df(V + (int64_t)k * N + i));
+                        wi = df_norm(wi);
+                    }
+                    const dfl vi = df_mul(wi, s_scale);
                     st_df(W + i, vi);
                     const float di = dinv[i];
                     st_df(z + i, df_norm(dfl{vi.hi * di, __fmaf_rn(vi.hi, di, -vi.hi * di) + vi.lo * di}));
