@@ -47,8 +47,8 @@ def load_peaks():
 # DRAM bytes (read + write) per launch of a kernel from an ncu capture of this bench, valid only while the kernel's
 # sources are unchanged: {(kernel, workload): (bytes, sha256 prefix of the sources)}.
 MEASURED_TRAFFIC = {
-    ("k_momentum32", "spheres64"): (430_606_208, "552843c65fb7e106"),
-    ("k_momentum_df", "spheres64"): (1_227_177_088, "d7022d08b5124638"),
+    ("k_momentum32", "spheres64"): (430_613_760, "4089d1f6ff8956b1"),
+    ("k_momentum_df", "spheres64"): (1_226_857_344, "62ce77f8aa7a978e"),
 }
 TRAFFIC_SOURCES = {"k_momentum32": ("paper_2401_07805_gb300/csrc/momentum32.cu",
                                     "paper_2401_07805_gb300/csrc/basis_ct.cuh",
@@ -751,7 +751,7 @@ def main():
     # algorithmic bytes and against the bytes streamed with the quadrature-point cache) are beside it.
     df_peak = fp32_peak / DF_FMA_INSTR
     roofline = dict(bound="alu",
-                    kernel="k_momentum_df<2,4,0,8> (FP64-accurate momentum apply with divergence row in double-float "
+                    kernel="k_momentum_df<2,4,0,8,false> (FP64-accurate momentum apply with divergence row in double-float "
                            "arithmetic, 100 per step)",
                     achieved=mom64["tflops"], peak=df_peak, unit="TFLOP/s", frac=mom64["tflops"] / df_peak,
                     traffic=measured_traffic("k_momentum_df", WORKLOAD), flop_per_launch=counts["mom_flop"],
@@ -763,7 +763,7 @@ def main():
                              frac=mom64["hbm_frac"], bytes_per_launch=counts["mom64_alg_bytes"],
                              frac_streamed=mom64["hbm_frac_streamed"], streamed_bytes=counts["mom64_bytes"],
                              peak_source=f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"),
-                    fp32_kernel=dict(kernel="k_momentum32<2,32,3> (FP32 momentum apply)", bound="hbm",
+                    fp32_kernel=dict(kernel="k_momentum32<2,32,3,false> (FP32 momentum apply)", bound="hbm",
                                      achieved=mom32["alg_bytes"] / (mom32["ms"] * 1e6), peak=hbm, unit="GB/s",
                                      frac=mom32["hbm_frac"], frac_streamed=mom32["hbm_frac_streamed"],
                                      traffic=measured_traffic("k_momentum32", WORKLOAD),

@@ -6,17 +6,25 @@
 // when a nodal normal field is set (e.g. the projected normal of Eq. normal_vector_regularized), its normalized
 // interpolant (ls_frozen_normal).  The FP64 advection runs in double-float arithmetic (k_levelset_advect_df: the FP64
 // pipe bounds the FP64 version); the reinitialization operators stay in FP64.
+#include <type_traits>
+
 #include "dfloat.cuh"
 #include "physics.cuh"
 
 namespace evap {
 
-template <typename T, int MODE>
+template <typename T, int MODE, bool DET>
 __global__ void __launch_bounds__(128) k_levelset(MeshArgs<T> m, Basis<T> bas, const T* __restrict__ phi,
                                                   const T* __restrict__ nf, const T* __restrict__ ug,
                                                   const T* __restrict__ x, T* __restrict__ y, int colour) {
     int cx, cy, cz;
-    if (!colour_cell(blockIdx.x * (int64_t)blockDim.x + threadIdx.x, m.n, colour, cx, cy, cz)) return;
+    if constexpr (DET) {
+        if (!colour_cell(blockIdx.x * (int64_t)blockDim.x + threadIdx.x, m.n, colour, cx, cy, cz)) return;
+    } else {  // written out: the shared helper's form of this test cost the atomic variant 100 registers
+        const int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+        if (cell >= m.ncell) return;
+        cx = (int)(cell % m.n), cy = (int)((cell / m.n) % m.n), cz = (int)(cell / ((int64_t)m.n * m.n));
+    }
     const int n = m.n;
     const int64_t m1 = n + 1;
     int64_t node[8];
@@ -85,17 +93,24 @@ __global__ void __launch_bounds__(128) k_levelset(MeshArgs<T> m, Basis<T> bas, c
         for (int j = 0; j < 8; ++j) out[j] += N[j] * Fv + dR[j][0] * Gf[0] + dR[j][1] * Gf[1] + dR[j][2] * Gf[2];
     }
 #pragma unroll
-    for (int j = 0; j < 8; ++j) acc_add(&y[node[j]], out[j], colour >= 0);
+    for (int j = 0; j < 8; ++j) acc_add(&y[node[j]], out[j], DET);
 }
 
 // EVAP_ADVECT for the FP64 applies in double-float arithmetic (dfloat.cuh): the same sums with x converted per node,
 // u_Gamma read from its double-float copy, every product and sum on hi + lo FP32 pairs, the scatter in FP64.  The
 // shape values at the Gauss points are compile-time doubles split into pairs.
+template <bool DET>
 __global__ void __launch_bounds__(128) k_levelset_advect_df(MeshArgs<double> m, dfl W, dfl thdt_ih,
                                                             const float2* __restrict__ ug, const double* __restrict__ x,
                                                             double* __restrict__ y, int colour) {
     int cx, cy, cz;
-    if (!colour_cell(blockIdx.x * (int64_t)blockDim.x + threadIdx.x, m.n, colour, cx, cy, cz)) return;
+    if constexpr (DET) {
+        if (!colour_cell(blockIdx.x * (int64_t)blockDim.x + threadIdx.x, m.n, colour, cx, cy, cz)) return;
+    } else {  // written out: the shared helper's form of this test cost the atomic variant 100 registers
+        const int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+        if (cell >= m.ncell) return;
+        cx = (int)(cell % m.n), cy = (int)((cell / m.n) % m.n), cz = (int)(cell / ((int64_t)m.n * m.n));
+    }
     const int n = m.n;
     const int64_t m1 = n + 1;
     int64_t node[8];
@@ -150,7 +165,7 @@ __global__ void __launch_bounds__(128) k_levelset_advect_df(MeshArgs<double> m, 
         for (int j = 0; j < 8; ++j) df_fma(out[j], N[j], Fv);
     }
 #pragma unroll
-    for (int j = 0; j < 8; ++j) acc_add(&y[node[j]], df_to_double(df_norm(out[j])), colour >= 0);
+    for (int j = 0; j < 8; ++j) acc_add(&y[node[j]], df_to_double(df_norm(out[j])), DET);
 }
 
 template <typename T>
@@ -164,32 +179,36 @@ int launch_levelset(evap_mesh* h, int mode, const T* x, T* y, cudaStream_t s) {
     int rc = launch_fill<T>(y, m.Nphi, T(0), s);
     if (rc) return rc;
     const int threads = 128;
-    const int c0 = h->deterministic ? 0 : -1, c1 = h->deterministic ? 8 : 0;  // colour passes, or one atomic pass
-    for (int colour = c0; colour < (c1 > c0 + 1 ? c1 : c0 + 1); ++colour) {
-        const int64_t cells = colour_cells(m.n, colour);
-        if (cells == 0) continue;
-        const unsigned grid = (unsigned)((cells + threads - 1) / threads);
-        bool done = false;
-        if constexpr (sizeof(T) == 8) {
-            if (mode == EVAP_ADVECT) {  // FP64-accurate advection in double-float arithmetic
-                const dfl W = df_from_double(0.125 * (double)m.vol_w);  // 2-point Gauss weights 1/2 per direction
-                const dfl thdt_ih = df_from_double((double)m.theta * (double)m.dt * (double)m.inv_h);
-                k_levelset_advect_df<<<grid, threads, 0, s>>>(m, W, thdt_ih, (const float2*)h->ugammadf,
-                                                              (const double*)x, (double*)y, colour);
-                done = true;
+    // colour passes (deterministic) or one atomic pass, each variant compiled apart
+    auto go = [&](auto det) -> int {
+        constexpr bool DET = decltype(det)::value;
+        for (int colour = DET ? 0 : -1; colour < (DET ? 8 : 0); ++colour) {
+            const int64_t cells = colour_cells(m.n, colour);
+            if (cells == 0) continue;
+            const unsigned grid = (unsigned)((cells + threads - 1) / threads);
+            bool done = false;
+            if constexpr (sizeof(T) == 8) {
+                if (mode == EVAP_ADVECT) {  // FP64-accurate advection in double-float arithmetic
+                    const dfl W = df_from_double(0.125 * (double)m.vol_w);  // 2-point Gauss weights 1/2 per direction
+                    const dfl thdt_ih = df_from_double((double)m.theta * (double)m.dt * (double)m.inv_h);
+                    k_levelset_advect_df<DET><<<grid, threads, 0, s>>>(m, W, thdt_ih, (const float2*)h->ugammadf,
+                                                                       (const double*)x, (double*)y, colour);
+                    done = true;
+                }
             }
+            if (done) {
+            } else if (mode == EVAP_ADVECT) {
+                k_levelset<T, EVAP_ADVECT, DET><<<grid, threads, 0, s>>>(m, b, phi, nullptr, ug, x, y, colour);
+            } else if (mode == EVAP_REINIT) {
+                k_levelset<T, EVAP_REINIT, DET><<<grid, threads, 0, s>>>(m, b, phi, nf, ug, x, y, colour);
+            } else {
+                k_levelset<T, EVAP_REINIT_RHS, DET><<<grid, threads, 0, s>>>(m, b, phi, nf, ug, x, y, colour);
+            }
+            EVAP_CHECK_LAUNCH("levelset");
         }
-        if (done) {
-        } else if (mode == EVAP_ADVECT) {
-            k_levelset<T, EVAP_ADVECT><<<grid, threads, 0, s>>>(m, b, phi, nullptr, ug, x, y, colour);
-        } else if (mode == EVAP_REINIT) {
-            k_levelset<T, EVAP_REINIT><<<grid, threads, 0, s>>>(m, b, phi, nf, ug, x, y, colour);
-        } else {
-            k_levelset<T, EVAP_REINIT_RHS><<<grid, threads, 0, s>>>(m, b, phi, nf, ug, x, y, colour);
-        }
-        EVAP_CHECK_LAUNCH("levelset");
-    }
-    return EVAP_OK;
+        return EVAP_OK;
+    };
+    return h->deterministic ? go(std::true_type{}) : go(std::false_type{});
 }
 template int launch_levelset<double>(evap_mesh*, int, const double*, double*, cudaStream_t);
 template int launch_levelset<float>(evap_mesh*, int, const float*, float*, cudaStream_t);

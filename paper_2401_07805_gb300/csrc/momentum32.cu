@@ -30,7 +30,7 @@ struct Scale32 {
 };
 
 
-template <int P, int CB, int MINB>
+template <int P, int CB, int MINB, bool DET>
 __global__ void __launch_bounds__(CB*(P + 1) * (P + 1), MINB)
     k_momentum32(MeshArgs<float> m, Scale32 hs, const int8_t* __restrict__ code,
                  const int32_t* __restrict__ tindex, const float* __restrict__ table, const float* __restrict__ qc32,
@@ -45,16 +45,19 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1), MINB)
     const int lc = tid % CB, l = tid / CB;
     const int n = m.n, M = m.M;
     // A block holds CB consecutive cells of one x-row: (cx, cy, cz) = (CB * xb + lc, row % n, row / n).  In a colour
-    // pass (colour = pb + 2 py + 4 pz >= 0) the blocks with xb = pb mod 2 of the rows with cy = py, cz = pz mod 2:
-    // two such blocks share no node, and inside a block the even cells scatter before the odd ones.
+    // pass (DET, colour = pb + 2 py + 4 pz) the blocks with xb = pb mod 2 of the rows with cy = py, cz = pz mod 2:
+    // two such blocks share no node, and inside a block the even cells scatter before the odd ones.  The atomic
+    // variant (DET false) is compiled apart: it ignores colour and adds each result as soon as it is formed.
     const int nxc = (n + CB - 1) / CB;
     int cx, cy, cz;
+    int64_t cell;
     bool active;
-    if (colour < 0) {
+    if constexpr (!DET) {
         const int row = (int)(blockIdx.x / (unsigned)nxc);
         cx = ((int)blockIdx.x - row * nxc) * CB + lc;
         cy = row % n;
         cz = row / n;
+        cell = cx + (int64_t)n * row;
         active = cx < n;
     } else {
         const int pb = colour & 1, py = (colour >> 1) & 1, pz = colour >> 2;
@@ -64,10 +67,9 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1), MINB)
         cx = xb * CB + lc;
         cy = 2 * (rowc % hy) + py;
         cz = 2 * (rowc / hy) + pz;
+        cell = cx + (int64_t)n * (cy + (int64_t)n * cz);
         active = cx < n;
     }
-    const bool plain = colour >= 0;
-    const int64_t cell = cx + (int64_t)n * (cy + (int64_t)n * cz);
     float* cs = sm + lc;
     auto S_ = [cs](int slot) -> float& { return cs[slot * CB]; };
     auto at = [](int z, int yy, int xx) { return xx + Q * (yy + Q * z); };
@@ -156,7 +158,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1), MINB)
             const int8_t cc = code[cell];
             const float* tb = cc == CELL_TABLE ? table + (int64_t)tindex[cell] * TAB_K * NQ : nullptr;
             // the cache's block of 32 x-consecutive cells holding this cell, and its place in it
-            const int64_t cblk = (int64_t)(cy + n * cz) * nxc + cx / CB;
+            const int64_t cblk = DET ? (int64_t)(cy + n * cz) * nxc + cx / CB : (int64_t)blockIdx.x;
             const float* cq = qc32 + cblk * QC32_K * NQ * 32 + cx % CB;
             const float wyz = B.wf[qy] * B.wf[qz];
             float Pv[3][Q], Py[3][Q], Pz[3][Q], Pd[2];
@@ -294,6 +296,8 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1), MINB)
 #pragma unroll
                     for (int q = 0; q < Q; ++q) v += (float)B.S[q][k] * r[q] + (float)B.D[q][k] * rz[q];
                     o[c][k] = v;
+                    if constexpr (!DET)
+                        if (keep[k]) atomicAdd(&y[c * m.Nu + zbase + k * MM], v);
                 }
             }
             if (div) {
@@ -303,22 +307,29 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1), MINB)
                     s0 += (float)B.N1[q][0] * v;
                     s1 += (float)B.N1[q][1] * v;
                 }
+                if constexpr (!DET) {
+                    const int64_t m1 = n + 1;
+                    atomicAdd(&yp[(cx + jx) + m1 * ((cy + jy) + m1 * (cz + 0))], s0);
+                    atomicAdd(&yp[(cx + jx) + m1 * ((cy + jy) + m1 * (cz + 1))], s1);
+                }
             }
         }
-        // atomic adds in one go; in a colour pass the even cells of the block first, then (after a block barrier)
-        // the odd ones, so that the two cells of a shared x-face never write at once
-        for (int par = 0; par < (plain ? 2 : 1); ++par) {
-            if (plain && par == 1) __syncthreads();
-            if (active && (!plain || (lc & 1) == par)) {
+        // colour pass: plain read-modify-writes, the even cells of the block first, then (after a block barrier) the
+        // odd ones, so that the two cells of a shared x-face never write at once
+        if constexpr (DET) {
+            for (int par = 0; par < 2; ++par) {
+                if (par == 1) __syncthreads();
+                if (active && (lc & 1) == par) {
 #pragma unroll
-                for (int c = 0; c < 3; ++c)
+                    for (int c = 0; c < 3; ++c)
 #pragma unroll
-                    for (int k = 0; k < Q; ++k)
-                        if (keep[k]) acc_add(&y[c * m.Nu + zbase + k * MM], o[c][k], plain);
-                if (div) {
-                    const int64_t m1 = n + 1;
-                    acc_add(&yp[(cx + jx) + m1 * ((cy + jy) + m1 * (cz + 0))], s0, plain);
-                    acc_add(&yp[(cx + jx) + m1 * ((cy + jy) + m1 * (cz + 1))], s1, plain);
+                        for (int k = 0; k < Q; ++k)
+                            if (keep[k]) y[c * m.Nu + zbase + k * MM] += o[c][k];
+                    if (div) {
+                        const int64_t m1 = n + 1;
+                        yp[(cx + jx) + m1 * ((cy + jy) + m1 * (cz + 0))] += s0;
+                        yp[(cx + jx) + m1 * ((cy + jy) + m1 * (cz + 1))] += s1;
+                    }
                 }
             }
         }
@@ -338,7 +349,7 @@ static int launch32(const evap_mesh* h, const MeshArgs<float>& m, const Scale32&
     constexpr int MINB = P == 2 ? EVAP_M32_MINB2 : 1;  // 35 KB / 80 KB of shared memory per block
     if (!h->deterministic) {
         const unsigned grid = (unsigned)(((m.n + CB - 1) / CB) * (int64_t)m.n * m.n);
-        k_momentum32<P, CB, MINB><<<grid, CB * L, 0, s>>>(m, hs, h->cell_code, h->table_index, h->table32, h->qc32, x,
+        k_momentum32<P, CB, MINB, false><<<grid, CB * L, 0, s>>>(m, hs, h->cell_code, h->table_index, h->table32, h->qc32, x,
                                                            y, yp, -1);
         EVAP_CHECK_LAUNCH("momentum32");
         return EVAP_OK;
@@ -349,7 +360,7 @@ static int launch32(const evap_mesh* h, const MeshArgs<float>& m, const Scale32&
         const int64_t hxb = (nxc - pb + 1) / 2, hy = (m.n - py + 1) / 2, hz = (m.n - pz + 1) / 2;
         const int64_t grid = hxb * hy * hz;
         if (grid == 0) continue;
-        k_momentum32<P, CB, MINB><<<(unsigned)grid, CB * L, 0, s>>>(m, hs, h->cell_code, h->table_index, h->table32,
+        k_momentum32<P, CB, MINB, true><<<(unsigned)grid, CB * L, 0, s>>>(m, hs, h->cell_code, h->table_index, h->table32,
                                                                      h->qc32, x, y, yp, colour);
         EVAP_CHECK_LAUNCH("momentum32");
     }

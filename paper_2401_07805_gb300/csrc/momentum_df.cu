@@ -57,7 +57,7 @@ constexpr size_t df_coeff_smem() {
 #define EVAP_DF_MINB2_PRES 8
 #endif
 
-template <int P, int CB, bool PRES, int MINB = 1>
+template <int P, int CB, bool PRES, int MINB, bool DET>
 __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1), MINB)
     k_momentum_df(MeshArgs<double> m, DfBasis bas, const float2* __restrict__ qc, const double* __restrict__ x,
                   double* __restrict__ y, double* __restrict__ yp, const double* __restrict__ pin, int colour) {
@@ -69,9 +69,9 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1), MINB)
     const int tid = threadIdx.x;
     const int lc = tid / NQ, t = tid % NQ;
     int cx = 0, cy = 0, cz = 0;
-    const bool active = colour_cell((int64_t)blockIdx.x * CB + lc, m.n, colour, cx, cy, cz);
+    const bool active = colour_cell((int64_t)blockIdx.x * CB + lc, m.n, DET ? colour : -1, cx, cy, cz);
     const int64_t cell = cx + (int64_t)m.n * (cy + (int64_t)m.n * cz);
-    const bool plain = colour >= 0;  // a colour pass: no other cell of the launch touches this cell's nodes
+    constexpr bool plain = DET;  // a colour pass: no other cell of the launch touches this cell's nodes
     float2* myq = sqc + (int64_t)lc * QC_K * NQ + t;
     if (active) {  // each thread fetches (and later reads) only its own point's coefficients
         const float2* src = qc + cell * QC_K * NQ + t;
@@ -324,12 +324,19 @@ int launch_momentum_df(evap_mesh* h, const MeshArgs<double>& m, const double* x,
     if (m.P == 2) {
         constexpr int CB = EVAP_DF_CB2, MINB = EVAP_DF_MINB2, MINBP = EVAP_DF_MINB2_PRES;
         constexpr size_t dyn = df_coeff_smem<2, CB>();
-        rc = p ? run(k_momentum_df<2, CB, true, MINBP>, CB, CB * 27, dyn)
-               : run(k_momentum_df<2, CB, false, MINB>, CB, CB * 27, dyn);
+        const bool det = h->deterministic;
+        rc = p ? run(det ? k_momentum_df<2, CB, true, MINBP, true> : k_momentum_df<2, CB, true, MINBP, false>, CB,
+                     CB * 27, dyn)
+               : run(det ? k_momentum_df<2, CB, false, MINB, true> : k_momentum_df<2, CB, false, MINB, false>, CB,
+                     CB * 27, dyn);
     } else {
         constexpr int CB = 4;
         constexpr size_t dyn = df_coeff_smem<3, CB>();
-        rc = p ? run(k_momentum_df<3, CB, true>, CB, CB * 64, dyn) : run(k_momentum_df<3, CB, false>, CB, CB * 64, dyn);
+        const bool det = h->deterministic;
+        rc = p ? run(det ? k_momentum_df<3, CB, true, 1, true> : k_momentum_df<3, CB, true, 1, false>, CB, CB * 64,
+                     dyn)
+               : run(det ? k_momentum_df<3, CB, false, 1, true> : k_momentum_df<3, CB, false, 1, false>, CB, CB * 64,
+                     dyn);
     }
     return rc;
 }
