@@ -30,6 +30,12 @@ struct Scale32 {
 };
 
 
+// blocks per SM for Q2 (a register cap): measured at 64^3 (100 applies, ms) 3 blocks (72 registers) 0.174, 2 (90)
+// 0.180, 4 (56, spills) 0.230
+#ifndef EVAP_M32_MINB2
+#define EVAP_M32_MINB2 3
+#endif
+
 template <int P, int CB, int MINB, bool DET>
 __global__ void __launch_bounds__(CB*(P + 1) * (P + 1), MINB)
     k_momentum32(MeshArgs<float> m, Scale32 hs, const int8_t* __restrict__ code,
@@ -159,7 +165,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1), MINB)
             const float* tb = cc == CELL_TABLE ? table + (int64_t)tindex[cell] * TAB_K * NQ : nullptr;
             // the cache's block of 32 x-consecutive cells holding this cell, and its place in it
             const int64_t cblk = DET ? (int64_t)(cy + n * cz) * nxc + cx / CB : (int64_t)blockIdx.x;
-            const float* cq = qc32 + cblk * QC32_K * NQ * 32 + cx % CB;
+            const float* cq = qc32 + cblk * QC32_K * NQ * 32 + (DET ? cx % CB : lc);
             const float wyz = B.wf[qy] * B.wf[qz];
             float Pv[3][Q], Py[3][Q], Pz[3][Q], Pd[2];
 #pragma unroll
@@ -276,7 +282,40 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1), MINB)
     }
     __syncthreads();
     // ---------------------------------------------------------------- z-lines backwards and scatter
-    {
+    if constexpr (!DET) {  // atomic adds as soon as each result is formed
+        const int i = l % Q, j = l / Q;
+        if (active) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float r[Q], rz[Q];
+#pragma unroll
+                for (int q = 0; q < Q; ++q) {
+                    r[q] = S_(c * NQ + at(q, j, i));
+                    rz[q] = S_(OFF_Z + c * NQ + at(q, j, i));
+                }
+#pragma unroll
+                for (int k = 0; k < Q; ++k) {
+                    float o = 0.f;
+#pragma unroll
+                    for (int q = 0; q < Q; ++q) o += (float)B.S[q][k] * r[q] + (float)B.D[q][k] * rz[q];
+                    if (keep[k]) atomicAdd(&y[c * m.Nu + zbase + k * MM], o);
+                }
+            }
+            if (yp && l < 4) {  // divergence row: z-sweep, Q1 node (jx, jy, jz)
+                const int jx = l % 2, jy = l / 2;
+                float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+                for (int q = 0; q < Q; ++q) {
+                    const float v = S_(OFF_QD + jx + 2 * (jy + 2 * q));
+                    s0 += (float)B.N1[q][0] * v;
+                    s1 += (float)B.N1[q][1] * v;
+                }
+                const int64_t m1 = n + 1;
+                atomicAdd(&yp[(cx + jx) + m1 * ((cy + jy) + m1 * (cz + 0))], s0);
+                atomicAdd(&yp[(cx + jx) + m1 * ((cy + jy) + m1 * (cz + 1))], s1);
+            }
+        }
+    } else {  // colour pass: the results kept, then written cell by cell
         const int i = l % Q, j = l / Q;
         float o[3][Q], s0 = 0.f, s1 = 0.f;
         const bool div = yp && l < 4;  // divergence row: z-sweep, Q1 node (jx, jy, jz)
@@ -296,8 +335,6 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1), MINB)
 #pragma unroll
                     for (int q = 0; q < Q; ++q) v += (float)B.S[q][k] * r[q] + (float)B.D[q][k] * rz[q];
                     o[c][k] = v;
-                    if constexpr (!DET)
-                        if (keep[k]) atomicAdd(&y[c * m.Nu + zbase + k * MM], v);
                 }
             }
             if (div) {
@@ -307,40 +344,28 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1), MINB)
                     s0 += (float)B.N1[q][0] * v;
                     s1 += (float)B.N1[q][1] * v;
                 }
-                if constexpr (!DET) {
-                    const int64_t m1 = n + 1;
-                    atomicAdd(&yp[(cx + jx) + m1 * ((cy + jy) + m1 * (cz + 0))], s0);
-                    atomicAdd(&yp[(cx + jx) + m1 * ((cy + jy) + m1 * (cz + 1))], s1);
-                }
             }
         }
-        // colour pass: plain read-modify-writes, the even cells of the block first, then (after a block barrier) the
-        // odd ones, so that the two cells of a shared x-face never write at once
-        if constexpr (DET) {
-            for (int par = 0; par < 2; ++par) {
-                if (par == 1) __syncthreads();
-                if (active && (lc & 1) == par) {
+        // plain read-modify-writes: the even cells of the block first, then (after a block barrier) the odd ones,
+        // so that the two cells of a shared x-face never write at once
+        for (int par = 0; par < 2; ++par) {
+            if (par == 1) __syncthreads();
+            if (active && (lc & 1) == par) {
 #pragma unroll
-                    for (int c = 0; c < 3; ++c)
+                for (int c = 0; c < 3; ++c)
 #pragma unroll
-                        for (int k = 0; k < Q; ++k)
-                            if (keep[k]) y[c * m.Nu + zbase + k * MM] += o[c][k];
-                    if (div) {
-                        const int64_t m1 = n + 1;
-                        yp[(cx + jx) + m1 * ((cy + jy) + m1 * (cz + 0))] += s0;
-                        yp[(cx + jx) + m1 * ((cy + jy) + m1 * (cz + 1))] += s1;
-                    }
+                    for (int k = 0; k < Q; ++k)
+                        if (keep[k]) y[c * m.Nu + zbase + k * MM] += o[c][k];
+                if (div) {
+                    const int64_t m1 = n + 1;
+                    yp[(cx + jx) + m1 * ((cy + jy) + m1 * (cz + 0))] += s0;
+                    yp[(cx + jx) + m1 * ((cy + jy) + m1 * (cz + 1))] += s1;
                 }
             }
         }
     }
 }
 
-// blocks per SM for Q2 (a register cap): measured at 64^3 (100 applies, ms) 3 blocks (72 registers) 0.174, 2 (90)
-// 0.180, 4 (56, spills) 0.230
-#ifndef EVAP_M32_MINB2
-#define EVAP_M32_MINB2 3
-#endif
 template <int P>
 static int launch32(const evap_mesh* h, const MeshArgs<float>& m, const Scale32& hs, const float* x, float* y,
                     float* yp, cudaStream_t s) {

@@ -46,7 +46,9 @@ constexpr size_t df_coeff_smem() {
 // Block shape for Q2: CB cells per block (one thread per point), at least MINB blocks per SM (which caps the
 // registers).  Measured at 64^3 on GB300, 100 back-to-back applies with the divergence row (ms per apply):
 // CB 4 / MINB 8 (64 registers) 0.685; CB 4 / 6 0.699; CB 8 / 4 0.700; CB 8 without a minimum (72 registers) 0.691;
-// CB 8 / 3 0.722; CB 4 / 1 (89 registers) 0.738; CB 8 / 1 0.848; CB 12 / 1 1.207.
+// CB 8 / 3 0.722; CB 4 / 1 (89 registers) 0.738; CB 8 / 1 0.848; CB 12 / 1 1.207.  Single- and two-warp blocks,
+// on another box against CB 4 / 8 at 0.691 there: CB 1 / 28 (72 registers) 0.695, CB 1 / 20 0.728, CB 2 / 14 0.709,
+// CB 3 / 10 0.720.
 #ifndef EVAP_DF_CB2
 #define EVAP_DF_CB2 4
 #endif
