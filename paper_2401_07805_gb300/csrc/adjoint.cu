@@ -1,6 +1,7 @@
 // Adjoint of the momentum apply, FP64-accurate.  The u0 terms and the material coefficients come from the
 // quadrature-point cache of set_fields (the double-float pairs the forward apply uses, so g_x is its transpose to
-// rounding); the material-law derivatives are recomputed in FP64 from phi at the points of the interface zone.
+// rounding); the chain-rule factors that depend only on phi and mdot (H'(d) d'(phi), its phi-derivative, the normal,
+// 1/|grad phi|, c_1 delta, ...) come from the adjoint table that set_fields fills in FP64 for the interface cells.
 //
 // L = w . A(phi, u0) x + w_p . (B x - g(phi, mdot))  (velocity block and divergence row of Eq. weakNavierStokes).
 // Per quadrature point with W the weight, (X, G) values/gradients of x, (Om, OmG) of w, (U, GU) of u0, pi of w_p:
@@ -48,11 +49,13 @@ __global__ void k_adjoint_init(int M, int64_t Nu, int64_t Np, unsigned faces, co
 // K = n_sub + 1: level-set shape functions per direction on a velocity cell (Q1 on its n_sub sub-intervals).
 // The interpolation of x and w, the value / gradient sensitivities and their testing run in double-float arithmetic
 // (dfloat.cuh) on the FP32 pipe, with the coefficients of the double-float cache (the pairs of the FP64 values the
-// forward apply uses); the material-law derivatives of the interface-zone points and the level-set test sweeps run in
-// FP64 (only table cells carry them: blocks without a table cell skip the sweeps).
+// forward apply uses); so do the material-law sensitivities of the interface-zone points, with the factors of the
+// adjoint table.  The level-set test sweeps run in FP64 (only table cells carry them: blocks without a table cell skip
+// the sweeps).
 // Block shape for Q2 on the velocity mesh's level set: CB cells per block, at least MINB blocks per SM (a register
-// cap).  Measured at 64^3 on GB300 (20 back-to-back adjoints, ms): CB 7 / MINB 3 (96 registers, some spills) 2.995;
-// 8 / 2 3.158; 7 / 2 (168 registers) 3.261; 4 / 4 3.403; 4 / 3 3.526; 6 / 2 3.696.
+// cap).  Measured at 64^3 on GB300 (20 back-to-back adjoints, ms), with the zone sensitivities from the adjoint
+// table: CB 7 / MINB 3 (96 registers, some spills) 1.962; 8 / 2 2.126; 7 / 2 2.150; 6 / 3 2.241; 4 / 4 2.301.
+// Before the table (zone work in FP64): 7 / 3 2.995; 8 / 2 3.158; 7 / 2 3.261; 4 / 4 3.403; 4 / 3 3.526.
 #ifndef EVAP_ADJ_CB2
 #define EVAP_ADJ_CB2 7
 #endif
@@ -62,9 +65,9 @@ __global__ void k_adjoint_init(int M, int64_t Nu, int64_t Np, unsigned faces, co
 
 template <int P, int CB, int K, int MINB = 2>
 __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1), MINB)
-    k_adjoint(MeshArgs<double> m, DfBasis dfb, Basis<double> bas, const double* __restrict__ phi,
-              const double* __restrict__ mdot, const int8_t* __restrict__ code, const int32_t* __restrict__ tindex,
-              const double* __restrict__ table, const float2* __restrict__ qcd, const double* __restrict__ w,
+    k_adjoint(MeshArgs<double> m, DfBasis dfb, Basis<double> bas, dfl rho_liq, dfl rho_gas,
+              const int8_t* __restrict__ code, const int32_t* __restrict__ tindex, const float2* __restrict__ adjt,
+              const float2* __restrict__ qcd, const double* __restrict__ w,
               const double* __restrict__ wp, const double* __restrict__ x, double* gx, double* gu, double* gphi,
               double* gm, int colour) {
     constexpr int Q = P + 1, NQ = Q * Q * Q;
@@ -157,13 +160,13 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1), MINB)
         // cached coefficients (k_qp_coeffs): 0 W rho c_m, 1..3 W rho u0, 4..12 newton W rho grad u0, 13 2 W mu, 17 W
         const float2* qp = qcd + cell * QC_K * NQ + t;
         const dfl W = ld_df(qp + 17 * NQ);
-        const int8_t cc = code[cell];
-        const double rho_c = tcell ? table[(int64_t)tindex[cell] * TAB_K * NQ + t]
-                                   : (cc == CELL_LIQUID ? m.rho_H1 : m.rho_H0);
-        const dfl wr = df_mul(W, df_from_double(rho_c));  // the W rho of the forward apply
+        // this point's entries of the adjoint table (table cells only; k_fill_table)
+        const float2* ap = tcell ? adjt + (int64_t)tindex[cell] * ADJ_K * NQ + t : nullptr;
+        const dfl rho = tcell ? ld_df(ap + ADJ_RHO * NQ) : (code[cell] == CELL_LIQUID ? rho_liq : rho_gas);
+        const dfl wr = df_mul(W, rho);  // the W rho of the forward apply
         // w_p (pressure space, Q1 on the cell) and the level set (its own mesh; only in table cells) at the point
         const double tx = bas.t[a], ty = bas.t[b], tz = bas.t[c];
-        double ph = 0, pi = 0;
+        double pi = 0;
         if (wp) {  // trilinear interpolation by successive linear interpolation (14 FP64 operations, not 40)
             const double* w0 = wp + cx + m1 * (cy + m1 * cz);
             double e[2][2];
@@ -177,12 +180,9 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1), MINB)
             const double f0 = fma(ty, e[0][1] - e[0][0], e[0][0]), f1 = fma(ty, e[1][1] - e[1][0], e[1][0]);
             pi = fma(tz, f1 - f0, f0);
         }
-        double gp[3] = {0, 0, 0}, md = 0.0;
-        if (tcell) ls_at(phi, m, cx, cy, cz, tx, ty, tz, ph, gp);
         // the phi / mdot sensitivities and the normal are needed only in the interface zone (or with the correction
         // applied everywhere), which lies in table cells; elsewhere H is 0 or 1 and its derivatives vanish
-        const bool zone = tcell && fabs(ph) < PHI_BAND;
-        const bool full = zone || (tcell && m.stress != 0 && m.corr_zone != 0);
+        const bool full = tcell && (ap[ADJ_ZONE * NQ].x != 0.f || (m.stress != 0 && m.corr_zone != 0));
         const dfl wm = ld_df(qp + 13 * NQ);
         const dfl hwm = df_scale2(wm, 0.5f);
         const dfl Wpi = df_mul(W, df_from_double(pi));
@@ -208,93 +208,93 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1), MINB)
                 gug[d][e] = m.newton ? df_mul(wr, df_mul(Om[d], X[e])) : dfl{0.f, 0.f};
             }
         }
-        if (full) {  // material-law derivatives in FP64 (interface-zone points only)
-            double Xd[3], Gd[3][3], Omd[3], OmGd[3][3];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                Xd[k] = df_to_double(X[k]);
-                Omd[k] = df_to_double(Om[k]);
-#pragma unroll
-                for (int l = 0; l < 3; ++l) {
-                    Gd[k][l] = df_to_double(G[k][l]);
-                    OmGd[k][l] = df_to_double(OmG[k][l]);
-                }
-            }
-            double qv[QC_K];
-#pragma unroll
-            for (int k = 0; k < QC_K; ++k) {
-                const dfl v = ld_df(qp + k * NQ);
-                qv[k] = df_to_double(v);
-            }
-            const double Wd = qv[17], wmd = qv[13];
-            const double wrd = Wd * rho_c;
-            double gm_[3];
-            ls_at(mdot, m, cx, cy, cz, tx, ty, tz, md, gm_);
-            const Material mat = material(ph, gp[0], gp[1], gp[2], m);
-            const double rho = mat.rho;
-            const double zg = correction_on(m, mat.zone) ? 1.0 : 0.0;
-            const double* nv = mat.n;
-            const double tr = Gd[0][0] + Gd[1][1] + Gd[2][2];
-            double nOn = 0.0;
-#pragma unroll
-            for (int i = 0; i < 3; ++i)
-#pragma unroll
-                for (int j = 0; j < 3; ++j) nOn += nv[i] * OmGd[i][j] * nv[j];
-            const dfl corr = df_from_double(wmd * zg * nOn);
-#pragma unroll
-            for (int d = 0; d < 3; ++d) gxg[d][d] = df_sub(gxg[d][d], corr);
-            double dH = 0.0, d2H = 0.0, dd = 0.0, d2d = 0.0;
-            if (mat.zone) {
-                const double dist = m.eps * log((1.0 + ph) / (1.0 - ph));
-                double sn, cs;
-                sincos(PI * dist / (3.0 * m.eps), &sn, &cs);
-                dH = (1.0 + cs) / (6.0 * m.eps);
-                d2H = -PI * sn / (18.0 * m.eps * m.eps);
-                const double om = 1.0 - ph * ph;
-                dd = 2.0 * m.eps / om;
-                d2d = 4.0 * m.eps * ph / (om * om);
-            }
-            // coefficient sensitivities; u0 and newton grad u0 from the cached W rho u0 / (W rho)
-            const double iwr = 1.0 / wrd;
-            double dL_drho = 0.0, dL_dmu = 0.0, dL_dn[3];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                const double Fk = m.c_mass * Xd[k] +
-                                  (qv[1] * Gd[k][0] + qv[2] * Gd[k][1] + qv[3] * Gd[k][2] + qv[4 + 3 * k] * Xd[0] +
-                                   qv[5 + 3 * k] * Xd[1] + qv[6 + 3 * k] * Xd[2]) * iwr;
-                dL_drho += Omd[k] * Fk;
-#pragma unroll
-                for (int l = 0; l < 3; ++l)
-                    dL_dmu += OmGd[k][l] * (0.5 * (Gd[k][l] + Gd[l][k]) - zg * tr * nv[k] * nv[l]);
-            }
-            dL_drho *= Wd;
-            dL_dmu *= 2.0 * Wd;
+        if (full) {  // material-law sensitivities (interface-zone points only), double-float arithmetic
+            const dfl nv[3] = {ld_df(ap + (ADJ_N + 0) * NQ), ld_df(ap + (ADJ_N + 1) * NQ), ld_df(ap + (ADJ_N + 2) * NQ)};
+            const bool zg = ap[ADJ_ZG * NQ].x != 0.f;
+            const dfl tr = df_add(df_add(G[0][0], G[1][1]), G[2][2]);
+            // OmG n, OmG^T n and n . OmG n
+            dfl on[3], otn[3];
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
-                double sacc = 0.0;
+                dfl u = df_prod(OmG[i][0], nv[0]), v = df_prod(OmG[0][i], nv[0]);
 #pragma unroll
-                for (int j = 0; j < 3; ++j) sacc += (OmGd[i][j] + OmGd[j][i]) * nv[j];
-                dL_dn[i] = -wmd * zg * tr * sacc;
+                for (int j = 1; j < 3; ++j) {
+                    df_fma(u, OmG[i][j], nv[j]);
+                    df_fma(v, OmG[j][i], nv[j]);
+                }
+                on[i] = df_norm(u);
+                otn[i] = df_norm(v);
             }
-            const double krho = 1.0 / m.rho_l - 1.0 / m.rho_g;  // d(1/rho)/dH, Eq. (rhoEff)
-            const double drho_dH = -rho * rho * krho;
-            const double dmu_dH = m.mu_l - m.mu_g;
-            dphi = (dL_drho * drho_dH + dL_dmu * dmu_dH) * dH * dd;
-            const double gn = sqrt(gp[0] * gp[0] + gp[1] * gp[1] + gp[2] * gp[2]);
-            if (gn * m.h > GRAD_TINY) {
-                const double pn = dL_dn[0] * nv[0] + dL_dn[1] * nv[1] + dL_dn[2] * nv[2];
+            dfl nOn = df_prod(nv[0], on[0]);
+            df_fma(nOn, nv[1], on[1]);
+            df_fma(nOn, nv[2], on[2]);
+            nOn = df_norm(nOn);
+            if (zg) {  // the corrected strain's term of g_x
+                const dfl corr = df_mul(wm, nOn);
 #pragma unroll
-                for (int i = 0; i < 3; ++i) dg[i] = (dL_dn[i] - pn * nv[i]) / gn;
+                for (int d = 0; d < 3; ++d) gxg[d][d] = df_sub(gxg[d][d], corr);
             }
-            if (wp) {  // through v_dil = mdot c_1 delta (Eq. evaporDil)
-                const double kdil = dilation_coefficient(m);
-                const double dL_dv = -Wd * pi;
-                const double delta = mat.zone ? dH * dd * gn : 0.0;
-                dm = dL_dv * kdil * delta;
-                dphi += dL_dv * md * kdil * (d2H * dd * dd + dH * d2d) * gn;
+            // dL/drho = W Om . (c_m X + G u0 + newton grad u0 X) = (1/rho) sum_k Om_k (cached W rho terms)_k
+            const dfl U[3] = {ld_df(qp + 1 * NQ), ld_df(qp + 2 * NQ), ld_df(qp + 3 * NQ)};
+            dfl sr{0.f, 0.f};
 #pragma unroll
-                for (int i = 0; i < 3; ++i) dg[i] += dL_dv * md * kdil * dH * dd * nv[i];
+            for (int k = 0; k < 3; ++k) {
+                dfl f = df_prod(c0, X[k]);
+#pragma unroll
+                for (int b2 = 0; b2 < 3; ++b2) df_fma(f, U[b2], G[k][b2]);
+                if (m.newton) {
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) df_fma(f, ld_df(qp + (4 + 3 * k + d) * NQ), X[d]);
+                }
+                if (k == 0)
+                    sr = df_prod(Om[0], df_norm(f));
+                else
+                    df_fma(sr, Om[k], df_norm(f));
             }
+            const dfl dL_drho = df_mul(ld_df(ap + ADJ_IRHO * NQ), df_norm(sr));
+            // dL/dmu = 2 W (OmG : sym G - z tr(G) n . OmG n)
+            dfl smu = df_prod(OmG[0][0], G[0][0]);
+            df_fma(smu, OmG[1][1], G[1][1]);
+            df_fma(smu, OmG[2][2], G[2][2]);
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+#pragma unroll
+                for (int l = k + 1; l < 3; ++l)
+                    df_fma(smu, df_add(OmG[k][l], OmG[l][k]), df_scale2(df_add(G[k][l], G[l][k]), 0.5f));
+            if (zg) df_fma(smu, df_neg(tr), nOn);
+            const dfl dL_dmu = df_mul(df_scale2(W, 2.0f), df_norm(smu));
+            // dL/dn = -2 W mu z tr(G) (OmG + OmG^T) n; its part normal to n drops out (dn/dgrad phi)
+            dfl dLdn[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+            if (zg) {
+                const dfl wtr = df_neg(df_mul(wm, tr));
+#pragma unroll
+                for (int i = 0; i < 3; ++i) dLdn[i] = df_mul(wtr, df_add(on[i], otn[i]));
+            }
+            dfl dp = df_prod(dL_drho, ld_df(ap + ADJ_CRHO * NQ));
+            df_fma(dp, dL_dmu, ld_df(ap + ADJ_CMU * NQ));
+            dfl pn = df_prod(dLdn[0], nv[0]);
+            df_fma(pn, dLdn[1], nv[1]);
+            df_fma(pn, dLdn[2], nv[2]);
+            pn = df_neg(df_norm(pn));
+            const dfl ign = ld_df(ap + ADJ_IGN * NQ);
+            dfl dgv[3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                dfl u = dLdn[i];
+                df_fma(u, pn, nv[i]);
+                dgv[i] = df_mul(df_norm(u), ign);
+            }
+            if (wp) {  // through v_dil = mdot c_1 delta (Eq. evaporDil), dL/dv_dil = -W pi
+                const dfl dLdv = df_neg(Wpi);
+                dm = df_to_double(df_mul(dLdv, ld_df(ap + ADJ_KD1 * NQ)));
+                df_fma(dp, dLdv, ld_df(ap + ADJ_KD2 * NQ));
+                const dfl k3 = df_mul(dLdv, ld_df(ap + ADJ_KD3 * NQ));
+#pragma unroll
+                for (int i = 0; i < 3; ++i) dgv[i] = df_add(dgv[i], df_mul(k3, nv[i]));
+            }
+            dphi = df_to_double(df_norm(dp));
+#pragma unroll
+            for (int i = 0; i < 3; ++i) dg[i] = df_to_double(dgv[i]);
         }
     }
     __syncthreads();
@@ -431,14 +431,15 @@ int launch_adjoint(evap_mesh* h, const double* w, const double* wp, const double
     EVAP_CHECK_LAUNCH("adjoint_init");
     const DfBasis dfb = make_df_basis(h->b, m.inv_h);
     const float2* qcd = reinterpret_cast<const float2*>(h->qcdf);
+    const dfl rho_liq = df_from_double(m.rho_H1), rho_gas = df_from_double(m.rho_H0);  // rho outside table cells
     const int c0 = h->deterministic ? 0 : -1, c1 = h->deterministic ? 8 : 0;  // colour passes, or one atomic pass
     auto run = [&](auto kern, int CB, int threads) -> int {
         for (int colour = c0; colour < std::max(c1, c0 + 1); ++colour) {
             const int64_t cells = colour_cells(m.n, colour);
             if (cells == 0) continue;
-            kern<<<(unsigned)((cells + CB - 1) / CB), threads, 0, s>>>(m, dfb, h->b, h->phi, h->mdot, h->cell_code,
-                                                                       h->table_index, h->table, qcd, w, wp, x, gx,
-                                                                       gu, gphi, gm, colour);
+            kern<<<(unsigned)((cells + CB - 1) / CB), threads, 0, s>>>(m, dfb, h->b, rho_liq, rho_gas, h->cell_code,
+                                                                       h->table_index, h->adj_table, qcd, w, wp, x,
+                                                                       gx, gu, gphi, gm, colour);
             EVAP_CHECK_LAUNCH("adjoint");
         }
         return EVAP_OK;

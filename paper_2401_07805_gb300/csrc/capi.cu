@@ -179,7 +179,7 @@ static int check_inputs(evap_mesh* h, const char* who, cudaStream_t s, std::init
 
 static void free_all(evap_mesh* h) {
     void* ptrs[] = {h->phi, h->u, h->mdot, h->u32, h->phi32, h->cell_code, h->table_index, h->table_count,
-                    h->table, h->table32, h->qc, h->qcdf, h->qc32, h->ugamma, h->ugamma32, h->ugammadf, h->cpp_flags, h->flag_count, h->band_list,
+                    h->table, h->table32, h->adj_table, h->qc, h->qcdf, h->qc32, h->ugamma, h->ugamma32, h->ugammadf, h->cpp_flags, h->flag_count, h->band_list,
                     h->band_count, h->band_y, h->cpp_evals, h->ls_normal_store, h->ls_normal32_store, h->geo_ws, h->geo_elem, h->geo_kry, h->schur_S, h->diag,
                     h->diag32, h->ws, h->red, h->cont_rhs, h->sd_ws, h->sd_red, h->nonfinite, h->step_ws,
                     h->tp_fac, h->tp_sigma, h->tp_sigma64};

@@ -120,6 +120,7 @@ struct evap_mesh {
     int64_t table_cap = 0;           // cells the table can hold
     double* table = nullptr;
     float* table32 = nullptr;
+    float2* adj_table = nullptr;  // [table_cap][ADJ_K][nq] pairs for the adjoint
     // quadrature-point coefficients of the FP64 momentum operator, all cells [ncell][QC_K][nq]
     double* qc = nullptr;
     // the same coefficients as double-float pairs (hi, lo) [ncell][QC_K][nq] for the double-float FP64 apply
@@ -191,6 +192,24 @@ struct evap_mesh {
     int64_t tp_off[3] = {0, 0, 0};
     bool tp_valid = false;    // FP32 Sigma of the current diagonal
     bool tp64_valid = false;  // FP64 Sigma of the current diagonal
+};
+
+// Adjoint table, per quadrature point of a table cell (double-float pairs, the FP64 values of k_fill_table): the
+// factors of the adjoint's chain rule that depend only on phi and mdot (Eqs. heaviside, rhoEff, muEff,
+// normal_vector, delta, evaporDil): see adjoint.cu.
+enum AdjSlot : int {
+    ADJ_CRHO = 0,  // (drho/dH) H'(d) d'(phi) in the zone, else 0
+    ADJ_CMU,       // (dmu/dH) H'(d) d'(phi) in the zone, else 0
+    ADJ_N,         // 3 slots: the unit normal (0 where |grad phi| h <= GRAD_TINY)
+    ADJ_ZG = ADJ_N + 3,  // correction gate z (1 or 0)
+    ADJ_IGN,       // 1 / |grad phi| (0 where the normal is 0)
+    ADJ_KD1,       // c_1 delta (the v_dil factor of mdot)
+    ADJ_KD2,       // mdot c_1 (H''(d) d'(phi)^2 + H'(d) d''(phi)) |grad phi|
+    ADJ_KD3,       // mdot c_1 H'(d) d'(phi)
+    ADJ_IRHO,      // 1 / rho
+    ADJ_RHO,       // rho
+    ADJ_ZONE,      // 1 in the zone |phi| < tanh(3/2), else 0
+    ADJ_K
 };
 
 #include <functional>  // host-side declarations below

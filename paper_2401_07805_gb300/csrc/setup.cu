@@ -2,6 +2,7 @@
 // the level-set transport velocity with closest-point projection (App. C).
 #include <cmath>
 
+#include "dfloat.cuh"
 #include "physics.cuh"
 
 namespace evap {
@@ -100,7 +101,7 @@ __global__ void k_classify(MeshArgs<double> m, Basis<double> b, const double* __
 // with the sign of App. A, dilation_coefficient).
 __global__ void k_fill_table(MeshArgs<double> m, Basis<double> b, const double* __restrict__ phi,
                              const double* __restrict__ mdot, const int8_t* __restrict__ code,
-                             const int32_t* __restrict__ tindex, double* table, float* table32) {
+                             const int32_t* __restrict__ tindex, double* table, float* table32, float2* adj) {
     const int nq = b.Q * b.Q * b.Q;
     const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t cell = gid / nq;
@@ -122,6 +123,40 @@ __global__ void k_fill_table(MeshArgs<double> m, Basis<double> b, const double* 
         table[base + (int64_t)k * nq] = vals[k];
         table32[base + (int64_t)k * nq] = (float)vals[k];
     }
+    // adjoint factors: H'(d) d'(phi) and its phi-derivative (H''(d) d'(phi)^2 + H'(d) d''(phi)) in the zone
+    double dHdd = 0.0, d2 = 0.0;
+    if (mat.zone) {
+        const double d = m.eps * log((1.0 + ph) / (1.0 - ph));
+        double sn, cs;
+        sincos(PI * d / (3.0 * m.eps), &sn, &cs);
+        const double dH = (1.0 + cs) / (6.0 * m.eps), d2H = -PI * sn / (18.0 * m.eps * m.eps);
+        const double om = 1.0 - ph * ph;
+        const double dd = 2.0 * m.eps / om, d2d = 4.0 * m.eps * ph / (om * om);
+        dHdd = dH * dd;
+        d2 = d2H * dd * dd + dH * d2d;
+    }
+    const double gn = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    const double kdil = dilation_coefficient(m);
+    double av[ADJ_K];
+    av[ADJ_CRHO] = -mat.rho * mat.rho * (1.0 / m.rho_l - 1.0 / m.rho_g) * dHdd;
+    av[ADJ_CMU] = (m.mu_l - m.mu_g) * dHdd;
+    av[ADJ_N + 0] = mat.n[0];
+    av[ADJ_N + 1] = mat.n[1];
+    av[ADJ_N + 2] = mat.n[2];
+    av[ADJ_ZG] = z;
+    av[ADJ_IGN] = gn * m.h > GRAD_TINY ? 1.0 / gn : 0.0;
+    av[ADJ_KD1] = kdil * mat.delta;
+    av[ADJ_KD2] = md * kdil * d2 * gn;
+    av[ADJ_KD3] = md * kdil * dHdd;
+    av[ADJ_IRHO] = 1.0 / mat.rho;
+    av[ADJ_RHO] = mat.rho;
+    av[ADJ_ZONE] = mat.zone ? 1.0 : 0.0;
+    const int64_t abase = (int64_t)tindex[cell] * ADJ_K * nq + q;
+#pragma unroll
+    for (int k = 0; k < ADJ_K; ++k) {
+        const dfl v = df_from_double(av[k]);
+        adj[abase + (int64_t)k * nq] = make_float2(v.hi, v.lo);
+    }
 }
 
 int launch_setup_coefficients(evap_mesh* h, cudaStream_t s) {
@@ -139,18 +174,22 @@ int launch_setup_coefficients(evap_mesh* h, cudaStream_t s) {
     if (count > h->table_cap) {
         if (h->table) cudaFree(h->table);
         if (h->table32) cudaFree(h->table32);
+        if (h->adj_table) cudaFree(h->adj_table);
         h->table = nullptr;
         h->table32 = nullptr;
+        h->adj_table = nullptr;
         h->table_cap = 0;
         const int64_t cap = count + count / 8 + 16;
         EVAP_CUDA(cudaMalloc(&h->table, cap * TAB_K * nq * sizeof(double)));
         EVAP_CUDA(cudaMalloc(&h->table32, cap * TAB_K * nq * sizeof(float)));
+        EVAP_CUDA(cudaMalloc(&h->adj_table, cap * ADJ_K * nq * sizeof(float2)));
         h->table_cap = cap;
     }
     if (count > 0) {
         const int64_t total = m.ncell * nq;
         k_fill_table<<<blocks_for(total, 256, 1LL << 40), 256, 0, s>>>(m, h->b, h->phi, h->mdot, h->cell_code,
-                                                                       h->table_index, h->table, h->table32);
+                                                                       h->table_index, h->table, h->table32,
+                                                                       h->adj_table);
         EVAP_CHECK_LAUNCH("fill_table");
     }
     return EVAP_OK;
