@@ -19,6 +19,7 @@
 // cell subdivided n_sub times per direction).
 #include <algorithm>
 
+#include "async_copy.cuh"
 #include "dfloat.cuh"
 #include "physics.cuh"
 
@@ -54,7 +55,8 @@ __global__ void k_adjoint_init(int M, int64_t Nu, int64_t Np, unsigned faces, co
 // the sweeps).
 // Block shape for Q2 on the velocity mesh's level set: CB cells per block, at least MINB blocks per SM (a register
 // cap).  Measured at 64^3 on GB300 (20 back-to-back adjoints, ms), with the zone sensitivities from the adjoint
-// table: CB 7 / MINB 3 (96 registers, some spills) 1.962; 8 / 2 2.126; 7 / 2 2.150; 6 / 3 2.241; 4 / 4 2.301.
+// table: CB 7 / MINB 3 (96 registers, some spills) 1.962; 8 / 2 2.126; 7 / 2 2.150; 6 / 3 2.241; 4 / 4 2.301; with
+// the cached coefficients copied into shared memory by cp.async during the interpolation sweeps, 7 / 3 1.853.
 // Before the table (zone work in FP64): 7 / 3 2.995; 8 / 2 3.158; 7 / 2 3.261; 4 / 4 3.403; 4 / 3 3.526.
 #ifndef EVAP_ADJ_CB2
 #define EVAP_ADJ_CB2 7
@@ -76,12 +78,21 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1), MINB)
     __shared__ double sNL[Q][K], sDL[Q][K];
     __shared__ dfl buf[2][CB][12][NQ];
     __shared__ double q1a[CB][5][K * Q * Q], q1b[CB][5][K * K * Q];  // level-set test sweeps (FP64)
+    extern __shared__ float2 sqc[];  // [cell][QC_K][point]: this block's cached coefficients, copied during the sweeps
     const int tid = threadIdx.x;
     const int lc = tid / NQ, t = tid % NQ;
     int cx = 0, cy = 0, cz = 0;
     const bool active = colour_cell((int64_t)blockIdx.x * CB + lc, m.n, colour, cx, cy, cz);
     const int64_t cell = cx + (int64_t)m.n * (cy + (int64_t)m.n * cz);
     const bool plain = colour >= 0;  // a colour pass: no other cell of the launch touches this cell's nodes
+    float2* myq = sqc + (int64_t)lc * QC_K * NQ + t;
+    if (active) {  // each thread fetches (and later reads) only its own point's coefficients: 0..3, 13, 17, newton 4..12
+        const float2* src = qcd + cell * QC_K * NQ + t;
+#pragma unroll
+        for (int k = 0; k < QC_K; ++k)
+            if (k < 4 || k == 13 || k == 17 || (m.newton && k <= 12)) cp_async8(myq + k * NQ, src + k * NQ);
+    }
+    cp_async_commit();
     if (tid < Q * Q) {
         sS[tid / Q][tid % Q] = dfb.S[tid / Q][tid % Q];
         sDc[tid / Q][tid % Q] = dfb.Dc[tid / Q][tid % Q];
@@ -158,7 +169,8 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1), MINB)
         dfl (*G)[3] = &Gr[0];
         dfl (*OmG)[3] = &Gr[3];
         // cached coefficients (k_qp_coeffs): 0 W rho c_m, 1..3 W rho u0, 4..12 newton W rho grad u0, 13 2 W mu, 17 W
-        const float2* qp = qcd + cell * QC_K * NQ + t;
+        cp_async_wait_all();
+        const float2* qp = myq;
         const dfl W = ld_df(qp + 17 * NQ);
         // this point's entries of the adjoint table (table cells only; k_fill_table)
         const float2* ap = tcell ? adjt + (int64_t)tindex[cell] * ADJ_K * NQ + t : nullptr;
@@ -434,10 +446,14 @@ int launch_adjoint(evap_mesh* h, const double* w, const double* wp, const double
     const dfl rho_liq = df_from_double(m.rho_H1), rho_gas = df_from_double(m.rho_H0);  // rho outside table cells
     const int c0 = h->deterministic ? 0 : -1, c1 = h->deterministic ? 8 : 0;  // colour passes, or one atomic pass
     auto run = [&](auto kern, int CB, int threads) -> int {
+        const size_t dyn = sizeof(float2) * QC_K * threads;  // the block's cached coefficients (threads = CB NQ)
+        EVAP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+        EVAP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                       (int)cudaSharedmemCarveoutMaxShared));
         for (int colour = c0; colour < std::max(c1, c0 + 1); ++colour) {
             const int64_t cells = colour_cells(m.n, colour);
             if (cells == 0) continue;
-            kern<<<(unsigned)((cells + CB - 1) / CB), threads, 0, s>>>(m, dfb, h->b, rho_liq, rho_gas, h->cell_code,
+            kern<<<(unsigned)((cells + CB - 1) / CB), threads, dyn, s>>>(m, dfb, h->b, rho_liq, rho_gas, h->cell_code,
                                                                        h->table_index, h->adj_table, qcd, w, wp, x,
                                                                        gx, gu, gphi, gm, colour);
             EVAP_CHECK_LAUNCH("adjoint");

@@ -25,18 +25,11 @@
 // gate z n is zero (outside the interface zone), and the Newton terms on Picard meshes.
 #include <algorithm>
 
+#include "async_copy.cuh"
 #include "dfloat.cuh"
 #include "physics.cuh"
 
 namespace evap {
-
-// 8-byte asynchronous copy global -> shared (cp.async, completion tracked per thread by commit / wait groups)
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 template <int P, int CB>
 constexpr size_t df_coeff_smem() {
