@@ -52,6 +52,31 @@ constexpr size_t df_coeff_smem() {
 #define EVAP_DF_MINB2_PRES 8
 #endif
 
+// Normalization of the sweep results (the closing Fast2Sum of each dot product).  A result that is converted to FP64
+// next (the last transposed sweep) or that only starts a new accumulation (the value flux F, whose hi and lo enter
+// the test sum through TwoSum) loses nothing when left unnormalized (hi + lo stays exact).  A result that is then
+// multiplied carries its larger lo part into the rounded cross terms.  EVAP_DF_LAZY: 0 normalize all; 3 skip only the
+// free cases; 2 also the gradients; 1 every sweep result.  Measured at 64^3 (ms per apply; relative error of the
+// smoke case against the oracle): 0 0.6925, 4.8e-15; 3 0.6812, 5.7e-15; 2 0.6767, 5.7e-15; 1 0.6639, 8.9e-15, and
+// with 1 the coupled step's velocity-pressure solve no longer reaches its 1e-10 (its rounding floor rises to 1.2e-10).
+#ifndef EVAP_DF_LAZY
+#define EVAP_DF_LAZY 2
+#endif
+template <int Q, bool LAZY>
+__device__ __forceinline__ dfl df_dot_lz(const dfl* c, const dfl* v, int stride) {
+    if constexpr (LAZY) {
+        dfl s = df_prod(c[0], v[0]);
+#pragma unroll
+        for (int k = 1; k < Q; ++k) df_fma(s, c[k], v[k * stride]);
+        return s;
+    } else {
+        return df_dot<Q>(c, v, stride);
+    }
+}
+constexpr bool LZ_SWEEP = EVAP_DF_LAZY == 1;                    // interpolation and transposed sweeps, w
+constexpr bool LZ_GRAD = EVAP_DF_LAZY == 1 || EVAP_DF_LAZY == 2;  // gradients at the points
+constexpr bool LZ_FREE = EVAP_DF_LAZY != 0;                      // the last sweep, the value flux
+
 template <int P, int CB, bool PRES, int MINB, bool DET>
 __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1), MINB)
     k_momentum_df(MeshArgs<double> m, DfBasis bas, const float2* __restrict__ qc, const double* __restrict__ x,
@@ -98,7 +123,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1), MINB)
 #pragma unroll
         for (int k = 0; k < Q; ++k) Sa[k] = sS[a][k];
 #pragma unroll
-        for (int f = 0; f < 3; ++f) buf[1][f][lc][t] = df_dot<Q>(Sa, &buf[0][f][lc][Q * (b + Q * c)], 1);
+        for (int f = 0; f < 3; ++f) buf[1][f][lc][t] = df_dot_lz<Q, LZ_SWEEP>(Sa, &buf[0][f][lc][Q * (b + Q * c)], 1);
     }
     __syncthreads();
     if (active) {
@@ -106,7 +131,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1), MINB)
 #pragma unroll
         for (int k = 0; k < Q; ++k) Sb[k] = sS[b][k];
 #pragma unroll
-        for (int f = 0; f < 3; ++f) buf[0][f][lc][t] = df_dot<Q>(Sb, &buf[1][f][lc][a + Q * Q * c], Q);
+        for (int f = 0; f < 3; ++f) buf[0][f][lc][t] = df_dot_lz<Q, LZ_SWEEP>(Sb, &buf[1][f][lc][a + Q * Q * c], Q);
     }
     __syncthreads();
     if (active) {
@@ -114,7 +139,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1), MINB)
 #pragma unroll
         for (int k = 0; k < Q; ++k) Sc[k] = sS[c][k];
 #pragma unroll
-        for (int f = 0; f < 3; ++f) buf[1][f][lc][t] = df_dot<Q>(Sc, &buf[0][f][lc][a + Q * b], Q * Q);
+        for (int f = 0; f < 3; ++f) buf[1][f][lc][t] = df_dot_lz<Q, LZ_SWEEP>(Sc, &buf[0][f][lc][a + Q * b], Q * Q);
     }
     __syncthreads();
     // quadrature-point fluxes from the cached coefficients
@@ -132,9 +157,9 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1), MINB)
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
                 X[k] = buf[1][k][lc][t];
-                G[k][0] = df_dot<Q>(Da, &buf[1][k][lc][Q * (b + Q * c)], 1);
-                G[k][1] = df_dot<Q>(Db, &buf[1][k][lc][a + Q * Q * c], Q);
-                G[k][2] = df_dot<Q>(Dz, &buf[1][k][lc][a + Q * b], Q * Q);
+                G[k][0] = df_dot_lz<Q, LZ_GRAD>(Da, &buf[1][k][lc][Q * (b + Q * c)], 1);
+                G[k][1] = df_dot_lz<Q, LZ_GRAD>(Db, &buf[1][k][lc][a + Q * Q * c], Q);
+                G[k][2] = df_dot_lz<Q, LZ_GRAD>(Dz, &buf[1][k][lc][a + Q * b], Q * Q);
             }
         }
         cp_async_wait_all();
@@ -150,7 +175,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1), MINB)
 #pragma unroll
                 for (int d = 0; d < 3; ++d) df_fma(v, ld_df(q + (4 + 3 * k + d) * NQ), X[d]);
             }
-            F[k] = df_norm(v);
+            F[k] = LZ_FREE ? v : df_norm(v);
         }
         const dfl c13 = ld_df(q + 13 * NQ);
         const dfl tr = df_add(df_add(G[0][0], G[1][1]), G[2][2]);
@@ -224,7 +249,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1), MINB)
                 df_fma(s, Eb[r], buf[i1 / 6][i1 % 6][lc][a + Q * (r + Q * c)]);
                 df_fma(s, Ec[r], buf[i2 / 6][i2 % 6][lc][a + Q * (b + Q * r)]);
             }
-            wv[k] = df_norm(s);
+            wv[k] = LZ_SWEEP ? s : df_norm(s);
         }
         // divergence row, Q1 test functions: sum_q N1_j(q) r_q by three sweeps; x-sweep here: [jx][qy][qz]
         if (yp && t < 2 * Q * Q) {
@@ -254,7 +279,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1), MINB)
 #pragma unroll
         for (int k = 0; k < Q; ++k) Tc[k] = sS[k][c];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) buf[1][k][lc][t] = df_dot<Q>(Tc, &buf[0][k][lc][a + Q * b], Q * Q);
+        for (int k = 0; k < 3; ++k) buf[1][k][lc][t] = df_dot_lz<Q, LZ_SWEEP>(Tc, &buf[0][k][lc][a + Q * b], Q * Q);
         if (yp && t < 8) {  // z-sweep: Q1 node (jx, jy, jz)
             const int jx = t & 1, jy = (t >> 1) & 1, jz = t >> 2;
             dfl s = df_prod(sN1[0][jz], q1b[lc][jx + 2 * (jy + 2 * 0)]);
@@ -270,7 +295,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1), MINB)
 #pragma unroll
         for (int k = 0; k < Q; ++k) Tb[k] = sS[k][b];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) buf[0][k][lc][t] = df_dot<Q>(Tb, &buf[1][k][lc][a + Q * Q * c], Q);
+        for (int k = 0; k < 3; ++k) buf[0][k][lc][t] = df_dot_lz<Q, LZ_SWEEP>(Tb, &buf[1][k][lc][a + Q * Q * c], Q);
     }
     __syncthreads();
     if (active && !cons) {
@@ -279,7 +304,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1), MINB)
         for (int k = 0; k < Q; ++k) Ta[k] = sS[k][a];
 #pragma unroll
         for (int k = 0; k < 3; ++k)
-            acc_add(&y[k * m.Nu + gidx], df_to_double(df_dot<Q>(Ta, &buf[0][k][lc][Q * (b + Q * c)], 1)), plain);
+            acc_add(&y[k * m.Nu + gidx], df_to_double(df_dot_lz<Q, LZ_FREE>(Ta, &buf[0][k][lc][Q * (b + Q * c)], 1)), plain);
     }
 }
 
