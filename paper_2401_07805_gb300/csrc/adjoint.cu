@@ -58,6 +58,24 @@ __global__ void k_adjoint_init(int M, int64_t Nu, int64_t Np, unsigned faces, co
 // table: CB 7 / MINB 3 (96 registers, some spills) 1.962; 8 / 2 2.126; 7 / 2 2.150; 6 / 3 2.241; 4 / 4 2.301; with
 // the cached coefficients copied into shared memory by cp.async during the interpolation sweeps, 7 / 3 1.853.
 // Before the table (zone work in FP64): 7 / 3 2.995; 8 / 2 3.158; 7 / 2 3.261; 4 / 4 3.403; 4 / 3 3.526.
+// Normalization as in the forward double-float apply: the gradients at the points, the value sensitivities that
+// start the test sums and the last transposed sweep (converted to FP64 next) are left unnormalized (0: normalize).
+// Measured at 64^3: 1.856 -> 1.831 ms, the smoke case's gradients still within 5e-15 of the oracle's.
+#ifndef EVAP_ADJ_LAZY
+#define EVAP_ADJ_LAZY 1
+#endif
+template <int Q>
+__device__ __forceinline__ dfl adj_dot_lazy(const dfl* c, const dfl* v, int stride) {
+#if EVAP_ADJ_LAZY
+    dfl s = df_prod(c[0], v[0]);
+#pragma unroll
+    for (int k = 1; k < Q; ++k) df_fma(s, c[k], v[k * stride]);
+    return s;
+#else
+    return df_dot<Q>(c, v, stride);
+#endif
+}
+
 #ifndef EVAP_ADJ_CB2
 #define EVAP_ADJ_CB2 7
 #endif
@@ -159,9 +177,9 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1), MINB)
 #pragma unroll
             for (int f = 0; f < 6; ++f) {
                 V[f] = buf[1][lc][f][t];
-                Gr[f][0] = df_dot<Q>(Da, &buf[1][lc][f][Q * (b + Q * c)], 1);
-                Gr[f][1] = df_dot<Q>(Db, &buf[1][lc][f][a + Q * Q * c], Q);
-                Gr[f][2] = df_dot<Q>(Dz, &buf[1][lc][f][a + Q * b], Q * Q);
+                Gr[f][0] = adj_dot_lazy<Q>(Da, &buf[1][lc][f][Q * (b + Q * c)], 1);
+                Gr[f][1] = adj_dot_lazy<Q>(Db, &buf[1][lc][f][a + Q * Q * c], Q);
+                Gr[f][2] = adj_dot_lazy<Q>(Dz, &buf[1][lc][f][a + Q * b], Q * Q);
             }
         }
         const dfl* X = &V[0];
@@ -207,7 +225,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1), MINB)
 #pragma unroll
                 for (int k = 0; k < 3; ++k) df_fma(v, Om[k], ld_df(qp + (4 + 3 * k + d) * NQ));
             }
-            gxv[d] = df_norm(v);
+            gxv[d] = EVAP_ADJ_LAZY ? v : df_norm(v);
             dfl u = df_prod(Om[0], G[0][d]);
             df_fma(u, Om[1], G[1][d]);
             df_fma(u, Om[2], G[2][d]);
@@ -426,7 +444,7 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1), MINB)
         for (int k = 0; k < Q; ++k) Ta[k] = sS[k][a];
 #pragma unroll
         for (int f = 0; f < 6; ++f) {
-            const double s = df_to_double(df_dot<Q>(Ta, &buf[0][lc][f][Q * (b + Q * c)], 1));
+            const double s = df_to_double(adj_dot_lazy<Q>(Ta, &buf[0][lc][f][Q * (b + Q * c)], 1));
             if (f < 3) {
                 if (gx && !cons) acc_add(&gx[f * m.Nu + gidx], s, plain);
             } else if (gu) {
