@@ -8,6 +8,7 @@
 //                     arithmetic, not HBM, bounds these operators, and the material law and the u0 interpolation
 //                     would otherwise be recomputed by every apply
 //   launch_momentum   dispatch: FP64 -> double-float kernel, FP32 -> line kernel; the lifting variant (all columns)
+#include "dfloat.cuh"
 #include "physics.cuh"
 
 namespace evap {
@@ -43,21 +44,25 @@ __global__ void __launch_bounds__(256) k_momentum_init(int M, int64_t Nu, unsign
 // Slots 1..12 are also stored in FP32 for the FP32 apply (slots 1..3 divided by h: that kernel takes reference
 // gradients), in its 32-cell block layout
 // qc32[((blk * QC32_K + k) * NQ + pt) * 32 + lane], cell (32 xb + lane, row) in block blk = xb + ceil(n / 32) row.
+// The interpolation of u0 and every product run in double-float arithmetic (dfloat.cuh) on the FP32 pipe: the FP64
+// pipe keeps the conversions (u0 in, the FP64 copy of each coefficient out) and the few scalar factors.  The
+// double-float results are the pairs of the apply's cache as they stand; the FP64 copy is their sum (within 2^-48).
 template <int P, int CB>
 __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
-    k_qp_coeffs(MeshArgs<double> m, Basis<double> bas, const int8_t* __restrict__ code,
-                const int32_t* __restrict__ tindex, const double* __restrict__ table, const double* __restrict__ u0,
-                double* __restrict__ qc, float2* __restrict__ qcdf, float* __restrict__ qc32) {
+    k_qp_coeffs(MeshArgs<double> m, Basis<double> bas, DfBasis dfb, dfl cm_df, dfl invh_df,
+                const int8_t* __restrict__ code, const int32_t* __restrict__ tindex, const double* __restrict__ table,
+                const double* __restrict__ u0, double* __restrict__ qc, float2* __restrict__ qcdf,
+                float* __restrict__ qc32) {
     constexpr int Q = P + 1, NQ = Q * Q * Q;
-    __shared__ double sS[Q][Q], sDc[Q][Q];
-    __shared__ double buf[2][CB][3][NQ];
+    __shared__ dfl sS[Q][Q], sDc[Q][Q];
+    __shared__ dfl buf[2][CB][3][NQ];
     const int tid = threadIdx.x;
     const int lc = tid / NQ, t = tid % NQ;
     const int64_t cell = (int64_t)blockIdx.x * CB + lc;
     const bool active = cell < m.ncell;
     if (tid < Q * Q) {
-        sS[tid / Q][tid % Q] = bas.S[tid / Q][tid % Q];
-        sDc[tid / Q][tid % Q] = bas.Dc[tid / Q][tid % Q];
+        sS[tid / Q][tid % Q] = dfb.S[tid / Q][tid % Q];
+        sDc[tid / Q][tid % Q] = dfb.Dc[tid / Q][tid % Q];  // physical: Dc / h
     }
     const int a = t % Q, b = (t / Q) % Q, c = t / (Q * Q);
     const int n = m.n, M = m.M;
@@ -65,53 +70,55 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
         const int cx = (int)(cell % n), cy = (int)((cell / n) % n), cz = (int)(cell / ((int64_t)n * n));
         const int64_t gidx = (P * cx + a) + (int64_t)M * ((P * cy + b) + (int64_t)M * (P * cz + c));
 #pragma unroll
-        for (int k = 0; k < 3; ++k) buf[0][lc][k][t] = u0[k * m.Nu + gidx];
+        for (int k = 0; k < 3; ++k) buf[0][lc][k][t] = df_from_double(u0[k * m.Nu + gidx]);
     }
     __syncthreads();
-    if (active)
+    if (active) {
+        dfl Sa[Q];
 #pragma unroll
-        for (int f = 0; f < 3; ++f) {
-            double s = 0;
+        for (int k = 0; k < Q; ++k) Sa[k] = sS[a][k];
 #pragma unroll
-            for (int k = 0; k < Q; ++k) s += sS[a][k] * buf[0][lc][f][k + Q * (b + Q * c)];
-            buf[1][lc][f][t] = s;
-        }
+        for (int f = 0; f < 3; ++f) buf[1][lc][f][t] = df_dot<Q>(Sa, &buf[0][lc][f][Q * (b + Q * c)], 1);
+    }
     __syncthreads();
-    if (active)
+    if (active) {
+        dfl Sb[Q];
 #pragma unroll
-        for (int f = 0; f < 3; ++f) {
-            double s = 0;
+        for (int k = 0; k < Q; ++k) Sb[k] = sS[b][k];
 #pragma unroll
-            for (int k = 0; k < Q; ++k) s += sS[b][k] * buf[1][lc][f][a + Q * (k + Q * c)];
-            buf[0][lc][f][t] = s;
-        }
+        for (int f = 0; f < 3; ++f) buf[0][lc][f][t] = df_dot<Q>(Sb, &buf[1][lc][f][a + Q * Q * c], Q);
+    }
     __syncthreads();
-    if (active)
+    if (active) {
+        dfl Sc[Q];
 #pragma unroll
-        for (int f = 0; f < 3; ++f) {
-            double s = 0;
+        for (int k = 0; k < Q; ++k) Sc[k] = sS[c][k];
 #pragma unroll
-            for (int k = 0; k < Q; ++k) s += sS[c][k] * buf[0][lc][f][a + Q * (b + Q * k)];
-            buf[1][lc][f][t] = s;
-        }
+        for (int f = 0; f < 3; ++f) buf[1][lc][f][t] = df_dot<Q>(Sc, &buf[0][lc][f][a + Q * b], Q * Q);
+    }
     __syncthreads();
     if (!active) return;
-    double U[3], GU[3][3];
+    dfl U[3], GU[3][3];
+    {
+        dfl Da[Q], Db[Q], Dz[Q];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        U[k] = buf[1][lc][k][t];
-        double g0 = 0, g1 = 0, g2 = 0;
-#pragma unroll
-        for (int r = 0; r < Q; ++r) {
-            g0 += sDc[a][r] * buf[1][lc][k][r + Q * (b + Q * c)];
-            g1 += sDc[b][r] * buf[1][lc][k][a + Q * (r + Q * c)];
-            g2 += sDc[c][r] * buf[1][lc][k][a + Q * (b + Q * r)];
+        for (int k = 0; k < Q; ++k) {
+            Da[k] = sDc[a][k];
+            Db[k] = sDc[b][k];
+            Dz[k] = sDc[c][k];
         }
-        GU[k][0] = g0 * m.inv_h; GU[k][1] = g1 * m.inv_h; GU[k][2] = g2 * m.inv_h;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            U[k] = buf[1][lc][k][t];
+            GU[k][0] = df_dot<Q>(Da, &buf[1][lc][k][Q * (b + Q * c)], 1);
+            GU[k][1] = df_dot<Q>(Db, &buf[1][lc][k][a + Q * Q * c], Q);
+            GU[k][2] = df_dot<Q>(Dz, &buf[1][lc][k][a + Q * b], Q * Q);
+        }
     }
     double rho, mu, nz[3], vd;
     const int8_t cc = code[cell];
-    if (cc == CELL_TABLE) {
+    const bool tab = cc == CELL_TABLE;
+    if (tab) {
         const double* tb = table + (int64_t)tindex[cell] * TAB_K * NQ + t;
         rho = tb[0]; mu = tb[NQ]; nz[0] = tb[2 * NQ]; nz[1] = tb[3 * NQ]; nz[2] = tb[4 * NQ]; vd = tb[5 * NQ];
     } else {
@@ -122,32 +129,34 @@ __global__ void __launch_bounds__(CB*(P + 1) * (P + 1) * (P + 1))
         vd = 0.0;
     }
     const double W = bas.w[a] * bas.w[b] * bas.w[c] * m.vol_w;
-    const double wr = W * rho;
-    double v[QC_K];
-    v[0] = wr * m.c_mass;
+    const dfl wr = df_from_double(W * rho);
+    dfl v[QC_K];
+    v[0] = df_mul(wr, cm_df);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) v[1 + k] = wr * U[k];
+    for (int k = 0; k < 3; ++k) v[1 + k] = df_mul(wr, U[k]);
 #pragma unroll
     for (int k = 0; k < 3; ++k)
 #pragma unroll
-        for (int d = 0; d < 3; ++d) v[4 + 3 * k + d] = m.newton ? wr * GU[k][d] : 0.0;
-    v[13] = 2.0 * W * mu;
-    v[14] = nz[0]; v[15] = nz[1]; v[16] = nz[2];
-    v[17] = W;
-    v[18] = W * vd;
+        for (int d = 0; d < 3; ++d) v[4 + 3 * k + d] = m.newton ? df_mul(wr, GU[k][d]) : dfl{0.f, 0.f};
+    v[13] = df_from_double(2.0 * W * mu);
+    const dfl z0{0.f, 0.f};
+    v[14] = tab ? df_from_double(nz[0]) : z0;
+    v[15] = tab ? df_from_double(nz[1]) : z0;
+    v[16] = tab ? df_from_double(nz[2]) : z0;
+    v[17] = df_from_double(W);
+    v[18] = tab ? df_from_double(W * vd) : z0;
     const int64_t base = cell * QC_K * NQ + t;
 #pragma unroll
     for (int k = 0; k < QC_K; ++k) {
-        qc[base + (int64_t)k * NQ] = v[k];
-        const float hi = (float)v[k];
-        qcdf[base + (int64_t)k * NQ] = make_float2(hi, (float)(v[k] - (double)hi));
+        qc[base + (int64_t)k * NQ] = df_to_double(v[k]);
+        qcdf[base + (int64_t)k * NQ] = make_float2(v[k].hi, v[k].lo);
     }
     const int64_t row = cell / n;
     const int cx = (int)(cell - row * n);
     const int64_t blk = cx / 32 + (int64_t)((n + 31) / 32) * row;
     float* dst = qc32 + (blk * QC32_K * NQ + t) * 32 + (cx % 32);
 #pragma unroll
-    for (int k = 0; k < QC32_K; ++k) dst[(int64_t)k * NQ * 32] = (float)(k < 3 ? v[1 + k] * m.inv_h : v[1 + k]);
+    for (int k = 0; k < QC32_K; ++k) dst[(int64_t)k * NQ * 32] = k < 3 ? df_mul(v[1 + k], invh_df).hi : v[1 + k].hi;
 }
 
 int launch_qp_coeffs(evap_mesh* h, cudaStream_t s) {
@@ -176,14 +185,16 @@ int launch_qp_coeffs(evap_mesh* h, cudaStream_t s) {
         EVAP_CUDA(cudaMalloc(&h->qc32, need32 * sizeof(float)));
         h->qc32_len = need32;
     }
+    const DfBasis dfb = make_df_basis(h->b, m.inv_h);
+    const dfl cm = df_from_double(m.c_mass), ih = df_from_double(m.inv_h);
     if (m.P == 2) {
         constexpr int CB = 8;
-        k_qp_coeffs<2, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 27, 0, s>>>(m, h->b, h->cell_code, h->table_index,
-                                                                                  h->table, h->u, h->qc, (float2*)h->qcdf, h->qc32);
+        k_qp_coeffs<2, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 27, 0, s>>>(
+            m, h->b, dfb, cm, ih, h->cell_code, h->table_index, h->table, h->u, h->qc, (float2*)h->qcdf, h->qc32);
     } else {
         constexpr int CB = 4;
-        k_qp_coeffs<3, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 64, 0, s>>>(m, h->b, h->cell_code, h->table_index,
-                                                                                  h->table, h->u, h->qc, (float2*)h->qcdf, h->qc32);
+        k_qp_coeffs<3, CB><<<(unsigned)((m.ncell + CB - 1) / CB), CB * 64, 0, s>>>(
+            m, h->b, dfb, cm, ih, h->cell_code, h->table_index, h->table, h->u, h->qc, (float2*)h->qcdf, h->qc32);
     }
     EVAP_CHECK_LAUNCH("qp_coeffs");
     return EVAP_OK;
