@@ -2,9 +2,10 @@
 // y_p = B x - g (Eq. continuity with the dilation rate of Eq. evaporDil): the pieces shared by its implementations.
 //   k_momentum_init   y = x on the Dirichlet DoFs, 0 elsewhere (the scatter of the applies adds the free rows)
 //   k_qp_coeffs       the quadrature-point coefficients of the operator (W rho c_m, W rho u0, W rho grad u0, 2 W mu,
-//                     z n, W, W v_dil), evaluated once per set_fields in FP64 and stored in FP64 (adjoint, Jacobi
-//                     diagonal, continuity right-hand side), as double-float pairs (the FP64-accurate apply of
-//                     momentum_df.cu) and, for the u0 terms, in FP32 (the FP32 apply of momentum32.cu): on GB300 the
+//                     z n, W, W v_dil), evaluated once per set_fields in double-float arithmetic and stored as
+//                     double-float pairs (the FP64-accurate apply of momentum_df.cu and the adjoint), in FP64 (Jacobi
+//                     diagonal, continuity right-hand side, mass load) and, for the u0 terms, in FP32 (the FP32
+//                     apply of momentum32.cu): on GB300 the
 //                     arithmetic, not HBM, bounds these operators, and the material law and the u0 interpolation
 //                     would otherwise be recomputed by every apply
 //   launch_momentum   dispatch: FP64 -> double-float kernel, FP32 -> line kernel; the lifting variant (all columns)
