@@ -216,8 +216,9 @@ int evap_surface_tension(evap_handle h, const double* n, const double* kappa, do
 
 /* Adjoint of the momentum apply for L = w . A(phi, mdot, u) x + w_p . (B x - g(phi, mdot)):
  *   g_x = A^T w + B^T w_p,  g_u0 = dL/du [3 N_u],  g_phi = dL/dphi [N_phi],  g_mdot = dL/dmdot [N_phi],
- * with the quadrature-point coefficients of evap_set_fields and the material-law derivatives recomputed at the
- * points of the interface zone.  w [3 N_u] and x [3 N_u] required; w_p [N_p] may be
+ * with the quadrature-point coefficients of evap_set_fields and the chain-rule factors of the material law that
+ * depend only on phi and mdot (tabulated by evap_set_fields at the points of the interface cells); x and w are
+ * interpolated in the call.  w [3 N_u] and x [3 N_u] required; w_p [N_p] may be
  * NULL (no divergence row); any g_* may be NULL (not computed).  FP64 only. */
 int evap_apply_adjoint(evap_handle h, const double* w, const double* w_p, const double* x, double* g_x,
                        double* g_u0, double* g_phi, double* g_mdot, void* stream);
