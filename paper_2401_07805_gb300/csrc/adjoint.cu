@@ -56,7 +56,8 @@ __global__ void k_adjoint_init(int M, int64_t Nu, int64_t Np, unsigned faces, co
 // Block shape for Q2 on the velocity mesh's level set: CB cells per block, at least MINB blocks per SM (a register
 // cap).  Measured at 64^3 on GB300 (20 back-to-back adjoints, ms), with the zone sensitivities from the adjoint
 // table: CB 7 / MINB 3 (96 registers, some spills) 1.962; 8 / 2 2.126; 7 / 2 2.150; 6 / 3 2.241; 4 / 4 2.301; with
-// the cached coefficients copied into shared memory by cp.async during the interpolation sweeps, 7 / 3 1.853.
+// the cached coefficients copied into shared memory by cp.async during the interpolation sweeps, 7 / 3 1.853; with
+// the lazy normalization below, 7 / 3 1.836, 8 / 2 1.974, 7 / 2 1.978.
 // Before the table (zone work in FP64): 7 / 3 2.995; 8 / 2 3.158; 7 / 2 3.261; 4 / 4 3.403; 4 / 3 3.526.
 // Normalization as in the forward double-float apply: the gradients at the points, the value sensitivities that
 // start the test sums and the last transposed sweep (converted to FP64 next) are left unnormalized (0: normalize).

@@ -30,8 +30,8 @@ struct Scale32 {
 };
 
 
-// blocks per SM for Q2 (a register cap): measured at 64^3 (100 applies, ms) 3 blocks (72 registers) 0.174, 2 (90)
-// 0.180, 4 (56, spills) 0.230
+// blocks per SM for Q2 (a register cap): measured at 64^3 (100 applies, ms) 3 blocks (72 registers) 0.145, 2 (90)
+// 0.171, 4 (56, spills) 0.222
 #ifndef EVAP_M32_MINB2
 #define EVAP_M32_MINB2 3
 #endif
