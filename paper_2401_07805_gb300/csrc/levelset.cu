@@ -4,8 +4,9 @@
 //   EVAP_REINIT_RHS  y_i = sum_q W [ N_i x / dtau + (grad N_i . n) (1 - x^2) / 2 ]        explicit compressive flux
 // with n the frozen normal at the quadrature point: grad phi / |grad phi| of the level set (Eq. normal_vector), or,
 // when a nodal normal field is set (e.g. the projected normal of Eq. normal_vector_regularized), its normalized
-// interpolant (ls_frozen_normal).  The FP64 advection runs in double-float arithmetic (k_levelset_advect_df: the FP64
-// pipe bounds the FP64 version); the reinitialization operators stay in FP64.
+// interpolant (ls_frozen_normal).  The FP64 advection runs in double-float arithmetic (the FP64 pipe bounds the FP64
+// version), sum-factorized (k_levelset_advect_sf; k_levelset_advect_df evaluates the same sums directly); the
+// reinitialization operators stay in FP64.
 #include <type_traits>
 
 #include "dfloat.cuh"
@@ -168,6 +169,143 @@ __global__ void __launch_bounds__(128) k_levelset_advect_df(MeshArgs<double> m, 
     for (int j = 0; j < 8; ++j) acc_add(&y[node[j]], df_to_double(df_norm(out[j])), DET);
 }
 
+// The same operator by sum factorization: the trilinear interpolation of x and u_Gamma to the 2^3 Gauss points and
+// the testing with the shape functions as three 1D sweeps of the 2 x 2 matrix N[q][j] (N_0 = 1 - t, N_1 = t at the
+// Gauss points t), the reference gradient of x as differences along its own direction interpolated along the other
+// two: 132 two-term double-float dot products per cell in place of the direct sums' 8 x 7 eight-term ones.
+constexpr float dfc_hi(double v) { return (float)v; }
+constexpr float dfc_lo(double v) { return (float)(v - (double)(float)v); }
+__device__ __forceinline__ dfl dot2(dfl c0, dfl v0, dfl c1, dfl v1) {
+    dfl s = df_prod(c0, v0);
+    df_fma(s, c1, v1);
+    return df_norm(s);
+}
+template <bool DET>
+__global__ void __launch_bounds__(128) k_levelset_advect_sf(MeshArgs<double> m, dfl W, dfl thdt_ih,
+                                                            const float2* __restrict__ ug, const double* __restrict__ x,
+                                                            double* __restrict__ y, int colour) {
+    int cx, cy, cz;
+    if constexpr (DET) {
+        if (!colour_cell(blockIdx.x * (int64_t)blockDim.x + threadIdx.x, m.n, colour, cx, cy, cz)) return;
+    } else {
+        const int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+        if (cell >= m.ncell) return;
+        cx = (int)(cell % m.n), cy = (int)((cell / m.n) % m.n), cz = (int)(cell / ((int64_t)m.n * m.n));
+    }
+    constexpr double t0 = g2_point(0), t1 = g2_point(1);
+    // N[q][j]: shape function j (0: 1 - t, 1: t) at Gauss point q
+    const dfl N[2][2] = {{{dfc_hi(1.0 - t0), dfc_lo(1.0 - t0)}, {dfc_hi(t0), dfc_lo(t0)}},
+                         {{dfc_hi(1.0 - t1), dfc_lo(1.0 - t1)}, {dfc_hi(t1), dfc_lo(t1)}}};
+    const int n = m.n;
+    const int64_t m1 = n + 1;
+    int64_t node[8];  // j = ja + 2 jb + 4 jc
+#pragma unroll
+    for (int j = 0; j < 8; ++j) node[j] = (cx + (j & 1)) + m1 * ((cy + ((j >> 1) & 1)) + m1 * (cz + (j >> 2)));
+    // values of a nodal field at the points q = qx + 2 qy + 4 qz
+    auto interp = [&](const dfl* f, dfl* out) {
+        dfl fx[8], fxy[8];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int q = 0; q < 2; ++q) fx[q + 2 * r] = dot2(N[q][0], f[2 * r], N[q][1], f[2 * r + 1]);
+#pragma unroll
+        for (int jc = 0; jc < 2; ++jc)
+#pragma unroll
+            for (int qy = 0; qy < 2; ++qy)
+#pragma unroll
+                for (int qx = 0; qx < 2; ++qx)
+                    fxy[qx + 2 * (qy + 2 * jc)] = dot2(N[qy][0], fx[qx + 2 * (0 + 2 * jc)], N[qy][1], fx[qx + 2 * (1 + 2 * jc)]);
+#pragma unroll
+        for (int qz = 0; qz < 2; ++qz)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) out[r + 4 * qz] = dot2(N[qz][0], fxy[r], N[qz][1], fxy[r + 4]);
+    };
+    dfl X[8], GXx[4], GXy[4], GXz[4];  // GXx[qy + 2 qz], GXy[qx + 2 qz], GXz[qx + 2 qy] (reference gradient)
+    {
+        dfl f[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) f[j] = df_from_double(x[node[j]]);
+        dfl fx[8], dx[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+#pragma unroll
+            for (int q = 0; q < 2; ++q) fx[q + 2 * r] = dot2(N[q][0], f[2 * r], N[q][1], f[2 * r + 1]);
+            dx[r] = df_sub(f[2 * r + 1], f[2 * r]);  // r = jb + 2 jc
+        }
+        dfl fxy[8], dxb[4], dy[4];
+#pragma unroll
+        for (int jc = 0; jc < 2; ++jc) {
+#pragma unroll
+            for (int qy = 0; qy < 2; ++qy) {
+#pragma unroll
+                for (int qx = 0; qx < 2; ++qx)
+                    fxy[qx + 2 * (qy + 2 * jc)] = dot2(N[qy][0], fx[qx + 2 * (0 + 2 * jc)], N[qy][1], fx[qx + 2 * (1 + 2 * jc)]);
+                dxb[qy + 2 * jc] = dot2(N[qy][0], dx[0 + 2 * jc], N[qy][1], dx[1 + 2 * jc]);
+            }
+#pragma unroll
+            for (int qx = 0; qx < 2; ++qx) dy[qx + 2 * jc] = df_sub(fx[qx + 2 * (1 + 2 * jc)], fx[qx + 2 * (0 + 2 * jc)]);
+        }
+#pragma unroll
+        for (int qz = 0; qz < 2; ++qz) {
+#pragma unroll
+            for (int r = 0; r < 4; ++r) X[r + 4 * qz] = dot2(N[qz][0], fxy[r], N[qz][1], fxy[r + 4]);
+#pragma unroll
+            for (int qy = 0; qy < 2; ++qy) GXx[qy + 2 * qz] = dot2(N[qz][0], dxb[qy], N[qz][1], dxb[qy + 2]);
+#pragma unroll
+            for (int qx = 0; qx < 2; ++qx) GXy[qx + 2 * qz] = dot2(N[qz][0], dy[qx], N[qz][1], dy[qx + 2]);
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) GXz[r] = df_sub(fxy[r + 4], fxy[r]);
+    }
+    dfl Fv[8];
+    {
+        dfl U[3][8];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            dfl f[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) f[j] = ld_df(ug + d * m.Nphi + node[j]);
+            interp(f, U[d]);
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int qx = q & 1, qy = (q >> 1) & 1, qz = q >> 2;
+            dfl ug_gx = df_prod(U[0][q], GXx[qy + 2 * qz]);
+            df_fma(ug_gx, U[1][q], GXy[qx + 2 * qz]);
+            df_fma(ug_gx, U[2][q], GXz[qx + 2 * qy]);
+            dfl v = X[q];
+            df_fma(v, thdt_ih, df_norm(ug_gx));
+            Fv[q] = df_mul(W, df_norm(v));
+        }
+    }
+    // test: out_j = sum_q N_j(q) Fv_q by the transposed sweeps z, y, x
+    dfl T1[8], T2[8];
+#pragma unroll
+    for (int jc = 0; jc < 2; ++jc)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) T1[r + 4 * jc] = dot2(N[0][jc], Fv[r], N[1][jc], Fv[r + 4]);  // r = qx + 2 qy
+#pragma unroll
+    for (int jc = 0; jc < 2; ++jc)
+#pragma unroll
+        for (int jb = 0; jb < 2; ++jb)
+#pragma unroll
+            for (int qx = 0; qx < 2; ++qx)
+                T2[qx + 2 * (jb + 2 * jc)] = dot2(N[0][jb], T1[qx + 2 * (0 + 2 * jc)], N[1][jb], T1[qx + 2 * (1 + 2 * jc)]);
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int ja = 0; ja < 2; ++ja) {
+            const dfl o = dot2(N[0][ja], T2[2 * r], N[1][ja], T2[2 * r + 1]);
+            acc_add(&y[node[ja + 2 * r]], df_to_double(o), DET);
+        }
+}
+
+// Level-set advection kernel: 1 the sum-factorized k_levelset_advect_sf, 0 the direct sums of k_levelset_advect_df.
+// Measured at 64^3 (275 k DoFs, 100 back-to-back applies): 45.2 against 57.8 us per apply.
+#ifndef EVAP_LS_SF
+#define EVAP_LS_SF 1
+#endif
+
 template <typename T>
 int launch_levelset(evap_mesh* h, int mode, const T* x, T* y, cudaStream_t s) {
     const MeshArgs<T> m = ls_args<T>(h);  // Q1 on the level-set mesh
@@ -191,7 +329,8 @@ int launch_levelset(evap_mesh* h, int mode, const T* x, T* y, cudaStream_t s) {
                 if (mode == EVAP_ADVECT) {  // FP64-accurate advection in double-float arithmetic
                     const dfl W = df_from_double(0.125 * (double)m.vol_w);  // 2-point Gauss weights 1/2 per direction
                     const dfl thdt_ih = df_from_double((double)m.theta * (double)m.dt * (double)m.inv_h);
-                    k_levelset_advect_df<DET><<<grid, threads, 0, s>>>(m, W, thdt_ih, (const float2*)h->ugammadf,
+                    (EVAP_LS_SF ? k_levelset_advect_sf<DET> : k_levelset_advect_df<DET>)<<<grid, threads, 0, s>>>(
+                        m, W, thdt_ih, (const float2*)h->ugammadf,
                                                                        (const double*)x, (double*)y, colour);
                     done = true;
                 }
